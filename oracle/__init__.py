@@ -1,0 +1,250 @@
+"""FP64 CPU oracle of the 1d3v PIC/MCC cycle and of test-particle transport.
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline / reference legs of ``bench.py``.  The product path
+(``paper_1607_04069_gb300``) never imports this package, and this package
+never imports the product path.  The C source ``pic_oracle.c`` is the
+definition; this module only compiles it with gcc and marshals numpy arrays.
+
+Paper: Trieschmann, Schmidt & Mussenbrock, arXiv:1607.04069, Sec. "Kinetic
+Particle Simulation", "Particle-In-Cell Scheme" and "Test Particle Method".
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pic_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# counter slots of orc_counters (same order as the enum in pic_oracle.c)
+COUNTERS = ["n_e", "n_i", "n_tp", "imp_e_l", "imp_e_r", "imp_i_l", "imp_i_r", "ionizations",
+            "sputtered_l", "sputtered_r", "tp_dep_l", "tp_dep_r", "numerics", "elastic",
+            "excitation", "cx", "iso", "tp_coll", "capacity"]
+
+DIAG = {"phi": 0, "n_e": 1, "n_i": 2, "gamma_e": 3, "gamma_i": 4, "eedf": 5, "iedf_l": 6,
+        "iedf_r": 7, "ieadf_l": 8, "ieadf_r": 9, "sputter_e_l": 10, "sputter_e_r": 11,
+        "sputter_ang_l": 12, "sputter_ang_r": 13, "tp_dens": 14, "tp_vx": 15}
+
+E, I, TP = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into oracle/_build/liboracle.so (plain gcc, -O2,
+    no FMA contraction so every product and sum rounds as written)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+           "-shared", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class Params(C.Structure):
+    """Mirror of ``orc_params`` in pic_oracle.c."""
+    _fields_ = [("L", C.c_double), ("p", C.c_double), ("Tg", C.c_double), ("f", C.c_double),
+                ("V0", C.c_double), ("w", C.c_double), ("dt", C.c_double),
+                ("te0", C.c_double), ("ti0", C.c_double), ("tp_dt", C.c_double),
+                ("sigma_tp", C.c_double), ("seed", C.c_uint64), ("ncell", C.c_int32),
+                ("sputter", C.c_int32), ("tp_every", C.c_int32), ("diag_every", C.c_int32)]
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            vp, i64, i32, u32, dbl = C.c_void_p, C.c_int64, C.c_int32, C.c_uint32, C.c_double
+            sig = {
+                "orc_philox": (None, [vp, vp, vp]),
+                "orc_sigma_e": (None, [dbl, vp]),
+                "orc_sigma_i": (dbl, [dbl]),
+                "orc_yield": (dbl, [dbl]),
+                "orc_emit": (None, [dbl, dbl, dbl, dbl, dbl, vp]),
+                "orc_deposit": (None, [vp, i64, i32, vp]),
+                "orc_poisson": (None, [i32, dbl, dbl, vp, vp, dbl, vp, vp]),
+                "orc_create": (vp, [C.POINTER(Params), i64, i64, i64]),
+                "orc_destroy": (None, [vp]),
+                "orc_derived": (None, [vp, vp]),
+                "orc_init_species": (None, [vp, C.c_int, i64, dbl]),
+                "orc_set_species": (C.c_int, [vp, C.c_int, i64, vp, vp, vp, vp, vp]),
+                "orc_get_species": (i64, [vp, C.c_int, i64, vp, vp, vp, vp, vp]),
+                "orc_field": (None, [vp]),
+                "orc_get_field": (None, [vp, vp, vp, vp, vp]),
+                "orc_set_field": (None, [vp, vp]),
+                "orc_counters": (None, [vp, vp]),
+                "orc_step": (None, [vp, i64]),
+                "orc_tp_step": (None, [vp, i64, dbl]),
+                "orc_tp_launch": (None, [vp, i64, dbl]),
+                "orc_diag": (i64, [vp, C.c_int, vp, i64]),
+                "orc_reset_averages": (None, [vp]),
+                "orc_get_step": (u32, [vp]),
+                "orc_set_step": (None, [vp, u32]),
+                "orc_get_tp_step": (u32, [vp]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+# ---------------------------------------------------------------- primitives
+def philox(ctr, key):
+    """Philox4x32-10 block: 4 counter words, 2 key words -> 4 words."""
+    c = np.asarray(ctr, dtype=np.uint32).copy()
+    k = np.asarray(key, dtype=np.uint32).copy()
+    out = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox(_p(c), _p(k), _p(out))
+    return out
+
+
+def sigma_e(eps):
+    out = np.zeros(3)
+    lib().orc_sigma_e(float(eps), _p(out))
+    return out
+
+
+def sigma_i(eps):
+    return lib().orc_sigma_i(float(eps))
+
+
+def sputter_yield(E):
+    return lib().orc_yield(float(E))
+
+
+def emit(uE, uT, uP, Emax, direction=1.0):
+    out = np.zeros(3)
+    lib().orc_emit(float(uE), float(uT), float(uP), float(Emax), float(direction), _p(out))
+    return out
+
+
+def deposit(xi, ncell):
+    """CIC deposit of positions given in cell units; int64[ncell+1] result."""
+    xi = np.ascontiguousarray(xi, dtype=np.float64)
+    q = np.zeros(ncell + 1, dtype=np.int64)
+    lib().orc_deposit(_p(xi), xi.size, int(ncell), _p(q))
+    return q
+
+
+def poisson(ncell, dx, w, q_i, q_e, v_left):
+    q_i = np.ascontiguousarray(q_i, dtype=np.int64)
+    q_e = np.ascontiguousarray(q_e, dtype=np.int64)
+    phi = np.zeros(ncell + 1)
+    E = np.zeros(ncell + 1)
+    lib().orc_poisson(int(ncell), float(dx), float(w), _p(q_i), _p(q_e), float(v_left),
+                      _p(phi), _p(E))
+    return phi, E
+
+
+# ---------------------------------------------------------------- simulation
+class Oracle:
+    """One discharge in the oracle.  ``prm`` is a dict with the keys of
+    :class:`Params` (SI units, temperatures of the initial loading in eV)."""
+
+    def __init__(self, prm: dict, cap_e: int, cap_i: int, cap_tp: int = 0):
+        self.prm = dict(prm)
+        P = Params()
+        for name, _ in Params._fields_:
+            setattr(P, name, prm.get(name, 0))
+        self._P = P
+        self.ncell = int(prm["ncell"])
+        self.h = lib().orc_create(C.byref(P), int(cap_e), int(cap_i), int(cap_tp))
+        self.cap = [int(cap_e), int(cap_i), int(cap_tp)]
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            lib().orc_destroy(h)
+            self.h = None
+
+    def derived(self):
+        out = np.zeros(8)
+        lib().orc_derived(self.h, _p(out))
+        keys = ["n_gas", "dx", "nu_max_e", "nu_max_i", "p_max_e", "p_max_i", "eps_max", "lambda"]
+        return dict(zip(keys, out.tolist()))
+
+    def init_species(self, s, n, T_eV):
+        lib().orc_init_species(self.h, int(s), int(n), float(T_eV))
+
+    def set_species(self, s, xi, vx, vy, vz, ids):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (xi, vx, vy, vz)]
+        ids = np.ascontiguousarray(ids, dtype=np.uint64)
+        rc = lib().orc_set_species(self.h, int(s), ids.size, *[_p(a) for a in arrs], _p(ids))
+        if rc != 0:
+            raise ValueError("capacity exceeded")
+
+    def get_species(self, s):
+        cap = self.cap[s]
+        out = [np.zeros(cap) for _ in range(4)]
+        ids = np.zeros(cap, dtype=np.uint64)
+        n = lib().orc_get_species(self.h, int(s), cap, *[_p(a) for a in out], _p(ids))
+        return {"xi": out[0][:n], "vx": out[1][:n], "vy": out[2][:n], "vz": out[3][:n],
+                "id": ids[:n]}
+
+    def field(self):
+        lib().orc_field(self.h)
+
+    def get_field(self):
+        n = self.ncell + 1
+        E, phi = np.zeros(n), np.zeros(n)
+        qe, qi = np.zeros(n, dtype=np.int64), np.zeros(n, dtype=np.int64)
+        lib().orc_get_field(self.h, _p(E), _p(phi), _p(qe), _p(qi))
+        return {"E": E, "phi": phi, "q_e": qe, "q_i": qi}
+
+    def set_field(self, E):
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        lib().orc_set_field(self.h, _p(E))
+
+    def counters(self):
+        out = np.zeros(len(COUNTERS), dtype=np.int64)
+        lib().orc_counters(self.h, _p(out))
+        return dict(zip(COUNTERS, out.tolist()))
+
+    def step(self, n=1):
+        lib().orc_step(self.h, int(n))
+
+    def tp_step(self, n, dt_tp):
+        lib().orc_tp_step(self.h, int(n), float(dt_tp))
+
+    def tp_launch(self, n, E_ion):
+        lib().orc_tp_launch(self.h, int(n), float(E_ion))
+
+    def diag(self, kind):
+        k = DIAG[kind] if isinstance(kind, str) else int(kind)
+        cap = 128 * 90 + 16
+        out = np.zeros(max(cap, self.ncell + 1))
+        n = lib().orc_diag(self.h, k, _p(out), out.size)
+        return out[:n].copy()
+
+    def reset_averages(self):
+        lib().orc_reset_averages(self.h)
+
+    @property
+    def step_index(self):
+        return int(lib().orc_get_step(self.h))
+
+    @step_index.setter
+    def step_index(self, l):
+        lib().orc_set_step(self.h, int(l))
+
+    @property
+    def tp_step_index(self):
+        return int(lib().orc_get_tp_step(self.h))

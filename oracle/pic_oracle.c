@@ -1,0 +1,841 @@
+/*
+ * pic_oracle.c -- plain, slow, FP64 CPU oracle of the 1d3v electrostatic
+ * particle-in-cell / Monte Carlo collision (PIC/MCC) cycle and of the
+ * test-particle (TP) transport of sputtered atoms described in
+ * Trieschmann, Schmidt & Mussenbrock, "Particle-in-Cell/Test-Particle
+ * Simulations of Technological Plasmas" (arXiv:1607.04069).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path calls this file:
+ * it exists so that tests, the smoke check and the CPU-baseline leg of the
+ * benchmark can check the CUDA path against an independent implementation.
+ * It shares no code, header, table or constant with the CUDA path; both are
+ * written from the same paper and the same readings of it.
+ *
+ * Style: every particle is processed in index order with plain loops; no
+ * blocking, no fusion, no reordering beyond what the paper's cycle states
+ * (Sec. "Particle-In-Cell Scheme", Fig. 4: charge assignment -> field solve
+ * -> field interpolation -> push -> wall interaction -> collisions).
+ *
+ * Positions are kept in units of the cell size, xi = x / dx, so that the
+ * linear-weighting rule (Sec. "Charge Assignment") is evaluated exactly for
+ * positions that the GPU path stores as 32-bit fixed point.
+ *
+ * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), counter
+ * (id_lo, id_hi, step, purpose), key (seed_lo, seed_hi).  The purpose codes
+ * are listed below; they define which random word is used for what.
+ *
+ * Parity pins for every function here live in tests/test_oracle_pins.py.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---- physical constants (CODATA 2018 exact/recommended values) ---- */
+#define O_QE 1.602176634e-19      /* elementary charge, C          */
+#define O_ME 9.1093837015e-31     /* electron mass, kg             */
+#define O_AMU 1.66053906660e-27   /* atomic mass unit, kg          */
+#define O_KB 1.380649e-23         /* Boltzmann constant, J/K       */
+#define O_EPS0 8.8541878128e-12   /* vacuum permittivity, F/m      */
+#define O_PI 3.14159265358979323846
+#define O_MAR (39.948 * O_AMU)    /* argon atom / ion mass         */
+#define O_MAL (26.98 * O_AMU)     /* aluminium atom mass           */
+
+/* ---- analytic cross sections and surface model (readings of the paper) ---- */
+#define O_SIG_EL 1e-19            /* e-Ar elastic, m^2, constant          */
+#define O_EXC_TH 11.5             /* e-Ar excitation threshold, eV        */
+#define O_EXC_SIG 1e-20           /* excitation magnitude scale, m^2      */
+#define O_ION_TH 15.8             /* e-Ar ionisation threshold, eV        */
+#define O_LOTZ_A 4.5e-18          /* Lotz constant a, m^2 eV^2            */
+#define O_LOTZ_Q 6.0              /* Lotz shell occupation q              */
+#define O_ARP_SIG 5e-19           /* Ar+-Ar iso and CX: 5e-19 (1eV/eps)^.5 */
+#define O_UB 3.4                  /* Al surface binding energy, eV        */
+#define O_SP_TH 30.0              /* sputter threshold, eV                */
+#define O_SP_MAXN 16              /* at most 16 sputter trials per impact */
+
+/* ---- random-stream purposes (the third/fourth counter words) ---- */
+enum {
+    PUR_INIT = 1,        /* initial loading: step word 0 and 1          */
+    PUR_COLL = 2,        /* per-step candidate test, process, direction */
+    PUR_IONIZE = 3,      /* ionisation energy split, ejected direction  */
+    PUR_NEWION = 4,      /* Maxwellian velocity of the newborn ion      */
+    PUR_BIRTH_ID = 5,    /* ids of the ionisation children              */
+    PUR_GAS = 6,         /* gas partner of an Ar+ collision             */
+    PUR_SP_TRIAL = 16,   /* +k/4: sputter trials                        */
+    PUR_SP_EMIT = 32,    /* +k: energy/angle of the k-th sputtered atom */
+    PUR_SP_ID = 48,      /* +k: id of the k-th sputtered atom           */
+    PUR_TP_GAS = 64,     /* gas partner of a TP step                    */
+    PUR_TP_COLL = 65,    /* TP collision test and scattering direction  */
+    PUR_TP_LAUNCH = 66   /* mono-energetic source launch                */
+};
+
+/* species and id tags (top two bits of the 64-bit id) */
+#define SP_E 0
+#define SP_I 1
+#define SP_TP 2
+static const uint64_t TAG[3] = {0ull, 1ull << 62, 2ull << 62};
+#define ID_MASK ((1ull << 62) - 1)
+
+/* histogram shapes */
+#define NB_IEDF 512    /* ion energy, [0, 2 V0] eV            */
+#define NB_IEADF_E 128 /* IEADF energy bins, [0, 2 V0] eV     */
+#define NB_ANG 90      /* 1-degree angle bins, [0, 90) deg     */
+#define NB_EEDF 256    /* 0.25 eV bins, [0, 64) eV             */
+#define NB_SPE 600     /* 0.5 eV bins, [0, 300) eV              */
+
+/* counters exported by orc_counters() */
+enum {
+    C_NE, C_NI, C_NTP, C_IMP_E_L, C_IMP_E_R, C_IMP_I_L, C_IMP_I_R, C_IONIZ,
+    C_SPUT_L, C_SPUT_R, C_TPDEP_L, C_TPDEP_R, C_NUMERICS, C_ELASTIC, C_EXCIT,
+    C_CX, C_ISO, C_TPCOLL, C_CAPACITY, C_NCOUNT
+};
+
+/* Discharge parameters (SI units unless marked). */
+typedef struct {
+    double L, p, Tg, f, V0;       /* gap, pressure, gas T, RF frequency, amplitude */
+    double w, dt;                 /* superparticle weight (1/m^2), time step       */
+    double te0, ti0;              /* initial temperatures, eV                      */
+    double tp_dt, sigma_tp;       /* TP time step for orc_tp_step, hard-sphere xs  */
+    uint64_t seed;
+    int32_t ncell;                /* N cells, N+1 nodes                            */
+    int32_t sputter;              /* ion impacts launch sputtered atoms            */
+    int32_t tp_every;             /* coupled TP sub-cycle (0: no coupled TP)       */
+    int32_t diag_every;           /* flux / EEDF sampling stride                   */
+} orc_params;
+
+typedef struct {
+    int64_t n, cap;
+    double *xi, *vx, *vy, *vz;
+    uint64_t *id;
+    uint8_t *alive;
+} orc_sp;
+
+typedef struct {
+    orc_params P;
+    orc_sp sp[3];
+    double *E, *phi;
+    int64_t *q[2];
+    uint32_t step, tp_step;
+    /* derived quantities */
+    double ngas, dx, nu_max_e, nu_max_i, p_max_e, p_max_i, eps_max;
+    /* diagnostics */
+    double *sum_q[2], *sum_phi, *sum_flux[2], *tp_dens, *tp_vx;
+    int64_t n_avg, n_flux, n_tp_samp;
+    int64_t *iedf[2], *ieadf[2], *eedf, *sp_e[2], *sp_ang[2];
+    int64_t cnt[C_NCOUNT];
+} orc_state;
+
+/* ======================= Philox4x32-10 (Salmon et al. 2011) ============== */
+void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; r++) {
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static void draw(uint64_t seed, uint64_t id, uint32_t step, uint32_t purpose, uint32_t out[4])
+{
+    uint32_t ctr[4] = {(uint32_t)id, (uint32_t)(id >> 32), step, purpose};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    orc_philox(ctr, key, out);
+}
+
+/* uniform in (0,1): the top 23 bits of a word plus one half, times 2^-23 */
+static double u23(uint32_t w) { return ((double)(w >> 9) + 0.5) * 0x1p-23; }
+
+/* Box-Muller (Sec. "Kinetic Particle Simulation": Maxwellian sampling) */
+static void box_muller(uint32_t a, uint32_t b, double *n1, double *n2)
+{
+    double r = sqrt(-2.0 * log(u23(a)));
+    double t = 2.0 * O_PI * u23(b);
+    *n1 = r * cos(t);
+    *n2 = r * sin(t);
+}
+
+/* uniform direction on the unit sphere: cos(theta) = 1 - 2R, phi = 2 pi R */
+static void iso_dir(uint32_t a, uint32_t b, double d[3])
+{
+    double c = 1.0 - 2.0 * u23(a);
+    double s = sqrt(fmax(0.0, 1.0 - c * c));
+    double ph = 2.0 * O_PI * u23(b);
+    d[0] = c; d[1] = s * cos(ph); d[2] = s * sin(ph);
+}
+
+static uint64_t child_id(uint32_t lo, uint32_t hi, int species)
+{
+    return ((((uint64_t)hi << 32) | lo) & ID_MASK) | TAG[species];
+}
+
+/* ======================= cross sections ================================== */
+/* electron-argon, eps in eV, result in m^2 (Sec. "Particle Collisions") */
+void orc_sigma_e(double eps, double out[3])
+{
+    out[0] = O_SIG_EL;
+    out[1] = eps > O_EXC_TH ? O_EXC_SIG * (1.0 - O_EXC_TH / eps) : 0.0;
+    out[2] = eps > O_ION_TH ? O_LOTZ_A * O_LOTZ_Q * log(eps / O_ION_TH) / (eps * O_ION_TH) : 0.0;
+}
+
+/* Ar+-Ar isotropic and charge exchange (each channel), eps in eV */
+double orc_sigma_i(double eps) { return O_ARP_SIG * sqrt(1.0 / eps); }
+
+/* sputter yield of Al by Ar+ at normal incidence, E in eV */
+double orc_yield(double E) { return E > O_SP_TH ? 0.1 * sqrt(E / O_SP_TH - 1.0) : 0.0; }
+
+/* maximum fraction of energy passed in a binary Ar -> Al collision */
+static double lambda_ar_al(void) { return 4.0 * O_MAR * O_MAL / ((O_MAR + O_MAL) * (O_MAR + O_MAL)); }
+
+/* Sigmund-Thompson energy E/(E+Ub)^3 truncated at Emax and cosine angle
+ * (Sec. "Wall Interactions" of the TPM): energy from the inverse of the
+ * truncated CDF (E/(E+Ub))^2, polar angle theta = arccos(sqrt(R)), azimuth
+ * 2 pi R.  dir = +1 launches into +x (left electrode), -1 into -x. */
+void orc_emit(double uE, double uT, double uP, double Emax, double dir, double v[3])
+{
+    double Fmax = (Emax / (Emax + O_UB)) * (Emax / (Emax + O_UB));
+    double s = sqrt(uE * Fmax);
+    double Es = O_UB * s / (1.0 - s);
+    double speed = sqrt(2.0 * Es * O_QE / O_MAL);
+    double ct = sqrt(uT);
+    double st = sqrt(fmax(0.0, 1.0 - uT));
+    double ps = 2.0 * O_PI * uP;
+    v[0] = dir * speed * ct;
+    v[1] = speed * st * cos(ps);
+    v[2] = speed * st * sin(ps);
+}
+
+/* ======================= charge assignment =============================== */
+/* Linear (cloud-in-cell) weighting (Sec. "Charge Assignment"): a particle
+ * at xi in cell j = floor(xi), f = xi - j, gives 2^32 - floor(f 2^32) to node
+ * j and floor(f 2^32) to node j+1, so each particle deposits exactly 2^32.
+ * Particles with xi < 0 are treated as removed. */
+void orc_deposit(const double *xi, int64_t n, int32_t ncell, int64_t *q)
+{
+    for (int64_t k = 0; k < n; k++) {
+        if (!(xi[k] >= 0.0)) continue;
+        double j = floor(xi[k]);
+        double f = xi[k] - j;
+        int64_t wr = (int64_t)floor(f * 4294967296.0);
+        int64_t wl = 4294967296LL - wr;
+        int64_t m = (int64_t)j;
+        if (m < 0 || m >= ncell) continue;
+        q[m] += wl;
+        q[m + 1] += wr;
+    }
+}
+
+/* ======================= field solve ===================================== */
+/* Poisson (Sec. "EM Field Solver"): (phi[m+1] - 2 phi[m] + phi[m-1])/dx^2 =
+ * -rho[m]/eps0 on interior nodes, phi[0] = v_left, phi[N] = 0, solved with
+ * the Thomas algorithm.  rho[m] = e w (q_i - q_e) / (2^32 V_m) with node
+ * volume V_m = dx inside and dx/2 on the electrodes.  E[m] = -(phi[m+1] -
+ * phi[m-1])/(2 dx) inside; on the electrodes Gauss's law over the half cell. */
+void orc_poisson(int32_t N, double dx, double w, const int64_t *q_i, const int64_t *q_e,
+                 double v_left, double *phi, double *E)
+{
+    double *rho = (double *)malloc(sizeof(double) * (N + 1));
+    double *cp = (double *)malloc(sizeof(double) * (N + 1));
+    double *dp = (double *)malloc(sizeof(double) * (N + 1));
+    for (int m = 0; m <= N; m++) {
+        double vol = (m == 0 || m == N) ? 0.5 * dx : dx;
+        rho[m] = O_QE * w * (double)(q_i[m] - q_e[m]) / (4294967296.0 * vol);
+    }
+    phi[0] = v_left;
+    phi[N] = 0.0;
+    if (N >= 2) {
+        /* rows m = 1..N-1: a = 1, b = -2, c = 1 */
+        for (int m = 1; m <= N - 1; m++) {
+            double d = -dx * dx * rho[m] / O_EPS0;
+            if (m == 1) d -= phi[0];
+            if (m == N - 1) d -= phi[N];
+            if (m == 1) {
+                cp[m] = 1.0 / -2.0;
+                dp[m] = d / -2.0;
+            } else {
+                double den = -2.0 - cp[m - 1];
+                cp[m] = 1.0 / den;
+                dp[m] = (d - dp[m - 1]) / den;
+            }
+        }
+        phi[N - 1] = dp[N - 1];
+        for (int m = N - 2; m >= 1; m--) phi[m] = dp[m] - cp[m] * phi[m + 1];
+    }
+    for (int m = 1; m <= N - 1; m++) E[m] = -(phi[m + 1] - phi[m - 1]) / (2.0 * dx);
+    E[0] = (phi[0] - phi[1]) / dx - rho[0] * dx / (2.0 * O_EPS0);
+    E[N] = (phi[N - 1] - phi[N]) / dx + rho[N] * dx / (2.0 * O_EPS0);
+    free(rho); free(cp); free(dp);
+}
+
+/* ======================= state =========================================== */
+static void sp_alloc(orc_sp *s, int64_t cap)
+{
+    s->n = 0; s->cap = cap;
+    s->xi = (double *)calloc(cap ? cap : 1, sizeof(double));
+    s->vx = (double *)calloc(cap ? cap : 1, sizeof(double));
+    s->vy = (double *)calloc(cap ? cap : 1, sizeof(double));
+    s->vz = (double *)calloc(cap ? cap : 1, sizeof(double));
+    s->id = (uint64_t *)calloc(cap ? cap : 1, sizeof(uint64_t));
+    s->alive = (uint8_t *)calloc(cap ? cap : 1, 1);
+}
+
+static void sp_free(orc_sp *s)
+{
+    free(s->xi); free(s->vx); free(s->vy); free(s->vz); free(s->id); free(s->alive);
+}
+
+static double mass_of(int s) { return s == SP_E ? O_ME : (s == SP_I ? O_MAR : O_MAL); }
+static double charge_of(int s) { return s == SP_E ? -O_QE : (s == SP_I ? O_QE : 0.0); }
+
+static int64_t append(orc_state *S, int s, double xi, double vx, double vy, double vz, uint64_t id)
+{
+    orc_sp *p = &S->sp[s];
+    if (p->n >= p->cap) { S->cnt[C_CAPACITY]++; return -1; }
+    int64_t k = p->n++;
+    p->xi[k] = xi; p->vx[k] = vx; p->vy[k] = vy; p->vz[k] = vz; p->id[k] = id; p->alive[k] = 1;
+    return k;
+}
+
+static double v_rf(const orc_state *S, uint32_t l)
+{
+    return S->P.V0 * sin(2.0 * O_PI * S->P.f * (double)l * S->P.dt);
+}
+
+/* deposit both charged species and solve the field for time step l */
+static void field_for_step(orc_state *S, uint32_t l)
+{
+    int N = S->P.ncell;
+    for (int s = 0; s < 2; s++) {
+        memset(S->q[s], 0, sizeof(int64_t) * (N + 1));
+        orc_sp *p = &S->sp[s];
+        for (int64_t k = 0; k < p->n; k++) {
+            if (!p->alive[k]) continue;
+            orc_deposit(&p->xi[k], 1, N, S->q[s]);
+        }
+    }
+    orc_poisson(N, S->dx, S->P.w, S->q[SP_I], S->q[SP_E], v_rf(S, l), S->phi, S->E);
+}
+
+/* derived quantities of the null-collision method (Sec. "Particle
+ * Collisions"): nu_max is the maximum over energy of n sigma_sum(eps)
+ * sqrt(2 eps / m_r).  Electrons: the sum of the closed-form maxima of the
+ * three cross sections at the highest admitted energy eps_max = 2 V0 + 100 eV.
+ * Ar+: sigma(eps) g is constant, so nu_max is exact. */
+static void derive(orc_state *S)
+{
+    orc_params *P = &S->P;
+    S->ngas = P->p / (O_KB * P->Tg);
+    S->dx = P->L / (double)P->ncell;
+    S->eps_max = 2.0 * P->V0 + 100.0;
+    double sig_ion_max = O_LOTZ_A * O_LOTZ_Q / (exp(1.0) * O_ION_TH * O_ION_TH);
+    double sig_sum_max = O_SIG_EL + O_EXC_SIG + sig_ion_max;
+    S->nu_max_e = S->ngas * sig_sum_max * sqrt(2.0 * S->eps_max * O_QE / O_ME);
+    double mr = O_MAR / 2.0;
+    S->nu_max_i = 2.0 * S->ngas * O_ARP_SIG * sqrt(2.0 * O_QE / mr);
+    S->p_max_e = 1.0 - exp(-S->nu_max_e * P->dt);
+    S->p_max_i = 1.0 - exp(-S->nu_max_i * P->dt);
+}
+
+orc_state *orc_create(const orc_params *P, int64_t cap_e, int64_t cap_i, int64_t cap_tp)
+{
+    orc_state *S = (orc_state *)calloc(1, sizeof(orc_state));
+    S->P = *P;
+    int N = P->ncell;
+    sp_alloc(&S->sp[SP_E], cap_e);
+    sp_alloc(&S->sp[SP_I], cap_i);
+    sp_alloc(&S->sp[SP_TP], cap_tp);
+    S->E = (double *)calloc(N + 1, sizeof(double));
+    S->phi = (double *)calloc(N + 1, sizeof(double));
+    for (int s = 0; s < 2; s++) {
+        S->q[s] = (int64_t *)calloc(N + 1, sizeof(int64_t));
+        S->sum_q[s] = (double *)calloc(N + 1, sizeof(double));
+        S->sum_flux[s] = (double *)calloc(N + 1, sizeof(double));
+        S->iedf[s] = (int64_t *)calloc(NB_IEDF, sizeof(int64_t));
+        S->ieadf[s] = (int64_t *)calloc(NB_IEADF_E * NB_ANG, sizeof(int64_t));
+        S->sp_e[s] = (int64_t *)calloc(NB_SPE, sizeof(int64_t));
+        S->sp_ang[s] = (int64_t *)calloc(NB_ANG, sizeof(int64_t));
+    }
+    S->sum_phi = (double *)calloc(N + 1, sizeof(double));
+    S->tp_dens = (double *)calloc(N + 1, sizeof(double));
+    S->tp_vx = (double *)calloc(N + 1, sizeof(double));
+    S->eedf = (int64_t *)calloc(NB_EEDF, sizeof(int64_t));
+    derive(S);
+    return S;
+}
+
+void orc_destroy(orc_state *S)
+{
+    if (!S) return;
+    for (int s = 0; s < 3; s++) sp_free(&S->sp[s]);
+    free(S->E); free(S->phi); free(S->sum_phi); free(S->tp_dens); free(S->tp_vx); free(S->eedf);
+    for (int s = 0; s < 2; s++) {
+        free(S->q[s]); free(S->sum_q[s]); free(S->sum_flux[s]); free(S->iedf[s]);
+        free(S->ieadf[s]); free(S->sp_e[s]); free(S->sp_ang[s]);
+    }
+    free(S);
+}
+
+void orc_derived(const orc_state *S, double out[8])
+{
+    out[0] = S->ngas; out[1] = S->dx; out[2] = S->nu_max_e; out[3] = S->nu_max_i;
+    out[4] = S->p_max_e; out[5] = S->p_max_i; out[6] = S->eps_max; out[7] = lambda_ar_al();
+}
+
+/* Initial loading (Sec. "Kinetic Particle Simulation"): positions uniform
+ * over the gap, velocities Maxwellian at temperature T (eV), by Box-Muller.
+ * The sampled velocity is taken as v^(-1/2).  Ids are tag | k. */
+void orc_init_species(orc_state *S, int s, int64_t n, double T_eV)
+{
+    orc_sp *p = &S->sp[s];
+    double vth = sqrt(T_eV * O_QE / mass_of(s));
+    double N = (double)S->P.ncell;
+    p->n = 0;
+    for (int64_t k = 0; k < n && k < p->cap; k++) {
+        uint64_t id = TAG[s] | (uint64_t)k;
+        uint32_t a[4], b[4];
+        draw(S->P.seed, id, 0, PUR_INIT, a);
+        draw(S->P.seed, id, 1, PUR_INIT, b);
+        double xi = N * (double)(a[0] | 1u) * 0x1p-32;
+        double n1, n2, n3, n4;
+        box_muller(a[1], a[2], &n1, &n2);
+        box_muller(b[0], b[1], &n3, &n4);
+        append(S, s, xi, vth * n1, vth * n2, vth * n3, id);
+    }
+}
+
+/* Load an arbitrary particle set (seeded synthetic inputs in tests). */
+int orc_set_species(orc_state *S, int s, int64_t n, const double *xi, const double *vx,
+                    const double *vy, const double *vz, const uint64_t *id)
+{
+    orc_sp *p = &S->sp[s];
+    if (n > p->cap) return -1;
+    p->n = 0;
+    for (int64_t k = 0; k < n; k++) append(S, s, xi[k], vx[k], vy[k], vz[k], id[k]);
+    for (int64_t k = 0; k < n; k++) p->alive[k] = xi[k] >= 0.0;
+    return 0;
+}
+
+/* Copy out the alive particles (index order). Returns the number copied. */
+int64_t orc_get_species(const orc_state *S, int s, int64_t cap, double *xi, double *vx,
+                        double *vy, double *vz, uint64_t *id)
+{
+    const orc_sp *p = &S->sp[s];
+    int64_t m = 0;
+    for (int64_t k = 0; k < p->n; k++) {
+        if (!p->alive[k]) continue;
+        if (m < cap) {
+            xi[m] = p->xi[k]; vx[m] = p->vx[k]; vy[m] = p->vy[k]; vz[m] = p->vz[k]; id[m] = p->id[k];
+        }
+        m++;
+    }
+    return m;
+}
+
+/* deposit + solve for the current state at the current step (creation) */
+void orc_field(orc_state *S) { field_for_step(S, S->step); }
+
+void orc_get_field(const orc_state *S, double *E, double *phi, int64_t *q_e, int64_t *q_i)
+{
+    int N = S->P.ncell;
+    memcpy(E, S->E, sizeof(double) * (N + 1));
+    memcpy(phi, S->phi, sizeof(double) * (N + 1));
+    memcpy(q_e, S->q[SP_E], sizeof(int64_t) * (N + 1));
+    memcpy(q_i, S->q[SP_I], sizeof(int64_t) * (N + 1));
+}
+
+void orc_set_field(orc_state *S, const double *E)
+{
+    memcpy(S->E, E, sizeof(double) * (S->P.ncell + 1));
+}
+
+void orc_counters(const orc_state *S, int64_t *out)
+{
+    for (int c = 0; c < C_NCOUNT; c++) out[c] = S->cnt[c];
+    for (int s = 0; s < 3; s++) {
+        int64_t a = 0;
+        for (int64_t k = 0; k < S->sp[s].n; k++) a += S->sp[s].alive[k];
+        out[C_NE + s] = a;
+    }
+}
+
+/* ======================= the PIC/MCC step ================================ */
+static void hist_add(int64_t *h, int nb, double x, double xmax)
+{
+    int b = (int)(x / xmax * (double)nb);
+    if (b < 0) b = 0;
+    if (b > nb - 1) b = nb - 1;
+    h[b]++;
+}
+
+/* sputter launch at an ion impact (Sec. "Wall Interactions" of the TPM):
+ * Y(E) = 0.1 sqrt(E/30 eV - 1) above 30 eV, N = ceil(Y) trials, each
+ * succeeding when R <= Y/N; each success inserts an atom at the impact
+ * point with a Thompson energy and a cosine angle, aimed into the gap. */
+static void sputter(orc_state *S, uint64_t ion_id, uint32_t l, double E, int electrode)
+{
+    double Y = orc_yield(E);
+    if (Y <= 0.0) return;
+    int Nt = (int)ceil(Y);
+    if (Nt > O_SP_MAXN) Nt = O_SP_MAXN;
+    double Emax = lambda_ar_al() * E;
+    double N = (double)S->P.ncell;
+    for (int k = 0; k < Nt; k++) {
+        uint32_t t[4];
+        draw(S->P.seed, ion_id, l, PUR_SP_TRIAL + (k >> 2), t);
+        if (!(u23(t[k & 3]) <= Y / (double)Nt)) continue;
+        uint32_t ce[4], ci[4];
+        draw(S->P.seed, ion_id, l, PUR_SP_EMIT + k, ce);
+        draw(S->P.seed, ion_id, l, PUR_SP_ID + k, ci);
+        double v[3];
+        orc_emit(u23(ce[0]), u23(ce[1]), u23(ce[2]), Emax, electrode == 0 ? 1.0 : -1.0, v);
+        double xi = electrode == 0 ? N * 0x1p-32 : N * (1.0 - 0x1p-32);
+        if (append(S, SP_TP, xi, v[0], v[1], v[2], child_id(ci[0], ci[1], SP_TP)) >= 0)
+            S->cnt[electrode == 0 ? C_SPUT_L : C_SPUT_R]++;
+    }
+}
+
+/* electron null-collision MCC for one particle (Sec. "Particle Collisions") */
+static void mcc_electron(orc_state *S, int64_t k, uint32_t l)
+{
+    orc_sp *p = &S->sp[SP_E];
+    uint32_t c[4];
+    draw(S->P.seed, p->id[k], l, PUR_COLL, c);
+    if (!((double)c[0] * 0x1p-32 < S->p_max_e)) return;     /* not a candidate */
+    double v2 = p->vx[k] * p->vx[k] + p->vy[k] * p->vy[k] + p->vz[k] * p->vz[k];
+    double v = sqrt(v2);
+    double eps = 0.5 * O_ME * v2 / O_QE;
+    if (eps > S->eps_max) S->cnt[C_NUMERICS]++;
+    double sg[3];
+    orc_sigma_e(eps, sg);
+    double nu_el = S->ngas * sg[0] * v;
+    double nu_exc = S->ngas * sg[1] * v;
+    double nu_ion = S->ngas * sg[2] * v;
+    double r = u23(c[1]) * S->nu_max_e;
+    double d[3];
+    iso_dir(c[2], c[3], d);
+    if (r < nu_el) {
+        double cchi = v > 0.0 ? (d[0] * p->vx[k] + d[1] * p->vy[k] + d[2] * p->vz[k]) / v : 1.0;
+        double fac = 1.0 - (2.0 * O_ME / O_MAR) * (1.0 - cchi);
+        double vn = v * sqrt(fac);
+        p->vx[k] = vn * d[0]; p->vy[k] = vn * d[1]; p->vz[k] = vn * d[2];
+        S->cnt[C_ELASTIC]++;
+    } else if (r < nu_el + nu_exc) {
+        double vn = sqrt(2.0 * (eps - O_EXC_TH) * O_QE / O_ME);
+        p->vx[k] = vn * d[0]; p->vy[k] = vn * d[1]; p->vz[k] = vn * d[2];
+        S->cnt[C_EXCIT]++;
+    } else if (r < nu_el + nu_exc + nu_ion) {
+        double epr = eps - O_ION_TH;
+        uint32_t ci[4], cn[4], cb[4];
+        draw(S->P.seed, p->id[k], l, PUR_IONIZE, ci);
+        draw(S->P.seed, p->id[k], l, PUR_NEWION, cn);
+        draw(S->P.seed, p->id[k], l, PUR_BIRTH_ID, cb);
+        double e_ej = u23(ci[0]) * epr;
+        double e_sc = epr - e_ej;
+        double vs = sqrt(2.0 * e_sc * O_QE / O_ME);
+        double ve = sqrt(2.0 * e_ej * O_QE / O_ME);
+        double d2[3];
+        iso_dir(ci[1], ci[2], d2);
+        double n1, n2, n3, n4;
+        box_muller(cn[0], cn[1], &n1, &n2);
+        box_muller(cn[2], cn[3], &n3, &n4);
+        double vg = sqrt(O_KB * S->P.Tg / O_MAR);
+        double xi = p->xi[k];
+        p->vx[k] = vs * d[0]; p->vy[k] = vs * d[1]; p->vz[k] = vs * d[2];
+        append(S, SP_E, xi, ve * d2[0], ve * d2[1], ve * d2[2], child_id(cb[0], cb[1], SP_E));
+        append(S, SP_I, xi, vg * n1, vg * n2, vg * n3, child_id(cb[2], cb[3], SP_I));
+        S->cnt[C_IONIZ]++;
+    }
+}
+
+/* Ar+ null-collision MCC with a thermal gas partner (Sec. "Kinetic Particle
+ * Simulation": v_r = |v - v_bg|, v_bg Maxwellian; Sec. "Particle Collisions") */
+static void mcc_ion(orc_state *S, int64_t k, uint32_t l)
+{
+    orc_sp *p = &S->sp[SP_I];
+    uint32_t c[4];
+    draw(S->P.seed, p->id[k], l, PUR_COLL, c);
+    if (!((double)c[0] * 0x1p-32 < S->p_max_i)) return;
+    uint32_t cg[4];
+    draw(S->P.seed, p->id[k], l, PUR_GAS, cg);
+    double n1, n2, n3, n4;
+    box_muller(cg[0], cg[1], &n1, &n2);
+    box_muller(cg[2], cg[3], &n3, &n4);
+    double vg = sqrt(O_KB * S->P.Tg / O_MAR);
+    double w[3] = {vg * n1, vg * n2, vg * n3};
+    double g[3] = {p->vx[k] - w[0], p->vy[k] - w[1], p->vz[k] - w[2]};
+    double gm = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    double mr = O_MAR / 2.0;
+    double eps = 0.5 * mr * gm * gm / O_QE;
+    double nu_cx = gm > 0.0 ? S->ngas * orc_sigma_i(eps) * gm : 0.0;
+    double nu_iso = nu_cx;
+    double r = u23(c[1]) * S->nu_max_i;
+    if (r < nu_cx) {
+        p->vx[k] = w[0]; p->vy[k] = w[1]; p->vz[k] = w[2];
+        S->cnt[C_CX]++;
+    } else if (r < nu_cx + nu_iso) {
+        double d[3];
+        iso_dir(c[2], c[3], d);
+        double v0[3] = {p->vx[k], p->vy[k], p->vz[k]};
+        p->vx[k] = 0.5 * (v0[0] + w[0]) + 0.5 * gm * d[0];
+        p->vy[k] = 0.5 * (v0[1] + w[1]) + 0.5 * gm * d[1];
+        p->vz[k] = 0.5 * (v0[2] + w[2]) + 0.5 * gm * d[2];
+        S->cnt[C_ISO]++;
+    }
+}
+
+static void wall_ion(orc_state *S, int64_t k, uint32_t l, int electrode)
+{
+    orc_sp *p = &S->sp[SP_I];
+    double v2 = p->vx[k] * p->vx[k] + p->vy[k] * p->vy[k] + p->vz[k] * p->vz[k];
+    double E = 0.5 * O_MAR * v2 / O_QE;
+    double ct = v2 > 0.0 ? fabs(p->vx[k]) / sqrt(v2) : 1.0;
+    if (ct > 1.0) ct = 1.0;
+    double th = acos(ct) * 180.0 / O_PI;
+    double emax = 2.0 * S->P.V0;
+    hist_add(S->iedf[electrode], NB_IEDF, E, emax);
+    int be = (int)(E / emax * NB_IEADF_E);
+    if (be > NB_IEADF_E - 1) be = NB_IEADF_E - 1;
+    int ba = (int)th;
+    if (ba > NB_ANG - 1) ba = NB_ANG - 1;
+    S->ieadf[electrode][be * NB_ANG + ba]++;
+    S->cnt[electrode == 0 ? C_IMP_I_L : C_IMP_I_R]++;
+    if (S->P.sputter) sputter(S, p->id[k], l, E, electrode);
+}
+
+void orc_tp_step(orc_state *S, int64_t nsteps, double dt_tp);
+
+/* One PIC/MCC cycle l -> l+1 for both charged species (Fig. 4 order: the
+ * field E^l is already known; interpolate, push (leapfrog, Eqs. for r and
+ * v), walls, collisions; then charge assignment and field solve for l+1). */
+static void pic_one_step(orc_state *S)
+{
+    uint32_t l = S->step;
+    int N = S->P.ncell;
+    double dx = S->dx;
+    int64_t n_start[2] = {S->sp[SP_E].n, S->sp[SP_I].n};   /* births of this step wait */
+    for (int s = 0; s < 2; s++) {
+        orc_sp *p = &S->sp[s];
+        double qm = charge_of(s) / mass_of(s);
+        int64_t n0 = n_start[s];
+        for (int64_t k = 0; k < n0; k++) {
+            if (!p->alive[k]) continue;
+            /* field interpolation (Sec. "Field Interpolation") */
+            double j = floor(p->xi[k]);
+            double f = p->xi[k] - j;
+            int m = (int)j;
+            double Ek = (1.0 - f) * S->E[m] + f * S->E[m + 1];
+            /* leapfrog (Eqs. pushinv, pushinr) */
+            p->vx[k] = p->vx[k] + qm * Ek * S->P.dt;
+            p->xi[k] = p->xi[k] + p->vx[k] * S->P.dt / dx;
+            /* wall interaction (Sec. "Wall Interaction"): absorb */
+            if (p->xi[k] <= 0.0 || p->xi[k] >= (double)N) {
+                int el = p->xi[k] <= 0.0 ? 0 : 1;
+                p->alive[k] = 0;
+                if (s == SP_E) S->cnt[el == 0 ? C_IMP_E_L : C_IMP_E_R]++;
+                else wall_ion(S, k, l, el);
+                continue;
+            }
+            /* collisions */
+            if (s == SP_E) mcc_electron(S, k, l);
+            else mcc_ion(S, k, l);
+        }
+    }
+    S->step = l + 1;
+    field_for_step(S, S->step);
+    /* time averages (Sec. "Kinetic Particle Simulation": averaging) */
+    for (int m = 0; m <= N; m++) {
+        S->sum_q[0][m] += (double)S->q[0][m];
+        S->sum_q[1][m] += (double)S->q[1][m];
+        S->sum_phi[m] += S->phi[m];
+    }
+    S->n_avg++;
+    if (S->P.diag_every > 0 && S->step % (uint32_t)S->P.diag_every == 0) {
+        for (int s = 0; s < 2; s++) {
+            orc_sp *p = &S->sp[s];
+            for (int64_t k = 0; k < p->n; k++) {
+                if (!p->alive[k]) continue;
+                double j = floor(p->xi[k]);
+                double f = p->xi[k] - j;
+                int m = (int)j;
+                S->sum_flux[s][m] += (1.0 - f) * p->vx[k];
+                S->sum_flux[s][m + 1] += f * p->vx[k];
+                if (s == SP_E && p->xi[k] >= 0.45 * N && p->xi[k] < 0.55 * N) {
+                    double v2 = p->vx[k] * p->vx[k] + p->vy[k] * p->vy[k] + p->vz[k] * p->vz[k];
+                    hist_add(S->eedf, NB_EEDF, 0.5 * O_ME * v2 / O_QE, 64.0);
+                }
+            }
+        }
+        S->n_flux++;
+    }
+    if (S->P.sputter && S->P.tp_every > 0 && S->step % (uint32_t)S->P.tp_every == 0)
+        orc_tp_step(S, 1, S->P.tp_every * S->P.dt);
+}
+
+void orc_step(orc_state *S, int64_t nsteps)
+{
+    for (int64_t i = 0; i < nsteps; i++) pic_one_step(S);
+}
+
+/* ======================= test particles ================================== */
+/* One TP step (Sec. "Test Particle Method"): free flight x += v_x dt, sticking
+ * at either wall with the absorbed flux recorded, and a binary hard-sphere
+ * collision with a thermal Ar partner with probability 1 - exp(-n sigma g dt)
+ * (Eq. collisionprobability1 with tau_c = 1/(n sigma g)); isotropic
+ * scattering in the centre-of-mass frame. */
+void orc_tp_step(orc_state *S, int64_t nsteps, double dt_tp)
+{
+    orc_sp *p = &S->sp[SP_TP];
+    int N = S->P.ncell;
+    double dx = S->dx;
+    double vg = sqrt(O_KB * S->P.Tg / O_MAR);
+    double mu = O_MAL + O_MAR;
+    for (int64_t it = 0; it < nsteps; it++) {
+        uint32_t s = S->tp_step;
+        for (int64_t k = 0; k < p->n; k++) {
+            if (!p->alive[k]) continue;
+            p->xi[k] = p->xi[k] + p->vx[k] * dt_tp / dx;
+            if (p->xi[k] <= 0.0 || p->xi[k] >= (double)N) {
+                int el = p->xi[k] <= 0.0 ? 0 : 1;
+                double v2 = p->vx[k] * p->vx[k] + p->vy[k] * p->vy[k] + p->vz[k] * p->vz[k];
+                double E = 0.5 * O_MAL * v2 / O_QE;
+                double ct = v2 > 0.0 ? fabs(p->vx[k]) / sqrt(v2) : 1.0;
+                if (ct > 1.0) ct = 1.0;
+                hist_add(S->sp_e[el], NB_SPE, E, 300.0);
+                int ba = (int)(acos(ct) * 180.0 / O_PI);
+                if (ba > NB_ANG - 1) ba = NB_ANG - 1;
+                S->sp_ang[el][ba]++;
+                S->cnt[el == 0 ? C_TPDEP_L : C_TPDEP_R]++;
+                p->alive[k] = 0;
+                continue;
+            }
+            uint32_t cg[4], cc[4];
+            draw(S->P.seed, p->id[k], s, PUR_TP_GAS, cg);
+            double n1, n2, n3, n4;
+            box_muller(cg[0], cg[1], &n1, &n2);
+            box_muller(cg[2], cg[3], &n3, &n4);
+            double w[3] = {vg * n1, vg * n2, vg * n3};
+            double g[3] = {p->vx[k] - w[0], p->vy[k] - w[1], p->vz[k] - w[2]};
+            double gm = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+            double P = 1.0 - exp(-S->ngas * S->P.sigma_tp * gm * dt_tp);
+            draw(S->P.seed, p->id[k], s, PUR_TP_COLL, cc);
+            if (u23(cc[0]) < P) {
+                double d[3];
+                iso_dir(cc[1], cc[2], d);
+                double vc[3] = {(O_MAL * p->vx[k] + O_MAR * w[0]) / mu,
+                                (O_MAL * p->vy[k] + O_MAR * w[1]) / mu,
+                                (O_MAL * p->vz[k] + O_MAR * w[2]) / mu};
+                p->vx[k] = vc[0] + (O_MAR / mu) * gm * d[0];
+                p->vy[k] = vc[1] + (O_MAR / mu) * gm * d[1];
+                p->vz[k] = vc[2] + (O_MAR / mu) * gm * d[2];
+                S->cnt[C_TPCOLL]++;
+            }
+        }
+        /* grid moments of the TP density and mean velocity (Sec. "Limitations
+         * and Constraints" of the TPM: cell-based averages) */
+        for (int64_t k = 0; k < p->n; k++) {
+            if (!p->alive[k]) continue;
+            double j = floor(p->xi[k]);
+            double f = p->xi[k] - j;
+            int m = (int)j;
+            S->tp_dens[m] += 1.0 - f;
+            S->tp_dens[m + 1] += f;
+            S->tp_vx[m] += (1.0 - f) * p->vx[k];
+            S->tp_vx[m + 1] += f * p->vx[k];
+        }
+        S->n_tp_samp++;
+        S->tp_step = s + 1;
+    }
+}
+
+/* Mono-energetic source: n atoms launched from the left electrode with a
+ * Thompson energy (cut off at Lambda E_ion) and a cosine angle; ids tag|k. */
+void orc_tp_launch(orc_state *S, int64_t n, double E_ion)
+{
+    double Emax = lambda_ar_al() * E_ion;
+    double N = (double)S->P.ncell;
+    for (int64_t k = 0; k < n; k++) {
+        uint64_t id = TAG[SP_TP] | (uint64_t)k;
+        uint32_t ce[4];
+        draw(S->P.seed, id, 0, PUR_TP_LAUNCH, ce);
+        double v[3];
+        orc_emit(u23(ce[0]), u23(ce[1]), u23(ce[2]), Emax, 1.0, v);
+        append(S, SP_TP, N * 0x1p-32, v[0], v[1], v[2], id);
+    }
+}
+
+/* ======================= diagnostics export ============================== */
+/* kind: 0 phi, 1 n_e, 2 n_i (m^-3), 3 Gamma_e, 4 Gamma_i (m^-2 s^-1),
+ * 5 EEDF, 6 IEDF left, 7 IEDF right, 8 IEADF left, 9 IEADF right,
+ * 10 sputtered energy left, 11 right, 12 sputtered angle left, 13 right,
+ * 14 TP density (m^-3), 15 TP mean v_x sum (m^-2 s^-1 like Gamma).
+ * Returns the number of values written. */
+int64_t orc_diag(const orc_state *S, int kind, double *out, int64_t cap)
+{
+    int N = S->P.ncell;
+    double dx = S->dx, w = S->P.w;
+    int64_t n = 0;
+#define PUT(v) do { if (n < cap) out[n] = (v); n++; } while (0)
+    switch (kind) {
+    case 0:
+        for (int m = 0; m <= N; m++) PUT(S->n_avg ? S->sum_phi[m] / S->n_avg : 0.0);
+        break;
+    case 1: case 2:
+        for (int m = 0; m <= N; m++) {
+            double vol = (m == 0 || m == N) ? 0.5 * dx : dx;
+            PUT(S->n_avg ? w * S->sum_q[kind - 1][m] / (4294967296.0 * vol * S->n_avg) : 0.0);
+        }
+        break;
+    case 3: case 4:
+        for (int m = 0; m <= N; m++) {
+            double vol = (m == 0 || m == N) ? 0.5 * dx : dx;
+            PUT(S->n_flux ? w * S->sum_flux[kind - 3][m] / (vol * S->n_flux) : 0.0);
+        }
+        break;
+    case 5: for (int b = 0; b < NB_EEDF; b++) PUT((double)S->eedf[b]); break;
+    case 6: case 7: for (int b = 0; b < NB_IEDF; b++) PUT((double)S->iedf[kind - 6][b]); break;
+    case 8: case 9:
+        for (int b = 0; b < NB_IEADF_E * NB_ANG; b++) PUT((double)S->ieadf[kind - 8][b]);
+        break;
+    case 10: case 11: for (int b = 0; b < NB_SPE; b++) PUT((double)S->sp_e[kind - 10][b]); break;
+    case 12: case 13: for (int b = 0; b < NB_ANG; b++) PUT((double)S->sp_ang[kind - 12][b]); break;
+    case 14: case 15:
+        for (int m = 0; m <= N; m++) {
+            double vol = (m == 0 || m == N) ? 0.5 * dx : dx;
+            const double *a = kind == 14 ? S->tp_dens : S->tp_vx;
+            PUT(S->n_tp_samp ? w * a[m] / (vol * S->n_tp_samp) : 0.0);
+        }
+        break;
+    default: break;
+    }
+#undef PUT
+    return n;
+}
+
+void orc_reset_averages(orc_state *S)
+{
+    int N = S->P.ncell;
+    for (int m = 0; m <= N; m++) {
+        S->sum_q[0][m] = S->sum_q[1][m] = S->sum_phi[m] = 0.0;
+        S->sum_flux[0][m] = S->sum_flux[1][m] = 0.0;
+        S->tp_dens[m] = S->tp_vx[m] = 0.0;
+    }
+    S->n_avg = S->n_flux = S->n_tp_samp = 0;
+    memset(S->eedf, 0, sizeof(int64_t) * NB_EEDF);
+    for (int s = 0; s < 2; s++) {
+        memset(S->iedf[s], 0, sizeof(int64_t) * NB_IEDF);
+        memset(S->ieadf[s], 0, sizeof(int64_t) * NB_IEADF_E * NB_ANG);
+        memset(S->sp_e[s], 0, sizeof(int64_t) * NB_SPE);
+        memset(S->sp_ang[s], 0, sizeof(int64_t) * NB_ANG);
+    }
+}
+
+uint32_t orc_get_step(const orc_state *S) { return S->step; }
+void orc_set_step(orc_state *S, uint32_t l) { S->step = l; }
+uint32_t orc_get_tp_step(const orc_state *S) { return S->tp_step; }

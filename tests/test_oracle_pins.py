@@ -1,0 +1,482 @@
+"""Pins of the FP64 oracle against things other than itself: published
+known-answer vectors, values printed in the paper, closed forms, exact
+invariants and textbook kinetic theory.  CPU only.
+
+Each test names the part of the paper (arXiv:1607.04069) the pinned oracle
+function implements.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+from scipy import special, stats
+
+import oracle as O
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+QE, ME, AMU, KB, EPS0 = 1.602176634e-19, 9.1093837015e-31, 1.66053906660e-27, 1.380649e-23, 8.8541878128e-12
+MAR, MAL = 39.948 * AMU, 26.98 * AMU
+
+
+def prm(**kw):
+    p = dict(L=0.05, p=0.0, Tg=300.0, f=13.56e6, V0=0.0, w=0.0, dt=1e-10, te0=2.0, ti0=0.026,
+             tp_dt=1e-9, sigma_tp=3e-19, seed=7, ncell=1024, sputter=0, tp_every=0, diag_every=1)
+    p.update(kw)
+    return p
+
+
+def load(orc, s, xi, v, ids=None):
+    n = len(xi)
+    if ids is None:
+        ids = np.arange(n, dtype=np.uint64) | np.uint64([0, 1 << 62, 2 << 62][s])
+    orc.set_species(s, xi, v[0], v[1], v[2], ids)
+
+
+# ------------------------------------------------------------------ RNG
+def test_philox_known_answers():
+    """Philox4x32-10 (Salmon et al. SC'11) against its published KAT vectors."""
+    rows = [l.split() for l in open(os.path.join(HERE, "golden", "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = O.philox(v[0:4], v[4:6])
+        assert [int(x) for x in out] == v[6:10]
+
+
+def test_gas_density_printed_in_paper():
+    """n = p/(k_B T) reproduces the Ar density the paper prints (Sec. 'Simulation Scenario')."""
+    rows = [l.split() for l in open(os.path.join(HERE, "golden", "paper_gas_density.txt"))
+            if l.strip() and not l.startswith("#")]
+    p, T, n_cm3, tol = map(float, rows[0])
+    orc = O.Oracle(prm(p=p, Tg=T), 1, 1)
+    n = orc.derived()["n_gas"] * 1e-6
+    assert abs(n / n_cm3 - 1.0) < tol
+
+
+# ------------------------------------------------------------------ charge assignment
+def test_deposit_conserves_charge_and_dipole_exactly():
+    """Linear weighting (Sec. 'Charge Assignment') conserves each particle's
+    charge (2^32 per particle) and, for positions on the 2^-32 grid, the
+    first moment exactly: sum_m m q_m = 2^32 sum_k xi_k."""
+    rng = np.random.default_rng(3)
+    N = 1024
+    pos = rng.integers(1, 2**32, size=50_000, dtype=np.uint64)
+    xi = pos.astype(np.float64) * (N / 2.0**32)
+    q = O.deposit(xi, N)
+    assert int(q.sum()) == 2**32 * len(xi)
+    lhs = sum(int(m) * int(qm) for m, qm in enumerate(q))
+    rhs = sum(int(p) for p in pos) * N          # 2^32 * sum(xi) with xi = pos N / 2^32
+    assert lhs == rhs
+    assert (q >= 0).all()
+
+
+def test_deposit_special_positions():
+    """A particle on a node deposits everything there; one at mid-cell splits evenly;
+    a removed particle (xi < 0) deposits nothing."""
+    q = O.deposit(np.array([5.0, 7.5, -1.0]), 16)
+    assert q[5] == 2**32 and q[6] == 0
+    assert q[7] == 2**31 and q[8] == 2**31
+    assert q.sum() == 2 * 2**32
+
+
+# ------------------------------------------------------------------ field solve
+def test_poisson_constant_rho_matches_closed_form():
+    """rho = const: phi = V_L (1 - x/L) + rho0 x (L - x)/(2 eps0), reproduced
+    exactly by the discrete scheme (Sec. 'EM Field Solver'); E from the
+    central difference and the half-cell Gauss rule is exact too."""
+    N, L, w, VL = 256, 0.05, 1e11, 123.0
+    dx = L / N
+    Q = 3_000_000 * 2**32 // 1000
+    q_i = np.full(N + 1, Q, dtype=np.int64)
+    q_i[0] = q_i[N] = Q // 2                      # half-volume boundary nodes
+    q_e = np.zeros(N + 1, dtype=np.int64)
+    phi, E = O.poisson(N, dx, w, q_i, q_e, VL)
+    rho0 = QE * w * Q / (2**32 * dx)
+    x = np.arange(N + 1) * dx
+    phi_ref = VL * (1 - x / L) + rho0 * x * (L - x) / (2 * EPS0)
+    E_ref = VL / L - rho0 * (L - 2 * x) / (2 * EPS0)
+    scale = np.abs(phi_ref).max()
+    assert np.abs(phi - phi_ref).max() / scale < 1e-12
+    assert np.abs(E - E_ref).max() / np.abs(E_ref).max() < 1e-10
+
+
+def test_poisson_sine_matches_discrete_eigensolution():
+    """rho_m = rho0 sin(pi x_m / L): phi_m = rho0 dx^2 sin(pi x_m/L) /
+    (2 eps0 (1 - cos(pi dx / L))) solves the discrete equation exactly."""
+    N, L, w = 512, 0.05, 1e11
+    dx = L / N
+    x = np.arange(N + 1) * dx
+    amp = 1e15
+    q_i = np.rint(amp * np.sin(np.pi * x / L)).astype(np.int64)
+    q_i[0] = q_i[N] = 0
+    rho = QE * w * q_i / (2**32 * dx)
+    phi, _ = O.poisson(N, dx, w, q_i, np.zeros(N + 1, dtype=np.int64), 0.0)
+    rho0 = QE * w * amp / (2**32 * dx)
+    phi_ref = rho0 * dx**2 * np.sin(np.pi * x / L) / (2 * EPS0 * (1 - np.cos(np.pi * dx / L)))
+    assert np.abs(phi - phi_ref).max() / np.abs(phi_ref).max() < 1e-9   # rint of q_i: 1e-15 rel
+
+
+def test_poisson_double_sum_identity_random_charge():
+    """Thomas result against the independent double prefix sum
+    phi_m = phi_0 + m D0 - (dx^2/eps0) sum_{k<m} S_k, evaluated exactly in rationals."""
+    rng = np.random.default_rng(11)
+    N, L, w, VL = 128, 0.025, 1.25e12, -87.5
+    dx = L / N
+    q_i = rng.integers(0, 2**44, size=N + 1, dtype=np.int64)
+    q_e = rng.integers(0, 2**44, size=N + 1, dtype=np.int64)
+    phi, E = O.poisson(N, dx, w, q_i, q_e, VL)
+    A = Fraction(dx) * Fraction(QE) * Fraction(w) / (2**32 * Fraction(EPS0))  # dx^2 rho / eps0 per unit q
+    qn = [int(a) - int(b) for a, b in zip(q_i, q_e)]
+    S = [0] * (N + 1)
+    for m in range(1, N + 1):
+        S[m] = S[m - 1] + qn[m]
+    T = [0] * (N + 1)
+    for m in range(1, N + 1):
+        T[m] = T[m - 1] + S[m - 1]
+    D0 = (Fraction(0) - Fraction(VL) + A * T[N]) / N
+    ref = [float(Fraction(VL) + m * D0 - A * T[m]) for m in range(N + 1)]
+    ref = np.array(ref)
+    assert np.abs(phi - ref).max() / np.abs(ref).max() < 1e-12
+    Eref = np.array([float(-(2 * D0 - A * (S[m] + S[m - 1])) / (2 * Fraction(dx))) for m in range(1, N)])
+    assert np.abs(E[1:N] - Eref).max() / np.abs(Eref).max() < 1e-10
+
+
+# ------------------------------------------------------------------ push / interpolation
+def test_leapfrog_uniform_field_closed_form():
+    """Eqs. pushinr/pushinv in a uniform field with v^{-1/2} = v0 - a dt/2:
+    x_n = x0 + v0 n dt + a (n dt)^2 / 2 exactly (FP64 round-off only)."""
+    N, L, dt = 1024, 1.0, 1e-10
+    orc = O.Oracle(prm(L=L, ncell=N, dt=dt), 4, 4)
+    dx = L / N
+    E0 = 35.0
+    x0 = np.array([0.3, 0.5, 0.61, 0.42])
+    v0 = np.array([1e5, -2e5, 0.0, 3e5])
+    a = -QE / ME * E0
+    load(orc, 0, x0 / dx, [v0 - a * dt / 2, v0 * 0, v0 * 0])
+    for n in range(1, 201):
+        orc.set_field(np.full(N + 1, E0))
+        orc.step(1)
+        sp = orc.get_species(0)
+        ref = x0 + v0 * n * dt + a * (n * dt) ** 2 / 2
+        assert np.allclose(sp["xi"] * dx, ref, rtol=1e-11, atol=1e-13)
+
+
+def test_leapfrog_linear_field_discrete_oscillator():
+    """Field interpolation (Sec. 'Field Interpolation') is exact for a field
+    linear in x; leapfrog then gives the discrete oscillator
+    x_n - xc = X cos(n theta), cos(theta) = 1 - (w dt)^2 / 2."""
+    N, L, dt = 256, 0.01, 2e-11
+    dx = L / N
+    orc = O.Oracle(prm(L=L, ncell=N, dt=dt), 3, 3)
+    xc, kappa = 0.005, 2e6               # E = kappa (x - xc): restoring for electrons
+    om2 = QE / ME * kappa
+    th = math.acos(1 - om2 * dt * dt / 2)
+    X = np.array([1e-3, -2e-3, 0.5e-3])
+    a0 = -om2 * X
+    vm = X * (math.cos(th) - 1) / dt - a0 * dt
+    load(orc, 0, (xc + X) / dx, [vm, 0 * X, 0 * X])
+    Enode = kappa * (np.arange(N + 1) * dx - xc)
+    for n in range(1, 301):
+        orc.set_field(Enode)
+        orc.step(1)
+        x = orc.get_species(0)["xi"] * dx
+        assert np.allclose(x - xc, X * np.cos(n * th), rtol=0, atol=1e-12)
+
+
+# ------------------------------------------------------------------ initial loading
+def test_initial_loading_is_uniform_and_maxwellian():
+    """Uniform positions and Box-Muller Maxwellian velocities
+    (Sec. 'Kinetic Particle Simulation'): KS of x against U(0,L), of each
+    velocity component against N(0, kT/m), and <E> = 3/2 T."""
+    N = 64
+    orc = O.Oracle(prm(ncell=N, seed=8), 100_000, 1)
+    orc.init_species(0, 100_000, 2.0)
+    sp = orc.get_species(0)
+    assert stats.kstest(sp["xi"] / N, "uniform").pvalue > 1e-3
+    vth = math.sqrt(2.0 * QE / ME)
+    for c in ("vx", "vy", "vz"):
+        assert stats.kstest(sp[c] / vth, "norm").pvalue > 1e-3
+    E = 0.5 * ME * (sp["vx"]**2 + sp["vy"]**2 + sp["vz"]**2) / QE
+    assert abs(E.mean() / 3.0 - 1) < 4 * math.sqrt(2 / 3 / len(E))
+    assert len(np.unique(sp["id"])) == len(E)
+
+
+# ------------------------------------------------------------------ null-collision MCC
+def test_cross_section_shapes():
+    """Lotz-form ionisation peaks at eps = e*I with a q/(e I^2); thresholds hold."""
+    s = O.sigma_e(11.5)
+    assert s[1] == 0 and s[2] == 0 and s[0] == 1e-19
+    assert O.sigma_e(15.8)[2] == 0
+    eps = np.linspace(16, 200, 20001)
+    si = np.array([O.sigma_e(e)[2] for e in eps])
+    assert abs(eps[si.argmax()] / (math.e * 15.8) - 1) < 1e-3
+    assert abs(si.max() / (4.5e-18 * 6 / (math.e * 15.8**2)) - 1) < 1e-6
+    assert abs(O.sigma_e(1e9)[1] / 1e-20 - 1) < 1e-7
+    assert abs(O.sigma_i(1.0) - 5e-19) < 1e-30 and abs(O.sigma_i(4.0) - 2.5e-19) < 1e-30
+
+
+def _mono(n, speed, rng):
+    d = rng.standard_normal((3, n))
+    d /= np.linalg.norm(d, axis=0)
+    return d * speed
+
+
+def test_electron_null_collision_rate_constant_sigma():
+    """Below every threshold only elastic scattering (constant sigma) is real:
+    the real-collision fraction per step is P_max nu_el(v) / nu_max (binomial)."""
+    rng = np.random.default_rng(5)
+    n, p, T, dt = 200_000, 3.0, 300.0, 1e-9
+    orc = O.Oracle(prm(L=1.0, ncell=1024, p=p, Tg=T, dt=dt), n, 1)
+    eps = 5.0
+    v = math.sqrt(2 * eps * QE / ME)
+    load(orc, 0, np.full(n, 512.3), _mono(n, v, rng))
+    orc.step(1)
+    c = orc.counters()
+    ngas = p / (KB * T)
+    sig_max = 1e-19 + 1e-20 + 4.5e-18 * 6 / (math.e * 15.8**2)
+    nu_max = ngas * sig_max * math.sqrt(2 * 100.0 * QE / ME)           # eps_max = 2 V0 + 100 eV
+    pexp = (1 - math.exp(-nu_max * dt)) * ngas * 1e-19 * v / nu_max
+    assert c["excitation"] == 0 and c["ionizations"] == 0
+    assert abs(c["elastic"] - n * pexp) < 4.5 * math.sqrt(n * pexp * (1 - pexp))
+
+
+def test_ion_candidate_rate_is_velocity_independent():
+    """Ar+: sigma(eps) g is constant, so the collision rate does not depend on
+    the velocity and CX and isotropic scattering each take half."""
+    n, p, T, dt = 200_000, 3.0, 300.0, 1e-7
+    ngas = p / (KB * T)
+    nu = 2 * ngas * 5e-19 * math.sqrt(2 * QE / (MAR / 2))
+    pexp = 1 - math.exp(-nu * dt)
+    for speed in (100.0, 3000.0):
+        rng = np.random.default_rng(int(speed))
+        orc = O.Oracle(prm(L=10.0, ncell=1024, p=p, Tg=T, dt=dt, seed=int(speed)), 1, n)
+        load(orc, 1, np.full(n, 400.0), _mono(n, speed, rng))
+        orc.step(1)
+        c = orc.counters()
+        tot = c["cx"] + c["iso"]
+        assert abs(tot - n * pexp) < 4.5 * math.sqrt(n * pexp * (1 - pexp))
+        assert abs(c["cx"] - tot / 2) < 4.5 * math.sqrt(tot / 4)
+
+
+def test_ion_thermal_relaxation():
+    """Field off, ions at E0 >> kT: <E>_n = E_g + (E0 - E_g)(1 - 3/4 P_max)^n,
+    E_g = 3/2 kT; after many steps the energy follows the chi^2_3 law."""
+    n, p, T, dt = 60_000, 3.0, 300.0, 1e-7
+    rng = np.random.default_rng(9)
+    orc = O.Oracle(prm(L=100.0, ncell=1024, p=p, Tg=T, dt=dt), 1, n)
+    E0 = 1.0
+    load(orc, 1, np.full(n, 512.0) + rng.uniform(-1, 1, n), _mono(n, math.sqrt(2 * E0 * QE / MAR), rng))
+    ngas = p / (KB * T)
+    P = 1 - math.exp(-2 * ngas * 5e-19 * math.sqrt(2 * QE / (MAR / 2)) * dt)
+    Eg = 1.5 * KB * T / QE
+    for steps in (5, 10):
+        orc.step(5)
+        sp = orc.get_species(1)
+        E = 0.5 * MAR * (sp["vx"]**2 + sp["vy"]**2 + sp["vz"]**2) / QE
+        ref = Eg + (E0 - Eg) * (1 - 0.75 * P) ** steps
+        assert abs(E.mean() / ref - 1) < 0.01
+    orc.step(90)
+    sp = orc.get_species(1)
+    E = 0.5 * MAR * (sp["vx"]**2 + sp["vy"]**2 + sp["vz"]**2) / QE
+    kT = KB * T / QE
+    assert stats.kstest(E / kT, stats.gamma(1.5).cdf).pvalue > 1e-3
+
+
+def test_electron_elastic_energy_loss():
+    """Mean fractional energy loss per elastic collision = 2 m_e / M (<1 - cos chi> = 1)."""
+    rng = np.random.default_rng(21)
+    n, dt = 200_000, 1e-9
+    orc = O.Oracle(prm(L=1.0, ncell=1024, p=3.0, dt=dt), n, 1)
+    v = math.sqrt(2 * 5.0 * QE / ME)
+    v0 = _mono(n, v, rng)
+    load(orc, 0, np.full(n, 512.7), v0)
+    orc.step(1)
+    sp = orc.get_species(0)
+    v1 = np.stack([sp["vx"], sp["vy"], sp["vz"]])
+    hit = np.any(v1 != v0, axis=0)
+    loss = 1 - (v1[:, hit]**2).sum(0) / v**2
+    ref = 2 * ME / MAR
+    se = ref * math.sqrt(1 / 3) / math.sqrt(hit.sum())
+    assert hit.sum() == orc.counters()["elastic"]
+    assert abs(loss.mean() - ref) < 5 * se
+
+
+def test_inelastic_bookkeeping_at_50eV():
+    """At 50 eV: process fractions follow sigma_el : sigma_exc : sigma_ion,
+    excitation removes exactly 11.5 eV, ionisation removes 15.8 eV and
+    creates one e-/Ar+ pair at the parent's position."""
+    rng = np.random.default_rng(33)
+    n, dt = 200_000, 2e-10
+    orc = O.Oracle(prm(L=1.0, ncell=1024, p=3.0, dt=dt), 2 * n, n)
+    eps = 50.0
+    v = math.sqrt(2 * eps * QE / ME)
+    v0 = _mono(n, v, rng)
+    load(orc, 0, np.full(n, 512.25), v0)
+    orc.step(1)
+    c = orc.counters()
+    s_el, s_exc, s_ion = 1e-19, 1e-20 * (1 - 11.5 / eps), 4.5e-18 * 6 * math.log(eps / 15.8) / (eps * 15.8)
+    tot = c["elastic"] + c["excitation"] + c["ionizations"]
+    for k, s in (("elastic", s_el), ("excitation", s_exc), ("ionizations", s_ion)):
+        pk = s / (s_el + s_exc + s_ion)
+        assert abs(c[k] - tot * pk) < 4.5 * math.sqrt(tot * pk * (1 - pk))
+    e = orc.get_species(0)
+    i = orc.get_species(1)
+    assert len(e["xi"]) == n + c["ionizations"] and len(i["xi"]) == c["ionizations"]
+    Ee = 0.5 * ME * (e["vx"]**2 + e["vy"]**2 + e["vz"]**2) / QE
+    exc = np.abs(Ee[:n] - (eps - 11.5)) < 1e-9
+    assert exc.sum() == c["excitation"]
+    # energy balance over all electrons: -11.5 per excitation, -15.8 per ionisation,
+    # elastic losses of mean 2 m/M eps each
+    dE = Ee.sum() - n * eps
+    exp_dE = -11.5 * c["excitation"] - 15.8 * c["ionizations"] - 2 * ME / MAR * eps * c["elastic"]
+    assert abs(dE - exp_dE) < 6 * 2 * ME / MAR * eps * math.sqrt(c["elastic"] / 3) + 1e-6 * n
+    # the pair is born at the parent's position x^{l+1}, electron and ion together
+    assert np.array_equal(e["xi"][n:], i["xi"])
+    assert np.isin(i["xi"], e["xi"][:n]).all()
+
+
+# ------------------------------------------------------------------ walls and sputtering
+def test_sputter_yield_values():
+    assert O.sputter_yield(30.0) == 0.0 and O.sputter_yield(10.0) == 0.0
+    assert abs(O.sputter_yield(300.0) - 0.3) < 1e-15
+    assert abs(O.sputter_yield(120.0) - 0.1 * math.sqrt(3)) < 1e-15
+
+
+@pytest.mark.parametrize("E_ion,Y", [(300.0, 0.3), (12030.0, 2.0)])
+def test_sputter_births_per_impact(E_ion, Y):
+    """Ions reaching the target with energy E: mean number of sputtered atoms
+    per impact = Y(E) (binomial); an integer yield gives exactly Y each."""
+    n = 100_000
+    rng = np.random.default_rng(int(E_ion))
+    orc = O.Oracle(prm(sputter=1, V0=0.0, dt=1e-10), 1, n, 3 * n)
+    v = math.sqrt(2 * E_ion * QE / MAR)
+    load(orc, 1, rng.uniform(1e-3, 2e-3, n), [np.full(n, -v), np.zeros(n), np.zeros(n)])
+    orc.step(1)
+    c = orc.counters()
+    assert c["imp_i_l"] == n
+    if Y == int(Y):
+        assert c["sputtered_l"] == int(Y) * n
+    else:
+        assert abs(c["sputtered_l"] - n * Y) < 4.5 * math.sqrt(n * Y * (1 - Y))
+    tp = orc.get_species(2)
+    Lam = 4 * MAR * MAL / (MAR + MAL) ** 2
+    Es = 0.5 * MAL * (tp["vx"]**2 + tp["vy"]**2 + tp["vz"]**2) / QE
+    assert (tp["vx"] > 0).all() and (Es <= Lam * E_ion * (1 + 1e-12)).all()
+
+
+def test_thompson_cosine_distributions():
+    """Sputtered-atom launch: energy follows the truncated Thompson CDF
+    (E/(E+Ub))^2 / (Emax/(Emax+Ub))^2; cos(theta) law gives <cos theta> = 2/3
+    and P(theta < t) = sin^2 t."""
+    n = 200_000
+    orc = O.Oracle(prm(), 1, 1, n)
+    orc.tp_launch(n, 300.0)
+    tp = orc.get_species(2)
+    v2 = tp["vx"]**2 + tp["vy"]**2 + tp["vz"]**2
+    E = 0.5 * MAL * v2 / QE
+    Ub = 3.4
+    Emax = 4 * MAR * MAL / (MAR + MAL) ** 2 * 300.0
+    cdf = lambda e: (np.clip(e, 0, Emax) / (np.clip(e, 0, Emax) + Ub))**2 / (Emax / (Emax + Ub))**2
+    assert stats.kstest(E, cdf).pvalue > 1e-3
+    ct = tp["vx"] / np.sqrt(v2)
+    assert (ct > 0).all()
+    assert abs(ct.mean() - 2 / 3) < 4 * math.sqrt(1 / 18 / n)
+    th = np.arccos(np.clip(ct, -1, 1))
+    assert stats.kstest(th, lambda t: np.sin(np.clip(t, 0, np.pi / 2))**2).pvalue > 1e-3
+    ph = np.arctan2(tp["vz"], tp["vy"])
+    assert stats.kstest((ph + np.pi) / (2 * np.pi), "uniform").pvalue > 1e-3
+
+
+# ------------------------------------------------------------------ test particles
+def test_tp_ballistic_flight_without_collisions():
+    """sigma = 0: every atom reaches the far wall at the step it must,
+    with its energy and angle recorded, and counts are conserved."""
+    N, L, dt, K = 1024, 0.05, 1e-9, 37
+    n = 1000
+    orc = O.Oracle(prm(L=L, ncell=N, sigma_tp=0.0, p=0.5), 1, 1, n)
+    vx = L / (K * dt) * (1 + 1e-9)
+    load(orc, 2, np.full(n, N * 2.0**-32), [np.full(n, vx), np.zeros(n), np.zeros(n)])
+    orc.tp_step(K - 1, dt)
+    assert orc.counters()["n_tp"] == n
+    orc.tp_step(1, dt)
+    c = orc.counters()
+    assert c["tp_dep_r"] == n and c["n_tp"] == 0 and c["tp_coll"] == 0
+    ang = orc.diag("sputter_ang_r")
+    assert ang[0] == n
+    e = orc.diag("sputter_e_r")
+    E = 0.5 * MAL * vx**2 / QE
+    assert e[min(int(E / 300 * 600), 599)] == n
+
+
+def test_tp_collision_rate_in_maxwellian_gas():
+    """TP collision probability per step for speed v in a Maxwellian gas:
+    n sigma <g> dt - (n sigma dt)^2 <g^2>/2 + O(3), with the textbook mean
+    relative speed <g> = c[(s + 1/(2s)) erf(s) + exp(-s^2)/sqrt(pi)],
+    s = v/c, c = sqrt(2kT/M) and <g^2> = v^2 + 3kT/M."""
+    n, p, T, dt, sig = 400_000, 0.5, 300.0, 2e-8, 3e-19
+    for v in (300.0, 2000.0):
+        rng = np.random.default_rng(int(v))
+        orc = O.Oracle(prm(L=100.0, ncell=1024, p=p, Tg=T, sigma_tp=sig), 1, 1, n)
+        load(orc, 2, np.full(n, 512.0), _mono(n, v, rng))
+        orc.tp_step(1, dt)
+        ngas = p / (KB * T)
+        c = math.sqrt(2 * KB * T / MAR)
+        s = v / c
+        g = c * ((s + 1 / (2 * s)) * special.erf(s) + math.exp(-s * s) / math.sqrt(math.pi))
+        g2 = v * v + 3 * KB * T / MAR
+        x = ngas * sig * dt
+        pexp = x * g - x * x * g2 / 2
+        got = orc.counters()["tp_coll"]
+        assert abs(got - n * pexp) < 4.5 * math.sqrt(n * pexp)
+
+
+def test_tp_thermalizes_to_gas_temperature():
+    """Hard-sphere Al-Ar collisions relax the Al velocity distribution to a
+    Maxwellian at the gas temperature: <v_x^2> = kT/M_Al."""
+    n, p, T = 40_000, 5.0, 300.0
+    rng = np.random.default_rng(4)
+    orc = O.Oracle(prm(L=1e6, ncell=1024, p=p, Tg=T, sigma_tp=3e-19), 1, 1, n)
+    load(orc, 2, np.full(n, 512.0) + rng.uniform(-1, 1, n), _mono(n, math.sqrt(2 * 5 * QE / MAL), rng))
+    orc.tp_step(300, 1e-6)            # P ~ 0.2 per step: ~60 collisions per atom
+    tp = orc.get_species(2)
+    ref = KB * T / MAL
+    for comp in ("vx", "vy", "vz"):
+        assert abs((tp[comp]**2).mean() / ref - 1) < 0.03
+
+
+# ------------------------------------------------------------------ conservation, diagnostics
+def test_charge_and_particle_conservation_over_steps():
+    """Every step: sum of deposits = 2^32 x alive particles per species;
+    ionisation creates equal numbers of electrons and ions."""
+    prmd = prm(L=0.025, ncell=128, p=3.0, V0=100.0, w=1.25e12 * 10, dt=1.0 / 13.56e6 / 400)
+    orc = O.Oracle(prmd, 12_000, 12_000)
+    orc.init_species(0, 2000, 2.0)
+    orc.init_species(1, 2000, 0.026)
+    orc.field()
+    for _ in range(40):
+        orc.step(5)
+        f = orc.get_field()
+        c = orc.counters()
+        assert int(f["q_e"].sum()) == 2**32 * c["n_e"]
+        assert int(f["q_i"].sum()) == 2**32 * c["n_i"]
+        assert c["n_e"] + c["imp_e_l"] + c["imp_e_r"] == 2000 + c["ionizations"]
+        assert c["n_i"] + c["imp_i_l"] + c["imp_i_r"] == 2000 + c["ionizations"]
+
+
+def test_density_diagnostic_normalisation():
+    """Uniform loading gives <n> = w N / L at every node, including the
+    half-volume electrode nodes."""
+    n, N, L = 400_000, 64, 0.02
+    w = 1e15 * L / n
+    orc = O.Oracle(prm(L=L, ncell=N, w=w, dt=1e-13), n, 1)
+    orc.init_species(0, n, 0.01)
+    orc.field()
+    orc.step(1)
+    ne = orc.diag("n_e")
+    per = n / N
+    assert abs(ne[1:N].mean() / 1e15 - 1) < 4 / math.sqrt(n)
+    assert abs(ne[0] / 1e15 - 1) < 5 / math.sqrt(per / 2)
+    assert abs(ne[N] / 1e15 - 1) < 5 / math.sqrt(per / 2)
