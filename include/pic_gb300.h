@@ -1,0 +1,210 @@
+/*
+ * pic_gb300.h -- C ABI of the GB300 (sm_103a) engine for the self-consistent
+ * particle-in-cell / Monte Carlo collision cycle of a capacitive RF argon
+ * discharge and the test-particle transport of sputtered Al atoms, after
+ * Trieschmann, Schmidt & Mussenbrock, "Particle-in-Cell/Test-Particle
+ * Simulations of Technological Plasmas" (arXiv:1607.04069).
+ *
+ * Conventions
+ *   - Every function returns PIC_OK (0) or a negative PIC_ERR_* code;
+ *     pic_strerror() names it and pic_last_error() gives the detail of the
+ *     last failure on the calling thread.
+ *   - "host" pointers are ordinary CPU memory owned by the caller; "device"
+ *     pointers are CUDA global memory on the context's device, owned by the
+ *     caller.  The context owns everything else it allocates.
+ *   - Work is enqueued on the CUDA stream given to pic_create (a
+ *     cudaStream_t passed as void*, NULL = legacy default stream) and runs
+ *     asynchronously; functions that return host data synchronise that
+ *     stream first.  A context must not be used by two threads at once.
+ *   - Positions: with pos_precision 32 a position is the unsigned 32-bit
+ *     fixed-point fraction of the gap, x = pos L / 2^32 (pos 0 marks a
+ *     removed slot); with pos_precision 64 it is a double in cell units,
+ *     xi = x / dx (negative marks a removed slot).  Test particles always
+ *     use the 32-bit form.  Velocities are float32 (m/s), ids uint64.
+ *   - Species: 0 = electrons, 1 = Ar+, 2 = sputtered Al test particles.
+ */
+#ifndef PIC_GB300_H
+#define PIC_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIC_OK 0
+#define PIC_ERR_INVALID_ARG (-1)     /* a pointer, size or value is out of range          */
+#define PIC_ERR_UNSTABLE_PARAMS (-2) /* strict mode: dx >= lambda_D or w_p dt >= 1       */
+#define PIC_ERR_OUT_OF_MEMORY (-3)   /* device allocation failed                           */
+#define PIC_ERR_CAPACITY (-4)        /* a birth or launch did not fit the slot capacity    */
+#define PIC_ERR_NUMERICS (-5)        /* an electron exceeded the null-collision energy cap */
+#define PIC_ERR_CUDA (-7)            /* a CUDA call failed (detail in pic_last_error)      */
+#define PIC_ERR_NO_DEVICE (-8)       /* no CUDA device is visible                          */
+
+enum pic_species { PIC_ELECTRON = 0, PIC_ION = 1, PIC_ATOM = 2 };
+
+/* Discharge description.  SI units unless marked.  The discharge is the 1D
+ * two-electrode setup of Sec. "Simulation Scenario": gap L, the left
+ * electrode driven by V_rf(t) = V0 sin(2 pi f t), the right one grounded,
+ * argon at constant pressure and temperature. */
+typedef struct pic_params {
+    double gap_m, pressure_pa, gas_temp_k, rf_freq_hz, rf_volt_v;
+    double weight;          /* physical particles per superparticle per m^2 (Sec. "Kinetic
+                               Particle Simulation": w = q_k / Q_k)                        */
+    double dt;              /* PIC time step, s                                            */
+    double te0_ev, ti0_ev;  /* temperatures of the initial uniform Maxwellian loading, eV  */
+    double tp_dt;           /* test-particle time step used by tp_step(), s                */
+    double sigma_tp;        /* Al-Ar hard-sphere cross section, m^2                        */
+    int64_t n_e0, n_i0;     /* initial superparticles per charged species                  */
+    int64_t cap_e, cap_i, cap_tp; /* slot capacity per species (0: 5/4 of the initial count
+                                     plus 65536)                                          */
+    uint64_t seed;          /* key of the Philox4x32-10 random stream                      */
+    int32_t n_cells;        /* N cells (N+1 nodes); a power of two, 4..4096                */
+    int32_t pos_precision;  /* 32 or 64, see "Positions" above                             */
+    int32_t sputter_enable; /* Ar+ impacts launch Al test particles                        */
+    int32_t tp_every;       /* coupled TP sub-cycle: one TP step of tp_every*dt after every
+                               tp_every PIC steps (0 = none)                              */
+    int32_t diag_every;     /* sampling stride of fluxes, EEDF and TP moments (0 = never)  */
+    int32_t sort_every_e, sort_every_i, sort_every_tp; /* compaction periods (0 = never)   */
+    int32_t ctas_per_sm;    /* CTAs per SM of the per-step launch (0 = occupancy limit)    */
+    int32_t strict;         /* reject parameters violating dx < lambda_D or w_p dt < 1
+                               (Sec. "Limitations and Constraints")                        */
+} pic_params;
+
+/* Mono-energetic Ar+ source for tp_launch: n atoms leave the left electrode
+ * with Sigmund-Thompson energies cut off at Lambda*e_ion_ev and cosine
+ * angles (Sec. "Wall Interactions" of the test-particle method). */
+typedef struct tp_source {
+    int64_t n;
+    double e_ion_ev;
+} tp_source;
+
+typedef struct pic_ctx pic_ctx; /* opaque */
+
+/* Fill *p with the 25 mm / 128-cell / 100 V / 3 Pa discharge. */
+int pic_params_default(pic_params* p);
+
+/* Create a discharge: validate p, allocate its state on the current CUDA
+ * device, load n_e0 / n_i0 superparticles uniformly with Maxwellian
+ * velocities (Sec. "Kinetic Particle Simulation": initial loading) and
+ * solve the field of that state (Sec. "EM Field Solver").  `stream` is a
+ * cudaStream_t or NULL.  On success *out owns the context. */
+int pic_create(const pic_params* p, void* stream, pic_ctx** out);
+
+/* Release everything the context owns (waits for its stream). */
+void pic_destroy(pic_ctx* ctx);
+
+/* Advance n_steps PIC/MCC cycles (Sec. "Particle-In-Cell Scheme", Fig. 4:
+ * field interpolation, leapfrog push (Eqs. pushinr, pushinv), wall
+ * absorption with sputtered-atom launch, null-collision MCC (Sec. "Particle
+ * Collisions"), linear charge assignment into exact int64 fixed point, and
+ * the Poisson solve with the RF boundary value).  Periodic compaction and
+ * coupled TP steps follow sort_every_* and tp_every.  Asynchronous: returns
+ * the launch status; device-side conditions surface in pic_sync. */
+int pic_step(pic_ctx* ctx, int64_t n_steps);
+
+/* Wait for the context's stream; returns PIC_ERR_CAPACITY or
+ * PIC_ERR_NUMERICS if the device recorded either since the last call. */
+int pic_sync(pic_ctx* ctx);
+
+/* Diagnostics (Sec. "Simulation Results", Figs. 5-9), written to host memory:
+ *  0 PHI      time-averaged potential, V, N+1 nodes
+ *  1 NE 2 NI  time-averaged densities, m^-3, N+1 nodes
+ *  3 GAMMA_E 4 GAMMA_I  time-averaged particle fluxes, m^-2 s^-1
+ *  5 VE 6 VI  mean velocities Gamma/n, m/s
+ *  7 EEDF     electron energies in the central 10% of the gap, 256 x 0.25 eV
+ *  8 IEDF_L 9 IEDF_R  Ar+ impact energies, 512 bins over [0, 2 V0]
+ * 10 IEADF_L 11 IEADF_R  Ar+ impact energy x angle, 128 x 90 (energy-major)
+ * 12 SPUTTER_E_L 13 SPUTTER_E_R  Al deposition energies, 600 x 0.5 eV
+ * 14 SPUTTER_ANG_L 15 SPUTTER_ANG_R  Al deposition angles, 90 x 1 deg
+ * 16 TP_DENS  time-averaged Al density, m^-3;  17 TP_V  Al mean v_x, m/s
+ * 18 E        instantaneous field, V/m;  19 PHI_NOW  instantaneous potential
+ * Histograms are raw counts.  Writes min(cap, size) values, *n_written = size. */
+enum pic_diag_kind {
+    PIC_DIAG_PHI = 0, PIC_DIAG_NE, PIC_DIAG_NI, PIC_DIAG_GAMMA_E, PIC_DIAG_GAMMA_I, PIC_DIAG_VE,
+    PIC_DIAG_VI, PIC_DIAG_EEDF, PIC_DIAG_IEDF_L, PIC_DIAG_IEDF_R, PIC_DIAG_IEADF_L,
+    PIC_DIAG_IEADF_R, PIC_DIAG_SPUTTER_E_L, PIC_DIAG_SPUTTER_E_R, PIC_DIAG_SPUTTER_ANG_L,
+    PIC_DIAG_SPUTTER_ANG_R, PIC_DIAG_TP_DENS, PIC_DIAG_TP_V, PIC_DIAG_E, PIC_DIAG_PHI_NOW,
+    PIC_DIAG_COUNT
+};
+int pic_diag(pic_ctx* ctx, int kind, double* host_out, int64_t cap, int64_t* n_written);
+
+/* Restart all time averages and histograms (Sec. "Kinetic Particle
+ * Simulation": averaging once a (periodic) steady state is reached). */
+int pic_reset_averages(pic_ctx* ctx);
+
+/* Event counters, host int64[cap]: n_e, n_i, n_tp (slots in use), step,
+ * tp_step, impacts e L/R, Ar+ L/R, ionisations, sputtered L/R, Al deposited
+ * L/R, numerics, elastic, excitation, CX, isotropic, TP collisions,
+ * capacity.  Synchronises.  *n_written = number of counters (23). */
+int pic_counters(pic_ctx* ctx, int64_t* host_out, int64_t cap, int64_t* n_written);
+
+/* Copy the alive particles of one species to host buffers of length cap
+ * (any may be NULL): xi = x/dx (double, cell units), vx, vy, vz, id.
+ * *n_out = number alive (may exceed cap; then only cap are written). */
+int pic_get_species(pic_ctx* ctx, int species, int64_t cap, double* xi, float* vx, float* vy,
+                    float* vz, uint64_t* id, int64_t* n_out);
+
+/* Replace the particles of one species by n host-side particles.  pos is in
+ * the storage form of the species (uint32 or double, see "Positions").  The
+ * field is re-solved for the new state unless keep_field is nonzero. */
+int pic_set_species(pic_ctx* ctx, int species, int64_t n, const void* pos, const float* vx,
+                    const float* vy, const float* vz, const uint64_t* id, int keep_field);
+
+/* Instantaneous field state, host double/int64 arrays of N+1 (any may be
+ * NULL): E (V/m), phi (V), and the last deposit q_e, q_i in units of 2^-32
+ * superparticles per node. */
+int pic_get_field(pic_ctx* ctx, double* E, double* phi, int64_t* q_e, int64_t* q_i);
+
+/* Overwrite the nodal field used by the next step's interpolation. */
+int pic_set_field(pic_ctx* ctx, const double* E);
+
+/* Launch sputtered atoms from a mono-energetic source (see tp_source). */
+int tp_launch(pic_ctx* ctx, const tp_source* src);
+
+/* Advance the test particles n_steps of tp_dt (Sec. "Test Particle Method":
+ * free flight, sticking at the walls, hard-sphere collisions with a thermal
+ * Ar partner).  If n_alive is not NULL the stream is synchronised and the
+ * number of atoms still in flight is returned. */
+int tp_step(pic_ctx* ctx, int64_t n_steps, int64_t* n_alive);
+
+/* Compact one species now (drop removed slots, counting sort by cell). */
+int pic_compact(pic_ctx* ctx, int species);
+
+/* CUDA-event timing of the per-step kernel launches on the context's stream.
+ * pic_timing(ctx, 1) starts recording; pic_kernel_time returns the summed
+ * device time (ms) and launch count of kind 0 = PIC step kernel,
+ * 1 = TP step kernel, 2 = compaction, since timing was (re)enabled. */
+int pic_timing(pic_ctx* ctx, int enable);
+int pic_kernel_time(pic_ctx* ctx, int kind, double* ms, int64_t* launches);
+
+/* Derived quantities of the discharge, host double[8]: n_gas, dx,
+ * nu_max_e, nu_max_i, P_max_e, P_max_i, eps_max, Lambda. */
+int pic_derived(pic_ctx* ctx, double* host_out8);
+
+/* ---- stateless hot-path operations on caller device buffers ---- */
+
+/* Linear (cloud-in-cell) charge assignment (Sec. "Charge Assignment"):
+ * adds 2^32 - floor(f 2^32) to node j and floor(f 2^32) to node j+1 for each
+ * of the n particles at device positions pos (uint32 fixed point when
+ * pos_precision = 32, double cell units when 64), j = floor(xi), f = xi - j.
+ * Removed slots are skipped.  q: device int64[n_cells+1], accumulated into
+ * (not cleared).  Exact and independent of particle order. */
+int pic_op_deposit(const void* pos, int pos_precision, int64_t n, int32_t n_cells, int64_t* q,
+                   void* stream);
+
+/* Field solve (Sec. "EM Field Solver"): from device int64 node counts q_i,
+ * q_e (units of 2^-32 superparticles of weight w), solve
+ * (phi[m+1] - 2 phi[m] + phi[m-1]) / dx^2 = -rho[m]/eps0 with phi[0] =
+ * v_left, phi[N] = 0, and E = -dphi/dx (central inside, half-cell Gauss on
+ * the electrodes).  phi, E: device double[n_cells+1]. */
+int pic_op_poisson(const int64_t* q_i, const int64_t* q_e, int32_t n_cells, double dx, double weight,
+                   double v_left, double* phi, double* E, void* stream);
+
+const char* pic_strerror(int code);
+const char* pic_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIC_GB300_H */

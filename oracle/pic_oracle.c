@@ -120,7 +120,7 @@ typedef struct {
     double ngas, dx, nu_max_e, nu_max_i, p_max_e, p_max_i, eps_max;
     /* diagnostics */
     double *sum_q[2], *sum_phi, *sum_flux[2], *tp_dens, *tp_vx;
-    int64_t n_avg, n_flux, n_tp_samp;
+    int64_t n_avg, n_flux, n_tp_samp, tp_launched;
     int64_t *iedf[2], *ieadf[2], *eedf, *sp_e[2], *sp_ang[2];
     int64_t cnt[C_NCOUNT];
 } orc_state;
@@ -738,8 +738,10 @@ void orc_tp_step(orc_state *S, int64_t nsteps, double dt_tp)
             }
         }
         /* grid moments of the TP density and mean velocity (Sec. "Limitations
-         * and Constraints" of the TPM: cell-based averages) */
-        for (int64_t k = 0; k < p->n; k++) {
+         * and Constraints" of the TPM: cell-based averages), sampled every
+         * diag_every TP steps */
+        int samp = S->P.diag_every > 0 && (s + 1) % (uint32_t)S->P.diag_every == 0;
+        for (int64_t k = 0; samp && k < p->n; k++) {
             if (!p->alive[k]) continue;
             double j = floor(p->xi[k]);
             double f = p->xi[k] - j;
@@ -749,19 +751,22 @@ void orc_tp_step(orc_state *S, int64_t nsteps, double dt_tp)
             S->tp_vx[m] += (1.0 - f) * p->vx[k];
             S->tp_vx[m + 1] += f * p->vx[k];
         }
-        S->n_tp_samp++;
+        if (samp) S->n_tp_samp++;
         S->tp_step = s + 1;
     }
 }
 
 /* Mono-energetic source: n atoms launched from the left electrode with a
- * Thompson energy (cut off at Lambda E_ion) and a cosine angle; ids tag|k. */
+ * Thompson energy (cut off at Lambda E_ion) and a cosine angle; ids
+ * tag | (atoms launched before + k). */
 void orc_tp_launch(orc_state *S, int64_t n, double E_ion)
 {
     double Emax = lambda_ar_al() * E_ion;
     double N = (double)S->P.ncell;
+    int64_t id0 = S->tp_launched;
+    S->tp_launched += n;
     for (int64_t k = 0; k < n; k++) {
-        uint64_t id = TAG[SP_TP] | (uint64_t)k;
+        uint64_t id = TAG[SP_TP] | (uint64_t)(id0 + k);
         uint32_t ce[4];
         draw(S->P.seed, id, 0, PUR_TP_LAUNCH, ce);
         double v[3];

@@ -1,0 +1,261 @@
+"""GB300 engine for the PIC/MCC + test-particle hot path of arXiv:1607.04069.
+
+A thin ctypes binding of the C ABI in ``include/pic_gb300.h``: argument
+marshalling only -- every step of the method runs in the CUDA kernels of
+``_build/libpic_gb300.so``.  There is no CPU fallback: if the library is not
+built, every entry point raises.  PyTorch supplies streams and the device
+buffers of the stateless operations.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import workloads  # noqa: F401  (input recipes, no method arithmetic)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpic_gb300.so")
+_lib = None
+
+SPECIES = {"e": 0, "i": 1, "tp": 2}
+DIAG = {"phi": 0, "n_e": 1, "n_i": 2, "gamma_e": 3, "gamma_i": 4, "v_e": 5, "v_i": 6, "eedf": 7,
+        "iedf_l": 8, "iedf_r": 9, "ieadf_l": 10, "ieadf_r": 11, "sputter_e_l": 12,
+        "sputter_e_r": 13, "sputter_ang_l": 14, "sputter_ang_r": 15, "tp_dens": 16, "tp_v": 17,
+        "E": 18, "phi_now": 19}
+COUNTERS = ["n_e_slots", "n_i_slots", "n_tp_slots", "step", "tp_step", "imp_e_l", "imp_e_r",
+            "imp_i_l", "imp_i_r", "ionizations", "sputtered_l", "sputtered_r", "tp_dep_l",
+            "tp_dep_r", "numerics", "elastic", "excitation", "cx", "iso", "tp_coll", "capacity"]
+KERNEL = {"step": 0, "tp": 1, "compact": 2}
+
+
+class PicError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+class PicParams(C.Structure):
+    """Mirror of ``pic_params``."""
+    _fields_ = [("gap_m", C.c_double), ("pressure_pa", C.c_double), ("gas_temp_k", C.c_double),
+                ("rf_freq_hz", C.c_double), ("rf_volt_v", C.c_double), ("weight", C.c_double),
+                ("dt", C.c_double), ("te0_ev", C.c_double), ("ti0_ev", C.c_double),
+                ("tp_dt", C.c_double), ("sigma_tp", C.c_double), ("n_e0", C.c_int64),
+                ("n_i0", C.c_int64), ("cap_e", C.c_int64), ("cap_i", C.c_int64),
+                ("cap_tp", C.c_int64), ("seed", C.c_uint64), ("n_cells", C.c_int32),
+                ("pos_precision", C.c_int32), ("sputter_enable", C.c_int32),
+                ("tp_every", C.c_int32), ("diag_every", C.c_int32), ("sort_every_e", C.c_int32),
+                ("sort_every_i", C.c_int32), ("sort_every_tp", C.c_int32),
+                ("ctas_per_sm", C.c_int32), ("strict", C.c_int32)]
+
+
+class TpSource(C.Structure):
+    _fields_ = [("n", C.c_int64), ("e_ion_ev", C.c_double)]
+
+
+def lib():
+    """Load the engine library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"CUDA engine library missing ({LIB_PATH}); build it with "
+                              "`python -m paper_1607_04069_gb300.build`")
+        L = C.CDLL(LIB_PATH)
+        vp, i64, i32, dbl, pi64 = C.c_void_p, C.c_int64, C.c_int32, C.c_double, C.POINTER(C.c_int64)
+        sig = {
+            "pic_params_default": [C.POINTER(PicParams)],
+            "pic_create": [C.POINTER(PicParams), vp, C.POINTER(vp)],
+            "pic_step": [vp, i64],
+            "pic_sync": [vp],
+            "pic_diag": [vp, C.c_int, vp, i64, pi64],
+            "pic_reset_averages": [vp],
+            "pic_counters": [vp, vp, i64, pi64],
+            "pic_get_species": [vp, C.c_int, i64, vp, vp, vp, vp, vp, pi64],
+            "pic_set_species": [vp, C.c_int, i64, vp, vp, vp, vp, vp, C.c_int],
+            "pic_get_field": [vp, vp, vp, vp, vp],
+            "pic_set_field": [vp, vp],
+            "tp_launch": [vp, C.POINTER(TpSource)],
+            "tp_step": [vp, i64, pi64],
+            "pic_compact": [vp, C.c_int],
+            "pic_timing": [vp, C.c_int],
+            "pic_kernel_time": [vp, C.c_int, C.POINTER(dbl), pi64],
+            "pic_derived": [vp, vp],
+            "pic_op_deposit": [vp, C.c_int, i64, i32, vp, vp],
+            "pic_op_poisson": [vp, vp, i32, dbl, dbl, dbl, vp, vp, vp],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = C.c_int
+        L.pic_destroy.argtypes = [vp]
+        L.pic_destroy.restype = None
+        L.pic_strerror.argtypes = [C.c_int]
+        L.pic_strerror.restype = C.c_char_p
+        L.pic_last_error.argtypes = []
+        L.pic_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        L = lib()
+        raise PicError(rc, f"{L.pic_strerror(rc).decode()}: {L.pic_last_error().decode()}")
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def default_params() -> PicParams:
+    p = PicParams()
+    _check(lib().pic_params_default(C.byref(p)))
+    return p
+
+
+def params_from_workload(cfg: dict, **over) -> PicParams:
+    """Fill a PicParams from a workload dict (see ``workloads``)."""
+    p = default_params()
+    for name, _ in PicParams._fields_:
+        if name in cfg:
+            setattr(p, name, cfg[name])
+    for k, v in over.items():
+        setattr(p, k, v)
+    return p
+
+
+class Discharge:
+    """One discharge on the current CUDA device (``pic_create`` .. ``pic_destroy``)."""
+
+    def __init__(self, params, stream=None):
+        if isinstance(params, dict):
+            params = params_from_workload(params)
+        self.params = params
+        self.stream = _stream_handle(stream)
+        h = C.c_void_p()
+        _check(lib().pic_create(C.byref(params), C.c_void_p(self.stream), C.byref(h)))
+        self.h = h
+        self.n_cells = params.n_cells
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pic_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def step(self, n=1):
+        _check(lib().pic_step(self.h, int(n)))
+
+    def sync(self):
+        _check(lib().pic_sync(self.h))
+
+    def diag(self, kind) -> np.ndarray:
+        k = DIAG[kind] if isinstance(kind, str) else int(kind)
+        n = C.c_int64()
+        _check(lib().pic_diag(self.h, k, None, 0, C.byref(n)))
+        out = np.zeros(n.value)
+        _check(lib().pic_diag(self.h, k, _ptr(out), out.size, C.byref(n)))
+        return out
+
+    def reset_averages(self):
+        _check(lib().pic_reset_averages(self.h))
+
+    def counters(self) -> dict:
+        out = np.zeros(64, dtype=np.int64)
+        n = C.c_int64()
+        _check(lib().pic_counters(self.h, _ptr(out), out.size, C.byref(n)))
+        return dict(zip(COUNTERS, out[: n.value].tolist()))
+
+    def get_species(self, s) -> dict:
+        s = SPECIES.get(s, s)
+        n = C.c_int64()
+        _check(lib().pic_get_species(self.h, s, 0, None, None, None, None, None, C.byref(n)))
+        m = n.value
+        xi = np.zeros(m)
+        v = [np.zeros(m, dtype=np.float32) for _ in range(3)]
+        ids = np.zeros(m, dtype=np.uint64)
+        _check(lib().pic_get_species(self.h, s, m, _ptr(xi), *[_ptr(a) for a in v], _ptr(ids),
+                                     C.byref(n)))
+        return {"xi": xi, "vx": v[0], "vy": v[1], "vz": v[2], "id": ids}
+
+    def set_species(self, s, pos, vx, vy, vz, ids, keep_field=False):
+        s = SPECIES.get(s, s)
+        p64 = self.params.pos_precision == 64 and s != 2
+        pos = np.ascontiguousarray(pos, dtype=np.float64 if p64 else np.uint32)
+        arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (vx, vy, vz)]
+        ids = np.ascontiguousarray(ids, dtype=np.uint64)
+        _check(lib().pic_set_species(self.h, s, pos.size, _ptr(pos), *[_ptr(a) for a in arrs],
+                                     _ptr(ids), int(bool(keep_field))))
+
+    def get_field(self) -> dict:
+        n = self.n_cells + 1
+        E, phi = np.zeros(n), np.zeros(n)
+        qe, qi = np.zeros(n, dtype=np.int64), np.zeros(n, dtype=np.int64)
+        _check(lib().pic_get_field(self.h, _ptr(E), _ptr(phi), _ptr(qe), _ptr(qi)))
+        return {"E": E, "phi": phi, "q_e": qe, "q_i": qi}
+
+    def set_field(self, E):
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        _check(lib().pic_set_field(self.h, _ptr(E)))
+
+    def tp_launch(self, n, e_ion_ev):
+        src = TpSource(int(n), float(e_ion_ev))
+        _check(lib().tp_launch(self.h, C.byref(src)))
+
+    def tp_step(self, n=1, count_alive=True):
+        a = C.c_int64()
+        _check(lib().tp_step(self.h, int(n), C.byref(a) if count_alive else None))
+        return a.value if count_alive else None
+
+    def compact(self, s):
+        _check(lib().pic_compact(self.h, SPECIES.get(s, s)))
+
+    def timing(self, enable=True):
+        _check(lib().pic_timing(self.h, int(bool(enable))))
+
+    def kernel_time(self, kind="step"):
+        ms, n = C.c_double(), C.c_int64()
+        _check(lib().pic_kernel_time(self.h, KERNEL.get(kind, kind), C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+    def derived(self) -> dict:
+        out = np.zeros(8)
+        _check(lib().pic_derived(self.h, _ptr(out)))
+        keys = ["n_gas", "dx", "nu_max_e", "nu_max_i", "p_max_e", "p_max_i", "eps_max", "lambda"]
+        return dict(zip(keys, out.tolist()))
+
+
+# ------------------------------------------------------------------ stateless ops (torch buffers)
+def op_deposit(pos, n_cells: int, q=None, stream=None):
+    """Linear charge assignment of device positions ``pos`` (torch uint32 /
+    int32 fixed point or float64 cell units) into int64 ``q`` (returned)."""
+    import torch
+    prec = 64 if pos.dtype == torch.float64 else 32
+    if q is None:
+        q = torch.zeros(n_cells + 1, dtype=torch.int64, device=pos.device)
+    _check(lib().pic_op_deposit(C.c_void_p(pos.data_ptr()), prec, pos.numel(), int(n_cells),
+                                C.c_void_p(q.data_ptr()), C.c_void_p(_stream_handle(stream))))
+    return q
+
+
+def op_poisson(q_i, q_e, n_cells: int, dx: float, weight: float, v_left: float, stream=None):
+    """Field solve from device int64 node counts; returns (phi, E) float64 tensors."""
+    import torch
+    phi = torch.empty(n_cells + 1, dtype=torch.float64, device=q_i.device)
+    E = torch.empty_like(phi)
+    _check(lib().pic_op_poisson(C.c_void_p(q_i.data_ptr()), C.c_void_p(q_e.data_ptr()),
+                                int(n_cells), float(dx), float(weight), float(v_left),
+                                C.c_void_p(phi.data_ptr()), C.c_void_p(E.data_ptr()),
+                                C.c_void_p(_stream_handle(stream))))
+    return phi, E

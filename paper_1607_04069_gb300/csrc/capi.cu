@@ -1,0 +1,794 @@
+// capi.cu -- host side of the C ABI declared in include/pic_gb300.h.
+//
+// Owns the device state of one discharge (one allocation, carved into the
+// structure-of-arrays particle store, the per-step histograms and the
+// diagnostic accumulators), schedules the per-step kernels on the caller's
+// stream and converts diagnostics to physical units on the host.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pic_gb300.h"
+#include "common.cuh"
+#include "launch.h"
+
+using namespace pg;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg)
+{
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? PIC_ERR_OUT_OF_MEMORY : PIC_ERR_CUDA;
+}
+
+#define CK(expr)                                                         \
+    do {                                                                 \
+        cudaError_t e__ = (expr);                                        \
+        if (e__ != cudaSuccess) return cuda_fail(e__, #expr);            \
+    } while (0)
+
+struct Timer {                       // CUDA-event pairs around launches
+    std::vector<cudaEvent_t> ev;
+    size_t used = 0;
+    double ms = 0.0;
+    long long launches = 0;
+};
+
+}  // namespace
+
+struct pic_ctx {
+    pic_params p;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    Dev d;                           // kernel descriptor (device pointers + constants)
+    Dev d_coupled;                   // same, with the coupled TP time step
+    void* arena = nullptr;
+    size_t arena_bytes = 0, small_bytes = 0;
+    int sms = 0, grid_mover = 0, grid_tp = 0, grid_sort = 0;
+    long long h_step = 0, h_tp_step = 0, tp_launched = 0;
+    double derived[8];
+    bool timing = false;
+    Timer timers[3];
+};
+
+namespace {
+
+bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int ilog2(int v)
+{
+    int k = 0;
+    while ((1 << k) < v) ++k;
+    return k;
+}
+
+// Carve the arena.  Small, zero-initialised items first.
+struct Layout {
+    size_t off = 0;
+    template <typename T>
+    T* take(char* base, size_t count)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T* p = (T*)(base + off);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+void carve(pic_ctx* c, char* base, size_t* small_end, size_t* total)
+{
+    Layout L;
+    const int N1 = c->p.n_cells + 1;
+    Dev& d = c->d;
+    d.ctl = L.take<Ctl>(base, 1);
+    for (int s = 0; s < 2; ++s) {
+        d.q[s] = L.take<unsigned long long>(base, N1);
+        d.q_last[s] = L.take<unsigned long long>(base, N1);
+        d.flux[s] = L.take<long long>(base, N1);
+        d.diag.sum_q[s] = L.take<double>(base, N1);
+        d.diag.sum_flux[s] = L.take<double>(base, N1);
+        d.diag.iedf[s] = L.take<unsigned long long>(base, kNbIedf);
+        d.diag.ieadf[s] = L.take<unsigned long long>(base, kNbIeadfE * kNbAng);
+        d.diag.sp_e[s] = L.take<unsigned long long>(base, kNbSpE);
+        d.diag.sp_ang[s] = L.take<unsigned long long>(base, kNbAng);
+    }
+    d.diag.sum_phi = L.take<double>(base, N1);
+    d.diag.tp_dens = L.take<double>(base, N1);
+    d.diag.tp_vx = L.take<double>(base, N1);
+    d.diag.eedf = L.take<unsigned long long>(base, kNbEedf);
+    d.tp_q = L.take<unsigned long long>(base, N1);
+    d.tp_flux = L.take<long long>(base, N1);
+    d.E32 = L.take<float>(base, N1);
+    d.E64 = L.take<double>(base, N1);
+    d.phi = L.take<double>(base, N1);
+    d.sort_cnt = L.take<unsigned int>(base, c->p.n_cells);
+    d.sort_off = L.take<unsigned int>(base, c->p.n_cells);
+    *small_end = (L.off + 255) & ~(size_t)255;
+    const long long cap[3] = {c->p.cap_e, c->p.cap_i, c->p.cap_tp};
+    for (int s = 0; s < 3; ++s)
+        for (int h = 0; h < 2; ++h) {
+            SpBuf& B = d.buf[s][h];
+            const size_t n = (size_t)(cap[s] > 0 ? cap[s] : 1);
+            if (c->p.pos_precision == 64 && s != kTP) B.pos = L.take<double>(base, n);
+            else B.pos = L.take<uint32_t>(base, n);
+            B.vx = L.take<float>(base, n);
+            B.vy = L.take<float>(base, n);
+            B.vz = L.take<float>(base, n);
+            B.id = L.take<uint64_t>(base, n);
+        }
+    *total = (L.off + 255) & ~(size_t)255;
+}
+
+int validate(const pic_params* p)
+{
+    if (!p) return fail(PIC_ERR_INVALID_ARG, "params is NULL");
+    if (!(p->gap_m > 0) || !(p->dt > 0) || !(p->gas_temp_k > 0) || !(p->pressure_pa >= 0) ||
+        !(p->weight >= 0) || !(p->rf_freq_hz >= 0))
+        return fail(PIC_ERR_INVALID_ARG, "gap, dt and gas temperature must be > 0; pressure, weight, "
+                                         "frequency >= 0");
+    if (!pow2(p->n_cells) || p->n_cells < 4 || p->n_cells > 4096)
+        return fail(PIC_ERR_INVALID_ARG, "n_cells must be a power of two in [4, 4096]");
+    if (p->pos_precision != 32 && p->pos_precision != 64)
+        return fail(PIC_ERR_INVALID_ARG, "pos_precision must be 32 or 64");
+    if (p->n_e0 < 0 || p->n_i0 < 0 || p->cap_e < p->n_e0 || p->cap_i < p->n_i0 || p->cap_tp < 0)
+        return fail(PIC_ERR_INVALID_ARG, "counts must be >= 0 and within the capacities");
+    if (p->cap_e >= (1ll << 31) || p->cap_i >= (1ll << 31) || p->cap_tp >= (1ll << 32) - 1)
+        return fail(PIC_ERR_INVALID_ARG, "capacity above the 32-bit slot index range");
+    if (p->tp_every < 0 || p->diag_every < 0 || p->sort_every_e < 0 || p->sort_every_i < 0 ||
+        p->sort_every_tp < 0 || p->ctas_per_sm < 0)
+        return fail(PIC_ERR_INVALID_ARG, "negative period");
+    if (!(p->tp_dt >= 0) || !(p->sigma_tp >= 0)) return fail(PIC_ERR_INVALID_ARG, "tp_dt, sigma_tp >= 0");
+    return PIC_OK;
+}
+
+// Null-collision bounds (Sec. "Particle Collisions"): nu_max = max over energy
+// of n sigma_sum(eps) sqrt(2 eps/m_r).  Electrons: sum of the closed-form
+// maxima of the three cross sections at the highest admitted energy
+// eps_max = 2 V0 + 100 eV.  Ar+: sigma(eps) g is constant, nu_max exact.
+void derive(pic_ctx* c)
+{
+    const pic_params& p = c->p;
+    const double ngas = p.pressure_pa / (kKB * p.gas_temp_k);
+    const double dx = p.gap_m / (double)p.n_cells;
+    const double eps_max = 2.0 * p.rf_volt_v + 100.0;
+    const double sig_ion_max = kLotzA * kLotzQ / (std::exp(1.0) * kIonTh * kIonTh);
+    const double sig_sum_max = kSigEl + kExcSig + sig_ion_max;
+    const double nu_max_e = ngas * sig_sum_max * std::sqrt(2.0 * eps_max * kQE / kME);
+    const double mr = kMAR / 2.0;
+    const double nu_max_i = 2.0 * ngas * kArpSig * std::sqrt(2.0 * kQE / mr);
+    const double p_max_e = 1.0 - std::exp(-nu_max_e * p.dt);
+    const double p_max_i = 1.0 - std::exp(-nu_max_i * p.dt);
+    const double lam = 4.0 * kMAR * kMAL / ((kMAR + kMAL) * (kMAR + kMAL));
+    double* o = c->derived;
+    o[0] = ngas; o[1] = dx; o[2] = nu_max_e; o[3] = nu_max_i; o[4] = p_max_e; o[5] = p_max_i;
+    o[6] = eps_max; o[7] = lam;
+
+    Dev& d = c->d;
+    d.ncell = p.n_cells;
+    d.kshift = ilog2(p.n_cells);
+    d.pos64 = p.pos_precision == 64;
+    d.L = p.gap_m;
+    d.dx = dx;
+    d.inv_dx = 1.0 / dx;
+    d.A = dx * kQE * p.weight / (4294967296.0 * kEPS0);
+    d.V0 = p.rf_volt_v;
+    d.omega = 2.0 * kPI * p.rf_freq_hz;
+    d.dt = p.dt;
+    d.qm_dt[kE] = (float)(-kQE / kME * p.dt);
+    d.qm_dt[kI] = (float)(kQE / kMAR * p.dt);
+    d.push32 = (float)(p.dt * 4294967296.0 / p.gap_m);
+    d.push64 = p.dt / dx;
+    d.thr[kE] = (unsigned long long)std::ceil(p_max_e * 4294967296.0);
+    d.thr[kI] = (unsigned long long)std::ceil(p_max_i * 4294967296.0);
+    d.ngas_f = (float)ngas;
+    d.nu_max_e = (float)nu_max_e;
+    d.nu_max_i = (float)nu_max_i;
+    d.eps_max = (float)eps_max;
+    d.vth_gas = (float)std::sqrt(kKB * p.gas_temp_k / kMAR);
+    d.tp_scale = (float)(p.tp_dt * 4294967296.0 / p.gap_m);
+    d.tp_nsig_dt = (float)(ngas * p.sigma_tp * p.tp_dt);
+    d.Emax_hist = (float)(2.0 * p.rf_volt_v > 0 ? 2.0 * p.rf_volt_v : 1.0);
+    d.sputter = p.sputter_enable != 0;
+    d.diag_every = p.diag_every;
+    d.eedf_lo = (unsigned int)std::ceil(0.45 * 4294967296.0);
+    d.eedf_hi = (unsigned int)std::ceil(0.55 * 4294967296.0);
+    d.eedf_lo64 = 0.45 * p.n_cells;
+    d.eedf_hi64 = 0.55 * p.n_cells;
+    d.seed = p.seed;
+    c->d_coupled = d;
+    const double dtc = p.tp_every * p.dt;
+    c->d_coupled.tp_scale = (float)(dtc * 4294967296.0 / p.gap_m);
+    c->d_coupled.tp_nsig_dt = (float)(ngas * p.sigma_tp * dtc);
+}
+
+void sync_desc(pic_ctx* c)          // keep the coupled descriptor's pointers in step
+{
+    const Dev keep = c->d_coupled;
+    c->d_coupled = c->d;
+    c->d_coupled.tp_scale = keep.tp_scale;
+    c->d_coupled.tp_nsig_dt = keep.tp_nsig_dt;
+}
+
+int timer_begin(pic_ctx* c, int k, cudaEvent_t* stop)
+{
+    *stop = nullptr;
+    if (!c->timing) return PIC_OK;
+    Timer& t = c->timers[k];
+    if (t.used + 2 > t.ev.size()) {
+        for (int i = 0; i < 64; ++i) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e));
+            t.ev.push_back(e);
+        }
+    }
+    CK(cudaEventRecord(t.ev[t.used], c->stream));
+    *stop = t.ev[t.used + 1];
+    t.used += 2;
+    return PIC_OK;
+}
+
+int timer_end(pic_ctx* c, cudaEvent_t stop)
+{
+    if (stop) CK(cudaEventRecord(stop, c->stream));
+    return PIC_OK;
+}
+
+int timers_collect(pic_ctx* c)
+{
+    for (int k = 0; k < 3; ++k) {
+        Timer& t = c->timers[k];
+        for (size_t i = 0; i + 1 < t.used; i += 2) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, t.ev[i], t.ev[i + 1]));
+            t.ms += ms;
+            t.launches += 1;
+        }
+        t.used = 0;
+    }
+    return PIC_OK;
+}
+
+int run_tp_step(pic_ctx* c, const Dev& d)
+{
+    cudaEvent_t stop;
+    int rc = timer_begin(c, 1, &stop);
+    if (rc) return rc;
+    CK(launch_tp_step(d, c->grid_tp, c->stream));
+    rc = timer_end(c, stop);
+    if (rc) return rc;
+    c->h_tp_step++;
+    if (c->p.sort_every_tp > 0 && c->h_tp_step % c->p.sort_every_tp == 0) {
+        rc = timer_begin(c, 2, &stop);
+        if (rc) return rc;
+        CK(launch_sort(c->d, kTP, c->grid_sort, c->stream));
+        rc = timer_end(c, stop);
+    }
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pic_params_default(pic_params* p)
+{
+    if (!p) return fail(PIC_ERR_INVALID_ARG, "p is NULL");
+    std::memset(p, 0, sizeof(*p));
+    p->gap_m = 0.025;
+    p->pressure_pa = 3.0;
+    p->gas_temp_k = 300.0;
+    p->rf_freq_hz = 13.56e6;
+    p->rf_volt_v = 100.0;
+    p->n_e0 = p->n_i0 = 20000;
+    p->weight = 1e15 * p->gap_m / 20000.0;
+    p->dt = 1.0 / 13.56e6 / 400.0;
+    p->te0_ev = 2.0;
+    p->ti0_ev = 0.026;
+    p->tp_dt = 1e-9;
+    p->sigma_tp = 3e-19;
+    p->seed = 1234;
+    p->n_cells = 128;
+    p->pos_precision = 64;
+    p->diag_every = 10;
+    p->sort_every_e = 20;
+    p->sort_every_i = 200;
+    p->sort_every_tp = 50;
+    return PIC_OK;
+}
+
+int pic_create(const pic_params* pin, void* stream, pic_ctx** out)
+{
+    if (!out) return fail(PIC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int rc = validate(pin);
+    if (rc) return rc;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
+        return fail(PIC_ERR_NO_DEVICE, "no CUDA device visible");
+    pic_ctx* c = new pic_ctx();
+    c->p = *pin;
+    if (c->p.cap_e == 0) c->p.cap_e = c->p.n_e0 + c->p.n_e0 / 4 + 65536;
+    if (c->p.cap_i == 0) c->p.cap_i = c->p.n_i0 + c->p.n_i0 / 4 + 65536;
+    if (c->p.cap_tp == 0) c->p.cap_tp = 65536;
+    c->stream = (cudaStream_t)stream;
+    cudaGetDevice(&c->device);
+    derive(c);
+    if (c->p.strict && c->p.n_e0 > 0) {
+        const double n0 = c->p.weight * (double)c->p.n_e0 / c->p.gap_m;
+        const double lam_d = std::sqrt(kEPS0 * c->p.te0_ev / (n0 * kQE));
+        const double wp = std::sqrt(n0 * kQE * kQE / (kEPS0 * kME));
+        if (!(c->d.dx < lam_d) || !(wp * c->p.dt < 1.0)) {
+            char buf[160];
+            std::snprintf(buf, sizeof buf, "dx = %.3g m vs lambda_D = %.3g m, w_p dt = %.3g", c->d.dx,
+                          lam_d, wp * c->p.dt);
+            delete c;
+            return fail(PIC_ERR_UNSTABLE_PARAMS, buf);
+        }
+    }
+    size_t small_end = 0, total = 0;
+    carve(c, nullptr, &small_end, &total);
+    cudaError_t e = cudaMalloc(&c->arena, total);
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_fail(e, "cudaMalloc(state)");
+    }
+    c->arena_bytes = total;
+    c->small_bytes = small_end;
+    carve(c, (char*)c->arena, &small_end, &total);
+    sync_desc(c);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, c->device) != cudaSuccess) {
+        pic_destroy(c);
+        return fail(PIC_ERR_CUDA, "cudaGetDeviceProperties");
+    }
+    c->sms = prop.multiProcessorCount;
+    const int per_sm = c->p.ctas_per_sm > 0 ? c->p.ctas_per_sm : 4;
+    c->grid_mover = c->sms * per_sm;
+    c->grid_tp = c->sms * 4;
+    c->grid_sort = c->sms * 8;
+
+    Ctl h;
+    std::memset(&h, 0, sizeof h);
+    h.n[kE] = c->p.n_e0;
+    h.n[kI] = c->p.n_i0;
+    h.cap[kE] = c->p.cap_e;
+    h.cap[kI] = c->p.cap_i;
+    h.cap[kTP] = c->p.cap_tp;
+    e = cudaMemsetAsync(c->arena, 0, c->small_bytes, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d.ctl, &h, sizeof h, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = launch_init(c->d, kE, c->p.n_e0, (float)std::sqrt(c->p.te0_ev * kQE / kME), c->stream);
+    if (e == cudaSuccess) e = launch_init(c->d, kI, c->p.n_i0, (float)std::sqrt(c->p.ti0_ev * kQE / kMAR), c->stream);
+    if (e == cudaSuccess) e = launch_mover(c->d, c->grid_mover, 1, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        pic_destroy(c);
+        return cuda_fail(e, "pic_create initial loading");
+    }
+    *out = c;
+    return PIC_OK;
+}
+
+void pic_destroy(pic_ctx* c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (auto& t : c->timers)
+        for (auto ev : t.ev) cudaEventDestroy(ev);
+    if (c->arena) cudaFree(c->arena);
+    delete c;
+}
+
+int pic_step(pic_ctx* c, int64_t n)
+{
+    if (!c || n < 0) return fail(PIC_ERR_INVALID_ARG, "bad context or step count");
+    CK(cudaSetDevice(c->device));
+    for (int64_t k = 0; k < n; ++k) {
+        cudaEvent_t stop;
+        int rc = timer_begin(c, 0, &stop);
+        if (rc) return rc;
+        CK(launch_mover(c->d, c->grid_mover, 0, c->stream));
+        rc = timer_end(c, stop);
+        if (rc) return rc;
+        c->h_step++;
+        for (int s = 0; s < 2; ++s) {
+            const int every = s == kE ? c->p.sort_every_e : c->p.sort_every_i;
+            if (every > 0 && c->h_step % every == 0) {
+                rc = timer_begin(c, 2, &stop);
+                if (rc) return rc;
+                CK(launch_sort(c->d, s, c->grid_sort, c->stream));
+                rc = timer_end(c, stop);
+                if (rc) return rc;
+            }
+        }
+        if (c->p.sputter_enable && c->p.tp_every > 0 && c->h_step % c->p.tp_every == 0) {
+            rc = run_tp_step(c, c->d_coupled);
+            if (rc) return rc;
+        }
+        if (c->timing && c->timers[0].used >= 4096) {
+            CK(cudaStreamSynchronize(c->stream));
+            rc = timers_collect(c);
+            if (rc) return rc;
+        }
+    }
+    return PIC_OK;
+}
+
+int pic_sync(pic_ctx* c)
+{
+    if (!c) return fail(PIC_ERR_INVALID_ARG, "ctx is NULL");
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(c->stream));
+    int rc = timers_collect(c);
+    if (rc) return rc;
+    unsigned int err = 0;
+    CK(cudaMemcpy(&err, &c->d.ctl->err, sizeof err, cudaMemcpyDeviceToHost));
+    if (err) {
+        CK(cudaMemsetAsync(&c->d.ctl->err, 0, sizeof err, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        if (err & kErrCapacity) return fail(PIC_ERR_CAPACITY, "a birth or launch exceeded the capacity");
+        if (err & kErrNumerics) return fail(PIC_ERR_NUMERICS, "electron energy above eps_max");
+    }
+    return PIC_OK;
+}
+
+int pic_timing(pic_ctx* c, int enable)
+{
+    if (!c) return fail(PIC_ERR_INVALID_ARG, "ctx is NULL");
+    CK(cudaStreamSynchronize(c->stream));
+    int rc = timers_collect(c);
+    if (rc) return rc;
+    for (auto& t : c->timers) {
+        t.ms = 0.0;
+        t.launches = 0;
+    }
+    c->timing = enable != 0;
+    return PIC_OK;
+}
+
+int pic_kernel_time(pic_ctx* c, int kind, double* ms, int64_t* launches)
+{
+    if (!c || kind < 0 || kind > 2) return fail(PIC_ERR_INVALID_ARG, "bad kind");
+    CK(cudaStreamSynchronize(c->stream));
+    int rc = timers_collect(c);
+    if (rc) return rc;
+    if (ms) *ms = c->timers[kind].ms;
+    if (launches) *launches = c->timers[kind].launches;
+    return PIC_OK;
+}
+
+int pic_derived(pic_ctx* c, double* out)
+{
+    if (!c || !out) return fail(PIC_ERR_INVALID_ARG, "NULL argument");
+    std::memcpy(out, c->derived, sizeof c->derived);
+    return PIC_OK;
+}
+
+static int read_ctl(pic_ctx* c, Ctl* h)
+{
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpy(h, c->d.ctl, sizeof *h, cudaMemcpyDeviceToHost));
+    return PIC_OK;
+}
+
+int pic_diag(pic_ctx* c, int kind, double* out, int64_t cap, int64_t* n_written)
+{
+    if (!c || (!out && cap > 0) || kind < 0 || kind >= PIC_DIAG_COUNT)
+        return fail(PIC_ERR_INVALID_ARG, "bad diag request");
+    CK(cudaSetDevice(c->device));
+    Ctl h;
+    int rc = read_ctl(c, &h);
+    if (rc) return rc;
+    const int N = c->p.n_cells, N1 = N + 1;
+    const double dx = c->d.dx, w = c->p.weight;
+    std::vector<double> v;
+    auto getd = [&](const double* src, size_t n, std::vector<double>& dst) -> int {
+        dst.resize(n);
+        CK(cudaMemcpy(dst.data(), src, n * sizeof(double), cudaMemcpyDeviceToHost));
+        return PIC_OK;
+    };
+    auto getu = [&](const unsigned long long* src, size_t n, std::vector<double>& dst) -> int {
+        std::vector<unsigned long long> t(n);
+        CK(cudaMemcpy(t.data(), src, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+        dst.assign(t.begin(), t.end());
+        return PIC_OK;
+    };
+    auto vol = [&](int m) { return (m == 0 || m == N) ? 0.5 * dx : dx; };
+    std::vector<double> a, b;
+    switch (kind) {
+    case PIC_DIAG_PHI:
+        if ((rc = getd(c->d.diag.sum_phi, N1, v))) return rc;
+        for (auto& x : v) x = h.n_avg ? x / (double)h.n_avg : 0.0;
+        break;
+    case PIC_DIAG_NE: case PIC_DIAG_NI:
+        if ((rc = getd(c->d.diag.sum_q[kind - PIC_DIAG_NE], N1, v))) return rc;
+        for (int m = 0; m < N1; ++m) v[m] = h.n_avg ? w * v[m] / (4294967296.0 * vol(m) * h.n_avg) : 0.0;
+        break;
+    case PIC_DIAG_GAMMA_E: case PIC_DIAG_GAMMA_I:
+        if ((rc = getd(c->d.diag.sum_flux[kind - PIC_DIAG_GAMMA_E], N1, v))) return rc;
+        for (int m = 0; m < N1; ++m) v[m] = h.n_flux ? w * v[m] / (vol(m) * h.n_flux) : 0.0;
+        break;
+    case PIC_DIAG_VE: case PIC_DIAG_VI: {
+        const int s = kind - PIC_DIAG_VE;
+        if ((rc = getd(c->d.diag.sum_flux[s], N1, a))) return rc;
+        if ((rc = getd(c->d.diag.sum_q[s], N1, b))) return rc;
+        v.resize(N1);
+        for (int m = 0; m < N1; ++m) {
+            // Gamma/n with both averages: (sum_flux/n_flux) / (sum_q / (2^32 n_avg))
+            const double nq = b[m] / (4294967296.0 * (h.n_avg ? h.n_avg : 1));
+            v[m] = (h.n_flux && nq > 0) ? (a[m] / h.n_flux) / nq : 0.0;
+        }
+        break;
+    }
+    case PIC_DIAG_EEDF:
+        if ((rc = getu(c->d.diag.eedf, kNbEedf, v))) return rc;
+        break;
+    case PIC_DIAG_IEDF_L: case PIC_DIAG_IEDF_R:
+        if ((rc = getu(c->d.diag.iedf[kind - PIC_DIAG_IEDF_L], kNbIedf, v))) return rc;
+        break;
+    case PIC_DIAG_IEADF_L: case PIC_DIAG_IEADF_R:
+        if ((rc = getu(c->d.diag.ieadf[kind - PIC_DIAG_IEADF_L], kNbIeadfE * kNbAng, v))) return rc;
+        break;
+    case PIC_DIAG_SPUTTER_E_L: case PIC_DIAG_SPUTTER_E_R:
+        if ((rc = getu(c->d.diag.sp_e[kind - PIC_DIAG_SPUTTER_E_L], kNbSpE, v))) return rc;
+        break;
+    case PIC_DIAG_SPUTTER_ANG_L: case PIC_DIAG_SPUTTER_ANG_R:
+        if ((rc = getu(c->d.diag.sp_ang[kind - PIC_DIAG_SPUTTER_ANG_L], kNbAng, v))) return rc;
+        break;
+    case PIC_DIAG_TP_DENS:
+        if ((rc = getd(c->d.diag.tp_dens, N1, v))) return rc;
+        for (int m = 0; m < N1; ++m) v[m] = h.n_tp_samp ? w * v[m] / (vol(m) * h.n_tp_samp) : 0.0;
+        break;
+    case PIC_DIAG_TP_V:
+        if ((rc = getd(c->d.diag.tp_vx, N1, a))) return rc;
+        if ((rc = getd(c->d.diag.tp_dens, N1, b))) return rc;
+        v.resize(N1);
+        for (int m = 0; m < N1; ++m) v[m] = b[m] > 0 ? a[m] / b[m] : 0.0;
+        break;
+    case PIC_DIAG_E:
+        if ((rc = getd(c->d.E64, N1, v))) return rc;
+        break;
+    case PIC_DIAG_PHI_NOW:
+        if ((rc = getd(c->d.phi, N1, v))) return rc;
+        break;
+    }
+    const int64_t n = (int64_t)v.size();
+    for (int64_t i = 0; i < n && i < cap; ++i) out[i] = v[i];
+    if (n_written) *n_written = n;
+    return PIC_OK;
+}
+
+int pic_reset_averages(pic_ctx* c)
+{
+    if (!c) return fail(PIC_ERR_INVALID_ARG, "ctx is NULL");
+    CK(cudaSetDevice(c->device));
+    const int N1 = c->p.n_cells + 1;
+    const Diag& g = c->d.diag;
+    for (int s = 0; s < 2; ++s) {
+        CK(cudaMemsetAsync(g.sum_q[s], 0, N1 * sizeof(double), c->stream));
+        CK(cudaMemsetAsync(g.sum_flux[s], 0, N1 * sizeof(double), c->stream));
+        CK(cudaMemsetAsync(g.iedf[s], 0, kNbIedf * 8, c->stream));
+        CK(cudaMemsetAsync(g.ieadf[s], 0, kNbIeadfE * kNbAng * 8, c->stream));
+        CK(cudaMemsetAsync(g.sp_e[s], 0, kNbSpE * 8, c->stream));
+        CK(cudaMemsetAsync(g.sp_ang[s], 0, kNbAng * 8, c->stream));
+    }
+    CK(cudaMemsetAsync(g.sum_phi, 0, N1 * sizeof(double), c->stream));
+    CK(cudaMemsetAsync(g.tp_dens, 0, N1 * sizeof(double), c->stream));
+    CK(cudaMemsetAsync(g.tp_vx, 0, N1 * sizeof(double), c->stream));
+    CK(cudaMemsetAsync(g.eedf, 0, kNbEedf * 8, c->stream));
+    CK(cudaMemsetAsync(&c->d.ctl->n_avg, 0, 3 * sizeof(long long), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
+
+int pic_counters(pic_ctx* c, int64_t* out, int64_t cap, int64_t* n_written)
+{
+    if (!c || (!out && cap > 0)) return fail(PIC_ERR_INVALID_ARG, "bad arguments");
+    CK(cudaSetDevice(c->device));
+    Ctl h;
+    int rc = read_ctl(c, &h);
+    if (rc) return rc;
+    int64_t v[5 + kNumCnt];
+    v[0] = h.n[kE]; v[1] = h.n[kI]; v[2] = h.n[kTP]; v[3] = h.step; v[4] = h.tp_step;
+    // order: impacts e L/R, Ar+ L/R, ionisations, sputtered L/R, Al deposited L/R,
+    // numerics, elastic, excitation, CX, isotropic, TP collisions, capacity
+    const int order[kNumCnt] = {kCntImpEL, kCntImpER, kCntImpIL, kCntImpIR, kCntIoniz, kCntSputL,
+                                kCntSputR, kCntTpDepL, kCntTpDepR, kCntNumerics, kCntElastic,
+                                kCntExcit, kCntCx, kCntIso, kCntTpColl, kCntCapacity};
+    for (int i = 0; i < kNumCnt; ++i) v[5 + i] = (int64_t)h.cnt[order[i]];
+    const int64_t n = 5 + kNumCnt;
+    for (int64_t i = 0; i < n && i < cap; ++i) out[i] = v[i];
+    if (n_written) *n_written = n;
+    return PIC_OK;
+}
+
+int pic_get_species(pic_ctx* c, int s, int64_t cap, double* xi, float* vx, float* vy, float* vz,
+                    uint64_t* id, int64_t* n_out)
+{
+    if (!c || s < 0 || s > 2 || cap < 0) return fail(PIC_ERR_INVALID_ARG, "bad arguments");
+    CK(cudaSetDevice(c->device));
+    Ctl h;
+    int rc = read_ctl(c, &h);
+    if (rc) return rc;
+    const long long n = h.n[s];
+    const SpBuf& B = c->d.buf[s][h.cur[s]];
+    const bool p64 = c->p.pos_precision == 64 && s != kTP;
+    std::vector<unsigned char> pos((size_t)n * (p64 ? 8 : 4));
+    std::vector<float> a((size_t)n), b((size_t)n), cc((size_t)n);
+    std::vector<uint64_t> ids((size_t)n);
+    if (n > 0) {
+        CK(cudaMemcpy(pos.data(), B.pos, pos.size(), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(a.data(), B.vx, n * 4, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(b.data(), B.vy, n * 4, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(cc.data(), B.vz, n * 4, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(ids.data(), B.id, n * 8, cudaMemcpyDeviceToHost));
+    }
+    const double scale = (double)c->p.n_cells * 0x1p-32;
+    int64_t m = 0;
+    for (long long k = 0; k < n; ++k) {
+        double x;
+        if (p64) {
+            x = ((const double*)pos.data())[k];
+            if (!(x >= 0.0)) continue;
+        } else {
+            const uint32_t u = ((const uint32_t*)pos.data())[k];
+            if (u == 0) continue;
+            x = (double)u * scale;
+        }
+        if (m < cap) {
+            if (xi) xi[m] = x;
+            if (vx) vx[m] = a[k];
+            if (vy) vy[m] = b[k];
+            if (vz) vz[m] = cc[k];
+            if (id) id[m] = ids[k];
+        }
+        ++m;
+    }
+    if (n_out) *n_out = m;
+    return PIC_OK;
+}
+
+int pic_set_species(pic_ctx* c, int s, int64_t n, const void* pos, const float* vx, const float* vy,
+                    const float* vz, const uint64_t* id, int keep_field)
+{
+    if (!c || s < 0 || s > 2 || n < 0 || (n > 0 && (!pos || !vx || !vy || !vz || !id)))
+        return fail(PIC_ERR_INVALID_ARG, "bad arguments");
+    const long long cap = s == kE ? c->p.cap_e : (s == kI ? c->p.cap_i : c->p.cap_tp);
+    if (n > cap) return fail(PIC_ERR_CAPACITY, "more particles than the species capacity");
+    CK(cudaSetDevice(c->device));
+    Ctl h;
+    int rc = read_ctl(c, &h);
+    if (rc) return rc;
+    const SpBuf& B = c->d.buf[s][h.cur[s]];
+    const bool p64 = c->p.pos_precision == 64 && s != kTP;
+    if (n > 0) {
+        CK(cudaMemcpyAsync(B.pos, pos, (size_t)n * (p64 ? 8 : 4), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(B.vx, vx, (size_t)n * 4, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(B.vy, vy, (size_t)n * 4, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(B.vz, vz, (size_t)n * 4, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(B.id, id, (size_t)n * 8, cudaMemcpyHostToDevice, c->stream));
+    }
+    long long nn = n;
+    CK(cudaMemcpyAsync(&c->d.ctl->n[s], &nn, sizeof nn, cudaMemcpyHostToDevice, c->stream));
+    if (!keep_field && s != kTP) CK(launch_mover(c->d, c->grid_mover, 1, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
+
+int pic_get_field(pic_ctx* c, double* E, double* phi, int64_t* q_e, int64_t* q_i)
+{
+    if (!c) return fail(PIC_ERR_INVALID_ARG, "ctx is NULL");
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(c->stream));
+    const size_t N1 = (size_t)c->p.n_cells + 1;
+    if (E) CK(cudaMemcpy(E, c->d.E64, N1 * 8, cudaMemcpyDeviceToHost));
+    if (phi) CK(cudaMemcpy(phi, c->d.phi, N1 * 8, cudaMemcpyDeviceToHost));
+    if (q_e) CK(cudaMemcpy(q_e, c->d.q_last[kE], N1 * 8, cudaMemcpyDeviceToHost));
+    if (q_i) CK(cudaMemcpy(q_i, c->d.q_last[kI], N1 * 8, cudaMemcpyDeviceToHost));
+    return PIC_OK;
+}
+
+int pic_set_field(pic_ctx* c, const double* E)
+{
+    if (!c || !E) return fail(PIC_ERR_INVALID_ARG, "NULL argument");
+    CK(cudaSetDevice(c->device));
+    const size_t N1 = (size_t)c->p.n_cells + 1;
+    std::vector<float> f(N1);
+    for (size_t m = 0; m < N1; ++m) f[m] = (float)E[m];
+    CK(cudaMemcpyAsync(c->d.E64, E, N1 * 8, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d.E32, f.data(), N1 * 4, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
+
+int tp_launch(pic_ctx* c, const tp_source* src)
+{
+    if (!c || !src || src->n < 0 || !(src->e_ion_ev >= 0)) return fail(PIC_ERR_INVALID_ARG, "bad source");
+    CK(cudaSetDevice(c->device));
+    const float Emax = (float)(c->derived[7] * src->e_ion_ev);
+    CK(launch_tp_launch(c->d, src->n, c->tp_launched, Emax, c->stream));
+    c->tp_launched += src->n;
+    return PIC_OK;
+}
+
+int tp_step(pic_ctx* c, int64_t n, int64_t* n_alive)
+{
+    if (!c || n < 0) return fail(PIC_ERR_INVALID_ARG, "bad arguments");
+    CK(cudaSetDevice(c->device));
+    for (int64_t k = 0; k < n; ++k) {
+        int rc = run_tp_step(c, c->d);
+        if (rc) return rc;
+    }
+    if (n_alive) {
+        Ctl h;
+        int rc = read_ctl(c, &h);
+        if (rc) return rc;
+        *n_alive = c->tp_launched + (int64_t)h.cnt[kCntSputL] + (int64_t)h.cnt[kCntSputR] -
+                   (int64_t)h.cnt[kCntTpDepL] - (int64_t)h.cnt[kCntTpDepR];
+    }
+    return PIC_OK;
+}
+
+int pic_compact(pic_ctx* c, int s)
+{
+    if (!c || s < 0 || s > 2) return fail(PIC_ERR_INVALID_ARG, "bad species");
+    CK(cudaSetDevice(c->device));
+    CK(launch_sort(c->d, s, c->grid_sort, c->stream));
+    return PIC_OK;
+}
+
+int pic_op_deposit(const void* pos, int prec, int64_t n, int32_t n_cells, int64_t* q, void* stream)
+{
+    if ((!pos && n > 0) || !q || n < 0 || (prec != 32 && prec != 64) || !pow2(n_cells) || n_cells < 4 ||
+        n_cells > 4096)
+        return fail(PIC_ERR_INVALID_ARG, "bad deposit arguments");
+    if (n == 0) return PIC_OK;
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    long long g = (n + 2047) / 2048;
+    if (g > sms * 4) g = sms * 4;
+    CK(launch_op_deposit(pos, prec == 64, n, n_cells, ilog2(n_cells), (unsigned long long*)q, (int)g,
+                         (cudaStream_t)stream));
+    return PIC_OK;
+}
+
+int pic_op_poisson(const int64_t* q_i, const int64_t* q_e, int32_t n_cells, double dx, double w,
+                   double v_left, double* phi, double* E, void* stream)
+{
+    if (!q_i || !q_e || n_cells < 2 || n_cells > 1 << 20 || !(dx > 0)) return fail(PIC_ERR_INVALID_ARG, "bad poisson arguments");
+    const double A = dx * kQE * w / (4294967296.0 * kEPS0);
+    CK(launch_op_poisson((const long long*)q_i, (const long long*)q_e, n_cells, A, 1.0 / dx, v_left, phi,
+                         E, (cudaStream_t)stream));
+    return PIC_OK;
+}
+
+const char* pic_strerror(int code)
+{
+    switch (code) {
+    case PIC_OK: return "ok";
+    case PIC_ERR_INVALID_ARG: return "invalid argument";
+    case PIC_ERR_UNSTABLE_PARAMS: return "parameters violate dx < lambda_D or w_p dt < 1";
+    case PIC_ERR_OUT_OF_MEMORY: return "device out of memory";
+    case PIC_ERR_CAPACITY: return "particle capacity exceeded";
+    case PIC_ERR_NUMERICS: return "electron energy above the null-collision bound";
+    case PIC_ERR_CUDA: return "CUDA error";
+    case PIC_ERR_NO_DEVICE: return "no CUDA device";
+    default: return "unknown error";
+    }
+}
+
+const char* pic_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

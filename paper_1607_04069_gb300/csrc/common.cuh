@@ -1,0 +1,255 @@
+// common.cuh -- device-side building blocks shared by the kernels of the
+// GB300 PIC/MCC + test-particle engine (sm_103a).
+//
+// Everything here is written from arXiv:1607.04069 (Trieschmann, Schmidt &
+// Mussenbrock) and from Salmon et al., SC'11 (Philox).  The random-stream
+// layout (counter words, purpose codes, which word feeds which draw) is the
+// engine's stream definition; it is fixed so that any implementation of the
+// method that follows it draws the same numbers.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pg {
+
+// ---------------------------------------------------------------- constants
+// CODATA 2018
+constexpr double kQE = 1.602176634e-19;
+constexpr double kME = 9.1093837015e-31;
+constexpr double kAMU = 1.66053906660e-27;
+constexpr double kKB = 1.380649e-23;
+constexpr double kEPS0 = 8.8541878128e-12;
+constexpr double kPI = 3.14159265358979323846;
+constexpr double kMAR = 39.948 * kAMU;
+constexpr double kMAL = 26.98 * kAMU;
+
+// analytic cross sections (e-Ar: constant elastic; linear-onset excitation;
+// one-term Lotz ionisation.  Ar+-Ar: 5e-19 (1 eV/eps)^1/2 per channel)
+constexpr double kSigEl = 1e-19;
+constexpr double kExcTh = 11.5;
+constexpr double kExcSig = 1e-20;
+constexpr double kIonTh = 15.8;
+constexpr double kLotzA = 4.5e-18;
+constexpr double kLotzQ = 6.0;
+constexpr double kArpSig = 5e-19;
+// sputtering of Al by Ar+: threshold, surface binding energy, max trials
+constexpr double kSpTh = 30.0;
+constexpr double kUb = 3.4;
+constexpr int kSpMaxN = 16;
+
+// histogram shapes
+constexpr int kNbIedf = 512;     // ion energy, [0, 2 V0]
+constexpr int kNbIeadfE = 128;   // ion energy x angle, energy axis
+constexpr int kNbAng = 90;       // 1-degree bins, [0, 90)
+constexpr int kNbEedf = 256;     // 0.25 eV bins, [0, 64)
+constexpr int kNbSpE = 600;      // 0.5 eV bins, [0, 300)
+
+// random-stream purposes (fourth counter word)
+enum : uint32_t {
+    kPurInit = 1, kPurColl = 2, kPurIonize = 3, kPurNewIon = 4, kPurBirthId = 5, kPurGas = 6,
+    kPurSpTrial = 16, kPurSpEmit = 32, kPurSpId = 48, kPurTpGas = 64, kPurTpColl = 65,
+    kPurTpLaunch = 66
+};
+
+// species and id tags
+enum { kE = 0, kI = 1, kTP = 2 };
+__host__ __device__ constexpr uint64_t id_tag(int s) { return (uint64_t)s << 62; }
+constexpr uint64_t kIdMask = (1ull << 62) - 1;
+
+// counters (device, unsigned long long)
+enum {
+    kCntImpEL, kCntImpER, kCntImpIL, kCntImpIR, kCntIoniz, kCntSputL, kCntSputR, kCntTpDepL,
+    kCntTpDepR, kCntNumerics, kCntElastic, kCntExcit, kCntCx, kCntIso, kCntTpColl, kCntCapacity,
+    kNumCnt
+};
+
+// error bits of Ctl::err
+enum : uint32_t { kErrCapacity = 1u, kErrNumerics = 2u, kErrIndex = 4u };
+
+// ---------------------------------------------------------------- state
+struct SpBuf {                 // one species, one ping-pong half (structure of arrays)
+    void* pos;                 // uint32 fixed point x 2^32/L, or double x/dx (64-bit mode)
+    float* vx;
+    float* vy;
+    float* vz;
+    uint64_t* id;
+};
+
+struct Ctl {                   // device control block
+    long long n[3];            // slots in use per species (alive + removed holes)
+    long long births[3];       // appended by the running kernel
+    long long cap[3];
+    unsigned int step, tp_step;
+    unsigned int done, tp_done, sort_done;
+    unsigned int cur[3];       // active ping-pong half per species
+    unsigned int err;
+    unsigned int pad;
+    long long n_avg, n_flux, n_tp_samp;
+    long long sort_total;
+    unsigned long long cnt[kNumCnt];
+};
+
+struct Diag {                  // accumulators of the time-averaged diagnostics
+    double* sum_q[2];          // sum over steps of q_e, q_i (units of 2^-32 particles)
+    double* sum_phi;
+    double* sum_flux[2];       // sum over samples of sum_k S_m(x_k) v_x,k
+    double* tp_dens;           // sum over TP steps of sum_k S_m(x_k)
+    double* tp_vx;             // sum over TP steps of sum_k S_m(x_k) v_x,k
+    unsigned long long* iedf[2];
+    unsigned long long* ieadf[2];
+    unsigned long long* eedf;
+    unsigned long long* sp_e[2];
+    unsigned long long* sp_ang[2];
+};
+
+struct Dev {                   // everything a kernel needs, passed by value
+    SpBuf buf[3][2];
+    Ctl* ctl;
+    Diag diag;
+    unsigned long long* q[2];        // per-step charge histograms (e, i)
+    unsigned long long* q_last[2];   // copy of the last solved deposit (diagnostics)
+    long long* flux[2];              // per-sample flux histograms (e, i), units 2^-16 m/s
+    unsigned long long* tp_q;        // per-TP-step density histogram
+    long long* tp_flux;              // per-TP-step v_x histogram
+    float* E32;                      // field at the nodes for the gather
+    double* E64;
+    double* phi;
+    unsigned int* sort_cnt;          // [ncell] cell counts (sort scratch)
+    unsigned int* sort_off;          // [ncell] running offsets (sort scratch)
+    // geometry
+    int ncell, kshift, pos64, pad0;
+    double L, dx, inv_dx;
+    // field solve: phi[m+1] - 2 phi[m] + phi[m-1] = -A q_net[m]; A = dx e w / (2^32 eps0)
+    double A, V0, omega, dt;
+    // push
+    float qm_dt[2];                  // (q/m) dt
+    float push32;                    // dt 2^32 / L  (fixed-point displacement per m/s)
+    float pad1;
+    double push64;                   // dt / dx      (cell-unit displacement per m/s)
+    // collisions
+    unsigned long long thr[2];       // candidate iff first word < thr (= ceil(P_max 2^32))
+    float ngas_f, nu_max_e, nu_max_i, eps_max;
+    float vth_gas;                   // sqrt(k Tg / M_Ar)
+    float tp_scale;                  // dt_tp 2^32 / L
+    float tp_nsig_dt;                // n sigma_tp dt_tp
+    float Emax_hist;                 // 2 V0 (ion histograms)
+    int sputter, diag_every;
+    unsigned int eedf_lo, eedf_hi;   // fixed-point window of the EEDF sample (0.45 L, 0.55 L)
+    double eedf_lo64, eedf_hi64;
+    uint64_t seed;
+};
+
+// ---------------------------------------------------------------- Philox4x32-10
+__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 draw(uint64_t seed, uint64_t id, uint32_t step, uint32_t purpose)
+{
+    return philox(make_uint4((uint32_t)id, (uint32_t)(id >> 32), step, purpose), (uint32_t)seed,
+                  (uint32_t)(seed >> 32));
+}
+
+// uniform in (0,1) on the 2^-23 grid (top 23 bits + 1/2), exact in float
+__device__ __forceinline__ float u23(uint32_t w) { return ((float)(w >> 9) + 0.5f) * 0x1p-23f; }
+
+__device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b)
+{
+    const float r = sqrtf(-2.0f * logf(u23(a)));
+    float s, c;
+    sincospif(2.0f * u23(b), &s, &c);
+    return make_float2(r * c, r * s);
+}
+
+__device__ __forceinline__ float3 iso_dir(uint32_t a, uint32_t b)
+{
+    const float c = 1.0f - 2.0f * u23(a);
+    const float s = sqrtf(fmaxf(0.0f, 1.0f - c * c));
+    float sp, cp;
+    sincospif(2.0f * u23(b), &sp, &cp);
+    return make_float3(c, s * cp, s * sp);
+}
+
+__device__ __forceinline__ uint64_t child_id(uint32_t lo, uint32_t hi, int s)
+{
+    return ((((uint64_t)hi << 32) | lo) & kIdMask) | id_tag(s);
+}
+
+// Thompson energy (truncated at Emax, by inversion of (E/(E+Ub))^2) and cosine
+// angle; dir = +1 into +x (left electrode), -1 into -x.
+__device__ __forceinline__ float3 emit(float uE, float uT, float uP, float Emax, float dir)
+{
+    const float t = Emax / (Emax + (float)kUb);
+    const float s = sqrtf(uE * t * t);
+    const float Es = (float)kUb * s / (1.0f - s);
+    const float speed = sqrtf(2.0f * Es * (float)(kQE / kMAL));
+    const float ct = sqrtf(uT);
+    const float st = sqrtf(fmaxf(0.0f, 1.0f - uT));
+    float sp, cp;
+    sincospif(2.0f * uP, &sp, &cp);
+    return make_float3(dir * speed * ct, speed * st * cp, speed * st * sp);
+}
+
+__device__ __forceinline__ float lambda_ar_al()
+{
+    return (float)(4.0 * kMAR * kMAL / ((kMAR + kMAL) * (kMAR + kMAL)));
+}
+
+// ---------------------------------------------------------------- warp deposit
+// Linear weighting of one particle per lane into a shared int64 histogram:
+// node j gets 2^32 - wr, node j+1 gets wr.  Lanes whose cells span at most
+// 4 consecutive cells are summed in registers first (counts by ballot,
+// weights by two 32-bit reductions of 24+8 bits), so a sorted warp issues a
+// handful of atomics instead of 64.  Integer sums: exact, order-independent.
+__device__ __forceinline__ void warp_deposit(unsigned long long* sq, bool act, uint32_t j, uint32_t wr)
+{
+    const unsigned FULL = 0xffffffffu;
+    const uint32_t jmin = __reduce_min_sync(FULL, act ? j : 0xffffffffu);
+    if (jmin == 0xffffffffu) return;
+    const uint32_t jmax = __reduce_max_sync(FULL, act ? j : 0u);
+    const int lane = threadIdx.x & 31;
+    if (jmax - jmin < 4) {
+        const int span = (int)(jmax - jmin);
+        unsigned long long prevR = 0;
+        for (int c = 0; c <= span; ++c) {
+            const bool in = act && (j == jmin + (uint32_t)c);
+            const unsigned m = __ballot_sync(FULL, in);
+            const uint32_t hi = __reduce_add_sync(FULL, in ? (wr >> 8) : 0u);
+            const uint32_t lo = __reduce_add_sync(FULL, in ? (wr & 0xffu) : 0u);
+            const unsigned long long R = ((unsigned long long)hi << 8) + lo;
+            const unsigned long long node = ((unsigned long long)__popc(m) << 32) - R + prevR;
+            if (lane == c && node) atomicAdd(&sq[jmin + c], node);
+            prevR = R;
+        }
+        if (lane == span + 1 && prevR) atomicAdd(&sq[jmin + span + 1], prevR);
+    } else if (act) {
+        atomicAdd(&sq[j], (1ull << 32) - wr);
+        if (wr) atomicAdd(&sq[j + 1], (unsigned long long)wr);
+    }
+}
+
+// cell index and right-node weight of a position
+__device__ __forceinline__ void cell_of(uint32_t pos, int kshift, uint32_t& j, uint32_t& wr)
+{
+    j = pos >> (32 - kshift);
+    wr = pos << kshift;            // (xi - j) 2^32, exact
+}
+__device__ __forceinline__ void cell_of(double xi, int, uint32_t& j, uint32_t& wr)
+{
+    const double fj = floor(xi);
+    j = (uint32_t)fj;
+    wr = (uint32_t)((xi - fj) * 4294967296.0);   // floor of f 2^32 (f 2^32 exact, f < 1)
+}
+
+__device__ __forceinline__ bool is_alive(uint32_t pos) { return pos != 0u; }
+__device__ __forceinline__ bool is_alive(double xi) { return xi >= 0.0; }
+
+}  // namespace pg

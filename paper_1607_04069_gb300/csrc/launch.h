@@ -1,0 +1,25 @@
+// launch.h -- host-side launchers of the device kernels (internal to the library).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace pg {
+
+constexpr int kMoverThreads = 256;
+constexpr int kTpThreads = 256;
+
+size_t mover_smem(int ncell);
+size_t tp_smem(int ncell);
+cudaError_t launch_init(const Dev& d, int s, long long n, float vth, cudaStream_t st);
+// mode 0: one PIC/MCC step; mode 1: deposit the current state and solve the field
+cudaError_t launch_mover(const Dev& d, int grid, int mode, cudaStream_t st);
+cudaError_t launch_sort(const Dev& d, int s, int grid, cudaStream_t st);
+cudaError_t launch_tp_step(const Dev& d, int grid, cudaStream_t st);
+cudaError_t launch_tp_launch(const Dev& d, long long n, long long id0, float Emax, cudaStream_t st);
+cudaError_t launch_op_deposit(const void* pos, int pos64, long long n, int ncell, int kshift,
+                              unsigned long long* q, int grid, cudaStream_t st);
+cudaError_t launch_op_poisson(const long long* qi, const long long* qe, int N, double A, double inv_dx,
+                              double v_left, double* phi, double* E64, cudaStream_t st);
+
+}  // namespace pg

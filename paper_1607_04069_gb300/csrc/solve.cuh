@@ -1,0 +1,180 @@
+// solve.cuh -- one-CTA field solve for the 1D electrostatic PIC cycle.
+//
+// Poisson's equation discretised as in the paper's field-solver paragraph
+// (Sec. "EM Field Solver and External Lumped Circuits"):
+//     (phi[m+1] - 2 phi[m] + phi[m-1]) / dx^2 = -rho[m] / eps0,  m = 1..N-1,
+// with phi[0] = V_rf(t), phi[N] = 0, and E[m] = -(phi[m+1] - phi[m-1]) / (2 dx).
+// With rho[m] = e w q[m] / (2^32 dx) (q in units of 2^-32 superparticles)
+// the rows read  phi[m+1] - 2 phi[m] + phi[m-1] = -A q[m],
+// A = dx e w / (2^32 eps0).  For this constant-coefficient Dirichlet system
+// the Thomas elimination collapses to two prefix sums:
+//     S_m = sum_{j=1..m} q[j],   T_m = sum_{k<m} S_k,
+//     D0  = (phi[N] - phi[0] + A T_N) / N,
+//     phi[m] = phi[0] + m D0 - A T_m,
+//     E[m]   = -(2 D0 - A (S_m + S_{m-1})) / (2 dx)              (inside),
+//     E[0]   = -(D0 + A q[0]) / dx,   E[N] = -(D0 - A S_N) / dx  (half-cell Gauss).
+// S is summed in int64 and T in int128, so both are exact and independent of
+// the block shape; the only roundings are the final FP64 products.
+#pragma once
+#include "common.cuh"
+
+namespace pg {
+
+__device__ __forceinline__ long long shfl_up_t(long long v, int d)
+{
+    return __shfl_up_sync(0xffffffffu, v, d);
+}
+__device__ __forceinline__ __int128 shfl_up_t(__int128 v, int d)
+{
+    const unsigned long long lo = (unsigned long long)v;
+    const long long hi = (long long)(v >> 64);
+    const unsigned long long lo2 = __shfl_up_sync(0xffffffffu, lo, d);
+    const long long hi2 = __shfl_up_sync(0xffffffffu, hi, d);
+    return (__int128)(((unsigned __int128)(unsigned long long)hi2 << 64) | lo2);
+}
+
+// Exclusive scan over the block (blockDim.x a multiple of 32, <= 1024).
+// `sh` must hold 32 elements.  `total` receives the block total.
+template <typename T>
+__device__ T block_exclusive_scan(T v, T* sh, T& total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    T x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const T y = shfl_up_t(x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) sh[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        T w = lane < nw ? sh[lane] : (T)0;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const T y = shfl_up_t(w, d);
+            if (lane >= d) w += y;
+        }
+        sh[lane] = w;
+    }
+    __syncthreads();
+    const T off = wid ? sh[wid - 1] : (T)0;
+    total = sh[nw - 1];
+    __syncthreads();
+    return off + x - v;
+}
+
+__device__ __forceinline__ double i128_to_double(__int128 x)
+{
+    const bool neg = x < 0;
+    const unsigned __int128 u = neg ? (unsigned __int128)(-x) : (unsigned __int128)x;
+    const double d = (double)(unsigned long long)(u >> 64) * 18446744073709551616.0 +
+                     (double)(unsigned long long)u;
+    return neg ? -d : d;
+}
+
+// net charge count at node m: ions minus electrons
+struct QNet {
+    const unsigned long long* qi;
+    const unsigned long long* qe;
+    bool cg;   // read through L2 (data written by atomics of other CTAs of this kernel)
+    __device__ __forceinline__ long long operator()(int m) const
+    {
+        const unsigned long long a = cg ? __ldcg(qi + m) : qi[m];
+        const unsigned long long b = cg ? __ldcg(qe + m) : qe[m];
+        return (long long)(a - b);
+    }
+};
+
+// Solve for phi and E with one CTA.  Any output pointer may be null.
+__device__ __noinline__ static void poisson_block(const QNet& qn, int N, double A, double inv_dx, double v_left,
+                              double* phi, double* E64, float* E32)
+{
+    __shared__ long long sh64[32];
+    __shared__ __int128 sh128[32];
+    const int T = blockDim.x, t = threadIdx.x;
+    const int N1 = N + 1;
+    const int seg = (N1 + T - 1) / T;
+    const int m0 = min(t * seg, N1), m1 = min(m0 + seg, N1);
+
+    long long a = 0;
+    for (int m = m0; m < m1; ++m)
+        if (m >= 1) a += qn(m);
+    long long totS;
+    const long long Sprev = block_exclusive_scan(a, sh64, totS);
+
+    __int128 b = 0;
+    long long S = Sprev;
+    for (int m = m0; m < m1; ++m) {
+        if (m >= 1) S += qn(m);
+        b += (__int128)S;
+    }
+    __int128 totT;
+    const __int128 Tpre = block_exclusive_scan(b, sh128, totT);
+    const __int128 TN = totT - (__int128)totS;
+    const double D0 = (0.0 - v_left + A * i128_to_double(TN)) / (double)N;
+
+    S = Sprev;
+    __int128 Tm = Tpre;
+    for (int m = m0; m < m1; ++m) {
+        const long long q = qn(m);
+        const long long Sm = m >= 1 ? S + q : 0;
+        const double ph = v_left + (double)m * D0 - A * i128_to_double(Tm);
+        double E;
+        if (m == 0) E = -(D0 + A * (double)q) * inv_dx;
+        else if (m == N) E = -(D0 - A * (double)Sm) * inv_dx;
+        else E = -(2.0 * D0 - A * (double)(Sm + S)) * (0.5 * inv_dx);
+        if (phi) phi[m] = ph;
+        if (E64) E64[m] = E;
+        if (E32) E32[m] = (float)E;
+        Tm += (__int128)Sm;
+        S = Sm;
+    }
+}
+
+// Finish of a PIC step (or of a standalone deposit), run by the last CTA of
+// the launch: solve for the field at step l_new, accumulate the time
+// averages, clear the per-step histograms, and commit counters.
+// `advance`: this launch moved the particles from step l_new-1 to l_new.
+__device__ static void finish_step(const Dev& d, unsigned int l_new, bool advance, bool sample)
+{
+    const int N = d.ncell, N1 = N + 1;
+    const double v_left = d.V0 * sin(d.omega * (double)l_new * d.dt);
+    QNet qn{d.q[kI], d.q[kE], true};
+    poisson_block(qn, N, d.A, d.inv_dx, v_left, d.phi, d.E64, d.E32);
+    __syncthreads();
+    for (int m = threadIdx.x; m < N1; m += blockDim.x) {
+        const unsigned long long qe = __ldcg(d.q[kE] + m), qi = __ldcg(d.q[kI] + m);
+        if (advance) {
+            d.diag.sum_q[kE][m] += (double)qe;
+            d.diag.sum_q[kI][m] += (double)qi;
+            d.diag.sum_phi[m] += d.phi[m];
+            if (sample) {
+                d.diag.sum_flux[kE][m] += (double)__ldcg(d.flux[kE] + m) * 0x1p-16;
+                d.diag.sum_flux[kI][m] += (double)__ldcg(d.flux[kI] + m) * 0x1p-16;
+            }
+        }
+        d.q_last[kE][m] = qe;
+        d.q_last[kI][m] = qi;
+        d.q[kE][m] = 0;
+        d.q[kI][m] = 0;
+        d.flux[kE][m] = 0;
+        d.flux[kI][m] = 0;
+    }
+    if (threadIdx.x == 0) {
+        Ctl* c = d.ctl;
+        if (advance) {
+            c->step = l_new;
+            c->n_avg += 1;
+            if (sample) c->n_flux += 1;
+        }
+        for (int s = 0; s < 3; ++s) {
+            long long n = c->n[s] + c->births[s];
+            if (n > c->cap[s]) n = c->cap[s];
+            c->n[s] = n;
+            c->births[s] = 0;
+        }
+        c->done = 0;
+    }
+}
+
+}  // namespace pg

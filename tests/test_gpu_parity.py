@@ -1,0 +1,319 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (written out per test):
+* integer work -- charge deposits, ids, counters, histograms of integer
+  keys -- is compared bit for bit;
+* the FP32 push against the FP64 oracle: one-step velocity and displacement
+  within 1e-5 relative (plus one 2^-32 L fixed-point unit for positions);
+* the FP64 field solve within 1e-12 relative to max |phi|.
+Random decisions (collision candidate, process, sputter trial) are taken
+from identical Philox words on both sides, so they must agree exactly.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1607_04069_gb300 import workloads as W
+
+from helpers import gpu_discharge, match, oracle_for
+
+pytestmark = pytest.mark.gpu
+
+QE, ME, AMU = 1.602176634e-19, 9.1093837015e-31, 1.66053906660e-27
+MAR, MAL = 39.948 * AMU, 26.98 * AMU
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    import paper_1607_04069_gb300 as P
+    P.lib()
+    yield
+
+
+def _torch_pos(pos):
+    import torch
+    if pos.dtype == np.uint32:
+        return torch.from_numpy(pos.view(np.int32).copy()).cuda()
+    return torch.from_numpy(pos.copy()).cuda()
+
+
+# ------------------------------------------------------------------ initial loading / Philox
+@pytest.mark.parametrize("prec", [32, 64])
+def test_initial_loading_bit_identical_positions(prec):
+    """Philox stream on the GPU reproduces the oracle's: positions (raw Philox
+    words) bit for bit, Box-Muller velocities within FP32 rounding."""
+    n = 50_001
+    cfg = W.ccp_small(n_per_species=n)
+    cfg["pos_precision"] = prec
+    d = gpu_discharge(cfg)
+    orc = oracle_for(cfg)
+    orc.init_species(0, n, cfg["te0_ev"])
+    orc.init_species(1, n, cfg["ti0_ev"])
+    for s, T, m in ((0, cfg["te0_ev"], ME), (1, cfg["ti0_ev"], MAR)):
+        g, o = d.get_species(s), orc.get_species(s)
+        assert np.array_equal(g["id"], o["id"])
+        assert np.array_equal(g["xi"], o["xi"])
+        vth = math.sqrt(T * QE / m)
+        for c in ("vx", "vy", "vz"):
+            assert np.abs(g[c] - o[c]).max() <= 2e-6 * vth * 8
+    d.close()
+
+
+# ------------------------------------------------------------------ deposit (bit-exact)
+@pytest.mark.parametrize("ncell", [4, 128, 1024, 4096])
+@pytest.mark.parametrize("layout", ["random", "sorted", "one_cell", "with_dead"])
+def test_deposit_bit_exact(ncell, layout):
+    """Linear weighting into int64: identical to the oracle bit for bit, for
+    random and cell-sorted particles (the warp-aggregated path), all in one
+    cell, and with removed slots; n spans several CTAs plus a ragged tail."""
+    import paper_1607_04069_gb300 as P
+    rng = np.random.default_rng(ncell + len(layout))
+    n = 1_000_003
+    pos = W.fixed_positions(rng, n)
+    if layout == "sorted":
+        pos = np.sort(pos)
+    elif layout == "one_cell":
+        cell = 2**32 // ncell
+        base = min(5, ncell - 1) * cell + cell // 4
+        pos = (pos.astype(np.uint64) % (cell // 2) + base).astype(np.uint32)
+    elif layout == "with_dead":
+        pos[rng.random(n) < 0.1] = 0
+    xi = pos.astype(np.float64) * (ncell / 2.0**32)
+    xi[pos == 0] = -1.0
+    q = P.op_deposit(_torch_pos(pos), ncell).cpu().numpy()
+    assert np.array_equal(q, O.deposit(xi, ncell))
+    # 64-bit positions in cell units: same values, same deposit
+    q64 = P.op_deposit(_torch_pos(xi), ncell).cpu().numpy()
+    assert np.array_equal(q64, O.deposit(xi, ncell))
+
+
+def test_deposit_edge_sizes():
+    import paper_1607_04069_gb300 as P
+    import torch
+    for n in (0, 1, 31, 32, 33, 257):
+        rng = np.random.default_rng(n)
+        pos = W.fixed_positions(rng, max(n, 1))[:n]
+        xi = pos.astype(np.float64) * (64 / 2.0**32)
+        t = _torch_pos(pos) if n else torch.zeros(0, dtype=torch.int32, device="cuda")
+        q = P.op_deposit(t, 64).cpu().numpy()
+        assert np.array_equal(q, O.deposit(xi, 64))
+
+
+# ------------------------------------------------------------------ field solve
+@pytest.mark.parametrize("ncell", [4, 128, 1024, 2048, 4096])
+def test_poisson_matches_oracle(ncell):
+    """Exact double-prefix-sum solve on the GPU vs the oracle's Thomas sweep:
+    within 1e-12 of max |phi| (E within 1e-10 of max |E|)."""
+    import paper_1607_04069_gb300 as P
+    import torch
+    rng = np.random.default_rng(ncell)
+    L, w = 0.05, 1e11
+    dx = L / ncell
+    q_i = rng.integers(0, 2**46, size=ncell + 1, dtype=np.int64)
+    q_e = q_i + rng.integers(-2**40, 2**40, size=ncell + 1, dtype=np.int64)
+    for v_left in (0.0, 300.0, -123.4):
+        phi, E = P.op_poisson(torch.from_numpy(q_i).cuda(), torch.from_numpy(q_e).cuda(), ncell,
+                              dx, w, v_left)
+        phi, E = phi.cpu().numpy(), E.cpu().numpy()
+        phi_o, E_o = O.poisson(ncell, dx, w, q_i, q_e, v_left)
+        assert np.abs(phi - phi_o).max() <= 1e-12 * np.abs(phi_o).max()
+        assert np.abs(E - E_o).max() <= 1e-10 * np.abs(E_o).max()
+
+
+# ------------------------------------------------------------------ one-step push
+def _load_both(d, orc, sets, prec):
+    for s, st in sets.items():
+        d.set_species(s, st["pos"], st["vx"], st["vy"], st["vz"], st["id"])
+        orc.set_species(s, st["xi"], st["vx"].astype(np.float64), st["vy"].astype(np.float64),
+                        st["vz"].astype(np.float64), st["id"])
+
+
+def _smooth_field(ncell, scale, seed):
+    rng = np.random.default_rng(seed)
+    x = np.linspace(0, 1, ncell + 1)
+    E = np.zeros(ncell + 1)
+    for k in range(1, 6):
+        E += rng.normal() * np.sin(k * np.pi * x + rng.uniform(0, np.pi))
+    return scale * E
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_one_step_push_parity(prec):
+    """Gather + leapfrog + wall, collisions off (p = 0): every particle's
+    v_x^{l+1/2} and displacement within 1e-5 relative of the oracle, v_y, v_z
+    untouched, the same particles absorbed, and Sum q = 2^32 x alive."""
+    ncell = 1024
+    cfg = W.ccp_sputter(n_per_species=1000, n_cells=ncell)
+    cfg.update(pressure_pa=0.0, pos_precision=prec, sputter_enable=0, sort_every_e=0,
+               sort_every_i=0, n_e0=0, n_i0=0, cap_e=300_000, cap_i=300_000)
+    d = gpu_discharge(cfg)
+    orc = oracle_for(cfg, cap=300_000)
+    sets = {0: W.random_particles(200_001, ncell, 0, 2e6, 1, prec),
+            1: W.random_particles(100_003, ncell, 1, 3e4, 2, prec)}
+    _load_both(d, orc, sets, prec)
+    E = _smooth_field(ncell, 2e4, 3)
+    d.set_field(E)
+    orc.set_field(E)
+    d.step(1)
+    d.sync()
+    orc.step(1)
+    unit = ncell / 2.0**32
+    dt = cfg["dt"]
+    for s in (0, 1):
+        g, o, only_g, only_o = match(d.get_species(s), orc.get_species(s))
+        x0 = dict(zip(sets[s]["id"].tolist(), sets[s]["xi"].tolist()))
+        assert len(only_g) == 0 and len(only_o) == 0, (len(only_g), len(only_o))
+        xi0 = np.array([x0[i] for i in o["id"].tolist()])
+        disp_o = o["xi"] - xi0
+        tol = 1e-5 * np.abs(disp_o) + (2 * unit if prec == 32 else 1e-9)
+        assert (np.abs(g["xi"] - o["xi"]) <= tol).all()
+        v0 = dict(zip(sets[s]["id"].tolist(), sets[s]["vx"].tolist()))
+        vx0 = np.array([v0[i] for i in o["id"].tolist()])
+        assert (np.abs(g["vx"] - o["vx"]) <= 1e-5 * (np.abs(vx0) + np.abs(o["vx"] - vx0)) + 1e-3).all()
+        vy0 = dict(zip(sets[s]["id"].tolist(), sets[s]["vy"].tolist()))
+        assert np.array_equal(g["vy"], np.array([vy0[i] for i in g["id"].tolist()], dtype=np.float32))
+    f, fo = d.get_field(), orc.get_field()
+    c = d.counters()
+    alive = [len(d.get_species(s)["id"]) for s in (0, 1)]
+    assert int(f["q_e"].sum()) == 2**32 * alive[0] and int(f["q_i"].sum()) == 2**32 * alive[1]
+    assert np.abs(f["E"] - fo["E"]).max() <= 1e-5 * np.abs(fo["E"]).max()
+    oc = orc.counters()
+    assert c["imp_e_l"] + c["imp_e_r"] == oc["imp_e_l"] + oc["imp_e_r"]
+    d.close()
+
+
+# ------------------------------------------------------------------ one-step MCC
+@pytest.mark.parametrize("case", ["electrons", "ions"])
+def test_one_step_collision_parity(case):
+    """Null-collision MCC from identical Philox words: the same particles
+    collide with the same process, post-collision velocities within FP32
+    rounding, ionisation children with the same ids and states."""
+    ncell = 256
+    cfg = W.ccp_small(n_per_species=1000)
+    cfg.update(n_cells=ncell, pressure_pa=3.0, rf_volt_v=100.0, pos_precision=32,
+               sort_every_e=0, sort_every_i=0, n_e0=0, n_i0=0, cap_e=400_000, cap_i=400_000,
+               gap_m=1.0, dt=1e-10 if case == "electrons" else 1e-8)
+    d = gpu_discharge(cfg)
+    orc = oracle_for(cfg, cap=400_000)
+    sets = {0: W.random_particles(100_000, ncell, 0, math.sqrt(20 * QE / ME), 5, 32),
+            1: W.random_particles(100_000, ncell, 1, 2e3, 6, 32)}
+    if case == "electrons":
+        sets[1] = W.random_particles(0, ncell, 1, 1.0, 7, 32)
+    _load_both(d, orc, sets, 32)
+    E = np.zeros(ncell + 1)
+    d.set_field(E)
+    orc.set_field(E)
+    d.step(1)
+    d.sync()
+    orc.step(1)
+    c, oc = d.counters(), orc.counters()
+    keys = ["elastic", "excitation", "ionizations"] if case == "electrons" else ["cx", "iso"]
+    for k in keys:
+        assert c[k] == oc[k], (k, c[k], oc[k])
+    assert sum(c[k] for k in keys) > 500
+    for s in (0, 1):
+        g, o, only_g, only_o = match(d.get_species(s), orc.get_species(s))
+        assert len(only_g) == 0 and len(only_o) == 0
+        vmag = np.sqrt(o["vx"]**2 + o["vy"]**2 + o["vz"]**2)
+        for comp in ("vx", "vy", "vz"):
+            assert (np.abs(g[comp] - o[comp]) <= 2e-5 * vmag + 1e-2).all(), comp
+    d.close()
+
+
+# ------------------------------------------------------------------ sputtering
+def test_sputter_launch_parity():
+    """Ar+ impacts at 310 eV: the same trials succeed, the sputtered atoms
+    carry the same ids, Thompson/cosine velocities within FP32 rounding, and
+    the IEDF counts agree."""
+    ncell = 1024
+    cfg = W.ccp_sputter(n_per_species=1000, n_cells=ncell)
+    cfg.update(pressure_pa=0.0, n_e0=0, n_i0=0, cap_e=1000, cap_i=200_000, cap_tp=200_000,
+               sort_every_e=0, sort_every_i=0, tp_every=0, dt=1e-10, rf_volt_v=300.0)
+    d = gpu_discharge(cfg)
+    orc = oracle_for(cfg, cap=200_000)
+    n = 100_000
+    rng = np.random.default_rng(12)
+    pos = rng.integers(1, 2000, size=n, dtype=np.uint64).astype(np.uint32)
+    v = math.sqrt(2 * 310.0 * QE / MAR)          # 310 eV: away from an IEDF bin edge
+    ids = np.arange(n, dtype=np.uint64) | np.uint64(1 << 62)
+    vx = np.full(n, -v, dtype=np.float32)
+    zero = np.zeros(n, dtype=np.float32)
+    d.set_species(1, pos, vx, zero, zero, ids)
+    orc.set_species(1, pos.astype(np.float64) * ncell / 2.0**32, vx.astype(np.float64), zero * 0.0,
+                    zero * 0.0, ids)
+    d.set_field(np.zeros(ncell + 1))
+    orc.set_field(np.zeros(ncell + 1))
+    d.step(1)
+    d.sync()
+    orc.step(1)
+    c, oc = d.counters(), orc.counters()
+    assert c["imp_i_l"] == oc["imp_i_l"] == n
+    assert c["sputtered_l"] == oc["sputtered_l"] > 0
+    g, o, only_g, only_o = match(d.get_species(2), orc.get_species(2))
+    assert len(only_g) == 0 and len(only_o) == 0
+    for comp in ("vx", "vy", "vz"):
+        assert np.abs(g[comp] - o[comp]).max() <= 1e-4 * np.abs(o["vx"]).max()
+    assert np.array_equal(d.diag("iedf_l"), orc.diag("iedf_l"))
+    d.close()
+
+
+# ------------------------------------------------------------------ test particles
+def test_tp_transport_parity():
+    """Mono-energetic 300 eV source, 200 TP steps of 1 ns: every atom's state
+    within FP32 rounding of the oracle's, the same atoms deposited, and the
+    counts conserved (launched = deposited + in flight)."""
+    cfg = W.tp_transport(n_atoms=50_000)
+    cfg.update(cap_tp=60_000, n_e0=0, n_i0=0, sort_every_tp=0)
+    d = gpu_discharge(cfg)
+    orc = oracle_for(cfg, cap=10, cap_tp=60_000)
+    d.tp_launch(50_000, 300.0)
+    orc.tp_launch(50_000, 300.0)
+    alive = d.tp_step(200)
+    orc.tp_step(200, cfg["tp_dt"])
+    c, oc = d.counters(), orc.counters()
+    assert c["tp_dep_l"] + c["tp_dep_r"] + alive == 50_000
+    assert abs(c["tp_coll"] - oc["tp_coll"]) <= 2
+    assert abs(c["tp_dep_r"] - oc["tp_dep_r"]) <= 2 and abs(c["tp_dep_l"] - oc["tp_dep_l"]) <= 2
+    g, o, only_g, only_o = match(d.get_species(2), orc.get_species(2))
+    assert len(only_g) + len(only_o) <= 4
+    vmag = np.sqrt(o["vx"]**2 + o["vy"]**2 + o["vz"]**2)
+    bad = np.abs(g["vx"] - o["vx"]) > 1e-3 * vmag + 1e-2
+    assert bad.sum() <= 4
+    d.close()
+
+
+# ------------------------------------------------------------------ determinism
+def test_bitwise_independent_of_order_and_sort_period():
+    """Randomness keyed by (id, step, purpose) and integer deposits make the
+    run independent of particle order and of the compaction period: 60 steps
+    from a shuffled input with compaction every step end bit-identical to 60
+    steps from the ordered input without compaction."""
+    cfg = W.ccp_small(n_per_species=20_000)
+    cfg.update(pos_precision=32, sort_every_e=0, sort_every_i=0)
+    a = gpu_discharge(cfg)
+    sp = {s: a.get_species(s) for s in (0, 1)}
+    b = gpu_discharge(cfg, sort_every_e=1, sort_every_i=3)
+    rng = np.random.default_rng(0)
+    for s in (0, 1):
+        perm = rng.permutation(len(sp[s]["id"]))
+        pos = np.rint(sp[s]["xi"][perm] * (2.0**32 / cfg["n_cells"])).astype(np.uint64).astype(np.uint32)
+        b.set_species(s, pos, sp[s]["vx"][perm], sp[s]["vy"][perm], sp[s]["vz"][perm], sp[s]["id"][perm])
+    a.step(60)
+    b.step(60)
+    a.sync()
+    b.sync()
+    for s in (0, 1):
+        ga, gb, oa, ob = match(a.get_species(s), b.get_species(s))
+        assert len(oa) == 0 and len(ob) == 0
+        for k in ("xi", "vx", "vy", "vz"):
+            assert np.array_equal(ga[k], gb[k]), k
+    for k in ("phi", "n_e", "n_i", "gamma_e", "iedf_l", "eedf"):
+        assert np.array_equal(a.diag(k), b.diag(k)), k
+    a.close()
+    b.close()
