@@ -311,16 +311,18 @@ int pic_create(const pic_params* pin, void* stream, pic_ctx** out)
 {
     if (!out) return fail(PIC_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
-    int rc = validate(pin);
+    if (!pin) return fail(PIC_ERR_INVALID_ARG, "params is NULL");
+    pic_params q = *pin;
+    if (q.cap_e == 0) q.cap_e = q.n_e0 + q.n_e0 / 4 + 65536;
+    if (q.cap_i == 0) q.cap_i = q.n_i0 + q.n_i0 / 4 + 65536;
+    if (q.cap_tp == 0) q.cap_tp = 65536;
+    int rc = validate(&q);
     if (rc) return rc;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
         return fail(PIC_ERR_NO_DEVICE, "no CUDA device visible");
     pic_ctx* c = new pic_ctx();
-    c->p = *pin;
-    if (c->p.cap_e == 0) c->p.cap_e = c->p.n_e0 + c->p.n_e0 / 4 + 65536;
-    if (c->p.cap_i == 0) c->p.cap_i = c->p.n_i0 + c->p.n_i0 / 4 + 65536;
-    if (c->p.cap_tp == 0) c->p.cap_tp = 65536;
+    c->p = q;
     c->stream = (cudaStream_t)stream;
     cudaGetDevice(&c->device);
     derive(c);
