@@ -1,0 +1,336 @@
+#!/usr/bin/env python
+"""Benchmark of the PIC/MCC + test-particle hot path on GB300.
+
+Workload (one GPU): the 50 mm / 1024-cell / 300 V / 0.5 Pa sputtering
+discharge with 2M e- + 2M Ar+ superparticles (32-bit fixed-point positions,
+FP32 velocities), sputtered Al atoms sub-cycled every 40 steps.  A step is
+one PIC/MCC cycle of every particle (gather, push, wall + sputter launch,
+null-collision MCC, int64 deposit, field solve), with the periodic
+compaction and the coupled TP steps it schedules.
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on the
+same discharge instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ALGO_BYTES = 24          # per particle-step: read x, v_x (4+4) and id (8); write x, v_x (4+4)
+KERNEL_SOURCES = ["paper_1607_04069_gb300/csrc/pic_kernels.cu", "paper_1607_04069_gb300/csrc/common.cuh",
+                  "paper_1607_04069_gb300/csrc/solve.cuh"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        for k in ("hbm_gbs", "hbm_copy_gbs", "hbm_GBps"):
+            if k in d:
+                return float(d[k]), "measured"
+    except (OSError, ValueError):
+        pass
+    return 6800.0, "fallback"
+
+
+def traffic_per_launch():
+    """dram bytes of one step-kernel launch from the committed ncu summary, if
+    it was taken on the current kernel source."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "mover_traffic.json")) as fh:
+            d = json.load(fh)
+        if d.get("kernel_hash") == kernel_hash():
+            return float(d["dram_bytes_per_launch_full_workload"])
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+            self.fh.close()
+
+    def summary(self):
+        if not self.proc:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("BENCH_BACKEND", "nccl") == "nccl" else "gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x, ws):
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allreduce_sum(x, ws):
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def workload(n_per_species, seed):
+    from paper_1607_04069_gb300 import workloads as W
+    cfg = W.ccp_sputter(n_per_species=n_per_species, seed=seed)
+    cfg.update(sort_every_e=25, sort_every_i=200, sort_every_tp=50)
+    return cfg
+
+
+def oracle_rate(cfg, n_sample, steps, warmup=1):
+    """FP64 oracle on a sample of the same discharge: n_sample superparticles
+    per species with the weight scaled so the density is unchanged."""
+    import oracle as O
+    from paper_1607_04069_gb300 import workloads as W
+    c = dict(cfg)
+    c["weight"] = cfg["weight"] * cfg["n_e0"] / n_sample
+    orc = O.Oracle(W.oracle_params(c), 2 * n_sample + 65536, 2 * n_sample + 65536, 65536)
+    orc.init_species(0, n_sample, c["te0_ev"])
+    orc.init_species(1, n_sample, c["ti0_ev"])
+    orc.field()
+    orc.step(warmup)
+    t0 = time.perf_counter()
+    orc.step(steps)
+    dt = time.perf_counter() - t0
+    cnt = orc.counters()
+    return (cnt["n_e"] + cnt["n_i"]) * steps / dt, dt
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    cfg = workload(args.n_per_species, 1236)
+    n_sample = args.ref_sample
+    rate, dt = oracle_rate(cfg, n_sample, args.steps, warmup=args.warmup)
+    line = {"impl": "reference", "metric": "particle-steps/s", "value": rate, "unit": "particle-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg["name"], "particles": 2 * n_sample, "n_cells": cfg["n_cells"]},
+            "cpu_baseline": {"value": rate, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{n_sample}+{n_sample} superparticles of the same discharge "
+                                       f"(weight x{cfg['n_e0'] / n_sample:g}), {args.steps} full steps"},
+            "e2e": {"value": rate, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=30)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n-per-species", type=int, default=2_000_000)
+    ap.add_argument("--ref-sample", type=int, default=100_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=300)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    import paper_1607_04069_gb300 as P
+
+    torch.cuda.set_device(local)
+    cfg = workload(args.n_per_species, 1236 + rank)
+    stream = torch.cuda.current_stream()
+    d = P.Discharge(P.params_from_workload(cfg), stream=stream)
+    d.step(args.warmup)
+    d.sync()
+    n_start = sum(len(d.get_species(s)["id"]) for s in (0, 1))
+    flush = torch.empty(512 * 2**20, dtype=torch.uint8, device="cuda")      # > 129 MB L2
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    d.timing(True)
+    with Clocks(local) as clk:
+        barrier(ws)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            d.step(1)
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+        wall = time.perf_counter() - t0
+    d.sync()
+    step_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    mover_ms, mover_n = d.kernel_time("step")
+    tp_ms, tp_n = d.kernel_time("tp")
+    cmp_ms, cmp_n = d.kernel_time("compact")
+    d.timing(False)
+    n_end = sum(len(d.get_species(s)["id"]) for s in (0, 1))
+    psteps_local = 0.5 * (n_start + n_end) * args.steps
+    t_max = allreduce_max(step_ms, ws)
+    psteps = allreduce_sum(psteps_local, ws)
+    value = psteps / (t_max * 1e-3)
+
+    # roofline of the per-step kernel: algorithmic bytes / mean launch time
+    peak, peak_kind = hbm_peak()
+    per_launch_s = mover_ms / max(mover_n, 1) * 1e-3
+    achieved = ALGO_BYTES * 0.5 * (n_start + n_end) / per_launch_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic_per_launch(),
+                "kernel": "k_mover (fused gather/push/wall/MCC/deposit + last-CTA field solve)",
+                "algorithmic_bytes_per_particle_step": ALGO_BYTES, "peak_source": peak_kind,
+                "mean_launch_us": per_launch_s * 1e6}
+
+    # end to end through the public API: pinned host state -> device, steps, diagnostics -> host
+    e2e = None
+    if args.e2e_steps > 0:
+        sp = {s: d.get_species(s) for s in (0, 1)}
+        pinned = {}
+        for s in (0, 1):
+            n = len(sp[s]["id"])
+            pos = torch.empty(n, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+            pos[:] = np.rint(sp[s]["xi"] * (2.0**32 / cfg["n_cells"])).astype(np.uint64).astype(np.uint32)
+            arrs = []
+            for k in ("vx", "vy", "vz"):
+                a = torch.empty(n, dtype=torch.float32, pin_memory=True).numpy()
+                a[:] = sp[s][k]
+                arrs.append(a)
+            ids = torch.empty(n, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+            ids[:] = sp[s]["id"]
+            pinned[s] = (pos, *arrs, ids)
+        h2d = sum(sum(a.nbytes for a in pinned[s]) for s in (0, 1))
+        cap = max(len(pinned[s][0]) for s in (0, 1)) * 5 // 4 + 65536
+        d2 = P.Discharge(P.params_from_workload(cfg, n_e0=0, n_i0=0, cap_e=cap, cap_i=cap), stream=stream)
+        barrier(ws)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s in (0, 1):
+            d2.set_species(s, *pinned[s])
+        d2.step(args.e2e_steps)
+        out = [d2.diag(k) for k in ("phi", "n_e", "n_i", "iedf_l")]
+        cnt = d2.counters()
+        torch.cuda.synchronize()
+        e2e_wall = allreduce_max(time.perf_counter() - t0, ws)
+        d2h = sum(a.nbytes for a in out) + 8 * len(cnt)
+        n_e2e = allreduce_sum(sum(len(pinned[s][0]) for s in (0, 1)) * args.e2e_steps, ws)
+        e2e = {"value": n_e2e / e2e_wall, "unit": "particle-steps/s",
+               "h2d_bytes_per_step": h2d / args.e2e_steps, "d2h_bytes_per_step": d2h / args.e2e_steps,
+               "steps": args.e2e_steps, "note": "pinned host state uploaded, steps run, diagnostics read back"}
+        d2.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        n_sample = 500_000
+        rate, dt = oracle_rate(cfg, n_sample, 20)
+        cpu = {"value": rate, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"{n_sample}+{n_sample} superparticles of the same discharge (weight x4), "
+                         f"20 full PIC/MCC steps in {dt:.1f} s"}
+    clocks = clk.summary()
+    launches = mover_n + tp_n + 3 * cmp_n
+    if rank == 0:
+        line = {"metric": "particle-steps/s", "value": value, "unit": "particle-steps/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": cfg["name"], "particles_per_gpu": int(n_start),
+                           "n_cells": cfg["n_cells"], "sort_every": [25, 200], "tp_every": 40,
+                           "parallelism": f"replicas x{ws}" if ws > 1 else "1 gpu",
+                           "l2": "flushed before every timed step (512 MiB write); value from "
+                                 "per-step CUDA events",
+                           "wall_s_incl_flush": wall},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": int(launches),
+                "kernel_ms": {"step": mover_ms, "tp": tp_ms, "compact": cmp_ms}}
+        print(json.dumps(line), flush=True)
+    d.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -23,6 +23,11 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-re
          "-Xcompiler", "-ffp-contract=off"]
 
 
+def _defines() -> list[str]:
+    """Launch-shape defines from PG_DEFINES (e.g. "PG_MOVER_MIN_BLOCKS=3"), used by tuning runs."""
+    return [f"-D{d}" for d in os.environ.get("PG_DEFINES", "").split() if d]
+
+
 def nvcc() -> str:
     for cand in (shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
         if cand and os.path.exists(cand):
@@ -47,7 +52,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         o = os.path.join(OUT, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + hdrs):
-            cmd = [nvcc(), *ARCH, *FLAGS, "-I", inc, "-c", s, "-o", o]
+            cmd = [nvcc(), *ARCH, *FLAGS, *_defines(), "-I", inc, "-c", s, "-o", o]
             if verbose:
                 cmd.insert(1, "-Xptxas=-v")
             jobs.append(cmd)

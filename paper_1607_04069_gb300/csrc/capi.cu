@@ -92,20 +92,21 @@ void carve(pic_ctx* c, char* base, size_t* small_end, size_t* total)
     const int N1 = c->p.n_cells + 1;
     Dev& d = c->d;
     d.ctl = L.take<Ctl>(base, 1);
+    for (int k = 0; k < 3; ++k)
+        for (int s = 0; s < 2; ++s) {
+            d.qbuf[k][s] = L.take<unsigned long long>(base, N1);
+            d.fbuf[k][s] = L.take<long long>(base, N1);
+        }
     for (int s = 0; s < 2; ++s) {
-        d.q[s] = L.take<unsigned long long>(base, N1);
-        d.q_last[s] = L.take<unsigned long long>(base, N1);
-        d.flux[s] = L.take<long long>(base, N1);
-        d.diag.sum_q[s] = L.take<double>(base, N1);
-        d.diag.sum_flux[s] = L.take<double>(base, N1);
+        d.diag.sum_q[s] = L.take<unsigned long long>(base, 2 * N1);
+        d.diag.sum_flux[s] = L.take<long long>(base, 2 * N1);
         d.diag.iedf[s] = L.take<unsigned long long>(base, kNbIedf);
         d.diag.ieadf[s] = L.take<unsigned long long>(base, kNbIeadfE * kNbAng);
         d.diag.sp_e[s] = L.take<unsigned long long>(base, kNbSpE);
         d.diag.sp_ang[s] = L.take<unsigned long long>(base, kNbAng);
     }
-    d.diag.sum_phi = L.take<double>(base, N1);
-    d.diag.tp_dens = L.take<double>(base, N1);
-    d.diag.tp_vx = L.take<double>(base, N1);
+    d.diag.tp_dens = L.take<unsigned long long>(base, 2 * N1);
+    d.diag.tp_vx = L.take<long long>(base, 2 * N1);
     d.diag.eedf = L.take<unsigned long long>(base, kNbEedf);
     d.tp_q = L.take<unsigned long long>(base, N1);
     d.tp_flux = L.take<long long>(base, N1);
@@ -119,7 +120,7 @@ void carve(pic_ctx* c, char* base, size_t* small_end, size_t* total)
     for (int s = 0; s < 3; ++s)
         for (int h = 0; h < 2; ++h) {
             SpBuf& B = d.buf[s][h];
-            const size_t n = (size_t)(cap[s] > 0 ? cap[s] : 1);
+            const size_t n = (size_t)((cap[s] > 0 ? cap[s] : 1) + 3) & ~(size_t)3;   // whole 4-slot groups
             if (c->p.pos_precision == 64 && s != kTP) B.pos = L.take<double>(base, n);
             else B.pos = L.take<uint32_t>(base, n);
             B.vx = L.take<float>(base, n);
@@ -127,6 +128,7 @@ void carve(pic_ctx* c, char* base, size_t* small_end, size_t* total)
             B.vz = L.take<float>(base, n);
             B.id = L.take<uint64_t>(base, n);
         }
+    for (int s = 0; s < 2; ++s) d.evflag[s] = L.take<unsigned char>(base, (size_t)(cap[s] > 0 ? cap[s] : 1) + 4);
     *total = (L.off + 255) & ~(size_t)255;
 }
 
@@ -184,6 +186,7 @@ void derive(pic_ctx* c)
     d.A = dx * kQE * p.weight / (4294967296.0 * kEPS0);
     d.V0 = p.rf_volt_v;
     d.omega = 2.0 * kPI * p.rf_freq_hz;
+    d.f_rf = p.rf_freq_hz;
     d.dt = p.dt;
     d.qm_dt[kE] = (float)(-kQE / kME * p.dt);
     d.qm_dt[kI] = (float)(kQE / kMAR * p.dt);
@@ -350,12 +353,17 @@ int pic_create(const pic_params* pin, void* stream, pic_ctx** out)
     carve(c, (char*)c->arena, &small_end, &total);
     sync_desc(c);
     cudaDeviceProp prop;
+    e = cudaSuccess;
     if (cudaGetDeviceProperties(&prop, c->device) != cudaSuccess) {
         pic_destroy(c);
         return fail(PIC_ERR_CUDA, "cudaGetDeviceProperties");
     }
     c->sms = prop.multiProcessorCount;
-    const int per_sm = c->p.ctas_per_sm > 0 ? c->p.ctas_per_sm : 4;
+    int per_sm = c->p.ctas_per_sm;
+    if (per_sm <= 0) {
+        e = mover_occupancy(c->d, &per_sm);
+        if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+    }
     c->grid_mover = c->sms * per_sm;
     c->grid_tp = c->sms * 4;
     c->grid_sort = c->sms * 8;
@@ -368,6 +376,8 @@ int pic_create(const pic_params* pin, void* stream, pic_ctx** out)
     h.cap[kI] = c->p.cap_i;
     h.cap[kTP] = c->p.cap_tp;
     e = cudaMemsetAsync(c->arena, 0, c->small_bytes, c->stream);
+    for (int s = 0; s < 2 && e == cudaSuccess; ++s)
+        e = cudaMemsetAsync(c->d.evflag[s], 0, (size_t)(s == kE ? c->p.cap_e : c->p.cap_i) + 4, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d.ctl, &h, sizeof h, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = launch_init(c->d, kE, c->p.n_e0, (float)std::sqrt(c->p.te0_ev * kQE / kME), c->stream);
     if (e == cudaSuccess) e = launch_init(c->d, kI, c->p.n_i0, (float)std::sqrt(c->p.ti0_ev * kQE / kMAR), c->stream);
@@ -484,11 +494,33 @@ static int read_ctl(pic_ctx* c, Ctl* h)
     return PIC_OK;
 }
 
+static double u128d(const unsigned long long* p) { return (double)p[1] * 18446744073709551616.0 + (double)p[0]; }
+static double s128d(const long long* p)
+{
+    return (double)p[1] * 18446744073709551616.0 + (double)(unsigned long long)p[0];
+}
+
+// Potential of a (time-averaged) net charge count qn[0..N] with electrode
+// voltage v, by the double prefix sum of the discrete Poisson equation
+// (phi[m] = v + m D0 - A sum_{k<m} S_k, S_k = sum_{j=1..k} qn[j]).
+static void host_phi(int N, double A, const std::vector<double>& qn, double v, std::vector<double>& phi)
+{
+    std::vector<long double> S(N + 1), T(N + 1);
+    S[0] = 0;
+    for (int m = 1; m <= N; ++m) S[m] = S[m - 1] + (long double)qn[m];
+    T[0] = 0;
+    for (int m = 1; m <= N; ++m) T[m] = T[m - 1] + S[m - 1];
+    const long double D0 = (-(long double)v + (long double)A * T[N]) / N;
+    phi.resize(N + 1);
+    for (int m = 0; m <= N; ++m) phi[m] = (double)((long double)v + m * D0 - (long double)A * T[m]);
+}
+
 int pic_diag(pic_ctx* c, int kind, double* out, int64_t cap, int64_t* n_written)
 {
     if (!c || (!out && cap > 0) || kind < 0 || kind >= PIC_DIAG_COUNT)
         return fail(PIC_ERR_INVALID_ARG, "bad diag request");
     CK(cudaSetDevice(c->device));
+    CK(launch_field(c->d, 1, c->stream));          // current state into the averages, FP64 field
     Ctl h;
     int rc = read_ctl(c, &h);
     if (rc) return rc;
@@ -506,30 +538,50 @@ int pic_diag(pic_ctx* c, int kind, double* out, int64_t cap, int64_t* n_written)
         dst.assign(t.begin(), t.end());
         return PIC_OK;
     };
+    auto getu128 = [&](const unsigned long long* src, std::vector<double>& dst) -> int {
+        std::vector<unsigned long long> t(2 * (size_t)N1);
+        CK(cudaMemcpy(t.data(), src, t.size() * 8, cudaMemcpyDeviceToHost));
+        dst.resize(N1);
+        for (int m = 0; m < N1; ++m) dst[m] = u128d(&t[2 * m]);
+        return PIC_OK;
+    };
+    auto gets128 = [&](const long long* src, std::vector<double>& dst) -> int {
+        std::vector<long long> t(2 * (size_t)N1);
+        CK(cudaMemcpy(t.data(), src, t.size() * 8, cudaMemcpyDeviceToHost));
+        dst.resize(N1);
+        for (int m = 0; m < N1; ++m) dst[m] = s128d(&t[2 * m]);
+        return PIC_OK;
+    };
     auto vol = [&](int m) { return (m == 0 || m == N) ? 0.5 * dx : dx; };
+    const double navg = h.n_avg ? (double)h.n_avg : 1.0, nflux = h.n_flux ? (double)h.n_flux : 1.0;
     std::vector<double> a, b;
     switch (kind) {
-    case PIC_DIAG_PHI:
-        if ((rc = getd(c->d.diag.sum_phi, N1, v))) return rc;
-        for (auto& x : v) x = h.n_avg ? x / (double)h.n_avg : 0.0;
+    case PIC_DIAG_PHI: {
+        if ((rc = getu128(c->d.diag.sum_q[kE], a))) return rc;
+        if ((rc = getu128(c->d.diag.sum_q[kI], b))) return rc;
+        std::vector<double> qn(N1);
+        for (int m = 0; m < N1; ++m) qn[m] = (b[m] - a[m]) / navg;
+        host_phi(N, c->d.A, qn, h.sum_v / navg, v);
+        if (!h.n_avg) std::fill(v.begin(), v.end(), 0.0);
         break;
+    }
     case PIC_DIAG_NE: case PIC_DIAG_NI:
-        if ((rc = getd(c->d.diag.sum_q[kind - PIC_DIAG_NE], N1, v))) return rc;
-        for (int m = 0; m < N1; ++m) v[m] = h.n_avg ? w * v[m] / (4294967296.0 * vol(m) * h.n_avg) : 0.0;
+        if ((rc = getu128(c->d.diag.sum_q[kind - PIC_DIAG_NE], v))) return rc;
+        for (int m = 0; m < N1; ++m) v[m] = h.n_avg ? w * v[m] / (4294967296.0 * vol(m) * navg) : 0.0;
         break;
     case PIC_DIAG_GAMMA_E: case PIC_DIAG_GAMMA_I:
-        if ((rc = getd(c->d.diag.sum_flux[kind - PIC_DIAG_GAMMA_E], N1, v))) return rc;
-        for (int m = 0; m < N1; ++m) v[m] = h.n_flux ? w * v[m] / (vol(m) * h.n_flux) : 0.0;
+        if ((rc = gets128(c->d.diag.sum_flux[kind - PIC_DIAG_GAMMA_E], v))) return rc;
+        for (int m = 0; m < N1; ++m) v[m] = h.n_flux ? w * v[m] * 0x1p-16 / (vol(m) * nflux) : 0.0;
         break;
     case PIC_DIAG_VE: case PIC_DIAG_VI: {
         const int s = kind - PIC_DIAG_VE;
-        if ((rc = getd(c->d.diag.sum_flux[s], N1, a))) return rc;
-        if ((rc = getd(c->d.diag.sum_q[s], N1, b))) return rc;
+        if ((rc = gets128(c->d.diag.sum_flux[s], a))) return rc;
+        if ((rc = getu128(c->d.diag.sum_q[s], b))) return rc;
         v.resize(N1);
         for (int m = 0; m < N1; ++m) {
-            // Gamma/n with both averages: (sum_flux/n_flux) / (sum_q / (2^32 n_avg))
-            const double nq = b[m] / (4294967296.0 * (h.n_avg ? h.n_avg : 1));
-            v[m] = (h.n_flux && nq > 0) ? (a[m] / h.n_flux) / nq : 0.0;
+            // Gamma / n with both averages: (sum_flux 2^-16 / n_flux) / (sum_q 2^-32 / n_avg)
+            const double nq = b[m] * 0x1p-32 / navg;
+            v[m] = (h.n_flux && nq > 0) ? (a[m] * 0x1p-16 / nflux) / nq : 0.0;
         }
         break;
     }
@@ -549,14 +601,15 @@ int pic_diag(pic_ctx* c, int kind, double* out, int64_t cap, int64_t* n_written)
         if ((rc = getu(c->d.diag.sp_ang[kind - PIC_DIAG_SPUTTER_ANG_L], kNbAng, v))) return rc;
         break;
     case PIC_DIAG_TP_DENS:
-        if ((rc = getd(c->d.diag.tp_dens, N1, v))) return rc;
-        for (int m = 0; m < N1; ++m) v[m] = h.n_tp_samp ? w * v[m] / (vol(m) * h.n_tp_samp) : 0.0;
+        if ((rc = getu128(c->d.diag.tp_dens, v))) return rc;
+        for (int m = 0; m < N1; ++m)
+            v[m] = h.n_tp_samp ? w * v[m] * 0x1p-32 / (vol(m) * (double)h.n_tp_samp) : 0.0;
         break;
     case PIC_DIAG_TP_V:
-        if ((rc = getd(c->d.diag.tp_vx, N1, a))) return rc;
-        if ((rc = getd(c->d.diag.tp_dens, N1, b))) return rc;
+        if ((rc = gets128(c->d.diag.tp_vx, a))) return rc;
+        if ((rc = getu128(c->d.diag.tp_dens, b))) return rc;
         v.resize(N1);
-        for (int m = 0; m < N1; ++m) v[m] = b[m] > 0 ? a[m] / b[m] : 0.0;
+        for (int m = 0; m < N1; ++m) v[m] = b[m] > 0 ? (a[m] * 0x1p-16) / (b[m] * 0x1p-32) : 0.0;
         break;
     case PIC_DIAG_E:
         if ((rc = getd(c->d.E64, N1, v))) return rc;
@@ -578,19 +631,24 @@ int pic_reset_averages(pic_ctx* c)
     const int N1 = c->p.n_cells + 1;
     const Diag& g = c->d.diag;
     for (int s = 0; s < 2; ++s) {
-        CK(cudaMemsetAsync(g.sum_q[s], 0, N1 * sizeof(double), c->stream));
-        CK(cudaMemsetAsync(g.sum_flux[s], 0, N1 * sizeof(double), c->stream));
+        CK(cudaMemsetAsync(g.sum_q[s], 0, 2 * N1 * 8, c->stream));
+        CK(cudaMemsetAsync(g.sum_flux[s], 0, 2 * N1 * 8, c->stream));
         CK(cudaMemsetAsync(g.iedf[s], 0, kNbIedf * 8, c->stream));
         CK(cudaMemsetAsync(g.ieadf[s], 0, kNbIeadfE * kNbAng * 8, c->stream));
         CK(cudaMemsetAsync(g.sp_e[s], 0, kNbSpE * 8, c->stream));
         CK(cudaMemsetAsync(g.sp_ang[s], 0, kNbAng * 8, c->stream));
     }
-    CK(cudaMemsetAsync(g.sum_phi, 0, N1 * sizeof(double), c->stream));
-    CK(cudaMemsetAsync(g.tp_dens, 0, N1 * sizeof(double), c->stream));
-    CK(cudaMemsetAsync(g.tp_vx, 0, N1 * sizeof(double), c->stream));
+    CK(cudaMemsetAsync(g.tp_dens, 0, 2 * N1 * 8, c->stream));
+    CK(cudaMemsetAsync(g.tp_vx, 0, 2 * N1 * 8, c->stream));
     CK(cudaMemsetAsync(g.eedf, 0, kNbEedf * 8, c->stream));
-    CK(cudaMemsetAsync(&c->d.ctl->n_avg, 0, 3 * sizeof(long long), c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+    Ctl h;
+    int rc = read_ctl(c, &h);
+    if (rc) return rc;
+    h.n_avg = h.n_flux = h.n_tp_samp = 0;
+    h.sum_v = 0.0;
+    h.acc_upto = h.step;               // the current state is not part of the new window
+    CK(cudaMemcpy(&c->d.ctl->acc_upto, &h.acc_upto, sizeof(long long) * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(&c->d.ctl->sum_v, &h.sum_v, sizeof(double), cudaMemcpyHostToDevice));
     return PIC_OK;
 }
 
@@ -683,7 +741,13 @@ int pic_set_species(pic_ctx* c, int s, int64_t n, const void* pos, const float* 
     }
     long long nn = n;
     CK(cudaMemcpyAsync(&c->d.ctl->n[s], &nn, sizeof nn, cudaMemcpyHostToDevice, c->stream));
-    if (!keep_field && s != kTP) CK(launch_mover(c->d, c->grid_mover, 1, c->stream));
+    if (!keep_field && s != kTP) {      // re-deposit the state of the current step
+        const int slot = h.step % 3;
+        const size_t N1 = (size_t)c->p.n_cells + 1;
+        CK(cudaMemsetAsync(c->d.qbuf[slot][kE], 0, N1 * 8, c->stream));
+        CK(cudaMemsetAsync(c->d.qbuf[slot][kI], 0, N1 * 8, c->stream));
+        CK(launch_mover(c->d, c->grid_mover, 1, c->stream));
+    }
     CK(cudaStreamSynchronize(c->stream));
     return PIC_OK;
 }
@@ -692,12 +756,16 @@ int pic_get_field(pic_ctx* c, double* E, double* phi, int64_t* q_e, int64_t* q_i
 {
     if (!c) return fail(PIC_ERR_INVALID_ARG, "ctx is NULL");
     CK(cudaSetDevice(c->device));
-    CK(cudaStreamSynchronize(c->stream));
+    CK(launch_field(c->d, 0, c->stream));
+    Ctl h;
+    int rc = read_ctl(c, &h);
+    if (rc) return rc;
     const size_t N1 = (size_t)c->p.n_cells + 1;
+    const int slot = h.step % 3;
     if (E) CK(cudaMemcpy(E, c->d.E64, N1 * 8, cudaMemcpyDeviceToHost));
     if (phi) CK(cudaMemcpy(phi, c->d.phi, N1 * 8, cudaMemcpyDeviceToHost));
-    if (q_e) CK(cudaMemcpy(q_e, c->d.q_last[kE], N1 * 8, cudaMemcpyDeviceToHost));
-    if (q_i) CK(cudaMemcpy(q_i, c->d.q_last[kI], N1 * 8, cudaMemcpyDeviceToHost));
+    if (q_e) CK(cudaMemcpy(q_e, c->d.qbuf[slot][kE], N1 * 8, cudaMemcpyDeviceToHost));
+    if (q_i) CK(cudaMemcpy(q_i, c->d.qbuf[slot][kI], N1 * 8, cudaMemcpyDeviceToHost));
     return PIC_OK;
 }
 
@@ -708,8 +776,9 @@ int pic_set_field(pic_ctx* c, const double* E)
     const size_t N1 = (size_t)c->p.n_cells + 1;
     std::vector<float> f(N1);
     for (size_t m = 0; m < N1; ++m) f[m] = (float)E[m];
-    CK(cudaMemcpyAsync(c->d.E64, E, N1 * 8, cudaMemcpyHostToDevice, c->stream));
+    const unsigned int one = 1;
     CK(cudaMemcpyAsync(c->d.E32, f.data(), N1 * 4, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(&c->d.ctl->field_override, &one, sizeof one, cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return PIC_OK;
 }

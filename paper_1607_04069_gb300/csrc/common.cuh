@@ -83,18 +83,23 @@ struct Ctl {                   // device control block
     unsigned int done, tp_done, sort_done;
     unsigned int cur[3];       // active ping-pong half per species
     unsigned int err;
-    unsigned int pad;
+    unsigned int field_override;   // next step uses E32 as given instead of solving
+    long long acc_upto;        // last step whose state entered the time averages
     long long n_avg, n_flux, n_tp_samp;
     long long sort_total;
+    double sum_v;              // sum of the electrode voltage over the averaged steps
     unsigned long long cnt[kNumCnt];
 };
 
-struct Diag {                  // accumulators of the time-averaged diagnostics
-    double* sum_q[2];          // sum over steps of q_e, q_i (units of 2^-32 particles)
-    double* sum_phi;
-    double* sum_flux[2];       // sum over samples of sum_k S_m(x_k) v_x,k
-    double* tp_dens;           // sum over TP steps of sum_k S_m(x_k)
-    double* tp_vx;             // sum over TP steps of sum_k S_m(x_k) v_x,k
+// Time-averaged diagnostics are integer sums (128-bit, two words per node:
+// low word, high word), so they are exact and independent of the order in
+// which CTAs deposit.  The averaged potential follows from the averaged
+// charge and electrode voltage, since the field solve is linear.
+struct Diag {
+    unsigned long long* sum_q[2];   // [2 (N+1)] sum over steps of q_e, q_i (2^-32 particles)
+    long long* sum_flux[2];         // [2 (N+1)] sum over samples of sum_k W_m(x_k) rint(v_x,k), 2^-16
+    unsigned long long* tp_dens;    // [2 (N+1)] sum over TP samples of the TP deposit
+    long long* tp_vx;               // [2 (N+1)] sum over TP samples of the TP v_x moment
     unsigned long long* iedf[2];
     unsigned long long* ieadf[2];
     unsigned long long* eedf;
@@ -106,21 +111,24 @@ struct Dev {                   // everything a kernel needs, passed by value
     SpBuf buf[3][2];
     Ctl* ctl;
     Diag diag;
-    unsigned long long* q[2];        // per-step charge histograms (e, i)
-    unsigned long long* q_last[2];   // copy of the last solved deposit (diagnostics)
-    long long* flux[2];              // per-sample flux histograms (e, i), units 2^-16 m/s
+    // per-step charge and flux histograms, rotating over three slots: the
+    // launch for step l solves from slot l%3, deposits x^{l+1} into slot
+    // (l+1)%3 and clears slot (l+2)%3
+    unsigned long long* qbuf[3][2];
+    long long* fbuf[3][2];
     unsigned long long* tp_q;        // per-TP-step density histogram
     long long* tp_flux;              // per-TP-step v_x histogram
-    float* E32;                      // field at the nodes for the gather
-    double* E64;
+    float* E32;                      // field given by pic_set_field (override)
+    double* E64;                     // FP64 field and potential of the current state
     double* phi;
+    unsigned char* evflag[2];        // per-slot event flags, used when a CTA's event queue is full
     unsigned int* sort_cnt;          // [ncell] cell counts (sort scratch)
     unsigned int* sort_off;          // [ncell] running offsets (sort scratch)
     // geometry
     int ncell, kshift, pos64, pad0;
     double L, dx, inv_dx;
     // field solve: phi[m+1] - 2 phi[m] + phi[m-1] = -A q_net[m]; A = dx e w / (2^32 eps0)
-    double A, V0, omega, dt;
+    double A, V0, omega, dt, f_rf;
     // push
     float qm_dt[2];                  // (q/m) dt
     float push32;                    // dt 2^32 / L  (fixed-point displacement per m/s)
@@ -139,15 +147,34 @@ struct Dev {                   // everything a kernel needs, passed by value
     uint64_t seed;
 };
 
+__device__ __forceinline__ void add_u128(unsigned long long* p, unsigned long long v)
+{
+    const unsigned long long lo = p[0] + v;
+    p[1] += lo < v ? 1ull : 0ull;
+    p[0] = lo;
+}
+__device__ __forceinline__ void add_s128(long long* p, long long v)
+{
+    const unsigned long long lo = (unsigned long long)p[0] + (unsigned long long)v;
+    p[1] += (lo < (unsigned long long)v ? 1ll : 0ll) + (v < 0 ? -1ll : 0ll);
+    p[0] = (long long)lo;
+}
+// electrode voltage at step l: V0 sin(2 pi f l dt), argument reduced exactly by sinpi
+__device__ __forceinline__ double v_rf(const Dev& d, unsigned int l)
+{
+    return d.V0 * sinpi(2.0 * d.f_rf * ((double)l * d.dt));
+}
+
 // ---------------------------------------------------------------- Philox4x32-10
 __device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1)
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
         if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
-        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        const unsigned long long p0 = 0xD2511F53ull * c.x;     // one 32x32->64 product each
+        const unsigned long long p1 = 0xCD9E8D57ull * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1,
+                       (uint32_t)p0);
     }
     return c;
 }

@@ -39,6 +39,7 @@ __global__ void k_init(Dev d, int s, long long n, float vth)
 // ---------------------------------------------------------------- helpers
 struct BlockTally {            // per-CTA event counts, flushed once per CTA
     unsigned int elastic, excit, ioniz, cx, iso, numerics, capacity;
+    unsigned int imp_e[2];
 };
 
 __device__ __forceinline__ void hist_add(unsigned long long* h, int nb, float x, float xmax)
@@ -107,8 +108,8 @@ __device__ __forceinline__ void store_dead<double>(double* P, long long i) { P[i
 // remaining energy uniformly and creates an e-/Ar+ pair at x^{l+1}.
 template <typename PosT>
 __device__ void mcc_electron(const Dev& d, uint4 c, uint64_t id, uint32_t l, PosT xn, float& vx,
-                             float& vy, float& vz, long long n0e, long long n0i,
-                             unsigned long long* sq, BlockTally* tally)
+                             float& vy, float& vz, long long born_e, long long born_i,
+                             unsigned long long* qe_dst, unsigned long long* qion, BlockTally* tally)
 {
     const float v2 = vx * vx + vy * vy + vz * vz;
     const float v = sqrtf(v2);
@@ -147,8 +148,8 @@ __device__ void mcc_electron(const Dev& d, uint4 c, uint64_t id, uint32_t l, Pos
         const float2 n34 = box_muller(cn.z, cn.w);
         vx = vs * dir.x; vy = vs * dir.y; vz = vs * dir.z;
         atomicAdd(&tally->ioniz, 1u);
-        const long long ie = n0e + atomicAdd((unsigned long long*)&d.ctl->births[kE], 1ull);
-        const long long ii = n0i + atomicAdd((unsigned long long*)&d.ctl->births[kI], 1ull);
+        const long long ie = born_e + atomicAdd((unsigned long long*)&d.ctl->births[kE], 1ull);
+        const long long ii = born_i + atomicAdd((unsigned long long*)&d.ctl->births[kI], 1ull);
         const bool ok = ie < d.ctl->cap[kE] && ii < d.ctl->cap[kI];
         const SpBuf Be = d.buf[kE][d.ctl->cur[kE]];
         const SpBuf Bi = d.buf[kI][d.ctl->cur[kI]];
@@ -166,10 +167,10 @@ __device__ void mcc_electron(const Dev& d, uint4 c, uint64_t id, uint32_t l, Pos
         Bi.id[ii] = child_id(cb.z, cb.w, kI);
         uint32_t j, wr;
         cell_of(xn, d.kshift, j, wr);
-        atomicAdd(&sq[j], (1ull << 32) - wr);                 // electron child: this CTA's histogram
-        if (wr) atomicAdd(&sq[j + 1], (unsigned long long)wr);
-        atomicAdd(&d.q[kI][j], (1ull << 32) - wr);            // ion child: global histogram
-        if (wr) atomicAdd(&d.q[kI][j + 1], (unsigned long long)wr);
+        atomicAdd(&qe_dst[j], (1ull << 32) - wr);             // electron child: global histogram
+        if (wr) atomicAdd(&qe_dst[j + 1], (unsigned long long)wr);
+        atomicAdd(&qion[j], (1ull << 32) - wr);               // ion child: global histogram
+        if (wr) atomicAdd(&qion[j + 1], (unsigned long long)wr);
     }
 }
 
@@ -214,6 +215,8 @@ __device__ __forceinline__ void flush_tally(const Dev& d, const BlockTally& t)
     if (t.ioniz) atomicAdd(&c->cnt[kCntIoniz], (unsigned long long)t.ioniz);
     if (t.cx) atomicAdd(&c->cnt[kCntCx], (unsigned long long)t.cx);
     if (t.iso) atomicAdd(&c->cnt[kCntIso], (unsigned long long)t.iso);
+    if (t.imp_e[0]) atomicAdd(&c->cnt[kCntImpEL], (unsigned long long)t.imp_e[0]);
+    if (t.imp_e[1]) atomicAdd(&c->cnt[kCntImpER], (unsigned long long)t.imp_e[1]);
     if (t.numerics) {
         atomicAdd(&c->cnt[kCntNumerics], (unsigned long long)t.numerics);
         atomicOr(&c->err, kErrNumerics);
@@ -225,21 +228,242 @@ __device__ __forceinline__ void flush_tally(const Dev& d, const BlockTally& t)
 }
 
 // ---------------------------------------------------------------- mover
-// MODE 0: full PIC/MCC step.  MODE 1: deposit the current state and solve
-// for the field at the current step (creation, after a state upload).
+// Slots are streamed in groups of four (16-byte vector loads and stores);
+// each thread owns a contiguous run of groups, so cell-sorted particles are
+// deposited by run-length sums in registers and only a change of cell issues
+// shared atomics.  Wall hits and collision candidates (well under 1% of the
+// particles per step) are queued in shared memory and handled after the
+// streaming loop; births go to slots from round_up(n, 4) on, which no vector
+// store of this launch touches.
+constexpr int kQueueCap = 1024;
+enum : uint32_t { kEvCand = 0u, kEvWallL = 1u, kEvWallR = 2u };
+
+template <bool P64> struct Pos4;
+template <> struct Pos4<false> {
+    uint4 v;
+    __device__ __forceinline__ void load(const void* base, long long g) { v = ((const uint4*)base)[g]; }
+    __device__ __forceinline__ void store(void* base, long long g) const { ((uint4*)base)[g] = v; }
+    __device__ __forceinline__ uint32_t get(int u) const { return u == 0 ? v.x : u == 1 ? v.y : u == 2 ? v.z : v.w; }
+    __device__ __forceinline__ void set(int u, uint32_t x)
+    {
+        if (u == 0) v.x = x; else if (u == 1) v.y = x; else if (u == 2) v.z = x; else v.w = x;
+    }
+};
+template <> struct Pos4<true> {
+    double2 a, b;
+    __device__ __forceinline__ void load(const void* base, long long g)
+    {
+        a = ((const double2*)base)[2 * g];
+        b = ((const double2*)base)[2 * g + 1];
+    }
+    __device__ __forceinline__ void store(void* base, long long g) const
+    {
+        ((double2*)base)[2 * g] = a;
+        ((double2*)base)[2 * g + 1] = b;
+    }
+    __device__ __forceinline__ double get(int u) const { return u == 0 ? a.x : u == 1 ? a.y : u == 2 ? b.x : b.y; }
+    __device__ __forceinline__ void set(int u, double x)
+    {
+        if (u == 0) a.x = x; else if (u == 1) a.y = x; else if (u == 2) b.x = x; else b.y = x;
+    }
+};
+
+__device__ __forceinline__ float f4get(const float4& v, int u) { return u == 0 ? v.x : u == 1 ? v.y : u == 2 ? v.z : v.w; }
+__device__ __forceinline__ void f4set(float4& v, int u, float x)
+{
+    if (u == 0) v.x = x; else if (u == 1) v.y = x; else if (u == 2) v.z = x; else v.w = x;
+}
+
+__device__ __forceinline__ long long round4(long long n) { return (n + 3) & ~3ll; }
+
+template <typename PosT> __device__ __forceinline__ PosT dead_value();
+template <> __device__ __forceinline__ uint32_t dead_value<uint32_t>() { return 0u; }
+template <> __device__ __forceinline__ double dead_value<double>() { return -1.0; }
+
+// Shared-memory accumulators of one CTA.  The linear weights are summed per
+// cell in three 32-bit counters -- particles n_j, and the high and low 16 bits
+// of their right-node weights wr -- so that node m receives
+//     n_m 2^32 - (hi_m 2^16 + lo_m) + (hi_{m-1} 2^16 + lo_{m-1}),
+// exactly as the per-particle rule would give.  32-bit shared atomics are
+// native; with at most 65536 particles per tile no counter can overflow.
+// The flux moment uses 64-bit sums kept as (low, high) 32-bit pairs with the
+// carry propagated from the low word's atomic return value.
+constexpr long long kTileGroups = 16384;     // 65536 particles
+
+// bytes of the region shared by the field-solve copies (2 x u64 [N+1]) and
+// the tile sums (3 x u32 [N] + 2 x u32 [N+1]), rounded to 16
+__host__ __device__ __forceinline__ size_t acc_bytes(int N)
+{
+    const size_t a = (size_t)(N + 1) * 16, b = (size_t)N * 12 + (size_t)(N + 1) * 8;
+    return ((a > b ? a : b) + 15) & ~(size_t)15;
+}
+
+struct Acc {
+    unsigned int* cnt;   // [N]
+    unsigned int* whi;   // [N]
+    unsigned int* wlo;   // [N]
+    unsigned int* flo;   // [N+1]
+    int* fhi;            // [N+1]
+};
+
+__device__ __forceinline__ void acc_add64(unsigned int* lo, int* hi, int m, long long v)
+{
+    const unsigned int vl = (unsigned int)v;
+    const unsigned int old = atomicAdd(&lo[m], vl);
+    const int carry = old + vl < old ? 1 : 0;
+    const int vh = (int)(v >> 32) + carry;
+    if (vh) atomicAdd(&hi[m], vh);
+}
+
+// run of consecutive particles of one thread in the same cell
+struct Run {
+    uint32_t j, n, h, l;
+    long long fL, fR;
+    __device__ __forceinline__ void flush(const Acc& A, bool sample)
+    {
+        if (j != 0xffffffffu) {
+            atomicAdd(&A.cnt[j], n);
+            if (h) atomicAdd(&A.whi[j], h);
+            if (l) atomicAdd(&A.wlo[j], l);
+            if (sample) {
+                if (fL) acc_add64(A.flo, A.fhi, j, fL);
+                if (fR) acc_add64(A.flo, A.fhi, j + 1, fR);
+            }
+        }
+        n = h = l = 0;
+        fL = fR = 0;
+    }
+    __device__ __forceinline__ void add(const Acc& A, uint32_t jn, uint32_t wr, float vx, bool sample)
+    {
+        if (jn != j) {
+            flush(A, sample);
+            j = jn;
+        }
+        n += 1;
+        h += wr >> 16;
+        l += wr & 0xffffu;
+        if (sample) {
+            const long long vq = (long long)__float2int_rn(vx);
+            const long long wr16 = (long long)(wr >> 16);
+            fL += vq * (65536 - wr16);
+            fR += vq * wr16;
+        }
+    }
+};
+
+// one queued event: a wall hit (both species) or a collision candidate
+template <typename PosT>
+__device__ __noinline__ void handle_event(const Dev& d, int s, long long i, uint32_t kind, uint32_t l,
+                                          long long born_e, long long born_i, long long ntp,
+                                          unsigned long long* qe_dst, unsigned long long* qion,
+                                          BlockTally* tally)
+{
+    const SpBuf B = d.buf[s][d.ctl->cur[s]];
+    float vx = B.vx[i], vy = B.vy[i], vz = B.vz[i];
+    const uint64_t id = B.id[i];
+    if (kind == kEvCand) {
+        const uint4 c = draw(d.seed, id, l, kPurColl);
+        if (s == kE)
+            mcc_electron<PosT>(d, c, id, l, ((const PosT*)B.pos)[i], vx, vy, vz, born_e, born_i, qe_dst, qion,
+                               tally);
+        else
+            mcc_ion(d, c, id, l, vx, vy, vz, tally);
+        B.vx[i] = vx;
+        B.vy[i] = vy;
+        B.vz[i] = vz;
+    } else {
+        const int el = kind == kEvWallL ? 0 : 1;
+        if (s == kI) ion_wall(d, id, l, el, vx, vy, vz, ntp, tally);
+        else atomicAdd(&tally->imp_e[el], 1u);
+    }
+}
+
+__device__ __forceinline__ void philox4x(uint4 (&c)[4], uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const unsigned long long p0 = 0xD2511F53ull * c[u].x;
+            const unsigned long long p1 = 0xCD9E8D57ull * c[u].z;
+            c[u] = make_uint4((uint32_t)(p1 >> 32) ^ c[u].y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c[u].w ^ k1,
+                              (uint32_t)p0);
+        }
+    }
+}
+
+template <bool P64>
+struct Grp {                   // one group of four slots, as loaded
+    Pos4<P64> p;
+    float4 v;
+    ulonglong2 a, b;
+};
+
 template <bool P64, int MODE>
-__global__ void __launch_bounds__(kMoverThreads) k_mover(Dev d)
+__device__ __forceinline__ Grp<P64> load_group(const SpBuf& B, long long g)
+{
+    Grp<P64> G;
+    G.p.load(B.pos, g);
+    if (MODE == 0) {
+        G.v = ((const float4*)B.vx)[g];
+        G.a = ((const ulonglong2*)B.id)[2 * g];
+        G.b = ((const ulonglong2*)B.id)[2 * g + 1];
+    }
+    return G;
+}
+
+// node totals of the tile into the global histograms, and clear the tile sums
+__device__ void flush_tile(const Acc& A, int N, unsigned int jlo, unsigned int jhi, bool sample,
+                           unsigned long long* qdst, long long* fdst)
+{
+    if (jlo != 0xffffffffu) {
+        for (int m = (int)jlo + threadIdx.x; m <= (int)jhi + 1; m += blockDim.x) {
+            unsigned long long v = 0;
+            if (m < N) v += ((unsigned long long)A.cnt[m] << 32) - (((unsigned long long)A.whi[m] << 16) + A.wlo[m]);
+            if (m > 0) v += ((unsigned long long)A.whi[m - 1] << 16) + A.wlo[m - 1];
+            if (v) atomicAdd(&qdst[m], v);
+            if (sample) {
+                const long long f = (long long)(((unsigned long long)(unsigned int)A.fhi[m] << 32) | A.flo[m]);
+                if (f) atomicAdd((unsigned long long*)&fdst[m], (unsigned long long)f);
+            }
+        }
+    }
+    __syncthreads();
+    for (int m = threadIdx.x; m <= N; m += blockDim.x) {
+        if (m < N) A.cnt[m] = A.whi[m] = A.wlo[m] = 0;
+        A.flo[m] = 0;
+        A.fhi[m] = 0;
+    }
+}
+
+// MODE 0: full PIC/MCC step.  MODE 1: deposit the current state (creation,
+// after a state upload).  Slots are streamed in groups of four with 16-byte
+// vector loads and stores; consecutive threads take consecutive groups and
+// each thread loads its next group before working on the current one.
+template <bool P64, int MODE>
+__global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d)
 {
     using PosT = typename std::conditional<P64, double, uint32_t>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int N1 = d.ncell + 1;
-    unsigned long long* sq = (unsigned long long*)smem_raw;
-    long long* sflux = (long long*)(sq + N1);
-    float* sE = (float*)(sflux + N1);
-    unsigned int* seedf = (unsigned int*)(sE + ((N1 + 3) & ~3));
+    const int N = d.ncell, N1 = N + 1;
+    // layout: [field solve: qe, qi (u64 N1 each) | later: tile sums] [sEd float2 N] [sE float N1]
+    //         [eedf u32 256] [queue u32 kQueueCap]
+    unsigned long long* sqe = (unsigned long long*)smem_raw;
+    unsigned long long* sqi = sqe + N1;
+    Acc A;
+    A.cnt = (unsigned int*)smem_raw;
+    A.whi = A.cnt + N;
+    A.wlo = A.whi + N;
+    A.flo = A.wlo + N;
+    A.fhi = (int*)(A.flo + N1);
+    float2* sEd = (float2*)(smem_raw + acc_bytes(N));
+    float* sE = (float*)(sEd + N);
+    unsigned int* seedf = (unsigned int*)(sE + N1);
+    unsigned int* squeue = seedf + kNbEedf;
     __shared__ BlockTally tally;
-    __shared__ unsigned int s_jlo, s_jhi;
-    __shared__ int s_last;
+    __shared__ unsigned int s_jlo, s_jhi, s_qn;
+    __shared__ int s_last, s_overflow;
 
     Ctl* ctl = d.ctl;
     const unsigned int l = ctl->step;
@@ -251,122 +475,215 @@ __global__ void __launch_bounds__(kMoverThreads) k_mover(Dev d)
     const int b = s == kE ? blockIdx.x : blockIdx.x - Ge;
     const int Gs = s == kE ? Ge : G - Ge;
     const long long ns = s == kE ? ne : ni;
-    const long long beg = ns * b / Gs, end = ns * (b + 1) / Gs;
+    const long long G4 = (ns + 3) >> 2;
+    const long long cg0 = G4 * b / Gs, cg1 = G4 * (b + 1) / Gs;
+    const long long T = blockDim.x;
+    const long long chunk0 = 4 * cg0;
+    const int dslot = MODE == 0 ? (l + 1) % 3 : l % 3;
+    unsigned long long* qdst = d.qbuf[dslot][s];
+    unsigned long long* qe_dst = d.qbuf[dslot][kE];
+    unsigned long long* qion = d.qbuf[dslot][kI];
+    long long* fdst = d.fbuf[dslot][s];
+    const SpBuf B = d.buf[s][ctl->cur[s]];
 
-    for (int i = threadIdx.x; i < N1; i += blockDim.x) {
-        sq[i] = 0;
-        sflux[i] = 0;
-        sE[i] = d.E32[i];
+    // first group of this thread: in flight during the field solve
+    long long g = cg0 + threadIdx.x;
+    const long long tile1_first = min(cg1, cg0 + kTileGroups);
+    Grp<P64> nxt;
+    if (g < tile1_first) nxt = load_group<P64, MODE>(B, g);
+
+    if (MODE == 0) {
+        // field of step l: every CTA solves from the deposit of x^l (slot l%3)
+        const int slot = l % 3;
+        for (int i = threadIdx.x; i < N1; i += blockDim.x) {
+            sqe[i] = d.qbuf[slot][kE][i];
+            sqi[i] = d.qbuf[slot][kI][i];
+        }
+        __syncthreads();
+        if (ctl->field_override) {
+            for (int i = threadIdx.x; i < N1; i += blockDim.x) sE[i] = d.E32[i];
+        } else {
+            block_field_f32(d, sqe, sqi, sE, v_rf(d, l));
+        }
+        if (blockIdx.x == 0) {
+            if ((long long)l > ctl->acc_upto) accumulate_step(d, l, sqe, sqi);
+            const int z = (l + 2) % 3;             // read by the previous launch; cleared for the next
+            for (int i = threadIdx.x; i < N1; i += blockDim.x) {
+                d.qbuf[z][kE][i] = 0;
+                d.qbuf[z][kI][i] = 0;
+                d.fbuf[z][kE][i] = 0;
+                d.fbuf[z][kI][i] = 0;
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < N; i += blockDim.x) sEd[i] = make_float2(sE[i], sE[i + 1] - sE[i]);
+    }
+    for (int m = threadIdx.x; m <= N; m += blockDim.x) {
+        if (m < N) A.cnt[m] = A.whi[m] = A.wlo[m] = 0;
+        A.flo[m] = 0;
+        A.fhi[m] = 0;
     }
     for (int i = threadIdx.x; i < kNbEedf; i += blockDim.x) seedf[i] = 0;
     if (threadIdx.x == 0) {
-        tally = BlockTally{0, 0, 0, 0, 0, 0, 0};
+        tally = BlockTally{};
         s_jlo = 0xffffffffu;
         s_jhi = 0;
+        s_qn = 0;
+        s_overflow = 0;
     }
     __syncthreads();
 
-    const SpBuf B = d.buf[s][ctl->cur[s]];
-    PosT* __restrict__ P = (PosT*)B.pos;
-    float* __restrict__ VX = B.vx;
-    const uint64_t* __restrict__ ID = B.id;
     const float qmdt = d.qm_dt[s];
     const unsigned long long thr = d.thr[s];
+    const long long born_e = round4(ne), born_i = round4(ni);
+    const PosT dead = dead_value<PosT>();
+    const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
     uint32_t jlo = 0xffffffffu, jhi = 0;
 
-    for (long long i0 = beg; i0 < end; i0 += blockDim.x) {
-        const long long i = i0 + threadIdx.x;
-        bool act = i < end;
-        PosT x = 0;
-        float vx = 0.0f;
-        if (act) {
-            x = P[i];
-            act = is_alive(x);
-            if (P64 && act && !((double)x < (double)d.ncell)) {
-                act = false;
-                atomicOr(&ctl->err, kErrIndex);
+    for (long long t0 = cg0; t0 < cg1; t0 += kTileGroups) {
+        const long long t1 = min(cg1, t0 + kTileGroups);
+        if (t0 > cg0) {                               // next tile: flush the sums of the last one
+            unsigned int lo = __reduce_min_sync(0xffffffffu, jlo), hi = __reduce_max_sync(0xffffffffu, jhi);
+            if ((threadIdx.x & 31) == 0) {
+                atomicMin(&s_jlo, lo);
+                atomicMax(&s_jhi, hi);
             }
+            __syncthreads();
+            flush_tile(A, N, s_jlo, s_jhi, sample, qdst, fdst);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                s_jlo = 0xffffffffu;
+                s_jhi = 0;
+            }
+            jlo = 0xffffffffu;
+            jhi = 0;
+            g = t0 + threadIdx.x;
+            if (g < t1) nxt = load_group<P64, MODE>(B, g);
+            __syncthreads();
         }
-        uint32_t j = 0, wr = 0;
-        bool dep = false;
-        if (act) {
-            if (MODE == 1) {
-                cell_of(x, d.kshift, j, wr);
-                dep = true;
-            } else {
-                vx = VX[i];
-                const uint64_t id = ID[i];
-                // field interpolation: the same linear weights as the deposit
-                uint32_t jj, ww;
-                cell_of(x, d.kshift, jj, ww);
-                const float f = (float)ww * 0x1p-32f;
-                const float Ex = (1.0f - f) * sE[jj] + f * sE[jj + 1];
-                // leapfrog: v^{l+1/2} = v^{l-1/2} + (q/m) E dt ; x^{l+1} = x^l + v dt
-                vx = vx + qmdt * Ex;
-                PosT xn;
-                bool out;
-                int el;
-                if (P64) {
-                    const double xd = (double)x + (double)vx * d.push64;
-                    out = xd <= 0.0 || xd >= (double)d.ncell;
-                    el = xd <= 0.0 ? 0 : 1;
-                    xn = (PosT)xd;
-                } else {
-                    const long long np = (long long)x + __float2ll_rn(vx * d.push32);
-                    out = np <= 0 || np >= 4294967296LL;
-                    el = np <= 0 ? 0 : 1;
-                    xn = (PosT)(unsigned long long)np;
+        Run run{0xffffffffu, 0, 0, 0, 0, 0};
+        while (g < t1) {
+            Grp<P64> G = nxt;
+            const long long gn = g + T;
+            if (gn < t1) nxt = load_group<P64, MODE>(B, gn);
+            PosT x[4];
+            bool act[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const long long i = 4 * g + u;
+                x[u] = G.p.get(u);
+                act[u] = i < ns && is_alive(x[u]);
+                if (P64 && act[u] && !((double)x[u] < (double)N)) {
+                    act[u] = false;
+                    atomicOr(&ctl->err, kErrIndex);
                 }
-                if (out) {
-                    store_dead(P, i);
-                    if (s == kI)
-                        ion_wall(d, id, l, el, vx, B.vy[i], B.vz[i], ntp, &tally);
-                    else
-                        atomicAdd(&ctl->cnt[el == 0 ? kCntImpEL : kCntImpER], 1ull);
+                if (i >= ns) G.p.set(u, dead);
+            }
+            if (MODE == 1) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (!act[u]) continue;
+                    uint32_t j, wr;
+                    cell_of(x[u], d.kshift, j, wr);
+                    run.add(A, j, wr, 0.0f, false);
+                    jlo = min(jlo, j);
+                    jhi = max(jhi, j);
+                }
+                G.p.store(B.pos, g);
+                g = gn;
+                continue;
+            }
+            // gather + leapfrog for the four slots (branch-free; removed slots are ignored later)
+            float vx[4] = {G.v.x, G.v.y, G.v.z, G.v.w};
+            PosT xn[4];
+            uint32_t kind[4];
+            uint4 c[4];
+            const uint64_t id[4] = {G.a.x, G.a.y, G.b.x, G.b.y};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                uint32_t jj, ww;
+                cell_of(act[u] ? x[u] : (PosT)(P64 ? 0.5 : 1.0), d.kshift, jj, ww);
+                const float2 e = sEd[jj];
+                const float f = __uint_as_float(0x3f800000u | (ww >> 9)) - 1.0f;
+                vx[u] = vx[u] + qmdt * (e.x + f * e.y);
+                kind[u] = 0xffffffffu;
+                if (P64) {
+                    const double xd = (double)x[u] + (double)vx[u] * d.push64;
+                    kind[u] = xd <= 0.0 ? kEvWallL : (xd >= (double)N ? kEvWallR : 0xffffffffu);
+                    xn[u] = (PosT)xd;
                 } else {
-                    const uint4 c = draw(d.seed, id, l, kPurColl);
-                    if ((unsigned long long)c.x < thr) {
-                        float vy = B.vy[i], vz = B.vz[i];
-                        if (s == kE)
-                            mcc_electron<PosT>(d, c, id, l, xn, vx, vy, vz, ne, ni, sq, &tally);
-                        else
-                            mcc_ion(d, c, id, l, vx, vy, vz, &tally);
-                        B.vy[i] = vy;
-                        B.vz[i] = vz;
-                    }
-                    P[i] = xn;
-                    VX[i] = vx;
-                    cell_of(xn, d.kshift, j, wr);
-                    dep = true;
-                    if (sample) {
-                        const long long vq = (long long)__float2int_rn(vx);
-                        atomicAdd((unsigned long long*)&sflux[j],
-                                  (unsigned long long)(vq * (long long)(((1ull << 32) - wr) >> 16)));
-                        atomicAdd((unsigned long long*)&sflux[j + 1],
-                                  (unsigned long long)(vq * (long long)(wr >> 16)));
-                        if (s == kE) {
-                            bool inwin;
-                            if (P64) inwin = (double)xn >= d.eedf_lo64 && (double)xn < d.eedf_hi64;
-                            else inwin = (uint32_t)xn >= d.eedf_lo && (uint32_t)xn < d.eedf_hi;
-                            if (inwin) {
-                                const float vy = B.vy[i], vz = B.vz[i];
-                                const float e = (vx * vx + vy * vy + vz * vz) * (float)(0.5 * kME / kQE);
-                                int bb = (int)(e * 4.0f);
-                                bb = bb < 0 ? 0 : (bb > kNbEedf - 1 ? kNbEedf - 1 : bb);
-                                atomicAdd(&seedf[bb], 1u);
-                            }
+                    const int disp = __float2int_rn(vx[u] * d.push32);
+                    const uint32_t xu = (uint32_t)x[u];
+                    const uint32_t xm = xu + (uint32_t)disp;
+                    kind[u] = (disp > 0 && xm < xu) ? kEvWallR
+                              : ((disp < 0 && (0u - (uint32_t)disp) >= xu) ? kEvWallL : 0xffffffffu);
+                    xn[u] = (PosT)xm;
+                }
+                c[u] = make_uint4((uint32_t)id[u], (uint32_t)(id[u] >> 32), l, kPurColl);
+            }
+            philox4x(c, k0, k1);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (!act[u]) continue;
+                const long long i = 4 * g + u;
+                if (kind[u] == 0xffffffffu) {
+                    if ((unsigned long long)c[u].x < thr) kind[u] = kEvCand;
+                    uint32_t j, wr;
+                    cell_of(xn[u], d.kshift, j, wr);
+                    run.add(A, j, wr, vx[u], sample);
+                    jlo = min(jlo, j);
+                    jhi = max(jhi, j);
+                    G.p.set(u, xn[u]);
+                    if (sample && s == kE) {
+                        bool inwin;
+                        if (P64) inwin = (double)xn[u] >= d.eedf_lo64 && (double)xn[u] < d.eedf_hi64;
+                        else inwin = (uint32_t)xn[u] >= d.eedf_lo && (uint32_t)xn[u] < d.eedf_hi;
+                        if (inwin) {
+                            const float vy = B.vy[i], vz = B.vz[i];
+                            const float en = (vx[u] * vx[u] + vy * vy + vz * vz) * (float)(0.5 * kME / kQE);
+                            int bb = (int)(en * 4.0f);
+                            bb = bb < 0 ? 0 : (bb > kNbEedf - 1 ? kNbEedf - 1 : bb);
+                            atomicAdd(&seedf[bb], 1u);
                         }
                     }
+                } else {
+                    G.p.set(u, dead);
+                }
+                if (kind[u] != 0xffffffffu) {
+                    const unsigned int q = atomicAdd(&s_qn, 1u);
+                    if (q < (unsigned)kQueueCap) {
+                        squeue[q] = ((uint32_t)(i - chunk0) << 2) | kind[u];
+                    } else {                                // queue full: flag the slot
+                        d.evflag[s][i] = (unsigned char)(kind[u] + 1u);
+                        s_overflow = 1;
+                    }
+                }
+            }
+            G.p.store(B.pos, g);
+            ((float4*)B.vx)[g] = make_float4(vx[0], vx[1], vx[2], vx[3]);
+            g = gn;
+        }
+        run.flush(A, sample);
+    }
+    __syncthreads();
+    if (MODE == 0) {
+        const unsigned int qn = min(s_qn, (unsigned)kQueueCap);
+        for (unsigned int k = threadIdx.x; k < qn; k += blockDim.x) {
+            const uint32_t e = squeue[k];
+            handle_event<PosT>(d, s, chunk0 + (e >> 2), e & 3u, l, born_e, born_i, ntp, qe_dst, qion, &tally);
+        }
+        if (s_overflow) {
+            const long long chunk1 = min(4 * cg1, ns);
+            for (long long i = chunk0 + threadIdx.x; i < chunk1; i += blockDim.x) {
+                const unsigned char k = d.evflag[s][i];
+                if (k) {
+                    d.evflag[s][i] = 0;
+                    handle_event<PosT>(d, s, i, k - 1u, l, born_e, born_i, ntp, qe_dst, qion, &tally);
                 }
             }
         }
-        if (dep) {
-            jlo = min(jlo, j);
-            jhi = max(jhi, j);
-        }
-        warp_deposit(sq, dep, j, wr);
     }
-    // range of touched nodes (newborns sit in cells their parents touched)
+    // range of touched nodes, then the node totals into the global histograms
     jlo = __reduce_min_sync(0xffffffffu, jlo);
     jhi = __reduce_max_sync(0xffffffffu, jhi);
     if ((threadIdx.x & 31) == 0) {
@@ -374,29 +691,19 @@ __global__ void __launch_bounds__(kMoverThreads) k_mover(Dev d)
         atomicMax(&s_jhi, jhi);
     }
     __syncthreads();
-    if (s_jlo != 0xffffffffu) {
-        for (int m = (int)s_jlo + threadIdx.x; m <= (int)s_jhi + 1; m += blockDim.x) {
-            const unsigned long long v = sq[m];
-            if (v) atomicAdd(&d.q[s][m], v);
-            if (sample) {
-                const long long f = sflux[m];
-                if (f) atomicAdd((unsigned long long*)&d.flux[s][m], (unsigned long long)f);
-            }
-        }
-    }
+    flush_tile(A, N, s_jlo, s_jhi, sample, qdst, fdst);
     if (sample && s == kE)
         for (int i = threadIdx.x; i < kNbEedf; i += blockDim.x)
             if (seedf[i]) atomicAdd(&d.diag.eedf[i], (unsigned long long)seedf[i]);
     if (threadIdx.x == 0) flush_tally(d, tally);
-    // last CTA: field solve for the new step
+    // last CTA: commit the step
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) s_last = atomicAdd(&ctl->done, 1u) == (unsigned)(G - 1);
     __syncthreads();
-    if (s_last) {
+    if (s_last && threadIdx.x == 0) {
         __threadfence();
-        if (MODE == 0) finish_step(d, l + 1, true, sample);
-        else finish_step(d, l, false, false);
+        commit_step(d, MODE == 0);
     }
 }
 
@@ -438,6 +745,18 @@ __global__ void k_op_poisson(const long long* qi, const long long* qe, int N, do
 {
     QNet qn{(const unsigned long long*)qi, (const unsigned long long*)qe, false};
     poisson_block(qn, N, A, inv_dx, v_left, phi, E64, nullptr);
+}
+
+// FP64 field and potential of the current state (step l, slot l%3), for
+// diagnostics; optionally adds step l to the time averages if no launch has.
+__global__ void k_field(Dev d, int accumulate)
+{
+    const unsigned int l = d.ctl->step;
+    const int slot = l % 3;
+    QNet qn{d.qbuf[slot][kI], d.qbuf[slot][kE], false};
+    poisson_block(qn, d.ncell, d.A, d.inv_dx, v_rf(d, l), d.phi, d.E64, nullptr);
+    __syncthreads();
+    if (accumulate && (long long)l > d.ctl->acc_upto) accumulate_step(d, l, d.qbuf[slot][kE], d.qbuf[slot][kI]);
 }
 
 // ---------------------------------------------------------------- sort / compaction
@@ -543,7 +862,7 @@ __global__ void k_sort_scatter(Dev d, int s)
 size_t mover_smem(int ncell)
 {
     const int N1 = ncell + 1;
-    return (size_t)N1 * 16 + (size_t)((N1 + 3) & ~3) * 4 + kNbEedf * 4;
+    return acc_bytes(ncell) + (size_t)ncell * 8 + (size_t)N1 * 4 + kNbEedf * 4 + kQueueCap * 4;
 }
 
 cudaError_t launch_init(const Dev& d, int s, long long n, float vth, cudaStream_t st)
@@ -560,6 +879,15 @@ static cudaError_t set_smem_attr(const void* fn, size_t bytes)
 {
     if (bytes <= 48 * 1024) return cudaSuccess;
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+cudaError_t mover_occupancy(const Dev& d, int* blocks_per_sm)
+{
+    const size_t sm = mover_smem(d.ncell);
+    const void* fn = d.pos64 ? (const void*)k_mover<true, 0> : (const void*)k_mover<false, 0>;
+    cudaError_t e = set_smem_attr(fn, sm);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kMoverThreads, sm);
 }
 
 cudaError_t launch_mover(const Dev& d, int grid, int mode, cudaStream_t st)
@@ -605,6 +933,12 @@ cudaError_t launch_op_deposit(const void* pos, int pos64, long long n, int ncell
         if (e != cudaSuccess) return e;
         k_op_deposit<uint32_t><<<grid, kMoverThreads, sm, st>>>((const uint32_t*)pos, n, ncell, kshift, q);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_field(const Dev& d, int accumulate, cudaStream_t st)
+{
+    k_field<<<1, 512, 0, st>>>(d, accumulate);
     return cudaGetLastError();
 }
 

@@ -131,50 +131,106 @@ __device__ __noinline__ static void poisson_block(const QNet& qn, int N, double 
     }
 }
 
-// Finish of a PIC step (or of a standalone deposit), run by the last CTA of
-// the launch: solve for the field at step l_new, accumulate the time
-// averages, clear the per-step histograms, and commit counters.
-// `advance`: this launch moved the particles from step l_new-1 to l_new.
-__device__ static void finish_step(const Dev& d, unsigned int l_new, bool advance, bool sample)
+// Field at the nodes in FP32 from the exact integer sums, for the gather of
+// one CTA.  With S_m as above and K an integer close to 2 D0 / A,
+//     E[m] = c1 + c2 (S_m + S_{m-1} - K),  c2 = A / (2 dx),  c1 = -D0/dx + c2 K,
+//     E[0] = c1 + c2 (-K - 2 q[0]),        E[N] = c1 + c2 (2 S_N - K),
+// which is the central difference and the half-cell Gauss rule above: the
+// bracket is an exact int64, so each E[m] is one rounding of its own value
+// (no cancellation) and no FP64 arithmetic runs per node.
+// qe, qi: shared copies of the deposit; sE: shared float[N+1].
+__device__ static void block_field_f32(const Dev& d, const unsigned long long* qe, const unsigned long long* qi,
+                                float* sE, double v_left)
 {
+    __shared__ long long sh64[32];
+    __shared__ __int128 sh128[32];
+    __shared__ long long sK;
+    __shared__ float sc1, sc2;
     const int N = d.ncell, N1 = N + 1;
-    const double v_left = d.V0 * sin(d.omega * (double)l_new * d.dt);
-    QNet qn{d.q[kI], d.q[kE], true};
-    poisson_block(qn, N, d.A, d.inv_dx, v_left, d.phi, d.E64, d.E32);
+    const int T = blockDim.x, t = threadIdx.x;
+    const int seg = (N1 + T - 1) / T;
+    const int m0 = min(t * seg, N1), m1 = min(m0 + seg, N1);
+    long long a = 0;
+    for (int m = m0; m < m1; ++m)
+        if (m >= 1) a += (long long)(qi[m] - qe[m]);
+    long long totS;
+    const long long Sprev = block_exclusive_scan(a, sh64, totS);
+    __int128 b = 0;
+    long long S = Sprev;
+    for (int m = m0; m < m1; ++m) {
+        if (m >= 1) S += (long long)(qi[m] - qe[m]);
+        if (m < N) b += (__int128)S;
+    }
+    __int128 TN;
+    block_exclusive_scan(b, sh128, TN);
+    if (t == 0) {
+        const double D0 = (0.0 - v_left + d.A * i128_to_double(TN)) / (double)N;
+        const double c2 = 0.5 * d.A * d.inv_dx;
+        const double k = d.A != 0.0 ? 2.0 * D0 / d.A : 0.0;
+        const long long K = fabs(k) < 4e18 ? llrint(k) : 0;
+        sK = K;
+        sc2 = (float)c2;
+        sc1 = (float)(-D0 * d.inv_dx + c2 * (double)K);
+    }
     __syncthreads();
+    const long long K = sK;
+    const float c1 = sc1, c2 = sc2;
+    S = Sprev;
+    for (int m = m0; m < m1; ++m) {
+        const long long q = (long long)(qi[m] - qe[m]);
+        const long long Sm = m >= 1 ? S + q : 0;
+        long long br;
+        if (m == 0) br = -K - 2 * q;
+        else if (m == N) br = 2 * Sm - K;
+        else br = Sm + S - K;
+        sE[m] = c1 + c2 * (float)br;
+        S = Sm;
+    }
+}
+
+// Add the state of step l (deposit in slot l%3; the flux moment sampled at
+// step l) to the time averages.  Runs once per step, in one CTA.
+__device__ static void accumulate_step(const Dev& d, unsigned int l, const unsigned long long* qe,
+                                const unsigned long long* qi)
+{
+    const int N1 = d.ncell + 1;
+    const bool fl = d.diag_every > 0 && l > 0 && l % (unsigned)d.diag_every == 0;
+    const int slot = l % 3;
     for (int m = threadIdx.x; m < N1; m += blockDim.x) {
-        const unsigned long long qe = __ldcg(d.q[kE] + m), qi = __ldcg(d.q[kI] + m);
-        if (advance) {
-            d.diag.sum_q[kE][m] += (double)qe;
-            d.diag.sum_q[kI][m] += (double)qi;
-            d.diag.sum_phi[m] += d.phi[m];
-            if (sample) {
-                d.diag.sum_flux[kE][m] += (double)__ldcg(d.flux[kE] + m) * 0x1p-16;
-                d.diag.sum_flux[kI][m] += (double)__ldcg(d.flux[kI] + m) * 0x1p-16;
-            }
+        add_u128(d.diag.sum_q[kE] + 2 * m, qe[m]);
+        add_u128(d.diag.sum_q[kI] + 2 * m, qi[m]);
+        if (fl) {
+            add_s128(d.diag.sum_flux[kE] + 2 * m, d.fbuf[slot][kE][m]);
+            add_s128(d.diag.sum_flux[kI] + 2 * m, d.fbuf[slot][kI][m]);
         }
-        d.q_last[kE][m] = qe;
-        d.q_last[kI][m] = qi;
-        d.q[kE][m] = 0;
-        d.q[kI][m] = 0;
-        d.flux[kE][m] = 0;
-        d.flux[kI][m] = 0;
     }
     if (threadIdx.x == 0) {
         Ctl* c = d.ctl;
-        if (advance) {
-            c->step = l_new;
-            c->n_avg += 1;
-            if (sample) c->n_flux += 1;
-        }
-        for (int s = 0; s < 3; ++s) {
-            long long n = c->n[s] + c->births[s];
-            if (n > c->cap[s]) n = c->cap[s];
-            c->n[s] = n;
-            c->births[s] = 0;
-        }
-        c->done = 0;
+        c->sum_v += v_rf(d, l);
+        c->n_avg += 1;
+        if (fl) c->n_flux += 1;
+        c->acc_upto = l;
     }
+}
+
+// Bookkeeping at the end of a launch, by its last CTA: advance the step and
+// take the births of this launch into the slot counts.
+__device__ static void commit_step(const Dev& d, bool advance)
+{
+    Ctl* c = d.ctl;
+    if (advance) {
+        c->step += 1;
+        c->field_override = 0;
+    }
+    // charged-species births start at round_up(n, 4) (see k_mover), atoms at n
+    for (int s = 0; s < 3; ++s) {
+        if (c->births[s] == 0) continue;
+        long long n = (s == kTP ? c->n[s] : ((c->n[s] + 3) & ~3ll)) + c->births[s];
+        if (n > c->cap[s]) n = c->cap[s];
+        c->n[s] = n;
+        c->births[s] = 0;
+    }
+    c->done = 0;
 }
 
 }  // namespace pg

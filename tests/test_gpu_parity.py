@@ -36,6 +36,11 @@ def _cuda():
     yield
 
 
+def _worst(err, ids, k=5):
+    i = np.argsort(err)[::-1][:k]
+    return [(int(ids[j]), float(err[j])) for j in i]
+
+
 def _torch_pos(pos):
     import torch
     if pos.dtype == np.uint32:
@@ -108,8 +113,11 @@ def test_deposit_edge_sizes():
 # ------------------------------------------------------------------ field solve
 @pytest.mark.parametrize("ncell", [4, 128, 1024, 2048, 4096])
 def test_poisson_matches_oracle(ncell):
-    """Exact double-prefix-sum solve on the GPU vs the oracle's Thomas sweep:
-    within 1e-12 of max |phi| (E within 1e-10 of max |E|)."""
+    """Exact double-prefix-sum solve on the GPU vs the oracle's Thomas sweep.
+    Tolerance: the oracle's own forward error, which grows with the condition
+    number of the 1D Laplacian (~ N^2): max(1e-12, N^2 eps / 100) of max
+    |phi| (pinned against exact rationals in test_oracle_pins)."""
+    tol = max(1e-12, ncell**2 * 2.2e-16 / 100)
     import paper_1607_04069_gb300 as P
     import torch
     rng = np.random.default_rng(ncell)
@@ -122,8 +130,8 @@ def test_poisson_matches_oracle(ncell):
                               dx, w, v_left)
         phi, E = phi.cpu().numpy(), E.cpu().numpy()
         phi_o, E_o = O.poisson(ncell, dx, w, q_i, q_e, v_left)
-        assert np.abs(phi - phi_o).max() <= 1e-12 * np.abs(phi_o).max()
-        assert np.abs(E - E_o).max() <= 1e-10 * np.abs(E_o).max()
+        assert np.abs(phi - phi_o).max() <= tol * np.abs(phi_o).max()
+        assert np.abs(E - E_o).max() <= 100 * tol * np.abs(E_o).max()
 
 
 # ------------------------------------------------------------------ one-step push
@@ -170,12 +178,16 @@ def test_one_step_push_parity(prec):
         x0 = dict(zip(sets[s]["id"].tolist(), sets[s]["xi"].tolist()))
         assert len(only_g) == 0 and len(only_o) == 0, (len(only_g), len(only_o))
         xi0 = np.array([x0[i] for i in o["id"].tolist()])
-        disp_o = o["xi"] - xi0
-        tol = 1e-5 * np.abs(disp_o) + (2 * unit if prec == 32 else 1e-9)
-        assert (np.abs(g["xi"] - o["xi"]) <= tol).all()
         v0 = dict(zip(sets[s]["id"].tolist(), sets[s]["vx"].tolist()))
         vx0 = np.array([v0[i] for i in o["id"].tolist()])
-        assert (np.abs(g["vx"] - o["vx"]) <= 1e-5 * (np.abs(vx0) + np.abs(o["vx"] - vx0)) + 1e-3).all()
+        # velocity error scale: |v_old| + |dv| (v^{l+1/2} may cancel to ~0)
+        vscale = np.abs(vx0) + np.abs(o["vx"] - vx0)
+        dvx = np.abs(g["vx"] - o["vx"])
+        assert (dvx <= 1e-5 * vscale + 1e-3).all(), _worst(dvx / (vscale + 1e-30), o["id"])
+        # displacement error: 1e-5 of the same scale times dt/dx, plus the position resolution
+        tol = 1e-5 * vscale * dt / (cfg["gap_m"] / ncell) + (2 * unit if prec == 32 else 1e-9)
+        dxi = np.abs(g["xi"] - o["xi"])
+        assert (dxi <= tol).all(), _worst(dxi / tol, o["id"])
         vy0 = dict(zip(sets[s]["id"].tolist(), sets[s]["vy"].tolist()))
         assert np.array_equal(g["vy"], np.array([vy0[i] for i in g["id"].tolist()], dtype=np.float32))
     f, fo = d.get_field(), orc.get_field()
@@ -217,12 +229,27 @@ def test_one_step_collision_parity(case):
     for k in keys:
         assert c[k] == oc[k], (k, c[k], oc[k])
     assert sum(c[k] for k in keys) > 500
-    for s in (0, 1):
+    for s, mass in ((0, ME), (1, MAR)):
         g, o, only_g, only_o = match(d.get_species(s), orc.get_species(s))
         assert len(only_g) == 0 and len(only_o) == 0
-        vmag = np.sqrt(o["vx"]**2 + o["vy"]**2 + o["vz"]**2)
-        for comp in ("vx", "vy", "vz"):
-            assert (np.abs(g[comp] - o[comp]) <= 2e-5 * vmag + 1e-2).all(), comp
+        # energies: FP32 rounding of the pre-collision energy (eps - threshold
+        # cancels near a threshold, so compare energies, not speeds)
+        e0 = {int(i): 0.5 * mass * (a * a + b * b + c * c) / QE for i, a, b, c in
+              zip(sets[s]["id"], sets[s]["vx"].astype(np.float64), sets[s]["vy"].astype(np.float64),
+                  sets[s]["vz"].astype(np.float64))}
+        e_ref = max(e0.values()) if e0 else 1.0
+        E0 = np.array([e0.get(int(i), e_ref) for i in o["id"]])
+        Eg = 0.5 * mass * (g["vx"].astype(np.float64)**2 + g["vy"]**2.0 + g["vz"]**2.0) / QE
+        Eo = 0.5 * mass * (o["vx"]**2 + o["vy"]**2 + o["vz"]**2) / QE
+        dE = np.abs(Eg - Eo)
+        assert (dE <= 2e-6 * (E0 + Eo + 16.0)).all(), _worst(dE / (E0 + Eo + 16.0), o["id"])
+        # directions
+        vg = np.stack([g["vx"], g["vy"], g["vz"]]).astype(np.float64)
+        vo = np.stack([o["vx"], o["vy"], o["vz"]])
+        ng, no = np.linalg.norm(vg, axis=0), np.linalg.norm(vo, axis=0)
+        ok = no > 0
+        ddir = np.linalg.norm(vg[:, ok] / ng[ok] - vo[:, ok] / no[ok], axis=0)
+        assert (ddir <= 1e-5).all(), _worst(ddir, o["id"][ok])
     d.close()
 
 
@@ -317,3 +344,123 @@ def test_bitwise_independent_of_order_and_sort_period():
         assert np.array_equal(a.diag(k), b.diag(k)), k
     a.close()
     b.close()
+
+
+# ------------------------------------------------------------------ full size, bench launch shape
+def test_full_size_step_matches_oracle():
+    """The sputtering discharge at its full size (2M e- + 2M Ar+, 1024 cells)
+    in the benchmark's launch configuration: after one step every particle
+    matches the oracle's within the one-step tolerances, charge is conserved
+    exactly, and the new field agrees to 1e-5 of max |E|."""
+    cfg = W.ccp_sputter()
+    cfg.update(sort_every_e=25, sort_every_i=200, sort_every_tp=50)
+    n = cfg["n_e0"]
+    d = gpu_discharge(cfg)
+    orc = oracle_for(cfg, cap=n + n // 4 + 65536)
+    orc.init_species(0, n, cfg["te0_ev"])
+    orc.init_species(1, n, cfg["ti0_ev"])
+    orc.field()
+    f0, fo0 = d.get_field(), orc.get_field()
+    assert np.array_equal(f0["q_e"], fo0["q_e"]) and np.array_equal(f0["q_i"], fo0["q_i"])
+    d.step(1)
+    d.sync()
+    orc.step(1)
+    for s, mass in ((0, ME), (1, MAR)):
+        g, o, only_g, only_o = match(d.get_species(s), orc.get_species(s))
+        assert len(only_g) == 0 and len(only_o) == 0
+        vmag = np.sqrt(o["vx"]**2 + o["vy"]**2 + o["vz"]**2)
+        for comp in ("vx", "vy", "vz"):
+            assert (np.abs(g[comp] - o[comp]) <= 2e-5 * vmag + 1e-2).all(), comp
+        unit = cfg["n_cells"] / 2.0**32
+        disp_tol = 2e-5 * vmag * cfg["dt"] / (cfg["gap_m"] / cfg["n_cells"]) + 2 * unit
+        assert (np.abs(g["xi"] - o["xi"]) <= disp_tol).all()
+    f, fo = d.get_field(), orc.get_field()
+    alive = [len(d.get_species(s)["id"]) for s in (0, 1)]
+    assert int(f["q_e"].sum()) == 2**32 * alive[0] and int(f["q_i"].sum()) == 2**32 * alive[1]
+    assert np.abs(f["E"] - fo["E"]).max() <= 1e-5 * np.abs(fo["E"]).max()
+    d.close()
+
+
+# ------------------------------------------------------------------ statistics at steady operation
+def _ks_hist(x, y):
+    from scipy.stats import kstwobign
+    n1, n2 = x.sum(), y.sum()
+    D = np.abs(np.cumsum(x) / n1 - np.cumsum(y) / n2).max()
+    return float(kstwobign.sf(D * math.sqrt(n1 * n2 / (n1 + n2)))), int(n1), int(n2)
+
+
+def test_time_averaged_profiles_and_iedf_match_oracle():
+    """The 25 mm / 128-cell / 100 V / 3 Pa discharge with 20k + 20k
+    superparticles and 64-bit positions, 20 RF periods: potential and
+    densities averaged over periods 10-20 within 3% relative L2 of the
+    oracle's (same seed); ion energy distributions at both electrodes pass a
+    two-sample KS test at p > 0.01."""
+    cfg = W.ccp_small()
+    n = cfg["n_e0"]
+    d = gpu_discharge(cfg)
+    orc = oracle_for(cfg, cap=3 * n)
+    orc.init_species(0, n, cfg["te0_ev"])
+    orc.init_species(1, n, cfg["ti0_ev"])
+    orc.field()
+    half = 400 * 10
+    d.step(half)
+    orc.step(half)
+    d.sync()
+    d.reset_averages()
+    orc.reset_averages()
+    d.step(half)
+    d.sync()
+    orc.step(half)
+    from helpers import rel_l2
+    for k in ("phi", "n_e", "n_i"):
+        assert rel_l2(d.diag(k), orc.diag(k)) < 0.03, k
+    for k in ("iedf_l", "iedf_r"):
+        p, n1, n2 = _ks_hist(d.diag(k), orc.diag(k))
+        assert n1 > 300 and n2 > 300 and p > 0.01, (k, p, n1, n2)
+    d.close()
+
+
+def test_tp_far_electrode_energy_distribution():
+    """Atoms from a 300 eV mono-energetic source crossing the 50 mm gap
+    (4 ns steps, run to deposition within 3000 steps): the energy
+    distribution of the atoms deposited on the far electrode passes a
+    two-sample KS test against the oracle's at p > 0.01."""
+    cfg = W.tp_transport(n_atoms=20_000)
+    cfg.update(cap_tp=20_000, n_e0=0, n_i0=0, tp_dt=4e-9, sort_every_tp=100)
+    d = gpu_discharge(cfg)
+    orc = oracle_for(cfg, cap=10, cap_tp=20_000)
+    d.tp_launch(20_000, 300.0)
+    orc.tp_launch(20_000, 300.0)
+    d.tp_step(3000, count_alive=False)
+    orc.tp_step(3000, 4e-9)
+    p, n1, n2 = _ks_hist(d.diag("sputter_e_r"), orc.diag("sputter_e_r"))
+    assert n1 > 1000 and p > 0.01, (p, n1, n2)
+    tpd, tpo = d.diag("tp_dens"), orc.diag("tp_dens")
+    from helpers import rel_l2
+    assert rel_l2(tpd, tpo) < 0.03
+    d.close()
+
+
+# ------------------------------------------------------------------ error paths
+def test_capacity_overflow_is_reported_and_state_stays_consistent():
+    """Ionisations beyond the slot capacity are dropped as pairs and reported
+    by pic_sync as a capacity error; the charge bookkeeping stays exact."""
+    import paper_1607_04069_gb300 as P
+    ncell = 64
+    cfg = W.ccp_small(n_per_species=1000)
+    cfg.update(n_cells=ncell, pressure_pa=30.0, gap_m=1.0, dt=1e-8, n_e0=0, n_i0=0,
+               cap_e=20_010, cap_i=20_010, sort_every_e=0, sort_every_i=0)
+    d = gpu_discharge(cfg)
+    st = W.random_particles(20_000, ncell, 0, math.sqrt(60 * QE / ME), 8, 64)
+    d.set_species(0, st["pos"], st["vx"], st["vy"], st["vz"], st["id"])
+    d.set_field(np.zeros(ncell + 1))
+    d.step(1)
+    with pytest.raises(P.PicError) as e:
+        d.sync()
+    assert e.value.code == -4
+    f = d.get_field()
+    ne, ni = len(d.get_species(0)["id"]), len(d.get_species(1)["id"])
+    assert int(f["q_e"].sum()) == 2**32 * ne and int(f["q_i"].sum()) == 2**32 * ni
+    assert ne - ni == 20_000 - d.counters()["imp_e_l"] - d.counters()["imp_e_r"] + d.counters()["imp_i_l"] + d.counters()["imp_i_r"]
+    d.sync()                   # the error is reported once
+    d.close()
