@@ -227,7 +227,11 @@ def main():
     d.step(args.warmup)
     d.sync()
     n_start = sum(len(d.get_species(s)["id"]) for s in (0, 1))
-    flush = torch.empty(512 * 2**20, dtype=torch.uint8, device="cuda")      # > 129 MB L2
+    # L2 flush between timed steps: write 512 MiB (> 129 MB L2), then read a
+    # separate 256 MiB buffer so the flush's dirty lines are written back
+    # before the step starts (the L2 then holds neither the state nor dirty data)
+    flush = torch.empty(512 * 2**20, dtype=torch.uint8, device="cuda")
+    clean = torch.ones(64 * 2**20, dtype=torch.int32, device="cuda")
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     d.timing(True)
@@ -237,6 +241,7 @@ def main():
         t0 = time.perf_counter()
         for k in range(args.steps):
             flush.zero_()
+            clean.max()
             starts[k].record(stream)
             d.step(1)
             ends[k].record(stream)
@@ -319,8 +324,8 @@ def main():
                 "config": {"workload": cfg["name"], "particles_per_gpu": int(n_start),
                            "n_cells": cfg["n_cells"], "sort_every": [25, 200], "tp_every": 40,
                            "parallelism": f"replicas x{ws}" if ws > 1 else "1 gpu",
-                           "l2": "flushed before every timed step (512 MiB write); value from "
-                                 "per-step CUDA events",
+                           "l2": "flushed before every timed step (512 MiB write, then a 256 MiB "
+                                 "read); value from per-step CUDA events",
                            "wall_s_incl_flush": wall},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": int(launches),

@@ -178,6 +178,18 @@ int pic_compact(pic_ctx* ctx, int species);
 int pic_timing(pic_ctx* ctx, int enable);
 int pic_kernel_time(pic_ctx* ctx, int kind, double* ms, int64_t* launches);
 
+/* Phase trace of the per-step launch (tracing aid): pic_trace(ctx, 1)
+ * allocates a device buffer into which every CTA of each subsequent step
+ * launch writes 12 words -- globaltimer stamps (ns) at start, after loading
+ * the deposit, after the field solve, at the end of the prologue, after the
+ * particle stream, after the queued events, after the histogram flush and at
+ * exit, then its species and its event count, then stamps after the launch
+ * set-up and after issuing the deposit copies.  pic_trace_read copies the
+ * words of the last launch (grid x 12) to host memory; *n_written =
+ * grid x 12.  pic_trace(ctx, 0) frees the buffer. */
+int pic_trace(pic_ctx* ctx, int enable);
+int pic_trace_read(pic_ctx* ctx, uint64_t* host_out, int64_t cap, int64_t* n_written);
+
 /* Derived quantities of the discharge, host double[8]: n_gas, dx,
  * nu_max_e, nu_max_i, P_max_e, P_max_i, eps_max, Lambda. */
 int pic_derived(pic_ctx* ctx, double* host_out8);

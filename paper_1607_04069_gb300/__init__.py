@@ -81,6 +81,8 @@ def lib():
             "pic_timing": [vp, C.c_int],
             "pic_kernel_time": [vp, C.c_int, C.POINTER(dbl), pi64],
             "pic_derived": [vp, vp],
+            "pic_trace": [vp, C.c_int],
+            "pic_trace_read": [vp, vp, i64, pi64],
             "pic_op_deposit": [vp, C.c_int, i64, i32, vp, vp],
             "pic_op_poisson": [vp, vp, i32, dbl, dbl, dbl, vp, vp, vp],
         }
@@ -228,6 +230,17 @@ class Discharge:
         ms, n = C.c_double(), C.c_int64()
         _check(lib().pic_kernel_time(self.h, KERNEL.get(kind, kind), C.byref(ms), C.byref(n)))
         return ms.value, n.value
+
+    def trace(self, enable=True):
+        _check(lib().pic_trace(self.h, int(bool(enable))))
+
+    def trace_read(self) -> np.ndarray:
+        """Per-CTA phase stamps of the last step launch, shape (grid, 12)."""
+        n = C.c_int64()
+        _check(lib().pic_trace_read(self.h, None, 0, C.byref(n)))
+        out = np.zeros(n.value, dtype=np.uint64)
+        _check(lib().pic_trace_read(self.h, _ptr(out), out.size, C.byref(n)))
+        return out.reshape(-1, 12)
 
     def derived(self) -> dict:
         out = np.zeros(8)

@@ -57,6 +57,8 @@ struct pic_ctx {
     size_t arena_bytes = 0, small_bytes = 0;
     int sms = 0, grid_mover = 0, grid_tp = 0, grid_sort = 0;
     long long h_step = 0, h_tp_step = 0, tp_launched = 0;
+    long long acc_upto = 0;          // last step whose state entered the time averages
+    unsigned int cur[3] = {0, 0, 0}; // active ping-pong halves (each compaction flips one)
     double derived[8];
     bool timing = false;
     Timer timers[3];
@@ -184,6 +186,7 @@ void derive(pic_ctx* c)
     d.dx = dx;
     d.inv_dx = 1.0 / dx;
     d.A = dx * kQE * p.weight / (4294967296.0 * kEPS0);
+    d.c2f = (float)(0.5 * d.A / dx);
     d.V0 = p.rf_volt_v;
     d.omega = 2.0 * kPI * p.rf_freq_hz;
     d.f_rf = p.rf_freq_hz;
@@ -221,6 +224,36 @@ void sync_desc(pic_ctx* c)          // keep the coupled descriptor's pointers in
     c->d_coupled = c->d;
     c->d_coupled.tp_scale = keep.tp_scale;
     c->d_coupled.tp_nsig_dt = keep.tp_nsig_dt;
+}
+
+// electrode voltage at step l (V0 sin(2 pi f t_l), t_l = l dt)
+double v_left_at(const pic_ctx* c, long long l)
+{
+    return c->p.rf_volt_v * std::sin(2.0 * kPI * c->p.rf_freq_hz * (double)l * c->p.dt);
+}
+
+StepArgs step_args(const pic_ctx* c, long long l, int accumulate)
+{
+    StepArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.v_left = v_left_at(c, l);
+    a.accumulate = accumulate;
+    a.step = (unsigned int)l;
+    for (int s = 0; s < 3; ++s) a.cur[s] = c->cur[s];
+    if (c->d.A == 0.0) {
+        a.field_mode = kFieldUniform;
+        a.e_uniform = (float)(a.v_left / c->p.gap_m);
+    } else {
+        const double va = 2.0 * a.v_left / c->d.A;
+        if (std::fabs(va) < 4.0e18) {
+            a.field_mode = kFieldInt;
+            a.va_i = std::llrint(va);
+            a.va_f = (float)(va - (double)a.va_i);
+        } else {
+            a.field_mode = kFieldF64;
+        }
+    }
+    return a;
 }
 
 int timer_begin(pic_ctx* c, int k, cudaEvent_t* stop)
@@ -275,6 +308,7 @@ int run_tp_step(pic_ctx* c, const Dev& d)
         rc = timer_begin(c, 2, &stop);
         if (rc) return rc;
         CK(launch_sort(c->d, kTP, c->grid_sort, c->stream));
+        c->cur[kTP] ^= 1u;
         rc = timer_end(c, stop);
     }
     return rc;
@@ -359,6 +393,7 @@ int pic_create(const pic_params* pin, void* stream, pic_ctx** out)
         return fail(PIC_ERR_CUDA, "cudaGetDeviceProperties");
     }
     c->sms = prop.multiProcessorCount;
+    c->d.trace = nullptr;
     int per_sm = c->p.ctas_per_sm;
     if (per_sm <= 0) {
         e = mover_occupancy(c->d, &per_sm);
@@ -381,7 +416,7 @@ int pic_create(const pic_params* pin, void* stream, pic_ctx** out)
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d.ctl, &h, sizeof h, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = launch_init(c->d, kE, c->p.n_e0, (float)std::sqrt(c->p.te0_ev * kQE / kME), c->stream);
     if (e == cudaSuccess) e = launch_init(c->d, kI, c->p.n_i0, (float)std::sqrt(c->p.ti0_ev * kQE / kMAR), c->stream);
-    if (e == cudaSuccess) e = launch_mover(c->d, c->grid_mover, 1, c->stream);
+    if (e == cudaSuccess) e = launch_mover(c->d, step_args(c, 0, 0), c->grid_mover, 1, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         pic_destroy(c);
@@ -399,7 +434,38 @@ void pic_destroy(pic_ctx* c)
     for (auto& t : c->timers)
         for (auto ev : t.ev) cudaEventDestroy(ev);
     if (c->arena) cudaFree(c->arena);
+    if (c->d.trace) cudaFree(c->d.trace);
     delete c;
+}
+
+int pic_trace(pic_ctx* c, int enable)
+{
+    if (!c) return fail(PIC_ERR_INVALID_ARG, "ctx is NULL");
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(c->stream));
+    if (enable && !c->d.trace) {
+        unsigned long long* t = nullptr;
+        CK(cudaMalloc(&t, (size_t)c->grid_mover * kTraceSlots * 8));
+        CK(cudaMemset(t, 0, (size_t)c->grid_mover * kTraceSlots * 8));
+        c->d.trace = t;
+    } else if (!enable && c->d.trace) {
+        CK(cudaFree(c->d.trace));
+        c->d.trace = nullptr;
+    }
+    sync_desc(c);
+    return PIC_OK;
+}
+
+int pic_trace_read(pic_ctx* c, uint64_t* out, int64_t cap, int64_t* n_written)
+{
+    if (!c || (!out && cap > 0)) return fail(PIC_ERR_INVALID_ARG, "bad arguments");
+    const int64_t n = c->d.trace ? (int64_t)c->grid_mover * kTraceSlots : 0;
+    if (n_written) *n_written = n;
+    if (n == 0 || cap <= 0) return PIC_OK;
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpy(out, c->d.trace, (size_t)(cap < n ? cap : n) * 8, cudaMemcpyDeviceToHost));
+    return PIC_OK;
 }
 
 int pic_step(pic_ctx* c, int64_t n)
@@ -410,7 +476,9 @@ int pic_step(pic_ctx* c, int64_t n)
         cudaEvent_t stop;
         int rc = timer_begin(c, 0, &stop);
         if (rc) return rc;
-        CK(launch_mover(c->d, c->grid_mover, 0, c->stream));
+        const int acc = c->h_step > c->acc_upto;
+        CK(launch_mover(c->d, step_args(c, c->h_step, acc), c->grid_mover, 0, c->stream));
+        if (acc) c->acc_upto = c->h_step;
         rc = timer_end(c, stop);
         if (rc) return rc;
         c->h_step++;
@@ -420,6 +488,7 @@ int pic_step(pic_ctx* c, int64_t n)
                 rc = timer_begin(c, 2, &stop);
                 if (rc) return rc;
                 CK(launch_sort(c->d, s, c->grid_sort, c->stream));
+                c->cur[s] ^= 1u;
                 rc = timer_end(c, stop);
                 if (rc) return rc;
             }
@@ -494,10 +563,11 @@ static int read_ctl(pic_ctx* c, Ctl* h)
     return PIC_OK;
 }
 
-static double u128d(const unsigned long long* p) { return (double)p[1] * 18446744073709551616.0 + (double)p[0]; }
+// split sums: word 0 sums the low 32 bits, word 1 the high 32 bits of each added value
+static double u128d(const unsigned long long* p) { return (double)p[1] * 4294967296.0 + (double)p[0]; }
 static double s128d(const long long* p)
 {
-    return (double)p[1] * 18446744073709551616.0 + (double)(unsigned long long)p[0];
+    return (double)p[1] * 4294967296.0 + (double)(unsigned long long)p[0];
 }
 
 // Potential of a (time-averaged) net charge count qn[0..N] with electrode
@@ -520,7 +590,11 @@ int pic_diag(pic_ctx* c, int kind, double* out, int64_t cap, int64_t* n_written)
     if (!c || (!out && cap > 0) || kind < 0 || kind >= PIC_DIAG_COUNT)
         return fail(PIC_ERR_INVALID_ARG, "bad diag request");
     CK(cudaSetDevice(c->device));
-    CK(launch_field(c->d, 1, c->stream));          // current state into the averages, FP64 field
+    {                                               // current state into the averages, FP64 field
+        const int acc = c->h_step > c->acc_upto;
+        CK(launch_field(c->d, v_left_at(c, c->h_step), acc, c->stream));
+        if (acc) c->acc_upto = c->h_step;
+    }
     Ctl h;
     int rc = read_ctl(c, &h);
     if (rc) return rc;
@@ -641,14 +715,10 @@ int pic_reset_averages(pic_ctx* c)
     CK(cudaMemsetAsync(g.tp_dens, 0, 2 * N1 * 8, c->stream));
     CK(cudaMemsetAsync(g.tp_vx, 0, 2 * N1 * 8, c->stream));
     CK(cudaMemsetAsync(g.eedf, 0, kNbEedf * 8, c->stream));
-    Ctl h;
-    int rc = read_ctl(c, &h);
-    if (rc) return rc;
-    h.n_avg = h.n_flux = h.n_tp_samp = 0;
-    h.sum_v = 0.0;
-    h.acc_upto = h.step;               // the current state is not part of the new window
-    CK(cudaMemcpy(&c->d.ctl->acc_upto, &h.acc_upto, sizeof(long long) * 4, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(&c->d.ctl->sum_v, &h.sum_v, sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemsetAsync(&c->d.ctl->n_avg, 0, 3 * sizeof(long long), c->stream));
+    CK(cudaMemsetAsync(&c->d.ctl->sum_v, 0, sizeof(double), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->acc_upto = c->h_step;           // the current state is not part of the new window
     return PIC_OK;
 }
 
@@ -746,7 +816,7 @@ int pic_set_species(pic_ctx* c, int s, int64_t n, const void* pos, const float* 
         const size_t N1 = (size_t)c->p.n_cells + 1;
         CK(cudaMemsetAsync(c->d.qbuf[slot][kE], 0, N1 * 8, c->stream));
         CK(cudaMemsetAsync(c->d.qbuf[slot][kI], 0, N1 * 8, c->stream));
-        CK(launch_mover(c->d, c->grid_mover, 1, c->stream));
+        CK(launch_mover(c->d, step_args(c, c->h_step, 0), c->grid_mover, 1, c->stream));
     }
     CK(cudaStreamSynchronize(c->stream));
     return PIC_OK;
@@ -756,7 +826,7 @@ int pic_get_field(pic_ctx* c, double* E, double* phi, int64_t* q_e, int64_t* q_i
 {
     if (!c) return fail(PIC_ERR_INVALID_ARG, "ctx is NULL");
     CK(cudaSetDevice(c->device));
-    CK(launch_field(c->d, 0, c->stream));
+    CK(launch_field(c->d, v_left_at(c, c->h_step), 0, c->stream));
     Ctl h;
     int rc = read_ctl(c, &h);
     if (rc) return rc;
@@ -816,6 +886,7 @@ int pic_compact(pic_ctx* c, int s)
     if (!c || s < 0 || s > 2) return fail(PIC_ERR_INVALID_ARG, "bad species");
     CK(cudaSetDevice(c->device));
     CK(launch_sort(c->d, s, c->grid_sort, c->stream));
+    c->cur[s] ^= 1u;
     return PIC_OK;
 }
 

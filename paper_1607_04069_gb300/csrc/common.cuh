@@ -84,28 +84,45 @@ struct Ctl {                   // device control block
     unsigned int cur[3];       // active ping-pong half per species
     unsigned int err;
     unsigned int field_override;   // next step uses E32 as given instead of solving
-    long long acc_upto;        // last step whose state entered the time averages
     long long n_avg, n_flux, n_tp_samp;
     long long sort_total;
     double sum_v;              // sum of the electrode voltage over the averaged steps
     unsigned long long cnt[kNumCnt];
 };
 
-// Time-averaged diagnostics are integer sums (128-bit, two words per node:
-// low word, high word), so they are exact and independent of the order in
-// which CTAs deposit.  The averaged potential follows from the averaged
-// charge and electrode voltage, since the field solve is linear.
+// Time-averaged diagnostics are integer sums, so they are exact and
+// independent of the order in which CTAs deposit.  Each node keeps two
+// 64-bit words: the sum of the low 32 bits and the sum of the high 32 bits
+// (arithmetic shift for signed moments) of the per-step value, so every step
+// adds with fire-and-forget reductions and the total is hi 2^32 + lo.  The
+// averaged potential follows from the averaged charge and electrode voltage,
+// since the field solve is linear.
 struct Diag {
-    unsigned long long* sum_q[2];   // [2 (N+1)] sum over steps of q_e, q_i (2^-32 particles)
-    long long* sum_flux[2];         // [2 (N+1)] sum over samples of sum_k W_m(x_k) rint(v_x,k), 2^-16
-    unsigned long long* tp_dens;    // [2 (N+1)] sum over TP samples of the TP deposit
-    long long* tp_vx;               // [2 (N+1)] sum over TP samples of the TP v_x moment
+    unsigned long long* sum_q[2];   // [2 (N+1)] per step: q_e, q_i (2^-32 particles)
+    long long* sum_flux[2];         // [2 (N+1)] per sample: sum_k W_m(x_k) rint(v_x,k), 2^-16
+    unsigned long long* tp_dens;    // [2 (N+1)] per TP sample: TP deposit
+    long long* tp_vx;               // [2 (N+1)] per TP sample: TP v_x moment
     unsigned long long* iedf[2];
     unsigned long long* ieadf[2];
     unsigned long long* eedf;
     unsigned long long* sp_e[2];
     unsigned long long* sp_ang[2];
 };
+
+// Per-launch inputs of a step computed on the host: the electrode voltage of
+// the step and 2 V / A split into an integer and a fraction, which keep the
+// per-CTA field solve free of FP64 arithmetic.
+struct StepArgs {
+    double v_left;
+    long long va_i;        // llrint(2 v_left / A)
+    float va_f;            // 2 v_left / A - va_i
+    float e_uniform;       // v_left / L, used when A == 0
+    int field_mode;        // 0: integer path, 1: FP64 path (|2V/A| >= 2^62), 2: no space charge
+    int accumulate;        // add the state of this step to the time averages
+    unsigned int step;     // step index l (equal to Ctl::step)
+    unsigned int cur[3];   // active ping-pong halves (equal to Ctl::cur)
+};
+enum { kFieldInt = 0, kFieldF64 = 1, kFieldUniform = 2 };
 
 struct Dev {                   // everything a kernel needs, passed by value
     SpBuf buf[3][2];
@@ -129,6 +146,8 @@ struct Dev {                   // everything a kernel needs, passed by value
     double L, dx, inv_dx;
     // field solve: phi[m+1] - 2 phi[m] + phi[m-1] = -A q_net[m]; A = dx e w / (2^32 eps0)
     double A, V0, omega, dt, f_rf;
+    float c2f;                       // A / (2 dx): E per unit of the integer bracket
+    float pad2;
     // push
     float qm_dt[2];                  // (q/m) dt
     float push32;                    // dt 2^32 / L  (fixed-point displacement per m/s)
@@ -145,24 +164,30 @@ struct Dev {                   // everything a kernel needs, passed by value
     unsigned int eedf_lo, eedf_hi;   // fixed-point window of the EEDF sample (0.45 L, 0.55 L)
     double eedf_lo64, eedf_hi64;
     uint64_t seed;
+    unsigned long long* trace;       // optional per-CTA phase timestamps of the last step launch
 };
 
-__device__ __forceinline__ void add_u128(unsigned long long* p, unsigned long long v)
+// global nanosecond timer, comparable across SMs
+__device__ __forceinline__ unsigned long long gtimer()
 {
-    const unsigned long long lo = p[0] + v;
-    p[1] += lo < v ? 1ull : 0ull;
-    p[0] = lo;
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
-__device__ __forceinline__ void add_s128(long long* p, long long v)
+// trace words per CTA: start, q loaded, field solved, prologue done, stream done, events done,
+// flush done, end, species, events count, set-up done, copies issued
+constexpr int kTraceSlots = 12;
+
+// add a per-step value to a split (lo, hi) sum with fire-and-forget reductions
+__device__ __forceinline__ void red_split(unsigned long long* p, unsigned long long v)
 {
-    const unsigned long long lo = (unsigned long long)p[0] + (unsigned long long)v;
-    p[1] += (lo < (unsigned long long)v ? 1ll : 0ll) + (v < 0 ? -1ll : 0ll);
-    p[0] = (long long)lo;
+    atomicAdd(p, v & 0xffffffffull);
+    if (v >> 32) atomicAdd(p + 1, v >> 32);
 }
-// electrode voltage at step l: V0 sin(2 pi f l dt), argument reduced exactly by sinpi
-__device__ __forceinline__ double v_rf(const Dev& d, unsigned int l)
+__device__ __forceinline__ void red_split_signed(long long* p, long long v)
 {
-    return d.V0 * sinpi(2.0 * d.f_rf * ((double)l * d.dt));
+    if (v & 0xffffffffll) atomicAdd((unsigned long long*)p, (unsigned long long)(v & 0xffffffffll));
+    if (v >> 32) atomicAdd((unsigned long long*)(p + 1), (unsigned long long)(v >> 32));
 }
 
 // ---------------------------------------------------------------- Philox4x32-10

@@ -18,10 +18,10 @@ size_t tp_smem(int ncell);
 cudaError_t mover_occupancy(const Dev& d, int* blocks_per_sm);
 cudaError_t launch_init(const Dev& d, int s, long long n, float vth, cudaStream_t st);
 // mode 0: one PIC/MCC step; mode 1: deposit the current state and solve the field
-cudaError_t launch_mover(const Dev& d, int grid, int mode, cudaStream_t st);
+cudaError_t launch_mover(const Dev& d, const StepArgs& a, int grid, int mode, cudaStream_t st);
 // FP64 field/potential of the current state; accumulate != 0 also adds the
 // current step to the time averages if no step launch has done so yet
-cudaError_t launch_field(const Dev& d, int accumulate, cudaStream_t st);
+cudaError_t launch_field(const Dev& d, double v_left, int accumulate, cudaStream_t st);
 cudaError_t launch_sort(const Dev& d, int s, int grid, cudaStream_t st);
 cudaError_t launch_tp_step(const Dev& d, int grid, cudaStream_t st);
 cudaError_t launch_tp_launch(const Dev& d, long long n, long long id0, float Emax, cudaStream_t st);

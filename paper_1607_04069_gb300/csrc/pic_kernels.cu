@@ -203,7 +203,7 @@ __device__ __forceinline__ int electron_ctas(long long ne, long long ni, int G)
 {
     if (ne <= 0) return 0;
     if (ni <= 0) return G;
-    int Ge = (int)((double)G * (double)ne / (double)(ne + ni) + 0.5);
+    int Ge = (int)((float)G * ((float)ne / (float)(ne + ni)) + 0.5f);
     return Ge < 1 ? 1 : (Ge > G - 1 ? G - 1 : Ge);
 }
 
@@ -292,10 +292,10 @@ constexpr long long kTileGroups = 16384;     // 65536 particles
 
 // bytes of the region shared by the field-solve copies (2 x u64 [N+1]) and
 // the tile sums (3 x u32 [N] + 2 x u32 [N+1]), rounded to 16
+__host__ __device__ __forceinline__ size_t q_bytes16(int N) { return ((size_t)(N + 1) * 8 + 15) & ~(size_t)15; }
 __host__ __device__ __forceinline__ size_t acc_bytes(int N)
 {
-    const size_t a = (size_t)(N + 1) * 16, b = (size_t)N * 12 + (size_t)(N + 1) * 8;
-    return ((a > b ? a : b) + 15) & ~(size_t)15;
+    return ((size_t)N * 12 + (size_t)(N + 1) * 8 + 15) & ~(size_t)15;
 }
 
 struct Acc {
@@ -315,41 +315,39 @@ __device__ __forceinline__ void acc_add64(unsigned int* lo, int* hi, int m, long
     if (vh) atomicAdd(&hi[m], vh);
 }
 
-// run of consecutive particles of one thread in the same cell
-struct Run {
-    uint32_t j, n, h, l;
-    long long fL, fR;
-    __device__ __forceinline__ void flush(const Acc& A, bool sample)
-    {
-        if (j != 0xffffffffu) {
-            atomicAdd(&A.cnt[j], n);
-            if (h) atomicAdd(&A.whi[j], h);
-            if (l) atomicAdd(&A.wlo[j], l);
-            if (sample) {
-                if (fL) acc_add64(A.flo, A.fhi, j, fL);
-                if (fR) acc_add64(A.flo, A.fhi, j + 1, fR);
-            }
-        }
-        n = h = l = 0;
-        fL = fR = 0;
-    }
-    __device__ __forceinline__ void add(const Acc& A, uint32_t jn, uint32_t wr, float vx, bool sample)
-    {
-        if (jn != j) {
-            flush(A, sample);
-            j = jn;
-        }
-        n += 1;
-        h += wr >> 16;
-        l += wr & 0xffffu;
-        if (sample) {
-            const long long vq = (long long)__float2int_rn(vx);
-            const long long wr16 = (long long)(wr >> 16);
-            fL += vq * (65536 - wr16);
-            fR += vq * wr16;
+// Deposit of one group of four slots into the tile sums: one set of
+// atomics when the group sits in one cell (cell-sorted particles), otherwise
+// one set per particle.  On sample steps also the flux moment.
+__device__ __forceinline__ void deposit_group(const Acc& A, const bool (&dep)[4], const uint32_t (&j)[4],
+                                              const uint32_t (&wr)[4], const float (&vx)[4], bool sample)
+{
+    const bool one = dep[0] && dep[1] && dep[2] && dep[3] && j[0] == j[1] && j[1] == j[2] && j[2] == j[3];
+    if (one) {
+        const uint32_t h = (wr[0] >> 16) + (wr[1] >> 16) + (wr[2] >> 16) + (wr[3] >> 16);
+        const uint32_t lo = (wr[0] & 0xffffu) + (wr[1] & 0xffffu) + (wr[2] & 0xffffu) + (wr[3] & 0xffffu);
+        atomicAdd(&A.cnt[j[0]], 4u);
+        atomicAdd(&A.whi[j[0]], h);
+        atomicAdd(&A.wlo[j[0]], lo);
+    } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (!dep[u]) continue;
+            atomicAdd(&A.cnt[j[u]], 1u);
+            atomicAdd(&A.whi[j[u]], wr[u] >> 16);
+            atomicAdd(&A.wlo[j[u]], wr[u] & 0xffffu);
         }
     }
-};
+    if (sample) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (!dep[u]) continue;
+            const long long vq = (long long)__float2int_rn(vx[u]);
+            const long long w16 = (long long)(wr[u] >> 16);
+            acc_add64(A.flo, A.fhi, j[u], vq * (65536 - w16));
+            acc_add64(A.flo, A.fhi, j[u] + 1, vq * w16);
+        }
+    }
+}
 
 // one queued event: a wall hit (both species) or a collision candidate
 template <typename PosT>
@@ -413,12 +411,13 @@ __device__ __forceinline__ Grp<P64> load_group(const SpBuf& B, long long g)
     return G;
 }
 
-// node totals of the tile into the global histograms, and clear the tile sums
+// node totals of the tile into the global histograms; clear the tile sums
+// when another tile follows
 __device__ void flush_tile(const Acc& A, int N, unsigned int jlo, unsigned int jhi, bool sample,
-                           unsigned long long* qdst, long long* fdst)
+                           unsigned long long* qdst, long long* fdst, bool clear, int t, int nt)
 {
     if (jlo != 0xffffffffu) {
-        for (int m = (int)jlo + threadIdx.x; m <= (int)jhi + 1; m += blockDim.x) {
+        for (int m = (int)jlo + t; m <= (int)jhi + 1; m += nt) {
             unsigned long long v = 0;
             if (m < N) v += ((unsigned long long)A.cnt[m] << 32) - (((unsigned long long)A.whi[m] << 16) + A.wlo[m]);
             if (m > 0) v += ((unsigned long long)A.whi[m - 1] << 16) + A.wlo[m - 1];
@@ -429,8 +428,9 @@ __device__ void flush_tile(const Acc& A, int N, unsigned int jlo, unsigned int j
             }
         }
     }
+    if (!clear) return;
     __syncthreads();
-    for (int m = threadIdx.x; m <= N; m += blockDim.x) {
+    for (int m = t; m <= N; m += nt) {
         if (m < N) A.cnt[m] = A.whi[m] = A.wlo[m] = 0;
         A.flo[m] = 0;
         A.fhi[m] = 0;
@@ -442,22 +442,23 @@ __device__ void flush_tile(const Acc& A, int N, unsigned int jlo, unsigned int j
 // vector loads and stores; consecutive threads take consecutive groups and
 // each thread loads its next group before working on the current one.
 template <bool P64, int MODE>
-__global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d)
+__global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d, StepArgs a)
 {
     using PosT = typename std::conditional<P64, double, uint32_t>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = d.ncell, N1 = N + 1;
-    // layout: [field solve: qe, qi (u64 N1 each) | later: tile sums] [sEd float2 N] [sE float N1]
-    //         [eedf u32 256] [queue u32 kQueueCap]
+    // layout: [qe u64 N1 | qi u64 N1, each padded to 16 bytes] [tile sums] [sEd float2 N]
+    //         [sE float N1] [eedf u32 256] [queue u32 kQueueCap]
     unsigned long long* sqe = (unsigned long long*)smem_raw;
-    unsigned long long* sqi = sqe + N1;
+    unsigned long long* sqi = (unsigned long long*)(smem_raw + q_bytes16(N));
+    unsigned char* sacc = smem_raw + 2 * q_bytes16(N);
     Acc A;
-    A.cnt = (unsigned int*)smem_raw;
+    A.cnt = (unsigned int*)sacc;
     A.whi = A.cnt + N;
     A.wlo = A.whi + N;
     A.flo = A.wlo + N;
     A.fhi = (int*)(A.flo + N1);
-    float2* sEd = (float2*)(smem_raw + acc_bytes(N));
+    float2* sEd = (float2*)(sacc + acc_bytes(N));
     float* sE = (float*)(sEd + N);
     unsigned int* seedf = (unsigned int*)(sE + N1);
     unsigned int* squeue = seedf + kNbEedf;
@@ -465,9 +466,24 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d)
     __shared__ unsigned int s_jlo, s_jhi, s_qn;
     __shared__ int s_last, s_overflow;
 
+    unsigned long long* tr = d.trace ? d.trace + (size_t)blockIdx.x * kTraceSlots : nullptr;
+    if (tr && threadIdx.x == 0) tr[0] = gtimer();
+    const unsigned int l = a.step;              // the host's step count (equal to ctl->step)
     Ctl* ctl = d.ctl;
-    const unsigned int l = ctl->step;
     const long long ne = ctl->n[kE], ni = ctl->n[kI], ntp = ctl->n[kTP];
+    if (MODE == 0) {
+        // both deposits of x^l (slot l%3) into shared memory: asynchronous
+        // 16-byte copies, all in flight at once (arrays 256-byte aligned, padded)
+        const int slot = l % 3;
+        const int nv = (N1 * 8 + 15) / 16;
+        for (int i = threadIdx.x; i < 2 * nv; i += blockDim.x) {
+            const int sp = i < nv ? kE : kI, k = i < nv ? i : i - nv;
+            const char* src = (const char*)d.qbuf[slot][sp] + 16 * k;
+            char* dst = (char*)(sp == kE ? sqe : sqi) + 16 * k;
+            const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src) : "memory");
+        }
+    }
     const bool sample = MODE == 0 && d.diag_every > 0 && ((l + 1) % (unsigned)d.diag_every == 0);
     const int G = gridDim.x;
     const int Ge = electron_ctas(ne, ni, G);
@@ -476,7 +492,9 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d)
     const int Gs = s == kE ? Ge : G - Ge;
     const long long ns = s == kE ? ne : ni;
     const long long G4 = (ns + 3) >> 2;
-    const long long cg0 = G4 * b / Gs, cg1 = G4 * (b + 1) / Gs;
+    const long long per = G4 / Gs, extra = G4 - per * Gs;     // balanced split of the groups
+    const long long cg0 = (long long)b * per + min((long long)b, extra);
+    const long long cg1 = cg0 + per + (b < extra ? 1 : 0);
     const long long T = blockDim.x;
     const long long chunk0 = 4 * cg0;
     const int dslot = MODE == 0 ? (l + 1) % 3 : l % 3;
@@ -484,54 +502,61 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d)
     unsigned long long* qe_dst = d.qbuf[dslot][kE];
     unsigned long long* qion = d.qbuf[dslot][kI];
     long long* fdst = d.fbuf[dslot][s];
-    const SpBuf B = d.buf[s][ctl->cur[s]];
+    const SpBuf B = d.buf[s][a.cur[s]];
+    if (tr && threadIdx.x == 0) tr[10] = gtimer();
 
     // first group of this thread: in flight during the field solve
     long long g = cg0 + threadIdx.x;
     const long long tile1_first = min(cg1, cg0 + kTileGroups);
     Grp<P64> nxt;
     if (g < tile1_first) nxt = load_group<P64, MODE>(B, g);
+    if (tr && threadIdx.x == 0) tr[11] = gtimer();
 
-    if (MODE == 0) {
-        // field of step l: every CTA solves from the deposit of x^l (slot l%3)
-        const int slot = l % 3;
-        for (int i = threadIdx.x; i < N1; i += blockDim.x) {
-            sqe[i] = d.qbuf[slot][kE][i];
-            sqi[i] = d.qbuf[slot][kI][i];
+    if (MODE == 0) asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();
+    if (tr && threadIdx.x == 0) tr[1] = gtimer();
+    {
+        // clear the tile sums; this CTA's share of the time averages and of
+        // clearing slot (l+2)%3
+        const int t = threadIdx.x, nt = blockDim.x;
+        for (int m = t; m <= N; m += nt) {
+            if (m < N) A.cnt[m] = A.whi[m] = A.wlo[m] = 0;
+            A.flo[m] = 0;
+            A.fhi[m] = 0;
         }
-        __syncthreads();
-        if (ctl->field_override) {
-            for (int i = threadIdx.x; i < N1; i += blockDim.x) sE[i] = d.E32[i];
-        } else {
-            block_field_f32(d, sqe, sqi, sE, v_rf(d, l));
+        for (int i = t; i < kNbEedf; i += nt) seedf[i] = 0;
+        if (t == 0) {
+            tally = BlockTally{};
+            s_jlo = 0xffffffffu;
+            s_jhi = 0;
+            s_qn = 0;
+            s_overflow = 0;
         }
-        if (blockIdx.x == 0) {
-            if ((long long)l > ctl->acc_upto) accumulate_step(d, l, sqe, sqi);
+        if (MODE == 0) {
+            const int m0 = N1 * blockIdx.x / G, m1 = N1 * (blockIdx.x + 1) / G;
+            if (a.accumulate) accumulate_nodes(d, l, sqe, sqi, m0, m1, a.v_left, blockIdx.x == 0, t, nt);
             const int z = (l + 2) % 3;             // read by the previous launch; cleared for the next
-            for (int i = threadIdx.x; i < N1; i += blockDim.x) {
+            for (int i = m0 + t; i < m1; i += nt) {
                 d.qbuf[z][kE][i] = 0;
                 d.qbuf[z][kI][i] = 0;
                 d.fbuf[z][kE][i] = 0;
                 d.fbuf[z][kI][i] = 0;
             }
+            // field of step l: every CTA solves from the deposit of x^l
+            if (ctl->field_override) {
+                for (int i = t; i < N1; i += nt) sE[i] = d.E32[i];
+            } else {
+                block_field_f32(d, sqe, sqi, sE, a);
+            }
         }
-        __syncthreads();
-        for (int i = threadIdx.x; i < N; i += blockDim.x) sEd[i] = make_float2(sE[i], sE[i + 1] - sE[i]);
-    }
-    for (int m = threadIdx.x; m <= N; m += blockDim.x) {
-        if (m < N) A.cnt[m] = A.whi[m] = A.wlo[m] = 0;
-        A.flo[m] = 0;
-        A.fhi[m] = 0;
-    }
-    for (int i = threadIdx.x; i < kNbEedf; i += blockDim.x) seedf[i] = 0;
-    if (threadIdx.x == 0) {
-        tally = BlockTally{};
-        s_jlo = 0xffffffffu;
-        s_jhi = 0;
-        s_qn = 0;
-        s_overflow = 0;
     }
     __syncthreads();
+    if (tr && threadIdx.x == 0) tr[2] = gtimer();
+    if (MODE == 0) {
+        for (int i = threadIdx.x; i < N; i += blockDim.x) sEd[i] = make_float2(sE[i], sE[i + 1] - sE[i]);
+        __syncthreads();
+    }
+    if (tr && threadIdx.x == 0) tr[3] = gtimer();
 
     const float qmdt = d.qm_dt[s];
     const unsigned long long thr = d.thr[s];
@@ -543,13 +568,13 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d)
     for (long long t0 = cg0; t0 < cg1; t0 += kTileGroups) {
         const long long t1 = min(cg1, t0 + kTileGroups);
         if (t0 > cg0) {                               // next tile: flush the sums of the last one
-            unsigned int lo = __reduce_min_sync(0xffffffffu, jlo), hi = __reduce_max_sync(0xffffffffu, jhi);
+            const unsigned int lo = __reduce_min_sync(0xffffffffu, jlo), hi = __reduce_max_sync(0xffffffffu, jhi);
             if ((threadIdx.x & 31) == 0) {
                 atomicMin(&s_jlo, lo);
                 atomicMax(&s_jhi, hi);
             }
             __syncthreads();
-            flush_tile(A, N, s_jlo, s_jhi, sample, qdst, fdst);
+            flush_tile(A, N, s_jlo, s_jhi, sample, qdst, fdst, true, threadIdx.x, blockDim.x);
             __syncthreads();
             if (threadIdx.x == 0) {
                 s_jlo = 0xffffffffu;
@@ -561,44 +586,46 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d)
             if (g < t1) nxt = load_group<P64, MODE>(B, g);
             __syncthreads();
         }
-        Run run{0xffffffffu, 0, 0, 0, 0, 0};
         while (g < t1) {
-            Grp<P64> G = nxt;
+            Grp<P64> Gc = nxt;
             const long long gn = g + T;
             if (gn < t1) nxt = load_group<P64, MODE>(B, gn);
+            const bool full = 4 * g + 3 < ns;       // all four slots below the slot count
             PosT x[4];
             bool act[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const long long i = 4 * g + u;
-                x[u] = G.p.get(u);
-                act[u] = i < ns && is_alive(x[u]);
+                x[u] = Gc.p.get(u);
+                act[u] = is_alive(x[u]) && (full || 4 * g + u < ns);
                 if (P64 && act[u] && !((double)x[u] < (double)N)) {
                     act[u] = false;
                     atomicOr(&ctl->err, kErrIndex);
                 }
-                if (i >= ns) G.p.set(u, dead);
+                if (!full && 4 * g + u >= ns) Gc.p.set(u, dead);
             }
+            uint32_t j[4], wr[4];
+            bool dep[4];
+            float vx[4] = {Gc.v.x, Gc.v.y, Gc.v.z, Gc.v.w};
             if (MODE == 1) {
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    if (!act[u]) continue;
-                    uint32_t j, wr;
-                    cell_of(x[u], d.kshift, j, wr);
-                    run.add(A, j, wr, 0.0f, false);
-                    jlo = min(jlo, j);
-                    jhi = max(jhi, j);
+                    dep[u] = act[u];
+                    cell_of(act[u] ? x[u] : (PosT)(P64 ? 0.5 : 1.0), d.kshift, j[u], wr[u]);
+                    if (dep[u]) {
+                        jlo = min(jlo, j[u]);
+                        jhi = max(jhi, j[u]);
+                    }
                 }
-                G.p.store(B.pos, g);
+                deposit_group(A, dep, j, wr, vx, false);
+                Gc.p.store(B.pos, g);
                 g = gn;
                 continue;
             }
             // gather + leapfrog for the four slots (branch-free; removed slots are ignored later)
-            float vx[4] = {G.v.x, G.v.y, G.v.z, G.v.w};
             PosT xn[4];
             uint32_t kind[4];
             uint4 c[4];
-            const uint64_t id[4] = {G.a.x, G.a.y, G.b.x, G.b.y};
+            const uint64_t id[4] = {Gc.a.x, Gc.a.y, Gc.b.x, Gc.b.y};
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 uint32_t jj, ww;
@@ -606,7 +633,6 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d)
                 const float2 e = sEd[jj];
                 const float f = __uint_as_float(0x3f800000u | (ww >> 9)) - 1.0f;
                 vx[u] = vx[u] + qmdt * (e.x + f * e.y);
-                kind[u] = 0xffffffffu;
                 if (P64) {
                     const double xd = (double)x[u] + (double)vx[u] * d.push64;
                     kind[u] = xd <= 0.0 ? kEvWallL : (xd >= (double)N ? kEvWallR : 0xffffffffu);
@@ -624,66 +650,53 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d)
             philox4x(c, k0, k1);
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
+                dep[u] = act[u] && kind[u] == 0xffffffffu;
+                cell_of(dep[u] ? xn[u] : (PosT)(P64 ? 0.5 : 1.0), d.kshift, j[u], wr[u]);
                 if (!act[u]) continue;
-                const long long i = 4 * g + u;
-                if (kind[u] == 0xffffffffu) {
+                if (dep[u]) {
+                    Gc.p.set(u, xn[u]);
+                    jlo = min(jlo, j[u]);
+                    jhi = max(jhi, j[u]);
                     if ((unsigned long long)c[u].x < thr) kind[u] = kEvCand;
-                    uint32_t j, wr;
-                    cell_of(xn[u], d.kshift, j, wr);
-                    run.add(A, j, wr, vx[u], sample);
-                    jlo = min(jlo, j);
-                    jhi = max(jhi, j);
-                    G.p.set(u, xn[u]);
-                    if (sample && s == kE) {
-                        bool inwin;
-                        if (P64) inwin = (double)xn[u] >= d.eedf_lo64 && (double)xn[u] < d.eedf_hi64;
-                        else inwin = (uint32_t)xn[u] >= d.eedf_lo && (uint32_t)xn[u] < d.eedf_hi;
-                        if (inwin) {
-                            const float vy = B.vy[i], vz = B.vz[i];
-                            const float en = (vx[u] * vx[u] + vy * vy + vz * vz) * (float)(0.5 * kME / kQE);
-                            int bb = (int)(en * 4.0f);
-                            bb = bb < 0 ? 0 : (bb > kNbEedf - 1 ? kNbEedf - 1 : bb);
-                            atomicAdd(&seedf[bb], 1u);
-                        }
-                    }
                 } else {
-                    G.p.set(u, dead);
+                    Gc.p.set(u, dead);
                 }
-                if (kind[u] != 0xffffffffu) {
-                    const unsigned int q = atomicAdd(&s_qn, 1u);
-                    if (q < (unsigned)kQueueCap) {
-                        squeue[q] = ((uint32_t)(i - chunk0) << 2) | kind[u];
-                    } else {                                // queue full: flag the slot
-                        d.evflag[s][i] = (unsigned char)(kind[u] + 1u);
-                        s_overflow = 1;
+            }
+            deposit_group(A, dep, j, wr, vx, sample);
+            if (sample && s == kE) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (!dep[u]) continue;
+                    bool inwin;
+                    if (P64) inwin = (double)xn[u] >= d.eedf_lo64 && (double)xn[u] < d.eedf_hi64;
+                    else inwin = (uint32_t)xn[u] >= d.eedf_lo && (uint32_t)xn[u] < d.eedf_hi;
+                    if (inwin) {
+                        const float vy = B.vy[4 * g + u], vz = B.vz[4 * g + u];
+                        const float en = (vx[u] * vx[u] + vy * vy + vz * vz) * (float)(0.5 * kME / kQE);
+                        int bb = (int)(en * 4.0f);
+                        bb = bb < 0 ? 0 : (bb > kNbEedf - 1 ? kNbEedf - 1 : bb);
+                        atomicAdd(&seedf[bb], 1u);
                     }
                 }
             }
-            G.p.store(B.pos, g);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (!act[u] || kind[u] == 0xffffffffu) continue;
+                const long long i = 4 * g + u;
+                const unsigned int q = atomicAdd(&s_qn, 1u);
+                if (q < (unsigned)kQueueCap) {
+                    squeue[q] = ((uint32_t)(i - chunk0) << 2) | kind[u];
+                } else {                                // queue full: flag the slot
+                    d.evflag[s][i] = (unsigned char)(kind[u] + 1u);
+                    s_overflow = 1;
+                }
+            }
+            Gc.p.store(B.pos, g);
             ((float4*)B.vx)[g] = make_float4(vx[0], vx[1], vx[2], vx[3]);
             g = gn;
         }
-        run.flush(A, sample);
     }
-    __syncthreads();
-    if (MODE == 0) {
-        const unsigned int qn = min(s_qn, (unsigned)kQueueCap);
-        for (unsigned int k = threadIdx.x; k < qn; k += blockDim.x) {
-            const uint32_t e = squeue[k];
-            handle_event<PosT>(d, s, chunk0 + (e >> 2), e & 3u, l, born_e, born_i, ntp, qe_dst, qion, &tally);
-        }
-        if (s_overflow) {
-            const long long chunk1 = min(4 * cg1, ns);
-            for (long long i = chunk0 + threadIdx.x; i < chunk1; i += blockDim.x) {
-                const unsigned char k = d.evflag[s][i];
-                if (k) {
-                    d.evflag[s][i] = 0;
-                    handle_event<PosT>(d, s, i, k - 1u, l, born_e, born_i, ntp, qe_dst, qion, &tally);
-                }
-            }
-        }
-    }
-    // range of touched nodes, then the node totals into the global histograms
+    // range of touched nodes
     jlo = __reduce_min_sync(0xffffffffu, jlo);
     jhi = __reduce_max_sync(0xffffffffu, jhi);
     if ((threadIdx.x & 31) == 0) {
@@ -691,11 +704,42 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d)
         atomicMax(&s_jhi, jhi);
     }
     __syncthreads();
-    flush_tile(A, N, s_jlo, s_jhi, sample, qdst, fdst);
+    if (tr && threadIdx.x == 0) tr[4] = gtimer();
+    // queued events on the first half of the CTA, node totals of the tile on
+    // the second half (the events deposit their births globally)
+    const int half = blockDim.x / 2;
+    if (MODE == 0 && (int)threadIdx.x < half) {
+        const unsigned int qn = min(s_qn, (unsigned)kQueueCap);
+        for (unsigned int k = threadIdx.x; k < qn; k += half) {
+            const uint32_t e = squeue[k];
+            handle_event<PosT>(d, s, chunk0 + (e >> 2), e & 3u, l, born_e, born_i, ntp, qe_dst, qion, &tally);
+        }
+    } else {
+        const int t = MODE == 0 ? threadIdx.x - half : threadIdx.x;
+        const int nt = MODE == 0 ? blockDim.x - half : blockDim.x;
+        flush_tile(A, N, s_jlo, s_jhi, sample, qdst, fdst, false, t, nt);
+    }
+    if (MODE == 0 && s_overflow) {
+        const long long chunk1 = min(4 * cg1, ns);
+        for (long long i = chunk0 + threadIdx.x; i < chunk1; i += blockDim.x) {
+            const unsigned char k = d.evflag[s][i];
+            if (k) {
+                d.evflag[s][i] = 0;
+                handle_event<PosT>(d, s, i, k - 1u, l, born_e, born_i, ntp, qe_dst, qion, &tally);
+            }
+        }
+    }
+    if (tr && threadIdx.x == 0) {
+        tr[5] = gtimer();
+        tr[8] = (unsigned long long)s;
+        tr[9] = (unsigned long long)s_qn;
+    }
+    __syncthreads();
     if (sample && s == kE)
         for (int i = threadIdx.x; i < kNbEedf; i += blockDim.x)
             if (seedf[i]) atomicAdd(&d.diag.eedf[i], (unsigned long long)seedf[i]);
     if (threadIdx.x == 0) flush_tally(d, tally);
+    if (tr && threadIdx.x == 0) tr[6] = gtimer();
     // last CTA: commit the step
     __threadfence();
     __syncthreads();
@@ -705,6 +749,7 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d)
         __threadfence();
         commit_step(d, MODE == 0);
     }
+    if (tr && threadIdx.x == 0) tr[7] = gtimer();
 }
 
 // ---------------------------------------------------------------- standalone ops
@@ -749,14 +794,16 @@ __global__ void k_op_poisson(const long long* qi, const long long* qe, int N, do
 
 // FP64 field and potential of the current state (step l, slot l%3), for
 // diagnostics; optionally adds step l to the time averages if no launch has.
-__global__ void k_field(Dev d, int accumulate)
+__global__ void k_field(Dev d, double v_left, int accumulate)
 {
     const unsigned int l = d.ctl->step;
     const int slot = l % 3;
     QNet qn{d.qbuf[slot][kI], d.qbuf[slot][kE], false};
-    poisson_block(qn, d.ncell, d.A, d.inv_dx, v_rf(d, l), d.phi, d.E64, nullptr);
+    poisson_block(qn, d.ncell, d.A, d.inv_dx, v_left, d.phi, d.E64, nullptr);
     __syncthreads();
-    if (accumulate && (long long)l > d.ctl->acc_upto) accumulate_step(d, l, d.qbuf[slot][kE], d.qbuf[slot][kI]);
+    if (accumulate)
+        accumulate_nodes(d, l, d.qbuf[slot][kE], d.qbuf[slot][kI], 0, d.ncell + 1, v_left, true, threadIdx.x,
+                         blockDim.x);
 }
 
 // ---------------------------------------------------------------- sort / compaction
@@ -862,7 +909,8 @@ __global__ void k_sort_scatter(Dev d, int s)
 size_t mover_smem(int ncell)
 {
     const int N1 = ncell + 1;
-    return acc_bytes(ncell) + (size_t)ncell * 8 + (size_t)N1 * 4 + kNbEedf * 4 + kQueueCap * 4;
+    return 2 * q_bytes16(ncell) + acc_bytes(ncell) + (size_t)ncell * 8 + (size_t)N1 * 4 + kNbEedf * 4 +
+           kQueueCap * 4;
 }
 
 cudaError_t launch_init(const Dev& d, int s, long long n, float vth, cudaStream_t st)
@@ -890,7 +938,7 @@ cudaError_t mover_occupancy(const Dev& d, int* blocks_per_sm)
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kMoverThreads, sm);
 }
 
-cudaError_t launch_mover(const Dev& d, int grid, int mode, cudaStream_t st)
+cudaError_t launch_mover(const Dev& d, const StepArgs& a, int grid, int mode, cudaStream_t st)
 {
     const size_t sm = mover_smem(d.ncell);
     const void* fn;
@@ -899,11 +947,11 @@ cudaError_t launch_mover(const Dev& d, int grid, int mode, cudaStream_t st)
     cudaError_t e = set_smem_attr(fn, sm);
     if (e != cudaSuccess) return e;
     if (d.pos64) {
-        if (mode == 0) k_mover<true, 0><<<grid, kMoverThreads, sm, st>>>(d);
-        else k_mover<true, 1><<<grid, kMoverThreads, sm, st>>>(d);
+        if (mode == 0) k_mover<true, 0><<<grid, kMoverThreads, sm, st>>>(d, a);
+        else k_mover<true, 1><<<grid, kMoverThreads, sm, st>>>(d, a);
     } else {
-        if (mode == 0) k_mover<false, 0><<<grid, kMoverThreads, sm, st>>>(d);
-        else k_mover<false, 1><<<grid, kMoverThreads, sm, st>>>(d);
+        if (mode == 0) k_mover<false, 0><<<grid, kMoverThreads, sm, st>>>(d, a);
+        else k_mover<false, 1><<<grid, kMoverThreads, sm, st>>>(d, a);
     }
     return cudaGetLastError();
 }
@@ -936,9 +984,9 @@ cudaError_t launch_op_deposit(const void* pos, int pos64, long long n, int ncell
     return cudaGetLastError();
 }
 
-cudaError_t launch_field(const Dev& d, int accumulate, cudaStream_t st)
+cudaError_t launch_field(const Dev& d, double v_left, int accumulate, cudaStream_t st)
 {
-    k_field<<<1, 512, 0, st>>>(d, accumulate);
+    k_field<<<1, 512, 0, st>>>(d, v_left, accumulate);
     return cudaGetLastError();
 }
 

@@ -136,46 +136,81 @@ __device__ __noinline__ static void poisson_block(const QNet& qn, int N, double 
 //     E[m] = c1 + c2 (S_m + S_{m-1} - K),  c2 = A / (2 dx),  c1 = -D0/dx + c2 K,
 //     E[0] = c1 + c2 (-K - 2 q[0]),        E[N] = c1 + c2 (2 S_N - K),
 // which is the central difference and the half-cell Gauss rule above: the
-// bracket is an exact int64, so each E[m] is one rounding of its own value
-// (no cancellation) and no FP64 arithmetic runs per node.
-// qe, qi: shared copies of the deposit; sE: shared float[N+1].
+// bracket is an exact int64, so each E[m] is one rounding of its own value.
+// K and c1 follow from T_N = sum_{j=1}^{N-1} (N - j) q_j in integer
+// arithmetic: with 2 V / A = va_i + va_f,
+//     2 D0 / A = (2 T_N - va_i - va_f) / N,  K = round((2 T_N - va_i) / N),
+//     c1 = c2 (va_f - rem) / N,  rem = 2 T_N - va_i - K N,
+// so no FP64 arithmetic runs per step (N is a power of two).  All warps of
+// the CTA take part; one block barrier.  qe, qi: shared copies of the
+// deposit; sE: shared float[N+1].
 __device__ static void block_field_f32(const Dev& d, const unsigned long long* qe, const unsigned long long* qi,
-                                float* sE, double v_left)
+                                       float* sE, const StepArgs& a)
 {
-    __shared__ long long sh64[32];
-    __shared__ __int128 sh128[32];
-    __shared__ long long sK;
-    __shared__ float sc1, sc2;
+    __shared__ long long s_wacc[32], s_wbhi[32];
+    __shared__ unsigned long long s_wblo[32];
+    const unsigned FULL = 0xffffffffu;
     const int N = d.ncell, N1 = N + 1;
-    const int T = blockDim.x, t = threadIdx.x;
-    const int seg = (N1 + T - 1) / T;
-    const int m0 = min(t * seg, N1), m1 = min(m0 + seg, N1);
-    long long a = 0;
-    for (int m = m0; m < m1; ++m)
-        if (m >= 1) a += (long long)(qi[m] - qe[m]);
-    long long totS;
-    const long long Sprev = block_exclusive_scan(a, sh64, totS);
-    __int128 b = 0;
-    long long S = Sprev;
-    for (int m = m0; m < m1; ++m) {
-        if (m >= 1) S += (long long)(qi[m] - qe[m]);
-        if (m < N) b += (__int128)S;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (a.field_mode == kFieldUniform) {
+        for (int m = threadIdx.x; m < N1; m += blockDim.x) sE[m] = a.e_uniform;
+        return;
     }
-    __int128 TN;
-    block_exclusive_scan(b, sh128, TN);
-    if (t == 0) {
-        const double D0 = (0.0 - v_left + d.A * i128_to_double(TN)) / (double)N;
-        const double c2 = 0.5 * d.A * d.inv_dx;
-        const double k = d.A != 0.0 ? 2.0 * D0 / d.A : 0.0;
-        const long long K = fabs(k) < 4e18 ? llrint(k) : 0;
-        sK = K;
-        sc2 = (float)c2;
-        sc1 = (float)(-D0 * d.inv_dx + c2 * (double)K);
+    // nodes of this warp, then of this lane
+    const int w0 = N1 * w / nw, w1 = N1 * (w + 1) / nw;
+    const int seg = (w1 - w0 + 31) / 32;
+    const int m0 = min(w0 + lane * seg, w1), m1 = min(m0 + seg, w1);
+    long long acc = 0, bhi = 0;
+    unsigned long long blo = 0;
+    for (int m = m0; m < m1; ++m) {
+        if (m < 1) continue;
+        const long long q = (long long)(qi[m] - qe[m]);
+        const unsigned int wt = (unsigned int)(N - m);
+        acc += q;
+        blo += (unsigned long long)(unsigned int)q * wt;     // (N - m) q = (q_hi 2^32 + q_lo)(N - m)
+        bhi += (q >> 32) * (long long)wt;
+    }
+    long long incl = acc;
+#pragma unroll
+    for (int k = 1; k < 32; k <<= 1) {
+        const long long y = __shfl_up_sync(FULL, incl, k);
+        if (lane >= k) incl += y;
+    }
+    unsigned long long rlo = blo;
+    long long rhi = bhi;
+#pragma unroll
+    for (int k = 16; k >= 1; k >>= 1) {
+        rlo += __shfl_xor_sync(FULL, rlo, k);
+        rhi += __shfl_xor_sync(FULL, rhi, k);
+    }
+    if (lane == 31) s_wacc[w] = incl;
+    if (lane == 0) {
+        s_wblo[w] = rlo;
+        s_wbhi[w] = rhi;
     }
     __syncthreads();
-    const long long K = sK;
-    const float c1 = sc1, c2 = sc2;
-    S = Sprev;
+    long long Sw = 0;
+    __int128 TN = 0;
+    for (int k = 0; k < nw; ++k) {
+        if (k < w) Sw += s_wacc[k];
+        TN += ((__int128)s_wbhi[k] << 32) + (__int128)s_wblo[k];
+    }
+    long long K;
+    float c1;
+    const float c2 = d.c2f;
+    if (a.field_mode == kFieldInt) {
+        const __int128 x = 2 * TN - (__int128)a.va_i;
+        const __int128 Kq = (x + (__int128)(N >> 1)) >> d.kshift;
+        const long long rem = (long long)(x - (Kq << d.kshift));
+        K = (long long)Kq;
+        c1 = c2 * ((a.va_f - (float)rem) / (float)N);
+    } else {
+        const double D0 = (0.0 - a.v_left + d.A * i128_to_double(TN)) / (double)N;
+        const double k = 2.0 * D0 / d.A;
+        K = fabs(k) < 4e18 ? llrint(k) : 0;
+        c1 = (float)(-D0 * d.inv_dx + 0.5 * d.A * d.inv_dx * (double)K);
+    }
+    long long S = Sw + incl - acc;                     // S_{m0 - 1}
     for (int m = m0; m < m1; ++m) {
         const long long q = (long long)(qi[m] - qe[m]);
         const long long Sm = m >= 1 ? S + q : 0;
@@ -189,27 +224,27 @@ __device__ static void block_field_f32(const Dev& d, const unsigned long long* q
 }
 
 // Add the state of step l (deposit in slot l%3; the flux moment sampled at
-// step l) to the time averages.  Runs once per step, in one CTA.
-__device__ static void accumulate_step(const Dev& d, unsigned int l, const unsigned long long* qe,
-                                const unsigned long long* qi)
+// step l) to the time averages for nodes [m0, m1); `count`: this CTA also
+// counts the step (exactly one CTA per step does).
+__device__ static void accumulate_nodes(const Dev& d, unsigned int l, const unsigned long long* qe,
+                                        const unsigned long long* qi, int m0, int m1, double v_left,
+                                        bool count, int t, int nt)
 {
-    const int N1 = d.ncell + 1;
     const bool fl = d.diag_every > 0 && l > 0 && l % (unsigned)d.diag_every == 0;
     const int slot = l % 3;
-    for (int m = threadIdx.x; m < N1; m += blockDim.x) {
-        add_u128(d.diag.sum_q[kE] + 2 * m, qe[m]);
-        add_u128(d.diag.sum_q[kI] + 2 * m, qi[m]);
+    for (int m = m0 + t; m < m1; m += nt) {
+        red_split(d.diag.sum_q[kE] + 2 * m, qe[m]);
+        red_split(d.diag.sum_q[kI] + 2 * m, qi[m]);
         if (fl) {
-            add_s128(d.diag.sum_flux[kE] + 2 * m, d.fbuf[slot][kE][m]);
-            add_s128(d.diag.sum_flux[kI] + 2 * m, d.fbuf[slot][kI][m]);
+            red_split_signed(d.diag.sum_flux[kE] + 2 * m, d.fbuf[slot][kE][m]);
+            red_split_signed(d.diag.sum_flux[kI] + 2 * m, d.fbuf[slot][kI][m]);
         }
     }
-    if (threadIdx.x == 0) {
+    if (count && t == 0) {
         Ctl* c = d.ctl;
-        c->sum_v += v_rf(d, l);
+        c->sum_v += v_left;
         c->n_avg += 1;
         if (fl) c->n_flux += 1;
-        c->acc_upto = l;
     }
 }
 

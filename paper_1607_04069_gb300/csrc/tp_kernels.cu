@@ -114,8 +114,8 @@ __global__ void __launch_bounds__(kTpThreads) k_tp_step(Dev d)
     __threadfence();
     for (int m = threadIdx.x; m < N1; m += blockDim.x) {
         if (sample) {
-            add_u128(d.diag.tp_dens + 2 * m, __ldcg(d.tp_q + m));
-            add_s128(d.diag.tp_vx + 2 * m, __ldcg(d.tp_flux + m));
+            red_split(d.diag.tp_dens + 2 * m, __ldcg(d.tp_q + m));
+            red_split_signed(d.diag.tp_vx + 2 * m, __ldcg(d.tp_flux + m));
         }
         d.tp_q[m] = 0;
         d.tp_flux[m] = 0;
