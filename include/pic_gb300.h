@@ -213,6 +213,35 @@ int pic_op_deposit(const void* pos, int pos_precision, int64_t n, int32_t n_cell
 int pic_op_poisson(const int64_t* q_i, const int64_t* q_e, int32_t n_cells, double dx, double weight,
                    double v_left, double* phi, double* E, void* stream);
 
+/* Counting sort by cell of a caller-owned particle set, allocating no device
+ * memory (the paper has no counterpart: this is the compaction of
+ * pic_compact for callers that cannot call cudaMalloc or any allocating
+ * routine, e.g. inside a host framework that owns all device memory).
+ *   pos_precision  32 (pos: uint32 fixed point) or 64 (pos: double cell units);
+ *   n              slots in the input, 0 <= n < 2^32;
+ *   n_cells        power of two in [4, 4096]; larger values are rejected with
+ *                  PIC_ERR_INVALID_ARG because the scratch is a fixed 32 KiB
+ *                  __device__ array inside the library (4096 counts + 4096
+ *                  offsets of 32 bits);
+ *   pos..id        device input arrays of n slots (removed slots -- pos 0,
+ *                  or negative xi -- and positions outside [0, n_cells) are
+ *                  dropped);
+ *   *_out          device output arrays with room for n slots, written in
+ *                  cell order (order within a cell is unspecified); they must
+ *                  not overlap the inputs;
+ *   n_out          device int64 receiving the number kept, or NULL;
+ *   stream         cudaStream_t as void*, NULL = legacy default stream.
+ * The work runs asynchronously on `stream`.  The first call on each device
+ * looks up the scratch array's address with that device current
+ * (cudaGetSymbolAddress), which loads the library's kernels there; make that
+ * first call before any stream capture.  All calls share the one scratch
+ * array: each call clears the counts it uses, and calls whose work may
+ * overlap on the GPU (other streams, other host threads) race on it, so the
+ * caller must order them. */
+int pic_op_sort_noalloc(int pos_precision, int64_t n, int32_t n_cells, const void* pos, const float* vx,
+                        const float* vy, const float* vz, const uint64_t* id, void* pos_out, float* vx_out,
+                        float* vy_out, float* vz_out, uint64_t* id_out, int64_t* n_out, void* stream);
+
 const char* pic_strerror(int code);
 const char* pic_last_error(void);
 

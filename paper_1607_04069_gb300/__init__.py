@@ -85,6 +85,7 @@ def lib():
             "pic_trace_read": [vp, vp, i64, pi64],
             "pic_op_deposit": [vp, C.c_int, i64, i32, vp, vp],
             "pic_op_poisson": [vp, vp, i32, dbl, dbl, dbl, vp, vp, vp],
+            "pic_op_sort_noalloc": [C.c_int, i64, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -272,3 +273,22 @@ def op_poisson(q_i, q_e, n_cells: int, dx: float, weight: float, v_left: float, 
                                 C.c_void_p(phi.data_ptr()), C.c_void_p(E.data_ptr()),
                                 C.c_void_p(_stream_handle(stream))))
     return phi, E
+
+
+def op_sort_noalloc(pos, vx, vy, vz, ids, n_cells: int, pos_out, vx_out, vy_out, vz_out, ids_out,
+                    n_out=None, stream=None):
+    """Counting sort by cell of device particle arrays into caller-owned
+    outputs, allocating no device memory (the library's static scratch holds
+    up to 4096 cells).  ``n_out``: optional device int64 tensor receiving the
+    number of particles kept.  Calls whose work may overlap on the GPU race on
+    the shared scratch and must be ordered by the caller."""
+    import torch
+    prec = 64 if pos.dtype == torch.float64 else 32
+    n = pos.numel()
+    for a in (vx, vy, vz, ids, pos_out, vx_out, vy_out, vz_out, ids_out):
+        if a.numel() < n:
+            raise ValueError("every particle array needs room for pos.numel() slots")
+    _check(lib().pic_op_sort_noalloc(prec, n, int(n_cells), *[C.c_void_p(a.data_ptr()) for a in
+                                     (pos, vx, vy, vz, ids, pos_out, vx_out, vy_out, vz_out, ids_out)],
+                                     None if n_out is None else C.c_void_p(n_out.data_ptr()),
+                                     C.c_void_p(_stream_handle(stream))))

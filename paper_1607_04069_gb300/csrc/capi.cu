@@ -47,6 +47,9 @@ struct Timer {                       // CUDA-event pairs around launches
 
 }  // namespace
 
+// error detail set by the library's other translation units
+void pg::set_last_error(const char* msg) { g_err = msg; }
+
 struct pic_ctx {
     pic_params p;
     int device = 0;

@@ -27,6 +27,8 @@ cudaError_t launch_tp_step(const Dev& d, int grid, cudaStream_t st);
 cudaError_t launch_tp_launch(const Dev& d, long long n, long long id0, float Emax, cudaStream_t st);
 cudaError_t launch_op_deposit(const void* pos, int pos64, long long n, int ncell, int kshift,
                               unsigned long long* q, int grid, cudaStream_t st);
+// record the detail that pic_last_error reports on the calling thread
+void set_last_error(const char* msg);
 cudaError_t launch_op_poisson(const long long* qi, const long long* qe, int N, double A, double inv_dx,
                               double v_left, double* phi, double* E64, cudaStream_t st);
 
