@@ -133,24 +133,25 @@ def barrier(ws):
         dist.barrier()
 
 
-def allreduce_max(x, ws):
+def _reduce(x, ws, op):
     if ws <= 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def allreduce_max(x, ws):
+    import torch.distributed as dist
+    return _reduce(x, ws, dist.ReduceOp.MAX)
 
 
 def allreduce_sum(x, ws):
-    if ws <= 1:
-        return x
-    import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce(x, ws, dist.ReduceOp.SUM)
 
 
 def workload(n_per_species, seed):

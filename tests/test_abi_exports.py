@@ -1,0 +1,32 @@
+"""The C-ABI library loads without a GPU and exports every function that
+include/pic_gb300.h declares (no compute call is made)."""
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "pic_gb300.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?(?:int|void|char|int64_t)\s*\*?\s*(\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1607_04069_gb300 import build
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    names = _declared()
+    assert len(names) >= 20
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_declares_the_same_functions():
+    import paper_1607_04069_gb300 as P
+    L = P.lib()
+    for n in _declared():
+        fn = getattr(L, n)
+        assert fn.restype is not None or n == "pic_destroy"
