@@ -25,7 +25,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-ALGO_BYTES = 24          # per particle-step: read x, v_x (4+4) and id (8); write x, v_x (4+4)
+ALGO_BYTES = 20          # per particle-step: read x, v_x, next-candidate step (4+4+4); write x, v_x (4+4)
 KERNEL_SOURCES = ["paper_1607_04069_gb300/csrc/pic_kernels.cu", "paper_1607_04069_gb300/csrc/common.cuh",
                   "paper_1607_04069_gb300/csrc/solve.cuh"]
 

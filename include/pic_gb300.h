@@ -180,13 +180,15 @@ int pic_kernel_time(pic_ctx* ctx, int kind, double* ms, int64_t* launches);
 
 /* Phase trace of the per-step launch (tracing aid): pic_trace(ctx, 1)
  * allocates a device buffer into which every CTA of each subsequent step
- * launch writes 12 words -- globaltimer stamps (ns) at start, after loading
+ * launch writes 16 words -- globaltimer stamps (ns) at start, after loading
  * the deposit, after the field solve, at the end of the prologue, after the
  * particle stream, after the queued events, after the histogram flush and at
- * exit, then its species and its event count, then stamps after the launch
- * set-up and after issuing the deposit copies.  pic_trace_read copies the
- * words of the last launch (grid x 12) to host memory; *n_written =
- * grid x 12.  pic_trace(ctx, 0) frees the buffer. */
+ * exit; its species; its event count (low 32 bits) and touched node range
+ * (high 32 bits); stamps after the launch set-up and after issuing the
+ * deposit copies; the longest single event (ns << 8 | event kind); its
+ * ionisations; the longest tile-flush thread (ns); one unused word.
+ * pic_trace_read copies the words of the last launch (grid x 16) to host
+ * memory; *n_written = grid x 16.  pic_trace(ctx, 0) frees the buffer. */
 int pic_trace(pic_ctx* ctx, int enable);
 int pic_trace_read(pic_ctx* ctx, uint64_t* host_out, int64_t cap, int64_t* n_written);
 

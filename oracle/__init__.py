@@ -97,6 +97,7 @@ def lib():
                 "orc_get_step": (u32, [vp]),
                 "orc_set_step": (None, [vp, u32]),
                 "orc_get_tp_step": (u32, [vp]),
+                "orc_gap": (u32, [dbl, u32]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -114,6 +115,12 @@ def philox(ctr, key):
     out = np.zeros(4, dtype=np.uint32)
     lib().orc_philox(_p(c), _p(k), _p(out))
     return out
+
+
+def gap(lam, w):
+    """Steps from one null-collision candidate to the next for nu_max dt =
+    lam, from the Philox word w (geometric law, see orc_gap)."""
+    return int(lib().orc_gap(float(lam), int(w) & 0xffffffff))
 
 
 def sigma_e(eps):

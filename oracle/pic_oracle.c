@@ -61,6 +61,8 @@ enum {
     PUR_NEWION = 4,      /* Maxwellian velocity of the newborn ion      */
     PUR_BIRTH_ID = 5,    /* ids of the ionisation children              */
     PUR_GAS = 6,         /* gas partner of an Ar+ collision             */
+    PUR_GAP = 7,         /* steps to the next candidate, after one      */
+    PUR_GAP0 = 8,        /* steps to the first candidate, on entry      */
     PUR_SP_TRIAL = 16,   /* +k/4: sputter trials                        */
     PUR_SP_EMIT = 32,    /* +k: energy/angle of the k-th sputtered atom */
     PUR_SP_ID = 48,      /* +k: id of the k-th sputtered atom           */
@@ -107,6 +109,7 @@ typedef struct {
     int64_t n, cap;
     double *xi, *vx, *vy, *vz;
     uint64_t *id;
+    uint32_t *nev;                /* step of the next null-collision candidate */
     uint8_t *alive;
 } orc_sp;
 
@@ -118,6 +121,7 @@ typedef struct {
     uint32_t step, tp_step;
     /* derived quantities */
     double ngas, dx, nu_max_e, nu_max_i, p_max_e, p_max_i, eps_max;
+    double lam[2];                /* nu_max dt of e- and Ar+                    */
     /* diagnostics */
     double *sum_q[2], *sum_phi, *sum_flux[2], *tp_dens, *tp_vx;
     int64_t n_avg, n_flux, n_tp_samp, tp_launched;
@@ -283,23 +287,51 @@ static void sp_alloc(orc_sp *s, int64_t cap)
     s->vy = (double *)calloc(cap ? cap : 1, sizeof(double));
     s->vz = (double *)calloc(cap ? cap : 1, sizeof(double));
     s->id = (uint64_t *)calloc(cap ? cap : 1, sizeof(uint64_t));
+    s->nev = (uint32_t *)calloc(cap ? cap : 1, sizeof(uint32_t));
     s->alive = (uint8_t *)calloc(cap ? cap : 1, 1);
 }
 
 static void sp_free(orc_sp *s)
 {
-    free(s->xi); free(s->vx); free(s->vy); free(s->vz); free(s->id); free(s->alive);
+    free(s->xi); free(s->vx); free(s->vy); free(s->vz); free(s->id); free(s->nev); free(s->alive);
 }
 
 static double mass_of(int s) { return s == SP_E ? O_ME : (s == SP_I ? O_MAR : O_MAL); }
 static double charge_of(int s) { return s == SP_E ? -O_QE : (s == SP_I ? O_QE : 0.0); }
 
-static int64_t append(orc_state *S, int s, double xi, double vx, double vy, double vz, uint64_t id)
+/* Null-collision candidates (Sec. "Particle Collisions"): every step a
+ * particle is a candidate with the fixed probability P_c,tot = 1 -
+ * exp(-nu_max dt), independently of the other steps.  The number of steps
+ * from one candidate to the next is then geometric, P(gap = n) =
+ * exp(-nu_max dt (n-1)) (1 - exp(-nu_max dt)), and it is drawn as the free
+ * flight time of Sec. "Kinetic Particle Simulation", tau = -tau_c ln R with
+ * tau_c = 1 / nu_max, counted in steps and rounded up:
+ *     gap = 1 + floor(-ln R / (nu_max dt)).
+ * Each particle keeps the step of its next candidate. */
+uint32_t orc_gap(double lam, uint32_t w)
+{
+    double x = -log(u23(w)) / lam;
+    if (!(x < 2147483646.0)) return 2147483647u;
+    return 1u + (uint32_t)floor(x);
+}
+
+/* step of the first candidate of a particle that is first pushed at step l0 */
+static uint32_t entry_nev(const orc_state *S, int s, uint64_t id, uint32_t l0)
+{
+    if (s == SP_TP) return 0;
+    uint32_t c[4];
+    draw(S->P.seed, id, l0, PUR_GAP0, c);
+    return l0 - 1u + orc_gap(S->lam[s], c[0]);
+}
+
+static int64_t append(orc_state *S, int s, double xi, double vx, double vy, double vz, uint64_t id,
+                      uint32_t l0)
 {
     orc_sp *p = &S->sp[s];
     if (p->n >= p->cap) { S->cnt[C_CAPACITY]++; return -1; }
     int64_t k = p->n++;
     p->xi[k] = xi; p->vx[k] = vx; p->vy[k] = vy; p->vz[k] = vz; p->id[k] = id; p->alive[k] = 1;
+    p->nev[k] = entry_nev(S, s, id, l0);
     return k;
 }
 
@@ -339,8 +371,10 @@ static void derive(orc_state *S)
     S->nu_max_e = S->ngas * sig_sum_max * sqrt(2.0 * S->eps_max * O_QE / O_ME);
     double mr = O_MAR / 2.0;
     S->nu_max_i = 2.0 * S->ngas * O_ARP_SIG * sqrt(2.0 * O_QE / mr);
-    S->p_max_e = 1.0 - exp(-S->nu_max_e * P->dt);
-    S->p_max_i = 1.0 - exp(-S->nu_max_i * P->dt);
+    S->lam[SP_E] = S->nu_max_e * P->dt;
+    S->lam[SP_I] = S->nu_max_i * P->dt;
+    S->p_max_e = 1.0 - exp(-S->lam[SP_E]);
+    S->p_max_i = 1.0 - exp(-S->lam[SP_I]);
 }
 
 orc_state *orc_create(const orc_params *P, int64_t cap_e, int64_t cap_i, int64_t cap_tp)
@@ -406,7 +440,7 @@ void orc_init_species(orc_state *S, int s, int64_t n, double T_eV)
         double n1, n2, n3, n4;
         box_muller(a[1], a[2], &n1, &n2);
         box_muller(b[0], b[1], &n3, &n4);
-        append(S, s, xi, vth * n1, vth * n2, vth * n3, id);
+        append(S, s, xi, vth * n1, vth * n2, vth * n3, id, 0);
     }
 }
 
@@ -417,7 +451,7 @@ int orc_set_species(orc_state *S, int s, int64_t n, const double *xi, const doub
     orc_sp *p = &S->sp[s];
     if (n > p->cap) return -1;
     p->n = 0;
-    for (int64_t k = 0; k < n; k++) append(S, s, xi[k], vx[k], vy[k], vz[k], id[k]);
+    for (int64_t k = 0; k < n; k++) append(S, s, xi[k], vx[k], vy[k], vz[k], id[k], S->step);
     for (int64_t k = 0; k < n; k++) p->alive[k] = xi[k] >= 0.0;
     return 0;
 }
@@ -496,7 +530,7 @@ static void sputter(orc_state *S, uint64_t ion_id, uint32_t l, double E, int ele
         double v[3];
         orc_emit(u23(ce[0]), u23(ce[1]), u23(ce[2]), Emax, electrode == 0 ? 1.0 : -1.0, v);
         double xi = electrode == 0 ? N * 0x1p-32 : N * (1.0 - 0x1p-32);
-        if (append(S, SP_TP, xi, v[0], v[1], v[2], child_id(ci[0], ci[1], SP_TP)) >= 0)
+        if (append(S, SP_TP, xi, v[0], v[1], v[2], child_id(ci[0], ci[1], SP_TP), 0) >= 0)
             S->cnt[electrode == 0 ? C_SPUT_L : C_SPUT_R]++;
     }
 }
@@ -505,9 +539,11 @@ static void sputter(orc_state *S, uint64_t ion_id, uint32_t l, double E, int ele
 static void mcc_electron(orc_state *S, int64_t k, uint32_t l)
 {
     orc_sp *p = &S->sp[SP_E];
-    uint32_t c[4];
+    if (p->nev[k] != l) return;                              /* not a candidate */
+    uint32_t c[4], cg[4];
     draw(S->P.seed, p->id[k], l, PUR_COLL, c);
-    if (!((double)c[0] * 0x1p-32 < S->p_max_e)) return;     /* not a candidate */
+    draw(S->P.seed, p->id[k], l, PUR_GAP, cg);
+    p->nev[k] = l + orc_gap(S->lam[SP_E], cg[0]);
     double v2 = p->vx[k] * p->vx[k] + p->vy[k] * p->vy[k] + p->vz[k] * p->vz[k];
     double v = sqrt(v2);
     double eps = 0.5 * O_ME * v2 / O_QE;
@@ -548,8 +584,8 @@ static void mcc_electron(orc_state *S, int64_t k, uint32_t l)
         double vg = sqrt(O_KB * S->P.Tg / O_MAR);
         double xi = p->xi[k];
         p->vx[k] = vs * d[0]; p->vy[k] = vs * d[1]; p->vz[k] = vs * d[2];
-        append(S, SP_E, xi, ve * d2[0], ve * d2[1], ve * d2[2], child_id(cb[0], cb[1], SP_E));
-        append(S, SP_I, xi, vg * n1, vg * n2, vg * n3, child_id(cb[2], cb[3], SP_I));
+        append(S, SP_E, xi, ve * d2[0], ve * d2[1], ve * d2[2], child_id(cb[0], cb[1], SP_E), l + 1);
+        append(S, SP_I, xi, vg * n1, vg * n2, vg * n3, child_id(cb[2], cb[3], SP_I), l + 1);
         S->cnt[C_IONIZ]++;
     }
 }
@@ -559,9 +595,11 @@ static void mcc_electron(orc_state *S, int64_t k, uint32_t l)
 static void mcc_ion(orc_state *S, int64_t k, uint32_t l)
 {
     orc_sp *p = &S->sp[SP_I];
-    uint32_t c[4];
+    if (p->nev[k] != l) return;                              /* not a candidate */
+    uint32_t c[4], cn[4];
     draw(S->P.seed, p->id[k], l, PUR_COLL, c);
-    if (!((double)c[0] * 0x1p-32 < S->p_max_i)) return;
+    draw(S->P.seed, p->id[k], l, PUR_GAP, cn);
+    p->nev[k] = l + orc_gap(S->lam[SP_I], cn[0]);
     uint32_t cg[4];
     draw(S->P.seed, p->id[k], l, PUR_GAS, cg);
     double n1, n2, n3, n4;
@@ -771,7 +809,7 @@ void orc_tp_launch(orc_state *S, int64_t n, double E_ion)
         draw(S->P.seed, id, 0, PUR_TP_LAUNCH, ce);
         double v[3];
         orc_emit(u23(ce[0]), u23(ce[1]), u23(ce[2]), Emax, 1.0, v);
-        append(S, SP_TP, N * 0x1p-32, v[0], v[1], v[2], id);
+        append(S, SP_TP, N * 0x1p-32, v[0], v[1], v[2], id, 0);
     }
 }
 

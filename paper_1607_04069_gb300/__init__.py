@@ -236,12 +236,12 @@ class Discharge:
         _check(lib().pic_trace(self.h, int(bool(enable))))
 
     def trace_read(self) -> np.ndarray:
-        """Per-CTA phase stamps of the last step launch, shape (grid, 12)."""
+        """Per-CTA phase stamps of the last step launch, shape (grid, 16)."""
         n = C.c_int64()
         _check(lib().pic_trace_read(self.h, None, 0, C.byref(n)))
         out = np.zeros(n.value, dtype=np.uint64)
         _check(lib().pic_trace_read(self.h, _ptr(out), out.size, C.byref(n)))
-        return out.reshape(-1, 12)
+        return out.reshape(-1, 16)
 
     def derived(self) -> dict:
         out = np.zeros(8)

@@ -120,6 +120,7 @@ void carve(pic_ctx* c, char* base, size_t* small_end, size_t* total)
     d.phi = L.take<double>(base, N1);
     d.sort_cnt = L.take<unsigned int>(base, c->p.n_cells);
     d.sort_off = L.take<unsigned int>(base, c->p.n_cells);
+    d.tally = L.take<unsigned long long>(base, (size_t)kMaxTallyRows * kNumCnt);
     *small_end = (L.off + 255) & ~(size_t)255;
     const long long cap[3] = {c->p.cap_e, c->p.cap_i, c->p.cap_tp};
     for (int s = 0; s < 3; ++s)
@@ -132,6 +133,7 @@ void carve(pic_ctx* c, char* base, size_t* small_end, size_t* total)
             B.vy = L.take<float>(base, n);
             B.vz = L.take<float>(base, n);
             B.id = L.take<uint64_t>(base, n);
+            B.nev = s == kTP ? nullptr : L.take<uint32_t>(base, n);
         }
     for (int s = 0; s < 2; ++s) d.evflag[s] = L.take<unsigned char>(base, (size_t)(cap[s] > 0 ? cap[s] : 1) + 4);
     *total = (L.off + 255) & ~(size_t)255;
@@ -174,8 +176,8 @@ void derive(pic_ctx* c)
     const double nu_max_e = ngas * sig_sum_max * std::sqrt(2.0 * eps_max * kQE / kME);
     const double mr = kMAR / 2.0;
     const double nu_max_i = 2.0 * ngas * kArpSig * std::sqrt(2.0 * kQE / mr);
-    const double p_max_e = 1.0 - std::exp(-nu_max_e * p.dt);
-    const double p_max_i = 1.0 - std::exp(-nu_max_i * p.dt);
+    const double p_max_e = 1.0 - std::exp(-(nu_max_e * p.dt));
+    const double p_max_i = 1.0 - std::exp(-(nu_max_i * p.dt));
     const double lam = 4.0 * kMAR * kMAL / ((kMAR + kMAL) * (kMAR + kMAL));
     double* o = c->derived;
     o[0] = ngas; o[1] = dx; o[2] = nu_max_e; o[3] = nu_max_i; o[4] = p_max_e; o[5] = p_max_i;
@@ -198,8 +200,13 @@ void derive(pic_ctx* c)
     d.qm_dt[kI] = (float)(kQE / kMAR * p.dt);
     d.push32 = (float)(p.dt * 4294967296.0 / p.gap_m);
     d.push64 = p.dt / dx;
-    d.thr[kE] = (unsigned long long)std::ceil(p_max_e * 4294967296.0);
-    d.thr[kI] = (unsigned long long)std::ceil(p_max_i * 4294967296.0);
+    d.cap[kE] = p.cap_e;
+    d.cap[kI] = p.cap_i;
+    d.cap[kTP] = p.cap_tp;
+    d.lam[kE] = nu_max_e * p.dt;
+    d.lam[kI] = nu_max_i * p.dt;
+    d.lamf[kE] = (float)d.lam[kE];
+    d.lamf[kI] = (float)d.lam[kI];
     d.ngas_f = (float)ngas;
     d.nu_max_e = (float)nu_max_e;
     d.nu_max_i = (float)nu_max_i;
@@ -403,6 +410,7 @@ int pic_create(const pic_params* pin, void* stream, pic_ctx** out)
         if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     }
     c->grid_mover = c->sms * per_sm;
+    if (c->grid_mover > kMaxTallyRows) c->grid_mover = kMaxTallyRows - kMaxTallyRows % c->sms;
     c->grid_tp = c->sms * 4;
     c->grid_sort = c->sms * 8;
 
@@ -739,7 +747,14 @@ int pic_counters(pic_ctx* c, int64_t* out, int64_t cap, int64_t* n_written)
     const int order[kNumCnt] = {kCntImpEL, kCntImpER, kCntImpIL, kCntImpIR, kCntIoniz, kCntSputL,
                                 kCntSputR, kCntTpDepL, kCntTpDepR, kCntNumerics, kCntElastic,
                                 kCntExcit, kCntCx, kCntIso, kCntTpColl, kCntCapacity};
-    for (int i = 0; i < kNumCnt; ++i) v[5 + i] = (int64_t)h.cnt[order[i]];
+    // the step launch keeps its counts per CTA (rows of d.tally)
+    std::vector<unsigned long long> rows((size_t)kMaxTallyRows * kNumCnt);
+    CK(cudaMemcpy(rows.data(), c->d.tally, rows.size() * 8, cudaMemcpyDeviceToHost));
+    unsigned long long tot[kNumCnt];
+    for (int k = 0; k < kNumCnt; ++k) tot[k] = h.cnt[k];
+    for (size_t r = 0; r < (size_t)kMaxTallyRows; ++r)
+        for (int k = 0; k < kNumCnt; ++k) tot[k] += rows[r * kNumCnt + k];
+    for (int i = 0; i < kNumCnt; ++i) v[5 + i] = (int64_t)tot[order[i]];
     const int64_t n = 5 + kNumCnt;
     for (int64_t i = 0; i < n && i < cap; ++i) out[i] = v[i];
     if (n_written) *n_written = n;
@@ -811,6 +826,7 @@ int pic_set_species(pic_ctx* c, int s, int64_t n, const void* pos, const float* 
         CK(cudaMemcpyAsync(B.vy, vy, (size_t)n * 4, cudaMemcpyHostToDevice, c->stream));
         CK(cudaMemcpyAsync(B.vz, vz, (size_t)n * 4, cudaMemcpyHostToDevice, c->stream));
         CK(cudaMemcpyAsync(B.id, id, (size_t)n * 8, cudaMemcpyHostToDevice, c->stream));
+        if (s != kTP) CK(launch_entry_nev(c->d, s, h.cur[s], n, (unsigned int)c->h_step, c->stream));
     }
     long long nn = n;
     CK(cudaMemcpyAsync(&c->d.ctl->n[s], &nn, sizeof nn, cudaMemcpyHostToDevice, c->stream));

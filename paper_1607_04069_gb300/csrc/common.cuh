@@ -47,6 +47,7 @@ constexpr int kNbSpE = 600;      // 0.5 eV bins, [0, 300)
 // random-stream purposes (fourth counter word)
 enum : uint32_t {
     kPurInit = 1, kPurColl = 2, kPurIonize = 3, kPurNewIon = 4, kPurBirthId = 5, kPurGas = 6,
+    kPurGap = 7, kPurGap0 = 8,
     kPurSpTrial = 16, kPurSpEmit = 32, kPurSpId = 48, kPurTpGas = 64, kPurTpColl = 65,
     kPurTpLaunch = 66
 };
@@ -73,22 +74,29 @@ struct SpBuf {                 // one species, one ping-pong half (structure of 
     float* vy;
     float* vz;
     uint64_t* id;
+    uint32_t* nev;             // step of the next null-collision candidate (e-, Ar+ only)
 };
 
 struct Ctl {                   // device control block
     long long n[3];            // slots in use per species (alive + removed holes)
-    long long births[3];       // appended by the running kernel
     long long cap[3];
     unsigned int step, tp_step;
-    unsigned int done, tp_done, sort_done;
     unsigned int cur[3];       // active ping-pong half per species
-    unsigned int err;
     unsigned int field_override;   // next step uses E32 as given instead of solving
     long long n_avg, n_flux, n_tp_samp;
     long long sort_total;
     double sum_v;              // sum of the electrode voltage over the averaged steps
-    unsigned long long cnt[kNumCnt];
+    // words updated by atomics while kernels run, each group on its own
+    // 128-byte line so that their queues at L2 do not delay the others
+    alignas(128) long long births[3];      // appended by the running kernel
+    alignas(128) unsigned int done, tp_done, sort_done;
+    alignas(128) unsigned int err;
+    alignas(128) unsigned long long cnt[kNumCnt];   // counts of the TP kernels
 };
+
+// per-CTA event counts of the step launch: row b of Dev::tally belongs to
+// CTA b, which adds its counts with reductions to its own row
+constexpr int kMaxTallyRows = 4096;
 
 // Time-averaged diagnostics are integer sums, so they are exact and
 // independent of the order in which CTAs deposit.  Each node keeps two
@@ -154,7 +162,10 @@ struct Dev {                   // everything a kernel needs, passed by value
     float pad1;
     double push64;                   // dt / dx      (cell-unit displacement per m/s)
     // collisions
-    unsigned long long thr[2];       // candidate iff first word < thr (= ceil(P_max 2^32))
+    long long cap[3];                // slot capacities (as Ctl::cap)
+    unsigned long long* tally;       // [kMaxTallyRows][kNumCnt] per-CTA event counts of the step launch
+    double lam[2];                   // nu_max dt: candidate gaps are geometric with P_max = 1 - exp(-lam)
+    float lamf[2];                   // the same rounded to float
     float ngas_f, nu_max_e, nu_max_i, eps_max;
     float vth_gas;                   // sqrt(k Tg / M_Ar)
     float tp_scale;                  // dt_tp 2^32 / L
@@ -175,8 +186,9 @@ __device__ __forceinline__ unsigned long long gtimer()
     return t;
 }
 // trace words per CTA: start, q loaded, field solved, prologue done, stream done, events done,
-// flush done, end, species, events count, set-up done, copies issued
-constexpr int kTraceSlots = 12;
+// flush done, end, species, events count | node range << 32, set-up done, copies issued,
+// longest event (ns << 8 | kind), ionisations, tile flush (ns), unused
+constexpr int kTraceSlots = 16;
 
 // add a per-step value to a split (lo, hi) sum with fire-and-forget reductions
 __device__ __forceinline__ void red_split(unsigned long long* p, unsigned long long v)
@@ -212,6 +224,38 @@ __device__ __forceinline__ uint4 draw(uint64_t seed, uint64_t id, uint32_t step,
 
 // uniform in (0,1) on the 2^-23 grid (top 23 bits + 1/2), exact in float
 __device__ __forceinline__ float u23(uint32_t w) { return ((float)(w >> 9) + 0.5f) * 0x1p-23f; }
+
+// Steps from one null-collision candidate to the next (Sec. "Particle
+// Collisions": every step is a candidate with P_max = 1 - exp(-nu_max dt),
+// independently of the other steps): the free flight time tau = -ln R / nu_max
+// (Sec. "Kinetic Particle Simulation") counted in steps and rounded up,
+// gap = 1 + floor(-ln R / (nu_max dt)), whose law is geometric with P_max.
+// The floor is that of the FP64 quotient, with R on the same 2^-23 grid as
+// every other uniform.  FP64 is slow on this part, so the quotient is first
+// formed in FP32 (logf within 1 ulp, lam rounded to float, one division:
+// relative error below 3e-7); when no integer lies within 4e-7 x of the FP32
+// value, its floor is the floor of the FP64 quotient, and only the other
+// cases evaluate the FP64 expression.
+__device__ __forceinline__ uint32_t gap_steps(double lam, float lamf, uint32_t w)
+{
+    const float uf = ((float)(w >> 9) + 0.5f) * 0x1p-23f;      // exact in float (24 bits)
+    const float xf = -logf(uf) / lamf;
+    if (xf < 1.0e6f) {
+        const float dl = 4e-7f * xf + 1e-6f;
+        const float a = floorf(xf - dl), b = floorf(xf + dl);
+        if (a == b) return 1u + (uint32_t)a;
+    }
+    const double u = ((double)(w >> 9) + 0.5) * 0x1p-23;
+    const double x = -log(u) / lam;
+    if (!(x < 2147483646.0)) return 2147483647u;
+    return 1u + (uint32_t)floor(x);
+}
+
+// step of the first candidate of an e- or Ar+ that is first pushed at step l0
+__device__ __forceinline__ uint32_t entry_nev(const Dev& d, int s, uint64_t id, uint32_t l0)
+{
+    return l0 - 1u + gap_steps(d.lam[s], d.lamf[s], draw(d.seed, id, l0, kPurGap0).x);
+}
 
 __device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b)
 {

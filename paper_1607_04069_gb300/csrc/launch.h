@@ -22,6 +22,8 @@ cudaError_t launch_mover(const Dev& d, const StepArgs& a, int grid, int mode, cu
 // FP64 field/potential of the current state; accumulate != 0 also adds the
 // current step to the time averages if no step launch has done so yet
 cudaError_t launch_field(const Dev& d, double v_left, int accumulate, cudaStream_t st);
+// first null-collision candidate step of n uploaded particles that are first pushed at step l0
+cudaError_t launch_entry_nev(const Dev& d, int s, unsigned int half, long long n, unsigned int l0, cudaStream_t st);
 cudaError_t launch_sort(const Dev& d, int s, int grid, cudaStream_t st);
 cudaError_t launch_tp_step(const Dev& d, int grid, cudaStream_t st);
 cudaError_t launch_tp_launch(const Dev& d, long long n, long long id0, float Emax, cudaStream_t st);

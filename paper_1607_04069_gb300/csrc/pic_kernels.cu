@@ -34,12 +34,13 @@ __global__ void k_init(Dev d, int s, long long n, float vth)
     B.vy[k] = vth * n12.y;
     B.vz[k] = vth * n34.x;
     B.id[k] = id;
+    if (s != kTP) B.nev[k] = entry_nev(d, s, id, 0);
 }
 
 // ---------------------------------------------------------------- helpers
 struct BlockTally {            // per-CTA event counts, flushed once per CTA
     unsigned int elastic, excit, ioniz, cx, iso, numerics, capacity;
-    unsigned int imp_e[2];
+    unsigned int imp_e[2], imp_i[2], sput[2];
 };
 
 __device__ __forceinline__ void hist_add(unsigned long long* h, int nb, float x, float xmax)
@@ -53,7 +54,7 @@ __device__ __forceinline__ void hist_add(unsigned long long* h, int nb, float x,
 // the IEDF / IEADF, then sputtered-atom launch (Sec. "Wall Interactions" of the
 // TPM: N = ceil(Y) trials with R <= Y/N, Thompson energy, cosine angle).
 __device__ void ion_wall(const Dev& d, uint64_t id, uint32_t l, int el, float vx, float vy, float vz,
-                         long long n_tp0, BlockTally* tally)
+                         long long n_tp0, unsigned int cur_tp, BlockTally* tally)
 {
     const float v2 = vx * vx + vy * vy + vz * vz;
     const float E = v2 * (float)(0.5 * kMAR / kQE);
@@ -66,13 +67,13 @@ __device__ void ion_wall(const Dev& d, uint64_t id, uint32_t l, int el, float vx
     int ba = (int)th;
     ba = ba < 0 ? 0 : (ba > kNbAng - 1 ? kNbAng - 1 : ba);
     atomicAdd(&d.diag.ieadf[el][be * kNbAng + ba], 1ull);
-    atomicAdd(&d.ctl->cnt[el == 0 ? kCntImpIL : kCntImpIR], 1ull);
+    atomicAdd(el == 0 ? &tally->imp_i[0] : &tally->imp_i[1], 1u);
     if (!d.sputter || !(E > (float)kSpTh)) return;
     const float Y = 0.1f * sqrtf(E / (float)kSpTh - 1.0f);
     int Nt = (int)ceilf(Y);
     Nt = Nt > kSpMaxN ? kSpMaxN : Nt;
     const float Emax = lambda_ar_al() * E;
-    const SpBuf T = d.buf[kTP][d.ctl->cur[kTP]];
+    const SpBuf T = d.buf[kTP][cur_tp];
     uint4 t = make_uint4(0, 0, 0, 0);
     for (int k = 0; k < Nt; ++k) {
         if ((k & 3) == 0) t = draw(d.seed, id, l, kPurSpTrial + (k >> 2));
@@ -82,7 +83,7 @@ __device__ void ion_wall(const Dev& d, uint64_t id, uint32_t l, int el, float vx
         const uint4 ci = draw(d.seed, id, l, kPurSpId + k);
         const float3 v = emit(u23(ce.x), u23(ce.y), u23(ce.z), Emax, el == 0 ? 1.0f : -1.0f);
         const long long idx = n_tp0 + atomicAdd((unsigned long long*)&d.ctl->births[kTP], 1ull);
-        if (idx >= d.ctl->cap[kTP]) {
+        if (idx >= d.cap[kTP]) {
             atomicAdd(&tally->capacity, 1u);
             continue;
         }
@@ -91,7 +92,7 @@ __device__ void ion_wall(const Dev& d, uint64_t id, uint32_t l, int el, float vx
         T.vy[idx] = v.y;
         T.vz[idx] = v.z;
         T.id[idx] = child_id(ci.x, ci.y, kTP);
-        atomicAdd(&d.ctl->cnt[el == 0 ? kCntSputL : kCntSputR], 1ull);
+        atomicAdd(el == 0 ? &tally->sput[0] : &tally->sput[1], 1u);
     }
 }
 
@@ -108,7 +109,7 @@ __device__ __forceinline__ void store_dead<double>(double* P, long long i) { P[i
 // remaining energy uniformly and creates an e-/Ar+ pair at x^{l+1}.
 template <typename PosT>
 __device__ void mcc_electron(const Dev& d, uint4 c, uint64_t id, uint32_t l, PosT xn, float& vx,
-                             float& vy, float& vz, long long born_e, long long born_i,
+                             float& vy, float& vz, long long born_e, long long born_i, uint3 cur,
                              unsigned long long* qe_dst, unsigned long long* qion, BlockTally* tally)
 {
     const float v2 = vx * vx + vy * vy + vz * vz;
@@ -150,21 +151,24 @@ __device__ void mcc_electron(const Dev& d, uint4 c, uint64_t id, uint32_t l, Pos
         atomicAdd(&tally->ioniz, 1u);
         const long long ie = born_e + atomicAdd((unsigned long long*)&d.ctl->births[kE], 1ull);
         const long long ii = born_i + atomicAdd((unsigned long long*)&d.ctl->births[kI], 1ull);
-        const bool ok = ie < d.ctl->cap[kE] && ii < d.ctl->cap[kI];
-        const SpBuf Be = d.buf[kE][d.ctl->cur[kE]];
-        const SpBuf Bi = d.buf[kI][d.ctl->cur[kI]];
+        const bool ok = ie < d.cap[kE] && ii < d.cap[kI];
+        const SpBuf Be = d.buf[kE][cur.x];
+        const SpBuf Bi = d.buf[kI][cur.y];
         if (!ok) {
             atomicAdd(&tally->capacity, 1u);
-            if (ie < d.ctl->cap[kE]) store_dead((PosT*)Be.pos, ie);
-            if (ii < d.ctl->cap[kI]) store_dead((PosT*)Bi.pos, ii);
+            if (ie < d.cap[kE]) store_dead((PosT*)Be.pos, ie);
+            if (ii < d.cap[kI]) store_dead((PosT*)Bi.pos, ii);
             return;
         }
         ((PosT*)Be.pos)[ie] = xn;
         Be.vx[ie] = ve * d2.x; Be.vy[ie] = ve * d2.y; Be.vz[ie] = ve * d2.z;
-        Be.id[ie] = child_id(cb.x, cb.y, kE);
+        const uint64_t ide = child_id(cb.x, cb.y, kE), idi = child_id(cb.z, cb.w, kI);
+        Be.id[ie] = ide;
+        Be.nev[ie] = entry_nev(d, kE, ide, l + 1);            // births are pushed from step l+1 on
         ((PosT*)Bi.pos)[ii] = xn;
         Bi.vx[ii] = d.vth_gas * n12.x; Bi.vy[ii] = d.vth_gas * n12.y; Bi.vz[ii] = d.vth_gas * n34.x;
-        Bi.id[ii] = child_id(cb.z, cb.w, kI);
+        Bi.id[ii] = idi;
+        Bi.nev[ii] = entry_nev(d, kI, idi, l + 1);
         uint32_t j, wr;
         cell_of(xn, d.kshift, j, wr);
         atomicAdd(&qe_dst[j], (1ull << 32) - wr);             // electron child: global histogram
@@ -209,32 +213,27 @@ __device__ __forceinline__ int electron_ctas(long long ne, long long ni, int G)
 
 __device__ __forceinline__ void flush_tally(const Dev& d, const BlockTally& t)
 {
-    Ctl* c = d.ctl;
-    if (t.elastic) atomicAdd(&c->cnt[kCntElastic], (unsigned long long)t.elastic);
-    if (t.excit) atomicAdd(&c->cnt[kCntExcit], (unsigned long long)t.excit);
-    if (t.ioniz) atomicAdd(&c->cnt[kCntIoniz], (unsigned long long)t.ioniz);
-    if (t.cx) atomicAdd(&c->cnt[kCntCx], (unsigned long long)t.cx);
-    if (t.iso) atomicAdd(&c->cnt[kCntIso], (unsigned long long)t.iso);
-    if (t.imp_e[0]) atomicAdd(&c->cnt[kCntImpEL], (unsigned long long)t.imp_e[0]);
-    if (t.imp_e[1]) atomicAdd(&c->cnt[kCntImpER], (unsigned long long)t.imp_e[1]);
-    if (t.numerics) {
-        atomicAdd(&c->cnt[kCntNumerics], (unsigned long long)t.numerics);
-        atomicOr(&c->err, kErrNumerics);
-    }
-    if (t.capacity) {
-        atomicAdd(&c->cnt[kCntCapacity], (unsigned long long)t.capacity);
-        atomicOr(&c->err, kErrCapacity);
-    }
+    unsigned long long* r = d.tally + (size_t)blockIdx.x * kNumCnt;
+    const unsigned int v[13] = {t.elastic, t.excit, t.ioniz, t.cx, t.iso, t.imp_e[0], t.imp_e[1],
+                                t.numerics, t.capacity, t.imp_i[0], t.imp_i[1], t.sput[0], t.sput[1]};
+    const int k[13] = {kCntElastic, kCntExcit, kCntIoniz, kCntCx, kCntIso, kCntImpEL, kCntImpER,
+                       kCntNumerics, kCntCapacity, kCntImpIL, kCntImpIR, kCntSputL, kCntSputR};
+#pragma unroll
+    for (int i = 0; i < 13; ++i)
+        if (v[i]) atomicAdd(&r[k[i]], (unsigned long long)v[i]);
+    if (t.numerics) atomicOr(&d.ctl->err, kErrNumerics);
+    if (t.capacity) atomicOr(&d.ctl->err, kErrCapacity);
 }
 
 // ---------------------------------------------------------------- mover
 // Slots are streamed in groups of four (16-byte vector loads and stores);
-// each thread owns a contiguous run of groups, so cell-sorted particles are
-// deposited by run-length sums in registers and only a change of cell issues
-// shared atomics.  Wall hits and collision candidates (well under 1% of the
-// particles per step) are queued in shared memory and handled after the
-// streaming loop; births go to slots from round_up(n, 4) on, which no vector
-// store of this launch touches.
+// consecutive threads take consecutive groups.  A step reads x, v_x and the
+// step of the next null-collision candidate and writes x and v_x; v_y, v_z
+// and the id are touched only by events.  Electrons reaching a wall are
+// counted in registers; Ar+ wall hits and collision candidates (well under
+// 1% of the particles per step) are queued in shared memory and handled after
+// the streaming loop; births go to slots from round_up(n, 4) on, which no
+// vector store of this launch touches.
 constexpr int kQueueCap = 1024;
 enum : uint32_t { kEvCand = 0u, kEvWallL = 1u, kEvWallR = 2u };
 
@@ -315,16 +314,28 @@ __device__ __forceinline__ void acc_add64(unsigned int* lo, int* hi, int m, long
     if (vh) atomicAdd(&hi[m], vh);
 }
 
-// Deposit of one group of four slots into the tile sums: one set of
-// atomics when the group sits in one cell (cell-sorted particles), otherwise
-// one set per particle.  On sample steps also the flux moment.
+// Deposit of one group of four slots into the tile sums.  When every active
+// lane of the warp holds four particles of one and the same cell (cell-sorted,
+// slow particles), the warp sums its weights with REDUX and one lane adds
+// them; otherwise one set of atomics per group when its four slots share a
+// cell, else one set per particle.  On sample steps also the flux moment.
 __device__ __forceinline__ void deposit_group(const Acc& A, const bool (&dep)[4], const uint32_t (&j)[4],
                                               const uint32_t (&wr)[4], const float (&vx)[4], bool sample)
 {
     const bool one = dep[0] && dep[1] && dep[2] && dep[3] && j[0] == j[1] && j[1] == j[2] && j[2] == j[3];
-    if (one) {
-        const uint32_t h = (wr[0] >> 16) + (wr[1] >> 16) + (wr[2] >> 16) + (wr[3] >> 16);
-        const uint32_t lo = (wr[0] & 0xffffu) + (wr[1] & 0xffffu) + (wr[2] & 0xffffu) + (wr[3] & 0xffffu);
+    const uint32_t h = (wr[0] >> 16) + (wr[1] >> 16) + (wr[2] >> 16) + (wr[3] >> 16);
+    const uint32_t lo = (wr[0] & 0xffffu) + (wr[1] & 0xffffu) + (wr[2] & 0xffffu) + (wr[3] & 0xffffu);
+    const unsigned m = __activemask();
+    const int leader = __ffs(m) - 1;
+    const uint32_t jl = __shfl_sync(m, j[0], leader);
+    if (__all_sync(m, one && j[0] == jl)) {
+        const uint32_t hs = __reduce_add_sync(m, h), ls = __reduce_add_sync(m, lo);
+        if ((int)(threadIdx.x & 31) == leader) {
+            atomicAdd(&A.cnt[jl], 4u * (unsigned)__popc(m));
+            atomicAdd(&A.whi[jl], hs);
+            atomicAdd(&A.wlo[jl], ls);
+        }
+    } else if (one) {
         atomicAdd(&A.cnt[j[0]], 4u);
         atomicAdd(&A.whi[j[0]], h);
         atomicAdd(&A.wlo[j[0]], lo);
@@ -352,18 +363,19 @@ __device__ __forceinline__ void deposit_group(const Acc& A, const bool (&dep)[4]
 // one queued event: a wall hit (both species) or a collision candidate
 template <typename PosT>
 __device__ __noinline__ void handle_event(const Dev& d, int s, long long i, uint32_t kind, uint32_t l,
-                                          long long born_e, long long born_i, long long ntp,
+                                          long long born_e, long long born_i, long long ntp, uint3 cur,
                                           unsigned long long* qe_dst, unsigned long long* qion,
                                           BlockTally* tally)
 {
-    const SpBuf B = d.buf[s][d.ctl->cur[s]];
+    const SpBuf B = d.buf[s][s == kE ? cur.x : cur.y];
     float vx = B.vx[i], vy = B.vy[i], vz = B.vz[i];
     const uint64_t id = B.id[i];
     if (kind == kEvCand) {
         const uint4 c = draw(d.seed, id, l, kPurColl);
+        B.nev[i] = l + gap_steps(d.lam[s], d.lamf[s], draw(d.seed, id, l, kPurGap).x);
         if (s == kE)
-            mcc_electron<PosT>(d, c, id, l, ((const PosT*)B.pos)[i], vx, vy, vz, born_e, born_i, qe_dst, qion,
-                               tally);
+            mcc_electron<PosT>(d, c, id, l, ((const PosT*)B.pos)[i], vx, vy, vz, born_e, born_i, cur, qe_dst,
+                               qion, tally);
         else
             mcc_ion(d, c, id, l, vx, vy, vz, tally);
         B.vx[i] = vx;
@@ -371,23 +383,8 @@ __device__ __noinline__ void handle_event(const Dev& d, int s, long long i, uint
         B.vz[i] = vz;
     } else {
         const int el = kind == kEvWallL ? 0 : 1;
-        if (s == kI) ion_wall(d, id, l, el, vx, vy, vz, ntp, tally);
+        if (s == kI) ion_wall(d, id, l, el, vx, vy, vz, ntp, cur.z, tally);
         else atomicAdd(&tally->imp_e[el], 1u);
-    }
-}
-
-__device__ __forceinline__ void philox4x(uint4 (&c)[4], uint32_t k0, uint32_t k1)
-{
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const unsigned long long p0 = 0xD2511F53ull * c[u].x;
-            const unsigned long long p1 = 0xCD9E8D57ull * c[u].z;
-            c[u] = make_uint4((uint32_t)(p1 >> 32) ^ c[u].y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c[u].w ^ k1,
-                              (uint32_t)p0);
-        }
     }
 }
 
@@ -395,7 +392,7 @@ template <bool P64>
 struct Grp {                   // one group of four slots, as loaded
     Pos4<P64> p;
     float4 v;
-    ulonglong2 a, b;
+    uint4 nv;                  // steps of the next candidate
 };
 
 template <bool P64, int MODE>
@@ -405,8 +402,7 @@ __device__ __forceinline__ Grp<P64> load_group(const SpBuf& B, long long g)
     G.p.load(B.pos, g);
     if (MODE == 0) {
         G.v = ((const float4*)B.vx)[g];
-        G.a = ((const ulonglong2*)B.id)[2 * g];
-        G.b = ((const ulonglong2*)B.id)[2 * g + 1];
+        G.nv = ((const uint4*)B.nev)[g];
     }
     return G;
 }
@@ -465,6 +461,7 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d,
     __shared__ BlockTally tally;
     __shared__ unsigned int s_jlo, s_jhi, s_qn;
     __shared__ int s_last, s_overflow;
+    __shared__ unsigned long long s_evmax, s_flushns;
 
     unsigned long long* tr = d.trace ? d.trace + (size_t)blockIdx.x * kTraceSlots : nullptr;
     if (tr && threadIdx.x == 0) tr[0] = gtimer();
@@ -531,6 +528,8 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d,
             s_jhi = 0;
             s_qn = 0;
             s_overflow = 0;
+            s_evmax = 0;
+            s_flushns = 0;
         }
         if (MODE == 0) {
             const int m0 = N1 * blockIdx.x / G, m1 = N1 * (blockIdx.x + 1) / G;
@@ -559,11 +558,11 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d,
     if (tr && threadIdx.x == 0) tr[3] = gtimer();
 
     const float qmdt = d.qm_dt[s];
-    const unsigned long long thr = d.thr[s];
     const long long born_e = round4(ne), born_i = round4(ni);
+    const uint3 cur3 = make_uint3(a.cur[kE], a.cur[kI], a.cur[kTP]);
     const PosT dead = dead_value<PosT>();
-    const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
     uint32_t jlo = 0xffffffffu, jhi = 0;
+    unsigned int imp_l = 0, imp_r = 0;          // electrons absorbed at x = 0 / x = L
 
     for (long long t0 = cg0; t0 < cg1; t0 += kTileGroups) {
         const long long t1 = min(cg1, t0 + kTileGroups);
@@ -590,18 +589,19 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d,
             Grp<P64> Gc = nxt;
             const long long gn = g + T;
             if (gn < t1) nxt = load_group<P64, MODE>(B, gn);
-            const bool full = 4 * g + 3 < ns;       // all four slots below the slot count
+            const long long rem64 = ns - 4 * g;       // slots of this group below the slot count
+            const int rem = rem64 >= 4 ? 4 : (int)rem64;
             PosT x[4];
             bool act[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 x[u] = Gc.p.get(u);
-                act[u] = is_alive(x[u]) && (full || 4 * g + u < ns);
+                act[u] = is_alive(x[u]) && u < rem;
                 if (P64 && act[u] && !((double)x[u] < (double)N)) {
                     act[u] = false;
                     atomicOr(&ctl->err, kErrIndex);
                 }
-                if (!full && 4 * g + u >= ns) Gc.p.set(u, dead);
+                if (u >= rem) Gc.p.set(u, dead);
             }
             uint32_t j[4], wr[4];
             bool dep[4];
@@ -624,8 +624,7 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d,
             // gather + leapfrog for the four slots (branch-free; removed slots are ignored later)
             PosT xn[4];
             uint32_t kind[4];
-            uint4 c[4];
-            const uint64_t id[4] = {Gc.a.x, Gc.a.y, Gc.b.x, Gc.b.y};
+            const uint32_t nv[4] = {Gc.nv.x, Gc.nv.y, Gc.nv.z, Gc.nv.w};
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 uint32_t jj, ww;
@@ -645,21 +644,26 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d,
                               : ((disp < 0 && (0u - (uint32_t)disp) >= xu) ? kEvWallL : 0xffffffffu);
                     xn[u] = (PosT)xm;
                 }
-                c[u] = make_uint4((uint32_t)id[u], (uint32_t)(id[u] >> 32), l, kPurColl);
             }
-            philox4x(c, k0, k1);
+            uint32_t evm = 0;                          // bit u: slot u goes to the event queue
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 dep[u] = act[u] && kind[u] == 0xffffffffu;
                 cell_of(dep[u] ? xn[u] : (PosT)(P64 ? 0.5 : 1.0), d.kshift, j[u], wr[u]);
-                if (!act[u]) continue;
+                Gc.p.set(u, dep[u] ? xn[u] : dead);
                 if (dep[u]) {
-                    Gc.p.set(u, xn[u]);
                     jlo = min(jlo, j[u]);
                     jhi = max(jhi, j[u]);
-                    if ((unsigned long long)c[u].x < thr) kind[u] = kEvCand;
+                }
+                const bool wall = act[u] && !dep[u];
+                const bool cand = dep[u] && (int)(nv[u] - l) <= 0;
+                if (cand) kind[u] = kEvCand;
+                if (s == kE) {                        // an electron at a wall is only counted
+                    imp_l += (wall && kind[u] == kEvWallL) ? 1u : 0u;
+                    imp_r += (wall && kind[u] == kEvWallR) ? 1u : 0u;
+                    evm |= cand ? 1u << u : 0u;
                 } else {
-                    Gc.p.set(u, dead);
+                    evm |= (cand || wall) ? 1u << u : 0u;
                 }
             }
             deposit_group(A, dep, j, wr, vx, sample);
@@ -679,21 +683,31 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d,
                     }
                 }
             }
+            if (evm) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (!act[u] || kind[u] == 0xffffffffu) continue;
-                const long long i = 4 * g + u;
-                const unsigned int q = atomicAdd(&s_qn, 1u);
-                if (q < (unsigned)kQueueCap) {
-                    squeue[q] = ((uint32_t)(i - chunk0) << 2) | kind[u];
-                } else {                                // queue full: flag the slot
-                    d.evflag[s][i] = (unsigned char)(kind[u] + 1u);
-                    s_overflow = 1;
+                for (int u = 0; u < 4; ++u) {
+                    if (!(evm & (1u << u))) continue;
+                    const long long i = 4 * g + u;
+                    const unsigned int q = atomicAdd(&s_qn, 1u);
+                    if (q < (unsigned)kQueueCap) {
+                        squeue[q] = ((uint32_t)(i - chunk0) << 2) | kind[u];
+                    } else {                            // queue full: flag the slot
+                        d.evflag[s][i] = (unsigned char)(kind[u] + 1u);
+                        s_overflow = 1;
+                    }
                 }
             }
             Gc.p.store(B.pos, g);
             ((float4*)B.vx)[g] = make_float4(vx[0], vx[1], vx[2], vx[3]);
             g = gn;
+        }
+    }
+    if (MODE == 0 && s == kE) {
+        imp_l = __reduce_add_sync(0xffffffffu, imp_l);
+        imp_r = __reduce_add_sync(0xffffffffu, imp_r);
+        if ((threadIdx.x & 31) == 0 && (imp_l | imp_r)) {
+            atomicAdd(&tally.imp_e[0], imp_l);
+            atomicAdd(&tally.imp_e[1], imp_r);
         }
     }
     // range of touched nodes
@@ -712,12 +726,17 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d,
         const unsigned int qn = min(s_qn, (unsigned)kQueueCap);
         for (unsigned int k = threadIdx.x; k < qn; k += half) {
             const uint32_t e = squeue[k];
-            handle_event<PosT>(d, s, chunk0 + (e >> 2), e & 3u, l, born_e, born_i, ntp, qe_dst, qion, &tally);
+            const unsigned long long te = tr ? gtimer() : 0ull;
+            handle_event<PosT>(d, s, chunk0 + (e >> 2), e & 3u, l, born_e, born_i, ntp, cur3, qe_dst, qion,
+                               &tally);
+            if (tr) atomicMax(&s_evmax, ((gtimer() - te) << 8) | (e & 3u));
         }
     } else {
         const int t = MODE == 0 ? threadIdx.x - half : threadIdx.x;
         const int nt = MODE == 0 ? blockDim.x - half : blockDim.x;
+        const unsigned long long tf = tr ? gtimer() : 0ull;
         flush_tile(A, N, s_jlo, s_jhi, sample, qdst, fdst, false, t, nt);
+        if (tr) atomicMax(&s_flushns, gtimer() - tf);
     }
     if (MODE == 0 && s_overflow) {
         const long long chunk1 = min(4 * cg1, ns);
@@ -725,21 +744,26 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d,
             const unsigned char k = d.evflag[s][i];
             if (k) {
                 d.evflag[s][i] = 0;
-                handle_event<PosT>(d, s, i, k - 1u, l, born_e, born_i, ntp, qe_dst, qion, &tally);
+                handle_event<PosT>(d, s, i, k - 1u, l, born_e, born_i, ntp, cur3, qe_dst, qion, &tally);
             }
         }
     }
     if (tr && threadIdx.x == 0) {
         tr[5] = gtimer();
         tr[8] = (unsigned long long)s;
-        tr[9] = (unsigned long long)s_qn;
+        tr[9] = (unsigned long long)s_qn | ((unsigned long long)(s_jhi - s_jlo + 1u) << 32);
     }
     __syncthreads();
     if (sample && s == kE)
         for (int i = threadIdx.x; i < kNbEedf; i += blockDim.x)
             if (seedf[i]) atomicAdd(&d.diag.eedf[i], (unsigned long long)seedf[i]);
     if (threadIdx.x == 0) flush_tally(d, tally);
-    if (tr && threadIdx.x == 0) tr[6] = gtimer();
+    if (tr && threadIdx.x == 0) {
+        tr[6] = gtimer();
+        tr[12] = s_evmax;
+        tr[13] = tally.ioniz;
+        tr[14] = s_flushns;
+    }
     // last CTA: commit the step
     __threadfence();
     __syncthreads();
@@ -804,6 +828,14 @@ __global__ void k_field(Dev d, double v_left, int accumulate)
     if (accumulate)
         accumulate_nodes(d, l, d.qbuf[slot][kE], d.qbuf[slot][kI], 0, d.ncell + 1, v_left, true, threadIdx.x,
                          blockDim.x);
+}
+
+// ---------------------------------------------------------------- uploaded state
+__global__ void k_entry_nev(Dev d, int s, unsigned int half, long long n, unsigned int l0)
+{
+    const SpBuf B = d.buf[s][half];
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        B.nev[k] = entry_nev(d, s, B.id[k], l0);
 }
 
 // ---------------------------------------------------------------- sort / compaction
@@ -892,6 +924,7 @@ __global__ void k_sort_scatter(Dev d, int s)
             Bn.vy[o] = A.vy[i];
             Bn.vz[o] = A.vz[i];
             Bn.id[o] = A.id[i];
+            if (s != kTP) Bn.nev[o] = A.nev[i];
         }
     }
     __threadfence();
@@ -953,6 +986,14 @@ cudaError_t launch_mover(const Dev& d, const StepArgs& a, int grid, int mode, cu
         if (mode == 0) k_mover<false, 0><<<grid, kMoverThreads, sm, st>>>(d, a);
         else k_mover<false, 1><<<grid, kMoverThreads, sm, st>>>(d, a);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_entry_nev(const Dev& d, int s, unsigned int half, long long n, unsigned int l0, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const long long b = (n + 255) / 256;
+    k_entry_nev<<<(int)(b < 4096 ? b : 4096), 256, 0, st>>>(d, s, half, n, l0);
     return cudaGetLastError();
 }
 

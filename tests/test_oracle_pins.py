@@ -227,6 +227,31 @@ def _mono(n, speed, rng):
     return d * speed
 
 
+def test_candidate_gap_is_geometric_with_the_per_step_probability():
+    """The steps between null-collision candidates: every step is a candidate
+    with probability P = 1 - exp(-nu_max dt) independently of the others
+    (Sec. "Particle Collisions"), so gap n has probability (1-P)^(n-1) P.
+    Checked by a chi-square test over gaps 1..40 plus the tail, the mean
+    1/P, and the exact special cases P(gap=1) boundary and lam = 0."""
+    lam = 0.05
+    P = 1 - math.exp(-lam)
+    words = [int(O.philox([k, 7, 3, 7], [11, 13])[0]) for k in range(60_000)]
+    g = np.array([O.gap(lam, w) for w in words])
+    assert g.min() >= 1
+    nmax = 40
+    obs = np.bincount(np.minimum(g, nmax + 1), minlength=nmax + 2)[1:]
+    pn = [(1 - P) ** (n - 1) * P for n in range(1, nmax + 1)]
+    exp_ = np.array(pn + [(1 - P) ** nmax]) * len(g)
+    chi2 = ((obs - exp_) ** 2 / exp_).sum()
+    assert stats.chi2.sf(chi2, len(exp_) - 1) > 1e-3
+    assert abs(g.mean() - 1 / P) < 5 * math.sqrt((1 - P) / P**2 / len(g))
+    # u = (w >> 9 + 1/2) 2^-23 close to 1 gives gap 1; a word with u <= exp(-lam) gives gap >= 2
+    assert O.gap(lam, 0xFFFFFFFF) == 1
+    w_edge = int((math.exp(-lam) / 2**-23 - 0.5)) << 9
+    assert O.gap(lam, w_edge) == 2
+    assert O.gap(0.0, 12345) == 2**31 - 1
+
+
 def test_electron_null_collision_rate_constant_sigma():
     """Below every threshold only elastic scattering (constant sigma) is real:
     the real-collision fraction per step is P_max nu_el(v) / nu_max (binomial)."""
