@@ -50,6 +50,28 @@ __device__ __forceinline__ void hist_add(unsigned long long* h, int nb, float x,
     atomicAdd(&h[b], 1ull);
 }
 
+// The event paths call their random draws, directions, Maxwellian samples,
+// candidate gaps and sputter launches out of line.  Frequent events (the
+// elastic collisions of electrons) keep that code in the instruction cache,
+// so a rare outcome -- an ionisation, an Ar+ collision, a sputtered atom --
+// fetches little code of its own; inlined, each rare path is a separate body
+// of code that is cold whenever it runs.
+__device__ __noinline__ uint4 ev_draw(uint64_t seed, uint64_t id, uint32_t step, uint32_t purpose)
+{
+    return draw(seed, id, step, purpose);
+}
+__device__ __noinline__ float3 ev_iso_dir(uint32_t a, uint32_t b) { return iso_dir(a, b); }
+__device__ __noinline__ float2 ev_box_muller(uint32_t a, uint32_t b) { return box_muller(a, b); }
+__device__ __noinline__ uint32_t ev_gap(double lam, float lamf, uint32_t w) { return gap_steps(lam, lamf, w); }
+__device__ __noinline__ float3 ev_emit(float uE, float uT, float uP, float Emax, float dir)
+{
+    return emit(uE, uT, uP, Emax, dir);
+}
+__device__ __forceinline__ uint32_t ev_entry_nev(const Dev& d, int s, uint64_t id, uint32_t l0)
+{
+    return l0 - 1u + ev_gap(d.lam[s], d.lamf[s], ev_draw(d.seed, id, l0, kPurGap0).x);
+}
+
 // Wall interaction of an Ar+ (Sec. "Wall Interaction"): energy and angle into
 // the IEDF / IEADF, then sputtered-atom launch (Sec. "Wall Interactions" of the
 // TPM: N = ceil(Y) trials with R <= Y/N, Thompson energy, cosine angle).
@@ -76,12 +98,12 @@ __device__ void ion_wall(const Dev& d, uint64_t id, uint32_t l, int el, float vx
     const SpBuf T = d.buf[kTP][cur_tp];
     uint4 t = make_uint4(0, 0, 0, 0);
     for (int k = 0; k < Nt; ++k) {
-        if ((k & 3) == 0) t = draw(d.seed, id, l, kPurSpTrial + (k >> 2));
+        if ((k & 3) == 0) t = ev_draw(d.seed, id, l, kPurSpTrial + (k >> 2));
         const uint32_t w = (k & 3) == 0 ? t.x : (k & 3) == 1 ? t.y : (k & 3) == 2 ? t.z : t.w;
         if (!(u23(w) <= Y / (float)Nt)) continue;
-        const uint4 ce = draw(d.seed, id, l, kPurSpEmit + k);
-        const uint4 ci = draw(d.seed, id, l, kPurSpId + k);
-        const float3 v = emit(u23(ce.x), u23(ce.y), u23(ce.z), Emax, el == 0 ? 1.0f : -1.0f);
+        const uint4 ce = ev_draw(d.seed, id, l, kPurSpEmit + k);
+        const uint4 ci = ev_draw(d.seed, id, l, kPurSpId + k);
+        const float3 v = ev_emit(u23(ce.x), u23(ce.y), u23(ce.z), Emax, el == 0 ? 1.0f : -1.0f);
         const long long idx = n_tp0 + atomicAdd((unsigned long long*)&d.ctl->births[kTP], 1ull);
         if (idx >= d.cap[kTP]) {
             atomicAdd(&tally->capacity, 1u);
@@ -124,7 +146,7 @@ __device__ void mcc_electron(const Dev& d, uint4 c, uint64_t id, uint32_t l, Pos
     const float nu_exc = d.ngas_f * s_exc * v;
     const float nu_ion = d.ngas_f * s_ion * v;
     const float r = u23(c.y) * d.nu_max_e;
-    const float3 dir = iso_dir(c.z, c.w);
+    const float3 dir = ev_iso_dir(c.z, c.w);
     if (r < nu_el) {
         const float cchi = v > 0.0f ? (dir.x * vx + dir.y * vy + dir.z * vz) / v : 1.0f;
         const float fac = 1.0f - (float)(2.0 * kME / kMAR) * (1.0f - cchi);
@@ -137,16 +159,16 @@ __device__ void mcc_electron(const Dev& d, uint4 c, uint64_t id, uint32_t l, Pos
         atomicAdd(&tally->excit, 1u);
     } else if (r < nu_el + nu_exc + nu_ion) {
         const float epr = eps - (float)kIonTh;
-        const uint4 ci = draw(d.seed, id, l, kPurIonize);
-        const uint4 cn = draw(d.seed, id, l, kPurNewIon);
-        const uint4 cb = draw(d.seed, id, l, kPurBirthId);
+        const uint4 ci = ev_draw(d.seed, id, l, kPurIonize);
+        const uint4 cn = ev_draw(d.seed, id, l, kPurNewIon);
+        const uint4 cb = ev_draw(d.seed, id, l, kPurBirthId);
         const float e_ej = u23(ci.x) * epr;
         const float e_sc = epr - e_ej;
         const float vs = sqrtf(e_sc * (float)(2.0 * kQE / kME));
         const float ve = sqrtf(e_ej * (float)(2.0 * kQE / kME));
-        const float3 d2 = iso_dir(ci.y, ci.z);
-        const float2 n12 = box_muller(cn.x, cn.y);
-        const float2 n34 = box_muller(cn.z, cn.w);
+        const float3 d2 = ev_iso_dir(ci.y, ci.z);
+        const float2 n12 = ev_box_muller(cn.x, cn.y);
+        const float2 n34 = ev_box_muller(cn.z, cn.w);
         vx = vs * dir.x; vy = vs * dir.y; vz = vs * dir.z;
         atomicAdd(&tally->ioniz, 1u);
         const long long ie = born_e + atomicAdd((unsigned long long*)&d.ctl->births[kE], 1ull);
@@ -164,11 +186,11 @@ __device__ void mcc_electron(const Dev& d, uint4 c, uint64_t id, uint32_t l, Pos
         Be.vx[ie] = ve * d2.x; Be.vy[ie] = ve * d2.y; Be.vz[ie] = ve * d2.z;
         const uint64_t ide = child_id(cb.x, cb.y, kE), idi = child_id(cb.z, cb.w, kI);
         Be.id[ie] = ide;
-        Be.nev[ie] = entry_nev(d, kE, ide, l + 1);            // births are pushed from step l+1 on
+        Be.nev[ie] = ev_entry_nev(d, kE, ide, l + 1);            // births are pushed from step l+1 on
         ((PosT*)Bi.pos)[ii] = xn;
         Bi.vx[ii] = d.vth_gas * n12.x; Bi.vy[ii] = d.vth_gas * n12.y; Bi.vz[ii] = d.vth_gas * n34.x;
         Bi.id[ii] = idi;
-        Bi.nev[ii] = entry_nev(d, kI, idi, l + 1);
+        Bi.nev[ii] = ev_entry_nev(d, kI, idi, l + 1);
         uint32_t j, wr;
         cell_of(xn, d.kshift, j, wr);
         atomicAdd(&qe_dst[j], (1ull << 32) - wr);             // electron child: global histogram
@@ -184,9 +206,9 @@ __device__ void mcc_electron(const Dev& d, uint4 c, uint64_t id, uint32_t l, Pos
 __device__ __forceinline__ void mcc_ion(const Dev& d, uint4 c, uint64_t id, uint32_t l, float& vx,
                                         float& vy, float& vz, BlockTally* tally)
 {
-    const uint4 cg = draw(d.seed, id, l, kPurGas);
-    const float2 n12 = box_muller(cg.x, cg.y);
-    const float2 n34 = box_muller(cg.z, cg.w);
+    const uint4 cg = ev_draw(d.seed, id, l, kPurGas);
+    const float2 n12 = ev_box_muller(cg.x, cg.y);
+    const float2 n34 = ev_box_muller(cg.z, cg.w);
     const float wx = d.vth_gas * n12.x, wy = d.vth_gas * n12.y, wz = d.vth_gas * n34.x;
     if (u23(c.y) < 0.5f) {
         vx = wx; vy = wy; vz = wz;
@@ -194,7 +216,7 @@ __device__ __forceinline__ void mcc_ion(const Dev& d, uint4 c, uint64_t id, uint
     } else {
         const float gx = vx - wx, gy = vy - wy, gz = vz - wz;
         const float gm = sqrtf(gx * gx + gy * gy + gz * gz);
-        const float3 dir = iso_dir(c.z, c.w);
+        const float3 dir = ev_iso_dir(c.z, c.w);
         vx = 0.5f * (vx + wx) + 0.5f * gm * dir.x;
         vy = 0.5f * (vy + wy) + 0.5f * gm * dir.y;
         vz = 0.5f * (vz + wz) + 0.5f * gm * dir.z;
@@ -371,8 +393,8 @@ __device__ __noinline__ void handle_event(const Dev& d, int s, long long i, uint
     float vx = B.vx[i], vy = B.vy[i], vz = B.vz[i];
     const uint64_t id = B.id[i];
     if (kind == kEvCand) {
-        const uint4 c = draw(d.seed, id, l, kPurColl);
-        B.nev[i] = l + gap_steps(d.lam[s], d.lamf[s], draw(d.seed, id, l, kPurGap).x);
+        const uint4 c = ev_draw(d.seed, id, l, kPurColl);
+        B.nev[i] = l + ev_gap(d.lam[s], d.lamf[s], ev_draw(d.seed, id, l, kPurGap).x);
         if (s == kE)
             mcc_electron<PosT>(d, c, id, l, ((const PosT*)B.pos)[i], vx, vy, vz, born_e, born_i, cur, qe_dst,
                                qion, tally);
