@@ -216,6 +216,24 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1)
     return c;
 }
 
+// N independent Philox4x32-10 blocks under one key, round by round, so their
+// multiply chains overlap
+template <int N>
+__device__ __forceinline__ void philox_n(uint4 (&c)[N], uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+#pragma unroll
+        for (int u = 0; u < N; ++u) {
+            const unsigned long long p0 = 0xD2511F53ull * c[u].x;
+            const unsigned long long p1 = 0xCD9E8D57ull * c[u].z;
+            c[u] = make_uint4((uint32_t)(p1 >> 32) ^ c[u].y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c[u].w ^ k1,
+                              (uint32_t)p0);
+        }
+    }
+}
+
 __device__ __forceinline__ uint4 draw(uint64_t seed, uint64_t id, uint32_t step, uint32_t purpose)
 {
     return philox(make_uint4((uint32_t)id, (uint32_t)(id >> 32), step, purpose), (uint32_t)seed,
@@ -236,19 +254,28 @@ __device__ __forceinline__ float u23(uint32_t w) { return ((float)(w >> 9) + 0.5
 // relative error below 3e-7); when no integer lies within 4e-7 x of the FP32
 // value, its floor is the floor of the FP64 quotient, and only the other
 // cases evaluate the FP64 expression.
-__device__ __forceinline__ uint32_t gap_steps(double lam, float lamf, uint32_t w)
+__device__ __forceinline__ bool gap_fast(float lamf, uint32_t w, uint32_t& gap)
 {
     const float uf = ((float)(w >> 9) + 0.5f) * 0x1p-23f;      // exact in float (24 bits)
     const float xf = -logf(uf) / lamf;
-    if (xf < 1.0e6f) {
-        const float dl = 4e-7f * xf + 1e-6f;
-        const float a = floorf(xf - dl), b = floorf(xf + dl);
-        if (a == b) return 1u + (uint32_t)a;
-    }
+    if (!(xf < 1.0e6f)) return false;
+    const float dl = 4e-7f * xf + 1e-6f;
+    const float a = floorf(xf - dl), b = floorf(xf + dl);
+    if (a != b) return false;
+    gap = 1u + (uint32_t)a;
+    return true;
+}
+__device__ __forceinline__ uint32_t gap_exact(double lam, uint32_t w)
+{
     const double u = ((double)(w >> 9) + 0.5) * 0x1p-23;
     const double x = -log(u) / lam;
     if (!(x < 2147483646.0)) return 2147483647u;
     return 1u + (uint32_t)floor(x);
+}
+__device__ __forceinline__ uint32_t gap_steps(double lam, float lamf, uint32_t w)
+{
+    uint32_t g;
+    return gap_fast(lamf, w, g) ? g : gap_exact(lam, w);
 }
 
 // step of the first candidate of an e- or Ar+ that is first pushed at step l0

@@ -50,38 +50,130 @@ __device__ __forceinline__ void hist_add(unsigned long long* h, int nb, float x,
     atomicAdd(&h[b], 1ull);
 }
 
-// The event paths call their random draws, directions, Maxwellian samples,
-// candidate gaps and sputter launches out of line.  Frequent events (the
-// elastic collisions of electrons) keep that code in the instruction cache,
-// so a rare outcome -- an ionisation, an Ar+ collision, a sputtered atom --
-// fetches little code of its own; inlined, each rare path is a separate body
-// of code that is cold whenever it runs.
-__device__ __noinline__ uint4 ev_draw(uint64_t seed, uint64_t id, uint32_t step, uint32_t purpose)
+// value that marks a removed slot
+template <typename PosT> __device__ __forceinline__ PosT dead_value();
+template <> __device__ __forceinline__ uint32_t dead_value<uint32_t>() { return 0u; }
+template <> __device__ __forceinline__ double dead_value<double>() { return -1.0; }
+
+// ---------------------------------------------------------------- events
+// An event is a dependent chain, and the last events of a CTA decide when it
+// ends.  Each event therefore draws its Philox blocks two at a time
+// (interleaved rounds) and keeps the frequent work inline, while rare
+// outcomes -- an ionisation, an Ar+ collision or wall hit, the FP64 branch of
+// a candidate gap -- run out of line and call the shared out-of-line draws,
+// directions and samples.  Those stay in the instruction cache because the
+// frequent events use them, so a rare outcome fetches little code of its
+// own; inlined, each rare path would be a separate body of code that is cold
+// whenever it runs.
+struct U4x2 {
+    uint4 a, b;
+};
+// two Philox blocks under the seed's key with interleaved rounds
+__device__ __noinline__ U4x2 ev_draw2(uint64_t seed, uint64_t ida, uint32_t stepa, uint32_t pa, uint64_t idb,
+                                      uint32_t stepb, uint32_t pb)
 {
-    return draw(seed, id, step, purpose);
+    uint4 c[2];
+    c[0] = make_uint4((uint32_t)ida, (uint32_t)(ida >> 32), stepa, pa);
+    c[1] = make_uint4((uint32_t)idb, (uint32_t)(idb >> 32), stepb, pb);
+    philox_n<2>(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+    return U4x2{c[0], c[1]};
 }
 __device__ __noinline__ float3 ev_iso_dir(uint32_t a, uint32_t b) { return iso_dir(a, b); }
 __device__ __noinline__ float2 ev_box_muller(uint32_t a, uint32_t b) { return box_muller(a, b); }
-__device__ __noinline__ uint32_t ev_gap(double lam, float lamf, uint32_t w) { return gap_steps(lam, lamf, w); }
+__device__ __noinline__ uint32_t ev_gap_exact(double lam, uint32_t w) { return gap_exact(lam, w); }
+__device__ __forceinline__ uint32_t ev_gap(double lam, float lamf, uint32_t w)
+{
+    uint32_t g;
+    return gap_fast(lamf, w, g) ? g : ev_gap_exact(lam, w);
+}
 __device__ __noinline__ float3 ev_emit(float uE, float uT, float uP, float Emax, float dir)
 {
     return emit(uE, uT, uP, Emax, dir);
 }
-__device__ __forceinline__ uint32_t ev_entry_nev(const Dev& d, int s, uint64_t id, uint32_t l0)
+
+// Ionisation (Sec. "Particle Collisions"): the remaining energy eps - 15.8 eV
+// is split uniformly between the scattered and the ejected electron (ci: the
+// IONIZE words), and an e-/Ar+ pair is born at x^{l+1}, the ion from the gas
+// Maxwellian, each child with its first candidate step (births are pushed
+// from step l+1 on).  The slots are reserved first: their atomics are the
+// longest wait and overlap the draws.  Returns the scattered electron's speed.
+template <typename PosT>
+__device__ __noinline__ float ev_ionize(const Dev& d, uint4 ci, uint64_t id, uint32_t l, PosT xn, float eps,
+                                        long long born_e, long long born_i, uint3 cur,
+                                        unsigned long long* qe_dst, unsigned long long* qion, BlockTally* tally)
 {
-    return l0 - 1u + ev_gap(d.lam[s], d.lamf[s], ev_draw(d.seed, id, l0, kPurGap0).x);
+    const long long ie = born_e + (long long)atomicAdd((unsigned long long*)&d.ctl->births[kE], 1ull);
+    const long long ii = born_i + (long long)atomicAdd((unsigned long long*)&d.ctl->births[kI], 1ull);
+    const U4x2 nb = ev_draw2(d.seed, id, l, kPurNewIon, id, l, kPurBirthId);
+    const uint4 cn = nb.a, cb = nb.b;
+    const uint64_t ide = child_id(cb.x, cb.y, kE), idi = child_id(cb.z, cb.w, kI);
+    const U4x2 g0 = ev_draw2(d.seed, ide, l + 1, kPurGap0, idi, l + 1, kPurGap0);
+    const float epr = eps - (float)kIonTh;
+    const float e_ej = u23(ci.x) * epr;
+    const float vs = sqrtf((epr - e_ej) * (float)(2.0 * kQE / kME));
+    const float ve = sqrtf(e_ej * (float)(2.0 * kQE / kME));
+    const float3 d2 = ev_iso_dir(ci.y, ci.z);
+    const float2 n12 = ev_box_muller(cn.x, cn.y);
+    const float2 n34 = ev_box_muller(cn.z, cn.w);
+    atomicAdd(&tally->ioniz, 1u);
+    const bool in_e = ie < d.cap[kE], in_i = ii < d.cap[kI];
+    const SpBuf Be = d.buf[kE][cur.x];
+    const SpBuf Bi = d.buf[kI][cur.y];
+    if (!(in_e && in_i)) {
+        atomicAdd(&tally->capacity, 1u);
+        if (in_e) ((PosT*)Be.pos)[ie] = dead_value<PosT>();
+        if (in_i) ((PosT*)Bi.pos)[ii] = dead_value<PosT>();
+        return vs;
+    }
+    ((PosT*)Be.pos)[ie] = xn;
+    Be.vx[ie] = ve * d2.x; Be.vy[ie] = ve * d2.y; Be.vz[ie] = ve * d2.z;
+    Be.id[ie] = ide;
+    Be.nev[ie] = l + ev_gap(d.lam[kE], d.lamf[kE], g0.a.x);
+    ((PosT*)Bi.pos)[ii] = xn;
+    Bi.vx[ii] = d.vth_gas * n12.x; Bi.vy[ii] = d.vth_gas * n12.y; Bi.vz[ii] = d.vth_gas * n34.x;
+    Bi.id[ii] = idi;
+    Bi.nev[ii] = l + ev_gap(d.lam[kI], d.lamf[kI], g0.b.x);
+    uint32_t j, wr;
+    cell_of(xn, d.kshift, j, wr);
+    atomicAdd(&qe_dst[j], (1ull << 32) - wr);             // both children into this step's deposit
+    if (wr) atomicAdd(&qe_dst[j + 1], (unsigned long long)wr);
+    atomicAdd(&qion[j], (1ull << 32) - wr);
+    if (wr) atomicAdd(&qion[j + 1], (unsigned long long)wr);
+    return vs;
 }
 
-// Wall interaction of an Ar+ (Sec. "Wall Interaction"): energy and angle into
-// the IEDF / IEADF, then sputtered-atom launch (Sec. "Wall Interactions" of the
-// TPM: N = ceil(Y) trials with R <= Y/N, Thompson energy, cosine angle).
-__device__ void ion_wall(const Dev& d, uint64_t id, uint32_t l, int el, float vx, float vy, float vz,
-                         long long n_tp0, unsigned int cur_tp, BlockTally* tally)
+// Ar+ candidate against a gas partner w from the Maxwellian: sigma(eps) g is
+// the same constant for both channels, so R nu_max < nu_cx reduces exactly
+// to R < 1/2 (R on the 2^-23 grid + 1/2, never 1/2): CX gives v' = w,
+// isotropic scattering v' = (v + w)/2 + |v - w|/2 n.
+__device__ __noinline__ float3 ev_ion_collide(const Dev& d, uint4 c, uint64_t id, uint32_t l, float3 v,
+                                              BlockTally* tally)
+{
+    const U4x2 g = ev_draw2(d.seed, id, l, kPurGas, id, l, kPurGas);
+    const float2 n12 = ev_box_muller(g.a.x, g.a.y);
+    const float2 n34 = ev_box_muller(g.a.z, g.a.w);
+    const float wx = d.vth_gas * n12.x, wy = d.vth_gas * n12.y, wz = d.vth_gas * n34.x;
+    if (u23(c.y) < 0.5f) {
+        atomicAdd(&tally->cx, 1u);
+        return make_float3(wx, wy, wz);
+    }
+    const float gx = v.x - wx, gy = v.y - wy, gz = v.z - wz;
+    const float gm = sqrtf(gx * gx + gy * gy + gz * gz);
+    const float3 dir = ev_iso_dir(c.z, c.w);
+    atomicAdd(&tally->iso, 1u);
+    return make_float3(0.5f * (v.x + wx) + 0.5f * gm * dir.x, 0.5f * (v.y + wy) + 0.5f * gm * dir.y,
+                       0.5f * (v.z + wz) + 0.5f * gm * dir.z);
+}
+
+// Ar+ at a wall (Sec. "Wall Interaction"): energy and angle into the IEDF and
+// IEADF, then sputtered-atom launch (Sec. "Wall Interactions" of the TPM):
+// N = ceil(Y) trials with R <= Y/N, Thompson energy, cosine angle.
+__device__ __noinline__ void ev_ion_wall(const Dev& d, uint64_t id, uint32_t l, int el, float vx, float vy, float vz,
+                                         long long n_tp0, unsigned int cur_tp, BlockTally* tally)
 {
     const float v2 = vx * vx + vy * vy + vz * vz;
     const float E = v2 * (float)(0.5 * kMAR / kQE);
-    float ct = v2 > 0.0f ? fabsf(vx) * rsqrtf(v2) : 1.0f;
-    ct = fminf(ct, 1.0f);
+    const float ct = fminf(v2 > 0.0f ? fabsf(vx) * rsqrtf(v2) : 1.0f, 1.0f);
     const float th = acosf(ct) * (float)(180.0 / kPI);
     hist_add(d.diag.iedf[el], kNbIedf, E, d.Emax_hist);
     int be = (int)(E / d.Emax_hist * (float)kNbIeadfE);
@@ -92,19 +184,17 @@ __device__ void ion_wall(const Dev& d, uint64_t id, uint32_t l, int el, float vx
     atomicAdd(el == 0 ? &tally->imp_i[0] : &tally->imp_i[1], 1u);
     if (!d.sputter || !(E > (float)kSpTh)) return;
     const float Y = 0.1f * sqrtf(E / (float)kSpTh - 1.0f);
-    int Nt = (int)ceilf(Y);
-    Nt = Nt > kSpMaxN ? kSpMaxN : Nt;
+    const int Nt = min((int)ceilf(Y), kSpMaxN);
     const float Emax = lambda_ar_al() * E;
     const SpBuf T = d.buf[kTP][cur_tp];
     uint4 t = make_uint4(0, 0, 0, 0);
     for (int k = 0; k < Nt; ++k) {
-        if ((k & 3) == 0) t = ev_draw(d.seed, id, l, kPurSpTrial + (k >> 2));
+        if ((k & 3) == 0) t = ev_draw2(d.seed, id, l, kPurSpTrial + (k >> 2), id, l, kPurSpTrial + (k >> 2)).a;
         const uint32_t w = (k & 3) == 0 ? t.x : (k & 3) == 1 ? t.y : (k & 3) == 2 ? t.z : t.w;
         if (!(u23(w) <= Y / (float)Nt)) continue;
-        const uint4 ce = ev_draw(d.seed, id, l, kPurSpEmit + k);
-        const uint4 ci = ev_draw(d.seed, id, l, kPurSpId + k);
-        const float3 v = ev_emit(u23(ce.x), u23(ce.y), u23(ce.z), Emax, el == 0 ? 1.0f : -1.0f);
-        const long long idx = n_tp0 + atomicAdd((unsigned long long*)&d.ctl->births[kTP], 1ull);
+        const U4x2 es = ev_draw2(d.seed, id, l, kPurSpEmit + k, id, l, kPurSpId + k);
+        const float3 v = ev_emit(u23(es.a.x), u23(es.a.y), u23(es.a.z), Emax, el == 0 ? 1.0f : -1.0f);
+        const long long idx = n_tp0 + (long long)atomicAdd((unsigned long long*)&d.ctl->births[kTP], 1ull);
         if (idx >= d.cap[kTP]) {
             atomicAdd(&tally->capacity, 1u);
             continue;
@@ -113,114 +203,8 @@ __device__ void ion_wall(const Dev& d, uint64_t id, uint32_t l, int el, float vx
         T.vx[idx] = v.x;
         T.vy[idx] = v.y;
         T.vz[idx] = v.z;
-        T.id[idx] = child_id(ci.x, ci.y, kTP);
+        T.id[idx] = child_id(es.b.x, es.b.y, kTP);
         atomicAdd(el == 0 ? &tally->sput[0] : &tally->sput[1], 1u);
-    }
-}
-
-template <typename PosT>
-__device__ __forceinline__ void store_dead(PosT* P, long long i);
-template <>
-__device__ __forceinline__ void store_dead<uint32_t>(uint32_t* P, long long i) { P[i] = 0u; }
-template <>
-__device__ __forceinline__ void store_dead<double>(double* P, long long i) { P[i] = -1.0; }
-
-// Electron null-collision MCC (Sec. "Particle Collisions"): process chosen by
-// R nu_max against the cumulative nu_el, nu_exc, nu_ion at the electron's
-// energy; elastic and excitation scatter isotropically, ionisation splits the
-// remaining energy uniformly and creates an e-/Ar+ pair at x^{l+1}.
-template <typename PosT>
-__device__ void mcc_electron(const Dev& d, uint4 c, uint64_t id, uint32_t l, PosT xn, float& vx,
-                             float& vy, float& vz, long long born_e, long long born_i, uint3 cur,
-                             unsigned long long* qe_dst, unsigned long long* qion, BlockTally* tally)
-{
-    const float v2 = vx * vx + vy * vy + vz * vz;
-    const float v = sqrtf(v2);
-    const float eps = v2 * (float)(0.5 * kME / kQE);
-    if (eps > d.eps_max) atomicAdd(&tally->numerics, 1u);
-    const float s_exc = eps > (float)kExcTh ? (float)kExcSig * (1.0f - (float)kExcTh / eps) : 0.0f;
-    const float s_ion = eps > (float)kIonTh
-                            ? (float)(kLotzA * kLotzQ) * logf(eps / (float)kIonTh) / (eps * (float)kIonTh)
-                            : 0.0f;
-    const float nu_el = d.ngas_f * (float)kSigEl * v;
-    const float nu_exc = d.ngas_f * s_exc * v;
-    const float nu_ion = d.ngas_f * s_ion * v;
-    const float r = u23(c.y) * d.nu_max_e;
-    const float3 dir = ev_iso_dir(c.z, c.w);
-    if (r < nu_el) {
-        const float cchi = v > 0.0f ? (dir.x * vx + dir.y * vy + dir.z * vz) / v : 1.0f;
-        const float fac = 1.0f - (float)(2.0 * kME / kMAR) * (1.0f - cchi);
-        const float vn = v * sqrtf(fac);
-        vx = vn * dir.x; vy = vn * dir.y; vz = vn * dir.z;
-        atomicAdd(&tally->elastic, 1u);
-    } else if (r < nu_el + nu_exc) {
-        const float vn = sqrtf((eps - (float)kExcTh) * (float)(2.0 * kQE / kME));
-        vx = vn * dir.x; vy = vn * dir.y; vz = vn * dir.z;
-        atomicAdd(&tally->excit, 1u);
-    } else if (r < nu_el + nu_exc + nu_ion) {
-        const float epr = eps - (float)kIonTh;
-        const uint4 ci = ev_draw(d.seed, id, l, kPurIonize);
-        const uint4 cn = ev_draw(d.seed, id, l, kPurNewIon);
-        const uint4 cb = ev_draw(d.seed, id, l, kPurBirthId);
-        const float e_ej = u23(ci.x) * epr;
-        const float e_sc = epr - e_ej;
-        const float vs = sqrtf(e_sc * (float)(2.0 * kQE / kME));
-        const float ve = sqrtf(e_ej * (float)(2.0 * kQE / kME));
-        const float3 d2 = ev_iso_dir(ci.y, ci.z);
-        const float2 n12 = ev_box_muller(cn.x, cn.y);
-        const float2 n34 = ev_box_muller(cn.z, cn.w);
-        vx = vs * dir.x; vy = vs * dir.y; vz = vs * dir.z;
-        atomicAdd(&tally->ioniz, 1u);
-        const long long ie = born_e + atomicAdd((unsigned long long*)&d.ctl->births[kE], 1ull);
-        const long long ii = born_i + atomicAdd((unsigned long long*)&d.ctl->births[kI], 1ull);
-        const bool ok = ie < d.cap[kE] && ii < d.cap[kI];
-        const SpBuf Be = d.buf[kE][cur.x];
-        const SpBuf Bi = d.buf[kI][cur.y];
-        if (!ok) {
-            atomicAdd(&tally->capacity, 1u);
-            if (ie < d.cap[kE]) store_dead((PosT*)Be.pos, ie);
-            if (ii < d.cap[kI]) store_dead((PosT*)Bi.pos, ii);
-            return;
-        }
-        ((PosT*)Be.pos)[ie] = xn;
-        Be.vx[ie] = ve * d2.x; Be.vy[ie] = ve * d2.y; Be.vz[ie] = ve * d2.z;
-        const uint64_t ide = child_id(cb.x, cb.y, kE), idi = child_id(cb.z, cb.w, kI);
-        Be.id[ie] = ide;
-        Be.nev[ie] = ev_entry_nev(d, kE, ide, l + 1);            // births are pushed from step l+1 on
-        ((PosT*)Bi.pos)[ii] = xn;
-        Bi.vx[ii] = d.vth_gas * n12.x; Bi.vy[ii] = d.vth_gas * n12.y; Bi.vz[ii] = d.vth_gas * n34.x;
-        Bi.id[ii] = idi;
-        Bi.nev[ii] = ev_entry_nev(d, kI, idi, l + 1);
-        uint32_t j, wr;
-        cell_of(xn, d.kshift, j, wr);
-        atomicAdd(&qe_dst[j], (1ull << 32) - wr);             // electron child: global histogram
-        if (wr) atomicAdd(&qe_dst[j + 1], (unsigned long long)wr);
-        atomicAdd(&qion[j], (1ull << 32) - wr);               // ion child: global histogram
-        if (wr) atomicAdd(&qion[j + 1], (unsigned long long)wr);
-    }
-}
-
-// Ar+ null-collision MCC against a Maxwellian gas partner.  sigma(eps) g is
-// the same constant for both channels, so the selection R nu_max < nu_cx
-// reduces exactly to R < 1/2 (R sits on the 2^-23 grid + 1/2, never at 1/2).
-__device__ __forceinline__ void mcc_ion(const Dev& d, uint4 c, uint64_t id, uint32_t l, float& vx,
-                                        float& vy, float& vz, BlockTally* tally)
-{
-    const uint4 cg = ev_draw(d.seed, id, l, kPurGas);
-    const float2 n12 = ev_box_muller(cg.x, cg.y);
-    const float2 n34 = ev_box_muller(cg.z, cg.w);
-    const float wx = d.vth_gas * n12.x, wy = d.vth_gas * n12.y, wz = d.vth_gas * n34.x;
-    if (u23(c.y) < 0.5f) {
-        vx = wx; vy = wy; vz = wz;
-        atomicAdd(&tally->cx, 1u);
-    } else {
-        const float gx = vx - wx, gy = vy - wy, gz = vz - wz;
-        const float gm = sqrtf(gx * gx + gy * gy + gz * gz);
-        const float3 dir = ev_iso_dir(c.z, c.w);
-        vx = 0.5f * (vx + wx) + 0.5f * gm * dir.x;
-        vy = 0.5f * (vy + wy) + 0.5f * gm * dir.y;
-        vz = 0.5f * (vz + wz) + 0.5f * gm * dir.z;
-        atomicAdd(&tally->iso, 1u);
     }
 }
 
@@ -297,9 +281,6 @@ __device__ __forceinline__ void f4set(float4& v, int u, float x)
 
 __device__ __forceinline__ long long round4(long long n) { return (n + 3) & ~3ll; }
 
-template <typename PosT> __device__ __forceinline__ PosT dead_value();
-template <> __device__ __forceinline__ uint32_t dead_value<uint32_t>() { return 0u; }
-template <> __device__ __forceinline__ double dead_value<double>() { return -1.0; }
 
 // Shared-memory accumulators of one CTA.  The linear weights are summed per
 // cell in three 32-bit counters -- particles n_j, and the high and low 16 bits
@@ -382,7 +363,12 @@ __device__ __forceinline__ void deposit_group(const Acc& A, const bool (&dep)[4]
     }
 }
 
-// one queued event: a wall hit (both species) or a collision candidate
+// One queued event: a collision candidate of either species (Sec. "Particle
+// Collisions"), or an Ar+ wall hit.  e- candidates: the process by R nu_max
+// against the cumulative nu_el, nu_exc, nu_ion at the electron's energy;
+// isotropic scattering; elastic loss 2 m_e/M (1 - cos chi); excitation
+// -11.5 eV; ionisation in ev_ionize.  Every candidate draws the step of its
+// next candidate.
 template <typename PosT>
 __device__ __noinline__ void handle_event(const Dev& d, int s, long long i, uint32_t kind, uint32_t l,
                                           long long born_e, long long born_i, long long ntp, uint3 cur,
@@ -392,22 +378,52 @@ __device__ __noinline__ void handle_event(const Dev& d, int s, long long i, uint
     const SpBuf B = d.buf[s][s == kE ? cur.x : cur.y];
     float vx = B.vx[i], vy = B.vy[i], vz = B.vz[i];
     const uint64_t id = B.id[i];
-    if (kind == kEvCand) {
-        const uint4 c = ev_draw(d.seed, id, l, kPurColl);
-        B.nev[i] = l + ev_gap(d.lam[s], d.lamf[s], ev_draw(d.seed, id, l, kPurGap).x);
-        if (s == kE)
-            mcc_electron<PosT>(d, c, id, l, ((const PosT*)B.pos)[i], vx, vy, vz, born_e, born_i, cur, qe_dst,
-                               qion, tally);
-        else
-            mcc_ion(d, c, id, l, vx, vy, vz, tally);
-        B.vx[i] = vx;
-        B.vy[i] = vy;
-        B.vz[i] = vz;
-    } else {
+    if (kind != kEvCand) {
         const int el = kind == kEvWallL ? 0 : 1;
-        if (s == kI) ion_wall(d, id, l, el, vx, vy, vz, ntp, cur.z, tally);
-        else atomicAdd(&tally->imp_e[el], 1u);
+        if (s == kI) ev_ion_wall(d, id, l, el, vx, vy, vz, ntp, cur.z, tally);
+        else atomicAdd(&tally->imp_e[el], 1u);          // (electrons at a wall are counted in the stream)
+        return;
     }
+    const U4x2 cg = ev_draw2(d.seed, id, l, kPurColl, id, l, kPurGap);
+    const uint4 c = cg.a;
+    B.nev[i] = l + ev_gap(d.lam[s], d.lamf[s], cg.b.x);
+    if (s == kE) {
+        const float v2 = vx * vx + vy * vy + vz * vz;
+        const float v = sqrtf(v2);
+        const float eps = v2 * (float)(0.5 * kME / kQE);
+        if (eps > d.eps_max) atomicAdd(&tally->numerics, 1u);
+        const float s_exc = eps > (float)kExcTh ? (float)kExcSig * (1.0f - (float)kExcTh / eps) : 0.0f;
+        const float s_ion = eps > (float)kIonTh
+                                ? (float)(kLotzA * kLotzQ) * logf(eps / (float)kIonTh) / (eps * (float)kIonTh)
+                                : 0.0f;
+        const float nu_el = d.ngas_f * (float)kSigEl * v;
+        const float nu_exc = d.ngas_f * s_exc * v;
+        const float nu_ion = d.ngas_f * s_ion * v;
+        const float r = u23(c.y) * d.nu_max_e;
+        const float3 dir = iso_dir(c.z, c.w);
+        float vn = -1.0f;
+        if (r < nu_el) {
+            const float cchi = v > 0.0f ? (dir.x * vx + dir.y * vy + dir.z * vz) / v : 1.0f;
+            vn = v * sqrtf(1.0f - (float)(2.0 * kME / kMAR) * (1.0f - cchi));
+            atomicAdd(&tally->elastic, 1u);
+        } else if (r < nu_el + nu_exc) {
+            vn = sqrtf((eps - (float)kExcTh) * (float)(2.0 * kQE / kME));
+            atomicAdd(&tally->excit, 1u);
+        } else if (r < nu_el + nu_exc + nu_ion) {
+            const uint4 ci = ev_draw2(d.seed, id, l, kPurIonize, id, l, kPurIonize).a;
+            vn = ev_ionize<PosT>(d, ci, id, l, ((const PosT*)B.pos)[i], eps, born_e, born_i, cur, qe_dst, qion,
+                                 tally);
+        }
+        if (vn >= 0.0f) {
+            vx = vn * dir.x; vy = vn * dir.y; vz = vn * dir.z;
+        }
+    } else {
+        const float3 nv = ev_ion_collide(d, c, id, l, make_float3(vx, vy, vz), tally);
+        vx = nv.x; vy = nv.y; vz = nv.z;
+    }
+    B.vx[i] = vx;
+    B.vy[i] = vy;
+    B.vz[i] = vz;
 }
 
 template <bool P64>
@@ -490,6 +506,7 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d,
     const unsigned int l = a.step;              // the host's step count (equal to ctl->step)
     Ctl* ctl = d.ctl;
     const long long ne = ctl->n[kE], ni = ctl->n[kI], ntp = ctl->n[kTP];
+    const unsigned int field_override = MODE == 0 ? ctl->field_override : 0u;
     if (MODE == 0) {
         // both deposits of x^l (slot l%3) into shared memory: asynchronous
         // 16-byte copies, all in flight at once (arrays 256-byte aligned, padded)
@@ -564,7 +581,7 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d,
                 d.fbuf[z][kI][i] = 0;
             }
             // field of step l: every CTA solves from the deposit of x^l
-            if (ctl->field_override) {
+            if (field_override) {
                 for (int i = t; i < N1; i += nt) sE[i] = d.E32[i];
             } else {
                 block_field_f32(d, sqe, sqi, sE, a);
