@@ -548,18 +548,14 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d,
     if (g < tile1_first) nxt = load_group<P64, MODE>(B, g);
     if (tr && threadIdx.x == 0) tr[11] = gtimer();
 
-    if (MODE == 0) asm volatile("cp.async.wait_all;\n" ::: "memory");
-    __syncthreads();
-    if (tr && threadIdx.x == 0) tr[1] = gtimer();
     {
-        // clear the tile sums; this CTA's share of the time averages and of
-        // clearing slot (l+2)%3
+        // work that needs no deposit, while its copies are in flight: clear the
+        // tile sums (cnt, whi, wlo, flo, fhi are contiguous) and the EEDF tally,
+        // and this CTA's share of slot (l+2)%3 (read by the previous launch,
+        // deposited into by the next)
         const int t = threadIdx.x, nt = blockDim.x;
-        for (int m = t; m <= N; m += nt) {
-            if (m < N) A.cnt[m] = A.whi[m] = A.wlo[m] = 0;
-            A.flo[m] = 0;
-            A.fhi[m] = 0;
-        }
+        uint4* z4 = (uint4*)A.cnt;
+        for (int k = t; k < (int)(acc_bytes(N) / 16); k += nt) z4[k] = make_uint4(0u, 0u, 0u, 0u);
         for (int i = t; i < kNbEedf; i += nt) seedf[i] = 0;
         if (t == 0) {
             tally = BlockTally{};
@@ -572,20 +568,24 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d,
         }
         if (MODE == 0) {
             const int m0 = N1 * blockIdx.x / G, m1 = N1 * (blockIdx.x + 1) / G;
-            if (a.accumulate) accumulate_nodes(d, l, sqe, sqi, m0, m1, a.v_left, blockIdx.x == 0, t, nt);
-            const int z = (l + 2) % 3;             // read by the previous launch; cleared for the next
+            const int z = (l + 2) % 3;
             for (int i = m0 + t; i < m1; i += nt) {
                 d.qbuf[z][kE][i] = 0;
                 d.qbuf[z][kI][i] = 0;
                 d.fbuf[z][kE][i] = 0;
                 d.fbuf[z][kI][i] = 0;
             }
-            // field of step l: every CTA solves from the deposit of x^l
-            if (field_override) {
-                for (int i = t; i < N1; i += nt) sE[i] = d.E32[i];
-            } else {
-                block_field_f32(d, sqe, sqi, sE, a);
-            }
+        }
+    }
+    if (MODE == 0) asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();
+    if (tr && threadIdx.x == 0) tr[1] = gtimer();
+    if (MODE == 0) {
+        // field of step l: every CTA solves from the deposit of x^l
+        if (field_override) {
+            for (int i = threadIdx.x; i < N1; i += blockDim.x) sE[i] = d.E32[i];
+        } else {
+            block_field_f32(d, sqe, sqi, sE, a);
         }
     }
     __syncthreads();
@@ -776,6 +776,10 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d,
         const unsigned long long tf = tr ? gtimer() : 0ull;
         flush_tile(A, N, s_jlo, s_jhi, sample, qdst, fdst, false, t, nt);
         if (tr) atomicMax(&s_flushns, gtimer() - tf);
+        if (MODE == 0 && a.accumulate) {         // this CTA's share of the time averages of step l
+            const int m0 = N1 * blockIdx.x / G, m1 = N1 * (blockIdx.x + 1) / G;
+            accumulate_nodes(d, l, sqe, sqi, m0, m1, a.v_left, blockIdx.x == 0, t, nt);
+        }
     }
     if (MODE == 0 && s_overflow) {
         const long long chunk1 = min(4 * cg1, ns);
