@@ -352,13 +352,26 @@ __device__ __forceinline__ void deposit_group(const Acc& A, const bool (&dep)[4]
         }
     }
     if (sample) {
+        if (one) {                            // four particles of one cell: one pair of sums
+            long long f0 = 0, f1 = 0;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            if (!dep[u]) continue;
-            const long long vq = (long long)__float2int_rn(vx[u]);
-            const long long w16 = (long long)(wr[u] >> 16);
-            acc_add64(A.flo, A.fhi, j[u], vq * (65536 - w16));
-            acc_add64(A.flo, A.fhi, j[u] + 1, vq * w16);
+            for (int u = 0; u < 4; ++u) {
+                const long long vq = (long long)__float2int_rn(vx[u]);
+                const long long w16 = (long long)(wr[u] >> 16);
+                f0 += vq * (65536 - w16);
+                f1 += vq * w16;
+            }
+            acc_add64(A.flo, A.fhi, j[0], f0);
+            acc_add64(A.flo, A.fhi, j[0] + 1, f1);
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (!dep[u]) continue;
+                const long long vq = (long long)__float2int_rn(vx[u]);
+                const long long w16 = (long long)(wr[u] >> 16);
+                acc_add64(A.flo, A.fhi, j[u], vq * (65536 - w16));
+                acc_add64(A.flo, A.fhi, j[u] + 1, vq * w16);
+            }
         }
     }
 }
@@ -431,16 +444,21 @@ struct Grp {                   // one group of four slots, as loaded
     Pos4<P64> p;
     float4 v;
     uint4 nv;                  // steps of the next candidate
+    float4 vy, vz;             // electrons on sample steps (EEDF)
 };
 
-template <bool P64, int MODE>
-__device__ __forceinline__ Grp<P64> load_group(const SpBuf& B, long long g)
+template <bool P64, int MODE, bool SAMPLE>
+__device__ __forceinline__ Grp<P64> load_group(const SpBuf& B, long long g, bool eedf)
 {
     Grp<P64> G;
     G.p.load(B.pos, g);
     if (MODE == 0) {
         G.v = ((const float4*)B.vx)[g];
         G.nv = ((const uint4*)B.nev)[g];
+        if (SAMPLE && eedf) {
+            G.vy = ((const float4*)B.vy)[g];
+            G.vz = ((const float4*)B.vz)[g];
+        }
     }
     return G;
 }
@@ -475,7 +493,7 @@ __device__ void flush_tile(const Acc& A, int N, unsigned int jlo, unsigned int j
 // after a state upload).  Slots are streamed in groups of four with 16-byte
 // vector loads and stores; consecutive threads take consecutive groups and
 // each thread loads its next group before working on the current one.
-template <bool P64, int MODE>
+template <bool P64, int MODE, bool SAMPLE>
 __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d, StepArgs a)
 {
     using PosT = typename std::conditional<P64, double, uint32_t>::type;
@@ -520,7 +538,9 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d,
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src) : "memory");
         }
     }
-    const bool sample = MODE == 0 && d.diag_every > 0 && ((l + 1) % (unsigned)d.diag_every == 0);
+    // sample steps (flux moment, EEDF) are a separate instantiation: the host
+    // launches it when (l + 1) % diag_every == 0
+    constexpr bool sample = MODE == 0 && SAMPLE;
     const int G = gridDim.x;
     const int Ge = electron_ctas(ne, ni, G);
     const int s = (int)blockIdx.x < Ge ? kE : kI;
@@ -545,7 +565,7 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d,
     long long g = cg0 + threadIdx.x;
     const long long tile1_first = min(cg1, cg0 + kTileGroups);
     Grp<P64> nxt;
-    if (g < tile1_first) nxt = load_group<P64, MODE>(B, g);
+    if (g < tile1_first) nxt = load_group<P64, MODE, SAMPLE>(B, g, s == kE);
     if (tr && threadIdx.x == 0) tr[11] = gtimer();
 
     {
@@ -621,13 +641,13 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d,
             jlo = 0xffffffffu;
             jhi = 0;
             g = t0 + threadIdx.x;
-            if (g < t1) nxt = load_group<P64, MODE>(B, g);
+            if (g < t1) nxt = load_group<P64, MODE, SAMPLE>(B, g, s == kE);
             __syncthreads();
         }
         while (g < t1) {
             Grp<P64> Gc = nxt;
             const long long gn = g + T;
-            if (gn < t1) nxt = load_group<P64, MODE>(B, gn);
+            if (gn < t1) nxt = load_group<P64, MODE, SAMPLE>(B, gn, s == kE);
             const long long rem64 = ns - 4 * g;       // slots of this group below the slot count
             const int rem = rem64 >= 4 ? 4 : (int)rem64;
             PosT x[4];
@@ -714,7 +734,7 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d,
                     if (P64) inwin = (double)xn[u] >= d.eedf_lo64 && (double)xn[u] < d.eedf_hi64;
                     else inwin = (uint32_t)xn[u] >= d.eedf_lo && (uint32_t)xn[u] < d.eedf_hi;
                     if (inwin) {
-                        const float vy = B.vy[4 * g + u], vz = B.vz[4 * g + u];
+                        const float vy = f4get(Gc.vy, u), vz = f4get(Gc.vz, u);
                         const float en = (vx[u] * vx[u] + vy * vy + vz * vz) * (float)(0.5 * kME / kQE);
                         int bb = (int)(en * 4.0f);
                         bb = bb < 0 ? 0 : (bb > kNbEedf - 1 ? kNbEedf - 1 : bb);
@@ -1008,28 +1028,30 @@ static cudaError_t set_smem_attr(const void* fn, size_t bytes)
 cudaError_t mover_occupancy(const Dev& d, int* blocks_per_sm)
 {
     const size_t sm = mover_smem(d.ncell);
-    const void* fn = d.pos64 ? (const void*)k_mover<true, 0> : (const void*)k_mover<false, 0>;
+    const void* fn = d.pos64 ? (const void*)k_mover<true, 0, false> : (const void*)k_mover<false, 0, false>;
     cudaError_t e = set_smem_attr(fn, sm);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kMoverThreads, sm);
 }
 
-cudaError_t launch_mover(const Dev& d, const StepArgs& a, int grid, int mode, cudaStream_t st)
+template <bool P64>
+static cudaError_t launch_mover_t(const Dev& d, const StepArgs& a, int grid, int mode, cudaStream_t st)
 {
     const size_t sm = mover_smem(d.ncell);
-    const void* fn;
-    if (d.pos64) fn = mode == 0 ? (const void*)k_mover<true, 0> : (const void*)k_mover<true, 1>;
-    else fn = mode == 0 ? (const void*)k_mover<false, 0> : (const void*)k_mover<false, 1>;
+    const bool sample = mode == 0 && d.diag_every > 0 && (a.step + 1u) % (unsigned)d.diag_every == 0;
+    const void* fn = mode == 1 ? (const void*)k_mover<P64, 1, false>
+                               : (sample ? (const void*)k_mover<P64, 0, true> : (const void*)k_mover<P64, 0, false>);
     cudaError_t e = set_smem_attr(fn, sm);
     if (e != cudaSuccess) return e;
-    if (d.pos64) {
-        if (mode == 0) k_mover<true, 0><<<grid, kMoverThreads, sm, st>>>(d, a);
-        else k_mover<true, 1><<<grid, kMoverThreads, sm, st>>>(d, a);
-    } else {
-        if (mode == 0) k_mover<false, 0><<<grid, kMoverThreads, sm, st>>>(d, a);
-        else k_mover<false, 1><<<grid, kMoverThreads, sm, st>>>(d, a);
-    }
+    if (mode == 1) k_mover<P64, 1, false><<<grid, kMoverThreads, sm, st>>>(d, a);
+    else if (sample) k_mover<P64, 0, true><<<grid, kMoverThreads, sm, st>>>(d, a);
+    else k_mover<P64, 0, false><<<grid, kMoverThreads, sm, st>>>(d, a);
     return cudaGetLastError();
+}
+
+cudaError_t launch_mover(const Dev& d, const StepArgs& a, int grid, int mode, cudaStream_t st)
+{
+    return d.pos64 ? launch_mover_t<true>(d, a, grid, mode, st) : launch_mover_t<false>(d, a, grid, mode, st);
 }
 
 cudaError_t launch_entry_nev(const Dev& d, int s, unsigned int half, long long n, unsigned int l0, cudaStream_t st)
