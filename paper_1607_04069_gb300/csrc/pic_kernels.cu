@@ -648,19 +648,22 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d,
             Grp<P64> Gc = nxt;
             const long long gn = g + T;
             if (gn < t1) nxt = load_group<P64, MODE, SAMPLE>(B, gn, s == kE);
-            const long long rem64 = ns - 4 * g;       // slots of this group below the slot count
-            const int rem = rem64 >= 4 ? 4 : (int)rem64;
+            if (4 * g + 4 > ns) {                     // the species' last group: slots past n are removed
+                const int rem = (int)(ns - 4 * g);
+#pragma unroll
+                for (int u = 1; u < 4; ++u)
+                    if (u >= rem) Gc.p.set(u, dead);
+            }
             PosT x[4];
             bool act[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 x[u] = Gc.p.get(u);
-                act[u] = is_alive(x[u]) && u < rem;
+                act[u] = is_alive(x[u]);
                 if (P64 && act[u] && !((double)x[u] < (double)N)) {
                     act[u] = false;
                     atomicOr(&ctl->err, kErrIndex);
                 }
-                if (u >= rem) Gc.p.set(u, dead);
             }
             uint32_t j[4], wr[4];
             bool dep[4];
@@ -686,8 +689,8 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d,
             const uint32_t nv[4] = {Gc.nv.x, Gc.nv.y, Gc.nv.z, Gc.nv.w};
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                uint32_t jj, ww;
-                cell_of(act[u] ? x[u] : (PosT)(P64 ? 0.5 : 1.0), d.kshift, jj, ww);
+                uint32_t jj, ww;                       // (32-bit: a removed slot, 0, reads cell 0)
+                cell_of(P64 && !act[u] ? (PosT)0.5 : x[u], d.kshift, jj, ww);
                 const float2 e = sEd[jj];
                 const float f = __uint_as_float(0x3f800000u | (ww >> 9)) - 1.0f;
                 vx[u] = vx[u] + qmdt * (e.x + f * e.y);
@@ -705,25 +708,29 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d,
                 }
             }
             uint32_t evm = 0;                          // bit u: slot u goes to the event queue
+            uint32_t wlm = 0, wrm = 0;                 // bit u: slot u left at x = 0 / x = L
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 dep[u] = act[u] && kind[u] == 0xffffffffu;
-                cell_of(dep[u] ? xn[u] : (PosT)(P64 ? 0.5 : 1.0), d.kshift, j[u], wr[u]);
+                // (32-bit: a position that left the gap wrapped around and still names a cell)
+                cell_of(P64 && !dep[u] ? (PosT)0.5 : xn[u], d.kshift, j[u], wr[u]);
                 Gc.p.set(u, dep[u] ? xn[u] : dead);
-                if (dep[u]) {
-                    jlo = min(jlo, j[u]);
-                    jhi = max(jhi, j[u]);
-                }
+                jlo = min(jlo, dep[u] ? j[u] : 0xffffffffu);
+                jhi = max(jhi, dep[u] ? j[u] : 0u);
                 const bool wall = act[u] && !dep[u];
                 const bool cand = dep[u] && (int)(nv[u] - l) <= 0;
                 if (cand) kind[u] = kEvCand;
-                if (s == kE) {                        // an electron at a wall is only counted
-                    imp_l += (wall && kind[u] == kEvWallL) ? 1u : 0u;
-                    imp_r += (wall && kind[u] == kEvWallR) ? 1u : 0u;
-                    evm |= cand ? 1u << u : 0u;
-                } else {
-                    evm |= (cand || wall) ? 1u << u : 0u;
+                wlm |= (wall && kind[u] == kEvWallL) ? 1u << u : 0u;
+                wrm |= (wall && kind[u] == kEvWallR) ? 1u << u : 0u;
+                evm |= cand ? 1u << u : 0u;
+            }
+            if (s == kE) {                             // an electron at a wall is only counted
+                if (wlm | wrm) {
+                    imp_l += __popc(wlm);
+                    imp_r += __popc(wrm);
                 }
+            } else {
+                evm |= wlm | wrm;
             }
             deposit_group(A, dep, j, wr, vx, sample);
             if (sample && s == kE) {
