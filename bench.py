@@ -184,7 +184,8 @@ def run_reference(args, ws, rank):
     if rank != 0:
         return
     cfg = workload(args.n_per_species, 1236)
-    n_sample = args.ref_sample
+    # bounded sample: about 6e7 particle-steps in all, so any --steps ends within minutes
+    n_sample = max(2000, min(args.ref_sample, int(3e7 / max(args.steps + args.warmup, 1))))
     rate, dt = oracle_rate(cfg, n_sample, args.steps, warmup=args.warmup)
     line = {"impl": "reference", "metric": "particle-steps/s", "value": rate, "unit": "particle-steps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
