@@ -157,7 +157,11 @@ def allreduce_sum(x, ws):
 def workload(n_per_species, seed):
     from paper_1607_04069_gb300 import workloads as W
     cfg = W.ccp_sputter(n_per_species=n_per_species, seed=seed)
-    cfg.update(sort_every_e=25, sort_every_i=200, sort_every_tp=50)
+    # compaction every 400 steps: it restores the cell order the Ar+ deposit
+    # profits from and removes the holes left by absorbed particles; electrons
+    # lose their order within a few steps, so compacting them more often only
+    # costs time
+    cfg.update(sort_every_e=400, sort_every_i=400, sort_every_tp=50)
     return cfg
 
 
@@ -184,8 +188,9 @@ def run_reference(args, ws, rank):
     if rank != 0:
         return
     cfg = workload(args.n_per_species, 1236)
-    # bounded sample: about 6e7 particle-steps in all, so any --steps ends within minutes
-    n_sample = max(2000, min(args.ref_sample, int(3e7 / max(args.steps + args.warmup, 1))))
+    # bounded sample: about 3e9 particle-steps in all (some 20 s on one core), so any
+    # --steps ends within minutes
+    n_sample = max(2000, min(args.ref_sample, int(1.5e9 / max(args.steps + args.warmup, 1))))
     rate, dt = oracle_rate(cfg, n_sample, args.steps, warmup=args.warmup)
     line = {"impl": "reference", "metric": "particle-steps/s", "value": rate, "unit": "particle-steps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -207,7 +212,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=30)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n-per-species", type=int, default=2_000_000)
-    ap.add_argument("--ref-sample", type=int, default=100_000)
+    ap.add_argument("--ref-sample", type=int, default=2_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=300)
     args = ap.parse_args()
@@ -311,11 +316,11 @@ def main():
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        n_sample = 500_000
-        rate, dt = oracle_rate(cfg, n_sample, 20)
+        n_sample, nst = cfg["n_e0"], 400            # the full discharge, 400 steps: some 10-20 s
+        rate, dt = oracle_rate(cfg, n_sample, nst)
         cpu = {"value": rate, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-               "sample": f"{n_sample}+{n_sample} superparticles of the same discharge (weight x4), "
-                         f"20 full PIC/MCC steps in {dt:.1f} s"}
+               "sample": f"{n_sample}+{n_sample} superparticles of the same discharge, "
+                         f"{nst} full PIC/MCC steps in {dt:.1f} s"}
     clocks = clk.summary()
     launches = mover_n + tp_n + 3 * cmp_n
     if rank == 0:
@@ -324,7 +329,7 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
                 "config": {"workload": cfg["name"], "particles_per_gpu": int(n_start),
-                           "n_cells": cfg["n_cells"], "sort_every": [25, 200], "tp_every": 40,
+                           "n_cells": cfg["n_cells"], "sort_every": [400, 400], "tp_every": 40,
                            "parallelism": f"replicas x{ws}" if ws > 1 else "1 gpu",
                            "l2": "flushed before every timed step (512 MiB write, then a 256 MiB "
                                  "read); value from per-step CUDA events",

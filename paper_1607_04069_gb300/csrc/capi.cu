@@ -427,6 +427,12 @@ int pic_create(const pic_params* pin, void* stream, pic_ctx** out)
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d.ctl, &h, sizeof h, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = launch_init(c->d, kE, c->p.n_e0, (float)std::sqrt(c->p.te0_ev * kQE / kME), c->stream);
     if (e == cudaSuccess) e = launch_init(c->d, kI, c->p.n_i0, (float)std::sqrt(c->p.ti0_ev * kQE / kMAR), c->stream);
+    // the loading is uniform in space but in id order: bring it into cell order
+    for (int sp = 0; sp < 2 && e == cudaSuccess; ++sp) {
+        if ((sp == kE ? c->p.n_e0 : c->p.n_i0) <= 0) continue;
+        e = launch_sort(c->d, sp, c->grid_sort, c->stream);
+        c->cur[sp] ^= 1u;
+    }
     if (e == cudaSuccess) e = launch_mover(c->d, step_args(c, 0, 0), c->grid_mover, 1, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
