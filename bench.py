@@ -184,6 +184,60 @@ def oracle_rate(cfg, n_sample, steps, warmup=1):
     return (cnt["n_e"] + cnt["n_i"]) * steps / dt, dt
 
 
+def measure_rows(d, cfg, peak, cmp_ms, cmp_n, nsort_particles, n_atoms):
+    """Per-row measurements besides the fused step kernel: test-particle flight
+    (a separate run of n_atoms atoms, far larger than L2), compaction, and the
+    FP64 field solve of the diagnostics."""
+    import torch
+    import paper_1607_04069_gb300 as P
+    from paper_1607_04069_gb300 import workloads as W
+    rows = {}
+    # a8: TP flight, one kernel per TP step
+    tc = W.tp_transport(n_atoms=n_atoms)
+    tc.update(cap_tp=n_atoms + 1024, n_e0=0, n_i0=0, sort_every_tp=0)
+    t = P.Discharge(P.params_from_workload(tc))
+    t.tp_launch(n_atoms, 300.0)
+    t.tp_step(3, count_alive=False)
+    t.sync()
+    t.timing(True)
+    t.tp_step(20, count_alive=False)
+    t.sync()
+    ms, n = t.kernel_time("tp")
+    t.close()
+    per = ms / n * 1e-3
+    tp_bytes = 28       # read x, v_x, v_y, v_z, id (24 B); write x (4 B); velocities only on collision
+    ach = tp_bytes * n_atoms / per / 1e9
+    rows["a8_tp_step"] = {"workload": "tp_transport: %d Al atoms, 0.5 Pa 300 K Ar, dt 1 ns" % n_atoms,
+                          "value": n_atoms / per, "unit": "atom-steps/s", "mean_launch_us": per * 1e6,
+                          "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                                       "frac": ach / peak, "algorithmic_bytes_per_atom_step": tp_bytes}}
+    # a9: compaction (counting sort by cell of one species) in the timed run
+    if cmp_n:
+        per_sort = cmp_ms / cmp_n * 1e-3
+        sb = 2 * 28 + 4       # read + write x, v_x, v_y, v_z, id, next-candidate step; one count pass
+        ach = sb * nsort_particles / per_sort / 1e9
+        rows["a9_compaction"] = {"value": nsort_particles / per_sort, "unit": "particles/s",
+                                 "mean_sort_us": per_sort * 1e6,
+                                 "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                                              "frac": ach / peak, "algorithmic_bytes_per_particle": sb}}
+    # a7 (diagnostic form): FP64 Thomas-equivalent solve of the current deposit, one CTA
+    f = d.get_field()
+    qi = torch.tensor(f["q_i"], device="cuda")
+    qe = torch.tensor(f["q_e"], device="cuda")
+    dx = cfg["gap_m"] / cfg["n_cells"]
+    for _ in range(3):
+        P.op_poisson(qi, qe, cfg["n_cells"], dx, cfg["weight"], 0.0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(20):
+        P.op_poisson(qi, qe, cfg["n_cells"], dx, cfg["weight"], 0.0)
+    e1.record()
+    torch.cuda.synchronize()
+    rows["a7_poisson_fp64"] = {"value": e0.elapsed_time(e1) / 20 * 1e3, "unit": "us per solve",
+                               "nodes": cfg["n_cells"] + 1, "bound": "latency (one CTA)"}
+    return rows
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -215,6 +269,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=2_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=300)
+    ap.add_argument("--no-rows", action="store_true")
+    ap.add_argument("--tp-atoms", type=int, default=100_000_000)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_setup()
@@ -323,6 +379,9 @@ def main():
                          f"{nst} full PIC/MCC steps in {dt:.1f} s"}
     clocks = clk.summary()
     launches = mover_n + tp_n + 3 * cmp_n
+    rows = None
+    if rank == 0 and not args.no_rows:
+        rows = measure_rows(d, cfg, peak, cmp_ms, cmp_n, 0.25 * (n_start + n_end), args.tp_atoms)
     if rank == 0:
         line = {"metric": "particle-steps/s", "value": value, "unit": "particle-steps/s", "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
@@ -335,7 +394,7 @@ def main():
                                  "read); value from per-step CUDA events",
                            "wall_s_incl_flush": wall},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": int(launches),
+                "gpu_launches": int(launches), "rows": rows,
                 "kernel_ms": {"step": mover_ms, "tp": tp_ms, "compact": cmp_ms}}
         print(json.dumps(line), flush=True)
     d.close()
