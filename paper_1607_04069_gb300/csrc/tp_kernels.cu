@@ -12,12 +12,58 @@
 
 namespace pg {
 
+// Tallies of one CTA's tile on sample steps: the deposit as 32-bit counters
+// (atoms n_j, high and low 16 bits of their right-node weights, as in the
+// step kernel) and the v_x moment as 64-bit sums kept in (low, high) 32-bit
+// pairs -- 64-bit shared atomics are not native.  With at most 65536 atoms
+// per tile no counter can overflow.
+constexpr long long kTpTileGroups = 16384;   // 65536 atoms
+struct TpAcc {
+    unsigned int *cnt, *whi, *wlo;   // [N]
+    unsigned int* flo;               // [N+1]
+    int* fhi;                        // [N+1]
+};
+
+__device__ __forceinline__ void tp_add64(const TpAcc& A, int m, long long v)
+{
+    const unsigned int vl = (unsigned int)v;
+    const unsigned int old = atomicAdd(&A.flo[m], vl);
+    const int vh = (int)(v >> 32) + (old + vl < old ? 1 : 0);
+    if (vh) atomicAdd(&A.fhi[m], vh);
+}
+
+__device__ void tp_flush(const TpAcc& A, int N, unsigned long long* q, long long* f, int t, int nt)
+{
+    for (int m = t; m <= N; m += nt) {
+        unsigned long long v = 0;
+        if (m < N) v += ((unsigned long long)A.cnt[m] << 32) - (((unsigned long long)A.whi[m] << 16) + A.wlo[m]);
+        if (m > 0) v += ((unsigned long long)A.whi[m - 1] << 16) + A.wlo[m - 1];
+        if (v) atomicAdd(&q[m], v);
+        const long long fv = (long long)(((unsigned long long)(unsigned int)A.fhi[m] << 32) | A.flo[m]);
+        if (fv) atomicAdd((unsigned long long*)&f[m], (unsigned long long)fv);
+    }
+    __syncthreads();                                   // node m also reads cell m-1: clear after all reads
+    for (int m = t; m <= N; m += nt) {
+        if (m < N) A.cnt[m] = A.whi[m] = A.wlo[m] = 0;
+        A.flo[m] = 0;
+        A.fhi[m] = 0;
+    }
+}
+
+// One TP step.  Atoms are taken in groups of four (16-byte vector loads of x
+// and v, 32 bytes of ids); each CTA owns a contiguous run of groups.  The two
+// Philox blocks of every atom (gas partner, collision test) are drawn for the
+// four atoms of a group at once, their rounds interleaved.
 __global__ void __launch_bounds__(kTpThreads) k_tp_step(Dev d)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int N1 = d.ncell + 1;
-    unsigned long long* sq = (unsigned long long*)smem_raw;
-    long long* sflux = (long long*)(sq + N1);
+    const int N = d.ncell;
+    TpAcc A;
+    A.cnt = (unsigned int*)smem_raw;
+    A.whi = A.cnt + N;
+    A.wlo = A.whi + N;
+    A.flo = A.wlo + N;
+    A.fhi = (int*)(A.flo + N + 1);
     __shared__ unsigned int s_coll;
     __shared__ int s_last;
 
@@ -25,86 +71,106 @@ __global__ void __launch_bounds__(kTpThreads) k_tp_step(Dev d)
     const unsigned int s = ctl->tp_step;
     const long long n = ctl->n[kTP];
     const bool sample = d.diag_every > 0 && ((s + 1) % (unsigned)d.diag_every == 0);
-    const long long beg = n * blockIdx.x / gridDim.x, end = n * (blockIdx.x + 1) / gridDim.x;
-    for (int i = threadIdx.x; i < N1; i += blockDim.x) {
-        sq[i] = 0;
-        sflux[i] = 0;
-    }
+    const long long G4 = (n + 3) >> 2;
+    const long long g0 = G4 * blockIdx.x / gridDim.x, g1 = G4 * (blockIdx.x + 1) / gridDim.x;
+    if (sample)
+        for (int m = threadIdx.x; m <= N; m += blockDim.x) {
+            if (m < N) A.cnt[m] = A.whi[m] = A.wlo[m] = 0;
+            A.flo[m] = 0;
+            A.fhi[m] = 0;
+        }
     if (threadIdx.x == 0) s_coll = 0;
     __syncthreads();
 
     const SpBuf B = d.buf[kTP][ctl->cur[kTP]];
-    uint32_t* __restrict__ P = (uint32_t*)B.pos;
     const float mu_al = (float)(kMAL / (kMAL + kMAR)), mu_ar = (float)(kMAR / (kMAL + kMAR));
-    for (long long i0 = beg; i0 < end; i0 += blockDim.x) {
-        const long long i = i0 + threadIdx.x;
-        bool act = i < end;
-        uint32_t x = 0;
-        if (act) {
-            x = P[i];
-            act = x != 0u;
-        }
-        uint32_t j = 0, wr = 0;
-        bool dep = false;
-        if (act) {
-            float vx = B.vx[i], vy = B.vy[i], vz = B.vz[i];
-            const uint64_t id = B.id[i];
-            const long long np = (long long)x + __float2ll_rn(vx * d.tp_scale);
-            if (np <= 0 || np >= 4294967296LL) {
-                const int el = np <= 0 ? 0 : 1;
-                const float v2 = vx * vx + vy * vy + vz * vz;
-                const float E = v2 * (float)(0.5 * kMAL / kQE);
-                float ct = v2 > 0.0f ? fabsf(vx) * rsqrtf(v2) : 1.0f;
-                ct = fminf(ct, 1.0f);
-                int be = (int)(E / 300.0f * (float)kNbSpE);
-                be = be < 0 ? 0 : (be > kNbSpE - 1 ? kNbSpE - 1 : be);
-                int ba = (int)(acosf(ct) * (float)(180.0 / kPI));
-                ba = ba < 0 ? 0 : (ba > kNbAng - 1 ? kNbAng - 1 : ba);
-                atomicAdd(&d.diag.sp_e[el][be], 1ull);
-                atomicAdd(&d.diag.sp_ang[el][ba], 1ull);
-                atomicAdd(&ctl->cnt[el == 0 ? kCntTpDepL : kCntTpDepR], 1ull);
-                P[i] = 0u;
-            } else {
-                x = (uint32_t)np;
-                const uint4 cg = draw(d.seed, id, s, kPurTpGas);
-                const float2 n12 = box_muller(cg.x, cg.y);
-                const float2 n34 = box_muller(cg.z, cg.w);
+    const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
+    unsigned int ncoll = 0;
+    for (long long t0 = g0; t0 < g1; t0 += kTpTileGroups) {
+        const long long t1 = min(g1, t0 + kTpTileGroups);
+        for (long long g = t0 + threadIdx.x; g < t1; g += blockDim.x) {
+            uint4 P = ((const uint4*)B.pos)[g];
+            uint32_t x[4] = {P.x, P.y, P.z, P.w};
+            if (4 * g + 4 > n)                             // slots past n hold no atom
+#pragma unroll
+                for (int u = 1; u < 4; ++u)
+                    if (4 * g + u >= n) x[u] = 0u;
+            if ((x[0] | x[1] | x[2] | x[3]) == 0u) continue;
+            const float4 VX = ((const float4*)B.vx)[g], VY = ((const float4*)B.vy)[g], VZ = ((const float4*)B.vz)[g];
+            const ulonglong2 Ia = ((const ulonglong2*)B.id)[2 * g], Ib = ((const ulonglong2*)B.id)[2 * g + 1];
+            float vx[4] = {VX.x, VX.y, VX.z, VX.w}, vy[4] = {VY.x, VY.y, VY.z, VY.w}, vz[4] = {VZ.x, VZ.y, VZ.z, VZ.w};
+            const uint64_t id[4] = {Ia.x, Ia.y, Ib.x, Ib.y};
+            uint4 cg[4], cc[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                cg[u] = make_uint4((uint32_t)id[u], (uint32_t)(id[u] >> 32), s, kPurTpGas);
+                cc[u] = make_uint4((uint32_t)id[u], (uint32_t)(id[u] >> 32), s, kPurTpColl);
+            }
+            philox_n<4>(cg, k0, k1);
+            philox_n<4>(cc, k0, k1);
+            bool moved = false;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (x[u] == 0u) continue;
+                const long long np = (long long)x[u] + __float2ll_rn(vx[u] * d.tp_scale);
+                if (np <= 0 || np >= 4294967296LL) {       // sticks at an electrode
+                    const int el = np <= 0 ? 0 : 1;
+                    const float v2 = vx[u] * vx[u] + vy[u] * vy[u] + vz[u] * vz[u];
+                    const float E = v2 * (float)(0.5 * kMAL / kQE);
+                    const float ct = fminf(v2 > 0.0f ? fabsf(vx[u]) * rsqrtf(v2) : 1.0f, 1.0f);
+                    int be = (int)(E / 300.0f * (float)kNbSpE);
+                    be = be < 0 ? 0 : (be > kNbSpE - 1 ? kNbSpE - 1 : be);
+                    int ba = (int)(acosf(ct) * (float)(180.0 / kPI));
+                    ba = ba < 0 ? 0 : (ba > kNbAng - 1 ? kNbAng - 1 : ba);
+                    atomicAdd(&d.diag.sp_e[el][be], 1ull);
+                    atomicAdd(&d.diag.sp_ang[el][ba], 1ull);
+                    atomicAdd(&ctl->cnt[el == 0 ? kCntTpDepL : kCntTpDepR], 1ull);
+                    x[u] = 0u;
+                    continue;
+                }
+                x[u] = (uint32_t)np;
+                const float2 n12 = box_muller(cg[u].x, cg[u].y);
+                const float2 n34 = box_muller(cg[u].z, cg[u].w);
                 const float wx = d.vth_gas * n12.x, wy = d.vth_gas * n12.y, wz = d.vth_gas * n34.x;
-                const float gx = vx - wx, gy = vy - wy, gz = vz - wz;
+                const float gx = vx[u] - wx, gy = vy[u] - wy, gz = vz[u] - wz;
                 const float gm = sqrtf(gx * gx + gy * gy + gz * gz);
                 const float Pc = -expm1f(-d.tp_nsig_dt * gm);
-                const uint4 cc = draw(d.seed, id, s, kPurTpColl);
-                if (u23(cc.x) < Pc) {
-                    const float3 dir = iso_dir(cc.y, cc.z);
-                    vx = mu_al * vx + mu_ar * wx + mu_ar * gm * dir.x;
-                    vy = mu_al * vy + mu_ar * wy + mu_ar * gm * dir.y;
-                    vz = mu_al * vz + mu_ar * wz + mu_ar * gm * dir.z;
-                    B.vx[i] = vx;
-                    B.vy[i] = vy;
-                    B.vz[i] = vz;
-                    atomicAdd(&s_coll, 1u);
+                if (u23(cc[u].x) < Pc) {                   // hard sphere, isotropic in the centre of mass
+                    const float3 dir = iso_dir(cc[u].y, cc[u].z);
+                    vx[u] = mu_al * vx[u] + mu_ar * wx + mu_ar * gm * dir.x;
+                    vy[u] = mu_al * vy[u] + mu_ar * wy + mu_ar * gm * dir.y;
+                    vz[u] = mu_al * vz[u] + mu_ar * wz + mu_ar * gm * dir.z;
+                    moved = true;
+                    ++ncoll;
                 }
-                P[i] = x;
                 if (sample) {
-                    cell_of(x, d.kshift, j, wr);
-                    dep = true;
-                    const long long vq = (long long)__float2int_rn(vx);
-                    atomicAdd((unsigned long long*)&sflux[j],
-                              (unsigned long long)(vq * (long long)(((1ull << 32) - wr) >> 16)));
-                    atomicAdd((unsigned long long*)&sflux[j + 1],
-                              (unsigned long long)(vq * (long long)(wr >> 16)));
+                    uint32_t j, wr;
+                    cell_of(x[u], d.kshift, j, wr);
+                    atomicAdd(&A.cnt[j], 1u);
+                    atomicAdd(&A.whi[j], wr >> 16);
+                    atomicAdd(&A.wlo[j], wr & 0xffffu);
+                    const long long vq = (long long)__float2int_rn(vx[u]);
+                    const long long w16 = (long long)(wr >> 16);
+                    tp_add64(A, j, vq * (65536 - w16));
+                    tp_add64(A, j + 1, vq * w16);
                 }
             }
+            ((uint4*)B.pos)[g] = make_uint4(x[0], x[1], x[2], x[3]);
+            if (moved) {
+                ((float4*)B.vx)[g] = make_float4(vx[0], vx[1], vx[2], vx[3]);
+                ((float4*)B.vy)[g] = make_float4(vy[0], vy[1], vy[2], vy[3]);
+                ((float4*)B.vz)[g] = make_float4(vz[0], vz[1], vz[2], vz[3]);
+            }
         }
-        if (sample) warp_deposit(sq, dep, j, wr);
+        if (sample) {                                      // this tile's tallies into the step's histograms
+            __syncthreads();
+            tp_flush(A, N, d.tp_q, d.tp_flux, threadIdx.x, blockDim.x);
+            __syncthreads();
+        }
     }
+    ncoll = __reduce_add_sync(0xffffffffu, ncoll);
+    if ((threadIdx.x & 31) == 0 && ncoll) atomicAdd(&s_coll, ncoll);
     __syncthreads();
-    if (sample) {
-        for (int m = threadIdx.x; m < N1; m += blockDim.x) {
-            if (sq[m]) atomicAdd(&d.tp_q[m], sq[m]);
-            if (sflux[m]) atomicAdd((unsigned long long*)&d.tp_flux[m], (unsigned long long)sflux[m]);
-        }
-    }
     if (threadIdx.x == 0 && s_coll) atomicAdd(&ctl->cnt[kCntTpColl], (unsigned long long)s_coll);
     __threadfence();
     __syncthreads();
@@ -112,7 +178,7 @@ __global__ void __launch_bounds__(kTpThreads) k_tp_step(Dev d)
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    for (int m = threadIdx.x; m < N1; m += blockDim.x) {
+    for (int m = threadIdx.x; m <= N; m += blockDim.x) {
         if (sample) {
             red_split(d.diag.tp_dens + 2 * m, __ldcg(d.tp_q + m));
             red_split_signed(d.diag.tp_vx + 2 * m, __ldcg(d.tp_flux + m));
@@ -156,7 +222,7 @@ __global__ void k_commit_count(Dev d, int s, long long add)
     d.ctl->n[s] = n > d.ctl->cap[s] ? d.ctl->cap[s] : n;
 }
 
-size_t tp_smem(int ncell) { return (size_t)(ncell + 1) * 16; }
+size_t tp_smem(int ncell) { return (size_t)ncell * 12 + (size_t)(ncell + 1) * 8; }
 
 cudaError_t launch_tp_step(const Dev& d, int grid, cudaStream_t st)
 {
