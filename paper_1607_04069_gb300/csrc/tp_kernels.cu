@@ -50,11 +50,28 @@ __device__ void tp_flush(const TpAcc& A, int N, unsigned long long* q, long long
     }
 }
 
+struct TpGrp {                 // one group of four atoms, as loaded
+    uint4 P;
+    float4 VX, VY, VZ;
+    ulonglong2 Ia, Ib;
+};
+__device__ __forceinline__ TpGrp tp_load(const SpBuf& B, long long g)
+{
+    TpGrp G;
+    G.P = ((const uint4*)B.pos)[g];
+    G.VX = ((const float4*)B.vx)[g];
+    G.VY = ((const float4*)B.vy)[g];
+    G.VZ = ((const float4*)B.vz)[g];
+    G.Ia = ((const ulonglong2*)B.id)[2 * g];
+    G.Ib = ((const ulonglong2*)B.id)[2 * g + 1];
+    return G;
+}
+
 // One TP step.  Atoms are taken in groups of four (16-byte vector loads of x
 // and v, 32 bytes of ids); each CTA owns a contiguous run of groups.  The two
 // Philox blocks of every atom (gas partner, collision test) are drawn for the
 // four atoms of a group at once, their rounds interleaved.
-__global__ void __launch_bounds__(kTpThreads) k_tp_step(Dev d)
+__global__ void __launch_bounds__(kTpThreads, 2) k_tp_step(Dev d)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = d.ncell;
@@ -88,16 +105,21 @@ __global__ void __launch_bounds__(kTpThreads) k_tp_step(Dev d)
     unsigned int ncoll = 0;
     for (long long t0 = g0; t0 < g1; t0 += kTpTileGroups) {
         const long long t1 = min(g1, t0 + kTpTileGroups);
-        for (long long g = t0 + threadIdx.x; g < t1; g += blockDim.x) {
-            uint4 P = ((const uint4*)B.pos)[g];
-            uint32_t x[4] = {P.x, P.y, P.z, P.w};
+        // each thread loads its next group before working on the current one
+        long long g = t0 + threadIdx.x;
+        TpGrp nxt;
+        if (g < t1) nxt = tp_load(B, g);
+        for (; g < t1; g += blockDim.x) {
+            const TpGrp cur = nxt;
+            if (g + blockDim.x < t1) nxt = tp_load(B, g + blockDim.x);
+            uint32_t x[4] = {cur.P.x, cur.P.y, cur.P.z, cur.P.w};
             if (4 * g + 4 > n)                             // slots past n hold no atom
 #pragma unroll
                 for (int u = 1; u < 4; ++u)
                     if (4 * g + u >= n) x[u] = 0u;
             if ((x[0] | x[1] | x[2] | x[3]) == 0u) continue;
-            const float4 VX = ((const float4*)B.vx)[g], VY = ((const float4*)B.vy)[g], VZ = ((const float4*)B.vz)[g];
-            const ulonglong2 Ia = ((const ulonglong2*)B.id)[2 * g], Ib = ((const ulonglong2*)B.id)[2 * g + 1];
+            const float4 VX = cur.VX, VY = cur.VY, VZ = cur.VZ;
+            const ulonglong2 Ia = cur.Ia, Ib = cur.Ib;
             float vx[4] = {VX.x, VX.y, VX.z, VX.w}, vy[4] = {VY.x, VY.y, VY.z, VY.w}, vz[4] = {VZ.x, VZ.y, VZ.z, VZ.w};
             const uint64_t id[4] = {Ia.x, Ia.y, Ib.x, Ib.y};
             uint4 cg[4], cc[4];
