@@ -921,8 +921,10 @@ __global__ void k_sort_count(Dev d, int s)
     __syncthreads();
     const long long n = d.ctl->n[s];
     const PosT* P = (const PosT*)d.buf[s][d.ctl->cur[s]].pos;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
+    // a contiguous run of slots per CTA: cell-ordered runs touch few cells, so
+    // few global atomics follow
+    const long long i0 = n * blockIdx.x / gridDim.x, i1 = n * (blockIdx.x + 1) / gridDim.x;
+    for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         const PosT x = P[i];
         if (!is_alive(x)) continue;
         uint32_t j, wr;
@@ -954,47 +956,81 @@ __global__ void k_sort_scan(Dev d)
     if (t == 0) d.ctl->sort_total = tot;
 }
 
+// Scatter: each CTA takes a contiguous run of slots, counts its particles per
+// cell in shared memory, reserves one sub-range per touched cell of the
+// cell's global range (one global atomic per cell and CTA instead of one per
+// warp and cell), and hands out slots of those sub-ranges with shared-memory
+// atomics.  Order inside a cell is unspecified.
 template <typename PosT>
 __global__ void k_sort_scatter(Dev d, int s)
 {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned int* cur_slot = (unsigned int*)smem_raw;          // [ncell]: count, then next slot
     __shared__ int s_last;
+    const int N = d.ncell;
     const long long n = d.ctl->n[s];
     const unsigned int cur = d.ctl->cur[s];
     const SpBuf A = d.buf[s][cur], Bn = d.buf[s][cur ^ 1u];
     const PosT* PA = (const PosT*)A.pos;
     PosT* PB = (PosT*)Bn.pos;
     const int lane = threadIdx.x & 31;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    const long long nround = (n + stride - 1) / stride * stride;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nround; i += stride) {
-        bool act = i < n;
-        PosT x = 0;
-        if (act) {
-            x = PA[i];
-            act = is_alive(x);
-        }
-        uint32_t j = 0xffffffffu, wr;
-        if (act) {
-            cell_of(x, d.kshift, j, wr);
-            if (j >= (uint32_t)d.ncell) {
-                act = false;
-                j = 0xffffffffu;
+    const long long i0 = n * blockIdx.x / gridDim.x, i1 = n * (blockIdx.x + 1) / gridDim.x;
+    // all lanes of a warp run the same number of iterations (warp-wide collectives below)
+    const long long i1r = i0 + (i1 - i0 + blockDim.x - 1) / blockDim.x * blockDim.x;
+    for (int m = threadIdx.x; m < N; m += blockDim.x) cur_slot[m] = 0;
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+        for (long long i = i0 + threadIdx.x; i < i1r; i += blockDim.x) {
+            bool act = i < i1;
+            PosT x = 0;
+            float fx = 0.0f, fy = 0.0f, fz = 0.0f;
+            uint64_t fid = 0;
+            uint32_t fnev = 0;
+            if (act) {
+                x = PA[i];
+                if (pass == 1) {                           // in flight while the slot is worked out
+                    fx = A.vx[i];
+                    fy = A.vy[i];
+                    fz = A.vz[i];
+                    fid = A.id[i];
+                    if (s != kTP) fnev = A.nev[i];
+                }
+                act = is_alive(x);
+            }
+            uint32_t j = 0xffffffffu, wr;
+            if (act) {
+                cell_of(x, d.kshift, j, wr);
+                if (j >= (uint32_t)N) {
+                    act = false;
+                    j = 0xffffffffu;
+                }
+            }
+            // lanes of one cell share one shared-memory atomic (cell-sorted input would
+            // otherwise serialise on a single counter)
+            const unsigned grp = __match_any_sync(0xffffffffu, j);
+            const int leader = __ffs(grp) - 1;
+            const int rank = __popc(grp & ((1u << lane) - 1u));
+            unsigned int base = 0;
+            if (act && lane == leader) base = atomicAdd(&cur_slot[j], (unsigned)__popc(grp));
+            if (pass == 0) continue;
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (act) {
+                const unsigned int o = base + rank;
+                PB[o] = x;
+                Bn.vx[o] = fx;
+                Bn.vy[o] = fy;
+                Bn.vz[o] = fz;
+                Bn.id[o] = fid;
+                if (s != kTP) Bn.nev[o] = fnev;
             }
         }
-        const unsigned grp = __match_any_sync(0xffffffffu, j);
-        const int leader = __ffs(grp) - 1;
-        const int rank = __popc(grp & ((1u << lane) - 1u));
-        unsigned int base = 0;
-        if (act && lane == leader) base = atomicAdd(&d.sort_off[j], (unsigned)__popc(grp));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (act) {
-            const unsigned int o = base + rank;
-            PB[o] = x;
-            Bn.vx[o] = A.vx[i];
-            Bn.vy[o] = A.vy[i];
-            Bn.vz[o] = A.vz[i];
-            Bn.id[o] = A.id[i];
-            if (s != kTP) Bn.nev[o] = A.nev[i];
+        __syncthreads();
+        if (pass == 0) {                                   // reserve this CTA's sub-range of every touched cell
+            for (int m = threadIdx.x; m < N; m += blockDim.x) {
+                const unsigned int c = cur_slot[m];
+                if (c) cur_slot[m] = atomicAdd(&d.sort_off[m], c);
+            }
+            __syncthreads();
         }
     }
     __threadfence();
@@ -1073,11 +1109,12 @@ cudaError_t launch_sort(const Dev& d, int s, int grid, cudaStream_t st)
 {
     const bool p64 = d.pos64 && s != kTP;
     const size_t sm = (size_t)d.ncell * 4;
-    if (p64) k_sort_count<double><<<grid, 256, sm, st>>>(d, s);
-    else k_sort_count<uint32_t><<<grid, 256, sm, st>>>(d, s);
+    const int gs = grid >= 8 ? grid / 4 : grid;     // longer runs per CTA: fewer cell reservations
+    if (p64) k_sort_count<double><<<gs, 1024, sm, st>>>(d, s);
+    else k_sort_count<uint32_t><<<gs, 1024, sm, st>>>(d, s);
     k_sort_scan<<<1, 1024, 0, st>>>(d);
-    if (p64) k_sort_scatter<double><<<grid, 256, 0, st>>>(d, s);
-    else k_sort_scatter<uint32_t><<<grid, 256, 0, st>>>(d, s);
+    if (p64) k_sort_scatter<double><<<gs, 1024, sm, st>>>(d, s);
+    else k_sort_scatter<uint32_t><<<gs, 1024, sm, st>>>(d, s);
     return cudaGetLastError();
 }
 
