@@ -244,6 +244,53 @@ int pic_op_sort_noalloc(int pos_precision, int64_t n, int32_t n_cells, const voi
                         const float* vy, const float* vz, const uint64_t* id, void* pos_out, float* vx_out,
                         float* vy_out, float* vz_out, uint64_t* id_out, int64_t* n_out, void* stream);
 
+/* ------------------------------------------------------------ batches
+ * Several independent discharges (for instance a scan over pressure or RF
+ * voltage) stepped together: one step launch per time step covers every
+ * member, each member owning a contiguous range of that launch's CTAs.  The
+ * paper has no counterpart; each member runs the same PIC/MCC cycle as
+ * pic_step (Sec. "Particle-In-Cell Scheme", Fig. 4) and its results are bit
+ * for bit those of the same discharge stepped alone.
+ *
+ * Members use 32-bit positions, one dt and one diag_every, a whole number
+ * of steps per RF period (1 / (f dt) integral, at most 2^24), and no coupled
+ * test-particle steps (tp_every 0).  The RF phase of step l is taken at
+ * l mod period in both forms.  A member joins (pic_batch_add) only while every
+ * current member stands at a multiple of diag_every steps, so that all of
+ * them sample on the same steps.  Each member keeps 2 or more CTAs,
+ * ceil((n_e0 + n_i0) / particles_per_cta) of them (default 65536). */
+typedef struct pic_batch pic_batch; /* opaque */
+
+/* Create an empty batch whose work goes to `stream` (cudaStream_t or NULL). */
+int pic_batch_create(void* stream, pic_batch** out);
+
+/* Create a member from p (as pic_create does, on the batch's stream) and
+ * return its slot index in *slot (the lowest free one).  The member starts
+ * at step 0. */
+int pic_batch_add(pic_batch* b, const pic_params* p, int* slot);
+
+/* Destroy the member in `slot` (waits for the batch's stream); the slot
+ * becomes free and the other members keep their slots and state. */
+int pic_batch_remove(pic_batch* b, int slot);
+
+/* The member's context, for pic_diag / pic_counters / pic_get_species /
+ * pic_sync.  Owned by the batch: do not pic_destroy it, and do not
+ * pic_step it while it belongs to the batch. */
+int pic_batch_ctx(pic_batch* b, int slot, pic_ctx** out);
+
+/* Particles per CTA when the launch is divided among members (>= 1024). */
+int pic_batch_set_target(pic_batch* b, int64_t particles_per_cta);
+
+/* Advance every member n_steps steps (one launch per step plus each
+ * member's due compactions).  Asynchronous, as pic_step. */
+int pic_batch_step(pic_batch* b, int64_t n_steps);
+
+/* pic_sync on every member; returns the first error. */
+int pic_batch_sync(pic_batch* b);
+
+/* Destroy every member and the batch. */
+void pic_batch_destroy(pic_batch* b);
+
 const char* pic_strerror(int code);
 const char* pic_last_error(void);
 

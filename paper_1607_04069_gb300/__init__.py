@@ -86,13 +86,21 @@ def lib():
             "pic_op_deposit": [vp, C.c_int, i64, i32, vp, vp],
             "pic_op_poisson": [vp, vp, i32, dbl, dbl, dbl, vp, vp, vp],
             "pic_op_sort_noalloc": [C.c_int, i64, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp],
+            "pic_batch_create": [vp, C.POINTER(vp)],
+            "pic_batch_add": [vp, C.POINTER(PicParams), C.POINTER(C.c_int)],
+            "pic_batch_remove": [vp, C.c_int],
+            "pic_batch_ctx": [vp, C.c_int, C.POINTER(vp)],
+            "pic_batch_set_target": [vp, i64],
+            "pic_batch_step": [vp, i64],
+            "pic_batch_sync": [vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
             fn.argtypes = args
             fn.restype = C.c_int
-        L.pic_destroy.argtypes = [vp]
-        L.pic_destroy.restype = None
+        for name in ("pic_destroy", "pic_batch_destroy"):
+            getattr(L, name).argtypes = [vp]
+            getattr(L, name).restype = None
         L.pic_strerror.argtypes = [C.c_int]
         L.pic_strerror.restype = C.c_char_p
         L.pic_last_error.argtypes = []
@@ -152,7 +160,8 @@ class Discharge:
 
     def close(self):
         if getattr(self, "h", None):
-            lib().pic_destroy(self.h)
+            if getattr(self, "_owned", True):
+                lib().pic_destroy(self.h)
             self.h = None
 
     __del__ = close
@@ -248,6 +257,57 @@ class Discharge:
         _check(lib().pic_derived(self.h, _ptr(out)))
         keys = ["n_gas", "dx", "nu_max_e", "nu_max_i", "p_max_e", "p_max_i", "eps_max", "lambda"]
         return dict(zip(keys, out.tolist()))
+
+
+class Batch:
+    """Independent discharges stepped together, one step launch for all of
+    them (``pic_batch_*``).  Members share dt and diag_every, use 32-bit
+    positions and a whole number of steps per RF period."""
+
+    def __init__(self, stream=None, particles_per_cta=None):
+        self.stream = _stream_handle(stream)
+        h = C.c_void_p()
+        _check(lib().pic_batch_create(C.c_void_p(self.stream), C.byref(h)))
+        self.h = h
+        self._params = {}
+        if particles_per_cta is not None:
+            _check(lib().pic_batch_set_target(self.h, int(particles_per_cta)))
+
+    def add(self, params) -> int:
+        if isinstance(params, dict):
+            params = params_from_workload(params)
+        slot = C.c_int()
+        _check(lib().pic_batch_add(self.h, C.byref(params), C.byref(slot)))
+        self._params[slot.value] = params
+        return slot.value
+
+    def remove(self, slot):
+        _check(lib().pic_batch_remove(self.h, int(slot)))
+        self._params.pop(int(slot), None)
+
+    def member(self, slot) -> Discharge:
+        """A view of the member in ``slot`` (diagnostics, counters, particles);
+        the batch owns it and steps it."""
+        h = C.c_void_p()
+        _check(lib().pic_batch_ctx(self.h, int(slot), C.byref(h)))
+        d = Discharge.__new__(Discharge)
+        d.h, d._owned, d.stream = h, False, self.stream
+        d.params = self._params[int(slot)]
+        d.n_cells = d.params.n_cells
+        return d
+
+    def step(self, n=1):
+        _check(lib().pic_batch_step(self.h, int(n)))
+
+    def sync(self):
+        _check(lib().pic_batch_sync(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pic_batch_destroy(self.h)
+            self.h = None
+
+    __del__ = close
 
 
 # ------------------------------------------------------------------ stateless ops (torch buffers)

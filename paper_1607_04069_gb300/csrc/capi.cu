@@ -62,6 +62,7 @@ struct pic_ctx {
     long long h_step = 0, h_tp_step = 0, tp_launched = 0;
     long long acc_upto = 0;          // last step whose state entered the time averages
     unsigned int cur[3] = {0, 0, 0}; // active ping-pong halves (each compaction flips one)
+    long long period = 0;            // steps per RF period when that is a whole number, else 0
     double derived[8];
     bool timing = false;
     Timer timers[3];
@@ -203,6 +204,12 @@ void derive(pic_ctx* c)
     d.cap[kE] = p.cap_e;
     d.cap[kI] = p.cap_i;
     d.cap[kTP] = p.cap_tp;
+    c->period = 0;
+    if (p.rf_freq_hz > 0) {
+        const double per = 1.0 / (p.rf_freq_hz * p.dt);
+        const long long P = std::llrint(per);
+        if (P >= 1 && P <= (1ll << 24) && std::fabs((double)P * p.rf_freq_hz * p.dt - 1.0) < 1e-9) c->period = P;
+    }
     d.lam[kE] = nu_max_e * p.dt;
     d.lam[kI] = nu_max_i * p.dt;
     d.lamf[kE] = (float)d.lam[kE];
@@ -237,9 +244,13 @@ void sync_desc(pic_ctx* c)          // keep the coupled descriptor's pointers in
 }
 
 // electrode voltage at step l (V0 sin(2 pi f t_l), t_l = l dt)
+// electrode voltage at step l, V0 sin(2 pi f t_l), evaluated at the phase of
+// step l within its RF period when a period is a whole number of steps (so a
+// step's voltage depends only on its phase, here and in batched stepping)
 double v_left_at(const pic_ctx* c, long long l)
 {
-    return c->p.rf_volt_v * std::sin(2.0 * kPI * c->p.rf_freq_hz * (double)l * c->p.dt);
+    const long long lp = c->period > 0 ? l % c->period : l;
+    return c->p.rf_volt_v * std::sin(2.0 * kPI * c->p.rf_freq_hz * (double)lp * c->p.dt);
 }
 
 StepArgs step_args(const pic_ctx* c, long long l, int accumulate)
@@ -957,5 +968,228 @@ const char* pic_strerror(int code)
 }
 
 const char* pic_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- batches
+struct pic_batch {
+    std::vector<pic_ctx*> ctx;             // slots; nullptr where a discharge was removed
+    std::vector<StepArgs*> phase;          // per slot: device table of the step arguments of one RF period
+    cudaStream_t stream = nullptr;
+    long long target = 65536;              // particles per CTA of the batched launch
+    BatchEntry* d_ent = nullptr;
+    int* d_owner = nullptr;
+    size_t ent_cap = 0, owner_cap = 0;
+    std::vector<BatchEntry> h_ent;
+    std::vector<int> h_owner;
+    int grid = 0, max_ncell = 0;
+    bool dirty = true;
+};
+
+namespace {
+
+int batch_rebuild(pic_batch* b)
+{
+    b->h_ent.clear();
+    b->h_owner.clear();
+    b->max_ncell = 0;
+    int cta = 0;
+    for (size_t k = 0; k < b->ctx.size(); ++k) {
+        pic_ctx* c = b->ctx[k];
+        if (!c) continue;
+        const long long np = c->p.n_e0 + c->p.n_i0;
+        const int ncta = (int)std::max(2ll, (np + b->target - 1) / b->target);
+        BatchEntry e;
+        std::memset(&e, 0, sizeof e);
+        e.d = c->d;
+        e.phase = b->phase[k];
+        e.period = (unsigned int)c->period;
+        e.cta0 = cta;
+        e.ncta = ncta;
+        b->h_ent.push_back(e);
+        for (int i = 0; i < ncta; ++i) b->h_owner.push_back((int)b->h_ent.size() - 1);
+        cta += ncta;
+        b->max_ncell = std::max(b->max_ncell, c->p.n_cells);
+    }
+    b->grid = cta;
+    if (b->h_ent.size() > b->ent_cap) {
+        if (b->d_ent) CK(cudaFree(b->d_ent));
+        b->d_ent = nullptr;
+        b->ent_cap = b->h_ent.size() + 16;
+        CK(cudaMalloc(&b->d_ent, b->ent_cap * sizeof(BatchEntry)));
+    }
+    if (b->h_owner.size() > b->owner_cap) {
+        if (b->d_owner) CK(cudaFree(b->d_owner));
+        b->d_owner = nullptr;
+        b->owner_cap = b->h_owner.size() + 256;
+        CK(cudaMalloc(&b->d_owner, b->owner_cap * sizeof(int)));
+    }
+    if (!b->h_owner.empty())
+        CK(cudaMemcpyAsync(b->d_owner, b->h_owner.data(), b->h_owner.size() * sizeof(int), cudaMemcpyHostToDevice,
+                           b->stream));
+    b->dirty = false;
+    return PIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pic_batch_create(void* stream, pic_batch** out)
+{
+    if (!out) return fail(PIC_ERR_INVALID_ARG, "out is NULL");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return fail(PIC_ERR_NO_DEVICE, "no CUDA device");
+    pic_batch* b = new pic_batch();
+    b->stream = (cudaStream_t)stream;
+    *out = b;
+    return PIC_OK;
+}
+
+int pic_batch_add(pic_batch* b, const pic_params* p, int* slot)
+{
+    if (!b || !p || !slot) return fail(PIC_ERR_INVALID_ARG, "bad arguments");
+    if (p->pos_precision != 32) return fail(PIC_ERR_INVALID_ARG, "batched discharges use 32-bit positions");
+    if (p->sputter_enable && p->tp_every > 0)
+        return fail(PIC_ERR_INVALID_ARG, "batched discharges run no coupled test-particle steps (tp_every 0)");
+    for (pic_ctx* o : b->ctx) {
+        if (!o) continue;
+        if (o->p.dt != p->dt || o->p.diag_every != p->diag_every)
+            return fail(PIC_ERR_INVALID_ARG, "a batch shares one dt and one diag_every");
+        if (o->p.diag_every > 0 && o->h_step % o->p.diag_every != 0)
+            return fail(PIC_ERR_INVALID_ARG, "discharges join a batch at a multiple of diag_every steps");
+        break;
+    }
+    pic_ctx* c = nullptr;
+    int rc = pic_create(p, b->stream, &c);
+    if (rc) return rc;
+    if (c->period <= 0) {
+        pic_destroy(c);
+        return fail(PIC_ERR_INVALID_ARG, "batched discharges need a whole number of steps per RF period");
+    }
+    std::vector<StepArgs> tab((size_t)c->period);
+    for (long long l = 0; l < c->period; ++l) tab[(size_t)l] = step_args(c, l, 1);
+    StepArgs* dt = nullptr;
+    cudaError_t e = cudaMalloc(&dt, tab.size() * sizeof(StepArgs));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(dt, tab.data(), tab.size() * sizeof(StepArgs), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        if (dt) cudaFree(dt);
+        pic_destroy(c);
+        return cuda_fail(e, "batch phase table");
+    }
+    size_t k = 0;
+    while (k < b->ctx.size() && b->ctx[k]) ++k;
+    if (k == b->ctx.size()) {
+        b->ctx.push_back(nullptr);
+        b->phase.push_back(nullptr);
+    }
+    b->ctx[k] = c;
+    b->phase[k] = dt;
+    b->dirty = true;
+    *slot = (int)k;
+    return PIC_OK;
+}
+
+int pic_batch_remove(pic_batch* b, int slot)
+{
+    if (!b || slot < 0 || slot >= (int)b->ctx.size() || !b->ctx[(size_t)slot])
+        return fail(PIC_ERR_INVALID_ARG, "no discharge in this slot");
+    CK(cudaStreamSynchronize(b->stream));
+    pic_destroy(b->ctx[(size_t)slot]);
+    CK(cudaFree(b->phase[(size_t)slot]));
+    b->ctx[(size_t)slot] = nullptr;
+    b->phase[(size_t)slot] = nullptr;
+    b->dirty = true;
+    return PIC_OK;
+}
+
+int pic_batch_ctx(pic_batch* b, int slot, pic_ctx** out)
+{
+    if (!b || !out || slot < 0 || slot >= (int)b->ctx.size() || !b->ctx[(size_t)slot])
+        return fail(PIC_ERR_INVALID_ARG, "no discharge in this slot");
+    *out = b->ctx[(size_t)slot];
+    return PIC_OK;
+}
+
+int pic_batch_set_target(pic_batch* b, int64_t particles_per_cta)
+{
+    if (!b || particles_per_cta < 1024) return fail(PIC_ERR_INVALID_ARG, "particles per CTA >= 1024");
+    b->target = particles_per_cta;
+    b->dirty = true;
+    return PIC_OK;
+}
+
+int pic_batch_step(pic_batch* b, int64_t n)
+{
+    if (!b || n < 0) return fail(PIC_ERR_INVALID_ARG, "bad batch or step count");
+    if (n == 0) return PIC_OK;
+    pic_ctx* first = nullptr;
+    for (pic_ctx* c : b->ctx) {
+        if (!c) continue;
+        if (!first) first = c;
+        const int de = c->p.diag_every;
+        if (de > 0 && c->h_step % de != first->h_step % de)
+            return fail(PIC_ERR_INVALID_ARG, "batch members out of step with the sampling period");
+    }
+    if (!first) return PIC_OK;
+    if (b->dirty) {
+        int rc = batch_rebuild(b);
+        if (rc) return rc;
+    }
+    // the first step of this call enters the averages unless a field call already added it
+    size_t e = 0;
+    for (pic_ctx* c : b->ctx) {
+        if (!c) continue;
+        b->h_ent[e].d = c->d;
+        b->h_ent[e].acc_from = (unsigned int)(c->acc_upto + 1);
+        ++e;
+    }
+    CK(cudaMemcpyAsync(b->d_ent, b->h_ent.data(), b->h_ent.size() * sizeof(BatchEntry), cudaMemcpyHostToDevice,
+                       b->stream));
+    const int de = first->p.diag_every;
+    for (int64_t k = 0; k < n; ++k) {
+        const long long l = first->h_step;
+        const bool sample = de > 0 && (l + 1) % de == 0;   // members sample on the same steps
+        CK(launch_mover_batch(b->d_ent, b->d_owner, b->grid, b->max_ncell, sample, b->stream));
+        for (pic_ctx* c : b->ctx) {
+            if (!c) continue;
+            c->acc_upto = c->h_step;
+            c->h_step++;
+            for (int s = 0; s < 2; ++s) {
+                const int every = s == kE ? c->p.sort_every_e : c->p.sort_every_i;
+                if (every > 0 && c->h_step % every == 0) {
+                    CK(launch_sort(c->d, s, c->grid_sort, b->stream));
+                    c->cur[s] ^= 1u;
+                }
+            }
+        }
+    }
+    return PIC_OK;
+}
+
+int pic_batch_sync(pic_batch* b)
+{
+    if (!b) return fail(PIC_ERR_INVALID_ARG, "batch is NULL");
+    for (pic_ctx* c : b->ctx) {
+        if (!c) continue;
+        int rc = pic_sync(c);
+        if (rc) return rc;
+    }
+    return PIC_OK;
+}
+
+void pic_batch_destroy(pic_batch* b)
+{
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    for (size_t k = 0; k < b->ctx.size(); ++k) {
+        if (b->ctx[k]) pic_destroy(b->ctx[k]);
+        if (b->phase[k]) cudaFree(b->phase[k]);
+    }
+    if (b->d_ent) cudaFree(b->d_ent);
+    if (b->d_owner) cudaFree(b->d_owner);
+    delete b;
+}
 
 }  // extern "C"

@@ -178,6 +178,17 @@ struct Dev {                   // everything a kernel needs, passed by value
     unsigned long long* trace;       // optional per-CTA phase timestamps of the last step launch
 };
 
+// One discharge of a batched step launch (several independent discharges,
+// one kernel per step): its descriptor, the step arguments of its RF phases,
+// and the CTAs of the launch that work on it.
+struct BatchEntry {
+    Dev d;
+    const StepArgs* phase;     // [period]: step l uses phase[l % period] (step, cur, accumulate set on device)
+    unsigned int period;
+    unsigned int acc_from;     // steps l >= acc_from enter the time averages
+    int cta0, ncta;            // CTAs [cta0, cta0 + ncta) of the launch
+};
+
 // global nanosecond timer, comparable across SMs
 __device__ __forceinline__ unsigned long long gtimer()
 {

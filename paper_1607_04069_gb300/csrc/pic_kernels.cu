@@ -217,9 +217,9 @@ __device__ __forceinline__ int electron_ctas(long long ne, long long ni, int G)
     return Ge < 1 ? 1 : (Ge > G - 1 ? G - 1 : Ge);
 }
 
-__device__ __forceinline__ void flush_tally(const Dev& d, const BlockTally& t)
+__device__ __forceinline__ void flush_tally(const Dev& d, const BlockTally& t, int cta)
 {
-    unsigned long long* r = d.tally + (size_t)blockIdx.x * kNumCnt;
+    unsigned long long* r = d.tally + (size_t)cta * kNumCnt;
     const unsigned int v[13] = {t.elastic, t.excit, t.ioniz, t.cx, t.iso, t.imp_e[0], t.imp_e[1],
                                 t.numerics, t.capacity, t.imp_i[0], t.imp_i[1], t.sput[0], t.sput[1]};
     const int k[13] = {kCntElastic, kCntExcit, kCntIoniz, kCntCx, kCntIso, kCntImpEL, kCntImpER,
@@ -493,8 +493,10 @@ __device__ void flush_tile(const Acc& A, int N, unsigned int jlo, unsigned int j
 // after a state upload).  Slots are streamed in groups of four with 16-byte
 // vector loads and stores; consecutive threads take consecutive groups and
 // each thread loads its next group before working on the current one.
+// The body of one step launch for one discharge, run by CTA `cta` of the
+// `ncta` CTAs the discharge has in the launch.
 template <bool P64, int MODE, bool SAMPLE>
-__global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d, StepArgs a)
+__device__ __forceinline__ void mover_body(const Dev& d, const StepArgs& a, int cta, int ncta, bool sample_on = true)
 {
     using PosT = typename std::conditional<P64, double, uint32_t>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -519,7 +521,7 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d,
     __shared__ int s_last, s_overflow;
     __shared__ unsigned long long s_evmax, s_flushns;
 
-    unsigned long long* tr = d.trace ? d.trace + (size_t)blockIdx.x * kTraceSlots : nullptr;
+    unsigned long long* tr = d.trace ? d.trace + (size_t)cta * kTraceSlots : nullptr;
     if (tr && threadIdx.x == 0) tr[0] = gtimer();
     const unsigned int l = a.step;              // the host's step count (equal to ctl->step)
     Ctl* ctl = d.ctl;
@@ -540,11 +542,11 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d,
     }
     // sample steps (flux moment, EEDF) are a separate instantiation: the host
     // launches it when (l + 1) % diag_every == 0
-    constexpr bool sample = MODE == 0 && SAMPLE;
-    const int G = gridDim.x;
+    const bool sample = MODE == 0 && SAMPLE && sample_on;
+    const int G = ncta;
     const int Ge = electron_ctas(ne, ni, G);
-    const int s = (int)blockIdx.x < Ge ? kE : kI;
-    const int b = s == kE ? blockIdx.x : blockIdx.x - Ge;
+    const int s = (int)cta < Ge ? kE : kI;
+    const int b = s == kE ? cta : cta - Ge;
     const int Gs = s == kE ? Ge : G - Ge;
     const long long ns = s == kE ? ne : ni;
     const long long G4 = (ns + 3) >> 2;
@@ -565,7 +567,7 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d,
     long long g = cg0 + threadIdx.x;
     const long long tile1_first = min(cg1, cg0 + kTileGroups);
     Grp<P64> nxt;
-    if (g < tile1_first) nxt = load_group<P64, MODE, SAMPLE>(B, g, s == kE);
+    if (g < tile1_first) nxt = load_group<P64, MODE, SAMPLE>(B, g, s == kE && sample);
     if (tr && threadIdx.x == 0) tr[11] = gtimer();
 
     {
@@ -587,7 +589,7 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d,
             s_flushns = 0;
         }
         if (MODE == 0) {
-            const int m0 = N1 * blockIdx.x / G, m1 = N1 * (blockIdx.x + 1) / G;
+            const int m0 = N1 * cta / G, m1 = N1 * (cta + 1) / G;
             const int z = (l + 2) % 3;
             for (int i = m0 + t; i < m1; i += nt) {
                 d.qbuf[z][kE][i] = 0;
@@ -641,13 +643,13 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d,
             jlo = 0xffffffffu;
             jhi = 0;
             g = t0 + threadIdx.x;
-            if (g < t1) nxt = load_group<P64, MODE, SAMPLE>(B, g, s == kE);
+            if (g < t1) nxt = load_group<P64, MODE, SAMPLE>(B, g, s == kE && sample);
             __syncthreads();
         }
         while (g < t1) {
             Grp<P64> Gc = nxt;
             const long long gn = g + T;
-            if (gn < t1) nxt = load_group<P64, MODE, SAMPLE>(B, gn, s == kE);
+            if (gn < t1) nxt = load_group<P64, MODE, SAMPLE>(B, gn, s == kE && sample);
             if (4 * g + 4 > ns) {                     // the species' last group: slots past n are removed
                 const int rem = (int)(ns - 4 * g);
 #pragma unroll
@@ -804,8 +806,8 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d,
         flush_tile(A, N, s_jlo, s_jhi, sample, qdst, fdst, false, t, nt);
         if (tr) atomicMax(&s_flushns, gtimer() - tf);
         if (MODE == 0 && a.accumulate) {         // this CTA's share of the time averages of step l
-            const int m0 = N1 * blockIdx.x / G, m1 = N1 * (blockIdx.x + 1) / G;
-            accumulate_nodes(d, l, sqe, sqi, m0, m1, a.v_left, blockIdx.x == 0, t, nt);
+            const int m0 = N1 * cta / G, m1 = N1 * (cta + 1) / G;
+            accumulate_nodes(d, l, sqe, sqi, m0, m1, a.v_left, cta == 0, t, nt);
         }
     }
     if (MODE == 0 && s_overflow) {
@@ -827,7 +829,7 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d,
     if (sample && s == kE)
         for (int i = threadIdx.x; i < kNbEedf; i += blockDim.x)
             if (seedf[i]) atomicAdd(&d.diag.eedf[i], (unsigned long long)seedf[i]);
-    if (threadIdx.x == 0) flush_tally(d, tally);
+    if (threadIdx.x == 0) flush_tally(d, tally, cta);
     if (tr && threadIdx.x == 0) {
         tr[6] = gtimer();
         tr[12] = s_evmax;
@@ -844,6 +846,44 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d,
         commit_step(d, MODE == 0);
     }
     if (tr && threadIdx.x == 0) tr[7] = gtimer();
+}
+
+template <bool P64, int MODE, bool SAMPLE>
+__global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d, StepArgs a)
+{
+    mover_body<P64, MODE, SAMPLE>(d, a, blockIdx.x, gridDim.x);
+}
+
+// One PIC/MCC step of every discharge of a batch in one launch.  Each CTA
+// belongs to one discharge (owner[]), copies that discharge's descriptor and
+// step arguments into shared memory and runs the step kernel's body for it;
+// the discharges' results do not depend on which others share the launch.
+template <bool SAMPLE>
+__global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks)
+    k_mover_batch(const BatchEntry* __restrict__ ent, const int* __restrict__ owner)
+{
+    __shared__ __align__(16) Dev sd;
+    __shared__ StepArgs sa;
+    __shared__ int s_k;
+    if (threadIdx.x == 0) s_k = owner[blockIdx.x];
+    __syncthreads();
+    const BatchEntry& e = ent[s_k];
+    const unsigned int* src = (const unsigned int*)&e.d;
+    unsigned int* dst = (unsigned int*)&sd;
+    for (int i = threadIdx.x; i < (int)(sizeof(Dev) / 4); i += blockDim.x) dst[i] = src[i];
+    if (threadIdx.x == 0) {
+        const Ctl* c = e.d.ctl;
+        const unsigned int l = c->step;
+        StepArgs a = e.phase[l % e.period];
+        a.step = l;
+        a.accumulate = l >= e.acc_from ? 1 : 0;
+        a.cur[0] = c->cur[0];
+        a.cur[1] = c->cur[1];
+        a.cur[2] = c->cur[2];
+        sa = a;
+    }
+    __syncthreads();
+    mover_body<false, 0, SAMPLE>(sd, sa, (int)blockIdx.x - e.cta0, e.ncta);
 }
 
 // ---------------------------------------------------------------- standalone ops
@@ -1089,6 +1129,18 @@ static cudaError_t launch_mover_t(const Dev& d, const StepArgs& a, int grid, int
     if (mode == 1) k_mover<P64, 1, false><<<grid, kMoverThreads, sm, st>>>(d, a);
     else if (sample) k_mover<P64, 0, true><<<grid, kMoverThreads, sm, st>>>(d, a);
     else k_mover<P64, 0, false><<<grid, kMoverThreads, sm, st>>>(d, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mover_batch(const BatchEntry* ent, const int* owner, int grid, int max_ncell, bool sample,
+                               cudaStream_t st)
+{
+    const size_t sm = mover_smem(max_ncell);
+    const void* fn = sample ? (const void*)k_mover_batch<true> : (const void*)k_mover_batch<false>;
+    cudaError_t e = set_smem_attr(fn, sm);
+    if (e != cudaSuccess) return e;
+    if (sample) k_mover_batch<true><<<grid, kMoverThreads, sm, st>>>(ent, owner);
+    else k_mover_batch<false><<<grid, kMoverThreads, sm, st>>>(ent, owner);
     return cudaGetLastError();
 }
 
