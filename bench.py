@@ -238,6 +238,80 @@ def measure_rows(d, cfg, peak, cmp_ms, cmp_n, nsort_particles, n_atoms):
     return rows
 
 
+def measure_batched(n_discharges, steps, warmup, peak, run_periods=20):
+    """The batched form: n_discharges independent discharges of uneven size
+    (workloads.batched) stepped by one launch per step, against the plain
+    loop that steps each of them alone.  Both are timed with CUDA events
+    around every step of all members; the state (some 20 GB for 256
+    members) is far larger than L2."""
+    import torch
+    import paper_1607_04069_gb300 as P
+    from paper_1607_04069_gb300 import workloads as W
+    cfgs = W.batched(n_discharges)
+    n_part = sum(c["n_e0"] + c["n_i0"] for c in cfgs)
+    stream = torch.cuda.current_stream()
+
+    def timed(step_all):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        for a, z in ev:
+            a.record(stream)
+            step_all()
+            z.record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(z) for a, z in ev) / steps
+
+    plain = [P.Discharge(P.params_from_workload(c), stream=stream) for c in cfgs]
+
+    def plain_step():
+        for d in plain:
+            d.step(1)
+
+    for _ in range(warmup):
+        plain_step()
+    plain_ms = timed(plain_step)
+    for d in plain:
+        d.sync()
+        d.close()
+    del plain
+    torch.cuda.synchronize()
+
+    b = P.Batch(stream=stream)
+    for c in cfgs:
+        b.add(P.params_from_workload(c))
+    best = b.autotune(steps_each=10)
+    b.graphs(True)
+    b.step(warmup + (-(warmup + 6 * 11)) % cfgs[0]["diag_every"])   # back onto the sampling grid
+    batch_ms = timed(lambda: b.step(1))
+    b.sync()
+    # graph replay of whole sampling periods
+    de = cfgs[0]["diag_every"]
+    nblk = max(1, steps // de)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(nblk * de)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    graph_ms = e0.elapsed_time(e1) / (nblk * de)
+    b.sync()
+    b.close()
+    steps_per_run = run_periods * cfgs[0]["steps_per_period"]
+    best_ms = min(batch_ms, graph_ms)
+    ach = ALGO_BYTES * n_part / (best_ms * 1e-3) / 1e9
+    return {"workload": f"{n_discharges} discharges, 256-2048 cells, 50k-2M per species (log-uniform), "
+                        f"0.3-5 Pa, 50-500 V, dt = T_RF/{cfgs[0]['steps_per_period']}",
+            "particles": n_part, "value": n_part / (best_ms * 1e-3), "unit": "particle-steps/s",
+            "ms_per_step": best_ms, "ms_per_step_single_launch": batch_ms, "ms_per_step_graph": graph_ms,
+            "plain_loop_ms_per_step": plain_ms, "plain_loop_particle_steps_per_s": n_part / (plain_ms * 1e-3),
+            "speedup_vs_plain_loop": plain_ms / best_ms, "particles_per_cta": best,
+            "discharges_per_hour": n_discharges * 3600.0 / (steps_per_run * best_ms * 1e-3),
+            "plain_loop_discharges_per_hour": n_discharges * 3600.0 / (steps_per_run * plain_ms * 1e-3),
+            "run_length": f"{run_periods} RF periods ({steps_per_run} steps) per discharge, rate from "
+                          f"{steps} timed steps",
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                         "algorithmic_bytes_per_particle_step": ALGO_BYTES}}
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -271,6 +345,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=300)
     ap.add_argument("--no-rows", action="store_true")
     ap.add_argument("--tp-atoms", type=int, default=100_000_000)
+    ap.add_argument("--batch-discharges", type=int, default=256)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_setup()
@@ -382,6 +457,8 @@ def main():
     rows = None
     if rank == 0 and not args.no_rows:
         rows = measure_rows(d, cfg, peak, cmp_ms, cmp_n, 0.25 * (n_start + n_end), args.tp_atoms)
+        if args.batch_discharges > 0:
+            rows["b_batched"] = measure_batched(args.batch_discharges, 30, 10, peak)
     if rank == 0:
         line = {"metric": "particle-steps/s", "value": value, "unit": "particle-steps/s", "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,

@@ -285,6 +285,27 @@ int pic_batch_set_target(pic_batch* b, int64_t particles_per_cta);
  * member's due compactions).  Asynchronous, as pic_step. */
 int pic_batch_step(pic_batch* b, int64_t n_steps);
 
+/* enable != 0: from the next pic_batch_step on, each run of diag_every
+ * steps that starts on a multiple of diag_every and contains no member's
+ * compaction before its last step is replayed from a CUDA graph of those
+ * launches (captured once, again after the membership changes).  Results
+ * are unchanged. */
+int pic_batch_graphs(pic_batch* b, int enable);
+
+/* Waits for the batch's stream, writes to *ms / *steps (host, may be NULL)
+ * the device time of the step launches and graph replays recorded since the
+ * last call and the steps they covered (compactions excluded), clears both,
+ * and turns recording on (enable != 0) or off. */
+int pic_batch_timing(pic_batch* b, int enable, double* ms, int64_t* steps);
+
+/* Choose the particles-per-CTA division of the launch: for each of the
+ * n_cand candidates (host array; NULL or n_cand 0: 8192 ... 262144 by
+ * powers of two) run one untimed step and steps_each timed steps, then keep
+ * the candidate with the least time per step (written to *best, may be
+ * NULL).  These are real steps of every member: the division changes no
+ * result, only the time. */
+int pic_batch_autotune(pic_batch* b, const int64_t* candidates, int n_cand, int64_t steps_each, int64_t* best);
+
 /* pic_sync on every member; returns the first error. */
 int pic_batch_sync(pic_batch* b);
 

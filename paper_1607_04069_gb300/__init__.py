@@ -93,6 +93,9 @@ def lib():
             "pic_batch_set_target": [vp, i64],
             "pic_batch_step": [vp, i64],
             "pic_batch_sync": [vp],
+            "pic_batch_graphs": [vp, C.c_int],
+            "pic_batch_timing": [vp, C.c_int, C.POINTER(dbl), pi64],
+            "pic_batch_autotune": [vp, vp, C.c_int, i64, pi64],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -301,6 +304,26 @@ class Batch:
 
     def sync(self):
         _check(lib().pic_batch_sync(self.h))
+
+    def graphs(self, enable=True):
+        _check(lib().pic_batch_graphs(self.h, int(bool(enable))))
+
+    def timing(self, enable=True):
+        """Turn launch timing on or off; returns (ms, steps) recorded since the last call."""
+        ms, n = C.c_double(), C.c_int64()
+        _check(lib().pic_batch_timing(self.h, int(bool(enable)), C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+    def autotune(self, candidates=None, steps_each=20) -> int:
+        """Pick the particles-per-CTA division by timing real steps; returns it."""
+        best = C.c_int64()
+        if candidates:
+            arr = (C.c_int64 * len(candidates))(*[int(c) for c in candidates])
+            _check(lib().pic_batch_autotune(self.h, C.cast(arr, C.c_void_p), len(candidates), int(steps_each),
+                                            C.byref(best)))
+        else:
+            _check(lib().pic_batch_autotune(self.h, None, 0, int(steps_each), C.byref(best)))
+        return best.value
 
     def close(self):
         if getattr(self, "h", None):

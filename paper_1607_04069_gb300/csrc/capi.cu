@@ -984,6 +984,18 @@ struct pic_batch {
     std::vector<int> h_owner;
     int grid = 0, max_ncell = 0;
     bool dirty = true;
+    // CUDA graph of one sampling period (diag_every launches), replayed while
+    // no compaction falls inside it; captured on a private stream
+    bool use_graph = false;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    // optional event pairs around each launch or graph replay, with the steps each covers
+    bool timing = false;
+    std::vector<cudaEvent_t> tev;
+    std::vector<int> tsteps;
+    size_t tused = 0;
+    double t_ms = 0.0;
+    long long t_steps = 0;
 };
 
 namespace {
@@ -1012,6 +1024,11 @@ int batch_rebuild(pic_batch* b)
         b->max_ncell = std::max(b->max_ncell, c->p.n_cells);
     }
     b->grid = cta;
+    if (b->gexec) {
+        CK(cudaGraphExecDestroy(b->gexec));
+        b->gexec = nullptr;
+    }
+    if (b->max_ncell > 0) CK(mover_batch_attr(b->max_ncell));
     if (b->h_ent.size() > b->ent_cap) {
         if (b->d_ent) CK(cudaFree(b->d_ent));
         b->d_ent = nullptr;
@@ -1028,6 +1045,95 @@ int batch_rebuild(pic_batch* b)
         CK(cudaMemcpyAsync(b->d_owner, b->h_owner.data(), b->h_owner.size() * sizeof(int), cudaMemcpyHostToDevice,
                            b->stream));
     b->dirty = false;
+    return PIC_OK;
+}
+
+// After one step of the batch: host step counts and each member's due compactions.
+int batch_advance(pic_batch* b)
+{
+    for (pic_ctx* c : b->ctx) {
+        if (!c) continue;
+        c->acc_upto = c->h_step;
+        c->h_step++;
+        for (int s = 0; s < 2; ++s) {
+            const int every = s == kE ? c->p.sort_every_e : c->p.sort_every_i;
+            if (every > 0 && c->h_step % every == 0) {
+                CK(launch_sort(c->d, s, c->grid_sort, b->stream));
+                c->cur[s] ^= 1u;
+            }
+        }
+    }
+    return PIC_OK;
+}
+
+// Whether a member compacts after one of the first m - 1 steps from step l on.
+bool batch_sort_inside(const pic_batch* b, long long l, int m)
+{
+    for (const pic_ctx* c : b->ctx) {
+        if (!c) continue;
+        for (int s = 0; s < 2; ++s) {
+            const int every = s == kE ? c->p.sort_every_e : c->p.sort_every_i;
+            if (every <= 0) continue;
+            for (int j = 1; j < m; ++j)
+                if ((l + j) % every == 0) return true;
+        }
+    }
+    return false;
+}
+
+// Capture m step launches (the last one sampling) into the batch's graph.
+int batch_capture(pic_batch* b, int m)
+{
+    if (!b->cap_stream) CK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+    CK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int j = 0; j < m && e == cudaSuccess; ++j)
+        e = launch_mover_batch(b->d_ent, b->d_owner, b->grid, b->max_ncell, j == m - 1, b->cap_stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->gexec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->gexec = nullptr;
+        return cuda_fail(e, "batch graph capture");
+    }
+    return PIC_OK;
+}
+
+int batch_timers_collect(pic_batch* b)
+{
+    for (size_t i = 0; i + 1 < b->tused; i += 2) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, b->tev[i], b->tev[i + 1]));
+        b->t_ms += ms;
+        b->t_steps += b->tsteps[i / 2];
+    }
+    b->tused = 0;
+    return PIC_OK;
+}
+
+// begin: record the start of a timed launch covering `steps` steps; else its end.
+int batch_timer(pic_batch* b, int steps, bool begin)
+{
+    if (!b->timing) return PIC_OK;
+    if (begin) {
+        if (b->tused + 2 > b->tev.size()) {
+            for (int i = 0; i < 64; ++i) {
+                cudaEvent_t ev;
+                CK(cudaEventCreate(&ev));
+                b->tev.push_back(ev);
+            }
+        }
+        b->tsteps.resize(b->tev.size() / 2);
+        b->tsteps[b->tused / 2] = steps;
+    }
+    CK(cudaEventRecord(b->tev[b->tused], b->stream));
+    ++b->tused;
+    if (!begin && b->tused >= 4096) {
+        CK(cudaStreamSynchronize(b->stream));
+        return batch_timers_collect(b);
+    }
     return PIC_OK;
 }
 
@@ -1148,23 +1254,85 @@ int pic_batch_step(pic_batch* b, int64_t n)
     CK(cudaMemcpyAsync(b->d_ent, b->h_ent.data(), b->h_ent.size() * sizeof(BatchEntry), cudaMemcpyHostToDevice,
                        b->stream));
     const int de = first->p.diag_every;
-    for (int64_t k = 0; k < n; ++k) {
+    int64_t k = 0;
+    while (k < n) {
         const long long l = first->h_step;
-        const bool sample = de > 0 && (l + 1) % de == 0;   // members sample on the same steps
-        CK(launch_mover_batch(b->d_ent, b->d_owner, b->grid, b->max_ncell, sample, b->stream));
-        for (pic_ctx* c : b->ctx) {
-            if (!c) continue;
-            c->acc_upto = c->h_step;
-            c->h_step++;
-            for (int s = 0; s < 2; ++s) {
-                const int every = s == kE ? c->p.sort_every_e : c->p.sort_every_i;
-                if (every > 0 && c->h_step % every == 0) {
-                    CK(launch_sort(c->d, s, c->grid_sort, b->stream));
-                    c->cur[s] ^= 1u;
-                }
-            }
+        const bool block = b->use_graph && de > 1 && l % de == 0 && n - k >= de && !batch_sort_inside(b, l, de);
+        if (block && !b->gexec) {
+            int rc = batch_capture(b, de);
+            if (rc) return rc;
+        }
+        int rc = batch_timer(b, block ? de : 1, true);
+        if (rc) return rc;
+        if (block) CK(cudaGraphLaunch(b->gexec, b->stream));
+        else CK(launch_mover_batch(b->d_ent, b->d_owner, b->grid, b->max_ncell, de > 0 && (l + 1) % de == 0,
+                                   b->stream));
+        rc = batch_timer(b, 0, false);
+        if (rc) return rc;
+        const int m = block ? de : 1;
+        for (int j = 0; j < m; ++j) {
+            rc = batch_advance(b);
+            if (rc) return rc;
+        }
+        k += m;
+    }
+    return PIC_OK;
+}
+
+int pic_batch_graphs(pic_batch* b, int enable)
+{
+    if (!b) return fail(PIC_ERR_INVALID_ARG, "batch is NULL");
+    b->use_graph = enable != 0;
+    return PIC_OK;
+}
+
+int pic_batch_timing(pic_batch* b, int enable, double* ms, int64_t* steps)
+{
+    if (!b) return fail(PIC_ERR_INVALID_ARG, "batch is NULL");
+    CK(cudaStreamSynchronize(b->stream));
+    int rc = batch_timers_collect(b);
+    if (rc) return rc;
+    if (ms) *ms = b->t_ms;
+    if (steps) *steps = b->t_steps;
+    b->t_ms = 0.0;
+    b->t_steps = 0;
+    b->timing = enable != 0;
+    return PIC_OK;
+}
+
+int pic_batch_autotune(pic_batch* b, const int64_t* candidates, int n_cand, int64_t steps_each, int64_t* best)
+{
+    static const int64_t kDefault[] = {8192, 16384, 32768, 65536, 131072, 262144};
+    if (!b || n_cand < 0 || steps_each < 1) return fail(PIC_ERR_INVALID_ARG, "bad autotune arguments");
+    if (!candidates || n_cand == 0) {
+        candidates = kDefault;
+        n_cand = (int)(sizeof(kDefault) / sizeof(kDefault[0]));
+    }
+    const bool was = b->timing;
+    double best_ms = 0.0;
+    int64_t best_t = b->target;
+    for (int i = 0; i < n_cand; ++i) {
+        int rc = pic_batch_set_target(b, candidates[i]);
+        if (rc) return rc;
+        rc = pic_batch_step(b, 1);                       // rebuild and first launch outside the window
+        if (rc) return rc;
+        rc = pic_batch_timing(b, 1, nullptr, nullptr);
+        if (rc) return rc;
+        rc = pic_batch_step(b, steps_each);
+        if (rc) return rc;
+        double ms = 0.0;
+        int64_t st = 0;
+        rc = pic_batch_timing(b, was, &ms, &st);
+        if (rc) return rc;
+        const double per = st > 0 ? ms / (double)st : 0.0;
+        if (i == 0 || per < best_ms) {
+            best_ms = per;
+            best_t = candidates[i];
         }
     }
+    int rc = pic_batch_set_target(b, best_t);
+    if (rc) return rc;
+    if (best) *best = best_t;
     return PIC_OK;
 }
 
@@ -1189,6 +1357,9 @@ void pic_batch_destroy(pic_batch* b)
     }
     if (b->d_ent) cudaFree(b->d_ent);
     if (b->d_owner) cudaFree(b->d_owner);
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    for (cudaEvent_t ev : b->tev) cudaEventDestroy(ev);
     delete b;
 }
 

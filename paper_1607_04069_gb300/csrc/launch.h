@@ -19,12 +19,15 @@ cudaError_t mover_occupancy(const Dev& d, int* blocks_per_sm);
 cudaError_t launch_init(const Dev& d, int s, long long n, float vth, cudaStream_t st);
 // mode 0: one PIC/MCC step; mode 1: deposit the current state and solve the field
 cudaError_t launch_mover(const Dev& d, const StepArgs& a, int grid, int mode, cudaStream_t st);
-// FP64 field/potential of the current state; accumulate != 0 also adds the
-// current step to the time averages if no step launch has done so yet
 // one step of every discharge of a batch (32-bit positions); sample: the launch
-// samples the moments of the discharges whose entry says so
+// samples the flux moments and the EEDF of every member.  mover_batch_attr
+// must have been called with max_ncell first.
 cudaError_t launch_mover_batch(const BatchEntry* ent, const int* owner, int grid, int max_ncell, bool sample,
                                cudaStream_t st);
+// the shared-memory attribute of both batch instantiations (set before a graph capture)
+cudaError_t mover_batch_attr(int max_ncell);
+// FP64 field/potential of the current state; accumulate != 0 also adds the
+// current step to the time averages if no step launch has done so yet
 cudaError_t launch_field(const Dev& d, double v_left, int accumulate, cudaStream_t st);
 // first null-collision candidate step of n uploaded particles that are first pushed at step l0
 cudaError_t launch_entry_nev(const Dev& d, int s, unsigned int half, long long n, unsigned int l0, cudaStream_t st);

@@ -1135,13 +1135,18 @@ static cudaError_t launch_mover_t(const Dev& d, const StepArgs& a, int grid, int
 cudaError_t launch_mover_batch(const BatchEntry* ent, const int* owner, int grid, int max_ncell, bool sample,
                                cudaStream_t st)
 {
-    const size_t sm = mover_smem(max_ncell);
-    const void* fn = sample ? (const void*)k_mover_batch<true> : (const void*)k_mover_batch<false>;
-    cudaError_t e = set_smem_attr(fn, sm);
-    if (e != cudaSuccess) return e;
+    const size_t sm = mover_smem(max_ncell);      // attribute set by mover_batch_attr
     if (sample) k_mover_batch<true><<<grid, kMoverThreads, sm, st>>>(ent, owner);
     else k_mover_batch<false><<<grid, kMoverThreads, sm, st>>>(ent, owner);
     return cudaGetLastError();
+}
+
+cudaError_t mover_batch_attr(int max_ncell)
+{
+    const size_t sm = mover_smem(max_ncell);
+    cudaError_t e = set_smem_attr((const void*)k_mover_batch<true>, sm);
+    if (e != cudaSuccess) return e;
+    return set_smem_attr((const void*)k_mover_batch<false>, sm);
 }
 
 cudaError_t launch_mover(const Dev& d, const StepArgs& a, int grid, int mode, cudaStream_t st)

@@ -13,6 +13,8 @@ Sec. "Simulation Scenario", with the sizes of the benchmark configurations):
   2M e- + 2M Ar+, 32-bit positions, sputtering on, TP sub-cycled x40.
 * ``tp_transport`` -- 100M Al atoms from a 300 eV mono-energetic Ar+ source,
   50 mm gap, hard spheres (3e-19 m^2) in 0.5 Pa / 300 K Ar, dt_tp = 1 ns.
+* ``batched``     -- many independent discharges of uneven size stepped
+  together, and ``poisson_arrivals`` for a stream of such requests.
 """
 from __future__ import annotations
 
@@ -52,6 +54,36 @@ def tp_transport(n_atoms: int = 100_000_000, seed: int = 1237) -> dict:
                 n_cells=1024, weight=1.0, dt=T_RF / 3000, n_e0=0, n_i0=0, te0_ev=2.0,
                 ti0_ev=0.026, seed=seed, pos_precision=32, sputter_enable=0, tp_every=0,
                 tp_dt=1e-9, sigma_tp=3e-19, diag_every=10, n_atoms=n_atoms, e_ion_ev=300.0)
+
+
+def batched(n_discharges: int = 256, seed: int = 1238, n_min: int = 50_000, n_max: int = 2_000_000,
+            steps_per_period: int = 3000) -> list[dict]:
+    """Independent discharges of uneven size for one batched launch: cell
+    counts 256-2048 (powers of two), 50k-2M superparticles per species
+    (log-uniform), 0.3-5 Pa (log-uniform), 50-500 V, gap 25-50 mm, all at
+    13.56 MHz with one dt = T_RF / steps_per_period, 32-bit positions, no
+    sputtering.  Density 1e15 m^-3 at load, so dx < lambda_D at 2 eV."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n_discharges):
+        n = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max)))))
+        n_cells = int(2 ** rng.integers(8, 12))
+        L = float(rng.uniform(0.025, 0.05))
+        p = float(math.exp(rng.uniform(math.log(0.3), math.log(5.0))))
+        V = float(rng.uniform(50.0, 500.0))
+        out.append(dict(name=f"member {k}: {L * 1e3:.1f} mm/{n_cells} cells/{V:.0f} V/{p:.2f} Pa, {n}+{n}",
+                        gap_m=L, pressure_pa=p, gas_temp_k=300.0, rf_freq_hz=F_RF, rf_volt_v=V,
+                        n_cells=n_cells, weight=1e15 * L / n, dt=T_RF / steps_per_period, n_e0=n, n_i0=n,
+                        te0_ev=2.0, ti0_ev=0.026, seed=seed * 1000 + k, pos_precision=32, sputter_enable=0,
+                        tp_every=0, tp_dt=1e-9, sigma_tp=3e-19, diag_every=10, sort_every_e=400,
+                        sort_every_i=400, steps_per_period=steps_per_period))
+    return out
+
+
+def poisson_arrivals(rate_hz: float, n: int, seed: int) -> np.ndarray:
+    """Arrival times (s) of n requests of a Poisson stream of the given mean rate."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate_hz, size=n))
 
 
 def oracle_params(cfg: dict) -> dict:

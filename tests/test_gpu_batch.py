@@ -130,3 +130,27 @@ def test_admission_rules(P):
     empty = P.Batch()
     empty.step(3)                                  # nothing to do
     empty.close()
+
+
+def test_graphs_timing_and_autotune_change_nothing(P):
+    """Graph replay (with a member whose compaction period, 33, is no
+    multiple of the sampling period, so some runs fall back to single
+    launches), the launch timers and the autotuner's candidate divisions
+    leave every member's state as it is when stepped alone."""
+    members = [MEMBERS[0], _cfg(6_000, 12, pressure_pa=5.0, sort_every_i=33), MEMBERS[2]]
+    b = P.Batch(particles_per_cta=16_384)
+    b.graphs(True)
+    slots = [b.add(P.params_from_workload(c)) for c in members]
+    b.step(5)                                      # off the sampling grid: single launches first
+    b.timing(True)
+    b.step(40)
+    ms, steps = b.timing(False)
+    assert steps == 40 and ms > 0.0
+    best = b.autotune([8192, 32768], steps_each=10)
+    assert best in (8192, 32768)
+    b.step(150 - 5 - 40 - 2 * 11)
+    b.sync()
+    got = [_state(b.member(k)) for k in slots]
+    b.close()
+    for k, c in enumerate(members):
+        _same(got[k], _alone(c, 150), f"member {k}")
