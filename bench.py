@@ -312,6 +312,52 @@ def measure_batched(n_discharges, steps, warmup, peak, run_periods=20):
                          "algorithmic_bytes_per_particle_step": ALGO_BYTES}}
 
 
+def measure_served(n_requests, rate_hz, max_periods, tol=0.01, seed=1239):
+    """The served form: a Poisson stream of discharge requests drawn from the
+    batched workload's ranges, each run to periodic steady state (relative
+    period-to-period change of the cycle-averaged n_e and n_i below tol, at
+    most max_periods RF periods) by the library's request loop, once with
+    the batched worker and once with the plain loop of pic_step calls.
+    Latency is completion minus arrival on the server's clock."""
+    import numpy as np
+    import paper_1607_04069_gb300 as P
+    from paper_1607_04069_gb300 import workloads as W
+    cfgs = W.batched(n_requests, seed=seed)
+    arrivals = W.poisson_arrivals(rate_hz, n_requests, seed)
+    out = {}
+    for mode, batched in (("batched", 1), ("plain_loop", 0)):
+        srv = P.Server(batched=batched, max_periods=max_periods, tol=tol)
+        t0 = srv.clock()
+        ids = []
+        for c, a in zip(cfgs, arrivals):
+            while srv.clock() < t0 + a:
+                time.sleep(min(0.005, max(0.0, t0 + a - srv.clock())))
+            ids.append(srv.submit(P.params_from_workload(c), t0 + a))
+        infos = [srv.wait(i) for i in ids]
+        st = srv.stats()
+        srv.close()
+        lat = np.array([i["t_done"] - i["t_arrival"] for i in infos])
+        ok = [i for i in infos if i["state"] in ("converged", "max_periods")]
+        span = max(i["t_done"] for i in infos) - (t0 + arrivals[0])
+        out[mode] = {"p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+                     "discharges_per_hour": len(ok) * 3600.0 / span, "span_s": span,
+                     "converged": sum(i["state"] == "converged" for i in infos),
+                     "hit_max_periods": sum(i["state"] == "max_periods" for i in infos),
+                     "failed": len(infos) - len(ok),
+                     "periods_mean": float(np.mean([i["periods"] for i in infos])),
+                     "last_change_median": float(np.median([i["change"] for i in infos])),
+                     "particle_steps_per_s_busy": st["particle_steps"] / max(st["busy_s"], 1e-9)}
+    b, l = out["batched"], out["plain_loop"]
+    return {"workload": f"{n_requests} requests, Poisson arrivals at {rate_hz:g}/s, sizes and conditions drawn "
+                        f"as in the batched workload, each run to steady state (relative change of the "
+                        f"period-averaged e- and Ar+ inventories < {tol:g} between RF periods, at most "
+                        f"{max_periods} periods)",
+            "value": b["discharges_per_hour"], "unit": "discharges/hour",
+            "p50_latency_s": b["p50_latency_s"], "p99_latency_s": b["p99_latency_s"],
+            "speedup_vs_plain_loop": b["discharges_per_hour"] / l["discharges_per_hour"],
+            "batched": b, "plain_loop": l}
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -346,6 +392,9 @@ def main():
     ap.add_argument("--no-rows", action="store_true")
     ap.add_argument("--tp-atoms", type=int, default=100_000_000)
     ap.add_argument("--batch-discharges", type=int, default=256)
+    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-rate", type=float, default=4.0)
+    ap.add_argument("--serve-max-periods", type=int, default=20)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_setup()
@@ -459,6 +508,8 @@ def main():
         rows = measure_rows(d, cfg, peak, cmp_ms, cmp_n, 0.25 * (n_start + n_end), args.tp_atoms)
         if args.batch_discharges > 0:
             rows["b_batched"] = measure_batched(args.batch_discharges, 30, 10, peak)
+        if args.serve_requests > 0:
+            rows["c_served"] = measure_served(args.serve_requests, args.serve_rate, args.serve_max_periods)
     if rank == 0:
         line = {"metric": "particle-steps/s", "value": value, "unit": "particle-steps/s", "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,

@@ -40,6 +40,7 @@ extern "C" {
 #define PIC_ERR_NUMERICS (-5)        /* an electron exceeded the null-collision energy cap */
 #define PIC_ERR_CUDA (-7)            /* a CUDA call failed (detail in pic_last_error)      */
 #define PIC_ERR_NO_DEVICE (-8)       /* no CUDA device is visible                          */
+#define PIC_ERR_TIMEOUT (-9)         /* pic_server_wait: the request had not finished      */
 
 enum pic_species { PIC_ELECTRON = 0, PIC_ION = 1, PIC_ATOM = 2 };
 
@@ -90,6 +91,10 @@ int pic_params_default(pic_params* p);
  * solve the field of that state (Sec. "EM Field Solver").  `stream` is a
  * cudaStream_t or NULL.  On success *out owns the context. */
 int pic_create(const pic_params* p, void* stream, pic_ctx** out);
+
+/* Device bytes pic_create would allocate for p (capacities left at 0 take
+ * their defaults); nothing is allocated.  For admission by memory budget. */
+int pic_state_bytes(const pic_params* p, int64_t* bytes);
 
 /* Release everything the context owns (waits for its stream). */
 void pic_destroy(pic_ctx* ctx);
@@ -258,7 +263,9 @@ int pic_op_sort_noalloc(int pos_precision, int64_t n, int32_t n_cells, const voi
  * l mod period in both forms.  A member joins (pic_batch_add) only while every
  * current member stands at a multiple of diag_every steps, so that all of
  * them sample on the same steps.  Each member keeps 2 or more CTAs,
- * ceil((n_e0 + n_i0) / particles_per_cta) of them (default 65536). */
+ * ceil((n_e0 + n_i0) / particles_per_cta) of them; by default (0) the
+ * division is automatic: two waves of resident CTAs over all members'
+ * particles, clamped to [2048, 16384] particles per CTA. */
 typedef struct pic_batch pic_batch; /* opaque */
 
 /* Create an empty batch whose work goes to `stream` (cudaStream_t or NULL). */
@@ -278,7 +285,8 @@ int pic_batch_remove(pic_batch* b, int slot);
  * pic_step it while it belongs to the batch. */
 int pic_batch_ctx(pic_batch* b, int slot, pic_ctx** out);
 
-/* Particles per CTA when the launch is divided among members (>= 1024). */
+/* Particles per CTA when the launch is divided among members (>= 1024, or
+ * 0 for the automatic division). */
 int pic_batch_set_target(pic_batch* b, int64_t particles_per_cta);
 
 /* Advance every member n_steps steps (one launch per step plus each
@@ -311,6 +319,101 @@ int pic_batch_sync(pic_batch* b);
 
 /* Destroy every member and the batch. */
 void pic_batch_destroy(pic_batch* b);
+
+/* ------------------------------------------------------------ serving
+ * A request loop that runs submitted discharges to periodic steady state.
+ * The paper has no counterpart; each discharge runs the PIC/MCC cycle of
+ * pic_step, and steady state is the criterion of its Sec. "Simulation
+ * Results": the cycle-averaged quantities no longer change from one RF
+ * period to the next.
+ *
+ * One worker thread (started by pic_server_create on the current device,
+ * with its own stream) admits queued requests in arrival order while the
+ * sum of their state sizes (pic_state_bytes) stays within the budget, keeps
+ * every admitted discharge resident, and steps them all together -- one
+ * pic_batch, or one pic_step call per discharge when batched is 0 -- in
+ * chunks of 1/chunks_per_period of an RF period (admission happens between
+ * chunks).  At each of a discharge's period boundaries it reads the
+ * period-averaged n_e and n_i; once at least min_periods periods have run and
+ * the relative change of both from the period before is below tol, the
+ * request completes with state CONVERGED (or MAX_PERIODS when max_periods > 0
+ * periods have run), its last period-averaged n_e, n_i and phi are kept on the
+ * host and its device state is released.  Requests follow the pic_batch rules
+ * (32-bit positions, one dt and diag_every, a whole number of steps per RF
+ * period that is a multiple of the chunk); others complete as FAILED, and a
+ * state larger than the whole budget as REJECTED.  The change is that of
+ * the inventory, the spatial integral of the density (criterion
+ * PIC_STEADY_INVENTORY, the default: in steady state generation and losses
+ * balance, Sec. "Simulation Results"), or of the profile in L2 over the
+ * nodes (PIC_STEADY_PROFILE, which the statistical noise of small
+ * discharges can keep above tol).  All functions are
+ * thread-safe.  Times are seconds on the server's monotonic clock
+ * (pic_server_clock), zero at creation. */
+typedef struct pic_server pic_server; /* opaque */
+
+typedef struct pic_server_opts {
+    int64_t hbm_budget_bytes;  /* device bytes the resident discharges may hold; 0: 80% of free memory */
+    int32_t min_periods;       /* RF periods before the steady-state test (>= 2)             */
+    int32_t max_periods;       /* a request ends after this many periods (0: no limit)       */
+    double tol;                /* steady state: relative L2 change of n_e and n_i below tol  */
+    int32_t batched;           /* 1: one batch launch per step; 0: a plain loop of pic_step   */
+    int32_t graphs;            /* batched: replay sampling periods from CUDA graphs          */
+    int32_t chunks_per_period; /* admission / check granularity (default 10)                  */
+    int32_t criterion;         /* PIC_STEADY_INVENTORY (default) or PIC_STEADY_PROFILE        */
+} pic_server_opts;
+
+enum pic_steady_criterion { PIC_STEADY_INVENTORY = 0, PIC_STEADY_PROFILE = 1 };
+
+enum pic_request_state {
+    PIC_REQ_QUEUED = 0, PIC_REQ_RUNNING, PIC_REQ_CONVERGED, PIC_REQ_MAX_PERIODS, PIC_REQ_REJECTED,
+    PIC_REQ_FAILED
+};
+
+typedef struct pic_request_info {
+    int64_t id;
+    int32_t state;             /* pic_request_state                                          */
+    int32_t periods;           /* RF periods completed                                       */
+    double t_arrival, t_admit, t_done;   /* server clock (s); -1 until reached               */
+    double change;             /* last period-to-period relative change (-1 before the 2nd)  */
+    int64_t bytes;             /* device bytes of the discharge's state                      */
+    int64_t particles;         /* initial superparticles, e- + Ar+                            */
+} pic_request_info;
+
+typedef struct pic_server_stats {
+    int64_t queued, running, done;       /* requests in each phase                          */
+    int64_t bytes_used, budget;          /* device bytes held by admitted requests; budget   */
+    int64_t chunks, steps;               /* step chunks the worker ran, and their steps      */
+    double particle_steps;               /* sum over chunks of initial particles x steps     */
+    double busy_s;                       /* worker time spent in the chunks                  */
+} pic_server_stats;
+
+/* Defaults: budget 0 (80% of free), min_periods 2, max_periods 0, tol 0.01,
+ * batched 1, graphs 1, chunks_per_period 10, criterion inventory. */
+int pic_server_opts_default(pic_server_opts* o);
+/* opts may be NULL (defaults). */
+int pic_server_create(const pic_server_opts* opts, pic_server** out);
+int pic_server_clock(pic_server* s, double* t);
+/* Queue a request; t_arrival (server clock, <= now; negative: now) is the
+ * time latency is measured from.  *id receives the request id. */
+int pic_server_submit(pic_server* s, const pic_params* p, double t_arrival, int64_t* id);
+/* Current state of a request (host struct, written by the call). */
+int pic_server_info(pic_server* s, int64_t id, pic_request_info* info);
+/* Block until the request has finished (timeout_s < 0: no limit); returns
+ * PIC_ERR_TIMEOUT if it has not within timeout_s.  info may be NULL. */
+int pic_server_wait(pic_server* s, int64_t id, double timeout_s, pic_request_info* info);
+/* Why a request FAILED or was REJECTED (NUL-terminated, at most cap bytes). */
+int pic_server_error(pic_server* s, int64_t id, char* out, int64_t cap);
+/* The last period-averaged profile of a request: what 0 = n_e, 1 = n_i
+ * (m^-3), 2 = phi (V), n_cells + 1 node values into host `out` (cap
+ * doubles; *n receives the count, 0 before the first period). */
+int pic_server_result(pic_server* s, int64_t id, int what, double* out, int64_t cap, int64_t* n);
+/* Drop a finished request's record. */
+int pic_server_forget(pic_server* s, int64_t id);
+/* Counters of the server (host struct); PIC_ERR_CUDA if the worker stopped
+ * on a device error (every running request then FAILED). */
+int pic_server_status(pic_server* s, pic_server_stats* out);
+/* Stop the worker (running requests are abandoned) and free everything. */
+void pic_server_destroy(pic_server* s);
 
 const char* pic_strerror(int code);
 const char* pic_last_error(void);

@@ -50,6 +50,35 @@ class PicParams(C.Structure):
                 ("ctas_per_sm", C.c_int32), ("strict", C.c_int32)]
 
 
+class ServerOpts(C.Structure):
+    """Mirror of ``pic_server_opts``."""
+    _fields_ = [("hbm_budget_bytes", C.c_int64), ("min_periods", C.c_int32), ("max_periods", C.c_int32),
+                ("tol", C.c_double), ("batched", C.c_int32), ("graphs", C.c_int32),
+                ("chunks_per_period", C.c_int32), ("criterion", C.c_int32)]
+
+
+class RequestInfo(C.Structure):
+    """Mirror of ``pic_request_info``."""
+    _fields_ = [("id", C.c_int64), ("state", C.c_int32), ("periods", C.c_int32), ("t_arrival", C.c_double),
+                ("t_admit", C.c_double), ("t_done", C.c_double), ("change", C.c_double),
+                ("bytes", C.c_int64), ("particles", C.c_int64)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["state"] = REQUEST_STATES[self.state]
+        return d
+
+
+class ServerStats(C.Structure):
+    """Mirror of ``pic_server_stats``."""
+    _fields_ = [("queued", C.c_int64), ("running", C.c_int64), ("done", C.c_int64), ("bytes_used", C.c_int64),
+                ("budget", C.c_int64), ("chunks", C.c_int64), ("steps", C.c_int64),
+                ("particle_steps", C.c_double), ("busy_s", C.c_double)]
+
+
+REQUEST_STATES = ["queued", "running", "converged", "max_periods", "rejected", "failed"]
+
+
 class TpSource(C.Structure):
     _fields_ = [("n", C.c_int64), ("e_ion_ev", C.c_double)]
 
@@ -96,12 +125,23 @@ def lib():
             "pic_batch_graphs": [vp, C.c_int],
             "pic_batch_timing": [vp, C.c_int, C.POINTER(dbl), pi64],
             "pic_batch_autotune": [vp, vp, C.c_int, i64, pi64],
+            "pic_state_bytes": [C.POINTER(PicParams), pi64],
+            "pic_server_opts_default": [C.POINTER(ServerOpts)],
+            "pic_server_create": [C.POINTER(ServerOpts), C.POINTER(vp)],
+            "pic_server_clock": [vp, C.POINTER(dbl)],
+            "pic_server_submit": [vp, C.POINTER(PicParams), dbl, pi64],
+            "pic_server_info": [vp, i64, C.POINTER(RequestInfo)],
+            "pic_server_wait": [vp, i64, dbl, C.POINTER(RequestInfo)],
+            "pic_server_error": [vp, i64, C.c_char_p, i64],
+            "pic_server_result": [vp, i64, C.c_int, vp, i64, pi64],
+            "pic_server_forget": [vp, i64],
+            "pic_server_status": [vp, C.POINTER(ServerStats)],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
             fn.argtypes = args
             fn.restype = C.c_int
-        for name in ("pic_destroy", "pic_batch_destroy"):
+        for name in ("pic_destroy", "pic_batch_destroy", "pic_server_destroy"):
             getattr(L, name).argtypes = [vp]
             getattr(L, name).restype = None
         L.pic_strerror.argtypes = [C.c_int]
@@ -328,6 +368,80 @@ class Batch:
     def close(self):
         if getattr(self, "h", None):
             lib().pic_batch_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+
+def state_bytes(params) -> int:
+    """Device bytes a discharge with these parameters holds (``pic_state_bytes``)."""
+    if isinstance(params, dict):
+        params = params_from_workload(params)
+    n = C.c_int64()
+    _check(lib().pic_state_bytes(C.byref(params), C.byref(n)))
+    return n.value
+
+
+class Server:
+    """Request loop running discharges to periodic steady state (``pic_server_*``).
+    Its worker thread owns the device work; every method is thread-safe."""
+
+    def __init__(self, **opts):
+        o = ServerOpts()
+        _check(lib().pic_server_opts_default(C.byref(o)))
+        for k, v in opts.items():
+            setattr(o, k, v)
+        h = C.c_void_p()
+        _check(lib().pic_server_create(C.byref(o), C.byref(h)))
+        self.h = h
+        self.opts = o
+
+    def clock(self) -> float:
+        t = C.c_double()
+        _check(lib().pic_server_clock(self.h, C.byref(t)))
+        return t.value
+
+    def submit(self, params, t_arrival=-1.0) -> int:
+        if isinstance(params, dict):
+            params = params_from_workload(params)
+        rid = C.c_int64()
+        _check(lib().pic_server_submit(self.h, C.byref(params), float(t_arrival), C.byref(rid)))
+        return rid.value
+
+    def info(self, rid) -> dict:
+        i = RequestInfo()
+        _check(lib().pic_server_info(self.h, int(rid), C.byref(i)))
+        return i.as_dict()
+
+    def wait(self, rid, timeout=-1.0) -> dict:
+        i = RequestInfo()
+        _check(lib().pic_server_wait(self.h, int(rid), float(timeout), C.byref(i)))
+        return i.as_dict()
+
+    def error(self, rid) -> str:
+        buf = C.create_string_buffer(512)
+        _check(lib().pic_server_error(self.h, int(rid), buf, len(buf)))
+        return buf.value.decode()
+
+    def result(self, rid, what) -> np.ndarray:
+        k = {"n_e": 0, "n_i": 1, "phi": 2}.get(what, what)
+        n = C.c_int64()
+        _check(lib().pic_server_result(self.h, int(rid), int(k), None, 0, C.byref(n)))
+        out = np.zeros(n.value)
+        _check(lib().pic_server_result(self.h, int(rid), int(k), _ptr(out), out.size, C.byref(n)))
+        return out
+
+    def forget(self, rid):
+        _check(lib().pic_server_forget(self.h, int(rid)))
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().pic_server_status(self.h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in st._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pic_server_destroy(self.h)
             self.h = None
 
     __del__ = close

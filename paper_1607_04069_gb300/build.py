@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libpic_gb300.so")
-SOURCES = ["capi.cu", "pic_kernels.cu", "tp_kernels.cu", "noalloc.cu"]
+SOURCES = ["capi.cu", "pic_kernels.cu", "tp_kernels.cu", "noalloc.cu", "server.cu"]
 HEADERS = ["common.cuh", "solve.cuh", "launch.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",

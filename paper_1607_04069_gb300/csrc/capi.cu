@@ -140,6 +140,14 @@ void carve(pic_ctx* c, char* base, size_t* small_end, size_t* total)
     *total = (L.off + 255) & ~(size_t)255;
 }
 
+// capacities left at 0: the initial load plus a quarter plus 65536 slots
+void default_caps(pic_params* q)
+{
+    if (q->cap_e == 0) q->cap_e = q->n_e0 + q->n_e0 / 4 + 65536;
+    if (q->cap_i == 0) q->cap_i = q->n_i0 + q->n_i0 / 4 + 65536;
+    if (q->cap_tp == 0) q->cap_tp = 65536;
+}
+
 int validate(const pic_params* p)
 {
     if (!p) return fail(PIC_ERR_INVALID_ARG, "params is NULL");
@@ -365,15 +373,29 @@ int pic_params_default(pic_params* p)
     return PIC_OK;
 }
 
+int pic_state_bytes(const pic_params* pin, int64_t* bytes)
+{
+    if (!pin || !bytes) return fail(PIC_ERR_INVALID_ARG, "NULL argument");
+    pic_params q = *pin;
+    default_caps(&q);
+    int rc = validate(&q);
+    if (rc) return rc;
+    pic_ctx tmp;
+    tmp.p = q;
+    derive(&tmp);
+    size_t small_end = 0, total = 0;
+    carve(&tmp, nullptr, &small_end, &total);
+    *bytes = (int64_t)total;
+    return PIC_OK;
+}
+
 int pic_create(const pic_params* pin, void* stream, pic_ctx** out)
 {
     if (!out) return fail(PIC_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!pin) return fail(PIC_ERR_INVALID_ARG, "params is NULL");
     pic_params q = *pin;
-    if (q.cap_e == 0) q.cap_e = q.n_e0 + q.n_e0 / 4 + 65536;
-    if (q.cap_i == 0) q.cap_i = q.n_i0 + q.n_i0 / 4 + 65536;
-    if (q.cap_tp == 0) q.cap_tp = 65536;
+    default_caps(&q);
     int rc = validate(&q);
     if (rc) return rc;
     int ndev = 0;
@@ -963,6 +985,7 @@ const char* pic_strerror(int code)
     case PIC_ERR_NUMERICS: return "electron energy above the null-collision bound";
     case PIC_ERR_CUDA: return "CUDA error";
     case PIC_ERR_NO_DEVICE: return "no CUDA device";
+    case PIC_ERR_TIMEOUT: return "timed out";
     default: return "unknown error";
     }
 }
@@ -976,7 +999,7 @@ struct pic_batch {
     std::vector<pic_ctx*> ctx;             // slots; nullptr where a discharge was removed
     std::vector<StepArgs*> phase;          // per slot: device table of the step arguments of one RF period
     cudaStream_t stream = nullptr;
-    long long target = 65536;              // particles per CTA of the batched launch
+    long long target = 0;                  // particles per CTA of the batched launch; 0: automatic
     BatchEntry* d_ent = nullptr;
     int* d_owner = nullptr;
     size_t ent_cap = 0, owner_cap = 0;
@@ -1005,12 +1028,31 @@ int batch_rebuild(pic_batch* b)
     b->h_ent.clear();
     b->h_owner.clear();
     b->max_ncell = 0;
+    long long total = 0;
+    for (pic_ctx* c : b->ctx)
+        if (c) {
+            b->max_ncell = std::max(b->max_ncell, c->p.n_cells);
+            total += c->p.n_e0 + c->p.n_i0;
+        }
+    int per_sm = 0;
+    if (b->max_ncell > 0) CK(mover_batch_attr(b->max_ncell, &per_sm));
+    long long target = b->target;
+    if (target <= 0) {
+        // automatic: at least two waves of resident CTAs, at most 16384
+        // particles per CTA (the best division the autotuner found for a
+        // launch of many waves), at least 2048
+        int dev = 0, sms = 1;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const long long slots = (long long)sms * std::max(per_sm, 1);
+        target = std::min(16384ll, std::max(2048ll, (total + 2 * slots - 1) / (2 * slots)));
+    }
     int cta = 0;
     for (size_t k = 0; k < b->ctx.size(); ++k) {
         pic_ctx* c = b->ctx[k];
         if (!c) continue;
         const long long np = c->p.n_e0 + c->p.n_i0;
-        const int ncta = (int)std::max(2ll, (np + b->target - 1) / b->target);
+        const int ncta = (int)std::max(2ll, (np + target - 1) / target);
         BatchEntry e;
         std::memset(&e, 0, sizeof e);
         e.d = c->d;
@@ -1021,14 +1063,12 @@ int batch_rebuild(pic_batch* b)
         b->h_ent.push_back(e);
         for (int i = 0; i < ncta; ++i) b->h_owner.push_back((int)b->h_ent.size() - 1);
         cta += ncta;
-        b->max_ncell = std::max(b->max_ncell, c->p.n_cells);
     }
     b->grid = cta;
     if (b->gexec) {
         CK(cudaGraphExecDestroy(b->gexec));
         b->gexec = nullptr;
     }
-    if (b->max_ncell > 0) CK(mover_batch_attr(b->max_ncell));
     if (b->h_ent.size() > b->ent_cap) {
         if (b->d_ent) CK(cudaFree(b->d_ent));
         b->d_ent = nullptr;
@@ -1220,7 +1260,8 @@ int pic_batch_ctx(pic_batch* b, int slot, pic_ctx** out)
 
 int pic_batch_set_target(pic_batch* b, int64_t particles_per_cta)
 {
-    if (!b || particles_per_cta < 1024) return fail(PIC_ERR_INVALID_ARG, "particles per CTA >= 1024");
+    if (!b || (particles_per_cta != 0 && particles_per_cta < 1024))
+        return fail(PIC_ERR_INVALID_ARG, "particles per CTA: 0 (automatic) or >= 1024");
     b->target = particles_per_cta;
     b->dirty = true;
     return PIC_OK;

@@ -24,8 +24,9 @@ cudaError_t launch_mover(const Dev& d, const StepArgs& a, int grid, int mode, cu
 // must have been called with max_ncell first.
 cudaError_t launch_mover_batch(const BatchEntry* ent, const int* owner, int grid, int max_ncell, bool sample,
                                cudaStream_t st);
-// the shared-memory attribute of both batch instantiations (set before a graph capture)
-cudaError_t mover_batch_attr(int max_ncell);
+// the shared-memory attribute of both batch instantiations (set before a graph
+// capture), and the resident CTAs per SM it allows (blocks_per_sm may be NULL)
+cudaError_t mover_batch_attr(int max_ncell, int* blocks_per_sm);
 // FP64 field/potential of the current state; accumulate != 0 also adds the
 // current step to the time averages if no step launch has done so yet
 cudaError_t launch_field(const Dev& d, double v_left, int accumulate, cudaStream_t st);

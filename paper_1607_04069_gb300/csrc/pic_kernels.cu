@@ -1141,12 +1141,15 @@ cudaError_t launch_mover_batch(const BatchEntry* ent, const int* owner, int grid
     return cudaGetLastError();
 }
 
-cudaError_t mover_batch_attr(int max_ncell)
+cudaError_t mover_batch_attr(int max_ncell, int* blocks_per_sm)
 {
     const size_t sm = mover_smem(max_ncell);
     cudaError_t e = set_smem_attr((const void*)k_mover_batch<true>, sm);
     if (e != cudaSuccess) return e;
-    return set_smem_attr((const void*)k_mover_batch<false>, sm);
+    e = set_smem_attr((const void*)k_mover_batch<false>, sm);
+    if (e != cudaSuccess || !blocks_per_sm) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, (const void*)k_mover_batch<false>,
+                                                         kMoverThreads, sm);
 }
 
 cudaError_t launch_mover(const Dev& d, const StepArgs& a, int grid, int mode, cudaStream_t st)

@@ -29,4 +29,34 @@ def test_binding_declares_the_same_functions():
     L = P.lib()
     for n in _declared():
         fn = getattr(L, n)
-        assert fn.restype is not None or n in ("pic_destroy", "pic_batch_destroy")
+        assert fn.restype is not None or n.endswith("_destroy")
+
+
+def test_ctypes_structs_match_the_header(tmp_path):
+    """Size and field offsets of every struct the binding mirrors, as the C
+    compiler lays them out from include/pic_gb300.h."""
+    import shutil
+    import subprocess
+    import pytest
+    import paper_1607_04069_gb300 as P
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    mirrors = {"pic_params": P.PicParams, "tp_source": P.TpSource, "pic_server_opts": P.ServerOpts,
+               "pic_request_info": P.RequestInfo, "pic_server_stats": P.ServerStats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pic_gb300.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in mirrors.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
