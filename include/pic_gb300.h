@@ -333,12 +333,12 @@ void pic_batch_destroy(pic_batch* b);
  * every admitted discharge resident, and steps them all together -- one
  * pic_batch, or one pic_step call per discharge when batched is 0 -- in
  * chunks of 1/chunks_per_period of an RF period (admission happens between
- * chunks).  At each of a discharge's period boundaries it reads the
- * period-averaged n_e and n_i; once at least min_periods periods have run and
- * the relative change of both from the period before is below tol, the
- * request completes with state CONVERGED (or MAX_PERIODS when max_periods > 0
- * periods have run), its last period-averaged n_e, n_i and phi are kept on the
- * host and its device state is released.  Requests follow the pic_batch rules
+ * chunks).  At the end of each window of window_periods RF periods it reads
+ * the discharge's window-averaged n_e and n_i; once at least min_periods
+ * periods have run and the relative change of both from the window before
+ * is below tol, the request completes with state CONVERGED (or MAX_PERIODS
+ * when max_periods > 0 periods have run), its last window-averaged n_e, n_i
+ * and phi are kept on the host and its device state is released.  Requests follow the pic_batch rules
  * (32-bit positions, one dt and diag_every, a whole number of steps per RF
  * period that is a multiple of the chunk); others complete as FAILED, and a
  * state larger than the whole budget as REJECTED.  The change is that of
@@ -360,6 +360,8 @@ typedef struct pic_server_opts {
     int32_t graphs;            /* batched: replay sampling periods from CUDA graphs          */
     int32_t chunks_per_period; /* admission / check granularity (default 10)                  */
     int32_t criterion;         /* PIC_STEADY_INVENTORY (default) or PIC_STEADY_PROFILE        */
+    int32_t window_periods;    /* RF periods per averaging window (>= 1, default 1)           */
+    int32_t pad;
 } pic_server_opts;
 
 enum pic_steady_criterion { PIC_STEADY_INVENTORY = 0, PIC_STEADY_PROFILE = 1 };
@@ -388,7 +390,8 @@ typedef struct pic_server_stats {
 } pic_server_stats;
 
 /* Defaults: budget 0 (80% of free), min_periods 2, max_periods 0, tol 0.01,
- * batched 1, graphs 1, chunks_per_period 10, criterion inventory. */
+ * batched 1, graphs 1, chunks_per_period 10, criterion inventory,
+ * window_periods 1. */
 int pic_server_opts_default(pic_server_opts* o);
 /* opts may be NULL (defaults). */
 int pic_server_create(const pic_server_opts* opts, pic_server** out);
@@ -403,9 +406,9 @@ int pic_server_info(pic_server* s, int64_t id, pic_request_info* info);
 int pic_server_wait(pic_server* s, int64_t id, double timeout_s, pic_request_info* info);
 /* Why a request FAILED or was REJECTED (NUL-terminated, at most cap bytes). */
 int pic_server_error(pic_server* s, int64_t id, char* out, int64_t cap);
-/* The last period-averaged profile of a request: what 0 = n_e, 1 = n_i
+/* The last window-averaged profile of a request: what 0 = n_e, 1 = n_i
  * (m^-3), 2 = phi (V), n_cells + 1 node values into host `out` (cap
- * doubles; *n receives the count, 0 before the first period). */
+ * doubles; *n receives the count, 0 before the first window ends). */
 int pic_server_result(pic_server* s, int64_t id, int what, double* out, int64_t cap, int64_t* n);
 /* Drop a finished request's record. */
 int pic_server_forget(pic_server* s, int64_t id);

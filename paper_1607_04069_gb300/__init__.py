@@ -54,7 +54,8 @@ class ServerOpts(C.Structure):
     """Mirror of ``pic_server_opts``."""
     _fields_ = [("hbm_budget_bytes", C.c_int64), ("min_periods", C.c_int32), ("max_periods", C.c_int32),
                 ("tol", C.c_double), ("batched", C.c_int32), ("graphs", C.c_int32),
-                ("chunks_per_period", C.c_int32), ("criterion", C.c_int32)]
+                ("chunks_per_period", C.c_int32), ("criterion", C.c_int32), ("window_periods", C.c_int32),
+                ("pad", C.c_int32)]
 
 
 class RequestInfo(C.Structure):

@@ -5,8 +5,9 @@
 // state fits the device-memory budget, keeps every admitted discharge
 // resident, steps all of them together (one pic_batch, or a plain loop of
 // pic_step calls when batching is off) in chunks of a fraction of an RF
-// period, and at each discharge's period boundary compares its
-// period-averaged electron and ion densities with those of the period before.
+// period, and at the end of each window of whole RF periods compares a
+// discharge's window-averaged electron and ion densities with those of the
+// window before.
 // A discharge whose relative change (of the inventories, the spatial integrals
 // of the densities, or of the profiles in L2 over the nodes; the larger of the
 // two species) falls below the tolerance has reached periodic steady state: its
@@ -43,8 +44,8 @@ struct Request {
     long long steps = 0;                 // steps run since admission
     int slot = -1;                       // batch slot (batched mode)
     pic_ctx* ctx = nullptr;              // the discharge while it runs
-    std::vector<double> prev[2];         // previous period's n_e, n_i
-    std::vector<double> res[3];          // last period's n_e, n_i, phi
+    std::vector<double> prev[2];         // previous window's n_e, n_i
+    std::vector<double> res[3];          // last window's n_e, n_i, phi
     std::string err;
 };
 
@@ -164,10 +165,18 @@ bool admit(pic_server* S, Request* r)
     return true;
 }
 
-// At r's period boundary: period averages, steady-state test, new window.
+// At r's period boundary; at the end of each window of window_periods
+// periods: the window's averages, the steady-state test and a new window.
 // Returns the state r ends in, or PIC_REQ_RUNNING.
 int period_check(pic_server* S, Request* r, std::string* err)
 {
+    int periods;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        periods = ++r->info.periods;
+    }
+    const bool capped = S->o.max_periods > 0 && periods >= S->o.max_periods;
+    if (periods % S->o.window_periods != 0) return capped ? PIC_REQ_MAX_PERIODS : PIC_REQ_RUNNING;
     std::vector<double> v[3];
     const int kinds[3] = {PIC_DIAG_NE, PIC_DIAG_NI, PIC_DIAG_PHI};
     for (int k = 0; k < 3; ++k) {
@@ -201,12 +210,10 @@ int period_check(pic_server* S, Request* r, std::string* err)
     r->prev[0] = v[0];
     r->prev[1] = v[1];
     std::lock_guard<std::mutex> lk(S->mu);
-    r->info.periods += 1;
     r->info.change = std::isfinite(change) ? change : -1.0;
     for (int k = 0; k < 3; ++k) r->res[k] = v[k];
-    if (r->info.periods >= S->o.min_periods && change < S->o.tol) return PIC_REQ_CONVERGED;
-    if (S->o.max_periods > 0 && r->info.periods >= S->o.max_periods) return PIC_REQ_MAX_PERIODS;
-    return PIC_REQ_RUNNING;
+    if (periods >= S->o.min_periods && change < S->o.tol) return PIC_REQ_CONVERGED;
+    return capped ? PIC_REQ_MAX_PERIODS : PIC_REQ_RUNNING;
 }
 
 void fail_all(pic_server* S, const std::string& why)
@@ -310,6 +317,8 @@ int pic_server_opts_default(pic_server_opts* o)
     o->batched = 1;
     o->graphs = 1;
     o->chunks_per_period = 10;
+    o->criterion = PIC_STEADY_INVENTORY;
+    o->window_periods = 1;
     return PIC_OK;
 }
 
@@ -324,8 +333,10 @@ int pic_server_create(const pic_server_opts* opts, pic_server** out)
     if (opts) o = *opts;
     else pic_server_opts_default(&o);
     if (o.min_periods < 2 || o.max_periods < 0 || !(o.tol > 0) || o.hbm_budget_bytes < 0 ||
-        o.chunks_per_period < 0 || (o.criterion != PIC_STEADY_INVENTORY && o.criterion != PIC_STEADY_PROFILE)) {
-        set_last_error("min_periods >= 2, max_periods >= 0, tol > 0, budget >= 0, criterion 0 or 1");
+        o.chunks_per_period < 0 || (o.criterion != PIC_STEADY_INVENTORY && o.criterion != PIC_STEADY_PROFILE) ||
+        o.window_periods < 1) {
+        set_last_error("min_periods >= 2, max_periods >= 0, tol > 0, budget >= 0, criterion 0 or 1, "
+                       "window_periods >= 1");
         return PIC_ERR_INVALID_ARG;
     }
     int ndev = 0;

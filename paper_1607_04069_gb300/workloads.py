@@ -62,7 +62,8 @@ def batched(n_discharges: int = 256, seed: int = 1238, n_min: int = 50_000, n_ma
     counts 256-2048 (powers of two), 50k-2M superparticles per species
     (log-uniform), 0.3-5 Pa (log-uniform), 50-500 V, gap 25-50 mm, all at
     13.56 MHz with one dt = T_RF / steps_per_period, 32-bit positions, no
-    sputtering.  Density 1e15 m^-3 at load, so dx < lambda_D at 2 eV."""
+    sputtering.  Density 2e15 m^-3 at load (dx < lambda_D = 0.235 mm at
+    2 eV, w_p dt = 0.06); member k has seed 10^6 + k."""
     rng = np.random.default_rng(seed)
     out = []
     for k in range(n_discharges):
@@ -73,8 +74,8 @@ def batched(n_discharges: int = 256, seed: int = 1238, n_min: int = 50_000, n_ma
         V = float(rng.uniform(50.0, 500.0))
         out.append(dict(name=f"member {k}: {L * 1e3:.1f} mm/{n_cells} cells/{V:.0f} V/{p:.2f} Pa, {n}+{n}",
                         gap_m=L, pressure_pa=p, gas_temp_k=300.0, rf_freq_hz=F_RF, rf_volt_v=V,
-                        n_cells=n_cells, weight=1e15 * L / n, dt=T_RF / steps_per_period, n_e0=n, n_i0=n,
-                        te0_ev=2.0, ti0_ev=0.026, seed=seed * 1000 + k, pos_precision=32, sputter_enable=0,
+                        n_cells=n_cells, weight=2e15 * L / n, dt=T_RF / steps_per_period, n_e0=n, n_i0=n,
+                        te0_ev=2.0, ti0_ev=0.026, seed=10**6 + k, pos_precision=32, sputter_enable=0,
                         tp_every=0, tp_dt=1e-9, sigma_tp=3e-19, diag_every=10, sort_every_e=400,
                         sort_every_i=400, steps_per_period=steps_per_period))
     return out

@@ -36,13 +36,14 @@ def _cfg(n, seed, **over):
     return c
 
 
-def _alone(cfg, periods):
+def _alone(cfg, periods, window=1):
     d = gpu_discharge(cfg)
     out = None
-    for _ in range(periods):
+    for p in range(periods):
         d.step(PERIOD)
-        out = {k: d.diag(k) for k in ("n_e", "n_i", "phi")}
-        d.reset_averages()
+        if (p + 1) % window == 0:
+            out = {k: d.diag(k) for k in ("n_e", "n_i", "phi")}
+            d.reset_averages()
     d.sync()
     d.close()
     return out
@@ -96,3 +97,16 @@ def test_wait_times_out_and_close_abandons(P):
     assert e.value.code == -9
     assert s.info(r)["state"] in ("queued", "running")
     s.close()
+
+
+def test_averaging_windows_of_two_periods(P):
+    c = _cfg(5_000, 51)
+    s = P.Server(max_periods=4, window_periods=2, tol=1e-12, criterion=1)
+    r = s.submit(P.params_from_workload(c))
+    info = s.wait(r, timeout=120.0)
+    got = {k: s.result(r, k) for k in ("n_e", "n_i", "phi")}
+    s.close()
+    assert info["state"] == "max_periods" and info["periods"] == 4 and info["change"] > 0.0
+    want = _alone(c, 4, window=2)
+    for k in ("n_e", "n_i", "phi"):
+        assert np.array_equal(got[k], want[k]), k
