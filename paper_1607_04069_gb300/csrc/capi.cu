@@ -570,6 +570,7 @@ int pic_sync(pic_ctx* c)
         CK(cudaStreamSynchronize(c->stream));
         if (err & kErrCapacity) return fail(PIC_ERR_CAPACITY, "a birth or launch exceeded the capacity");
         if (err & kErrNumerics) return fail(PIC_ERR_NUMERICS, "electron energy above eps_max");
+        if (err & kErrIndex) return fail(PIC_ERR_NUMERICS, "a 64-bit position outside [0, n_cells)");
     }
     return PIC_OK;
 }
