@@ -58,7 +58,8 @@ class Params(C.Structure):
                 ("V0", C.c_double), ("w", C.c_double), ("dt", C.c_double),
                 ("te0", C.c_double), ("ti0", C.c_double), ("tp_dt", C.c_double),
                 ("sigma_tp", C.c_double), ("seed", C.c_uint64), ("ncell", C.c_int32),
-                ("sputter", C.c_int32), ("tp_every", C.c_int32), ("diag_every", C.c_int32)]
+                ("sputter", C.c_int32), ("tp_every", C.c_int32), ("diag_every", C.c_int32),
+                ("waveform", C.c_int32), ("circuit", C.c_int32), ("phase", C.c_double), ("cb", C.c_double)]
 
 
 def _p(a):
@@ -98,6 +99,7 @@ def lib():
                 "orc_set_step": (None, [vp, u32]),
                 "orc_get_tp_step": (u32, [vp]),
                 "orc_gap": (u32, [dbl, u32]),
+                "orc_source_voltage": (dbl, [vp, u32]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -243,6 +245,10 @@ class Oracle:
 
     def reset_averages(self):
         lib().orc_reset_averages(self.h)
+
+    def source_voltage(self, l):
+        """Source voltage at step l (before any series capacitor)."""
+        return float(lib().orc_source_voltage(self.h, int(l)))
 
     @property
     def step_index(self):

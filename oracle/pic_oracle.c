@@ -103,6 +103,10 @@ typedef struct {
     int32_t sputter;              /* ion impacts launch sputtered atoms            */
     int32_t tp_every;             /* coupled TP sub-cycle (0: no coupled TP)       */
     int32_t diag_every;           /* flux / EEDF sampling stride                   */
+    int32_t waveform;             /* 0: V0 sin(wt); 1: V0 [cos(wt + phase) + cos 2wt] */
+    int32_t circuit;              /* 0: the source sets phi[0]; 1: series capacitor  */
+    double phase;                 /* waveform 1: phase of the fundamental, rad      */
+    double cb;                    /* circuit 1: capacitance per electrode area, F/m^2 */
 } orc_params;
 
 typedef struct {
@@ -335,9 +339,49 @@ static int64_t append(orc_state *S, int s, double xi, double vx, double vy, doub
     return k;
 }
 
-static double v_rf(const orc_state *S, uint32_t l)
+/* Source voltage at step l (Sec. "Simulation Scenario"): a sine of
+ * amplitude V0, or the fundamental and its second harmonic,
+ * V0 [cos(w t + phase) + cos(2 w t)], whose relative phase makes a
+ * geometrically symmetric discharge electrically asymmetric. */
+double orc_source_voltage(const orc_state *S, uint32_t l)
 {
-    return S->P.V0 * sin(2.0 * O_PI * S->P.f * (double)l * S->P.dt);
+    double wt = 2.0 * O_PI * S->P.f * (double)l * S->P.dt;
+    if (S->P.waveform == 1) return S->P.V0 * (cos(wt + S->P.phase) + cos(2.0 * wt));
+    return S->P.V0 * sin(wt);
+}
+
+/* Electrode potential with the source in series with a blocking capacitor
+ * (Sec. "Simulation Scenario", Sec. "EM Field Solver and External Lumped
+ * Circuits": the surface charge couples plasma and circuit).  Per unit
+ * electrode area the capacitor holds q; the left electrode carries sigma =
+ * q + w, w the charge the particles have delivered to it (ions minus
+ * electrons absorbed there since creation); Gauss's law over the half cell
+ * ties sigma to the field at the electrode, sigma = eps0 E_0; and the loop
+ * gives phi_0 = V - q/c.  E_0 is linear in phi_0: E_0 = E_0(charge, phi_0 =
+ * 0) + phi_0 E_0(no charge, phi_0 = 1), both from the discrete Poisson
+ * problem, so phi_0 = (c V - eps0 E_0(charge, 0) + w) / (c + eps0 E_0(no
+ * charge, 1)).  An infinite c is the ideal source, phi_0 = V; c = 0 is a
+ * floating electrode, sigma = w. */
+static double circuit_potential(orc_state *S, double V)
+{
+    if (isinf(S->P.cb)) return V;
+    int N = S->P.ncell;
+    double *phi = (double *)malloc(sizeof(double) * (N + 1));
+    double *E = (double *)malloc(sizeof(double) * (N + 1));
+    int64_t *zero = (int64_t *)calloc(N + 1, sizeof(int64_t));
+    orc_poisson(N, S->dx, S->P.w, S->q[SP_I], S->q[SP_E], 0.0, phi, E);
+    double e_charge = E[0];
+    orc_poisson(N, S->dx, S->P.w, zero, zero, 1.0, phi, E);
+    double e_unit = E[0];
+    free(phi); free(E); free(zero);
+    double w = O_QE * S->P.w * (double)(S->cnt[C_IMP_I_L] - S->cnt[C_IMP_E_L]);
+    return (S->P.cb * V - O_EPS0 * e_charge + w) / (S->P.cb + O_EPS0 * e_unit);
+}
+
+static double v_rf(orc_state *S, uint32_t l)
+{
+    double V = orc_source_voltage(S, l);
+    return S->P.circuit ? circuit_potential(S, V) : V;
 }
 
 /* deposit both charged species and solve the field for time step l */
@@ -358,14 +402,15 @@ static void field_for_step(orc_state *S, uint32_t l)
 /* derived quantities of the null-collision method (Sec. "Particle
  * Collisions"): nu_max is the maximum over energy of n sigma_sum(eps)
  * sqrt(2 eps / m_r).  Electrons: the sum of the closed-form maxima of the
- * three cross sections at the highest admitted energy eps_max = 2 V0 + 100 eV.
+ * three cross sections at the highest admitted energy eps_max = 2 V_peak + 100 eV
+ * (V_peak = V0 for the sine, 2 V0 for the two-harmonic waveform).
  * Ar+: sigma(eps) g is constant, so nu_max is exact. */
 static void derive(orc_state *S)
 {
     orc_params *P = &S->P;
     S->ngas = P->p / (O_KB * P->Tg);
     S->dx = P->L / (double)P->ncell;
-    S->eps_max = 2.0 * P->V0 + 100.0;
+    S->eps_max = 2.0 * (P->waveform == 1 ? 2.0 * P->V0 : P->V0) + 100.0;   /* peak source voltage */
     double sig_ion_max = O_LOTZ_A * O_LOTZ_Q / (exp(1.0) * O_ION_TH * O_ION_TH);
     double sig_sum_max = O_SIG_EL + O_EXC_SIG + sig_ion_max;
     S->nu_max_e = S->ngas * sig_sum_max * sqrt(2.0 * S->eps_max * O_QE / O_ME);

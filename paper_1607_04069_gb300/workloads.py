@@ -93,7 +93,8 @@ def oracle_params(cfg: dict) -> dict:
                 V0=cfg["rf_volt_v"], w=cfg["weight"], dt=cfg["dt"], te0=cfg["te0_ev"],
                 ti0=cfg["ti0_ev"], tp_dt=cfg["tp_dt"], sigma_tp=cfg["sigma_tp"], seed=cfg["seed"],
                 ncell=cfg["n_cells"], sputter=cfg["sputter_enable"], tp_every=cfg["tp_every"],
-                diag_every=cfg["diag_every"])
+                diag_every=cfg["diag_every"], waveform=cfg.get("waveform", 0), circuit=cfg.get("circuit", 0),
+                phase=cfg.get("rf_phase", 0.0), cb=cfg.get("c_block", math.inf))
 
 
 # ------------------------------------------------------------- particle sets

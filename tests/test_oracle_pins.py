@@ -508,3 +508,86 @@ def test_density_diagnostic_normalisation():
     assert abs(ne[1:N].mean() / 1e15 - 1) < 4 / math.sqrt(n)
     assert abs(ne[0] / 1e15 - 1) < 5 / math.sqrt(per / 2)
     assert abs(ne[N] / 1e15 - 1) < 5 / math.sqrt(per / 2)
+
+
+# ------------------------------------------------------------------ source waveform and external circuit
+def test_two_harmonic_waveform_extremes_and_mean():
+    """Sec. 'Simulation Scenario': V0 [cos(wt + phase) + cos(2wt)] with phase
+    0 peaks at 2 V0 (t = 0) and bottoms at -9/8 V0 (where cos wt = -1/4),
+    the asymmetry the electrical asymmetry effect rests on; both it and the
+    sine have zero mean over a period, and the sine peaks at V0."""
+    n, f, V0 = 40000, 13.56e6, 300.0
+    for waveform, vmax, vmin in ((1, 2.0 * V0, -1.125 * V0), (0, V0, -V0)):
+        orc = O.Oracle(prm(V0=V0, f=f, dt=1.0 / f / n, waveform=waveform, ncell=8), 1, 1)
+        v = np.array([orc.source_voltage(l) for l in range(n)])
+        assert v.max() == pytest.approx(vmax, rel=1e-12)
+        assert v.min() == pytest.approx(vmin, rel=1e-7)
+        assert abs(v.mean()) < 1e-9 * V0
+    orc = O.Oracle(prm(V0=V0, f=f, dt=1.0 / f / n, waveform=1, phase=math.pi / 2, ncell=8), 1, 1)
+    assert orc.source_voltage(0) == pytest.approx(V0, rel=1e-12)      # -sin(0) + cos(0)
+
+
+def test_series_capacitor_vacuum_divider():
+    """No charge in the gap: the blocking capacitor c and the vacuum gap
+    eps0/L (per unit area) in series divide the source voltage, phi_0 =
+    V c / (c + eps0/L), and the field is uniform, phi_0/L."""
+    L, N, f = 0.02, 64, 13.56e6
+    for ratio in (0.25, 1.0, 7.0):
+        cb = ratio * EPS0 / L
+        orc = O.Oracle(prm(L=L, ncell=N, V0=100.0, f=f, dt=1.0 / f / 400, circuit=1, cb=cb, w=1e10), 4, 4)
+        orc.step_index = 37
+        orc.field()
+        phi0 = orc.source_voltage(37) * cb / (cb + EPS0 / L)
+        fld = orc.get_field()
+        assert fld["phi"][0] == pytest.approx(phi0, rel=1e-13)
+        assert np.allclose(fld["E"], phi0 / L, rtol=1e-11, atol=0)
+        assert np.allclose(fld["phi"], phi0 * (1.0 - np.arange(N + 1) / N), rtol=0, atol=1e-12 * abs(phi0))
+
+
+def _small_discharge(**kw):
+    f = 13.56e6
+    p = prm(L=0.025, p=3.0, Tg=300.0, f=f, V0=100.0, w=1e15 * 0.025 / 3000, dt=1.0 / f / 400, ncell=64,
+            seed=11, diag_every=10)
+    p.update(kw)
+    orc = O.Oracle(p, 20000, 20000, 1)
+    orc.init_species(0, 3000, 2.0)
+    orc.init_species(1, 3000, 0.026)
+    orc.field()
+    return orc
+
+
+def test_infinite_blocking_capacitance_is_the_ideal_source():
+    """c -> infinity shorts the capacitor: 40 steps with the circuit and
+    c = inf leave exactly the state of the ideal source on the electrode."""
+    a = _small_discharge(circuit=1, cb=math.inf, waveform=1)
+    b = _small_discharge(circuit=0, waveform=1)
+    a.step(40)
+    b.step(40)
+    for s in (0, 1):
+        ga, gb = a.get_species(s), b.get_species(s)
+        for k in ("xi", "vx", "vy", "vz", "id"):
+            assert np.array_equal(ga[k], gb[k]), (s, k)
+    assert np.array_equal(a.get_field()["E"], b.get_field()["E"])
+
+
+def test_circuit_surface_charge_balance():
+    """Gauss's law at the driven electrode, eps0 E_0 = sigma = q + w, with w
+    the charge of the ions minus the electrons absorbed there: c = 0 is a
+    floating electrode (q = 0, so eps0 E_0 = w); a finite c obeys the loop
+    phi_0 = V - q/c.  Checked after several steps with wall losses."""
+    for cb in (0.0, 3.0 * EPS0 / 0.025):
+        orc = _small_discharge(circuit=1, cb=cb)
+        for _ in range(3):
+            orc.step(15)
+            c = orc.counters()
+            w = QE * orc.prm["w"] * (c["imp_i_l"] - c["imp_e_l"])
+            fld = orc.get_field()
+            sigma = EPS0 * fld["E"][0]
+            scale = EPS0 * np.abs(fld["E"]).max() + abs(w)
+            q = sigma - w
+            if cb == 0.0:
+                assert abs(q) <= 1e-10 * scale
+            else:
+                V = orc.source_voltage(orc.step_index)
+                assert fld["phi"][0] == pytest.approx(V - q / cb, abs=1e-9 * max(abs(V), abs(fld["phi"][0])))
+        assert c["imp_e_l"] + c["imp_i_l"] > 0
