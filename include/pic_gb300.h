@@ -46,8 +46,12 @@ enum pic_species { PIC_ELECTRON = 0, PIC_ION = 1, PIC_ATOM = 2 };
 
 /* Discharge description.  SI units unless marked.  The discharge is the 1D
  * two-electrode setup of Sec. "Simulation Scenario": gap L, the left
- * electrode driven by V_rf(t) = V0 sin(2 pi f t), the right one grounded,
- * argon at constant pressure and temperature. */
+ * electrode driven by the source V_rf(t), the right one grounded, argon at
+ * constant pressure and temperature.  The source is V0 sin(2 pi f t) or
+ * the paper's two-harmonic V0 [cos(2 pi f t + rf_phase) + cos(4 pi f t)],
+ * and drives the electrode directly or through a series blocking capacitor
+ * (surface-charge boundary condition, Sec. "EM Field Solver and External
+ * Lumped Circuits"). */
 typedef struct pic_params {
     double gap_m, pressure_pa, gas_temp_k, rf_freq_hz, rf_volt_v;
     double weight;          /* physical particles per superparticle per m^2 (Sec. "Kinetic
@@ -70,6 +74,15 @@ typedef struct pic_params {
     int32_t ctas_per_sm;    /* CTAs per SM of the per-step launch (0 = occupancy limit)    */
     int32_t strict;         /* reject parameters violating dx < lambda_D or w_p dt < 1
                                (Sec. "Limitations and Constraints")                        */
+    int32_t waveform;       /* 0: V0 sin(2 pi f t); 1: V0 [cos(2 pi f t + rf_phase) + cos(4 pi f t)] */
+    int32_t circuit;        /* 0: the source sets the electrode potential; 1: the source drives
+                               the electrode through the blocking capacitor c_block: per unit
+                               area the capacitor holds q, the electrode carries q plus the
+                               charge the particles brought to it (Gauss: eps0 E_0), and
+                               phi_0 = V_rf - q / c_block                                 */
+    double rf_phase;        /* waveform 1: phase of the fundamental, rad                    */
+    double c_block;         /* circuit 1: capacitance per unit electrode area, F/m^2, >= 0
+                               (0: floating electrode; INFINITY: same as circuit 0)        */
 } pic_params;
 
 /* Mono-energetic Ar+ source for tp_launch: n atoms leave the left electrode

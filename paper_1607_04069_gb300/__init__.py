@@ -47,7 +47,8 @@ class PicParams(C.Structure):
                 ("pos_precision", C.c_int32), ("sputter_enable", C.c_int32),
                 ("tp_every", C.c_int32), ("diag_every", C.c_int32), ("sort_every_e", C.c_int32),
                 ("sort_every_i", C.c_int32), ("sort_every_tp", C.c_int32),
-                ("ctas_per_sm", C.c_int32), ("strict", C.c_int32)]
+                ("ctas_per_sm", C.c_int32), ("strict", C.c_int32), ("waveform", C.c_int32),
+                ("circuit", C.c_int32), ("rf_phase", C.c_double), ("c_block", C.c_double)]
 
 
 class ServerOpts(C.Structure):

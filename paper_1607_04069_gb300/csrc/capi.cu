@@ -63,6 +63,7 @@ struct pic_ctx {
     long long acc_upto = 0;          // last step whose state entered the time averages
     unsigned int cur[3] = {0, 0, 0}; // active ping-pong halves (each compaction flips one)
     long long period = 0;            // steps per RF period when that is a whole number, else 0
+    double circ_beta = 0.0;          // series capacitor: 1 / (1 + L c / eps0)
     double derived[8];
     bool timing = false;
     Timer timers[3];
@@ -167,6 +168,10 @@ int validate(const pic_params* p)
         p->sort_every_tp < 0 || p->ctas_per_sm < 0)
         return fail(PIC_ERR_INVALID_ARG, "negative period");
     if (!(p->tp_dt >= 0) || !(p->sigma_tp >= 0)) return fail(PIC_ERR_INVALID_ARG, "tp_dt, sigma_tp >= 0");
+    if ((p->waveform != 0 && p->waveform != 1) || (p->circuit != 0 && p->circuit != 1))
+        return fail(PIC_ERR_INVALID_ARG, "waveform and circuit must be 0 or 1");
+    if (!std::isfinite(p->rf_phase) || (p->circuit == 1 && !(p->c_block >= 0)))
+        return fail(PIC_ERR_INVALID_ARG, "rf_phase must be finite and c_block >= 0");
     return PIC_OK;
 }
 
@@ -179,7 +184,9 @@ void derive(pic_ctx* c)
     const pic_params& p = c->p;
     const double ngas = p.pressure_pa / (kKB * p.gas_temp_k);
     const double dx = p.gap_m / (double)p.n_cells;
-    const double eps_max = 2.0 * p.rf_volt_v + 100.0;
+    // null-collision energy bound: twice the peak source voltage (V0 for the
+    // sine, 2 V0 for the two-harmonic waveform) plus 100 eV
+    const double eps_max = 2.0 * (p.waveform == 1 ? 2.0 * p.rf_volt_v : p.rf_volt_v) + 100.0;
     const double sig_ion_max = kLotzA * kLotzQ / (std::exp(1.0) * kIonTh * kIonTh);
     const double sig_sum_max = kSigEl + kExcSig + sig_ion_max;
     const double nu_max_e = ngas * sig_sum_max * std::sqrt(2.0 * eps_max * kQE / kME);
@@ -212,6 +219,12 @@ void derive(pic_ctx* c)
     d.cap[kE] = p.cap_e;
     d.cap[kI] = p.cap_i;
     d.cap[kTP] = p.cap_tp;
+    // series blocking capacitor (an infinite one is the ideal source)
+    d.circuit = p.circuit == 1 && std::isfinite(p.c_block);
+    const double beta = d.circuit ? 1.0 / (1.0 + p.gap_m * p.c_block / kEPS0) : 0.0;
+    c->circ_beta = beta;
+    d.circ_a = d.A > 0.0 ? 2.0 * (1.0 - beta) / d.A : 0.0;
+    d.circ_b = 2.0 * beta;
     c->period = 0;
     if (p.rf_freq_hz > 0) {
         const double per = 1.0 / (p.rf_freq_hz * p.dt);
@@ -255,10 +268,23 @@ void sync_desc(pic_ctx* c)          // keep the coupled descriptor's pointers in
 // electrode voltage at step l, V0 sin(2 pi f t_l), evaluated at the phase of
 // step l within its RF period when a period is a whole number of steps (so a
 // step's voltage depends only on its phase, here and in batched stepping)
+// source voltage at step l (Sec. "Simulation Scenario"): V0 sin(w t), or the
+// fundamental and its harmonic V0 [cos(w t + phase) + cos(2 w t)]; the phase
+// of step l is taken at l mod period when the period is a whole number of steps
 double v_left_at(const pic_ctx* c, long long l)
 {
     const long long lp = c->period > 0 ? l % c->period : l;
-    return c->p.rf_volt_v * std::sin(2.0 * kPI * c->p.rf_freq_hz * (double)lp * c->p.dt);
+    const double wt = 2.0 * kPI * c->p.rf_freq_hz * (double)lp * c->p.dt;
+    if (c->p.waveform == 1) return c->p.rf_volt_v * (std::cos(wt + c->p.rf_phase) + std::cos(2.0 * wt));
+    return c->p.rf_volt_v * std::sin(wt);
+}
+
+// the voltage the FP64 field solve starts from: the source voltage, or with
+// the series capacitor and no space charge the divided one
+double field_v_at(const pic_ctx* c, long long l)
+{
+    const double V = v_left_at(c, l);
+    return c->d.circuit && c->d.A == 0.0 ? (1.0 - c->circ_beta) * V : V;
 }
 
 StepArgs step_args(const pic_ctx* c, long long l, int accumulate)
@@ -269,6 +295,16 @@ StepArgs step_args(const pic_ctx* c, long long l, int accumulate)
     a.accumulate = accumulate;
     a.step = (unsigned int)l;
     for (int s = 0; s < 3; ++s) a.cur[s] = c->cur[s];
+    if (c->d.circuit) {
+        if (c->d.A == 0.0) {                     // no space charge: the capacitive divider
+            a.v_left *= 1.0 - c->circ_beta;
+            a.field_mode = kFieldUniform;
+            a.e_uniform = (float)(a.v_left / c->p.gap_m);
+        } else {
+            a.field_mode = kFieldCircuit;        // the launch forms the electrode potential
+        }
+        return a;
+    }
     if (c->d.A == 0.0) {
         a.field_mode = kFieldUniform;
         a.e_uniform = (float)(a.v_left / c->p.gap_m);
@@ -643,7 +679,7 @@ int pic_diag(pic_ctx* c, int kind, double* out, int64_t cap, int64_t* n_written)
     CK(cudaSetDevice(c->device));
     {                                               // current state into the averages, FP64 field
         const int acc = c->h_step > c->acc_upto;
-        CK(launch_field(c->d, v_left_at(c, c->h_step), acc, c->stream));
+        CK(launch_field(c->d, field_v_at(c, c->h_step), acc, c->stream));
         if (acc) c->acc_upto = c->h_step;
     }
     Ctl h;
@@ -885,7 +921,7 @@ int pic_get_field(pic_ctx* c, double* E, double* phi, int64_t* q_e, int64_t* q_i
 {
     if (!c) return fail(PIC_ERR_INVALID_ARG, "ctx is NULL");
     CK(cudaSetDevice(c->device));
-    CK(launch_field(c->d, v_left_at(c, c->h_step), 0, c->stream));
+    CK(launch_field(c->d, field_v_at(c, c->h_step), 0, c->stream));
     Ctl h;
     int rc = read_ctl(c, &h);
     if (rc) return rc;

@@ -86,11 +86,14 @@ struct Ctl {                   // device control block
     long long n_avg, n_flux, n_tp_samp;
     long long sort_total;
     double sum_v;              // sum of the electrode voltage over the averaged steps
+    long long wall_dn;         // ions minus electrons absorbed at x = 0 since creation (to the
+                               // end of the last step launch; the series-capacitor circuit)
     // words updated by atomics while kernels run, each group on its own
     // 128-byte line so that their queues at L2 do not delay the others
     alignas(128) long long births[3];      // appended by the running kernel
     alignas(128) unsigned int done, tp_done, sort_done;
     alignas(128) unsigned int err;
+    long long wall_delta;      // the running launch's share of wall_dn (moved over at commit)
     alignas(128) unsigned long long cnt[kNumCnt];   // counts of the TP kernels
 };
 
@@ -125,12 +128,13 @@ struct StepArgs {
     long long va_i;        // llrint(2 v_left / A)
     float va_f;            // 2 v_left / A - va_i
     float e_uniform;       // v_left / L, used when A == 0
-    int field_mode;        // 0: integer path, 1: FP64 path (|2V/A| >= 2^62), 2: no space charge
+    int field_mode;        // 0: integer path, 1: FP64 path (|2V/A| >= 2^62), 2: no space charge,
+                           // 3: series capacitor (v_left is the source voltage; see Dev::circ_a)
     int accumulate;        // add the state of this step to the time averages
     unsigned int step;     // step index l (equal to Ctl::step)
     unsigned int cur[3];   // active ping-pong halves (equal to Ctl::cur)
 };
-enum { kFieldInt = 0, kFieldF64 = 1, kFieldUniform = 2 };
+enum { kFieldInt = 0, kFieldF64 = 1, kFieldUniform = 2, kFieldCircuit = 3 };
 
 struct Dev {                   // everything a kernel needs, passed by value
     SpBuf buf[3][2];
@@ -154,6 +158,13 @@ struct Dev {                   // everything a kernel needs, passed by value
     double L, dx, inv_dx;
     // field solve: phi[m+1] - 2 phi[m] + phi[m-1] = -A q_net[m]; A = dx e w / (2^32 eps0)
     double A, V0, omega, dt, f_rf;
+    // series blocking capacitor: the electrode potential in units of A/2 is
+    //   2 phi_0 / A = circ_a V + circ_b (T_N + N q_0 + N 2^32 dn)
+    // with T_N = sum_j (N - j) q_j over the deposit, dn the ions minus the
+    // electrons absorbed at x = 0 (Ctl::wall_dn), circ_a = 2 (1 - beta) / A,
+    // circ_b = 2 beta, beta = 1 / (1 + L c / eps0)
+    double circ_a, circ_b;
+    int circuit, pad3;
     float c2f;                       // A / (2 dx): E per unit of the integer bracket
     float pad2;
     // push

@@ -229,6 +229,10 @@ __device__ __forceinline__ void flush_tally(const Dev& d, const BlockTally& t, i
         if (v[i]) atomicAdd(&r[k[i]], (unsigned long long)v[i]);
     if (t.numerics) atomicOr(&d.ctl->err, kErrNumerics);
     if (t.capacity) atomicOr(&d.ctl->err, kErrCapacity);
+    if (d.circuit) {                              // charge delivered to the driven electrode
+        const long long dn = (long long)t.imp_i[0] - (long long)t.imp_e[0];
+        if (dn) atomicAdd((unsigned long long*)&d.ctl->wall_delta, (unsigned long long)dn);
+    }
 }
 
 // ---------------------------------------------------------------- mover
@@ -602,12 +606,13 @@ __device__ __forceinline__ void mover_body(const Dev& d, const StepArgs& a, int 
     if (MODE == 0) asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();
     if (tr && threadIdx.x == 0) tr[1] = gtimer();
+    double v_el = a.v_left;                     // electrode potential of step l
     if (MODE == 0) {
         // field of step l: every CTA solves from the deposit of x^l
         if (field_override) {
             for (int i = threadIdx.x; i < N1; i += blockDim.x) sE[i] = d.E32[i];
         } else {
-            block_field_f32(d, sqe, sqi, sE, a);
+            v_el = block_field_f32(d, sqe, sqi, sE, a);
         }
     }
     __syncthreads();
@@ -807,7 +812,7 @@ __device__ __forceinline__ void mover_body(const Dev& d, const StepArgs& a, int 
         if (tr) atomicMax(&s_flushns, gtimer() - tf);
         if (MODE == 0 && a.accumulate) {         // this CTA's share of the time averages of step l
             const int m0 = N1 * cta / G, m1 = N1 * (cta + 1) / G;
-            accumulate_nodes(d, l, sqe, sqi, m0, m1, a.v_left, cta == 0, t, nt);
+            accumulate_nodes(d, l, sqe, sqi, m0, m1, v_el, cta == 0, t, nt);
         }
     }
     if (MODE == 0 && s_overflow) {
@@ -933,10 +938,12 @@ __global__ void k_field(Dev d, double v_left, int accumulate)
     const unsigned int l = d.ctl->step;
     const int slot = l % 3;
     QNet qn{d.qbuf[slot][kI], d.qbuf[slot][kE], false};
-    poisson_block(qn, d.ncell, d.A, d.inv_dx, v_left, d.phi, d.E64, nullptr);
+    const CircuitArgs circ{d.circ_a, d.circ_b, d.ctl->wall_dn};
+    const double v_el = poisson_block(qn, d.ncell, d.A, d.inv_dx, v_left, d.phi, d.E64, nullptr,
+                                      d.circuit && d.A > 0.0 ? &circ : nullptr);
     __syncthreads();
     if (accumulate)
-        accumulate_nodes(d, l, d.qbuf[slot][kE], d.qbuf[slot][kI], 0, d.ncell + 1, v_left, true, threadIdx.x,
+        accumulate_nodes(d, l, d.qbuf[slot][kE], d.qbuf[slot][kI], 0, d.ncell + 1, v_el, true, threadIdx.x,
                          blockDim.x);
 }
 

@@ -85,9 +85,19 @@ struct QNet {
     }
 };
 
+// Series blocking capacitor, for the solves below: with circ non-null the
+// electrode potential is not v_left but follows from the source voltage
+// v_left, the deposit and the charge absorbed at x = 0 (Dev::circ_a).
+struct CircuitArgs {
+    double a, b;          // Dev::circ_a, Dev::circ_b
+    long long dn;         // Ctl::wall_dn
+};
+
 // Solve for phi and E with one CTA.  Any output pointer may be null.
-__device__ __noinline__ static void poisson_block(const QNet& qn, int N, double A, double inv_dx, double v_left,
-                              double* phi, double* E64, float* E32)
+// Returns the electrode potential phi[0].
+__device__ __noinline__ static double poisson_block(const QNet& qn, int N, double A, double inv_dx, double v_left,
+                                                    double* phi, double* E64, float* E32,
+                                                    const CircuitArgs* circ = nullptr)
 {
     __shared__ long long sh64[32];
     __shared__ __int128 sh128[32];
@@ -111,6 +121,10 @@ __device__ __noinline__ static void poisson_block(const QNet& qn, int N, double 
     __int128 totT;
     const __int128 Tpre = block_exclusive_scan(b, sh128, totT);
     const __int128 TN = totT - (__int128)totS;
+    if (circ) {
+        const __int128 X = TN + (__int128)N * (__int128)qn(0) + ((__int128)N << 32) * (__int128)circ->dn;
+        v_left = 0.5 * A * (circ->a * v_left + circ->b * i128_to_double(X));
+    }
     const double D0 = (0.0 - v_left + A * i128_to_double(TN)) / (double)N;
 
     S = Sprev;
@@ -129,6 +143,7 @@ __device__ __noinline__ static void poisson_block(const QNet& qn, int N, double 
         Tm += (__int128)Sm;
         S = Sm;
     }
+    return v_left;
 }
 
 // Field at the nodes in FP32 from the exact integer sums, for the gather of
@@ -144,8 +159,12 @@ __device__ __noinline__ static void poisson_block(const QNet& qn, int N, double 
 // so no FP64 arithmetic runs per step (N is a power of two).  All warps of
 // the CTA take part; one block barrier.  qe, qi: shared copies of the
 // deposit; sE: shared float[N+1].
-__device__ static void block_field_f32(const Dev& d, const unsigned long long* qe, const unsigned long long* qi,
-                                       float* sE, const StepArgs& a)
+// Returns the electrode potential phi[0] of the solve; with the series
+// capacitor (field_mode kFieldCircuit) it is formed here from the source
+// voltage a.v_left, T_N, q_0 and the charge absorbed at x = 0, as 2 phi_0/A =
+// circ_a V + circ_b (T_N + N q_0 + N 2^32 dn), and then split as above.
+__device__ static double block_field_f32(const Dev& d, const unsigned long long* qe, const unsigned long long* qi,
+                                         float* sE, const StepArgs& a)
 {
     __shared__ long long s_wacc[32], s_wbhi[32];
     __shared__ unsigned long long s_wblo[32];
@@ -154,7 +173,7 @@ __device__ static void block_field_f32(const Dev& d, const unsigned long long* q
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (a.field_mode == kFieldUniform) {
         for (int m = threadIdx.x; m < N1; m += blockDim.x) sE[m] = a.e_uniform;
-        return;
+        return a.v_left;
     }
     // nodes of this warp, then of this lane
     const int w0 = N1 * w / nw, w1 = N1 * (w + 1) / nw;
@@ -198,14 +217,31 @@ __device__ static void block_field_f32(const Dev& d, const unsigned long long* q
     long long K;
     float c1;
     const float c2 = d.c2f;
-    if (a.field_mode == kFieldInt) {
-        const __int128 x = 2 * TN - (__int128)a.va_i;
+    int mode = a.field_mode;
+    long long va_i = a.va_i;
+    float va_f = a.va_f;
+    double v_el = a.v_left;
+    if (mode == kFieldCircuit) {
+        const long long q0 = (long long)(qi[0] - qe[0]);
+        const __int128 X = TN + (__int128)N * q0 + ((__int128)N << 32) * (__int128)d.ctl->wall_dn;
+        const double va = d.circ_a * a.v_left + d.circ_b * i128_to_double(X);
+        v_el = 0.5 * d.A * va;
+        if (fabs(va) < 4.0e18) {
+            va_i = llrint(va);
+            va_f = (float)(va - (double)va_i);
+            mode = kFieldInt;
+        } else {
+            mode = kFieldF64;
+        }
+    }
+    if (mode == kFieldInt) {
+        const __int128 x = 2 * TN - (__int128)va_i;
         const __int128 Kq = (x + (__int128)(N >> 1)) >> d.kshift;
         const long long rem = (long long)(x - (Kq << d.kshift));
         K = (long long)Kq;
-        c1 = c2 * ((a.va_f - (float)rem) / (float)N);
+        c1 = c2 * ((va_f - (float)rem) / (float)N);
     } else {
-        const double D0 = (0.0 - a.v_left + d.A * i128_to_double(TN)) / (double)N;
+        const double D0 = (0.0 - v_el + d.A * i128_to_double(TN)) / (double)N;
         const double k = 2.0 * D0 / d.A;
         K = fabs(k) < 4e18 ? llrint(k) : 0;
         c1 = (float)(-D0 * d.inv_dx + 0.5 * d.A * d.inv_dx * (double)K);
@@ -221,6 +257,7 @@ __device__ static void block_field_f32(const Dev& d, const unsigned long long* q
         sE[m] = c1 + c2 * (float)br;
         S = Sm;
     }
+    return v_el;
 }
 
 // Add the state of step l (deposit in slot l%3; the flux moment sampled at
@@ -257,6 +294,8 @@ __device__ static void commit_step(const Dev& d, bool advance)
         c->step += 1;
         c->field_override = 0;
     }
+    c->wall_dn += c->wall_delta;                  // every CTA of the launch has added its share
+    c->wall_delta = 0;
     // charged-species births start at round_up(n, 4) (see k_mover), atoms at n
     for (int s = 0; s < 3; ++s) {
         if (c->births[s] == 0) continue;

@@ -42,6 +42,7 @@ MEMBERS = [
     _cfg(20_000, 11),
     _cfg(6_000, 12, pressure_pa=5.0, rf_volt_v=150.0),
     _cfg(33_000, 13, rf_volt_v=80.0, sort_every_e=0),
+    _cfg(9_000, 17, waveform=1, rf_phase=0.5, circuit=1, c_block=2.0 * 8.8541878128e-12 / 0.025),
 ]
 
 
@@ -76,9 +77,9 @@ def _same(a, b, what):
 
 def test_batch_equals_alone(P):
     steps = 120
-    b = P.Batch(particles_per_cta=16_384)          # 3, 2 and 5 CTAs
+    b = P.Batch(particles_per_cta=16_384)          # 3, 2, 5 and 2 CTAs
     slots = [b.add(P.params_from_workload(c)) for c in MEMBERS]
-    assert slots == [0, 1, 2]
+    assert slots == [0, 1, 2, 3]
     b.step(steps // 2)
     b.step(steps - steps // 2)
     b.sync()

@@ -1,0 +1,112 @@
+"""The series blocking capacitor and the two-harmonic source (Sec.
+"Simulation Scenario"; Sec. "EM Field Solver and External Lumped
+Circuits") through the C ABI, against the FP64 oracle.
+
+Tolerances: the field of the FP64 diagnostic solve within 1e-9 of max |E|
+(both sides solve the same integer deposit; the electrode potential is
+formed in FP64 from the same integer sums), the particles after one step
+within the one-step tolerances of the push tests, and the absorbed-particle
+counters exactly.
+"""
+import numpy as np
+import pytest
+
+from paper_1607_04069_gb300 import workloads as W
+
+from helpers import gpu_discharge, match, oracle_for
+
+pytestmark = pytest.mark.gpu
+
+EPS0 = 8.8541878128e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    yield
+
+
+def _circuit_cfg(n, ratio, **over):
+    c = W.ccp_sputter(n_per_species=n, n_cells=1024)
+    c.update(sputter_enable=0, tp_every=0, sort_every_e=0, sort_every_i=0, waveform=1, rf_phase=0.3,
+             circuit=1, c_block=ratio * EPS0 / c["gap_m"])
+    c.update(over)
+    return c
+
+
+def test_vacuum_divider():
+    """No particles: the field is uniform, (1 - beta) V(t) / L with beta = 1 /
+    (1 + L c / eps0), at the initial state and after steps."""
+    cfg = _circuit_cfg(1000, 3.0, n_e0=0, n_i0=0, cap_e=1024, cap_i=1024)
+    d = gpu_discharge(cfg)
+    orc = oracle_for(cfg, cap=1024)
+    orc.field()
+    for steps in (0, 7, 100):
+        if steps:
+            d.step(steps)
+            orc.step(steps)
+        f, fo = d.get_field(), orc.get_field()
+        L = cfg["gap_m"]
+        phi0 = orc.source_voltage(orc.step_index) * 3.0 / (3.0 + 1.0)
+        assert fo["phi"][0] == pytest.approx(phi0, rel=1e-12)
+        assert np.allclose(f["E"], phi0 / L, rtol=1e-12, atol=0), steps
+        assert np.abs(f["phi"] - fo["phi"]).max() <= 1e-12 * abs(phi0)
+    d.close()
+
+
+@pytest.mark.parametrize("ratio", [0.0, 3.0, 1e3])
+def test_one_step_with_circuit_matches_oracle(ratio):
+    """200k + 200k particles, 1024 cells, the two-harmonic source through a
+    capacitor of ratio x eps0/L per unit area (0: floating electrode): the
+    initial field, the absorbed counts, every particle after one step, and
+    the field after it (which includes the charge the step delivered to the
+    electrode)."""
+    cfg = _circuit_cfg(200_000, ratio)
+    n = cfg["n_e0"]
+    d = gpu_discharge(cfg)
+    orc = oracle_for(cfg, cap=n + n // 4 + 65536)
+    orc.init_species(0, n, cfg["te0_ev"])
+    orc.init_species(1, n, cfg["ti0_ev"])
+    orc.field()
+    f, fo = d.get_field(), orc.get_field()
+    assert np.array_equal(f["q_e"], fo["q_e"]) and np.array_equal(f["q_i"], fo["q_i"])
+    assert np.abs(f["E"] - fo["E"]).max() <= 1e-9 * np.abs(fo["E"]).max()
+    d.step(1)
+    d.sync()
+    orc.step(1)
+    c, oc = d.counters(), orc.counters()
+    for k in ("imp_e_l", "imp_e_r", "imp_i_l", "imp_i_r"):
+        assert c[k] == oc[k], k
+    assert c["imp_e_l"] + c["imp_i_l"] > 0
+    for s in (0, 1):
+        g, o, only_g, only_o = match(d.get_species(s), orc.get_species(s))
+        assert len(only_g) == 0 and len(only_o) == 0
+        vmag = np.sqrt(o["vx"]**2 + o["vy"]**2 + o["vz"]**2)
+        assert (np.abs(g["vx"] - o["vx"]) <= 2e-5 * vmag + 1e-2).all()
+        unit = cfg["n_cells"] / 2.0**32
+        disp_tol = 2e-5 * vmag * cfg["dt"] / (cfg["gap_m"] / cfg["n_cells"]) + 2 * unit
+        assert (np.abs(g["xi"] - o["xi"]) <= disp_tol).all()
+    f, fo = d.get_field(), orc.get_field()
+    assert np.abs(f["E"] - fo["E"]).max() <= 1e-5 * np.abs(fo["E"]).max()
+    assert f["phi"][0] == pytest.approx(fo["phi"][0], rel=1e-5, abs=1e-6 * np.abs(fo["phi"]).max())
+    d.close()
+
+
+def test_infinite_capacitance_is_the_ideal_source():
+    """c = inf takes the ideal-source path: the same state bit for bit as
+    circuit 0 after 50 steps."""
+    a = gpu_discharge(_circuit_cfg(50_000, 0.0, c_block=float("inf")))
+    b = gpu_discharge(_circuit_cfg(50_000, 0.0, circuit=0))
+    a.step(50)
+    b.step(50)
+    for s in (0, 1):
+        ga, gb = a.get_species(s), b.get_species(s)
+        oa, ob = np.argsort(ga["id"]), np.argsort(gb["id"])
+        for k in ("xi", "vx", "vy", "vz", "id"):
+            assert np.array_equal(ga[k][oa], gb[k][ob]), (s, k)
+    assert np.array_equal(a.get_field()["E"], b.get_field()["E"])
+    a.close()
+    b.close()
