@@ -32,7 +32,8 @@ COUNTERS = ["n_e", "n_i", "n_tp", "imp_e_l", "imp_e_r", "imp_i_l", "imp_i_r", "i
 
 DIAG = {"phi": 0, "n_e": 1, "n_i": 2, "gamma_e": 3, "gamma_i": 4, "eedf": 5, "iedf_l": 6,
         "iedf_r": 7, "ieadf_l": 8, "ieadf_r": 9, "sputter_e_l": 10, "sputter_e_r": 11,
-        "sputter_ang_l": 12, "sputter_ang_r": 13, "tp_dens": 14, "tp_vx": 15}
+        "sputter_ang_l": 12, "sputter_ang_r": 13, "tp_dens": 14, "tp_vx": 15, "tpf_time": 16,
+        "tpf_vx": 17}
 
 E, I, TP = 0, 1, 2
 
@@ -100,6 +101,9 @@ def lib():
                 "orc_get_tp_step": (u32, [vp]),
                 "orc_gap": (u32, [dbl, u32]),
                 "orc_source_voltage": (dbl, [vp, u32]),
+                "orc_mean_rel_speed": (dbl, [dbl, dbl]),
+                "orc_tpf_partner": (C.c_int, [C.c_uint64, C.c_uint64, u32, dbl, vp, vp]),
+                "orc_tp_flight": (i64, [vp, i64]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -123,6 +127,20 @@ def gap(lam, w):
     """Steps from one null-collision candidate to the next for nu_max dt =
     lam, from the Philox word w (geometric law, see orc_gap)."""
     return int(lib().orc_gap(float(lam), int(w) & 0xffffffff))
+
+
+def mean_rel_speed(v, c):
+    """<|v - w|> of a particle of speed v in a Maxwellian gas of most probable speed c."""
+    return float(lib().orc_mean_rel_speed(float(v), float(c)))
+
+
+def tpf_partner(seed, atom_id, e, Tg, v):
+    """Collision partner of event e of an atom with velocity v (flux-weighted
+    Maxwellian sample); returns (w, proposals used)."""
+    vv = np.ascontiguousarray(v, dtype=np.float64)
+    w = np.zeros(3)
+    t = lib().orc_tpf_partner(int(seed), int(atom_id), int(e), float(Tg), _p(vv), _p(w))
+    return w, int(t)
 
 
 def sigma_e(eps):
@@ -235,6 +253,11 @@ class Oracle:
 
     def tp_launch(self, n, E_ion):
         lib().orc_tp_launch(self.h, int(n), float(E_ion))
+
+    def tp_flight(self, max_events):
+        """Event-driven flight of every live TP atom, at most max_events
+        events each; returns the atoms still alive."""
+        return int(lib().orc_tp_flight(self.h, int(max_events)))
 
     def diag(self, kind):
         k = DIAG[kind] if isinstance(kind, str) else int(kind)

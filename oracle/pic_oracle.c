@@ -68,8 +68,12 @@ enum {
     PUR_SP_ID = 48,      /* +k: id of the k-th sputtered atom           */
     PUR_TP_GAS = 64,     /* gas partner of a TP step                    */
     PUR_TP_COLL = 65,    /* TP collision test and scattering direction  */
-    PUR_TP_LAUNCH = 66   /* mono-energetic source launch                */
+    PUR_TP_LAUNCH = 66,  /* mono-energetic source launch                */
+    PUR_TPF_FLIGHT = 70, /* event-driven TP: free-flight time of event e */
+    PUR_TPF_SCATTER = 71,/* event-driven TP: scattering direction       */
+    PUR_TPF_PARTNER = 72 /* +2t, +2t+1: partner proposal t of event e    */
 };
+#define TPF_TRIES 64     /* partner proposals per collision (each accepted w.p. >= 1/2) */
 
 /* species and id tags (top two bits of the 64-bit id) */
 #define SP_E 0
@@ -128,6 +132,7 @@ typedef struct {
     double lam[2];                /* nu_max dt of e- and Ar+                    */
     /* diagnostics */
     double *sum_q[2], *sum_phi, *sum_flux[2], *tp_dens, *tp_vx;
+    double *tpf_time, *tpf_disp;  /* event-driven TP: residence time (s), signed path (m) per cell */
     int64_t n_avg, n_flux, n_tp_samp, tp_launched;
     int64_t *iedf[2], *ieadf[2], *eedf, *sp_e[2], *sp_ang[2];
     int64_t cnt[C_NCOUNT];
@@ -444,6 +449,8 @@ orc_state *orc_create(const orc_params *P, int64_t cap_e, int64_t cap_i, int64_t
     S->sum_phi = (double *)calloc(N + 1, sizeof(double));
     S->tp_dens = (double *)calloc(N + 1, sizeof(double));
     S->tp_vx = (double *)calloc(N + 1, sizeof(double));
+    S->tpf_time = (double *)calloc(N, sizeof(double));
+    S->tpf_disp = (double *)calloc(N, sizeof(double));
     S->eedf = (int64_t *)calloc(NB_EEDF, sizeof(int64_t));
     derive(S);
     return S;
@@ -454,6 +461,7 @@ void orc_destroy(orc_state *S)
     if (!S) return;
     for (int s = 0; s < 3; s++) sp_free(&S->sp[s]);
     free(S->E); free(S->phi); free(S->sum_phi); free(S->tp_dens); free(S->tp_vx); free(S->eedf);
+    free(S->tpf_time); free(S->tpf_disp);
     for (int s = 0; s < 2; s++) {
         free(S->q[s]); free(S->sum_q[s]); free(S->sum_flux[s]); free(S->iedf[s]);
         free(S->ieadf[s]); free(S->sp_e[s]); free(S->sp_ang[s]);
@@ -839,6 +847,151 @@ void orc_tp_step(orc_state *S, int64_t nsteps, double dt_tp)
     }
 }
 
+/* ======================= event-driven TP flight ========================== */
+/* The gridless alternative of Sec. "Kinetic Particle Simulation" (free
+ * flight) and Sec. "Limitations and Constraints" (time-weighted densities):
+ * instead of testing for a collision every dt, each atom flies straight for
+ * a free-flight time tau = -tau_c ln R_f, tau_c = 1/nu, to its next
+ * collision or to a wall.  For hard spheres (sigma constant) in a Maxwellian
+ * gas the rate is nu(v) = n sigma <|v - w|>, the relative speed averaged over
+ * the gas (closed form below), and at a collision the partner w has the
+ * density |v - w| f(w) / <|v - w|>: the collision law of the per-step test
+ * of orc_tp_step in the limit dt -> 0.  Random words of event e of an atom:
+ * Philox(id, e, TPF_FLIGHT), (id, e, TPF_PARTNER + 2t [+1]) for proposal t,
+ * (id, e, TPF_SCATTER); e is kept per atom (orc_sp.nev).  Residence time and
+ * signed path length are added per cell for each straight segment. */
+
+/* <|v - w|> for a particle of speed v in a Maxwellian gas of most probable
+ * speed c: c [(s + 1/(2s)) erf(s) + exp(-s^2)/sqrt(pi)], s = v/c (kinetic
+ * theory of the mean relative speed); its series 2c/sqrt(pi) (1 + s^2/3) for
+ * s < 1e-3. */
+double orc_mean_rel_speed(double v, double c)
+{
+    double s = v / c;
+    if (s < 1e-3) return 2.0 * c / sqrt(O_PI) * (1.0 + s * s / 3.0);
+    return c * ((s + 0.5 / s) * erf(s) + exp(-s * s) / sqrt(O_PI));
+}
+
+/* Partner of a collision of an atom with velocity v: rejection from the
+ * proposal (|v| + |w|) f(w), drawn as a mixture -- with probability |v| /
+ * (|v| + <|w|>) a Maxwellian w, otherwise a Maxwellian weighted by |w|
+ * (|w|^2/c^2 ~ Gamma(2), i.e. -ln(R1 R2), direction isotropic) -- and accepted
+ * with probability |v - w| / (|v| + |w|) <= 1.  Returns the proposals used
+ * (TPF_TRIES + 1 if none was accepted: w is then the last proposal). */
+int orc_tpf_partner(uint64_t seed, uint64_t id, uint32_t e, double Tg, const double v[3], double w[3])
+{
+    double c = sqrt(2.0 * O_KB * Tg / O_MAR);
+    double vg = c / sqrt(2.0);
+    double vm = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    double mw = 2.0 * c / sqrt(O_PI);
+    for (int t = 0; t < TPF_TRIES; t++) {
+        uint32_t a[4], b[4];
+        draw(seed, id, e, PUR_TPF_PARTNER + 2 * t, a);
+        draw(seed, id, e, PUR_TPF_PARTNER + 2 * t + 1, b);
+        if (u23(a[0]) * (vm + mw) < vm) {
+            double n1, n2, n3, n4;
+            box_muller(a[1], a[2], &n1, &n2);
+            box_muller(a[3], b[0], &n3, &n4);
+            w[0] = vg * n1; w[1] = vg * n2; w[2] = vg * n3;
+        } else {
+            double sp = c * sqrt(-log(u23(a[1]) * u23(a[2])));
+            double d[3];
+            iso_dir(a[3], b[0], d);
+            w[0] = sp * d[0]; w[1] = sp * d[1]; w[2] = sp * d[2];
+        }
+        double g[3] = {v[0] - w[0], v[1] - w[1], v[2] - w[2]};
+        double gm = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+        double wm = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+        if (u23(b[1]) * (vm + wm) < gm) return t + 1;
+    }
+    return TPF_TRIES + 1;
+}
+
+/* residence time and signed path of the straight segment xi0 -> xi1 (cell
+ * units) flown at v_x over tau seconds, cell by cell */
+static void tpf_segment(orc_state *S, double xi0, double xi1, double vx, double tau)
+{
+    int N = S->P.ncell;
+    double dx = S->dx;
+    if (vx == 0.0 || xi0 == xi1) {
+        int j = (int)floor(xi0);
+        if (j > N - 1) j = N - 1;
+        if (j < 0) j = 0;
+        S->tpf_time[j] += tau;
+        return;
+    }
+    double lo = fmin(xi0, xi1), hi = fmax(xi0, xi1);
+    int j0 = (int)floor(lo), j1 = (int)floor(hi);
+    if (j1 > N - 1) j1 = N - 1;
+    for (int j = j0; j <= j1; j++) {
+        double ov = fmin(hi, (double)(j + 1)) - fmax(lo, (double)j);
+        if (ov <= 0.0) continue;
+        S->tpf_time[j] += ov * dx / fabs(vx);
+        S->tpf_disp[j] += (vx > 0.0 ? ov : -ov) * dx;
+    }
+}
+
+/* Run every live TP atom through at most max_events flight events (in
+ * index order, atom by atom): flight to the next collision or to a wall,
+ * sticking there with the absorbed flux recorded, else a hard-sphere
+ * collision with a partner from the gas, isotropic in the centre-of-mass
+ * frame.  Returns the atoms still alive. */
+int64_t orc_tp_flight(orc_state *S, int64_t max_events)
+{
+    orc_sp *p = &S->sp[SP_TP];
+    int N = S->P.ncell;
+    double dx = S->dx;
+    double c = sqrt(2.0 * O_KB * S->P.Tg / O_MAR);
+    double mu = O_MAL + O_MAR;
+    int64_t alive = 0;
+    for (int64_t k = 0; k < p->n; k++) {
+        for (int64_t ev = 0; ev < max_events && p->alive[k]; ev++) {
+            uint32_t e = p->nev[k];
+            double v[3] = {p->vx[k], p->vy[k], p->vz[k]};
+            double vm = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+            double nu = S->ngas * S->P.sigma_tp * orc_mean_rel_speed(vm, c);
+            uint32_t f[4];
+            draw(S->P.seed, p->id[k], e, PUR_TPF_FLIGHT, f);
+            double tau = nu > 0.0 ? -log(u23(f[0])) / nu : INFINITY;
+            if (!(tau < INFINITY) && v[0] == 0.0) break;       /* no gas, no motion across the gap */
+            double xi0 = p->xi[k];
+            double xi1 = xi0 + v[0] * tau / dx;
+            if (xi1 <= 0.0 || xi1 >= (double)N) {            /* sticks at a wall */
+                int el = xi1 <= 0.0 ? 0 : 1;
+                double xw = el == 0 ? 0.0 : (double)N;
+                tpf_segment(S, xi0, xw, v[0], (xw - xi0) * dx / v[0]);
+                double E = 0.5 * O_MAL * vm * vm / O_QE;
+                double ct = vm > 0.0 ? fabs(v[0]) / vm : 1.0;
+                if (ct > 1.0) ct = 1.0;
+                hist_add(S->sp_e[el], NB_SPE, E, 300.0);
+                int ba = (int)(acos(ct) * 180.0 / O_PI);
+                if (ba > NB_ANG - 1) ba = NB_ANG - 1;
+                S->sp_ang[el][ba]++;
+                S->cnt[el == 0 ? C_TPDEP_L : C_TPDEP_R]++;
+                p->alive[k] = 0;
+                p->xi[k] = xw;
+                break;
+            }
+            tpf_segment(S, xi0, xi1, v[0], tau);
+            p->xi[k] = xi1;
+            double w[3];
+            orc_tpf_partner(S->P.seed, p->id[k], e, S->P.Tg, v, w);
+            double g[3] = {v[0] - w[0], v[1] - w[1], v[2] - w[2]};
+            double gm = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+            uint32_t sc[4];
+            draw(S->P.seed, p->id[k], e, PUR_TPF_SCATTER, sc);
+            double d[3];
+            iso_dir(sc[0], sc[1], d);
+            for (int i = 0; i < 3; i++) v[i] = (O_MAL * v[i] + O_MAR * w[i]) / mu + (O_MAR / mu) * gm * d[i];
+            p->vx[k] = v[0]; p->vy[k] = v[1]; p->vz[k] = v[2];
+            p->nev[k] = e + 1u;
+            S->cnt[C_TPCOLL]++;
+        }
+        if (p->alive[k]) alive++;
+    }
+    return alive;
+}
+
 /* Mono-energetic source: n atoms launched from the left electrode with a
  * Thompson energy (cut off at Lambda E_ion) and a cosine angle; ids
  * tag | (atoms launched before + k). */
@@ -862,7 +1015,9 @@ void orc_tp_launch(orc_state *S, int64_t n, double E_ion)
 /* kind: 0 phi, 1 n_e, 2 n_i (m^-3), 3 Gamma_e, 4 Gamma_i (m^-2 s^-1),
  * 5 EEDF, 6 IEDF left, 7 IEDF right, 8 IEADF left, 9 IEADF right,
  * 10 sputtered energy left, 11 right, 12 sputtered angle left, 13 right,
- * 14 TP density (m^-3), 15 TP mean v_x sum (m^-2 s^-1 like Gamma).
+ * 14 TP density (m^-3), 15 TP mean v_x sum (m^-2 s^-1 like Gamma),
+ * 16 event-driven TP residence time per cell (s), 17 its mean v_x per cell
+ * (signed path over residence time, m/s; 0 where no time was spent).
  * Returns the number of values written. */
 int64_t orc_diag(const orc_state *S, int kind, double *out, int64_t cap)
 {
@@ -899,6 +1054,10 @@ int64_t orc_diag(const orc_state *S, int kind, double *out, int64_t cap)
             const double *a = kind == 14 ? S->tp_dens : S->tp_vx;
             PUT(S->n_tp_samp ? w * a[m] / (vol * S->n_tp_samp) : 0.0);
         }
+        break;
+    case 16: for (int j = 0; j < N; j++) PUT(S->tpf_time[j]); break;
+    case 17:
+        for (int j = 0; j < N; j++) PUT(S->tpf_time[j] > 0.0 ? S->tpf_disp[j] / S->tpf_time[j] : 0.0);
         break;
     default: break;
     }

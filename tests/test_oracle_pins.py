@@ -591,3 +591,121 @@ def test_circuit_surface_charge_balance():
                 V = orc.source_voltage(orc.step_index)
                 assert fld["phi"][0] == pytest.approx(V - q / cb, abs=1e-9 * max(abs(V), abs(fld["phi"][0])))
         assert c["imp_e_l"] + c["imp_i_l"] > 0
+
+
+# ------------------------------------------------------------------ event-driven TP flight
+def test_mean_relative_speed_against_quadrature():
+    """<|v - w|> over a Maxwellian of most probable speed c, by numerical
+    integration over the partner's speed and angle, against the closed form
+    and its small-s series the event-driven flight uses for nu(v)."""
+    from scipy import integrate
+    c = 352.0
+    for s in (0.0, 5e-4, 2e-3, 0.3, 1.0, 2.5, 8.0):
+        v = s * c
+
+        def inner(u):
+            # angle average of |v - w| for |w| = u, in closed form over cos(theta)
+            if v == 0.0:
+                return u
+            a, b = abs(v - u), v + u
+            return (b**3 - a**3) / (6.0 * v * u) if u > 0 else v
+
+        num, _ = integrate.quad(lambda u: inner(u) * 4 * math.pi * u * u * math.exp(-u * u / (c * c))
+                                / (math.pi * c * c) ** 1.5, 0.0, 12 * c + v, limit=200, epsabs=0, epsrel=1e-12)
+        assert O.mean_rel_speed(v, c) == pytest.approx(num, rel=1e-9), s
+
+
+def test_flux_weighted_partner_sampler():
+    """Collision partners of an atom at speed v are drawn with density
+    |v - w| f(w)/<|v - w|>, so the mean relative speed over them is
+    <|v - w|^2>/<|v - w|> = (v^2 + 3c^2/2)/<|v - w|>, and the proposals
+    used per partner are geometric with mean (|v| + 2c/sqrt(pi))/<|v - w|>."""
+    T = 300.0
+    c = math.sqrt(2 * KB * T / MAR)
+    for vm in (50.0, 600.0, 4000.0):
+        v = np.array([0.6, -0.48, 0.64]) * vm
+        n = 40_000
+        g, tries = np.zeros(n), np.zeros(n)
+        for e in range(n):
+            w, t = O.tpf_partner(99, 7 | (2 << 62), e, T, v)
+            g[e] = np.linalg.norm(v - w)
+            tries[e] = t
+        gbar = O.mean_rel_speed(vm, c)
+        want = (vm * vm + 1.5 * c * c) / gbar
+        assert abs(g.mean() - want) < 4.5 * g.std() / math.sqrt(n)
+        mt = (vm + 2 * c / math.sqrt(math.pi)) / gbar
+        assert abs(tries.mean() - mt) < 4.5 * tries.std() / math.sqrt(n)
+        assert tries.max() <= 64
+
+
+def test_event_driven_flight_without_gas_is_ballistic():
+    """No gas (p = 0): every atom flies straight to the wall it heads for and
+    sticks there with its launch energy; each cell crossed whole collects
+    dx/|v_x| of residence time, so the cells away from the launch point all
+    hold the same time, the sum over the atoms of dx/|v_x|."""
+    n, N, L = 20_000, 64, 0.05
+    rng = np.random.default_rng(3)
+    orc = O.Oracle(prm(L=L, ncell=N, p=0.0, Tg=300.0, sigma_tp=3e-19), 1, 1, n)
+    v = _mono(n, 2000.0, rng)
+    xi = rng.uniform(0.2, 0.8, n) * N
+    load(orc, 2, xi, v)
+    assert orc.tp_flight(10) == 0
+    c = orc.counters()
+    right = v[0] > 0
+    assert c["tp_dep_r"] == int(right.sum()) and c["tp_dep_l"] == n - int(right.sum())
+    E = 0.5 * MAL * (v ** 2).sum(0) / QE
+    h = np.histogram(E[right], bins=600, range=(0.0, 300.0))[0]
+    assert np.array_equal(orc.diag("sputter_e_r"), h.astype(float))
+    t = orc.diag("tpf_time")
+    dx = L / N
+    full = np.ones(N, bool)
+    full[int(0.2 * N):int(0.8 * N) + 1] = False
+    want_r = (dx / np.abs(v[0][right])).sum()
+    want_l = (dx / np.abs(v[0][~right])).sum()
+    for j in np.nonzero(full)[0]:
+        want = want_r if j > 0.5 * N else want_l
+        assert t[j] == pytest.approx(want, rel=1e-10), j
+    path = np.where(right, N - xi, xi) * dx
+    assert t.sum() == pytest.approx((path / np.abs(v[0])).sum(), rel=1e-10)
+
+
+def test_event_driven_uncollided_fraction_in_cold_gas():
+    """A mono-energetic beam along +x into a cold gas (relative speed = the
+    atom's speed) crosses the gap without a collision with probability
+    exp(-n sigma L): the atoms that stick at the far wall in their first
+    event."""
+    n, N, L, ngas, sig, T = 200_000, 128, 0.03, 1.2e20, 3e-19, 1e-3
+    orc = O.Oracle(prm(L=L, ncell=N, p=ngas * KB * T, Tg=T, sigma_tp=sig), 1, 1, n)
+    v = np.zeros((3, n))
+    v[0] = 3000.0
+    load(orc, 2, np.full(n, 1e-6), v)
+    orc.tp_flight(1)
+    P = math.exp(-ngas * sig * L)
+    got = orc.counters()["tp_dep_r"]
+    assert abs(got - n * P) < 4.5 * math.sqrt(n * P * (1 - P))
+
+
+def test_event_driven_flight_agrees_with_the_per_step_test():
+    """The two TP transport schemes of the oracle, written independently --
+    the per-step collision test (orc_tp_step, dt = 5 ns, nu dt < 1e-3) and
+    the event-driven flight -- give the same energetic arrivals (> 2 eV) at
+    the far electrode from a 300 eV-ion source: count within 4.5 standard
+    deviations, energy distribution by a two-sample KS test."""
+    n, N, L = 3000, 64, 0.02
+    P = prm(L=L, ncell=N, p=0.5, Tg=300.0, sigma_tp=3e-19, seed=21)
+    a = O.Oracle(P, 1, 1, n)
+    b = O.Oracle(P, 1, 1, n)
+    a.tp_launch(n, 300.0)
+    b.tp_launch(n, 300.0)
+    a.tp_step(6000, 5e-9)                        # 30 us: energetic atoms have arrived
+    b.tp_flight(100_000)
+    edges = np.arange(601) * 0.5
+    ha, hb = a.diag("sputter_e_r"), b.diag("sputter_e_r")
+    sel = edges[:-1] >= 2.0
+    na, nb = ha[sel].sum(), hb[sel].sum()
+    assert na > 300 and abs(na - nb) < 4.5 * math.sqrt(na + nb)
+    ca, cb = np.cumsum(ha[sel]) / na, np.cumsum(hb[sel]) / nb
+    D = np.abs(ca - cb).max()
+    pval = stats.kstwobign.sf(D * math.sqrt(na * nb / (na + nb)))
+    assert pval > 1e-3, (pval, na, nb)
+    assert b.counters()["tp_dep_l"] + b.counters()["tp_dep_r"] == n
