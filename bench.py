@@ -211,6 +211,23 @@ def measure_rows(d, cfg, peak, cmp_ms, cmp_n, nsort_particles, n_atoms):
                           "value": n_atoms / per, "unit": "atom-steps/s", "mean_launch_us": per * 1e6,
                           "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                                        "frac": ach / peak, "algorithmic_bytes_per_atom_step": tp_bytes}}
+    # a8, event-driven form: the same source run to deposition, one launch per 32 events per atom
+    t = P.Discharge(P.params_from_workload(tc))
+    t.tp_launch(n_atoms, 300.0)
+    t.sync()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    left = t.tp_flight(10_000_000)
+    wall_s = time.perf_counter() - t0
+    cnt = t.counters()
+    events = cnt["tp_coll"] + cnt["tp_dep_l"] + cnt["tp_dep_r"]
+    rows["a8_tp_flight_to_deposition"] = {
+        "workload": "tp_transport: %d Al atoms from 300 eV Ar+ impacts, 50 mm, 0.5 Pa 300 K Ar, event-driven "
+                    "flight to deposition" % n_atoms,
+        "value": events / wall_s, "unit": "atom-events/s", "seconds_to_deposition": wall_s,
+        "events": int(events), "events_per_atom": events / n_atoms, "still_in_flight": int(left),
+        "deposited_far": int(cnt["tp_dep_r"]), "deposited_source": int(cnt["tp_dep_l"])}
+    t.close()
     # a9: compaction (counting sort by cell of one species) in the timed run
     if cmp_n:
         per_sort = cmp_ms / cmp_n * 1e-3

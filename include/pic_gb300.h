@@ -137,13 +137,17 @@ int pic_sync(pic_ctx* ctx);
  * 14 SPUTTER_ANG_L 15 SPUTTER_ANG_R  Al deposition angles, 90 x 1 deg
  * 16 TP_DENS  time-averaged Al density, m^-3;  17 TP_V  Al mean v_x, m/s
  * 18 E        instantaneous field, V/m;  19 PHI_NOW  instantaneous potential
+ * 20 TPF_TIME  event-driven TP flight (tp_flight): residence time summed over
+ *              the atoms, s, per cell (N values; Sec. "Limitations and
+ *              Constraints": time-weighted densities)
+ * 21 TPF_VX    its mean v_x per cell (signed path / residence time), m/s
  * Histograms are raw counts.  Writes min(cap, size) values, *n_written = size. */
 enum pic_diag_kind {
     PIC_DIAG_PHI = 0, PIC_DIAG_NE, PIC_DIAG_NI, PIC_DIAG_GAMMA_E, PIC_DIAG_GAMMA_I, PIC_DIAG_VE,
     PIC_DIAG_VI, PIC_DIAG_EEDF, PIC_DIAG_IEDF_L, PIC_DIAG_IEDF_R, PIC_DIAG_IEADF_L,
     PIC_DIAG_IEADF_R, PIC_DIAG_SPUTTER_E_L, PIC_DIAG_SPUTTER_E_R, PIC_DIAG_SPUTTER_ANG_L,
     PIC_DIAG_SPUTTER_ANG_R, PIC_DIAG_TP_DENS, PIC_DIAG_TP_V, PIC_DIAG_E, PIC_DIAG_PHI_NOW,
-    PIC_DIAG_COUNT
+    PIC_DIAG_TPF_TIME, PIC_DIAG_TPF_VX, PIC_DIAG_COUNT
 };
 int pic_diag(pic_ctx* ctx, int kind, double* host_out, int64_t cap, int64_t* n_written);
 
@@ -185,6 +189,20 @@ int tp_launch(pic_ctx* ctx, const tp_source* src);
  * Ar partner).  If n_alive is not NULL the stream is synchronised and the
  * number of atoms still in flight is returned. */
 int tp_step(pic_ctx* ctx, int64_t n_steps, int64_t* n_alive);
+
+/* Event-driven (gridless) flight of the test particles (Sec. "Kinetic
+ * Particle Simulation": free flight between collisions; Sec. "Limitations
+ * and Constraints": time-weighted densities): each live atom flies straight
+ * for tau = -ln(R) / nu(v) to its next collision or to an electrode, nu(v) =
+ * n sigma_tp <|v - w|> over the Maxwellian gas; at an electrode it sticks
+ * (Al deposition histograms and counters, as tp_step); otherwise it collides
+ * as a hard sphere with a partner drawn from the gas weighted by |v - w|.
+ * Each atom goes through at most max_events events in this call (launches of
+ * up to 32 events each; the call returns early once no atom is alive).
+ * Residence time and path are added per cell (PIC_DIAG_TPF_TIME, _VX).
+ * Synchronises the stream; *n_alive (may be NULL) receives the atoms still
+ * in flight. */
+int tp_flight(pic_ctx* ctx, int64_t max_events, int64_t* n_alive);
 
 /* Compact one species now (drop removed slots, counting sort by cell). */
 int pic_compact(pic_ctx* ctx, int species);

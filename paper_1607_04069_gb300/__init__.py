@@ -23,7 +23,7 @@ SPECIES = {"e": 0, "i": 1, "tp": 2}
 DIAG = {"phi": 0, "n_e": 1, "n_i": 2, "gamma_e": 3, "gamma_i": 4, "v_e": 5, "v_i": 6, "eedf": 7,
         "iedf_l": 8, "iedf_r": 9, "ieadf_l": 10, "ieadf_r": 11, "sputter_e_l": 12,
         "sputter_e_r": 13, "sputter_ang_l": 14, "sputter_ang_r": 15, "tp_dens": 16, "tp_v": 17,
-        "E": 18, "phi_now": 19}
+        "E": 18, "phi_now": 19, "tpf_time": 20, "tpf_vx": 21}
 COUNTERS = ["n_e_slots", "n_i_slots", "n_tp_slots", "step", "tp_step", "imp_e_l", "imp_e_r",
             "imp_i_l", "imp_i_r", "ionizations", "sputtered_l", "sputtered_r", "tp_dep_l",
             "tp_dep_r", "numerics", "elastic", "excitation", "cx", "iso", "tp_coll", "capacity"]
@@ -108,6 +108,7 @@ def lib():
             "pic_set_field": [vp, vp],
             "tp_launch": [vp, C.POINTER(TpSource)],
             "tp_step": [vp, i64, pi64],
+            "tp_flight": [vp, i64, pi64],
             "pic_compact": [vp, C.c_int],
             "pic_timing": [vp, C.c_int],
             "pic_kernel_time": [vp, C.c_int, C.POINTER(dbl), pi64],
@@ -274,6 +275,13 @@ class Discharge:
         a = C.c_int64()
         _check(lib().tp_step(self.h, int(n), C.byref(a) if count_alive else None))
         return a.value if count_alive else None
+
+    def tp_flight(self, max_events=1_000_000):
+        """Event-driven flight of the test particles, at most max_events
+        events per atom; returns the atoms still in flight."""
+        a = C.c_int64()
+        _check(lib().tp_flight(self.h, int(max_events), C.byref(a)))
+        return a.value
 
     def compact(self, s):
         _check(lib().pic_compact(self.h, SPECIES.get(s, s)))

@@ -113,6 +113,10 @@ void carve(pic_ctx* c, char* base, size_t* small_end, size_t* total)
         d.diag.sp_ang[s] = L.take<unsigned long long>(base, kNbAng);
     }
     d.diag.tp_dens = L.take<unsigned long long>(base, 2 * N1);
+    d.diag.tpf_tpart = L.take<long long>(base, N1);
+    d.diag.tpf_tdiff = L.take<long long>(base, N1);
+    d.diag.tpf_dpart = L.take<long long>(base, N1);
+    d.diag.tpf_ddiff = L.take<long long>(base, N1);
     d.diag.tp_vx = L.take<long long>(base, 2 * N1);
     d.diag.eedf = L.take<unsigned long long>(base, kNbEedf);
     d.tp_q = L.take<unsigned long long>(base, N1);
@@ -135,7 +139,7 @@ void carve(pic_ctx* c, char* base, size_t* small_end, size_t* total)
             B.vy = L.take<float>(base, n);
             B.vz = L.take<float>(base, n);
             B.id = L.take<uint64_t>(base, n);
-            B.nev = s == kTP ? nullptr : L.take<uint32_t>(base, n);
+            B.nev = L.take<uint32_t>(base, n);    // TP: index of the next flight event
         }
     for (int s = 0; s < 2; ++s) d.evflag[s] = L.take<unsigned char>(base, (size_t)(cap[s] > 0 ? cap[s] : 1) + 4);
     *total = (L.off + 255) & ~(size_t)255;
@@ -242,6 +246,10 @@ void derive(pic_ctx* c)
     d.vth_gas = (float)std::sqrt(kKB * p.gas_temp_k / kMAR);
     d.tp_scale = (float)(p.tp_dt * 4294967296.0 / p.gap_m);
     d.tp_nsig_dt = (float)(ngas * p.sigma_tp * p.tp_dt);
+    d.tpf_c = (float)std::sqrt(2.0 * kKB * p.gas_temp_k / kMAR);
+    d.tpf_nsig = (float)(ngas * p.sigma_tp);
+    d.tpf_scale = (float)(4294967296.0 / p.gap_m);
+    d.tpf_kt = (float)(256.0 * p.gap_m);
     d.Emax_hist = (float)(2.0 * p.rf_volt_v > 0 ? 2.0 * p.rf_volt_v : 1.0);
     d.sputter = p.sputter_enable != 0;
     d.diag_every = p.diag_every;
@@ -778,6 +786,23 @@ int pic_diag(pic_ctx* c, int kind, double* out, int64_t cap, int64_t* n_written)
     case PIC_DIAG_PHI_NOW:
         if ((rc = getd(c->d.phi, N1, v))) return rc;
         break;
+    case PIC_DIAG_TPF_TIME: case PIC_DIAG_TPF_VX: {
+        std::vector<long long> tp(N1), td(N1), dp(N1), dd(N1);
+        CK(cudaMemcpy(tp.data(), c->d.diag.tpf_tpart, N1 * 8, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(td.data(), c->d.diag.tpf_tdiff, N1 * 8, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(dp.data(), c->d.diag.tpf_dpart, N1 * 8, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(dd.data(), c->d.diag.tpf_ddiff, N1 * 8, cudaMemcpyDeviceToHost));
+        v.assign(N, 0.0);
+        long long ts = 0, ds = 0;
+        for (int j = 0; j < N; ++j) {
+            ts += td[j];
+            ds += dd[j];
+            const double t = (double)(tp[j] + ts) * 0x1p-40;             // s
+            const double path = (double)(dp[j] + ds) * (c->p.gap_m * 0x1p-32);   // m
+            v[j] = kind == PIC_DIAG_TPF_TIME ? t : (t > 0.0 ? path / t : 0.0);
+        }
+        break;
+    }
     }
     const int64_t n = (int64_t)v.size();
     for (int64_t i = 0; i < n && i < cap; ++i) out[i] = v[i];
@@ -800,6 +825,8 @@ int pic_reset_averages(pic_ctx* c)
         CK(cudaMemsetAsync(g.sp_ang[s], 0, kNbAng * 8, c->stream));
     }
     CK(cudaMemsetAsync(g.tp_dens, 0, 2 * N1 * 8, c->stream));
+    for (long long* a : {g.tpf_tpart, g.tpf_tdiff, g.tpf_dpart, g.tpf_ddiff})
+        CK(cudaMemsetAsync(a, 0, N1 * 8, c->stream));
     CK(cudaMemsetAsync(g.tp_vx, 0, 2 * N1 * 8, c->stream));
     CK(cudaMemsetAsync(g.eedf, 0, kNbEedf * 8, c->stream));
     CK(cudaMemsetAsync(&c->d.ctl->n_avg, 0, 3 * sizeof(long long), c->stream));
@@ -903,6 +930,7 @@ int pic_set_species(pic_ctx* c, int s, int64_t n, const void* pos, const float* 
         CK(cudaMemcpyAsync(B.vz, vz, (size_t)n * 4, cudaMemcpyHostToDevice, c->stream));
         CK(cudaMemcpyAsync(B.id, id, (size_t)n * 8, cudaMemcpyHostToDevice, c->stream));
         if (s != kTP) CK(launch_entry_nev(c->d, s, h.cur[s], n, (unsigned int)c->h_step, c->stream));
+        else CK(cudaMemsetAsync(B.nev, 0, (size_t)n * 4, c->stream));   // no flight event yet
     }
     long long nn = n;
     CK(cudaMemcpyAsync(&c->d.ctl->n[s], &nn, sizeof nn, cudaMemcpyHostToDevice, c->stream));
@@ -972,6 +1000,36 @@ int tp_step(pic_ctx* c, int64_t n, int64_t* n_alive)
         if (rc) return rc;
         *n_alive = c->tp_launched + (int64_t)h.cnt[kCntSputL] + (int64_t)h.cnt[kCntSputR] -
                    (int64_t)h.cnt[kCntTpDepL] - (int64_t)h.cnt[kCntTpDepR];
+    }
+    return PIC_OK;
+}
+
+int tp_flight(pic_ctx* c, int64_t max_events, int64_t* n_alive)
+{
+    if (!c || max_events < 0) return fail(PIC_ERR_INVALID_ARG, "bad arguments");
+    CK(cudaSetDevice(c->device));
+    constexpr int kEventsPerLaunch = 32;
+    unsigned long long alive = 0;
+    bool any = false;
+    for (int64_t done = 0; done < max_events;) {
+        const int k = (int)std::min<int64_t>(kEventsPerLaunch, max_events - done);
+        CK(cudaMemsetAsync(&c->d.ctl->tpf_alive, 0, sizeof(unsigned long long), c->stream));
+        CK(launch_tp_flight(c->d, k, c->grid_tp * 4, c->stream));
+        CK(cudaMemcpyAsync(&alive, &c->d.ctl->tpf_alive, sizeof alive, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        any = true;
+        done += k;
+        if (alive == 0) break;
+    }
+    if (n_alive) {
+        if (!any) {                                    // no launch: count the live atoms as they are
+            Ctl h;
+            int rc = read_ctl(c, &h);
+            if (rc) return rc;
+            alive = (unsigned long long)(c->tp_launched + (int64_t)h.cnt[kCntSputL] + (int64_t)h.cnt[kCntSputR] -
+                                         (int64_t)h.cnt[kCntTpDepL] - (int64_t)h.cnt[kCntTpDepR]);
+        }
+        *n_alive = (int64_t)alive;
     }
     return PIC_OK;
 }

@@ -49,7 +49,7 @@ enum : uint32_t {
     kPurInit = 1, kPurColl = 2, kPurIonize = 3, kPurNewIon = 4, kPurBirthId = 5, kPurGas = 6,
     kPurGap = 7, kPurGap0 = 8,
     kPurSpTrial = 16, kPurSpEmit = 32, kPurSpId = 48, kPurTpGas = 64, kPurTpColl = 65,
-    kPurTpLaunch = 66
+    kPurTpLaunch = 66, kPurTpfFlight = 70, kPurTpfScatter = 71, kPurTpfPartner = 72
 };
 
 // species and id tags
@@ -95,6 +95,7 @@ struct Ctl {                   // device control block
     alignas(128) unsigned int err;
     long long wall_delta;      // the running launch's share of wall_dn (moved over at commit)
     alignas(128) unsigned long long cnt[kNumCnt];   // counts of the TP kernels
+    alignas(128) unsigned long long tpf_alive;      // atoms alive after an event-driven flight launch
 };
 
 // per-CTA event counts of the step launch: row b of Dev::tally belongs to
@@ -118,6 +119,11 @@ struct Diag {
     unsigned long long* eedf;
     unsigned long long* sp_e[2];
     unsigned long long* sp_ang[2];
+    // event-driven TP flight, per cell: residence time (2^-40 s) and signed
+    // path (2^-32 L), each as a partial-cell term [N] plus a difference
+    // array [N+1] of the cells crossed whole (value of cell j: part[j] +
+    // sum_{i <= j} diff[i])
+    long long *tpf_tpart, *tpf_tdiff, *tpf_dpart, *tpf_ddiff;
 };
 
 // Per-launch inputs of a step computed on the host: the electrode voltage of
@@ -165,6 +171,11 @@ struct Dev {                   // everything a kernel needs, passed by value
     // circ_b = 2 beta, beta = 1 / (1 + L c / eps0)
     double circ_a, circ_b;
     int circuit, pad3;
+    // event-driven TP flight
+    float tpf_c;                     // most probable speed of the gas, sqrt(2 k T / M_Ar)
+    float tpf_nsig;                  // n sigma_tp, 1/m
+    float tpf_scale;                 // 2^32 / L: fixed-point units per metre
+    float tpf_kt;                    // 256 L: residence time (2^-40 s) per fixed-point unit at 1 m/s
     float c2f;                       // A / (2 dx): E per unit of the integer bracket
     float pad2;
     // push

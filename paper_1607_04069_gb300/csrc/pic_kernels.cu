@@ -204,6 +204,7 @@ __device__ __noinline__ void ev_ion_wall(const Dev& d, uint64_t id, uint32_t l, 
         T.vy[idx] = v.y;
         T.vz[idx] = v.z;
         T.id[idx] = child_id(es.b.x, es.b.y, kTP);
+        T.nev[idx] = 0u;
         atomicAdd(el == 0 ? &tally->sput[0] : &tally->sput[1], 1u);
     }
 }
@@ -1040,7 +1041,7 @@ __global__ void k_sort_scatter(Dev d, int s)
                     fy = A.vy[i];
                     fz = A.vz[i];
                     fid = A.id[i];
-                    if (s != kTP) fnev = A.nev[i];
+                    fnev = A.nev[i];
                 }
                 act = is_alive(x);
             }
@@ -1068,7 +1069,7 @@ __global__ void k_sort_scatter(Dev d, int s)
                 Bn.vy[o] = fy;
                 Bn.vz[o] = fz;
                 Bn.id[o] = fid;
-                if (s != kTP) Bn.nev[o] = fnev;
+                Bn.nev[o] = fnev;
             }
         }
         __syncthreads();

@@ -227,6 +227,161 @@ __global__ void __launch_bounds__(kTpThreads, 2) k_tp_step(Dev d)
     }
 }
 
+
+// ---------------------------------------------------------------- event-driven flight
+// The gridless alternative to the per-step collision test (Sec. "Kinetic
+// Particle Simulation": free flight tau = -tau_c ln R_f between events; Sec.
+// "Limitations and Constraints": densities weighted by flight duration).  For
+// hard spheres in a Maxwellian gas the rate is nu(v) = n sigma <|v - w|>, the
+// relative speed averaged over the gas; at a collision the partner has the
+// density |v - w| f(w) / <|v - w|>, drawn by rejection from the proposal
+// (|v| + |w|) f(w): with probability |v| / (|v| + <|w|>) a Maxwellian w,
+// otherwise a Maxwellian weighted by |w| (|w|^2 / c^2 = -ln(R1 R2), direction
+// isotropic), accepted with probability |v - w| / (|v| + |w|).  Event e of an
+// atom draws Philox(id, e, TPF_FLIGHT), (id, e, TPF_PARTNER + 2t [+1]) for
+// proposal t and (id, e, TPF_SCATTER); e is kept per atom (SpBuf::nev).  One
+// thread takes one atom through up to kmax events per launch.
+constexpr int kTpfTries = 64;                     // proposals per collision (each accepted w.p. >= 1/2)
+
+__device__ __forceinline__ float mean_rel_speed(float vm, float c)
+{
+    const float s = vm / c;
+    if (s < 1e-3f) return 1.1283792f * c * (1.0f + s * s * (1.0f / 3.0f));
+    return c * ((s + 0.5f / s) * erff(s) + expf(-s * s) * 0.5641896f);
+}
+
+__device__ __forceinline__ void tpf_add(long long* a, int i, long long v)
+{
+    if (v) atomicAdd((unsigned long long*)&a[i], (unsigned long long)v);
+}
+
+// residence time and signed path of the straight segment x0 -> x1 (fixed
+// point) flown at v_x; tau only where v_x = 0 (the atom stays in its cell)
+__device__ void tpf_segment(const Dev& d, long long x0, long long x1, float vx, float tau)
+{
+    const int S = 32 - d.kshift, N = d.ncell;
+    if (vx == 0.0f || x0 == x1) {
+        const int j = min(N - 1, (int)(x0 >> S));
+        tpf_add(d.diag.tpf_tpart, j, __float2ll_rn(tau * 1099511627776.0f));
+        return;
+    }
+    const long long lo = min(x0, x1), hi = max(x0, x1);
+    const long long sg = vx > 0.0f ? 1 : -1;
+    const float kt = d.tpf_kt / fabsf(vx);        // 2^-40 s per fixed-point unit
+    const int ja = min(N - 1, (int)(lo >> S)), jb = min(N - 1, (int)((hi - 1) >> S));
+    if (ja == jb) {
+        tpf_add(d.diag.tpf_tpart, ja, __float2ll_rn((float)(hi - lo) * kt));
+        tpf_add(d.diag.tpf_dpart, ja, sg * (hi - lo));
+        return;
+    }
+    const long long oa = ((long long)(ja + 1) << S) - lo, ob = hi - ((long long)jb << S);
+    tpf_add(d.diag.tpf_tpart, ja, __float2ll_rn((float)oa * kt));
+    tpf_add(d.diag.tpf_tpart, jb, __float2ll_rn((float)ob * kt));
+    tpf_add(d.diag.tpf_dpart, ja, sg * oa);
+    tpf_add(d.diag.tpf_dpart, jb, sg * ob);
+    if (jb > ja + 1) {                            // the cells crossed whole
+        const long long tc = __float2ll_rn((float)(1ll << S) * kt);
+        tpf_add(d.diag.tpf_tdiff, ja + 1, tc);
+        tpf_add(d.diag.tpf_tdiff, jb, -tc);
+        tpf_add(d.diag.tpf_ddiff, ja + 1, sg << S);
+        tpf_add(d.diag.tpf_ddiff, jb, -(sg << S));
+    }
+}
+
+__global__ void __launch_bounds__(kTpThreads) k_tp_flight(Dev d, int kmax)
+{
+    Ctl* ctl = d.ctl;
+    const SpBuf B = d.buf[kTP][ctl->cur[kTP]];
+    const long long n = ctl->n[kTP];
+    const float c = d.tpf_c, vg = 0.70710678f * d.tpf_c, mw = 1.1283792f * d.tpf_c;
+    const float mu_al = (float)(kMAL / (kMAL + kMAR)), mu_ar = (float)(kMAR / (kMAL + kMAR));
+    const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
+    unsigned int alive = 0, ncoll = 0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        uint32_t x = ((const uint32_t*)B.pos)[k];
+        if (x == 0u) continue;
+        float vx = B.vx[k], vy = B.vy[k], vz = B.vz[k];
+        const uint64_t id = B.id[k];
+        uint32_t e = B.nev[k];
+        bool live = true;
+        for (int ev = 0; ev < kmax; ++ev) {
+            const float vm = sqrtf(vx * vx + vy * vy + vz * vz);
+            const float nu = d.tpf_nsig * mean_rel_speed(vm, c);
+            const uint4 f = draw(d.seed, id, e, kPurTpfFlight);
+            const float tau = nu > 0.0f ? -logf(u23(f.x)) / nu : INFINITY;
+            if (!(tau < INFINITY) && vx == 0.0f) break;            // no gas, no motion across the gap
+            const float disp = vx * tau * d.tpf_scale;
+            long long x1 = 0;
+            int el = -1;
+            if (!(fabsf(disp) < 8.0e9f)) {
+                el = disp < 0.0f ? 0 : 1;
+            } else {
+                x1 = (long long)x + __float2ll_rn(disp);
+                if (x1 <= 0) el = 0;
+                else if (x1 >= 4294967296LL) el = 1;
+            }
+            if (el >= 0) {                                          // sticks at an electrode
+                tpf_segment(d, x, el == 0 ? 0ll : 4294967296LL, vx, tau);
+                const float E = vm * vm * (float)(0.5 * kMAL / kQE);
+                const float ct = fminf(vm > 0.0f ? fabsf(vx) / vm : 1.0f, 1.0f);
+                int be = (int)(E / 300.0f * (float)kNbSpE);
+                be = be < 0 ? 0 : (be > kNbSpE - 1 ? kNbSpE - 1 : be);
+                int ba = (int)(acosf(ct) * (float)(180.0 / kPI));
+                ba = ba < 0 ? 0 : (ba > kNbAng - 1 ? kNbAng - 1 : ba);
+                atomicAdd(&d.diag.sp_e[el][be], 1ull);
+                atomicAdd(&d.diag.sp_ang[el][ba], 1ull);
+                atomicAdd(&ctl->cnt[el == 0 ? kCntTpDepL : kCntTpDepR], 1ull);
+                live = false;
+                break;
+            }
+            tpf_segment(d, x, x1, vx, tau);
+            x = (uint32_t)x1;
+            // the collision partner, flux-weighted
+            float wx = 0.0f, wy = 0.0f, wz = 0.0f, gm = 0.0f;
+            for (int t = 0; t < kTpfTries; ++t) {
+                uint4 cw[2];
+                cw[0] = make_uint4((uint32_t)id, (uint32_t)(id >> 32), e, kPurTpfPartner + 2 * t);
+                cw[1] = make_uint4((uint32_t)id, (uint32_t)(id >> 32), e, kPurTpfPartner + 2 * t + 1);
+                philox_n<2>(cw, k0, k1);
+                const uint4 a = cw[0], b = cw[1];
+                if (u23(a.x) * (vm + mw) < vm) {
+                    const float2 n12 = box_muller(a.y, a.z), n34 = box_muller(a.w, b.x);
+                    wx = vg * n12.x; wy = vg * n12.y; wz = vg * n34.x;
+                } else {
+                    const float sp = c * sqrtf(-logf(u23(a.y) * u23(a.z)));
+                    const float3 dd = iso_dir(a.w, b.x);
+                    wx = sp * dd.x; wy = sp * dd.y; wz = sp * dd.z;
+                }
+                const float gx = vx - wx, gy = vy - wy, gz = vz - wz;
+                gm = sqrtf(gx * gx + gy * gy + gz * gz);
+                const float wm = sqrtf(wx * wx + wy * wy + wz * wz);
+                if (u23(b.y) * (vm + wm) < gm) break;
+            }
+            // hard sphere, isotropic in the centre of mass
+            const uint4 sc = draw(d.seed, id, e, kPurTpfScatter);
+            const float3 dir = iso_dir(sc.x, sc.y);
+            vx = mu_al * vx + mu_ar * wx + mu_ar * gm * dir.x;
+            vy = mu_al * vy + mu_ar * wy + mu_ar * gm * dir.y;
+            vz = mu_al * vz + mu_ar * wz + mu_ar * gm * dir.z;
+            ++e;
+            ++ncoll;
+        }
+        ((uint32_t*)B.pos)[k] = live ? x : 0u;
+        B.vx[k] = vx;
+        B.vy[k] = vy;
+        B.vz[k] = vz;
+        B.nev[k] = e;
+        alive += live ? 1u : 0u;
+    }
+    alive = __reduce_add_sync(0xffffffffu, alive);
+    ncoll = __reduce_add_sync(0xffffffffu, ncoll);
+    if ((threadIdx.x & 31) == 0) {
+        if (alive) atomicAdd(&ctl->tpf_alive, (unsigned long long)alive);
+        if (ncoll) atomicAdd(&ctl->cnt[kCntTpColl], (unsigned long long)ncoll);
+    }
+}
+
 // Mono-energetic ion source on the left electrode: n atoms with Thompson
 // energies (cut off at Lambda E_ion) and cosine angles, ids tag | (id0 + k).
 __global__ void k_tp_launch(Dev d, long long n, long long id0, float Emax)
@@ -248,6 +403,7 @@ __global__ void k_tp_launch(Dev d, long long n, long long id0, float Emax)
     B.vy[idx] = v.y;
     B.vz[idx] = v.z;
     B.id[idx] = id;
+    B.nev[idx] = 0u;
 }
 
 __global__ void k_commit_count(Dev d, int s, long long add)
@@ -257,6 +413,12 @@ __global__ void k_commit_count(Dev d, int s, long long add)
 }
 
 size_t tp_smem(int ncell) { return (size_t)ncell * 12 + (size_t)(ncell + 1) * 8; }
+
+cudaError_t launch_tp_flight(const Dev& d, int kmax, int grid, cudaStream_t st)
+{
+    k_tp_flight<<<grid, kTpThreads, 0, st>>>(d, kmax);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_tp_step(const Dev& d, int grid, cudaStream_t st)
 {
