@@ -1014,7 +1014,9 @@ int tp_flight(pic_ctx* c, int64_t max_events, int64_t* n_alive)
     for (int64_t done = 0; done < max_events;) {
         const int k = (int)std::min<int64_t>(kEventsPerLaunch, max_events - done);
         CK(cudaMemsetAsync(&c->d.ctl->tpf_alive, 0, sizeof(unsigned long long), c->stream));
-        CK(launch_tp_flight(c->d, k, c->grid_tp * 4, c->stream));
+        Ctl h;                                         // slots in use: the launch takes one CTA per 1024
+        CK(cudaMemcpy(&h.n[kTP], &c->d.ctl->n[kTP], sizeof(long long), cudaMemcpyDeviceToHost));
+        CK(launch_tp_flight(c->d, k, h.n[kTP], c->stream));
         CK(cudaMemcpyAsync(&alive, &c->d.ctl->tpf_alive, sizeof alive, cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
         any = true;

@@ -36,7 +36,7 @@ cudaError_t launch_sort(const Dev& d, int s, int grid, cudaStream_t st);
 cudaError_t launch_tp_step(const Dev& d, int grid, cudaStream_t st);
 // event-driven flight: every live TP atom through at most kmax events; the
 // atoms still alive are added to Ctl::tpf_alive
-cudaError_t launch_tp_flight(const Dev& d, int kmax, int grid, cudaStream_t st);
+cudaError_t launch_tp_flight(const Dev& d, int kmax, long long n, cudaStream_t st);
 cudaError_t launch_tp_launch(const Dev& d, long long n, long long id0, float Emax, cudaStream_t st);
 cudaError_t launch_op_deposit(const void* pos, int pos64, long long n, int ncell, int kshift,
                               unsigned long long* q, int grid, cudaStream_t st);

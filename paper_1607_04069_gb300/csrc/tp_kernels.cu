@@ -250,19 +250,46 @@ __device__ __forceinline__ float mean_rel_speed(float vm, float c)
     return c * ((s + 0.5f / s) * erff(s) + expf(-s * s) * 0.5641896f);
 }
 
-__device__ __forceinline__ void tpf_add(long long* a, int i, long long v)
+// Per-CTA tallies of a flight launch in shared memory, flushed once per
+// CTA: each cell array (residence time and path, partial-cell terms and
+// difference arrays) as two 32-bit parts, value = hi 2^16 + lo with lo = the
+// low 16 bits, and the Al deposition histograms.  A CTA takes at most
+// kTpfAtomsPerCta atoms through at most kTpfMaxEvents events, so a part sums
+// at most 1024 x 33 values below 2^16 (lo) or 2^14 (hi) and cannot
+// overflow; a value of 2^30 or more goes to global memory directly.
+constexpr int kTpfAtomsPerCta = 1024;
+constexpr int kTpfMaxEvents = 32;
+struct TpfAcc {
+    unsigned int* lo;         // [4][N+1]: tpart, tdiff, dpart, ddiff
+    int* hi;                  // [4][N+1]
+    unsigned int* spe;        // [2][kNbSpE]
+    unsigned int* spa;        // [2][kNbAng]
+    int n1;                   // N + 1
+};
+
+size_t tpf_smem(int N) { return (size_t)8 * 4 * (N + 1) + (size_t)4 * 2 * (kNbSpE + kNbAng); }
+
+__device__ __forceinline__ void tpf_add(const TpfAcc& A, long long* g, int k, int i, long long v)
 {
-    if (v) atomicAdd((unsigned long long*)&a[i], (unsigned long long)v);
+    if (!v) return;
+    if (v >= (1ll << 30) || v <= -(1ll << 30)) {
+        atomicAdd((unsigned long long*)&g[i], (unsigned long long)v);
+        return;
+    }
+    atomicAdd(&A.lo[k * A.n1 + i], (unsigned int)(v & 0xffff));
+    const int h = (int)(v >> 16);
+    if (h) atomicAdd(&A.hi[k * A.n1 + i], h);
 }
 
 // residence time and signed path of the straight segment x0 -> x1 (fixed
 // point) flown at v_x; tau only where v_x = 0 (the atom stays in its cell)
-__device__ void tpf_segment(const Dev& d, long long x0, long long x1, float vx, float tau)
+__device__ void tpf_segment(const Dev& d, const TpfAcc& A, long long x0, long long x1, float vx, float tau)
 {
     const int S = 32 - d.kshift, N = d.ncell;
+    const Diag& g = d.diag;
     if (vx == 0.0f || x0 == x1) {
         const int j = min(N - 1, (int)(x0 >> S));
-        tpf_add(d.diag.tpf_tpart, j, __float2ll_rn(tau * 1099511627776.0f));
+        tpf_add(A, g.tpf_tpart, 0, j, __float2ll_rn(tau * 1099511627776.0f));
         return;
     }
     const long long lo = min(x0, x1), hi = max(x0, x1);
@@ -270,47 +297,80 @@ __device__ void tpf_segment(const Dev& d, long long x0, long long x1, float vx, 
     const float kt = d.tpf_kt / fabsf(vx);        // 2^-40 s per fixed-point unit
     const int ja = min(N - 1, (int)(lo >> S)), jb = min(N - 1, (int)((hi - 1) >> S));
     if (ja == jb) {
-        tpf_add(d.diag.tpf_tpart, ja, __float2ll_rn((float)(hi - lo) * kt));
-        tpf_add(d.diag.tpf_dpart, ja, sg * (hi - lo));
+        tpf_add(A, g.tpf_tpart, 0, ja, __float2ll_rn((float)(hi - lo) * kt));
+        tpf_add(A, g.tpf_dpart, 2, ja, sg * (hi - lo));
         return;
     }
     const long long oa = ((long long)(ja + 1) << S) - lo, ob = hi - ((long long)jb << S);
-    tpf_add(d.diag.tpf_tpart, ja, __float2ll_rn((float)oa * kt));
-    tpf_add(d.diag.tpf_tpart, jb, __float2ll_rn((float)ob * kt));
-    tpf_add(d.diag.tpf_dpart, ja, sg * oa);
-    tpf_add(d.diag.tpf_dpart, jb, sg * ob);
+    tpf_add(A, g.tpf_tpart, 0, ja, __float2ll_rn((float)oa * kt));
+    tpf_add(A, g.tpf_tpart, 0, jb, __float2ll_rn((float)ob * kt));
+    tpf_add(A, g.tpf_dpart, 2, ja, sg * oa);
+    tpf_add(A, g.tpf_dpart, 2, jb, sg * ob);
     if (jb > ja + 1) {                            // the cells crossed whole
         const long long tc = __float2ll_rn((float)(1ll << S) * kt);
-        tpf_add(d.diag.tpf_tdiff, ja + 1, tc);
-        tpf_add(d.diag.tpf_tdiff, jb, -tc);
-        tpf_add(d.diag.tpf_ddiff, ja + 1, sg << S);
-        tpf_add(d.diag.tpf_ddiff, jb, -(sg << S));
+        tpf_add(A, g.tpf_tdiff, 1, ja + 1, tc);
+        tpf_add(A, g.tpf_tdiff, 1, jb, -tc);
+        tpf_add(A, g.tpf_ddiff, 3, ja + 1, sg << S);
+        tpf_add(A, g.tpf_ddiff, 3, jb, -(sg << S));
     }
 }
 
+// kmax <= kTpfMaxEvents; CTA b takes atoms [b kTpfAtomsPerCta, (b + 1) kTpfAtomsPerCta)
 __global__ void __launch_bounds__(kTpThreads) k_tp_flight(Dev d, int kmax)
 {
+    extern __shared__ __align__(16) unsigned char tpf_raw[];
     Ctl* ctl = d.ctl;
+    const int N1 = d.ncell + 1;
+    TpfAcc A;
+    A.n1 = N1;
+    A.lo = (unsigned int*)tpf_raw;
+    A.hi = (int*)tpf_raw + (size_t)4 * N1;
+    A.spe = (unsigned int*)tpf_raw + (size_t)8 * N1;
+    A.spa = A.spe + 2 * kNbSpE;
+    __shared__ unsigned int s_cnt[4];             // alive, collisions, deposited left, right
+    __shared__ unsigned int s_next;               // next atom of the CTA's range to take
+    for (int i = threadIdx.x; i < 8 * N1 + 2 * (kNbSpE + kNbAng); i += blockDim.x) ((unsigned int*)tpf_raw)[i] = 0;
+    if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0;
+    if (threadIdx.x == 0) s_next = 0;
+    __syncthreads();
+
     const SpBuf B = d.buf[kTP][ctl->cur[kTP]];
     const long long n = ctl->n[kTP];
     const float c = d.tpf_c, vg = 0.70710678f * d.tpf_c, mw = 1.1283792f * d.tpf_c;
     const float mu_al = (float)(kMAL / (kMAL + kMAR)), mu_ar = (float)(kMAR / (kMAL + kMAR));
     const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
-    unsigned int alive = 0, ncoll = 0;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
-         k += (long long)gridDim.x * blockDim.x) {
-        uint32_t x = ((const uint32_t*)B.pos)[k];
-        if (x == 0u) continue;
-        float vx = B.vx[k], vy = B.vy[k], vz = B.vz[k];
-        const uint64_t id = B.id[k];
-        uint32_t e = B.nev[k];
-        bool live = true;
-        for (int ev = 0; ev < kmax; ++ev) {
-            const float vm = sqrtf(vx * vx + vy * vy + vz * vz);
-            const float nu = d.tpf_nsig * mean_rel_speed(vm, c);
-            const uint4 f = draw(d.seed, id, e, kPurTpfFlight);
-            const float tau = nu > 0.0f ? -logf(u23(f.x)) / nu : INFINITY;
-            if (!(tau < INFINITY) && vx == 0.0f) break;            // no gas, no motion across the gap
+    unsigned int n_alive = 0, n_coll = 0, n_dep_l = 0, n_dep_r = 0;
+    const long long a0 = (long long)blockIdx.x * kTpfAtomsPerCta;
+    const long long na = min(n, a0 + kTpfAtomsPerCta) - a0;
+    // each thread takes the CTA's atoms one after another from a shared
+    // counter and runs one event per loop iteration, so the lanes of a warp
+    // stay on the same code whatever the number of events of their atoms
+    long long k = -1;
+    uint32_t x = 0u, e = 0u;
+    uint64_t id = 0;
+    float vx = 0.0f, vy = 0.0f, vz = 0.0f;
+    int ev = 0;
+    for (;;) {
+        if (k < 0) {                                               // take the next live atom
+            const long long q = (long long)atomicAdd(&s_next, 1u);
+            if (q >= na) break;
+            const long long kk = a0 + q;
+            x = ((const uint32_t*)B.pos)[kk];
+            if (x == 0u) continue;
+            k = kk;
+            vx = B.vx[k]; vy = B.vy[k]; vz = B.vz[k];
+            id = B.id[k];
+            e = B.nev[k];
+            ev = 0;
+        }
+        bool done = false, live = true;
+        const float vm = sqrtf(vx * vx + vy * vy + vz * vz);
+        const float nu = d.tpf_nsig * mean_rel_speed(vm, c);
+        const uint4 f = draw(d.seed, id, e, kPurTpfFlight);
+        const float tau = nu > 0.0f ? -logf(u23(f.x)) / nu : INFINITY;
+        if (!(tau < INFINITY) && vx == 0.0f) {
+            done = true;                                           // no gas, no motion across the gap
+        } else {
             const float disp = vx * tau * d.tpf_scale;
             long long x1 = 0;
             int el = -1;
@@ -321,64 +381,88 @@ __global__ void __launch_bounds__(kTpThreads) k_tp_flight(Dev d, int kmax)
                 if (x1 <= 0) el = 0;
                 else if (x1 >= 4294967296LL) el = 1;
             }
-            if (el >= 0) {                                          // sticks at an electrode
-                tpf_segment(d, x, el == 0 ? 0ll : 4294967296LL, vx, tau);
+            if (el >= 0) {                                         // sticks at an electrode
+                tpf_segment(d, A, x, el == 0 ? 0ll : 4294967296LL, vx, tau);
                 const float E = vm * vm * (float)(0.5 * kMAL / kQE);
                 const float ct = fminf(vm > 0.0f ? fabsf(vx) / vm : 1.0f, 1.0f);
                 int be = (int)(E / 300.0f * (float)kNbSpE);
                 be = be < 0 ? 0 : (be > kNbSpE - 1 ? kNbSpE - 1 : be);
                 int ba = (int)(acosf(ct) * (float)(180.0 / kPI));
                 ba = ba < 0 ? 0 : (ba > kNbAng - 1 ? kNbAng - 1 : ba);
-                atomicAdd(&d.diag.sp_e[el][be], 1ull);
-                atomicAdd(&d.diag.sp_ang[el][ba], 1ull);
-                atomicAdd(&ctl->cnt[el == 0 ? kCntTpDepL : kCntTpDepR], 1ull);
+                atomicAdd(&A.spe[el * kNbSpE + be], 1u);
+                atomicAdd(&A.spa[el * kNbAng + ba], 1u);
+                if (el == 0) ++n_dep_l;
+                else ++n_dep_r;
                 live = false;
-                break;
-            }
-            tpf_segment(d, x, x1, vx, tau);
-            x = (uint32_t)x1;
-            // the collision partner, flux-weighted
-            float wx = 0.0f, wy = 0.0f, wz = 0.0f, gm = 0.0f;
-            for (int t = 0; t < kTpfTries; ++t) {
-                uint4 cw[2];
-                cw[0] = make_uint4((uint32_t)id, (uint32_t)(id >> 32), e, kPurTpfPartner + 2 * t);
-                cw[1] = make_uint4((uint32_t)id, (uint32_t)(id >> 32), e, kPurTpfPartner + 2 * t + 1);
-                philox_n<2>(cw, k0, k1);
-                const uint4 a = cw[0], b = cw[1];
-                if (u23(a.x) * (vm + mw) < vm) {
-                    const float2 n12 = box_muller(a.y, a.z), n34 = box_muller(a.w, b.x);
-                    wx = vg * n12.x; wy = vg * n12.y; wz = vg * n34.x;
-                } else {
-                    const float sp = c * sqrtf(-logf(u23(a.y) * u23(a.z)));
-                    const float3 dd = iso_dir(a.w, b.x);
-                    wx = sp * dd.x; wy = sp * dd.y; wz = sp * dd.z;
+                done = true;
+            } else {
+                tpf_segment(d, A, x, x1, vx, tau);
+                x = (uint32_t)x1;
+                // the collision partner, flux-weighted
+                float wx = 0.0f, wy = 0.0f, wz = 0.0f, gm = 0.0f;
+                for (int t = 0; t < kTpfTries; ++t) {
+                    uint4 cw[2];
+                    cw[0] = make_uint4((uint32_t)id, (uint32_t)(id >> 32), e, kPurTpfPartner + 2 * t);
+                    cw[1] = make_uint4((uint32_t)id, (uint32_t)(id >> 32), e, kPurTpfPartner + 2 * t + 1);
+                    philox_n<2>(cw, k0, k1);
+                    const uint4 a = cw[0], b = cw[1];
+                    if (u23(a.x) * (vm + mw) < vm) {
+                        const float2 n12 = box_muller(a.y, a.z), n34 = box_muller(a.w, b.x);
+                        wx = vg * n12.x; wy = vg * n12.y; wz = vg * n34.x;
+                    } else {
+                        const float sp = c * sqrtf(-logf(u23(a.y) * u23(a.z)));
+                        const float3 dd = iso_dir(a.w, b.x);
+                        wx = sp * dd.x; wy = sp * dd.y; wz = sp * dd.z;
+                    }
+                    const float gx = vx - wx, gy = vy - wy, gz = vz - wz;
+                    gm = sqrtf(gx * gx + gy * gy + gz * gz);
+                    const float wm = sqrtf(wx * wx + wy * wy + wz * wz);
+                    if (u23(b.y) * (vm + wm) < gm) break;
                 }
-                const float gx = vx - wx, gy = vy - wy, gz = vz - wz;
-                gm = sqrtf(gx * gx + gy * gy + gz * gz);
-                const float wm = sqrtf(wx * wx + wy * wy + wz * wz);
-                if (u23(b.y) * (vm + wm) < gm) break;
+                // hard sphere, isotropic in the centre of mass
+                const uint4 sc = draw(d.seed, id, e, kPurTpfScatter);
+                const float3 dir = iso_dir(sc.x, sc.y);
+                vx = mu_al * vx + mu_ar * wx + mu_ar * gm * dir.x;
+                vy = mu_al * vy + mu_ar * wy + mu_ar * gm * dir.y;
+                vz = mu_al * vz + mu_ar * wz + mu_ar * gm * dir.z;
+                ++e;
+                ++n_coll;
+                done = ++ev == kmax;
             }
-            // hard sphere, isotropic in the centre of mass
-            const uint4 sc = draw(d.seed, id, e, kPurTpfScatter);
-            const float3 dir = iso_dir(sc.x, sc.y);
-            vx = mu_al * vx + mu_ar * wx + mu_ar * gm * dir.x;
-            vy = mu_al * vy + mu_ar * wy + mu_ar * gm * dir.y;
-            vz = mu_al * vz + mu_ar * wz + mu_ar * gm * dir.z;
-            ++e;
-            ++ncoll;
         }
-        ((uint32_t*)B.pos)[k] = live ? x : 0u;
-        B.vx[k] = vx;
-        B.vy[k] = vy;
-        B.vz[k] = vz;
-        B.nev[k] = e;
-        alive += live ? 1u : 0u;
+        if (done) {                                                // the atom leaves this launch
+            ((uint32_t*)B.pos)[k] = live ? x : 0u;
+            B.vx[k] = vx;
+            B.vy[k] = vy;
+            B.vz[k] = vz;
+            B.nev[k] = e;
+            n_alive += live ? 1u : 0u;
+            k = -1;
+        }
     }
-    alive = __reduce_add_sync(0xffffffffu, alive);
-    ncoll = __reduce_add_sync(0xffffffffu, ncoll);
-    if ((threadIdx.x & 31) == 0) {
-        if (alive) atomicAdd(&ctl->tpf_alive, (unsigned long long)alive);
-        if (ncoll) atomicAdd(&ctl->cnt[kCntTpColl], (unsigned long long)ncoll);
+    const unsigned int cnt[4] = {n_alive, n_coll, n_dep_l, n_dep_r};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const unsigned int v = __reduce_add_sync(0xffffffffu, cnt[i]);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_cnt[i], v);
+    }
+    __syncthreads();
+    const Diag& g = d.diag;
+    for (int i = threadIdx.x; i < 4 * N1; i += blockDim.x) {
+        const int k = i / N1, m = i - k * N1;
+        long long* dst = k == 0 ? g.tpf_tpart : (k == 1 ? g.tpf_tdiff : (k == 2 ? g.tpf_dpart : g.tpf_ddiff));
+        const long long v = ((long long)A.hi[i] << 16) + (long long)A.lo[i];
+        if (v) atomicAdd((unsigned long long*)&dst[m], (unsigned long long)v);
+    }
+    for (int i = threadIdx.x; i < 2 * kNbSpE; i += blockDim.x)
+        if (A.spe[i]) atomicAdd(&g.sp_e[i / kNbSpE][i % kNbSpE], (unsigned long long)A.spe[i]);
+    for (int i = threadIdx.x; i < 2 * kNbAng; i += blockDim.x)
+        if (A.spa[i]) atomicAdd(&g.sp_ang[i / kNbAng][i % kNbAng], (unsigned long long)A.spa[i]);
+    if (threadIdx.x == 0) {
+        if (s_cnt[0]) atomicAdd(&ctl->tpf_alive, (unsigned long long)s_cnt[0]);
+        if (s_cnt[1]) atomicAdd(&ctl->cnt[kCntTpColl], (unsigned long long)s_cnt[1]);
+        if (s_cnt[2]) atomicAdd(&ctl->cnt[kCntTpDepL], (unsigned long long)s_cnt[2]);
+        if (s_cnt[3]) atomicAdd(&ctl->cnt[kCntTpDepR], (unsigned long long)s_cnt[3]);
     }
 }
 
@@ -414,9 +498,18 @@ __global__ void k_commit_count(Dev d, int s, long long add)
 
 size_t tp_smem(int ncell) { return (size_t)ncell * 12 + (size_t)(ncell + 1) * 8; }
 
-cudaError_t launch_tp_flight(const Dev& d, int kmax, int grid, cudaStream_t st)
+cudaError_t launch_tp_flight(const Dev& d, int kmax, long long n, cudaStream_t st)
 {
-    k_tp_flight<<<grid, kTpThreads, 0, st>>>(d, kmax);
+    if (n <= 0) return cudaSuccess;
+    if (kmax > kTpfMaxEvents) kmax = kTpfMaxEvents;
+    const size_t sm = tpf_smem(d.ncell);
+    if (sm > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute((const void*)k_tp_flight,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    const long long grid = (n + kTpfAtomsPerCta - 1) / kTpfAtomsPerCta;
+    k_tp_flight<<<(unsigned)grid, kTpThreads, sm, st>>>(d, kmax);
     return cudaGetLastError();
 }
 
