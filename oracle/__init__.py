@@ -104,6 +104,9 @@ def lib():
                 "orc_mean_rel_speed": (dbl, [dbl, dbl]),
                 "orc_tpf_partner": (C.c_int, [C.c_uint64, C.c_uint64, u32, dbl, vp, vp]),
                 "orc_tp_flight": (i64, [vp, i64]),
+                "orc_width_to_peak": (dbl, [vp, C.c_int, dbl]),
+                "orc_rms_angle": (dbl, [vp, C.c_int]),
+                "orc_hypotheses": (None, [vp, vp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -141,6 +144,18 @@ def tpf_partner(seed, atom_id, e, Tg, v):
     w = np.zeros(3)
     t = lib().orc_tpf_partner(int(seed), int(atom_id), int(e), float(Tg), _p(vv), _p(w))
     return w, int(t)
+
+
+def width_to_peak(h, emax):
+    """Full width at half maximum over the peak energy of a histogram on [0, emax]."""
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    return float(lib().orc_width_to_peak(_p(h), h.size, float(emax)))
+
+
+def rms_angle(h):
+    """Root mean square angle (deg) of a 1-degree angle histogram."""
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    return float(lib().orc_rms_angle(_p(h), h.size))
 
 
 def sigma_e(eps):
@@ -268,6 +283,12 @@ class Oracle:
 
     def reset_averages(self):
         lib().orc_reset_averages(self.h)
+
+    def hypotheses(self):
+        """dE/E_max left/right, rms impact angle left/right (deg), max n_Ar+/n_Ar, max n_Al/n_Ar."""
+        out = np.zeros(6)
+        lib().orc_hypotheses(self.h, _p(out))
+        return out
 
     def source_voltage(self, l):
         """Source voltage at step l (before any series capacitor)."""

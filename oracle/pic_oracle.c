@@ -992,6 +992,66 @@ int64_t orc_tp_flight(orc_state *S, int64_t max_events)
     return alive;
 }
 
+/* ======================= hypothesis checks =============================== */
+int64_t orc_diag(const orc_state *S, int kind, double *out, int64_t cap);
+/* Sec. "Hypotheses validation": (A) ions strike the electrodes nearly
+ * mono-energetically and along the normal -- the width-to-peak ratio
+ * dE/E_max of the ion energy distribution and the angular spread of the
+ * impacts; (B) the charged and sputtered species are traces in the gas --
+ * the largest n_Ar+/n_Ar and n_Al/n_Ar.  Readings: E_max is the centre of
+ * the fullest bin, dE the full width at half maximum around it (the run of
+ * bins from the peak whose counts stay at or above half the peak, edge to
+ * edge); the spread is the root mean square impact angle over the angle
+ * histogram (bin centres). */
+double orc_width_to_peak(const double *h, int nb, double emax)
+{
+    int pk = 0;
+    for (int b = 1; b < nb; b++) if (h[b] > h[pk]) pk = b;
+    if (!(h[pk] > 0.0)) return 0.0;
+    int lo = pk, hi = pk;
+    while (lo > 0 && h[lo - 1] >= 0.5 * h[pk]) lo--;
+    while (hi < nb - 1 && h[hi + 1] >= 0.5 * h[pk]) hi++;
+    double bw = emax / nb;
+    return (double)(hi - lo + 1) * bw / ((pk + 0.5) * bw);
+}
+
+double orc_rms_angle(const double *h, int nb)
+{
+    double s = 0.0, s2 = 0.0;
+    for (int b = 0; b < nb; b++) {
+        double th = b + 0.5;
+        s += h[b];
+        s2 += h[b] * th * th;
+    }
+    return s > 0.0 ? sqrt(s2 / s) : 0.0;
+}
+
+/* out: dE/E_max at x = 0 and x = L, rms impact angle (deg) at x = 0 and
+ * x = L, max n_Ar+/n_Ar, max n_Al/n_Ar (time averages of the run so far) */
+void orc_hypotheses(const orc_state *S, double out[6])
+{
+    int N = S->P.ncell;
+    double *buf = (double *)malloc(sizeof(double) * (NB_IEADF_E * NB_ANG + N + 1));
+    for (int el = 0; el < 2; el++) {
+        orc_diag(S, 6 + el, buf, NB_IEDF);
+        out[el] = orc_width_to_peak(buf, NB_IEDF, 2.0 * S->P.V0);
+        orc_diag(S, 8 + el, buf, NB_IEADF_E * NB_ANG);
+        double ang[NB_ANG];
+        for (int b = 0; b < NB_ANG; b++) ang[b] = 0.0;
+        for (int e = 0; e < NB_IEADF_E; e++)
+            for (int b = 0; b < NB_ANG; b++) ang[b] += buf[e * NB_ANG + b];
+        out[2 + el] = orc_rms_angle(ang, NB_ANG);
+    }
+    double mi = 0.0, ma = 0.0;
+    orc_diag(S, 2, buf, N + 1);
+    for (int m = 0; m <= N; m++) mi = fmax(mi, buf[m]);
+    orc_diag(S, 14, buf, N + 1);
+    for (int m = 0; m <= N; m++) ma = fmax(ma, buf[m]);
+    out[4] = mi / S->ngas;
+    out[5] = ma / S->ngas;
+    free(buf);
+}
+
 /* Mono-energetic source: n atoms launched from the left electrode with a
  * Thompson energy (cut off at Lambda E_ion) and a cosine angle; ids
  * tag | (atoms launched before + k). */

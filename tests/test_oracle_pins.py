@@ -709,3 +709,46 @@ def test_event_driven_flight_agrees_with_the_per_step_test():
     pval = stats.kstwobign.sf(D * math.sqrt(na * nb / (na + nb)))
     assert pval > 1e-3, (pval, na, nb)
     assert b.counters()["tp_dep_l"] + b.counters()["tp_dep_r"] == n
+
+
+# ------------------------------------------------------------------ hypothesis checks
+def test_width_to_peak_and_rms_angle_closed_forms():
+    """Sec. 'Hypotheses validation' measures: the full width at half maximum
+    of a sampled Gaussian peak is 2 sqrt(2 ln 2) sigma to a bin; a box of W
+    bins starting at bin b0 has width W bins over a peak at bin b0 (its
+    first fullest bin); the rms angle of a one-bin histogram is the bin
+    centre, and of a flat one over [0, 90) deg it is sqrt(sum (b + 1/2)^2 / 90)."""
+    nb, emax = 512, 600.0
+    bw = emax / nb
+    c = (np.arange(nb) + 0.5) * bw
+    for E0, sig in ((300.0, 12.0), (80.0, 3.0)):
+        h = np.exp(-0.5 * ((c - E0) / sig) ** 2) * 1e6
+        r = O.width_to_peak(h, emax)
+        pk = (np.argmax(h) + 0.5) * bw
+        assert abs(r * pk - 2 * math.sqrt(2 * math.log(2)) * sig) <= 1.01 * bw
+    h = np.zeros(nb)
+    h[100:117] = 5.0
+    assert O.width_to_peak(h, emax) == pytest.approx(17 / 100.5, rel=1e-15)
+    one = np.zeros(90)
+    one[3] = 7
+    assert O.rms_angle(one) == pytest.approx(3.5, rel=1e-15)
+    flat = np.ones(90)
+    assert O.rms_angle(flat) == pytest.approx(math.sqrt(sum((b + 0.5) ** 2 for b in range(90)) / 90), rel=1e-14)
+    assert O.width_to_peak(np.zeros(nb), emax) == 0.0 and O.rms_angle(np.zeros(90)) == 0.0
+
+
+def test_hypotheses_read_the_run_diagnostics():
+    """orc_hypotheses combines the run's diagnostics as defined: the ion
+    energy distributions' width-to-peak, the energy-summed IEADF's rms
+    angle, and the largest averaged n_i and TP density over the gas density."""
+    orc = _small_discharge(sputter=1, V0=300.0, tp_every=10)
+    orc.step(400)
+    h = orc.hypotheses()
+    for el, side in ((0, "l"), (1, "r")):
+        assert h[el] == pytest.approx(O.width_to_peak(orc.diag("iedf_" + side), 600.0), rel=1e-15)
+        ang = orc.diag("ieadf_" + side).reshape(128, 90).sum(0)
+        assert h[2 + el] == pytest.approx(O.rms_angle(ang), rel=1e-15)
+    ngas = orc.derived()["n_gas"]
+    assert h[4] == pytest.approx(orc.diag("n_i").max() / ngas, rel=1e-15)
+    assert h[5] == pytest.approx(orc.diag("tp_dens").max() / ngas, rel=1e-15)
+    assert 0.0 < h[4] < 1e-3
