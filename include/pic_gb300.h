@@ -151,6 +151,17 @@ enum pic_diag_kind {
 };
 int pic_diag(pic_ctx* ctx, int kind, double* host_out, int64_t cap, int64_t* n_written);
 
+/* The checks of the paper's two modelling assumptions (Sec. "Hypotheses
+ * validation") from the time averages so far, into host_out[6]:
+ *   [0], [1]  dE/E_max of the Ar+ energy distribution at x = 0 and x = L:
+ *             full width at half maximum around the fullest bin over that
+ *             bin's centre energy (mono-energetic impact, assumption A)
+ *   [2], [3]  rms impact angle at x = 0 and x = L, degrees (normal impact)
+ *   [4]       max over the nodes of n_Ar+ / n_Ar (assumption B)
+ *   [5]       max over the nodes of n_Al / n_Ar (grid-based TP density)
+ * A histogram without counts gives 0. */
+int pic_hypotheses(pic_ctx* ctx, double* host_out);
+
 /* Restart all time averages and histograms (Sec. "Kinetic Particle
  * Simulation": averaging once a (periodic) steady state is reached). */
 int pic_reset_averages(pic_ctx* ctx);

@@ -109,6 +109,7 @@ def lib():
             "tp_launch": [vp, C.POINTER(TpSource)],
             "tp_step": [vp, i64, pi64],
             "tp_flight": [vp, i64, pi64],
+            "pic_hypotheses": [vp, vp],
             "pic_compact": [vp, C.c_int],
             "pic_timing": [vp, C.c_int],
             "pic_kernel_time": [vp, C.c_int, C.POINTER(dbl), pi64],
@@ -228,6 +229,14 @@ class Discharge:
 
     def reset_averages(self):
         _check(lib().pic_reset_averages(self.h))
+
+    def hypotheses(self) -> dict:
+        """The paper's checks of its modelling assumptions (``pic_hypotheses``)."""
+        out = np.zeros(6)
+        _check(lib().pic_hypotheses(self.h, _ptr(out)))
+        keys = ["dE_over_E_l", "dE_over_E_r", "rms_angle_l_deg", "rms_angle_r_deg", "n_ion_over_n_gas",
+                "n_al_over_n_gas"]
+        return dict(zip(keys, out.tolist()))
 
     def counters(self) -> dict:
         out = np.zeros(64, dtype=np.int64)

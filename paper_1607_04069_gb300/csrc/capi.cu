@@ -810,6 +810,51 @@ int pic_diag(pic_ctx* c, int kind, double* out, int64_t cap, int64_t* n_written)
     return PIC_OK;
 }
 
+int pic_hypotheses(pic_ctx* c, double* out)
+{
+    if (!c || !out) return fail(PIC_ERR_INVALID_ARG, "NULL argument");
+    const int N1 = c->p.n_cells + 1;
+    std::vector<double> h(kNbIeadfE * kNbAng > N1 ? kNbIeadfE * kNbAng : N1);
+    int64_t n = 0;
+    for (int el = 0; el < 2; ++el) {
+        // width-to-peak of the ion energy distribution: the fullest bin (the
+        // first of equals) and the run of bins around it at or above half of it
+        int rc = pic_diag(c, PIC_DIAG_IEDF_L + el, h.data(), (int64_t)h.size(), &n);
+        if (rc) return rc;
+        int pk = 0;
+        for (int b = 1; b < kNbIedf; ++b)
+            if (h[b] > h[pk]) pk = b;
+        double r = 0.0;
+        if (h[pk] > 0.0) {
+            int lo = pk, hi = pk;
+            while (lo > 0 && h[lo - 1] >= 0.5 * h[pk]) --lo;
+            while (hi < kNbIedf - 1 && h[hi + 1] >= 0.5 * h[pk]) ++hi;
+            r = (double)(hi - lo + 1) / (pk + 0.5);
+        }
+        out[el] = r;
+        // rms impact angle over the energy-summed angle histogram (bin centres)
+        rc = pic_diag(c, PIC_DIAG_IEADF_L + el, h.data(), (int64_t)h.size(), &n);
+        if (rc) return rc;
+        double s0 = 0.0, s2 = 0.0;
+        for (int b = 0; b < kNbAng; ++b) {
+            double col = 0.0;
+            for (int e = 0; e < kNbIeadfE; ++e) col += h[(size_t)e * kNbAng + b];
+            s0 += col;
+            s2 += col * (b + 0.5) * (b + 0.5);
+        }
+        out[2 + el] = s0 > 0.0 ? std::sqrt(s2 / s0) : 0.0;
+    }
+    const double ngas = c->derived[0];
+    for (int k = 0; k < 2; ++k) {
+        int rc = pic_diag(c, k == 0 ? PIC_DIAG_NI : PIC_DIAG_TP_DENS, h.data(), (int64_t)h.size(), &n);
+        if (rc) return rc;
+        double mx = 0.0;
+        for (int m = 0; m < N1; ++m) mx = std::max(mx, h[m]);
+        out[4 + k] = ngas > 0.0 ? mx / ngas : 0.0;
+    }
+    return PIC_OK;
+}
+
 int pic_reset_averages(pic_ctx* c)
 {
     if (!c) return fail(PIC_ERR_INVALID_ARG, "ctx is NULL");

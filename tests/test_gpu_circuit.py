@@ -110,3 +110,26 @@ def test_infinite_capacitance_is_the_ideal_source():
     assert np.array_equal(a.get_field()["E"], b.get_field()["E"])
     a.close()
     b.close()
+
+
+def test_hypothesis_checks_follow_their_definitions():
+    """pic_hypotheses applies to the GPU's own diagnostics the measures the
+    oracle pins (width-to-peak, rms angle, density fractions), and after a
+    sputtering run the paper's assumptions hold in this discharge: ions are
+    a trace (n_Ar+/n_Ar < 1e-4)."""
+    import oracle as O
+    cfg = W.ccp_sputter(n_per_species=100_000, n_cells=256)
+    cfg.update(sort_every_e=400, sort_every_i=400)
+    d = gpu_discharge(cfg)
+    d.step(3000)
+    h = d.hypotheses()
+    V0 = cfg["rf_volt_v"]
+    for el, side in ((0, "l"), (1, "r")):
+        assert h[f"dE_over_E_{side}"] == pytest.approx(O.width_to_peak(d.diag("iedf_" + side), 2 * V0), rel=1e-12)
+        ang = d.diag("ieadf_" + side).reshape(128, 90).sum(0)
+        assert h[f"rms_angle_{side}_deg"] == pytest.approx(O.rms_angle(ang), rel=1e-12)
+    ngas = d.derived()["n_gas"]
+    assert h["n_ion_over_n_gas"] == pytest.approx(d.diag("n_i").max() / ngas, rel=1e-12)
+    assert h["n_al_over_n_gas"] == pytest.approx(d.diag("tp_dens").max() / ngas, rel=1e-12)
+    assert 0.0 < h["n_ion_over_n_gas"] < 1e-4
+    d.close()
