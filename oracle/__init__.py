@@ -60,7 +60,9 @@ class Params(C.Structure):
                 ("te0", C.c_double), ("ti0", C.c_double), ("tp_dt", C.c_double),
                 ("sigma_tp", C.c_double), ("seed", C.c_uint64), ("ncell", C.c_int32),
                 ("sputter", C.c_int32), ("tp_every", C.c_int32), ("diag_every", C.c_int32),
-                ("waveform", C.c_int32), ("circuit", C.c_int32), ("phase", C.c_double), ("cb", C.c_double)]
+                ("waveform", C.c_int32), ("circuit", C.c_int32), ("phase", C.c_double), ("cb", C.c_double),
+                ("dref", C.c_double), ("omega", C.c_double), ("tref", C.c_double), ("tp_model", C.c_int32),
+                ("pad", C.c_int32)]
 
 
 def _p(a):
@@ -105,6 +107,9 @@ def lib():
                 "orc_tpf_partner": (C.c_int, [C.c_uint64, C.c_uint64, u32, dbl, vp, vp]),
                 "orc_tp_flight": (i64, [vp, i64]),
                 "orc_width_to_peak": (dbl, [vp, C.c_int, dbl]),
+                "orc_tp_sigma": (dbl, [vp, dbl]),
+                "orc_vhs_dref": (dbl, [dbl, dbl, dbl, dbl]),
+                "orc_tp_scatter": (None, [C.c_int, vp, u32, u32, vp]),
                 "orc_rms_angle": (dbl, [vp, C.c_int]),
                 "orc_hypotheses": (None, [vp, vp]),
             }
@@ -144,6 +149,19 @@ def tpf_partner(seed, atom_id, e, Tg, v):
     w = np.zeros(3)
     t = lib().orc_tpf_partner(int(seed), int(atom_id), int(e), float(Tg), _p(vv), _p(w))
     return w, int(t)
+
+
+def vhs_dref(mu_ref, t_ref, omega, mass):
+    """VHS reference diameter from the viscosity at T_ref (Eq. referencediameter)."""
+    return float(lib().orc_vhs_dref(float(mu_ref), float(t_ref), float(omega), float(mass)))
+
+
+def tp_scatter(model, g, r1, r2):
+    """Unit direction of the post-collision relative velocity (0/1 isotropic, 2 M1)."""
+    gg = np.ascontiguousarray(g, dtype=np.float64)
+    out = np.zeros(3)
+    lib().orc_tp_scatter(int(model), _p(gg), int(r1) & 0xffffffff, int(r2) & 0xffffffff, _p(out))
+    return out
 
 
 def width_to_peak(h, emax):
@@ -283,6 +301,10 @@ class Oracle:
 
     def reset_averages(self):
         lib().orc_reset_averages(self.h)
+
+    def tp_sigma(self, g):
+        """TP collision cross section at relative speed g (m^2)."""
+        return float(lib().orc_tp_sigma(self.h, float(g)))
 
     def hypotheses(self):
         """dE/E_max left/right, rms impact angle left/right (deg), max n_Ar+/n_Ar, max n_Al/n_Ar."""

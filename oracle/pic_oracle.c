@@ -71,8 +71,11 @@ enum {
     PUR_TP_LAUNCH = 66,  /* mono-energetic source launch                */
     PUR_TPF_FLIGHT = 70, /* event-driven TP: free-flight time of event e */
     PUR_TPF_SCATTER = 71,/* event-driven TP: scattering direction       */
-    PUR_TPF_PARTNER = 72 /* +2t, +2t+1: partner proposal t of event e    */
+    PUR_TPF_PARTNER = 72,/* +2t, +2t+1: partner proposal t of event e    */
+    PUR_TPF_CAND = 200,  /* VHS/M1 flight: candidate partner (200, 201)  */
+    PUR_TPF_GAMMA = 202  /* +t: gamma variate attempt t of a candidate   */
 };
+#define TPF_GAMMA_TRIES 32
 #define TPF_TRIES 64     /* partner proposals per collision (each accepted w.p. >= 1/2) */
 
 /* species and id tags (top two bits of the 64-bit id) */
@@ -111,6 +114,10 @@ typedef struct {
     int32_t circuit;              /* 0: the source sets phi[0]; 1: series capacitor  */
     double phase;                 /* waveform 1: phase of the fundamental, rad      */
     double cb;                    /* circuit 1: capacitance per electrode area, F/m^2 */
+    double dref, omega, tref;     /* TP models 1, 2: VHS reference diameter (m), viscosity index,
+                                     reference temperature (K) of the Al-Ar pair   */
+    int32_t tp_model;             /* TP collisions: 0 hard sphere (sigma_tp), 1 VHS, 2 M1 */
+    int32_t pad;
 } orc_params;
 
 typedef struct {
@@ -775,6 +782,55 @@ void orc_step(orc_state *S, int64_t nsteps)
 }
 
 /* ======================= test particles ================================== */
+/* ======================= TP collision models ============================= */
+/* Sec. "Binary Interactions": hard spheres (sigma_tp), the variable hard
+ * sphere model, sigma_T(g) = pi b_max(g)^2 with b_max from Eq.
+ * maximumimpactparameter for the Al-Ar pair (reduced mass m_r, reference
+ * diameter and viscosity index of the pair), and the M1 model, which uses
+ * the VHS law with d_ref,M1 = sqrt(4/3) d_ref,VHS.  Both VHS forms give
+ * sigma(g) g = K g^alpha with alpha = 2 - 2 omega. */
+static double tp_mr(void) { return O_MAL * O_MAR / (O_MAL + O_MAR); }
+
+double orc_tp_sigma(const orc_state *S, double g)
+{
+    const orc_params *P = &S->P;
+    if (P->tp_model == 0) return P->sigma_tp;
+    double d = P->tp_model == 2 ? sqrt(4.0 / 3.0) * P->dref : P->dref;
+    double b2 = d * d * pow(2.0 * O_KB * P->tref / (tp_mr() * g * g), P->omega - 0.5) / tgamma(2.5 - P->omega);
+    return O_PI * b2;
+}
+
+/* reference diameter from the viscosity mu_ref at T_ref (Eq. referencediameter) */
+double orc_vhs_dref(double mu_ref, double t_ref, double omega, double mass)
+{
+    return sqrt(15.0 * sqrt(mass * O_KB * t_ref / O_PI) / (8.0 * (2.5 - omega) * (3.5 - omega) * mu_ref));
+}
+
+/* Direction of the post-collision relative velocity for a scattering draw
+ * (r1, r2): hard spheres and VHS scatter isotropically in the centre-of-mass
+ * frame; M1 turns g by chi = pi (1 - b / b_max) with b = b_max sqrt(r1),
+ * at the azimuth eps = 2 pi r2 about g (the frame of g: e1 along g x x^, or
+ * g x y^ when |g_x| >= 0.9 |g|, e2 = g^ x e1). */
+void orc_tp_scatter(int model, const double g[3], uint32_t r1, uint32_t r2, double out[3])
+{
+    double gm = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    if (model != 2 || gm == 0.0) {
+        iso_dir(r1, r2, out);
+        return;
+    }
+    double u[3] = {g[0] / gm, g[1] / gm, g[2] / gm};
+    double a[3] = {0.0, 0.0, 0.0};
+    if (fabs(u[0]) < 0.9) a[0] = 1.0; else a[1] = 1.0;
+    double e1[3] = {u[1] * a[2] - u[2] * a[1], u[2] * a[0] - u[0] * a[2], u[0] * a[1] - u[1] * a[0]};
+    double n1 = sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+    for (int i = 0; i < 3; i++) e1[i] /= n1;
+    double e2[3] = {u[1] * e1[2] - u[2] * e1[1], u[2] * e1[0] - u[0] * e1[2], u[0] * e1[1] - u[1] * e1[0]};
+    double chi = O_PI * (1.0 - sqrt(u23(r1)));
+    double eps = 2.0 * O_PI * u23(r2);
+    double cc = cos(chi), sc = sin(chi), ce = cos(eps), se = sin(eps);
+    for (int i = 0; i < 3; i++) out[i] = cc * u[i] + sc * (ce * e1[i] + se * e2[i]);
+}
+
 /* One TP step (Sec. "Test Particle Method"): free flight x += v_x dt, sticking
  * at either wall with the absorbed flux recorded, and a binary hard-sphere
  * collision with a thermal Ar partner with probability 1 - exp(-n sigma g dt)
@@ -814,11 +870,12 @@ void orc_tp_step(orc_state *S, int64_t nsteps, double dt_tp)
             double w[3] = {vg * n1, vg * n2, vg * n3};
             double g[3] = {p->vx[k] - w[0], p->vy[k] - w[1], p->vz[k] - w[2]};
             double gm = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
-            double P = 1.0 - exp(-S->ngas * S->P.sigma_tp * gm * dt_tp);
+            double sig = gm > 0.0 ? orc_tp_sigma(S, gm) : 0.0;
+            double P = 1.0 - exp(-S->ngas * sig * gm * dt_tp);
             draw(S->P.seed, p->id[k], s, PUR_TP_COLL, cc);
             if (u23(cc[0]) < P) {
                 double d[3];
-                iso_dir(cc[1], cc[2], d);
+                orc_tp_scatter(S->P.tp_model, g, cc[1], cc[2], d);
                 double vc[3] = {(O_MAL * p->vx[k] + O_MAR * w[0]) / mu,
                                 (O_MAL * p->vy[k] + O_MAR * w[1]) / mu,
                                 (O_MAL * p->vz[k] + O_MAR * w[2]) / mu};
@@ -856,7 +913,10 @@ void orc_tp_step(orc_state *S, int64_t nsteps, double dt_tp)
  * gas the rate is nu(v) = n sigma <|v - w|>, the relative speed averaged over
  * the gas (closed form below), and at a collision the partner w has the
  * density |v - w| f(w) / <|v - w|>: the collision law of the per-step test
- * of orc_tp_step in the limit dt -> 0.  Random words of event e of an atom:
+ * of orc_tp_step in the limit dt -> 0.  With the VHS and M1 models
+ * (sigma(g) g = K g^alpha) the flight runs at a majorant rate and each
+ * candidate is a real collision or a null event (thinning); null events count
+ * as events.  Random words of event e of an atom:
  * Philox(id, e, TPF_FLIGHT), (id, e, TPF_PARTNER + 2t [+1]) for proposal t,
  * (id, e, TPF_SCATTER); e is kept per atom (orc_sp.nev).  Residence time and
  * signed path length are added per cell for each straight segment. */
@@ -907,6 +967,25 @@ int orc_tpf_partner(uint64_t seed, uint64_t id, uint32_t e, double Tg, const dou
     return TPF_TRIES + 1;
 }
 
+/* Gamma variate of shape k >= 1 (Marsaglia and Tsang, ACM TOMS 26, 2000):
+ * d = k - 1/3, x normal, v = (1 + x/sqrt(9d))^3, accepted when
+ * ln U < x^2/2 + d - d v + d ln v; attempt t draws (id, e, TPF_GAMMA + t). */
+static double gamma_mt(double k, uint64_t seed, uint64_t id, uint32_t e)
+{
+    double d = k - 1.0 / 3.0, cc = 1.0 / sqrt(9.0 * d);
+    for (int t = 0; t < TPF_GAMMA_TRIES; t++) {
+        uint32_t r[4];
+        draw(seed, id, e, PUR_TPF_GAMMA + t, r);
+        double x, unused;
+        box_muller(r[0], r[1], &x, &unused);
+        double v = 1.0 + cc * x;
+        if (v <= 0.0) continue;
+        v = v * v * v;
+        if (log(u23(r[2])) < 0.5 * x * x + d - d * v + d * log(v)) return d * v;
+    }
+    return d;
+}
+
 /* residence time and signed path of the straight segment xi0 -> xi1 (cell
  * units) flown at v_x over tau seconds, cell by cell */
 static void tpf_segment(orc_state *S, double xi0, double xi1, double vx, double tau)
@@ -949,7 +1028,17 @@ int64_t orc_tp_flight(orc_state *S, int64_t max_events)
             uint32_t e = p->nev[k];
             double v[3] = {p->vx[k], p->vy[k], p->vz[k]};
             double vm = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-            double nu = S->ngas * S->P.sigma_tp * orc_mean_rel_speed(vm, c);
+            double nu, alpha = 1.0, va = 0.0, ma = 0.0;
+            if (S->P.tp_model == 0) {
+                nu = S->ngas * S->P.sigma_tp * orc_mean_rel_speed(vm, c);
+            } else {
+                /* VHS / M1: sigma(g) g = K g^alpha; candidates at the majorant rate
+                 * n K (|v|^alpha + <|w|^alpha>) >= n K <|v - w|^alpha> (alpha <= 1) */
+                alpha = 2.0 - 2.0 * S->P.omega;
+                va = pow(vm, alpha);
+                ma = pow(c, alpha) * tgamma(0.5 * (3.0 + alpha)) / tgamma(1.5);
+                nu = S->ngas * orc_tp_sigma(S, 1.0) * (va + ma);
+            }
             uint32_t f[4];
             draw(S->P.seed, p->id[k], e, PUR_TPF_FLIGHT, f);
             double tau = nu > 0.0 ? -log(u23(f[0])) / nu : INFINITY;
@@ -975,13 +1064,41 @@ int64_t orc_tp_flight(orc_state *S, int64_t max_events)
             tpf_segment(S, xi0, xi1, v[0], tau);
             p->xi[k] = xi1;
             double w[3];
-            orc_tpf_partner(S->P.seed, p->id[k], e, S->P.Tg, v, w);
+            if (S->P.tp_model == 0) {
+                orc_tpf_partner(S->P.seed, p->id[k], e, S->P.Tg, v, w);
+            } else {
+                /* candidate partner from (|v|^alpha + |w|^alpha) f(w): a Maxwellian with
+                 * probability |v|^alpha / (|v|^alpha + <|w|^alpha>), else |w|^2/c^2 ~
+                 * Gamma((3 + alpha)/2) with an isotropic direction; a real collision
+                 * with probability |v - w|^alpha / (|v|^alpha + |w|^alpha), else none */
+                uint32_t a[4], b[4];
+                draw(S->P.seed, p->id[k], e, PUR_TPF_CAND, a);
+                draw(S->P.seed, p->id[k], e, PUR_TPF_CAND + 1, b);
+                if (u23(a[0]) * (va + ma) < va) {
+                    double vg = c / sqrt(2.0), n1, n2, n3, n4;
+                    box_muller(a[1], a[2], &n1, &n2);
+                    box_muller(a[3], b[0], &n3, &n4);
+                    w[0] = vg * n1; w[1] = vg * n2; w[2] = vg * n3;
+                } else {
+                    double sp = c * sqrt(gamma_mt(0.5 * (3.0 + alpha), S->P.seed, p->id[k], e));
+                    double dd[3];
+                    iso_dir(a[3], b[0], dd);
+                    w[0] = sp * dd[0]; w[1] = sp * dd[1]; w[2] = sp * dd[2];
+                }
+                double gg[3] = {v[0] - w[0], v[1] - w[1], v[2] - w[2]};
+                double gmm = sqrt(gg[0] * gg[0] + gg[1] * gg[1] + gg[2] * gg[2]);
+                double wm = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+                if (!(u23(b[1]) * (va + pow(wm, alpha)) < pow(gmm, alpha))) {
+                    p->nev[k] = e + 1u;                   /* a null event: the flight goes on */
+                    continue;
+                }
+            }
             double g[3] = {v[0] - w[0], v[1] - w[1], v[2] - w[2]};
             double gm = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
             uint32_t sc[4];
             draw(S->P.seed, p->id[k], e, PUR_TPF_SCATTER, sc);
             double d[3];
-            iso_dir(sc[0], sc[1], d);
+            orc_tp_scatter(S->P.tp_model, g, sc[0], sc[1], d);
             for (int i = 0; i < 3; i++) v[i] = (O_MAL * v[i] + O_MAR * w[i]) / mu + (O_MAR / mu) * gm * d[i];
             p->vx[k] = v[0]; p->vy[k] = v[1]; p->vz[k] = v[2];
             p->nev[k] = e + 1u;

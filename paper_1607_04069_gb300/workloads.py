@@ -94,7 +94,9 @@ def oracle_params(cfg: dict) -> dict:
                 ti0=cfg["ti0_ev"], tp_dt=cfg["tp_dt"], sigma_tp=cfg["sigma_tp"], seed=cfg["seed"],
                 ncell=cfg["n_cells"], sputter=cfg["sputter_enable"], tp_every=cfg["tp_every"],
                 diag_every=cfg["diag_every"], waveform=cfg.get("waveform", 0), circuit=cfg.get("circuit", 0),
-                phase=cfg.get("rf_phase", 0.0), cb=cfg.get("c_block", math.inf))
+                phase=cfg.get("rf_phase", 0.0), cb=cfg.get("c_block", math.inf),
+                dref=cfg.get("tp_dref", 0.0), omega=cfg.get("tp_omega", 0.5), tref=cfg.get("tp_tref", 273.0),
+                tp_model=cfg.get("tp_model", 0))
 
 
 # ------------------------------------------------------------- particle sets

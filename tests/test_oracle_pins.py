@@ -752,3 +752,91 @@ def test_hypotheses_read_the_run_diagnostics():
     assert h[4] == pytest.approx(orc.diag("n_i").max() / ngas, rel=1e-15)
     assert h[5] == pytest.approx(orc.diag("tp_dens").max() / ngas, rel=1e-15)
     assert 0.0 < h[4] < 1e-3
+
+
+# ------------------------------------------------------------------ VHS / M1 test-particle collisions
+def test_vhs_reference_diameter_of_argon():
+    """Eq. referencediameter turns argon's tabulated viscosity into its
+    tabulated VHS diameter (tests/golden/vhs_argon_bird1994.txt)."""
+    rows = [l.split() for l in open(os.path.join(HERE, "golden", "vhs_argon_bird1994.txt"))
+            if l.strip() and not l.startswith("#")]
+    mu, T, om, m, d, tol = map(float, rows[0])
+    assert abs(O.vhs_dref(mu, T, om, m * AMU) / d - 1.0) < tol
+
+
+def test_vhs_cross_section_law():
+    """Eq. maximumimpactparameter: sigma = pi b_max^2 falls as g^(1 - 2 omega);
+    omega = 1/2 is the hard sphere of diameter d_ref (Gamma(2) = 1); M1 takes
+    d_ref sqrt(4/3), so 4/3 of the VHS cross section."""
+    d = 4.17e-10
+    vhs = O.Oracle(prm(tp_model=1, dref=d, omega=0.81, tref=273.0), 1, 1, 1)
+    m1 = O.Oracle(prm(tp_model=2, dref=d, omega=0.81, tref=273.0), 1, 1, 1)
+    hs = O.Oracle(prm(tp_model=1, dref=d, omega=0.5, tref=273.0), 1, 1, 1)
+    for g in (50.0, 700.0, 5000.0):
+        assert vhs.tp_sigma(2 * g) / vhs.tp_sigma(g) == pytest.approx(2 ** (1 - 2 * 0.81), rel=1e-12)
+        assert m1.tp_sigma(g) == pytest.approx(4.0 / 3.0 * vhs.tp_sigma(g), rel=1e-12)
+        assert hs.tp_sigma(g) == pytest.approx(math.pi * d * d, rel=1e-14)
+    mr = MAL * MAR / (MAL + MAR)
+    g = 1234.0
+    bmax2 = d * d * (2 * KB * 273.0 / (mr * g * g)) ** (0.81 - 0.5) / special.gamma(2.5 - 0.81)
+    assert vhs.tp_sigma(g) == pytest.approx(math.pi * bmax2, rel=1e-12)
+
+
+def test_scattering_angle_laws():
+    """Sec. 'Binary Interactions': VHS scatters isotropically (cos chi
+    uniform on [-1, 1]); M1 deflects by chi = pi (1 - b/b_max) with b =
+    b_max sqrt(R), so P(chi <= x) = 1 - (1 - x/pi)^2; both keep |g|."""
+    rng = np.random.default_rng(8)
+    g = np.array([-0.3, 0.8, 0.52])
+    gh = g / np.linalg.norm(g)
+    n = 20000
+    words = rng.integers(0, 2**32, size=(n, 2), dtype=np.uint64)
+    for model, cdf in ((1, lambda x: (1 - np.cos(x)) / 2), (2, lambda x: 1 - (1 - x / np.pi) ** 2)):
+        chi = np.empty(n)
+        for i in range(n):
+            dvec = O.tp_scatter(model, g, int(words[i, 0]), int(words[i, 1]))
+            assert abs(np.linalg.norm(dvec) - 1.0) < 1e-12
+            chi[i] = math.acos(max(-1.0, min(1.0, float(dvec @ gh))))
+        assert stats.kstest(chi, cdf).pvalue > 1e-3, model
+
+
+def test_vhs_uncollided_fraction_in_cold_gas():
+    """A mono-energetic beam into a cold gas under the VHS law: the flight
+    with candidates at a majorant rate and null events keeps the atoms that
+    never collide at probability exp(-n sigma(v0) L); they reach the far
+    electrode along the normal (the first angle bin; an isotropic deflection
+    lands there with probability 8e-5)."""
+    n, N, L, ngas, T = 100_000, 128, 0.03, 1.2e20, 1e-3
+    v0 = 2400.0
+    orc = O.Oracle(prm(L=L, ncell=N, p=ngas * KB * T, Tg=T, tp_model=1, dref=4.17e-10, omega=0.81, tref=273.0),
+                   1, 1, n)
+    v = np.zeros((3, n))
+    v[0] = v0
+    load(orc, 2, np.full(n, 1e-6), v)
+    assert orc.tp_flight(100_000) == 0
+    got = orc.diag("sputter_ang_r")[0]            # still along the normal: never scattered
+    P = math.exp(-ngas * orc.tp_sigma(v0) * L)
+    assert abs(got - n * P) < 4.5 * math.sqrt(n * P * (1 - P))
+
+
+@pytest.mark.parametrize("model", [1, 2])
+def test_vhs_and_m1_flights_agree_with_the_per_step_test(model):
+    """Under the VHS and M1 laws the event-driven flight (majorant rate, null
+    events, gamma-distributed partner speeds) and the per-step test give the
+    same energetic arrivals at the far electrode from a 300 eV-ion source."""
+    n, N, L = 3000, 64, 0.02
+    P = prm(L=L, ncell=N, p=0.5, Tg=300.0, seed=23, tp_model=model, dref=4.17e-10, omega=0.81, tref=273.0)
+    a = O.Oracle(P, 1, 1, n)
+    b = O.Oracle(P, 1, 1, n)
+    a.tp_launch(n, 300.0)
+    b.tp_launch(n, 300.0)
+    a.tp_step(6000, 5e-9)
+    b.tp_flight(100_000)
+    edges = np.arange(601) * 0.5
+    ha, hb = a.diag("sputter_e_r"), b.diag("sputter_e_r")
+    sel = edges[:-1] >= 2.0
+    na, nb = ha[sel].sum(), hb[sel].sum()
+    assert na > 300 and abs(na - nb) < 4.5 * math.sqrt(na + nb)
+    D = np.abs(np.cumsum(ha[sel]) / na - np.cumsum(hb[sel]) / nb).max()
+    assert stats.kstwobign.sf(D * math.sqrt(na * nb / (na + nb))) > 1e-3
+    assert b.counters()["tp_dep_l"] + b.counters()["tp_dep_r"] == n
