@@ -83,7 +83,23 @@ typedef struct pic_params {
     double rf_phase;        /* waveform 1: phase of the fundamental, rad                    */
     double c_block;         /* circuit 1: capacitance per unit electrode area, F/m^2, >= 0
                                (0: floating electrode; INFINITY: same as circuit 0)        */
+    int32_t tp_model;       /* Al-Ar collisions of the test particles (Sec. "Binary
+                               Interactions"): 0 hard spheres of cross section sigma_tp;
+                               1 VHS, sigma = pi b_max^2 with b_max(g) of Eq.
+                               maximumimpactparameter, isotropic scattering; 2 M1, the same
+                               law with d_ref sqrt(4/3) and chi = pi (1 - b / b_max)     */
+    int32_t tp_pad;
+    double tp_dref;         /* models 1, 2: VHS reference diameter of the Al-Ar pair, m (see
+                               pic_vhs_dref)                                               */
+    double tp_omega;        /* models 1, 2: viscosity index, 0.5 .. 1                      */
+    double tp_tref;         /* models 1, 2: reference temperature, K                       */
 } pic_params;
+
+/* VHS reference diameter of a species from its viscosity mu_ref (Pa s) at
+ * t_ref (K), viscosity index omega and molecular mass (kg), Eq.
+ * referencediameter; for an unlike pair the paper averages the diameters and
+ * the indices of the two species. */
+double pic_vhs_dref(double mu_ref, double t_ref, double omega, double mass_kg);
 
 /* Mono-energetic Ar+ source for tp_launch: n atoms leave the left electrode
  * with Sigmund-Thompson energies cut off at Lambda*e_ion_ev and cosine

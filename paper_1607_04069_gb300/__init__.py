@@ -48,7 +48,9 @@ class PicParams(C.Structure):
                 ("tp_every", C.c_int32), ("diag_every", C.c_int32), ("sort_every_e", C.c_int32),
                 ("sort_every_i", C.c_int32), ("sort_every_tp", C.c_int32),
                 ("ctas_per_sm", C.c_int32), ("strict", C.c_int32), ("waveform", C.c_int32),
-                ("circuit", C.c_int32), ("rf_phase", C.c_double), ("c_block", C.c_double)]
+                ("circuit", C.c_int32), ("rf_phase", C.c_double), ("c_block", C.c_double),
+                ("tp_model", C.c_int32), ("tp_pad", C.c_int32), ("tp_dref", C.c_double),
+                ("tp_omega", C.c_double), ("tp_tref", C.c_double)]
 
 
 class ServerOpts(C.Structure):
@@ -150,6 +152,8 @@ def lib():
             getattr(L, name).restype = None
         L.pic_strerror.argtypes = [C.c_int]
         L.pic_strerror.restype = C.c_char_p
+        L.pic_vhs_dref.argtypes = [dbl, dbl, dbl, dbl]
+        L.pic_vhs_dref.restype = dbl
         L.pic_last_error.argtypes = []
         L.pic_last_error.restype = C.c_char_p
         _lib = L
@@ -390,6 +394,11 @@ class Batch:
             self.h = None
 
     __del__ = close
+
+
+def vhs_dref(mu_ref, t_ref, omega, mass_kg) -> float:
+    """VHS reference diameter from a viscosity (``pic_vhs_dref``)."""
+    return float(lib().pic_vhs_dref(float(mu_ref), float(t_ref), float(omega), float(mass_kg)))
 
 
 def state_bytes(params) -> int:

@@ -172,6 +172,9 @@ int validate(const pic_params* p)
         p->sort_every_tp < 0 || p->ctas_per_sm < 0)
         return fail(PIC_ERR_INVALID_ARG, "negative period");
     if (!(p->tp_dt >= 0) || !(p->sigma_tp >= 0)) return fail(PIC_ERR_INVALID_ARG, "tp_dt, sigma_tp >= 0");
+    if (p->tp_model < 0 || p->tp_model > 2 ||
+        (p->tp_model > 0 && !(p->tp_dref > 0 && p->tp_omega >= 0.5 && p->tp_omega <= 1.0 && p->tp_tref > 0)))
+        return fail(PIC_ERR_INVALID_ARG, "tp_model 0..2; VHS/M1 need tp_dref > 0, 0.5 <= tp_omega <= 1, tp_tref > 0");
     if ((p->waveform != 0 && p->waveform != 1) || (p->circuit != 0 && p->circuit != 1))
         return fail(PIC_ERR_INVALID_ARG, "waveform and circuit must be 0 or 1");
     if (!std::isfinite(p->rf_phase) || (p->circuit == 1 && !(p->c_block >= 0)))
@@ -250,6 +253,23 @@ void derive(pic_ctx* c)
     d.tpf_nsig = (float)(ngas * p.sigma_tp);
     d.tpf_scale = (float)(4294967296.0 / p.gap_m);
     d.tpf_kt = (float)(256.0 * p.gap_m);
+    d.tp_model = p.tp_model;
+    double nK = 0.0;                                    // n K of the VHS / M1 law
+    if (p.tp_model > 0) {
+        // sigma(g) g = K g^alpha, K = pi d^2 (2 k T_ref / m_r)^(omega - 1/2) / Gamma(5/2 - omega)
+        const double mr = kMAL * kMAR / (kMAL + kMAR);
+        const double dd = p.tp_model == 2 ? std::sqrt(4.0 / 3.0) * p.tp_dref : p.tp_dref;
+        const double K = kPI * dd * dd * std::pow(2.0 * kKB * p.tp_tref / mr, p.tp_omega - 0.5) /
+                         std::tgamma(2.5 - p.tp_omega);
+        const double alpha = 2.0 - 2.0 * p.tp_omega;
+        const double c = std::sqrt(2.0 * kKB * p.gas_temp_k / kMAR);
+        d.tp_alpha = (float)alpha;
+        nK = ngas * K;
+        d.tp_nK_dt = (float)(nK * p.tp_dt);
+        d.tpf_nK = (float)nK;
+        d.tpf_malpha = (float)(std::pow(c, alpha) * std::tgamma(0.5 * (3.0 + alpha)) / std::tgamma(1.5));
+        d.tpf_gk = (float)(0.5 * (3.0 + alpha));
+    }
     d.Emax_hist = (float)(2.0 * p.rf_volt_v > 0 ? 2.0 * p.rf_volt_v : 1.0);
     d.sputter = p.sputter_enable != 0;
     d.diag_every = p.diag_every;
@@ -262,6 +282,7 @@ void derive(pic_ctx* c)
     const double dtc = p.tp_every * p.dt;
     c->d_coupled.tp_scale = (float)(dtc * 4294967296.0 / p.gap_m);
     c->d_coupled.tp_nsig_dt = (float)(ngas * p.sigma_tp * dtc);
+    c->d_coupled.tp_nK_dt = (float)(nK * dtc);
 }
 
 void sync_desc(pic_ctx* c)          // keep the coupled descriptor's pointers in step
@@ -415,6 +436,11 @@ int pic_params_default(pic_params* p)
     p->sort_every_i = 200;
     p->sort_every_tp = 50;
     return PIC_OK;
+}
+
+double pic_vhs_dref(double mu_ref, double t_ref, double omega, double mass_kg)
+{
+    return std::sqrt(15.0 * std::sqrt(mass_kg * kKB * t_ref / kPI) / (8.0 * (2.5 - omega) * (3.5 - omega) * mu_ref));
 }
 
 int pic_state_bytes(const pic_params* pin, int64_t* bytes)

@@ -49,7 +49,8 @@ enum : uint32_t {
     kPurInit = 1, kPurColl = 2, kPurIonize = 3, kPurNewIon = 4, kPurBirthId = 5, kPurGas = 6,
     kPurGap = 7, kPurGap0 = 8,
     kPurSpTrial = 16, kPurSpEmit = 32, kPurSpId = 48, kPurTpGas = 64, kPurTpColl = 65,
-    kPurTpLaunch = 66, kPurTpfFlight = 70, kPurTpfScatter = 71, kPurTpfPartner = 72
+    kPurTpLaunch = 66, kPurTpfFlight = 70, kPurTpfScatter = 71, kPurTpfPartner = 72, kPurTpfCand = 200,
+    kPurTpfGamma = 202
 };
 
 // species and id tags
@@ -176,6 +177,14 @@ struct Dev {                   // everything a kernel needs, passed by value
     float tpf_nsig;                  // n sigma_tp, 1/m
     float tpf_scale;                 // 2^32 / L: fixed-point units per metre
     float tpf_kt;                    // 256 L: residence time (2^-40 s) per fixed-point unit at 1 m/s
+    // TP collision model: 0 hard spheres (tp_nsig_dt, tpf_nsig); 1 VHS, 2 M1 with
+    // sigma(g) g = K g^alpha
+    int tp_model;
+    float tp_alpha;                  // 2 - 2 omega
+    float tp_nK_dt;                  // n K dt of tp_step (per-step rate n K g^alpha dt)
+    float tpf_nK;                    // n K of the flight
+    float tpf_malpha;                // <|w|^alpha> of the Maxwellian gas
+    float tpf_gk;                    // (3 + alpha) / 2, the gamma shape of |w|^2/c^2
     float c2f;                       // A / (2 dx): E per unit of the integer bracket
     float pad2;
     // push

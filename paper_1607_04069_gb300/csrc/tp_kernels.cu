@@ -71,6 +71,38 @@ __device__ __forceinline__ TpGrp tp_load(const SpBuf& B, long long g)
 // and v, 32 bytes of ids); each CTA owns a contiguous run of groups.  The two
 // Philox blocks of every atom (gas partner, collision test) are drawn for the
 // four atoms of a group at once, their rounds interleaved.
+// Collision law of the TP kernels (Sec. "Binary Interactions"): the per-step
+// rate n sigma(g) g dt, for hard spheres n sigma_tp g dt and for the VHS and
+// M1 laws n K g^alpha dt.
+template <bool LAW>
+__device__ __forceinline__ float tp_rate_dt(const Dev& d, float nsig_dt, float nK_dt, float g)
+{
+    return LAW ? nK_dt * powf(g, d.tp_alpha) : nsig_dt * g;
+}
+
+// Direction of the post-collision relative velocity: isotropic for hard
+// spheres and VHS; M1 turns g by chi = pi (1 - sqrt(r1)) at the azimuth
+// 2 pi r2 about g (frame: e1 along g x x^, or g x y^ when |g_x| >= 0.9 |g|,
+// e2 = g^ x e1).
+__device__ __forceinline__ float3 tp_scatter_dir(int model, float gx, float gy, float gz, float gm, uint32_t r1, uint32_t r2)
+{
+    if (model != 2 || gm == 0.0f) return iso_dir(r1, r2);
+    const float ux = gx / gm, uy = gy / gm, uz = gz / gm;
+    const bool xa = fabsf(ux) < 0.9f;
+    // e1 = u x a with a = x^ or y^
+    float e1x = xa ? 0.0f : -uz, e1y = xa ? uz : 0.0f, e1z = xa ? -uy : ux;
+    const float n1 = sqrtf(e1x * e1x + e1y * e1y + e1z * e1z);
+    e1x /= n1; e1y /= n1; e1z /= n1;
+    const float e2x = uy * e1z - uz * e1y, e2y = uz * e1x - ux * e1z, e2z = ux * e1y - uy * e1x;
+    float sc, cc, se, ce;                       // chi = pi (1 - sqrt(r1)), eps = 2 pi r2
+    sincospif(1.0f - sqrtf(u23(r1)), &sc, &cc);
+    sincospif(2.0f * u23(r2), &se, &ce);
+    return make_float3(cc * ux + sc * (ce * e1x + se * e2x), cc * uy + sc * (ce * e1y + se * e2y),
+                       cc * uz + sc * (ce * e1z + se * e2z));
+}
+
+// LAW: the VHS / M1 laws (tp_model 1, 2); else hard spheres
+template <bool LAW>
 __global__ void __launch_bounds__(kTpThreads, 2) k_tp_step(Dev d)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -161,15 +193,16 @@ __global__ void __launch_bounds__(kTpThreads, 2) k_tp_step(Dev d)
                 const float r1s = -2.0f * logf(u23(cg[u].x)), r2s = -2.0f * logf(u23(cg[u].z));
                 const float vm = sqrtf(vx[u] * vx[u] + vy[u] * vy[u] + vz[u] * vz[u]);
                 const float gub = 1.0001f * (vm + d.vth_gas * sqrtf(r1s + r2s));
-                if (uc < -expm1f(-d.tp_nsig_dt * gub)) {
+                if (uc < -expm1f(-tp_rate_dt<LAW>(d, d.tp_nsig_dt, d.tp_nK_dt, gub))) {
                     const float2 n12 = box_muller(cg[u].x, cg[u].y);
                     const float2 n34 = box_muller(cg[u].z, cg[u].w);
                     const float wx = d.vth_gas * n12.x, wy = d.vth_gas * n12.y, wz = d.vth_gas * n34.x;
                     const float gx = vx[u] - wx, gy = vy[u] - wy, gz = vz[u] - wz;
                     const float gm = sqrtf(gx * gx + gy * gy + gz * gz);
-                    const float Pc = -expm1f(-d.tp_nsig_dt * gm);
-                    if (uc < Pc) {                             // hard sphere, isotropic in the centre of mass
-                        const float3 dir = iso_dir(cc[u].y, cc[u].z);
+                    const float Pc = -expm1f(-tp_rate_dt<LAW>(d, d.tp_nsig_dt, d.tp_nK_dt, gm));
+                    if (uc < Pc) {                             // scattering in the centre of mass
+                        const float3 dir = LAW ? tp_scatter_dir(d.tp_model, gx, gy, gz, gm, cc[u].y, cc[u].z)
+                                               : iso_dir(cc[u].y, cc[u].z);
                         vx[u] = mu_al * vx[u] + mu_ar * wx + mu_ar * gm * dir.x;
                         vy[u] = mu_al * vy[u] + mu_ar * wy + mu_ar * gm * dir.y;
                         vz[u] = mu_al * vz[u] + mu_ar * wz + mu_ar * gm * dir.z;
@@ -242,6 +275,22 @@ __global__ void __launch_bounds__(kTpThreads, 2) k_tp_step(Dev d)
 // proposal t and (id, e, TPF_SCATTER); e is kept per atom (SpBuf::nev).  One
 // thread takes one atom through up to kmax events per launch.
 constexpr int kTpfTries = 64;                     // proposals per collision (each accepted w.p. >= 1/2)
+
+// Gamma variate of shape k >= 1 (Marsaglia and Tsang, ACM TOMS 26, 2000),
+// attempt t from Philox(id, e, TPF_GAMMA + t); d after 32 rejections
+__device__ __noinline__ float gamma_mt(float k, uint64_t seed, uint64_t id, uint32_t e)
+{
+    const float dd = k - (1.0f / 3.0f), cc = 1.0f / sqrtf(9.0f * dd);
+    for (int t = 0; t < 32; ++t) {
+        const uint4 r = draw(seed, id, e, kPurTpfGamma + t);
+        const float x = box_muller(r.x, r.y).x;
+        float v = 1.0f + cc * x;
+        if (v <= 0.0f) continue;
+        v = v * v * v;
+        if (logf(u23(r.z)) < 0.5f * x * x + dd - dd * v + dd * logf(v)) return dd * v;
+    }
+    return dd;
+}
 
 __device__ __forceinline__ float mean_rel_speed(float vm, float c)
 {
@@ -316,6 +365,7 @@ __device__ void tpf_segment(const Dev& d, const TpfAcc& A, long long x0, long lo
 }
 
 // kmax <= kTpfMaxEvents; CTA b takes atoms [b kTpfAtomsPerCta, (b + 1) kTpfAtomsPerCta)
+template <bool LAW>
 __global__ void __launch_bounds__(kTpThreads) k_tp_flight(Dev d, int kmax)
 {
     extern __shared__ __align__(16) unsigned char tpf_raw[];
@@ -365,7 +415,9 @@ __global__ void __launch_bounds__(kTpThreads) k_tp_flight(Dev d, int kmax)
         }
         bool done = false, live = true;
         const float vm = sqrtf(vx * vx + vy * vy + vz * vz);
-        const float nu = d.tpf_nsig * mean_rel_speed(vm, c);
+        // hard spheres: the exact rate; VHS / M1: the majorant n K (|v|^alpha + <|w|^alpha>)
+        const float va = LAW ? powf(vm, d.tp_alpha) : 0.0f;
+        const float nu = LAW ? d.tpf_nK * (va + d.tpf_malpha) : d.tpf_nsig * mean_rel_speed(vm, c);
         const uint4 f = draw(d.seed, id, e, kPurTpfFlight);
         const float tau = nu > 0.0f ? -logf(u23(f.x)) / nu : INFINITY;
         if (!(tau < INFINITY) && vx == 0.0f) {
@@ -398,9 +450,11 @@ __global__ void __launch_bounds__(kTpThreads) k_tp_flight(Dev d, int kmax)
             } else {
                 tpf_segment(d, A, x, x1, vx, tau);
                 x = (uint32_t)x1;
-                // the collision partner, flux-weighted
+                // the collision partner, flux-weighted (hard spheres), or a candidate
+                // partner and the test whether it is a real collision (VHS / M1)
                 float wx = 0.0f, wy = 0.0f, wz = 0.0f, gm = 0.0f;
-                for (int t = 0; t < kTpfTries; ++t) {
+                bool real = true;
+                for (int t = 0; !LAW && t < kTpfTries; ++t) {
                     uint4 cw[2];
                     cw[0] = make_uint4((uint32_t)id, (uint32_t)(id >> 32), e, kPurTpfPartner + 2 * t);
                     cw[1] = make_uint4((uint32_t)id, (uint32_t)(id >> 32), e, kPurTpfPartner + 2 * t + 1);
@@ -419,14 +473,35 @@ __global__ void __launch_bounds__(kTpThreads) k_tp_flight(Dev d, int kmax)
                     const float wm = sqrtf(wx * wx + wy * wy + wz * wz);
                     if (u23(b.y) * (vm + wm) < gm) break;
                 }
-                // hard sphere, isotropic in the centre of mass
-                const uint4 sc = draw(d.seed, id, e, kPurTpfScatter);
-                const float3 dir = iso_dir(sc.x, sc.y);
-                vx = mu_al * vx + mu_ar * wx + mu_ar * gm * dir.x;
-                vy = mu_al * vy + mu_ar * wy + mu_ar * gm * dir.y;
-                vz = mu_al * vz + mu_ar * wz + mu_ar * gm * dir.z;
+                if (LAW) {
+                    uint4 cw[2];
+                    cw[0] = make_uint4((uint32_t)id, (uint32_t)(id >> 32), e, kPurTpfCand);
+                    cw[1] = make_uint4((uint32_t)id, (uint32_t)(id >> 32), e, kPurTpfCand + 1);
+                    philox_n<2>(cw, k0, k1);
+                    const uint4 a = cw[0], b = cw[1];
+                    if (u23(a.x) * (va + d.tpf_malpha) < va) {
+                        const float2 n12 = box_muller(a.y, a.z), n34 = box_muller(a.w, b.x);
+                        wx = vg * n12.x; wy = vg * n12.y; wz = vg * n34.x;
+                    } else {
+                        const float sp = c * sqrtf(gamma_mt(d.tpf_gk, d.seed, id, e));
+                        const float3 dd = iso_dir(a.w, b.x);
+                        wx = sp * dd.x; wy = sp * dd.y; wz = sp * dd.z;
+                    }
+                    const float gx = vx - wx, gy = vy - wy, gz = vz - wz;
+                    gm = sqrtf(gx * gx + gy * gy + gz * gz);
+                    const float wm = sqrtf(wx * wx + wy * wy + wz * wz);
+                    real = u23(b.y) * (va + powf(wm, d.tp_alpha)) < powf(gm, d.tp_alpha);
+                }
+                if (real) {                                        // scattering in the centre of mass
+                    const uint4 sc = draw(d.seed, id, e, kPurTpfScatter);
+                    const float3 dir = LAW ? tp_scatter_dir(d.tp_model, vx - wx, vy - wy, vz - wz, gm, sc.x, sc.y)
+                                           : iso_dir(sc.x, sc.y);
+                    vx = mu_al * vx + mu_ar * wx + mu_ar * gm * dir.x;
+                    vy = mu_al * vy + mu_ar * wy + mu_ar * gm * dir.y;
+                    vz = mu_al * vz + mu_ar * wz + mu_ar * gm * dir.z;
+                    ++n_coll;
+                }
                 ++e;
-                ++n_coll;
                 done = ++ev == kmax;
             }
         }
@@ -504,12 +579,13 @@ cudaError_t launch_tp_flight(const Dev& d, int kmax, long long n, cudaStream_t s
     if (kmax > kTpfMaxEvents) kmax = kTpfMaxEvents;
     const size_t sm = tpf_smem(d.ncell);
     if (sm > 48 * 1024) {
-        const cudaError_t e = cudaFuncSetAttribute((const void*)k_tp_flight,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        const void* fn = d.tp_model ? (const void*)k_tp_flight<true> : (const void*)k_tp_flight<false>;
+        const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
     }
     const long long grid = (n + kTpfAtomsPerCta - 1) / kTpfAtomsPerCta;
-    k_tp_flight<<<(unsigned)grid, kTpThreads, sm, st>>>(d, kmax);
+    if (d.tp_model) k_tp_flight<true><<<(unsigned)grid, kTpThreads, sm, st>>>(d, kmax);
+    else k_tp_flight<false><<<(unsigned)grid, kTpThreads, sm, st>>>(d, kmax);
     return cudaGetLastError();
 }
 
@@ -517,11 +593,12 @@ cudaError_t launch_tp_step(const Dev& d, int grid, cudaStream_t st)
 {
     const size_t sm = tp_smem(d.ncell);
     if (sm > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute((const void*)k_tp_step,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        const void* fn = d.tp_model ? (const void*)k_tp_step<true> : (const void*)k_tp_step<false>;
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
     }
-    k_tp_step<<<grid, kTpThreads, sm, st>>>(d);
+    if (d.tp_model) k_tp_step<true><<<grid, kTpThreads, sm, st>>>(d);
+    else k_tp_step<false><<<grid, kTpThreads, sm, st>>>(d);
     return cudaGetLastError();
 }
 

@@ -103,3 +103,55 @@ def test_without_gas_every_atom_flies_straight_to_its_electrode():
     t, to = d.diag("tpf_time"), orc.diag("tpf_time")
     assert np.allclose(t[1:], to[1:], rtol=1e-5)
     d.close()
+
+
+VHS = dict(tp_dref=4.17e-10, tp_omega=0.81, tp_tref=273.0)
+
+
+@pytest.mark.parametrize("model", [1, 2], ids=["vhs", "m1"])
+def test_vhs_and_m1_flights_match_oracle(model):
+    """The VHS and M1 laws (majorant rate, null events, gamma-distributed
+    candidate speeds, M1 deflections): after 4 events the atoms in flight
+    match the oracle's per atom, and run to deposition the deposits,
+    collisions and far-electrode energies agree as in the hard-sphere case."""
+    n = 30_000
+    cfg = _cfg(n, tp_model=model, **VHS)
+    d, orc = _pair(cfg, n)
+    d.tp_flight(4)
+    orc.tp_flight(4)
+    g, o, only_g, only_o = match(d.get_species(2), orc.get_species(2))
+    assert len(only_g) + len(only_o) <= n // 500
+    vm = np.sqrt(o["vx"]**2 + o["vy"]**2 + o["vz"]**2)
+    for k in ("vx", "vy", "vz"):
+        assert (np.abs(g[k] - o[k]) <= 1e-4 * vm + 1e-3).mean() > 0.998, k
+    assert d.tp_flight(1_000_000) == 0 and orc.tp_flight(1_000_000) == 0
+    c, oc = d.counters(), orc.counters()
+    for k in ("tp_dep_l", "tp_dep_r", "tp_coll"):
+        assert abs(c[k] - oc[k]) <= 0.01 * max(oc[k], 1000), (k, c[k], oc[k])
+    x, y = d.diag("sputter_e_r"), orc.diag("sputter_e_r")
+    D = np.abs(np.cumsum(x) / x.sum() - np.cumsum(y) / y.sum()).max()
+    assert stats.kstwobign.sf(D * math.sqrt(x.sum() * y.sum() / (x.sum() + y.sum()))) > 0.01
+    d.close()
+
+
+@pytest.mark.parametrize("model", [1, 2], ids=["vhs", "m1"])
+def test_vhs_and_m1_per_step_transport_matches_oracle(model):
+    """tp_step under the VHS and M1 laws (per-step probability 1 -
+    exp(-n K g^alpha dt) with a sampled partner): 200 steps of 1 ns, every
+    atom within FP32 rounding of the oracle's, the same atoms deposited."""
+    cfg = W.tp_transport(n_atoms=50_000)
+    cfg.update(cap_tp=60_000, n_e0=0, n_i0=0, sort_every_tp=0, tp_model=model, **VHS)
+    d = gpu_discharge(cfg)
+    orc = oracle_for(cfg, cap=10, cap_tp=60_000)
+    d.tp_launch(50_000, 300.0)
+    orc.tp_launch(50_000, 300.0)
+    alive = d.tp_step(200)
+    orc.tp_step(200, cfg["tp_dt"])
+    c, oc = d.counters(), orc.counters()
+    assert c["tp_dep_l"] + c["tp_dep_r"] + alive == 50_000
+    assert abs(c["tp_coll"] - oc["tp_coll"]) <= 3
+    g, o, only_g, only_o = match(d.get_species(2), orc.get_species(2))
+    assert len(only_g) + len(only_o) <= 6
+    vmag = np.sqrt(o["vx"]**2 + o["vy"]**2 + o["vz"]**2)
+    assert (np.abs(g["vx"] - o["vx"]) > 1e-3 * vmag + 1e-2).sum() <= 6
+    d.close()
