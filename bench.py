@@ -228,6 +228,41 @@ def measure_rows(d, cfg, peak, cmp_ms, cmp_n, nsort_particles, n_atoms):
         "events": int(events), "events_per_atom": events / n_atoms, "still_in_flight": int(left),
         "deposited_far": int(cnt["tp_dep_r"]), "deposited_source": int(cnt["tp_dep_l"])}
     t.close()
+    # the same run under the VHS and M1 laws (argon's VHS data for the Al-Ar pair)
+    for model, name in ((1, "vhs"), (2, "m1")):
+        tv = dict(tc, tp_model=model, tp_dref=4.17e-10, tp_omega=0.81, tp_tref=273.0)
+        t = P.Discharge(P.params_from_workload(tv))
+        t.tp_launch(n_atoms, 300.0)
+        t.sync()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        left = t.tp_flight(10_000_000)
+        wall_s = time.perf_counter() - t0
+        cnt = t.counters()
+        rows[f"a8_tp_flight_{name}_to_deposition"] = {
+            "value": n_atoms / wall_s, "unit": "atoms deposited/s", "seconds_to_deposition": wall_s,
+            "collisions_per_atom": cnt["tp_coll"] / n_atoms, "still_in_flight": int(left),
+            "deposited_far": int(cnt["tp_dep_r"])}
+        t.close()
+    # NEXT-1: the step with the two-harmonic source and the series capacitor
+    per_launch = {}
+    for name, over in (("circuit", dict(waveform=1, rf_phase=0.0, circuit=1,
+                                        c_block=10.0 * 8.8541878128e-12 / cfg["gap_m"])), ("ideal", {})):
+        dc = P.Discharge(P.params_from_workload(dict(cfg, **over)))
+        dc.step(30)
+        dc.sync()
+        dc.timing(True)
+        dc.step(300)
+        dc.sync()
+        ms, n = dc.kernel_time("step")
+        c2 = dc.counters()
+        dc.close()
+        per_launch[name] = (ms / n * 1e-3, c2["n_e_slots"] + c2["n_i_slots"])
+    per, slots = per_launch["circuit"]
+    rows["n1_circuit_step"] = {"workload": cfg["name"] + ", two-harmonic source through c = 10 eps0/L",
+                               "value": slots / per, "unit": "particle-steps/s", "mean_launch_us": per * 1e6,
+                               "ideal_source_mean_launch_us": per_launch["ideal"][0] * 1e6,
+                               "note": "mean step launch by CUDA events, both without an L2 flush between steps"}
     # a9: compaction (counting sort by cell of one species) in the timed run
     if cmp_n:
         per_sort = cmp_ms / cmp_n * 1e-3
