@@ -108,6 +108,8 @@ def lib():
                 "orc_tp_flight": (i64, [vp, i64]),
                 "orc_width_to_peak": (dbl, [vp, C.c_int, dbl]),
                 "orc_tp_sigma": (dbl, [vp, dbl]),
+                "orc_xs_interp": (dbl, [vp, vp, i64, dbl]),
+                "orc_set_cross_section": (C.c_int, [vp, C.c_int, i64, vp, vp]),
                 "orc_vhs_dref": (dbl, [dbl, dbl, dbl, dbl]),
                 "orc_tp_scatter": (None, [C.c_int, vp, u32, u32, vp]),
                 "orc_rms_angle": (dbl, [vp, C.c_int]),
@@ -149,6 +151,13 @@ def tpf_partner(seed, atom_id, e, Tg, v):
     w = np.zeros(3)
     t = lib().orc_tpf_partner(int(seed), int(atom_id), int(e), float(Tg), _p(vv), _p(w))
     return w, int(t)
+
+
+def xs_interp(E, sigma, eps):
+    """Tabulated cross section at eps: linear between points, constant outside."""
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    sg = np.ascontiguousarray(sigma, dtype=np.float64)
+    return float(lib().orc_xs_interp(_p(E), _p(sg), E.size, float(eps)))
 
 
 def vhs_dref(mu_ref, t_ref, omega, mass):
@@ -301,6 +310,14 @@ class Oracle:
 
     def reset_averages(self):
         lib().orc_reset_averages(self.h)
+
+    def set_cross_section(self, process, E, sigma):
+        """Tabulate e-Ar process 0/1/2 (elastic, excitation, ionisation); E in eV,
+        sigma in m^2; empty arrays restore the analytic form."""
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        sg = np.ascontiguousarray(sigma, dtype=np.float64)
+        if lib().orc_set_cross_section(self.h, int(process), E.size, _p(E), _p(sg)) != 0:
+            raise ValueError("bad cross-section table")
 
     def tp_sigma(self, g):
         """TP collision cross section at relative speed g (m^2)."""

@@ -140,6 +140,8 @@ typedef struct {
     /* diagnostics */
     double *sum_q[2], *sum_phi, *sum_flux[2], *tp_dens, *tp_vx;
     double *tpf_time, *tpf_disp;  /* event-driven TP: residence time (s), signed path (m) per cell */
+    double *xs_e[3], *xs_s[3];    /* tabulated e-Ar cross sections (eV, m^2), or NULL: analytic */
+    int64_t xs_n[3];
     int64_t n_avg, n_flux, n_tp_samp, tp_launched;
     int64_t *iedf[2], *ieadf[2], *eedf, *sp_e[2], *sp_ang[2];
     int64_t cnt[C_NCOUNT];
@@ -203,6 +205,30 @@ void orc_sigma_e(double eps, double out[3])
     out[0] = O_SIG_EL;
     out[1] = eps > O_EXC_TH ? O_EXC_SIG * (1.0 - O_EXC_TH / eps) : 0.0;
     out[2] = eps > O_ION_TH ? O_LOTZ_A * O_LOTZ_Q * log(eps / O_ION_TH) / (eps * O_ION_TH) : 0.0;
+}
+
+/* Tabulated cross section (Sec. "Particle Collisions": energy-dependent
+ * cross sections from look-up tables): linear interpolation between the
+ * points (E_i, sigma_i), E increasing, held constant beyond the first and
+ * last points. */
+double orc_xs_interp(const double *E, const double *sg, int64_t n, double eps)
+{
+    if (eps <= E[0]) return sg[0];
+    if (eps >= E[n - 1]) return sg[n - 1];
+    int64_t lo = 0, hi = n - 1;                  /* E[lo] <= eps < E[hi] */
+    while (hi - lo > 1) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (E[mid] <= eps) lo = mid; else hi = mid;
+    }
+    return sg[lo] + (eps - E[lo]) / (E[hi] - E[lo]) * (sg[hi] - sg[lo]);
+}
+
+/* the three e-Ar cross sections at eps: tabulated where a table is set */
+static void electron_sigma(const orc_state *S, double eps, double out[3])
+{
+    orc_sigma_e(eps, out);
+    for (int p = 0; p < 3; p++)
+        if (S->xs_n[p]) out[p] = orc_xs_interp(S->xs_e[p], S->xs_s[p], S->xs_n[p], eps);
 }
 
 /* Ar+-Ar isotropic and charge exchange (each channel), eps in eV */
@@ -423,8 +449,13 @@ static void derive(orc_state *S)
     S->ngas = P->p / (O_KB * P->Tg);
     S->dx = P->L / (double)P->ncell;
     S->eps_max = 2.0 * (P->waveform == 1 ? 2.0 * P->V0 : P->V0) + 100.0;   /* peak source voltage */
-    double sig_ion_max = O_LOTZ_A * O_LOTZ_Q / (exp(1.0) * O_ION_TH * O_ION_TH);
-    double sig_sum_max = O_SIG_EL + O_EXC_SIG + sig_ion_max;
+    double sig_max[3] = {O_SIG_EL, O_EXC_SIG, O_LOTZ_A * O_LOTZ_Q / (exp(1.0) * O_ION_TH * O_ION_TH)};
+    for (int q = 0; q < 3; q++)                  /* a table: its largest value */
+        if (S->xs_n[q]) {
+            sig_max[q] = 0.0;
+            for (int64_t i = 0; i < S->xs_n[q]; i++) sig_max[q] = fmax(sig_max[q], S->xs_s[q][i]);
+        }
+    double sig_sum_max = sig_max[0] + sig_max[1] + sig_max[2];
     S->nu_max_e = S->ngas * sig_sum_max * sqrt(2.0 * S->eps_max * O_QE / O_ME);
     double mr = O_MAR / 2.0;
     S->nu_max_i = 2.0 * S->ngas * O_ARP_SIG * sqrt(2.0 * O_QE / mr);
@@ -469,6 +500,7 @@ void orc_destroy(orc_state *S)
     for (int s = 0; s < 3; s++) sp_free(&S->sp[s]);
     free(S->E); free(S->phi); free(S->sum_phi); free(S->tp_dens); free(S->tp_vx); free(S->eedf);
     free(S->tpf_time); free(S->tpf_disp);
+    for (int q = 0; q < 3; q++) { free(S->xs_e[q]); free(S->xs_s[q]); }
     for (int s = 0; s < 2; s++) {
         free(S->q[s]); free(S->sum_q[s]); free(S->sum_flux[s]); free(S->iedf[s]);
         free(S->ieadf[s]); free(S->sp_e[s]); free(S->sp_ang[s]);
@@ -502,6 +534,32 @@ void orc_init_species(orc_state *S, int s, int64_t n, double T_eV)
         box_muller(b[0], b[1], &n3, &n4);
         append(S, s, xi, vth * n1, vth * n2, vth * n3, id, 0);
     }
+}
+
+/* Replace the analytic cross section of e-Ar process q (0 elastic, 1
+ * excitation, 2 ionisation) by a table of n points (n = 0: back to the
+ * analytic form); nu_max follows from the tables' largest values, and every
+ * electron's next candidate is drawn afresh from the current step (the
+ * candidate process is memoryless).  Returns -1 for a bad table. */
+int orc_set_cross_section(orc_state *S, int q, int64_t n, const double *E, const double *sg)
+{
+    if (q < 0 || q > 2 || n < 0 || n == 1) return -1;
+    for (int64_t i = 0; i < n; i++)
+        if (!(sg[i] >= 0.0) || (i > 0 && !(E[i] > E[i - 1]))) return -1;
+    free(S->xs_e[q]); free(S->xs_s[q]);
+    S->xs_e[q] = S->xs_s[q] = NULL;
+    S->xs_n[q] = n;
+    if (n) {
+        S->xs_e[q] = (double *)malloc(sizeof(double) * n);
+        S->xs_s[q] = (double *)malloc(sizeof(double) * n);
+        memcpy(S->xs_e[q], E, sizeof(double) * n);
+        memcpy(S->xs_s[q], sg, sizeof(double) * n);
+    }
+    derive(S);
+    orc_sp *p = &S->sp[SP_E];
+    for (int64_t k = 0; k < p->n; k++)
+        if (p->alive[k]) p->nev[k] = entry_nev(S, SP_E, p->id[k], S->step);
+    return 0;
 }
 
 /* Load an arbitrary particle set (seeded synthetic inputs in tests). */
@@ -609,7 +667,7 @@ static void mcc_electron(orc_state *S, int64_t k, uint32_t l)
     double eps = 0.5 * O_ME * v2 / O_QE;
     if (eps > S->eps_max) S->cnt[C_NUMERICS]++;
     double sg[3];
-    orc_sigma_e(eps, sg);
+    electron_sigma(S, eps, sg);
     double nu_el = S->ngas * sg[0] * v;
     double nu_exc = S->ngas * sg[1] * v;
     double nu_ion = S->ngas * sg[2] * v;

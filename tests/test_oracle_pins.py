@@ -840,3 +840,44 @@ def test_vhs_and_m1_flights_agree_with_the_per_step_test(model):
     D = np.abs(np.cumsum(ha[sel]) / na - np.cumsum(hb[sel]) / nb).max()
     assert stats.kstwobign.sf(D * math.sqrt(na * nb / (na + nb))) > 1e-3
     assert b.counters()["tp_dep_l"] + b.counters()["tp_dep_r"] == n
+
+
+# ------------------------------------------------------------------ tabulated electron cross sections
+def test_cross_section_table_interpolation_against_numpy():
+    """Linear interpolation of an LXcat-style table (constant beyond the
+    ends) against numpy.interp on random tables and energies, including the
+    table points themselves and energies outside it."""
+    rng = np.random.default_rng(12)
+    for n in (2, 7, 300):
+        E = np.sort(rng.uniform(0.0, 200.0, n))
+        E = np.unique(E)
+        sg = rng.uniform(0.0, 1e-19, E.size)
+        eps = np.concatenate([rng.uniform(-10.0, 250.0, 400), E])
+        got = np.array([O.xs_interp(E, sg, e) for e in eps])
+        assert np.allclose(got, np.interp(eps, E, sg), rtol=1e-14, atol=0.0)
+
+
+def test_constant_cross_section_table_gives_the_collision_rate():
+    """A table holding a constant elastic cross section (excitation and
+    ionisation tables zero): nu_max is n sigma v(eps_max), and electrons at
+    speed v collide per step with probability (1 - exp(-nu_max dt)) n sigma
+    v / nu_max."""
+    N, dt, n, p = 64, 2e-11, 200_000, 3.0
+    orc = O.Oracle(prm(L=1.0, ncell=N, p=p, Tg=300.0, dt=dt, V0=50.0), n + 10, 10)
+    E = np.array([0.0, 1000.0])
+    orc.set_cross_section(0, E, [2.5e-19, 2.5e-19])
+    orc.set_cross_section(1, E, [0.0, 0.0])
+    orc.set_cross_section(2, E, [0.0, 0.0])
+    ngas = p / (KB * 300.0)
+    eps_max = 2 * 50.0 + 100.0
+    assert orc.derived()["nu_max_e"] == pytest.approx(ngas * 2.5e-19 * math.sqrt(2 * eps_max * QE / ME), rel=1e-14)
+    v = math.sqrt(2 * 10.0 * QE / ME)
+    rng = np.random.default_rng(5)
+    load(orc, 0, rng.uniform(10, 50, n), _mono(n, v, rng))
+    orc.set_field(np.zeros(N + 1))
+    orc.step(1)
+    num = orc.derived()["nu_max_e"]
+    pexp = (1.0 - math.exp(-num * dt)) * ngas * 2.5e-19 * v / num   # candidate, then elastic
+    got = orc.counters()["elastic"]
+    assert abs(got - n * pexp) < 4.5 * math.sqrt(n * pexp)
+    assert orc.counters()["excitation"] == 0 and orc.counters()["ionizations"] == 0
