@@ -231,6 +231,16 @@ int tp_step(pic_ctx* ctx, int64_t n_steps, int64_t* n_alive);
  * in flight. */
 int tp_flight(pic_ctx* ctx, int64_t max_events, int64_t* n_alive);
 
+/* Tabulate the e-Ar cross section of process q (0 elastic, 1 excitation,
+ * 2 ionisation) from n host points (energy in eV, increasing; sigma in m^2,
+ * >= 0), as LXcat-style data are given (Sec. "Particle Collisions": cross
+ * sections from look-up tables): linear between the points, constant beyond
+ * the ends; n = 0 restores the analytic form.  The thresholds of the
+ * kinematics (11.5 and 15.8 eV) stay.  nu_max follows from the tables'
+ * largest values, and every electron's next null-collision candidate is
+ * drawn afresh from the current step.  Synchronises the stream. */
+int pic_set_cross_section(pic_ctx* ctx, int process, int64_t n, const double* energy_ev, const double* sigma_m2);
+
 /* Compact one species now (drop removed slots, counting sort by cell). */
 int pic_compact(pic_ctx* ctx, int species);
 

@@ -112,6 +112,7 @@ def lib():
             "tp_step": [vp, i64, pi64],
             "tp_flight": [vp, i64, pi64],
             "pic_hypotheses": [vp, vp],
+            "pic_set_cross_section": [vp, C.c_int, i64, vp, vp],
             "pic_compact": [vp, C.c_int],
             "pic_timing": [vp, C.c_int],
             "pic_kernel_time": [vp, C.c_int, C.POINTER(dbl), pi64],
@@ -295,6 +296,13 @@ class Discharge:
         a = C.c_int64()
         _check(lib().tp_flight(self.h, int(max_events), C.byref(a)))
         return a.value
+
+    def set_cross_section(self, process, energy_ev, sigma_m2):
+        """Tabulated e-Ar cross section of process 0/1/2 (``pic_set_cross_section``);
+        empty arrays restore the analytic form."""
+        E = np.ascontiguousarray(energy_ev, dtype=np.float64)
+        sg = np.ascontiguousarray(sigma_m2, dtype=np.float64)
+        _check(lib().pic_set_cross_section(self.h, int(process), E.size, _ptr(E), _ptr(sg)))
 
     def compact(self, s):
         _check(lib().pic_compact(self.h, SPECIES.get(s, s)))

@@ -4,6 +4,7 @@
 // structure-of-arrays particle store, the per-step histograms and the
 // diagnostic accumulators), schedules the per-step kernels on the caller's
 // stream and converts diagnostics to physical units on the host.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -64,6 +65,8 @@ struct pic_ctx {
     unsigned int cur[3] = {0, 0, 0}; // active ping-pong halves (each compaction flips one)
     long long period = 0;            // steps per RF period when that is a whole number, else 0
     double circ_beta = 0.0;          // series capacitor: 1 / (1 + L c / eps0)
+    std::vector<double> xs_e[3], xs_s[3];   // tabulated e-Ar cross sections (eV, m^2), empty: analytic
+    float2* xs_dev[3] = {nullptr, nullptr, nullptr};
     double derived[8];
     bool timing = false;
     Timer timers[3];
@@ -194,8 +197,12 @@ void derive(pic_ctx* c)
     // null-collision energy bound: twice the peak source voltage (V0 for the
     // sine, 2 V0 for the two-harmonic waveform) plus 100 eV
     const double eps_max = 2.0 * (p.waveform == 1 ? 2.0 * p.rf_volt_v : p.rf_volt_v) + 100.0;
-    const double sig_ion_max = kLotzA * kLotzQ / (std::exp(1.0) * kIonTh * kIonTh);
-    const double sig_sum_max = kSigEl + kExcSig + sig_ion_max;
+    // closed-form maxima of the analytic cross sections; a tabulated process
+    // contributes its largest tabulated value
+    double sig_max[3] = {kSigEl, kExcSig, kLotzA * kLotzQ / (std::exp(1.0) * kIonTh * kIonTh)};
+    for (int q = 0; q < 3; ++q)
+        if (!c->xs_s[q].empty()) sig_max[q] = *std::max_element(c->xs_s[q].begin(), c->xs_s[q].end());
+    const double sig_sum_max = sig_max[0] + sig_max[1] + sig_max[2];
     const double nu_max_e = ngas * sig_sum_max * std::sqrt(2.0 * eps_max * kQE / kME);
     const double mr = kMAR / 2.0;
     const double nu_max_i = 2.0 * ngas * kArpSig * std::sqrt(2.0 * kQE / mr);
@@ -291,12 +298,9 @@ void sync_desc(pic_ctx* c)          // keep the coupled descriptor's pointers in
     c->d_coupled = c->d;
     c->d_coupled.tp_scale = keep.tp_scale;
     c->d_coupled.tp_nsig_dt = keep.tp_nsig_dt;
+    c->d_coupled.tp_nK_dt = keep.tp_nK_dt;
 }
 
-// electrode voltage at step l (V0 sin(2 pi f t_l), t_l = l dt)
-// electrode voltage at step l, V0 sin(2 pi f t_l), evaluated at the phase of
-// step l within its RF period when a period is a whole number of steps (so a
-// step's voltage depends only on its phase, here and in batched stepping)
 // source voltage at step l (Sec. "Simulation Scenario"): V0 sin(w t), or the
 // fundamental and its harmonic V0 [cos(w t + phase) + cos(2 w t)]; the phase
 // of step l is taken at l mod period when the period is a whole number of steps
@@ -555,6 +559,8 @@ void pic_destroy(pic_ctx* c)
         for (auto ev : t.ev) cudaEventDestroy(ev);
     if (c->arena) cudaFree(c->arena);
     if (c->d.trace) cudaFree(c->d.trace);
+    for (float2* t : c->xs_dev)
+        if (t) cudaFree(t);
     delete c;
 }
 
@@ -1104,6 +1110,38 @@ int tp_flight(pic_ctx* c, int64_t max_events, int64_t* n_alive)
         }
         *n_alive = (int64_t)alive;
     }
+    return PIC_OK;
+}
+
+int pic_set_cross_section(pic_ctx* c, int q, int64_t n, const double* E, const double* sigma)
+{
+    if (!c || q < 0 || q > 2 || n < 0 || n == 1 || n > 65536 || (n > 0 && (!E || !sigma)))
+        return fail(PIC_ERR_INVALID_ARG, "process 0..2 and a table of 0 or 2..65536 points");
+    for (int64_t i = 0; i < n; ++i)
+        if (!(sigma[i] >= 0.0) || !std::isfinite(E[i]) || (i > 0 && !(E[i] > E[i - 1])))
+            return fail(PIC_ERR_INVALID_ARG, "energies must increase and cross sections be >= 0");
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(c->stream));
+    if (c->xs_dev[q]) CK(cudaFree(c->xs_dev[q]));
+    c->xs_dev[q] = nullptr;
+    c->xs_e[q].assign(E, E + n);
+    c->xs_s[q].assign(sigma, sigma + n);
+    if (n) {
+        std::vector<float2> t((size_t)n);
+        for (int64_t i = 0; i < n; ++i) t[(size_t)i] = make_float2((float)E[i], (float)sigma[i]);
+        CK(cudaMalloc(&c->xs_dev[q], sizeof(float2) * (size_t)n));
+        CK(cudaMemcpy(c->xs_dev[q], t.data(), sizeof(float2) * (size_t)n, cudaMemcpyHostToDevice));
+    }
+    c->d.xs_tab[q] = c->xs_dev[q];
+    c->d.xs_n[q] = (int)n;
+    derive(c);                                      // nu_max of the electrons from the tables
+    // the candidate process is memoryless: every electron's next candidate is
+    // drawn afresh from the current step at the new nu_max
+    Ctl h;
+    int rc = read_ctl(c, &h);
+    if (rc) return rc;
+    CK(launch_entry_nev(c->d, kE, h.cur[kE], h.n[kE], (unsigned int)c->h_step, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
     return PIC_OK;
 }
 

@@ -185,6 +185,10 @@ struct Dev {                   // everything a kernel needs, passed by value
     float tpf_nK;                    // n K of the flight
     float tpf_malpha;                // <|w|^alpha> of the Maxwellian gas
     float tpf_gk;                    // (3 + alpha) / 2, the gamma shape of |w|^2/c^2
+    // tabulated e-Ar cross sections (elastic, excitation, ionisation): (eV, m^2)
+    // points, linear between them, constant beyond; xs_n 0: the analytic form
+    const float2* xs_tab[3];
+    int xs_n[3], xs_pad;
     float c2f;                       // A / (2 dx): E per unit of the integer bracket
     float pad2;
     // push

@@ -86,6 +86,21 @@ __device__ __forceinline__ uint32_t ev_gap(double lam, float lamf, uint32_t w)
     uint32_t g;
     return gap_fast(lamf, w, g) ? g : ev_gap_exact(lam, w);
 }
+// tabulated cross section (Sec. "Particle Collisions": look-up tables):
+// linear between the points, constant beyond the first and the last
+__device__ __noinline__ float ev_xs_table(const float2* t, int n, float eps)
+{
+    if (eps <= t[0].x) return t[0].y;
+    if (eps >= t[n - 1].x) return t[n - 1].y;
+    int lo = 0, hi = n - 1;                       // t[lo].x <= eps < t[hi].x
+    while (hi - lo > 1) {
+        const int mid = lo + (hi - lo) / 2;
+        if (t[mid].x <= eps) lo = mid;
+        else hi = mid;
+    }
+    const float2 a = t[lo], b = t[hi];
+    return a.y + (eps - a.x) / (b.x - a.x) * (b.y - a.y);
+}
 __device__ __noinline__ float3 ev_emit(float uE, float uT, float uP, float Emax, float dir)
 {
     return emit(uE, uT, uP, Emax, dir);
@@ -410,11 +425,17 @@ __device__ __noinline__ void handle_event(const Dev& d, int s, long long i, uint
         const float v = sqrtf(v2);
         const float eps = v2 * (float)(0.5 * kME / kQE);
         if (eps > d.eps_max) atomicAdd(&tally->numerics, 1u);
-        const float s_exc = eps > (float)kExcTh ? (float)kExcSig * (1.0f - (float)kExcTh / eps) : 0.0f;
-        const float s_ion = eps > (float)kIonTh
-                                ? (float)(kLotzA * kLotzQ) * logf(eps / (float)kIonTh) / (eps * (float)kIonTh)
-                                : 0.0f;
-        const float nu_el = d.ngas_f * (float)kSigEl * v;
+        float s_el = (float)kSigEl;
+        float s_exc = eps > (float)kExcTh ? (float)kExcSig * (1.0f - (float)kExcTh / eps) : 0.0f;
+        float s_ion = eps > (float)kIonTh
+                          ? (float)(kLotzA * kLotzQ) * logf(eps / (float)kIonTh) / (eps * (float)kIonTh)
+                          : 0.0f;
+        if (d.xs_n[0] | d.xs_n[1] | d.xs_n[2]) {
+            if (d.xs_n[0]) s_el = ev_xs_table(d.xs_tab[0], d.xs_n[0], eps);
+            if (d.xs_n[1]) s_exc = ev_xs_table(d.xs_tab[1], d.xs_n[1], eps);
+            if (d.xs_n[2]) s_ion = ev_xs_table(d.xs_tab[2], d.xs_n[2], eps);
+        }
+        const float nu_el = d.ngas_f * s_el * v;
         const float nu_exc = d.ngas_f * s_exc * v;
         const float nu_ion = d.ngas_f * s_ion * v;
         const float r = u23(c.y) * d.nu_max_e;
