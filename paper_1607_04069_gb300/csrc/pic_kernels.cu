@@ -552,6 +552,9 @@ __device__ __forceinline__ void mover_body(const Dev& d, const StepArgs& a, int 
     const unsigned int l = a.step;              // the host's step count (equal to ctl->step)
     Ctl* ctl = d.ctl;
     const long long ne = ctl->n[kE], ni = ctl->n[kI], ntp = ctl->n[kTP];
+    // charge delivered to the driven electrode (series capacitor), loaded now so
+    // that its latency passes during the deposit copy
+    const long long wall_dn = MODE == 0 && a.field_mode == kFieldCircuit ? ctl->wall_dn : 0ll;
     const unsigned int field_override = MODE == 0 ? ctl->field_override : 0u;
     if (MODE == 0) {
         // both deposits of x^l (slot l%3) into shared memory: asynchronous
@@ -634,7 +637,7 @@ __device__ __forceinline__ void mover_body(const Dev& d, const StepArgs& a, int 
         if (field_override) {
             for (int i = threadIdx.x; i < N1; i += blockDim.x) sE[i] = d.E32[i];
         } else {
-            v_el = block_field_f32(d, sqe, sqi, sE, a);
+            v_el = block_field_f32(d, sqe, sqi, sE, a, wall_dn);
         }
     }
     __syncthreads();

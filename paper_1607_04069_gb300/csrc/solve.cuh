@@ -163,8 +163,9 @@ __device__ __noinline__ static double poisson_block(const QNet& qn, int N, doubl
 // capacitor (field_mode kFieldCircuit) it is formed here from the source
 // voltage a.v_left, T_N, q_0 and the charge absorbed at x = 0, as 2 phi_0/A =
 // circ_a V + circ_b (T_N + N q_0 + N 2^32 dn), and then split as above.
+// wall_dn: Ctl::wall_dn, loaded by the caller at the start of the launch.
 __device__ static double block_field_f32(const Dev& d, const unsigned long long* qe, const unsigned long long* qi,
-                                         float* sE, const StepArgs& a)
+                                         float* sE, const StepArgs& a, long long wall_dn)
 {
     __shared__ long long s_wacc[32], s_wbhi[32];
     __shared__ unsigned long long s_wblo[32];
@@ -223,7 +224,7 @@ __device__ static double block_field_f32(const Dev& d, const unsigned long long*
     double v_el = a.v_left;
     if (mode == kFieldCircuit) {
         const long long q0 = (long long)(qi[0] - qe[0]);
-        const __int128 X = TN + (__int128)N * q0 + ((__int128)N << 32) * (__int128)d.ctl->wall_dn;
+        const __int128 X = TN + (__int128)N * q0 + ((__int128)N << 32) * (__int128)wall_dn;
         const double va = d.circ_a * a.v_left + d.circ_b * i128_to_double(X);
         v_el = 0.5 * d.A * va;
         if (fabs(va) < 4.0e18) {
