@@ -483,7 +483,8 @@ int pic_server_forget(pic_server* s, int64_t id);
 /* Counters of the server (host struct); PIC_ERR_CUDA if the worker stopped
  * on a device error (every running request then FAILED). */
 int pic_server_status(pic_server* s, pic_server_stats* out);
-/* Stop the worker (running requests are abandoned) and free everything. */
+/* Stop the worker (running requests are abandoned) and free everything.  No
+ * other pic_server_* call on s may be running or start while it runs. */
 void pic_server_destroy(pic_server* s);
 
 const char* pic_strerror(int code);

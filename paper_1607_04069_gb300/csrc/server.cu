@@ -42,6 +42,7 @@ struct Request {
     pic_params p;
     pic_request_info info;
     long long steps = 0;                 // steps run since admission
+    long long period = 0;                // steps per RF period of this discharge
     int slot = -1;                       // batch slot (batched mode)
     pic_ctx* ctx = nullptr;              // the discharge while it runs
     std::vector<double> prev[2];         // previous window's n_e, n_i
@@ -90,7 +91,8 @@ struct pic_server {
     std::vector<Request*> running;       // touched by the worker only
     int64_t next_id = 1;
     int64_t bytes_used = 0;
-    long long period = 0, chunk = 0;     // steps per RF period and per worker chunk
+    long long period = 0, chunk = 0;     // steps per RF period of the first admitted request, and
+                                         // per worker chunk (a divisor of every admitted period)
     bool stop = false;
     std::string fatal;
     pic_server_stats st;
@@ -146,6 +148,7 @@ bool admit(pic_server* S, Request* r)
         finish(S, r, PIC_REQ_FAILED, why, false);
         return false;
     }
+    r->period = P;
     if (S->period == 0) {
         S->period = P;
         const int de = r->p.diag_every > 0 ? r->p.diag_every : 1;
@@ -272,7 +275,7 @@ void work(pic_server* S)
             r->steps += S->chunk;
             int state = PIC_REQ_RUNNING;
             std::string err;
-            if (r->steps % S->period == 0) state = period_check(S, r, &err);
+            if (r->steps % r->period == 0) state = period_check(S, r, &err);
             if (state == PIC_REQ_RUNNING) {
                 keep.push_back(r);
                 continue;

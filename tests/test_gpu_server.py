@@ -36,11 +36,11 @@ def _cfg(n, seed, **over):
     return c
 
 
-def _alone(cfg, periods, window=1):
+def _alone(cfg, periods, window=1, period=PERIOD):
     d = gpu_discharge(cfg)
     out = None
     for p in range(periods):
-        d.step(PERIOD)
+        d.step(period)
         if (p + 1) % window == 0:
             out = {k: d.diag(k) for k in ("n_e", "n_i", "phi")}
             d.reset_averages()
@@ -108,5 +108,21 @@ def test_averaging_windows_of_two_periods(P):
     s.close()
     assert info["state"] == "max_periods" and info["periods"] == 4 and info["change"] > 0.0
     want = _alone(c, 4, window=2)
+    for k in ("n_e", "n_i", "phi"):
+        assert np.array_equal(got[k], want[k]), k
+
+
+def test_plain_loop_checks_each_request_at_its_own_period(P):
+    """Without batching, discharges whose RF periods differ in steps share the
+    worker (the chunk divides both); each is tested at its own period ends."""
+    a = _cfg(4_000, 61)
+    b = _cfg(4_000, 62, dt=W.T_RF / (2 * PERIOD))
+    s = P.Server(batched=0, max_periods=2, tol=1e-12)
+    ra, rb = s.submit(P.params_from_workload(a)), s.submit(P.params_from_workload(b))
+    ia, ib = s.wait(ra, timeout=120.0), s.wait(rb, timeout=120.0)
+    got = {k: s.result(rb, k) for k in ("n_e", "n_i", "phi")}
+    s.close()
+    assert ia["state"] == ib["state"] == "max_periods" and ia["periods"] == ib["periods"] == 2
+    want = _alone(b, 2, period=2 * PERIOD)
     for k in ("n_e", "n_i", "phi"):
         assert np.array_equal(got[k], want[k]), k
