@@ -168,6 +168,24 @@ def workload(n_per_species, seed):
     return cfg
 
 
+def extra_launches(cfg, h):
+    """Kernels pic_step launches after the step kernel of host step h: a
+    compaction (three kernels) of each species whose period ends there, and
+    the coupled test-particle step (plus its own compaction) every tp_every
+    steps."""
+    n, h1 = 0, h + 1
+    for every in (cfg.get("sort_every_e", 0), cfg.get("sort_every_i", 0)):
+        if every > 0 and h1 % every == 0:
+            n += 3
+    te = cfg.get("tp_every", 0)
+    if cfg.get("sputter_enable", 0) and te > 0 and h1 % te == 0:
+        n += 1
+        ste = cfg.get("sort_every_tp", 0)
+        if ste > 0 and (h1 // te) % ste == 0:
+            n += 3
+    return n
+
+
 def oracle_rate(cfg, n_sample, steps, warmup=1):
     """FP64 oracle on a sample of the same discharge: n_sample superparticles
     per species with the weight scaled so the density is unchanged."""
@@ -479,7 +497,9 @@ def main():
     clean = torch.ones(64 * 2**20, dtype=torch.int32, device="cuda")
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    d.timing(True)
+    # the library's per-launch timers stay off here: their event records would
+    # add to every timed step; the step kernel's launch time is read from the
+    # per-step events of the steps that launch nothing else
     with Clocks(local) as clk:
         barrier(ws)
         torch.cuda.synchronize()
@@ -494,11 +514,26 @@ def main():
         barrier(ws)
         wall = time.perf_counter() - t0
     d.sync()
-    step_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    mover_ms, mover_n = d.kernel_time("step")
+    times = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    step_ms = sum(times)
+    extra = [extra_launches(cfg, args.warmup + k) for k in range(args.steps)]
+    alone = [t for t, x in zip(times, extra) if x == 0]
+    mover_ms, mover_n = sum(alone), len(alone)
+    launches = args.steps + sum(extra)
+    # the library's timers on a further 400 steps (one compaction of each
+    # species, ten test-particle steps): the compaction and TP launch times,
+    # and a check of the launch schedule counted above
+    d.timing(True)
+    d.step(400)
+    d.sync()
+    _, chk_mover = d.kernel_time("step")
     tp_ms, tp_n = d.kernel_time("tp")
     cmp_ms, cmp_n = d.kernel_time("compact")
     d.timing(False)
+    h0 = args.warmup + args.steps
+    want = sum(extra_launches(cfg, h0 + k) for k in range(400))
+    if chk_mover != 400 or tp_n + 3 * cmp_n != want:
+        raise RuntimeError(f"launch schedule: {tp_n} TP and {cmp_n} compaction launches, {want} kernels expected")
     n_end = sum(len(d.get_species(s)["id"]) for s in (0, 1))
     psteps_local = 0.5 * (n_start + n_end) * args.steps
     t_max = allreduce_max(step_ms, ws)
@@ -560,7 +595,6 @@ def main():
                "sample": f"{n_sample}+{n_sample} superparticles of the same discharge, "
                          f"{nst} full PIC/MCC steps in {dt:.1f} s"}
     clocks = clk.summary()
-    launches = mover_n + tp_n + 3 * cmp_n
     rows = None
     if rank == 0 and not args.no_rows:
         rows = measure_rows(d, cfg, peak, cmp_ms, cmp_n, 0.25 * (n_start + n_end), args.tp_atoms)
@@ -577,11 +611,14 @@ def main():
                            "n_cells": cfg["n_cells"], "sort_every": [400, 400], "tp_every": 40,
                            "parallelism": f"replicas x{ws}" if ws > 1 else "1 gpu",
                            "l2": "flushed before every timed step (512 MiB write, then a 256 MiB "
-                                 "read); value from per-step CUDA events",
+                                 "read); value from per-step CUDA events; the step kernel's launch "
+                                 "time from those of the steps that launch nothing else",
                            "wall_s_incl_flush": wall},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": int(launches), "rows": rows,
-                "kernel_ms": {"step": mover_ms, "tp": tp_ms, "compact": cmp_ms}}
+                "kernel_us": {"step_alone_mean": mover_ms / max(mover_n, 1) * 1e3, "steps_alone": mover_n,
+                              "tp_mean": tp_ms / max(tp_n, 1) * 1e3,
+                              "compact_mean": cmp_ms / max(cmp_n, 1) * 1e3}}
         print(json.dumps(line), flush=True)
     d.close()
     if ws > 1:
