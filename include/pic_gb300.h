@@ -406,10 +406,11 @@ void pic_batch_destroy(pic_batch* b);
  * periods have run and the relative change of both from the window before
  * is below tol, the request completes with state CONVERGED (or MAX_PERIODS
  * when max_periods > 0 periods have run), its last window-averaged n_e, n_i
- * and phi are kept on the host and its device state is released.  Requests follow the pic_batch rules
- * (32-bit positions, one dt and diag_every, a whole number of steps per RF
- * period that is a multiple of the chunk); others complete as FAILED, and a
- * state larger than the whole budget as REJECTED.  The change is that of
+ * and phi are kept on the host and its device state is released.  Every
+ * request needs a whole number of steps per RF period, a multiple of the
+ * chunk set by the first admitted request; batched, it also follows the
+ * pic_batch rules (32-bit positions, one dt and diag_every).  Others
+ * complete as FAILED, and a state larger than the whole budget as REJECTED.  The change is that of
  * the inventory, the spatial integral of the density (criterion
  * PIC_STEADY_INVENTORY, the default: in steady state generation and losses
  * balance, Sec. "Simulation Results"), or of the profile in L2 over the
