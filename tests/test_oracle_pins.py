@@ -395,6 +395,42 @@ def test_sputter_births_per_impact(E_ion, Y):
     assert (tp["vx"] > 0).all() and (Es <= Lam * E_ion * (1 + 1e-12)).all()
 
 
+def test_impact_and_energy_histograms_place_known_particles():
+    """Ion impacts (Sec. 'Wall Interactions': energy 1/2 M |v|^2 and angle to
+    the electrode normal, at the electrode reached; IEDF on [0, 2 V0] in 512
+    bins, IEADF 128 x 90 one-degree bins) and the EEDF (electrons in the
+    central 10 % of the gap, 0.25 eV bins) put particles of chosen energy and
+    angle in the bins those values name.  At step 0 the source voltage is 0
+    and zero weight leaves no space charge, so nothing accelerates them."""
+    N, L, V0 = 128, 0.025, 100.0
+    dt = 1.0 / 13.56e6 / 400
+    orc = O.Oracle(prm(L=L, ncell=N, dt=dt, V0=V0), 8, 8)
+    Ei = np.array([10.3, 55.6, 149.2, 199.7])             # eV
+    th = np.array([0.4, 30.5, 60.2, 88.7])                # degrees from the normal
+    sp = np.sqrt(2 * Ei * QE / MAR)
+    out = np.array([-1.0, -1.0, 1.0, 1.0])                # toward x = 0, x = 0, x = L, x = L
+    xi = np.where(out < 0, 1e-4, N - 1e-4)                # within one step of the electrode
+    load(orc, 1, xi, [out * sp * np.cos(np.radians(th)), sp * np.sin(np.radians(th)), 0 * sp])
+    Ee = np.array([0.6, 7.3, 33.1, 63.9, 12.0])           # the last one outside the window
+    ve = np.sqrt(2 * Ee * QE / ME)
+    load(orc, 0, np.array([64.0, 60.0, 66.5, 69.9, 0.3 * N]), [0 * ve, 0.6 * ve, 0.8 * ve])
+    orc.step(1)
+    c = orc.counters()
+    assert c["imp_i_l"] == 2 and c["imp_i_r"] == 2 and c["imp_e_l"] == c["imp_e_r"] == 0
+    want_iedf = {"l": [26, 142], "r": [381, 511]}          # floor(E / 200 eV * 512)
+    want_ieadf = {"l": [(6, 0), (35, 30)], "r": [(95, 60), (127, 88)]}   # floor(E / 200 * 128), floor(theta)
+    for side in "lr":
+        h = orc.diag("iedf_" + side)
+        assert h.shape == (512,) and h.sum() == 2
+        assert sorted(np.nonzero(h)[0].tolist()) == want_iedf[side]
+        h2 = orc.diag("ieadf_" + side).reshape(128, 90)
+        assert h2.sum() == 2
+        assert sorted(zip(*[a.tolist() for a in np.nonzero(h2)])) == want_ieadf[side]
+    e = orc.diag("eedf")
+    assert e.shape == (256,) and e.sum() == 4
+    assert np.nonzero(e)[0].tolist() == [2, 29, 132, 255]  # floor(E / 0.25 eV)
+
+
 def test_thompson_cosine_distributions():
     """Sputtered-atom launch: energy follows the truncated Thompson CDF
     (E/(E+Ub))^2 / (Emax/(Emax+Ub))^2; cos(theta) law gives <cos theta> = 2/3
