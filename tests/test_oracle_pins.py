@@ -546,6 +546,28 @@ def test_density_diagnostic_normalisation():
     assert abs(ne[N] / 1e15 - 1) < 5 / math.sqrt(per / 2)
 
 
+def test_flux_diagnostic_is_density_times_drift():
+    """The particle flux profile (Sec. 'Simulation Results') is the time
+    average of n <v_x>: with every electron drifting at u through a
+    field-free gap, Gamma = n u at every node, exactly up to the weights'
+    2^-32 rounding, at every node -- the depleted upstream electrode and the
+    half-volume ends included -- and for either sign of u."""
+    n, N, L, dt = 100_000, 64, 0.02, 1e-11
+    w = 1e15 * L / n
+    rng = np.random.default_rng(31)
+    for u in (2.0e5, -3.0e5):
+        orc = O.Oracle(prm(L=L, ncell=N, w=w, dt=dt), n, 1)
+        vt = rng.standard_normal((2, n)) * 1e5
+        load(orc, 0, rng.uniform(0.0, N, n), [np.full(n, u), vt[0], vt[1]])
+        for _ in range(5):
+            orc.set_field(np.zeros(N + 1))
+            orc.step(1)
+        ne, ge = orc.diag("n_e"), orc.diag("gamma_e")
+        assert (ne > 0).all()
+        assert np.allclose(ge, ne * u, rtol=1e-8, atol=0)
+        assert orc.counters()["imp_e_l" if u < 0 else "imp_e_r"] > 0
+
+
 # ------------------------------------------------------------------ source waveform and external circuit
 def test_two_harmonic_waveform_extremes_and_mean():
     """Sec. 'Simulation Scenario': V0 [cos(wt + phase) + cos(2wt)] with phase
