@@ -568,6 +568,23 @@ def test_flux_diagnostic_is_density_times_drift():
         assert orc.counters()["imp_e_l" if u < 0 else "imp_e_r"] > 0
 
 
+def test_time_averaged_vacuum_potential_closed_form():
+    """Time-averaged potential (Sec. 'Simulation Results'; reading: the
+    average of the states after steps 1 ... n): in an empty gap the solution
+    of Eq. poisson is the vacuum profile V(t)(1 - x/L), so the average is
+    (1 - x/L) V0 sum_{l=1..n} sin(l th) / n, th = 2 pi f dt, and the sine sum
+    has the closed form sin(n th/2) sin((n+1) th/2) / sin(th/2)."""
+    P, f, V0, N = 400, 13.56e6, 100.0, 16
+    th = 2 * math.pi / P
+    for n in (1, 37, 100, 400):
+        orc = O.Oracle(prm(V0=V0, f=f, dt=1.0 / f / P, ncell=N, L=0.02), 1, 1)
+        orc.field()
+        orc.step(n)
+        mean_sin = math.sin(n * th / 2) * math.sin((n + 1) * th / 2) / math.sin(th / 2) / n
+        want = (1.0 - np.arange(N + 1) / N) * V0 * mean_sin
+        assert np.allclose(orc.diag("phi"), want, rtol=0, atol=1e-9 * V0)
+
+
 # ------------------------------------------------------------------ source waveform and external circuit
 def test_two_harmonic_waveform_extremes_and_mean():
     """Sec. 'Simulation Scenario': V0 [cos(wt + phase) + cos(2wt)] with phase
