@@ -511,6 +511,40 @@ def test_tp_thermalizes_to_gas_temperature():
         assert abs((tp[comp]**2).mean() / ref - 1) < 0.03
 
 
+def test_tp_deposition_histograms_and_grid_moments():
+    """TP diagnostics (Sec. 'Wall Interactions' and 'Limitations and
+    Constraints' of the TPM): an atom that reaches an electrode is binned by
+    its energy 1/2 M_Al |v|^2 (0.5 eV bins on [0, 300)) and its angle to the
+    normal (1-degree bins) at that electrode; the grid moments of the atoms
+    in flight give a mean-velocity moment equal to density times a uniform
+    drift, and the density w n / L of a uniform load.  No gas: no collision."""
+    N, L, w, dt = 32, 0.02, 1e12, 1e-9
+    E = np.array([1.3, 47.6, 299.9, 12.2, 150.1])          # eV
+    th = np.array([2.5, 45.3, 80.1, 10.7, 70.7])           # degrees from the normal
+    out = np.array([1.0, 1.0, 1.0, -1.0, -1.0])            # three toward x = L, two toward x = 0
+    sp = np.sqrt(2 * E * QE / MAL)
+    n, u = 200_000, 500.0
+    rng = np.random.default_rng(41)
+    xi = np.concatenate([np.where(out > 0, N - 1e-4, 1e-4), rng.uniform(0.1, N - 0.1, n)])
+    vx = np.concatenate([out * sp * np.cos(np.radians(th)), np.full(n, u)])
+    vy = np.concatenate([sp * np.sin(np.radians(th)), rng.standard_normal(n) * 300.0])
+    orc = O.Oracle(prm(L=L, ncell=N, w=w, p=0.0), 1, 1, n + 8)
+    load(orc, 2, xi, [vx, vy, 0 * vy])
+    orc.tp_step(3, dt)
+    c = orc.counters()
+    assert c["tp_dep_r"] == 3 and c["tp_dep_l"] == 2 and c["tp_coll"] == 0
+    for side, bins, angs in (("r", [2, 95, 599], [2, 45, 80]), ("l", [24, 300], [10, 70])):
+        he, ha = orc.diag("sputter_e_" + side), orc.diag("sputter_ang_" + side)
+        assert he.shape == (600,) and ha.shape == (90,)
+        assert np.nonzero(he)[0].tolist() == bins and he.sum() == len(bins)
+        assert np.nonzero(ha)[0].tolist() == angs and ha.sum() == len(angs)
+    dens, mom = orc.diag("tp_dens"), orc.diag("tp_vx")
+    assert (dens > 0).all()
+    assert np.allclose(mom, dens * u, rtol=1e-12, atol=0)
+    n0 = w * n / (L * (N - 0.2) / N)                       # the loaded span is (0.1, N - 0.1) cells
+    assert abs(dens[2:N - 1].mean() / n0 - 1) < 4 / math.sqrt(n)
+
+
 # ------------------------------------------------------------------ conservation, diagnostics
 def test_charge_and_particle_conservation_over_steps():
     """Every step: sum of deposits = 2^32 x alive particles per species;
