@@ -366,6 +366,33 @@ def test_inelastic_bookkeeping_at_50eV():
     assert np.isin(i["xi"], e["xi"][:n]).all()
 
 
+def test_ionisation_products():
+    """Ionisation (Sec. 'Particle Collisions'): the energy left after the
+    15.8 eV threshold is shared by the scattered and the ejected electron,
+    the ejected one's share uniform on [0, eps - 15.8]; the new ion is drawn
+    from the gas Maxwellian (each velocity component normal with variance
+    k_B T_g / M_Ar) at the parent's position."""
+    rng = np.random.default_rng(35)
+    n, dt, eps, Tg = 200_000, 2e-10, 50.0, 300.0
+    orc = O.Oracle(prm(L=1.0, ncell=1024, p=3.0, Tg=Tg, dt=dt), 2 * n, n)
+    load(orc, 0, np.full(n, 512.25), _mono(n, math.sqrt(2 * eps * QE / ME), rng))
+    orc.step(1)
+    e, i = orc.get_species(0), orc.get_species(1)
+    k = orc.counters()["ionizations"]
+    assert k > 2000 and len(i["xi"]) == k
+    Ee = 0.5 * ME * (e["vx"]**2 + e["vy"]**2 + e["vz"]**2) / QE
+    ej = Ee[n:]                                               # the ejected electrons, in birth order
+    assert stats.kstest(ej / (eps - 15.8), "uniform").pvalue > 1e-3
+    # each parent sits at its child's position and carries the rest of the energy
+    par = {x: Ee[j] for j, x in enumerate(e["xi"][:n])}
+    pairs = np.array([par[x] + ej[m] for m, x in enumerate(e["xi"][n:])])
+    assert np.allclose(pairs, eps - 15.8, rtol=1e-5)
+    sig = math.sqrt(KB * Tg / MAR)
+    for c in ("vx", "vy", "vz"):
+        assert stats.kstest(i[c] / sig, "norm").pvalue > 1e-3
+    assert abs(np.mean(i["vx"]**2 + i["vy"]**2 + i["vz"]**2) / (3 * sig**2) - 1) < 5 * math.sqrt(2 / (3 * k))
+
+
 # ------------------------------------------------------------------ walls and sputtering
 def test_sputter_yield_values():
     assert O.sputter_yield(30.0) == 0.0 and O.sputter_yield(10.0) == 0.0
