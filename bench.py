@@ -17,6 +17,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -166,6 +167,20 @@ def workload(n_per_species, seed):
     # costs time
     cfg.update(sort_every_e=400, sort_every_i=400, sort_every_tp=50)
     return cfg
+
+
+def host_cpu():
+    """The host the CPU baseline ran on: logical CPUs and model name."""
+    model = platform.machine()
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"host_cpus": os.cpu_count(), "cpu_model": model}
 
 
 def extra_launches(cfg, h):
@@ -447,7 +462,7 @@ def run_reference(args, ws, rank):
             "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": cfg["name"], "particles": 2 * n_sample, "n_cells": cfg["n_cells"]},
-            "cpu_baseline": {"value": rate, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": rate, "unit": "particle-steps/s", "cores": 1, "kind": "oracle", **host_cpu(),
                              "sample": f"{n_sample}+{n_sample} superparticles of the same discharge "
                                        f"(weight x{cfg['n_e0'] / n_sample:g}), {args.steps} full steps"},
             "e2e": {"value": rate, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
@@ -591,7 +606,7 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         n_sample, nst = cfg["n_e0"], 400            # the full discharge, 400 steps: some 10-20 s
         rate, dt = oracle_rate(cfg, n_sample, nst)
-        cpu = {"value": rate, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+        cpu = {"value": rate, "unit": "particle-steps/s", "cores": 1, "kind": "oracle", **host_cpu(),
                "sample": f"{n_sample}+{n_sample} superparticles of the same discharge, "
                          f"{nst} full PIC/MCC steps in {dt:.1f} s"}
     clocks = clk.summary()
