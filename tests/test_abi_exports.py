@@ -60,3 +60,16 @@ def test_ctypes_structs_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """Without the built engine the binding raises instead of falling back
+    to anything else: every entry point goes through lib()."""
+    import pytest
+    import paper_1607_04069_gb300 as P
+    monkeypatch.setattr(P, "_lib", None)
+    monkeypatch.setattr(P, "LIB_PATH", os.path.join(ROOT, "no-such-dir", "libpic_gb300.so"))
+    with pytest.raises(ImportError, match="missing"):
+        P.lib()
+    with pytest.raises(ImportError):
+        P.default_params()
