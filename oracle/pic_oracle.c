@@ -618,12 +618,19 @@ void orc_counters(const orc_state *S, int64_t *out)
 }
 
 /* ======================= the PIC/MCC step ================================ */
+/* bin of x on [0, xmax) in nb bins; below the range the first bin, at or
+ * above it the last (the scaled value is clamped before the conversion) */
+static int bin_of(double x, double xmax, int nb)
+{
+    double t = x / xmax * (double)nb;
+    if (!(t < (double)nb)) return nb - 1;
+    if (!(t >= 0.0)) return 0;
+    return (int)t;
+}
+
 static void hist_add(int64_t *h, int nb, double x, double xmax)
 {
-    int b = (int)(x / xmax * (double)nb);
-    if (b < 0) b = 0;
-    if (b > nb - 1) b = nb - 1;
-    h[b]++;
+    h[bin_of(x, xmax, nb)]++;
 }
 
 /* sputter launch at an ion impact (Sec. "Wall Interactions" of the TPM):
@@ -754,10 +761,9 @@ static void wall_ion(orc_state *S, int64_t k, uint32_t l, int electrode)
     double ct = v2 > 0.0 ? fabs(p->vx[k]) / sqrt(v2) : 1.0;
     if (ct > 1.0) ct = 1.0;
     double th = acos(ct) * 180.0 / O_PI;
-    double emax = 2.0 * S->P.V0;
+    double emax = S->P.V0 > 0.0 ? 2.0 * S->P.V0 : 1.0;   /* [0, 2 V0]; [0, 1 eV] without a source */
     hist_add(S->iedf[electrode], NB_IEDF, E, emax);
-    int be = (int)(E / emax * NB_IEADF_E);
-    if (be > NB_IEADF_E - 1) be = NB_IEADF_E - 1;
+    int be = bin_of(E, emax, NB_IEADF_E);
     int ba = (int)th;
     if (ba > NB_ANG - 1) ba = NB_ANG - 1;
     S->ieadf[electrode][be * NB_ANG + ba]++;
@@ -1209,7 +1215,7 @@ void orc_hypotheses(const orc_state *S, double out[6])
     double *buf = (double *)malloc(sizeof(double) * (NB_IEADF_E * NB_ANG + N + 1));
     for (int el = 0; el < 2; el++) {
         orc_diag(S, 6 + el, buf, NB_IEDF);
-        out[el] = orc_width_to_peak(buf, NB_IEDF, 2.0 * S->P.V0);
+        out[el] = orc_width_to_peak(buf, NB_IEDF, S->P.V0 > 0.0 ? 2.0 * S->P.V0 : 1.0);
         orc_diag(S, 8 + el, buf, NB_IEADF_E * NB_ANG);
         double ang[NB_ANG];
         for (int b = 0; b < NB_ANG; b++) ang[b] = 0.0;
