@@ -306,10 +306,11 @@ int pic_op_poisson(const int64_t* q_i, const int64_t* q_e, int32_t n_cells, doub
  *                  not overlap the inputs;
  *   n_out          device int64 receiving the number kept, or NULL;
  *   stream         cudaStream_t as void*, NULL = legacy default stream.
- * The work runs asynchronously on `stream`.  The first call on each device
- * looks up the scratch array's address with that device current
- * (cudaGetSymbolAddress), which loads the library's kernels there; make that
- * first call before any stream capture.  All calls share the one scratch
+ * The work runs asynchronously on `stream`.  Every call looks up the scratch
+ * array's address with the current device (cudaGetSymbolAddress), so a
+ * device reset between calls is harmless; the first call on a device also
+ * loads the library's kernels there, so make it before any stream capture.
+ * All calls share the one scratch
  * array: each call clears the counts it uses, and calls whose work may
  * overlap on the GPU (other streams, other host threads) race on it, so the
  * caller must order them. */

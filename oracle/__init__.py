@@ -62,7 +62,7 @@ class Params(C.Structure):
                 ("sputter", C.c_int32), ("tp_every", C.c_int32), ("diag_every", C.c_int32),
                 ("waveform", C.c_int32), ("circuit", C.c_int32), ("phase", C.c_double), ("cb", C.c_double),
                 ("dref", C.c_double), ("omega", C.c_double), ("tref", C.c_double), ("tp_model", C.c_int32),
-                ("pad", C.c_int32)]
+                ("coll_mode", C.c_int32)]
 
 
 def _p(a):

@@ -117,7 +117,9 @@ typedef struct {
     double dref, omega, tref;     /* TP models 1, 2: VHS reference diameter (m), viscosity index,
                                      reference temperature (K) of the Al-Ar pair   */
     int32_t tp_model;             /* TP collisions: 0 hard sphere (sigma_tp), 1 VHS, 2 M1 */
-    int32_t pad;
+    int32_t coll_mode;            /* null-collision candidates of e- and Ar+: 0 geometric gaps
+                                     between candidates (orc_gap), 1 the paper's literal test,
+                                     a fresh R <= P_c,tot every step                   */
 } orc_params;
 
 typedef struct {
@@ -343,13 +345,18 @@ static double charge_of(int s) { return s == SP_E ? -O_QE : (s == SP_I ? O_QE : 
 
 /* Null-collision candidates (Sec. "Particle Collisions"): every step a
  * particle is a candidate with the fixed probability P_c,tot = 1 -
- * exp(-nu_max dt), independently of the other steps.  The number of steps
- * from one candidate to the next is then geometric, P(gap = n) =
- * exp(-nu_max dt (n-1)) (1 - exp(-nu_max dt)), and it is drawn as the free
- * flight time of Sec. "Kinetic Particle Simulation", tau = -tau_c ln R with
- * tau_c = 1 / nu_max, counted in steps and rounded up:
- *     gap = 1 + floor(-ln R / (nu_max dt)).
- * Each particle keeps the step of its next candidate. */
+ * exp(-nu_max dt), independently of the other steps.  Two equivalent
+ * procedures are kept:
+ *  - coll_mode 1, the paper's own: each step draws R = Philox(id, l, COLL)
+ *    word 0 and the particle is a candidate iff R < P_c,tot;
+ *  - coll_mode 0: the number of steps from one candidate to the next is
+ *    geometric, P(gap = n) = exp(-nu_max dt (n-1)) (1 - exp(-nu_max dt)), and
+ *    is drawn as the free flight time of Sec. "Kinetic Particle Simulation",
+ *    tau = -tau_c ln R with tau_c = 1 / nu_max, counted in steps and rounded
+ *    up: gap = 1 + floor(-ln R / (nu_max dt)).  Each particle keeps the step
+ *    of its next candidate.
+ * A candidate then uses the same words in both: Philox(id, l, COLL) words 1-3
+ * for the process and the scattering direction. */
 uint32_t orc_gap(double lam, uint32_t w)
 {
     double x = -log(u23(w)) / lam;
@@ -664,11 +671,17 @@ static void sputter(orc_state *S, uint64_t ion_id, uint32_t l, double E, int ele
 static void mcc_electron(orc_state *S, int64_t k, uint32_t l)
 {
     orc_sp *p = &S->sp[SP_E];
-    if (p->nev[k] != l) return;                              /* not a candidate */
-    uint32_t c[4], cg[4];
-    draw(S->P.seed, p->id[k], l, PUR_COLL, c);
-    draw(S->P.seed, p->id[k], l, PUR_GAP, cg);
-    p->nev[k] = l + orc_gap(S->lam[SP_E], cg[0]);
+    uint32_t c[4];
+    if (S->P.coll_mode == 1) {                               /* the literal per-step test */
+        draw(S->P.seed, p->id[k], l, PUR_COLL, c);
+        if (!(u23(c[0]) < S->p_max_e)) return;               /* not a candidate */
+    } else {
+        if (p->nev[k] != l) return;                          /* not a candidate */
+        uint32_t cg[4];
+        draw(S->P.seed, p->id[k], l, PUR_COLL, c);
+        draw(S->P.seed, p->id[k], l, PUR_GAP, cg);
+        p->nev[k] = l + orc_gap(S->lam[SP_E], cg[0]);
+    }
     double v2 = p->vx[k] * p->vx[k] + p->vy[k] * p->vy[k] + p->vz[k] * p->vz[k];
     double v = sqrt(v2);
     double eps = 0.5 * O_ME * v2 / O_QE;
@@ -720,11 +733,17 @@ static void mcc_electron(orc_state *S, int64_t k, uint32_t l)
 static void mcc_ion(orc_state *S, int64_t k, uint32_t l)
 {
     orc_sp *p = &S->sp[SP_I];
-    if (p->nev[k] != l) return;                              /* not a candidate */
-    uint32_t c[4], cn[4];
-    draw(S->P.seed, p->id[k], l, PUR_COLL, c);
-    draw(S->P.seed, p->id[k], l, PUR_GAP, cn);
-    p->nev[k] = l + orc_gap(S->lam[SP_I], cn[0]);
+    uint32_t c[4];
+    if (S->P.coll_mode == 1) {                               /* the literal per-step test */
+        draw(S->P.seed, p->id[k], l, PUR_COLL, c);
+        if (!(u23(c[0]) < S->p_max_i)) return;               /* not a candidate */
+    } else {
+        if (p->nev[k] != l) return;                          /* not a candidate */
+        uint32_t cn[4];
+        draw(S->P.seed, p->id[k], l, PUR_COLL, c);
+        draw(S->P.seed, p->id[k], l, PUR_GAP, cn);
+        p->nev[k] = l + orc_gap(S->lam[SP_I], cn[0]);
+    }
     uint32_t cg[4];
     draw(S->P.seed, p->id[k], l, PUR_GAS, cg);
     double n1, n2, n3, n4;

@@ -484,27 +484,53 @@ class Server:
 
 
 # ------------------------------------------------------------------ stateless ops (torch buffers)
+def _cuda_operands(tensors, names):
+    """Every operand a contiguous tensor on one CUDA device; returns that device."""
+    dev = None
+    for t, name in zip(tensors, names):
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if t.device.type != "cuda":
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if dev is None:
+            dev = t.device
+        elif t.device != dev:
+            raise ValueError(f"{name} is on {t.device}, the other operands on {dev}")
+    return dev
+
+
 def op_deposit(pos, n_cells: int, q=None, stream=None):
     """Linear charge assignment of device positions ``pos`` (torch uint32 /
     int32 fixed point or float64 cell units) into int64 ``q`` (returned)."""
     import torch
+    if pos.dtype not in (torch.int32, torch.uint32, torch.float64):
+        raise ValueError("pos must be int32/uint32 (fixed point) or float64 (cell units)")
     prec = 64 if pos.dtype == torch.float64 else 32
     if q is None:
         q = torch.zeros(n_cells + 1, dtype=torch.int64, device=pos.device)
-    _check(lib().pic_op_deposit(C.c_void_p(pos.data_ptr()), prec, pos.numel(), int(n_cells),
-                                C.c_void_p(q.data_ptr()), C.c_void_p(_stream_handle(stream))))
+    if q.dtype != torch.int64 or q.numel() < n_cells + 1:
+        raise ValueError("q must be an int64 tensor of at least n_cells + 1 elements")
+    dev = _cuda_operands((pos, q), ("pos", "q"))
+    with torch.cuda.device(dev):
+        _check(lib().pic_op_deposit(C.c_void_p(pos.data_ptr()), prec, pos.numel(), int(n_cells),
+                                    C.c_void_p(q.data_ptr()), C.c_void_p(_stream_handle(stream))))
     return q
 
 
 def op_poisson(q_i, q_e, n_cells: int, dx: float, weight: float, v_left: float, stream=None):
     """Field solve from device int64 node counts; returns (phi, E) float64 tensors."""
     import torch
-    phi = torch.empty(n_cells + 1, dtype=torch.float64, device=q_i.device)
+    for name, q in (("q_i", q_i), ("q_e", q_e)):
+        if q.dtype != torch.int64 or q.numel() < n_cells + 1:
+            raise ValueError(f"{name} must be an int64 tensor of at least n_cells + 1 elements")
+    dev = _cuda_operands((q_i, q_e), ("q_i", "q_e"))
+    phi = torch.empty(n_cells + 1, dtype=torch.float64, device=dev)
     E = torch.empty_like(phi)
-    _check(lib().pic_op_poisson(C.c_void_p(q_i.data_ptr()), C.c_void_p(q_e.data_ptr()),
-                                int(n_cells), float(dx), float(weight), float(v_left),
-                                C.c_void_p(phi.data_ptr()), C.c_void_p(E.data_ptr()),
-                                C.c_void_p(_stream_handle(stream))))
+    with torch.cuda.device(dev):
+        _check(lib().pic_op_poisson(C.c_void_p(q_i.data_ptr()), C.c_void_p(q_e.data_ptr()),
+                                    int(n_cells), float(dx), float(weight), float(v_left),
+                                    C.c_void_p(phi.data_ptr()), C.c_void_p(E.data_ptr()),
+                                    C.c_void_p(_stream_handle(stream))))
     return phi, E
 
 
@@ -516,12 +542,29 @@ def op_sort_noalloc(pos, vx, vy, vz, ids, n_cells: int, pos_out, vx_out, vy_out,
     number of particles kept.  Calls whose work may overlap on the GPU race on
     the shared scratch and must be ordered by the caller."""
     import torch
+    if pos.dtype not in (torch.int32, torch.uint32, torch.float64):
+        raise ValueError("pos must be int32/uint32 (fixed point) or float64 (cell units)")
+    if pos_out.dtype != pos.dtype:
+        raise ValueError("pos_out must have the dtype of pos")
+    for name, a in (("vx", vx), ("vy", vy), ("vz", vz), ("vx_out", vx_out), ("vy_out", vy_out),
+                    ("vz_out", vz_out)):
+        if a.dtype != torch.float32:
+            raise ValueError(f"{name} must be float32")
+    for name, a in (("ids", ids), ("ids_out", ids_out)):
+        if a.dtype not in (torch.int64, torch.uint64):
+            raise ValueError(f"{name} must be a 64-bit integer tensor")
+    if n_out is not None and (n_out.dtype != torch.int64 or n_out.numel() < 1):
+        raise ValueError("n_out must be an int64 tensor of at least one element")
     prec = 64 if pos.dtype == torch.float64 else 32
     n = pos.numel()
     for a in (vx, vy, vz, ids, pos_out, vx_out, vy_out, vz_out, ids_out):
         if a.numel() < n:
             raise ValueError("every particle array needs room for pos.numel() slots")
-    _check(lib().pic_op_sort_noalloc(prec, n, int(n_cells), *[C.c_void_p(a.data_ptr()) for a in
-                                     (pos, vx, vy, vz, ids, pos_out, vx_out, vy_out, vz_out, ids_out)],
-                                     None if n_out is None else C.c_void_p(n_out.data_ptr()),
-                                     C.c_void_p(_stream_handle(stream))))
+    ops = [pos, vx, vy, vz, ids, pos_out, vx_out, vy_out, vz_out, ids_out] + ([] if n_out is None else [n_out])
+    names = ["pos", "vx", "vy", "vz", "ids", "pos_out", "vx_out", "vy_out", "vz_out", "ids_out", "n_out"]
+    dev = _cuda_operands(ops, names)
+    with torch.cuda.device(dev):          # the static scratch of that device
+        _check(lib().pic_op_sort_noalloc(prec, n, int(n_cells), *[C.c_void_p(a.data_ptr()) for a in
+                                         (pos, vx, vy, vz, ids, pos_out, vx_out, vy_out, vz_out, ids_out)],
+                                         None if n_out is None else C.c_void_p(n_out.data_ptr()),
+                                         C.c_void_p(_stream_handle(stream))))

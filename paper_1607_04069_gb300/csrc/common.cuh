@@ -372,6 +372,19 @@ __device__ __forceinline__ float lambda_ar_al()
     return (float)(4.0 * kMAR * kMAL / ((kMAR + kMAL) * (kMAR + kMAL)));
 }
 
+// ---------------------------------------------------------------- histogram bins
+// Bin of an already scaled value t (bin width 1) among nb bins: below the
+// range the first bin, at or above it -- and NaN -- the last.  The value is
+// clamped before the conversion, so no out-of-range float is converted.
+__device__ __forceinline__ int clamp_bin(float t, int nb)
+{
+    if (!(t < (float)nb)) return nb - 1;
+    if (!(t >= 0.0f)) return 0;
+    return (int)t;
+}
+// bin of x on [0, xmax) in nb bins
+__device__ __forceinline__ int hist_bin(float x, float xmax, int nb) { return clamp_bin(x / xmax * (float)nb, nb); }
+
 // ---------------------------------------------------------------- warp deposit
 // Linear weighting of one particle per lane into a shared int64 histogram:
 // node j gets 2^32 - wr, node j+1 gets wr.  Lanes whose cells span at most

@@ -129,8 +129,12 @@ __global__ void k_na_scatter(const PosT* __restrict__ pos, const float* __restri
     }
 }
 
-// The scratch array's device address and the SM count of the current device,
-// looked up on the first call made with that device current.
+// The scratch array's device address and the SM count of the current device.
+// The address is looked up on every call (a host-side query once the
+// library's module is loaded on the device): a device reset or a new primary
+// context reloads the module, and an address kept from before would then
+// point at freed memory.  The first call on a device loads the module, so it
+// should come before any stream capture.  The SM count is kept per ordinal.
 int device_entry(DevEntry* out)
 {
     int dev = -1;
@@ -143,15 +147,15 @@ int device_entry(DevEntry* out)
         set_last_error("device ordinal above the no-alloc sort's device table");
         return PIC_ERR_INVALID_ARG;
     }
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_sort_scratch);
+    if (e != cudaSuccess || !p) {
+        set_last_error(e != cudaSuccess ? cudaGetErrorString(e) : "cudaGetSymbolAddress gave NULL");
+        return PIC_ERR_CUDA;
+    }
     std::lock_guard<std::mutex> lock(g_mu);
     DevEntry& d = g_dev[dev];
-    if (!d.scratch) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_sort_scratch);
-        if (e != cudaSuccess || !p) {
-            set_last_error(e != cudaSuccess ? cudaGetErrorString(e) : "cudaGetSymbolAddress gave NULL");
-            return PIC_ERR_CUDA;
-        }
+    if (d.sms < 1) {
         int sms = 0;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess || sms < 1) {
@@ -159,8 +163,8 @@ int device_entry(DevEntry* out)
             return PIC_ERR_CUDA;
         }
         d.sms = sms;
-        d.scratch = (unsigned int*)p;
     }
+    d.scratch = (unsigned int*)p;
     *out = d;
     return PIC_OK;
 }

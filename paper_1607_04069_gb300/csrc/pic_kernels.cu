@@ -45,9 +45,7 @@ struct BlockTally {            // per-CTA event counts, flushed once per CTA
 
 __device__ __forceinline__ void hist_add(unsigned long long* h, int nb, float x, float xmax)
 {
-    int b = (int)(x / xmax * (float)nb);
-    b = b < 0 ? 0 : (b > nb - 1 ? nb - 1 : b);
-    atomicAdd(&h[b], 1ull);
+    atomicAdd(&h[hist_bin(x, xmax, nb)], 1ull);
 }
 
 // value that marks a removed slot
@@ -191,10 +189,8 @@ __device__ __noinline__ void ev_ion_wall(const Dev& d, uint64_t id, uint32_t l, 
     const float ct = fminf(v2 > 0.0f ? fabsf(vx) * rsqrtf(v2) : 1.0f, 1.0f);
     const float th = acosf(ct) * (float)(180.0 / kPI);
     hist_add(d.diag.iedf[el], kNbIedf, E, d.Emax_hist);
-    int be = (int)(E / d.Emax_hist * (float)kNbIeadfE);
-    be = be < 0 ? 0 : (be > kNbIeadfE - 1 ? kNbIeadfE - 1 : be);
-    int ba = (int)th;
-    ba = ba < 0 ? 0 : (ba > kNbAng - 1 ? kNbAng - 1 : ba);
+    const int be = hist_bin(E, d.Emax_hist, kNbIeadfE);
+    const int ba = clamp_bin(th, kNbAng);
     atomicAdd(&d.diag.ieadf[el][be * kNbAng + ba], 1ull);
     atomicAdd(el == 0 ? &tally->imp_i[0] : &tally->imp_i[1], 1u);
     if (!d.sputter || !(E > (float)kSpTh)) return;
@@ -775,9 +771,7 @@ __device__ __forceinline__ void mover_body(const Dev& d, const StepArgs& a, int 
                     if (inwin) {
                         const float vy = f4get(Gc.vy, u), vz = f4get(Gc.vz, u);
                         const float en = (vx[u] * vx[u] + vy * vy + vz * vz) * (float)(0.5 * kME / kQE);
-                        int bb = (int)(en * 4.0f);
-                        bb = bb < 0 ? 0 : (bb > kNbEedf - 1 ? kNbEedf - 1 : bb);
-                        atomicAdd(&seedf[bb], 1u);
+                        atomicAdd(&seedf[hist_bin(en, 64.0f, kNbEedf)], 1u);
                     }
                 }
             }

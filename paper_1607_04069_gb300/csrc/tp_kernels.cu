@@ -172,10 +172,8 @@ __global__ void __launch_bounds__(kTpThreads, 2) k_tp_step(Dev d)
                     const float v2 = vx[u] * vx[u] + vy[u] * vy[u] + vz[u] * vz[u];
                     const float E = v2 * (float)(0.5 * kMAL / kQE);
                     const float ct = fminf(v2 > 0.0f ? fabsf(vx[u]) * rsqrtf(v2) : 1.0f, 1.0f);
-                    int be = (int)(E / 300.0f * (float)kNbSpE);
-                    be = be < 0 ? 0 : (be > kNbSpE - 1 ? kNbSpE - 1 : be);
-                    int ba = (int)(acosf(ct) * (float)(180.0 / kPI));
-                    ba = ba < 0 ? 0 : (ba > kNbAng - 1 ? kNbAng - 1 : ba);
+                    const int be = hist_bin(E, 300.0f, kNbSpE);
+                    const int ba = clamp_bin(acosf(ct) * (float)(180.0 / kPI), kNbAng);
                     atomicAdd(&d.diag.sp_e[el][be], 1ull);
                     atomicAdd(&d.diag.sp_ang[el][ba], 1ull);
                     atomicAdd(&ctl->cnt[el == 0 ? kCntTpDepL : kCntTpDepR], 1ull);
@@ -437,10 +435,8 @@ __global__ void __launch_bounds__(kTpThreads) k_tp_flight(Dev d, int kmax)
                 tpf_segment(d, A, x, el == 0 ? 0ll : 4294967296LL, vx, tau);
                 const float E = vm * vm * (float)(0.5 * kMAL / kQE);
                 const float ct = fminf(vm > 0.0f ? fabsf(vx) / vm : 1.0f, 1.0f);
-                int be = (int)(E / 300.0f * (float)kNbSpE);
-                be = be < 0 ? 0 : (be > kNbSpE - 1 ? kNbSpE - 1 : be);
-                int ba = (int)(acosf(ct) * (float)(180.0 / kPI));
-                ba = ba < 0 ? 0 : (ba > kNbAng - 1 ? kNbAng - 1 : ba);
+                const int be = hist_bin(E, 300.0f, kNbSpE);
+                const int ba = clamp_bin(acosf(ct) * (float)(180.0 / kPI), kNbAng);
                 atomicAdd(&A.spe[el * kNbSpE + be], 1u);
                 atomicAdd(&A.spa[el * kNbAng + ba], 1u);
                 if (el == 0) ++n_dep_l;

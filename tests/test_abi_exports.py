@@ -73,3 +73,44 @@ def test_missing_library_fails_loudly(monkeypatch):
         P.lib()
     with pytest.raises(ImportError):
         P.default_params()
+
+
+def test_stateless_ops_reject_mismatched_operands():
+    """op_sort_noalloc, op_deposit and op_poisson check dtypes, sizes and the
+    device before any call into the library: a float64 pos with a float32
+    pos_out would have the kernel write 8 bytes into 4-byte slots."""
+    import pytest
+    torch = pytest.importorskip("torch")
+    import paper_1607_04069_gb300 as P
+    n = 8
+    f32 = lambda: torch.zeros(n, dtype=torch.float32)
+    i64 = lambda: torch.zeros(n, dtype=torch.int64)
+    pos64 = torch.zeros(n, dtype=torch.float64)
+    args = dict(vx=f32(), vy=f32(), vz=f32(), ids=i64(), n_cells=64, vx_out=f32(), vy_out=f32(),
+                vz_out=f32(), ids_out=i64())
+    with pytest.raises(ValueError, match="pos_out"):
+        P.op_sort_noalloc(pos64, pos_out=torch.zeros(n, dtype=torch.float32), **args)
+    with pytest.raises(ValueError, match="pos must be"):
+        P.op_sort_noalloc(torch.zeros(n, dtype=torch.int64), pos_out=torch.zeros(n, dtype=torch.int64), **args)
+    bad = dict(args, ids=torch.zeros(n, dtype=torch.int32))
+    with pytest.raises(ValueError, match="ids"):
+        P.op_sort_noalloc(pos64, pos_out=torch.zeros(n, dtype=torch.float64), **bad)
+    bad = dict(args, vy=torch.zeros(n, dtype=torch.float64))
+    with pytest.raises(ValueError, match="vy"):
+        P.op_sort_noalloc(pos64, pos_out=torch.zeros(n, dtype=torch.float64), **bad)
+    with pytest.raises(ValueError, match="n_out"):
+        P.op_sort_noalloc(pos64, pos_out=torch.zeros(n, dtype=torch.float64), n_out=torch.zeros(1), **args)
+    with pytest.raises(ValueError, match="room"):
+        P.op_sort_noalloc(pos64, pos_out=torch.zeros(n - 1, dtype=torch.float64), **args)
+    with pytest.raises(ValueError, match="CUDA"):          # right dtypes, host memory
+        P.op_sort_noalloc(pos64, pos_out=torch.zeros(n, dtype=torch.float64), **args)
+    with pytest.raises(ValueError, match="contiguous"):
+        P.op_sort_noalloc(torch.zeros(2 * n, dtype=torch.float64)[::2], pos_out=pos64.clone(), **args)
+    with pytest.raises(ValueError, match="q must"):
+        P.op_deposit(torch.zeros(n, dtype=torch.int32), 64, q=torch.zeros(64, dtype=torch.int64))
+    with pytest.raises(ValueError, match="q must"):
+        P.op_deposit(torch.zeros(n, dtype=torch.int32), 64, q=torch.zeros(65, dtype=torch.float64))
+    with pytest.raises(ValueError, match="pos must"):
+        P.op_deposit(torch.zeros(n, dtype=torch.float32), 64)
+    with pytest.raises(ValueError, match="q_e"):
+        P.op_poisson(torch.zeros(65, dtype=torch.int64), torch.zeros(64, dtype=torch.int64), 64, 1e-4, 1.0, 0.0)

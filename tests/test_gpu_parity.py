@@ -254,20 +254,23 @@ def test_one_step_collision_parity(case):
 
 
 # ------------------------------------------------------------------ sputtering
-def test_sputter_launch_parity():
-    """Ar+ impacts at 310 eV: the same trials succeed, the sputtered atoms
+@pytest.mark.parametrize("E_ion,V0", [(310.0, 300.0), (700.0, 300.0), (310.0, 0.0)])
+def test_sputter_launch_parity(E_ion, V0):
+    """Ar+ impacts at E_ion: the same trials succeed, the sputtered atoms
     carry the same ids, Thompson/cosine velocities within FP32 rounding, and
-    the IEDF counts agree."""
+    the IEDF and IEADF counts agree bin for bin.  310 eV lies away from an
+    IEDF bin edge of [0, 2 V0]; 700 eV lies beyond 2 V0 and V0 = 0 gives the
+    [0, 1 eV] range, where every impact lands in the last bin."""
     ncell = 1024
     cfg = W.ccp_sputter(n_per_species=1000, n_cells=ncell)
-    cfg.update(pressure_pa=0.0, n_e0=0, n_i0=0, cap_e=1000, cap_i=200_000, cap_tp=200_000,
-               sort_every_e=0, sort_every_i=0, tp_every=0, dt=1e-10, rf_volt_v=300.0)
+    cfg.update(pressure_pa=0.0, n_e0=0, n_i0=0, cap_e=1000, cap_i=200_000, cap_tp=400_000,
+               sort_every_e=0, sort_every_i=0, tp_every=0, dt=1e-10, rf_volt_v=V0)
     d = gpu_discharge(cfg)
-    orc = oracle_for(cfg, cap=200_000)
+    orc = oracle_for(cfg, cap=400_000)
     n = 100_000
     rng = np.random.default_rng(12)
     pos = rng.integers(1, 2000, size=n, dtype=np.uint64).astype(np.uint32)
-    v = math.sqrt(2 * 310.0 * QE / MAR)          # 310 eV: away from an IEDF bin edge
+    v = math.sqrt(2 * E_ion * QE / MAR)
     ids = np.arange(n, dtype=np.uint64) | np.uint64(1 << 62)
     vx = np.full(n, -v, dtype=np.float32)
     zero = np.zeros(n, dtype=np.float32)
@@ -286,7 +289,10 @@ def test_sputter_launch_parity():
     assert len(only_g) == 0 and len(only_o) == 0
     for comp in ("vx", "vy", "vz"):
         assert np.abs(g[comp] - o[comp]).max() <= 1e-4 * np.abs(o["vx"]).max()
-    assert np.array_equal(d.diag("iedf_l"), orc.diag("iedf_l"))
+    for k in ("iedf_l", "ieadf_l"):
+        assert np.array_equal(d.diag(k), orc.diag(k)), k
+    if E_ion > 2 * V0:
+        assert d.diag("iedf_l")[-1] == n
     d.close()
 
 

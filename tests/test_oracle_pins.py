@@ -252,12 +252,15 @@ def test_candidate_gap_is_geometric_with_the_per_step_probability():
     assert O.gap(0.0, 12345) == 2**31 - 1
 
 
-def test_electron_null_collision_rate_constant_sigma():
+@pytest.mark.parametrize("mode", [0, 1])
+def test_electron_null_collision_rate_constant_sigma(mode):
     """Below every threshold only elastic scattering (constant sigma) is real:
-    the real-collision fraction per step is P_max nu_el(v) / nu_max (binomial)."""
+    the real-collision fraction per step is P_max nu_el(v) / nu_max (binomial),
+    with candidates by geometric gaps (mode 0) and by the paper's per-step
+    test R <= P_c,tot (mode 1)."""
     rng = np.random.default_rng(5)
     n, p, T, dt = 200_000, 3.0, 300.0, 1e-9
-    orc = O.Oracle(prm(L=1.0, ncell=1024, p=p, Tg=T, dt=dt), n, 1)
+    orc = O.Oracle(prm(L=1.0, ncell=1024, p=p, Tg=T, dt=dt, coll_mode=mode), n, 1)
     eps = 5.0
     v = math.sqrt(2 * eps * QE / ME)
     load(orc, 0, np.full(n, 512.3), _mono(n, v, rng))
@@ -271,22 +274,85 @@ def test_electron_null_collision_rate_constant_sigma():
     assert abs(c["elastic"] - n * pexp) < 4.5 * math.sqrt(n * pexp * (1 - pexp))
 
 
-def test_ion_candidate_rate_is_velocity_independent():
+@pytest.mark.parametrize("mode", [0, 1])
+def test_ion_candidate_rate_is_velocity_independent(mode):
     """Ar+: sigma(eps) g is constant, so the collision rate does not depend on
-    the velocity and CX and isotropic scattering each take half."""
+    the velocity and CX and isotropic scattering each take half (candidates by
+    geometric gaps, mode 0, or by the per-step test, mode 1)."""
     n, p, T, dt = 200_000, 3.0, 300.0, 1e-7
     ngas = p / (KB * T)
     nu = 2 * ngas * 5e-19 * math.sqrt(2 * QE / (MAR / 2))
     pexp = 1 - math.exp(-nu * dt)
     for speed in (100.0, 3000.0):
         rng = np.random.default_rng(int(speed))
-        orc = O.Oracle(prm(L=10.0, ncell=1024, p=p, Tg=T, dt=dt, seed=int(speed)), 1, n)
+        orc = O.Oracle(prm(L=10.0, ncell=1024, p=p, Tg=T, dt=dt, seed=int(speed), coll_mode=mode), 1, n)
         load(orc, 1, np.full(n, 400.0), _mono(n, speed, rng))
         orc.step(1)
         c = orc.counters()
         tot = c["cx"] + c["iso"]
         assert abs(tot - n * pexp) < 4.5 * math.sqrt(n * pexp * (1 - pexp))
         assert abs(c["cx"] - tot / 2) < 4.5 * math.sqrt(tot / 4)
+
+
+def test_candidates_per_step_are_binomial_in_both_modes():
+    """Sec. "Particle Collisions": every step each particle is a null-collision
+    candidate with probability P_c,tot = 1 - exp(-nu_max dt), independently of
+    the other steps and particles, so the candidates of one step are
+    Binomial(N, P).  Ar+ candidates are all real collisions (sigma g is
+    constant), so the per-step CX + isotropic counts show them.  Both the
+    paper's per-step test (mode 1) and the geometric gaps (mode 0) must give
+    the binomial mean and variance step by step, and the same total."""
+    n, p, T, steps = 50_000, 3.0, 300.0, 60
+    ngas = p / (KB * T)
+    nu = 2 * ngas * 5e-19 * math.sqrt(2 * QE / (MAR / 2))
+    dt = 0.02 / nu
+    P = 1 - math.exp(-nu * dt)
+    totals = []
+    for mode in (0, 1):
+        rng = np.random.default_rng(71)
+        orc = O.Oracle(prm(L=10.0, ncell=1024, p=p, Tg=T, dt=dt, seed=71, coll_mode=mode), 1, n)
+        load(orc, 1, np.full(n, 400.0) + rng.uniform(-1, 1, n), _mono(n, 500.0, rng))
+        per, last = [], 0
+        for _ in range(steps):
+            orc.step(1)
+            c = orc.counters()
+            per.append(c["cx"] + c["iso"] - last)
+            last = c["cx"] + c["iso"]
+        per = np.array(per, dtype=float)
+        mean, var = n * P, n * P * (1 - P)
+        assert abs(per.mean() - mean) < 4.5 * math.sqrt(var / steps), (mode, per.mean(), mean)
+        chi2 = ((per - mean) ** 2 / var).sum()                 # dispersion: chi^2 with `steps` dof
+        assert 1e-3 < stats.chi2.cdf(chi2, steps) < 1 - 1e-3, (mode, chi2)
+        totals.append(per.sum())
+    assert abs(totals[0] - totals[1]) < 4.5 * math.sqrt(2 * steps * n * P * (1 - P))
+
+
+def test_literal_and_geometric_modes_agree_over_the_discharge():
+    """The 25 mm / 128-cell / 100 V / 3 Pa discharge, 20k + 20k, 20 RF periods,
+    with the paper's per-step candidate test (mode 1) and with geometric gaps
+    (mode 0), three seeds each: the time-averaged potential and densities of
+    the two modes differ by no more than the seed-to-seed spread allows (the
+    difference of two three-seed means has the spread of one pair over sqrt(3);
+    2.5 times that), and the pooled ion energy distributions at both
+    electrodes pass a two-sample KS test at p > 0.01."""
+    from helpers import ks_hist, oracle_pool_run
+    from paper_1607_04069_gb300 import workloads as W
+    seeds = (1235, 3001, 3002)
+    cfgs = [dict(W.ccp_small(seed=s), coll_mode=m) for m in (0, 1) for s in seeds]
+    res = oracle_pool_run(cfgs, 4000, 4000)
+    geo, lit = res[:3], res[3:]
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    for k in ("phi", "n_e", "n_i"):
+        pairs = [rel(a[k], b[k]) for grp in (geo, lit) for a, b in ((grp[0], grp[1]), (grp[0], grp[2]),
+                                                                   (grp[1], grp[2]))]
+        spread = float(np.mean(pairs))
+        m0 = np.mean([r[k] for r in geo], axis=0)
+        m1 = np.mean([r[k] for r in lit], axis=0)
+        assert rel(m1, m0) < 2.5 * spread / math.sqrt(3), (k, rel(m1, m0), spread)
+        assert rel(m1, m0) < 0.03, k
+    for k in ("iedf_l", "iedf_r"):
+        pv, D, n1, n2 = ks_hist(sum(r[k] for r in geo), sum(r[k] for r in lit))
+        assert n1 > 3000 and n2 > 3000 and pv > 0.01, (k, pv, n1, n2)
 
 
 def test_ion_thermal_relaxation():
@@ -332,13 +398,14 @@ def test_electron_elastic_energy_loss():
     assert abs(loss.mean() - ref) < 5 * se
 
 
-def test_inelastic_bookkeeping_at_50eV():
+@pytest.mark.parametrize("mode", [0, 1])
+def test_inelastic_bookkeeping_at_50eV(mode):
     """At 50 eV: process fractions follow sigma_el : sigma_exc : sigma_ion,
     excitation removes exactly 11.5 eV, ionisation removes 15.8 eV and
-    creates one e-/Ar+ pair at the parent's position."""
+    creates one e-/Ar+ pair at the parent's position (both candidate modes)."""
     rng = np.random.default_rng(33)
     n, dt = 200_000, 2e-10
-    orc = O.Oracle(prm(L=1.0, ncell=1024, p=3.0, dt=dt), 2 * n, n)
+    orc = O.Oracle(prm(L=1.0, ncell=1024, p=3.0, dt=dt, coll_mode=mode), 2 * n, n)
     eps = 50.0
     v = math.sqrt(2 * eps * QE / ME)
     v0 = _mono(n, v, rng)
@@ -589,6 +656,59 @@ def test_charge_and_particle_conservation_over_steps():
         assert int(f["q_i"].sum()) == 2**32 * c["n_i"]
         assert c["n_e"] + c["imp_e_l"] + c["imp_e_r"] == 2000 + c["ionizations"]
         assert c["n_i"] + c["imp_i_l"] + c["imp_i_r"] == 2000 + c["ionizations"]
+
+
+@pytest.mark.parametrize("sigma_tp", [0.0, 3e-19])
+def test_sputter_to_test_particle_coupling(sigma_tp):
+    """The one-way coupling of the two modules (Sec. "Simulation Scenario",
+    Fig. 3; Sec. "Wall Interactions" of the TPM): ion impacts launch atoms,
+    and the atoms are advanced by a TP step of tp_every PIC steps after every
+    tp_every-th PIC step (sub-cycling).  Two waves of 300 eV Ar+ impacts, at
+    steps 0 and 505 on both electrodes of a 1 mm gap, no field, no charged
+    collisions before the walls.  At every check: TP steps = PIC steps //
+    tp_every; atoms launched (sputtered) = deposited at either electrode + in
+    flight; and with sigma_tp = 0 (ballistic) every atom in flight sits
+    exactly k sub-cycle flights v_x tp_every dt from its electrode, k the TP
+    steps since its wave."""
+    N, L, dt, every = 64, 1e-3, 1e-9, 10
+    n = 20_000
+    orc = O.Oracle(prm(L=L, ncell=N, p=0.5, sputter=1, tp_every=every, sigma_tp=sigma_tp, dt=dt,
+                       V0=0.0, w=0.0, seed=17), 1, 2 * n, 2 * n)
+    sp = math.sqrt(2 * 300.0 * QE / MAR)
+    rng = np.random.default_rng(17)
+
+    def wave(tag):
+        xi = np.concatenate([rng.uniform(1e-3, 2e-3, n), N - rng.uniform(1e-3, 2e-3, n)])
+        vx = np.concatenate([np.full(n, -sp), np.full(n, sp)])
+        ids = (np.arange(2 * n, dtype=np.uint64) + np.uint64(tag)) | np.uint64(1 << 62)
+        load(orc, 1, xi, [vx, np.zeros(2 * n), np.zeros(2 * n)], ids)
+
+    dx = L / N
+    wave(0)
+    orc.step(505)
+    m1 = orc.tp_step_index                                  # TP steps before the second wave
+    wave(1 << 20)
+    for chunk in (95, 400, 1000):
+        orc.step(chunk)
+        c = orc.counters()
+        assert orc.tp_step_index == orc.step_index // every
+        launched = c["sputtered_l"] + c["sputtered_r"]
+        assert launched > 0.25 * 4 * n
+        assert launched == c["tp_dep_l"] + c["tp_dep_r"] + c["n_tp"]
+        if sigma_tp == 0.0:
+            assert c["tp_coll"] == 0
+            tp = orc.get_species(2)
+            wall = np.where(tp["vx"] > 0, 0.0, float(N))
+            k = (tp["xi"] - wall) * dx / (tp["vx"] * every * dt)
+            m = orc.tp_step_index
+            ok = (np.abs(k - m) < 1e-6) | (np.abs(k - (m - m1)) < 1e-6)
+            assert ok.all(), k[~ok][:5]
+        else:
+            assert c["tp_coll"] > 0
+    assert c["tp_dep_l"] + c["tp_dep_r"] > 0.2 * launched
+    for side in "lr":
+        assert orc.diag("sputter_e_" + side).sum() == c["tp_dep_" + side]
+        assert orc.diag("sputter_ang_" + side).sum() == c["tp_dep_" + side]
 
 
 def test_density_diagnostic_normalisation():
