@@ -27,7 +27,12 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-ALGO_BYTES = 20          # per particle-step: read x, v_x, next-candidate step (4+4+4); write x, v_x (4+4)
+# Bytes the method moves per particle-step (read and write x, v_x, v_y, v_z; read the 8-byte id
+# that keys the random stream): the roofline's algorithmic figure.
+ALGO_BYTES = 40
+# Bytes this design moves per particle-step: read x, v_x and the step of the next collision
+# candidate, write x and v_x; v_y, v_z and the id are touched only by collisions and wall hits.
+DESIGN_BYTES = 20
 KERNEL_SOURCES = ["paper_1607_04069_gb300/csrc/pic_kernels.cu", "paper_1607_04069_gb300/csrc/common.cuh",
                   "paper_1607_04069_gb300/csrc/solve.cuh"]
 
@@ -159,6 +164,9 @@ def allreduce_sum(x, ws):
 
 
 def workload(n_per_species, seed):
+    """The sputtering discharge.  With several ranks it is one discharge of
+    ranks x n_per_species superparticles per species (the density kept by
+    the weight), split over the ranks: each holds n_per_species of each."""
     from paper_1607_04069_gb300 import workloads as W
     cfg = W.ccp_sputter(n_per_species=n_per_species, seed=seed)
     # compaction every 400 steps: it restores the cell order the Ar+ deposit
@@ -241,12 +249,16 @@ def measure_rows(d, cfg, peak, cmp_ms, cmp_n, nsort_particles, n_atoms):
     ms, n = t.kernel_time("tp")
     t.close()
     per = ms / n * 1e-3
-    tp_bytes = 28       # read x, v_x, v_y, v_z, id (24 B); write x (4 B); velocities only on collision
-    ach = tp_bytes * n_atoms / per / 1e9
-    rows["a8_tp_step"] = {"workload": "tp_transport: %d Al atoms, 0.5 Pa 300 K Ar, dt 1 ns" % n_atoms,
+    # the method moves x, v_x, v_y, v_z (read and write) and reads the id per atom-step (40 B);
+    # with thinned candidates this design reads x, v_x and the candidate step and writes x (16 B)
+    ach = ALGO_BYTES * n_atoms / per / 1e9
+    rows["a8_tp_step"] = {"workload": "tp_transport: %d Al atoms, 0.5 Pa 300 K Ar, dt 1 ns, thinned "
+                                      "collision candidates" % n_atoms,
                           "value": n_atoms / per, "unit": "atom-steps/s", "mean_launch_us": per * 1e6,
                           "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                                       "frac": ach / peak, "algorithmic_bytes_per_atom_step": tp_bytes}}
+                                       "frac": ach / peak, "algorithmic_bytes_per_atom_step": ALGO_BYTES,
+                                       "design_bytes_per_atom_step": 16,
+                                       "design_frac": 16 * n_atoms / per / 1e9 / peak}}
     # a8, event-driven form: the same source run to deposition, one launch per 32 events per atom
     t = P.Discharge(P.params_from_workload(tc))
     t.tp_launch(n_atoms, 300.0)
@@ -395,12 +407,13 @@ def measure_batched(n_discharges, steps, warmup, peak, run_periods=20):
             "ms_per_step": best_ms, "ms_per_step_single_launch": batch_ms, "ms_per_step_graph": graph_ms,
             "plain_loop_ms_per_step": plain_ms, "plain_loop_particle_steps_per_s": n_part / (plain_ms * 1e-3),
             "speedup_vs_plain_loop": plain_ms / best_ms, "particles_per_cta": best,
-            "discharges_per_hour": n_discharges * 3600.0 / (steps_per_run * best_ms * 1e-3),
-            "plain_loop_discharges_per_hour": n_discharges * 3600.0 / (steps_per_run * plain_ms * 1e-3),
-            "run_length": f"{run_periods} RF periods ({steps_per_run} steps) per discharge, rate from "
-                          f"{steps} timed steps",
+            "discharges_per_hour_extrapolated": n_discharges * 3600.0 / (steps_per_run * best_ms * 1e-3),
+            "plain_loop_discharges_per_hour_extrapolated": n_discharges * 3600.0 / (steps_per_run * plain_ms * 1e-3),
+            "run_length": f"extrapolated: {run_periods} RF periods ({steps_per_run} steps) per discharge at the "
+                          f"rate of {steps} timed steps",
             "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                         "algorithmic_bytes_per_particle_step": ALGO_BYTES}}
+                         "algorithmic_bytes_per_particle_step": ALGO_BYTES,
+                         "design_frac": DESIGN_BYTES * n_part / (best_ms * 1e-3) / 1e9 / peak}}
 
 
 def measure_served(n_requests, rate_hz, max_periods, tol=0.01, seed=1239):
@@ -449,6 +462,15 @@ def measure_served(n_requests, rate_hz, max_periods, tol=0.01, seed=1239):
             "batched": b, "plain_loop": l}
 
 
+def line_config(cfg, ws, n_per_species):
+    """The workload's description, the same in both arms' lines."""
+    return {"workload": cfg["name"], "particles_per_gpu": 2 * n_per_species, "n_cells": cfg["n_cells"],
+            "sort_every": [cfg["sort_every_e"], cfg["sort_every_i"]], "tp_every": cfg["tp_every"],
+            "parallelism": f"one discharge split over {ws} gpus (int64 deposit all-reduce per step)" if ws > 1
+                           else "1 gpu",
+            "l2": "flushed before every timed step (512 MiB write, then a 256 MiB read)"}
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -461,13 +483,30 @@ def run_reference(args, ws, rank):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": cfg["name"], "particles": 2 * n_sample, "n_cells": cfg["n_cells"]},
+            "config": line_config(cfg, args.gpus, args.n_per_species),
             "cpu_baseline": {"value": rate, "unit": "particle-steps/s", "cores": 1, "kind": "oracle", **host_cpu(),
                              "sample": f"{n_sample}+{n_sample} superparticles of the same discharge "
                                        f"(weight x{cfg['n_e0'] / n_sample:g}), {args.steps} full steps"},
             "e2e": {"value": rate, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def timed_steps(d, stream, k_steps, flush, clean):
+    """k_steps steps, each after an L2 flush and bracketed by CUDA events on
+    the step's stream; returns the per-step times (ms)."""
+    import torch
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(k_steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(k_steps)]
+    torch.cuda.synchronize()
+    for k in range(k_steps):
+        flush.zero_()
+        clean.max()
+        starts[k].record(stream)
+        d.step(1)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in zip(starts, ends)]
 
 
 def main():
@@ -497,78 +536,82 @@ def main():
     import torch
 
     import paper_1607_04069_gb300 as P
+    from paper_1607_04069_gb300 import shard
 
     torch.cuda.set_device(local)
-    cfg = workload(args.n_per_species, 1236 + rank)
+    # one discharge; with several ranks its superparticles are split over them
+    cfg_all = workload(args.n_per_species * ws, 1236)
+    cfg = shard.shard_workload(cfg_all, rank, ws)
     stream = torch.cuda.current_stream()
-    d = P.Discharge(P.params_from_workload(cfg), stream=stream)
+    sd = shard.SplitDischarge(cfg_all, rank, ws, stream=stream)
+    d = sd if ws > 1 else sd.d
     d.step(args.warmup)
-    d.sync()
-    n_start = sum(len(d.get_species(s)["id"]) for s in (0, 1))
+    sd.sync()
+    n_start = sd.alive() // ws
     # L2 flush between timed steps: write 512 MiB (> 129 MB L2), then read a
     # separate 256 MiB buffer so the flush's dirty lines are written back
     # before the step starts (the L2 then holds neither the state nor dirty data)
     flush = torch.empty(512 * 2**20, dtype=torch.uint8, device="cuda")
     clean = torch.ones(64 * 2**20, dtype=torch.int32, device="cuda")
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     # the library's per-launch timers stay off here: their event records would
     # add to every timed step; the step kernel's launch time is read from the
     # per-step events of the steps that launch nothing else
     with Clocks(local) as clk:
         barrier(ws)
-        torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for k in range(args.steps):
-            flush.zero_()
-            clean.max()
-            starts[k].record(stream)
-            d.step(1)
-            ends[k].record(stream)
-        torch.cuda.synchronize()
+        times = timed_steps(d, stream, args.steps, flush, clean)
         barrier(ws)
         wall = time.perf_counter() - t0
-    d.sync()
-    times = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    sd.sync()
+    n_end = sd.alive() // ws
     step_ms = sum(times)
     extra = [extra_launches(cfg, args.warmup + k) for k in range(args.steps)]
     alone = [t for t, x in zip(times, extra) if x == 0]
     mover_ms, mover_n = sum(alone), len(alone)
     launches = args.steps + sum(extra)
-    # the library's timers on a further 400 steps (one compaction of each
-    # species, ten test-particle steps): the compaction and TP launch times,
-    # and a check of the launch schedule counted above
-    d.timing(True)
-    d.step(400)
-    d.sync()
-    _, chk_mover = d.kernel_time("step")
-    tp_ms, tp_n = d.kernel_time("tp")
-    cmp_ms, cmp_n = d.kernel_time("compact")
-    d.timing(False)
+    t_max = allreduce_max(step_ms, ws)
+    psteps = allreduce_sum(0.5 * (n_start + n_end) * args.steps, ws)
+    value = psteps / (t_max * 1e-3)
+    # one whole schedule of 400 steps (a compaction of each species, ten coupled
+    # test-particle steps), timed the same way: the schedule-weighted step time
     h0 = args.warmup + args.steps
-    want = sum(extra_launches(cfg, h0 + k) for k in range(400))
+    sched = timed_steps(d, stream, 400, flush, clean)
+    sd.sync()
+    n_sched = sd.alive() // ws
+    sched_ms = allreduce_max(sum(sched), ws)
+    sched_value = allreduce_sum(0.5 * (n_end + n_sched) * 400, ws) / (sched_ms * 1e-3)
+    # the library's timers on a further 400 steps: the compaction and TP launch
+    # times, and a check of the launch schedule counted above
+    sd.d.timing(True)
+    d.step(400)
+    sd.sync()
+    _, chk_mover = sd.d.kernel_time("step")
+    tp_ms, tp_n = sd.d.kernel_time("tp")
+    cmp_ms, cmp_n = sd.d.kernel_time("compact")
+    sd.d.timing(False)
+    want = sum(extra_launches(cfg, h0 + 400 + k) for k in range(400))
     if chk_mover != 400 or tp_n + 3 * cmp_n != want:
         raise RuntimeError(f"launch schedule: {tp_n} TP and {cmp_n} compaction launches, {want} kernels expected")
-    n_end = sum(len(d.get_species(s)["id"]) for s in (0, 1))
-    psteps_local = 0.5 * (n_start + n_end) * args.steps
-    t_max = allreduce_max(step_ms, ws)
-    psteps = allreduce_sum(psteps_local, ws)
-    value = psteps / (t_max * 1e-3)
 
     # roofline of the per-step kernel: algorithmic bytes / mean launch time
     peak, peak_kind = hbm_peak()
     per_launch_s = mover_ms / max(mover_n, 1) * 1e-3
-    achieved = ALGO_BYTES * 0.5 * (n_start + n_end) / per_launch_s / 1e9
+    nmid = 0.5 * (n_start + n_end)
+    achieved = ALGO_BYTES * nmid / per_launch_s / 1e9
+    traffic = traffic_per_launch()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic_per_launch(),
-                "kernel": "k_mover (fused gather/push/wall/MCC/deposit + last-CTA field solve)",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "k_mover (fused gather/push/wall/MCC/deposit, per-CTA field solve)",
                 "algorithmic_bytes_per_particle_step": ALGO_BYTES, "peak_source": peak_kind,
+                "design_bytes_per_particle_step": DESIGN_BYTES,
+                "design_frac": DESIGN_BYTES * nmid / per_launch_s / 1e9 / peak,
+                "dram_frac": (traffic / per_launch_s / 1e9 / peak) if traffic else None,
                 "mean_launch_us": per_launch_s * 1e6}
 
     # end to end through the public API: pinned host state -> device, steps, diagnostics -> host
     e2e = None
     if args.e2e_steps > 0:
-        sp = {s: d.get_species(s) for s in (0, 1)}
+        sp = {s: sd.d.get_species(s) for s in (0, 1)}
         pinned = {}
         for s in (0, 1):
             n = len(sp[s]["id"])
@@ -585,12 +628,18 @@ def main():
         h2d = sum(sum(a.nbytes for a in pinned[s]) for s in (0, 1))
         cap = max(len(pinned[s][0]) for s in (0, 1)) * 5 // 4 + 65536
         d2 = P.Discharge(P.params_from_workload(cfg, n_e0=0, n_i0=0, cap_e=cap, cap_i=cap), stream=stream)
+        slot = d2.exchange_slot() if ws > 1 else None
         barrier(ws)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for s in (0, 1):
             d2.set_species(s, *pinned[s])
-        d2.step(args.e2e_steps)
+        if slot is not None:
+            shard.allreduce_(slot)
+        for _ in range(args.e2e_steps):
+            d2.step(1)
+            if slot is not None:
+                shard.allreduce_(slot)
         out = [d2.diag(k) for k in ("phi", "n_e", "n_i", "iedf_l")]
         cnt = d2.counters()
         torch.cuda.synchronize()
@@ -612,7 +661,7 @@ def main():
     clocks = clk.summary()
     rows = None
     if rank == 0 and not args.no_rows:
-        rows = measure_rows(d, cfg, peak, cmp_ms, cmp_n, 0.25 * (n_start + n_end), args.tp_atoms)
+        rows = measure_rows(sd.d, cfg, peak, cmp_ms, cmp_n, 0.25 * (n_start + n_end), args.tp_atoms)
         if args.batch_discharges > 0:
             rows["b_batched"] = measure_batched(args.batch_discharges, 30, 10, peak)
         if args.serve_requests > 0:
@@ -621,21 +670,20 @@ def main():
         line = {"metric": "particle-steps/s", "value": value, "unit": "particle-steps/s", "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-                "data": "synthetic",
-                "config": {"workload": cfg["name"], "particles_per_gpu": int(n_start),
-                           "n_cells": cfg["n_cells"], "sort_every": [400, 400], "tp_every": 40,
-                           "parallelism": f"replicas x{ws}" if ws > 1 else "1 gpu",
-                           "l2": "flushed before every timed step (512 MiB write, then a 256 MiB "
-                                 "read); value from per-step CUDA events; the step kernel's launch "
-                                 "time from those of the steps that launch nothing else",
-                           "wall_s_incl_flush": wall},
+                "data": "synthetic", "config": line_config(cfg_all, ws, args.n_per_species),
+                "timing": "value from per-step CUDA events after an L2 flush each; the step kernel's "
+                          "launch time from those of the steps that launch nothing else",
+                "wall_s_incl_flush": wall, "particles_start_end_per_gpu": [int(n_start), int(n_end)],
+                "schedule_400": {"ms_per_step": sched_ms / 400, "value": sched_value,
+                                 "note": "400 further steps timed the same way: one compaction of each "
+                                         "species and ten coupled test-particle steps fall inside"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": int(launches), "rows": rows,
                 "kernel_us": {"step_alone_mean": mover_ms / max(mover_n, 1) * 1e3, "steps_alone": mover_n,
                               "tp_mean": tp_ms / max(tp_n, 1) * 1e3,
                               "compact_mean": cmp_ms / max(cmp_n, 1) * 1e3}}
         print(json.dumps(line), flush=True)
-    d.close()
+    sd.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

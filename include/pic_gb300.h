@@ -88,11 +88,18 @@ typedef struct pic_params {
                                1 VHS, sigma = pi b_max^2 with b_max(g) of Eq.
                                maximumimpactparameter, isotropic scattering; 2 M1, the same
                                law with d_ref sqrt(4/3) and chi = pi (1 - b / b_max)     */
-    int32_t tp_pad;
+    int32_t tp_mode;        /* collisions of tp_step (Sec. "Test Particle Method", Eq.
+                               collisionprobability1 with a sampled Ar partner): 0 candidate
+                               steps at a majorant probability, geometric gaps kept per atom,
+                               thinned to the same per-step law; 1 the test drawn every step   */
     double tp_dref;         /* models 1, 2: VHS reference diameter of the Al-Ar pair, m (see
                                pic_vhs_dref)                                               */
     double tp_omega;        /* models 1, 2: viscosity index, 0.5 .. 1                      */
     double tp_tref;         /* models 1, 2: reference temperature, K                       */
+    int64_t id_offset;      /* the initial loading holds particles id_offset .. id_offset +
+                               n_e0 - 1 (and n_i0 - 1) of a larger loading (ids tag | k): one
+                               rank's share when a discharge's particles are split over
+                               ranks (see pic_exchange_slot); 0 for a whole discharge       */
 } pic_params;
 
 /* VHS reference diameter of a species from its viscosity mu_ref (Pa s) at
@@ -107,6 +114,10 @@ double pic_vhs_dref(double mu_ref, double t_ref, double omega, double mass_kg);
 typedef struct tp_source {
     int64_t n;
     double e_ion_ev;
+    int64_t first_id;       /* the atoms get ids tag | (first_id + k), k < n; a negative value
+                               continues after the atoms this context launched before.  A
+                               source split over ranks gives each rank its own id range, and
+                               the union is the one-rank source atom for atom            */
 } tp_source;
 
 typedef struct pic_ctx pic_ctx; /* opaque */
@@ -140,6 +151,24 @@ int pic_step(pic_ctx* ctx, int64_t n_steps);
 /* Wait for the context's stream; returns PIC_ERR_CAPACITY or
  * PIC_ERR_NUMERICS if the device recorded either since the last call. */
 int pic_sync(pic_ctx* ctx);
+
+/* One discharge whose superparticles are split over several contexts (one
+ * per rank, each created with its id_offset and share of n_e0 / n_i0).  The
+ * field solve of Sec. "EM Field Solver" needs the charge of all particles,
+ * which is the sum of the ranks' exact int64 deposits (Sec. "Charge
+ * Assignment"); every other part of the cycle is per particle, with random
+ * words keyed by the particle's id, so the split run equals the whole one.
+ * After pic_create and after every pic_step(ctx, 1), before the next step,
+ * the caller sums this device block over the ranks in place (an int64 sum
+ * all-reduce, e.g. NCCL on the context's stream): *dev receives the
+ * context-owned device int64[*n_words] of the current step -- the electron
+ * and ion deposits and their flux moments, padded with zeros.  Time averages
+ * of the charge, potential and fluxes are then those of the whole discharge
+ * on every rank; histograms, counters and test particles stay per rank and
+ * add up.  The pointer stays valid for the context's life; its contents
+ * change every step.  PIC_ERR_INVALID_ARG with circuit 1 (the series
+ * capacitor needs the whole wall charge each step). */
+int pic_exchange_slot(pic_ctx* ctx, int64_t** dev, int64_t* n_words);
 
 /* Diagnostics (Sec. "Simulation Results", Figs. 5-9), written to host memory:
  *  0 PHI      time-averaged potential, V, N+1 nodes

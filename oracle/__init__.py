@@ -62,7 +62,7 @@ class Params(C.Structure):
                 ("sputter", C.c_int32), ("tp_every", C.c_int32), ("diag_every", C.c_int32),
                 ("waveform", C.c_int32), ("circuit", C.c_int32), ("phase", C.c_double), ("cb", C.c_double),
                 ("dref", C.c_double), ("omega", C.c_double), ("tref", C.c_double), ("tp_model", C.c_int32),
-                ("coll_mode", C.c_int32)]
+                ("coll_mode", C.c_int32), ("tp_mode", C.c_int32), ("pad2", C.c_int32)]
 
 
 def _p(a):
@@ -87,6 +87,12 @@ def lib():
                 "orc_destroy": (None, [vp]),
                 "orc_derived": (None, [vp, vp]),
                 "orc_init_species": (None, [vp, C.c_int, i64, dbl]),
+                "orc_init_species_range": (None, [vp, C.c_int, i64, i64, dbl]),
+                "orc_step_particles": (None, [vp]),
+                "orc_step_field": (None, [vp]),
+                "orc_set_deposit": (None, [vp, vp, vp]),
+                "orc_solve": (None, [vp]),
+                "orc_tp_launch_ids": (None, [vp, i64, dbl, i64]),
                 "orc_set_species": (C.c_int, [vp, C.c_int, i64, vp, vp, vp, vp, vp]),
                 "orc_get_species": (i64, [vp, C.c_int, i64, vp, vp, vp, vp, vp]),
                 "orc_field": (None, [vp]),
@@ -102,6 +108,7 @@ def lib():
                 "orc_set_step": (None, [vp, u32]),
                 "orc_get_tp_step": (u32, [vp]),
                 "orc_gap": (u32, [dbl, u32]),
+                "orc_tp_gap": (u32, [dbl, u32]),
                 "orc_source_voltage": (dbl, [vp, u32]),
                 "orc_mean_rel_speed": (dbl, [dbl, dbl]),
                 "orc_tpf_partner": (C.c_int, [C.c_uint64, C.c_uint64, u32, dbl, vp, vp]),
@@ -137,6 +144,12 @@ def gap(lam, w):
     """Steps from one null-collision candidate to the next for nu_max dt =
     lam, from the Philox word w (geometric law, see orc_gap)."""
     return int(lib().orc_gap(float(lam), int(w) & 0xffffffff))
+
+
+def tp_gap(Ph, w):
+    """TP steps from one collision candidate to the next at the per-step
+    candidate probability Ph, from the Philox word w (geometric law)."""
+    return int(lib().orc_tp_gap(float(Ph), int(w) & 0xffffffff))
 
 
 def mean_rel_speed(v, c):
@@ -250,8 +263,27 @@ class Oracle:
         keys = ["n_gas", "dx", "nu_max_e", "nu_max_i", "p_max_e", "p_max_i", "eps_max", "lambda"]
         return dict(zip(keys, out.tolist()))
 
-    def init_species(self, s, n, T_eV):
-        lib().orc_init_species(self.h, int(s), int(n), float(T_eV))
+    def init_species(self, s, n, T_eV, first=0):
+        """The initial loading of particles first .. first + n - 1 (ids tag | k)."""
+        lib().orc_init_species_range(self.h, int(s), int(first), int(n), float(T_eV))
+
+    def step_particles(self):
+        """First half of a cycle: push, walls, collisions, charge assignment of the own particles."""
+        lib().orc_step_particles(self.h)
+
+    def step_field(self):
+        """Second half: field solve from the deposit, time averages, coupled TP step."""
+        lib().orc_step_field(self.h)
+
+    def solve(self):
+        """Field solve of the current step from the deposit held."""
+        lib().orc_solve(self.h)
+
+    def set_deposit(self, q_e, q_i):
+        """Replace the deposit the next field solve uses (int64[ncell+1] each)."""
+        a = np.ascontiguousarray(q_e, dtype=np.int64)
+        b = np.ascontiguousarray(q_i, dtype=np.int64)
+        lib().orc_set_deposit(self.h, _p(a), _p(b))
 
     def set_species(self, s, xi, vx, vy, vz, ids):
         arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (xi, vx, vy, vz)]
@@ -293,8 +325,13 @@ class Oracle:
     def tp_step(self, n, dt_tp):
         lib().orc_tp_step(self.h, int(n), float(dt_tp))
 
-    def tp_launch(self, n, E_ion):
-        lib().orc_tp_launch(self.h, int(n), float(E_ion))
+    def tp_launch(self, n, E_ion, first_id=None):
+        """Atoms of a mono-energetic source; first_id: ids first_id .. first_id + n - 1
+        (default: after the atoms launched before)."""
+        if first_id is None:
+            lib().orc_tp_launch(self.h, int(n), float(E_ion))
+        else:
+            lib().orc_tp_launch_ids(self.h, int(n), float(E_ion), int(first_id))
 
     def tp_flight(self, max_events):
         """Event-driven flight of every live TP atom, at most max_events

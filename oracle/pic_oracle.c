@@ -73,7 +73,11 @@ enum {
     PUR_TPF_SCATTER = 71,/* event-driven TP: scattering direction       */
     PUR_TPF_PARTNER = 72,/* +2t, +2t+1: partner proposal t of event e    */
     PUR_TPF_CAND = 200,  /* VHS/M1 flight: candidate partner (200, 201)  */
-    PUR_TPF_GAMMA = 202  /* +t: gamma variate attempt t of a candidate   */
+    PUR_TPF_GAMMA = 202, /* +t: gamma variate attempt t of a candidate   */
+    PUR_TP_CAND = 256,   /* TP step candidate: partner proposal (256, 257) */
+    PUR_TP_GAMMA = 258,  /* +t: gamma variate attempt t of that proposal  */
+    PUR_TP_GAP = 290,    /* TP steps to the next candidate, after one     */
+    PUR_TP_GAP0 = 291    /* TP steps to the first candidate              */
 };
 #define TPF_GAMMA_TRIES 32
 #define TPF_TRIES 64     /* partner proposals per collision (each accepted w.p. >= 1/2) */
@@ -120,6 +124,10 @@ typedef struct {
     int32_t coll_mode;            /* null-collision candidates of e- and Ar+: 0 geometric gaps
                                      between candidates (orc_gap), 1 the paper's literal test,
                                      a fresh R <= P_c,tot every step                   */
+    int32_t tp_mode;              /* TP step collisions: 0 candidates at a majorant rate with
+                                     geometric gaps, thinned to the per-step law
+                                     (orc_tp_step), 1 the literal test every step     */
+    int32_t pad2;
 } orc_params;
 
 typedef struct {
@@ -145,6 +153,7 @@ typedef struct {
     double *xs_e[3], *xs_s[3];    /* tabulated e-Ar cross sections (eV, m^2), or NULL: analytic */
     int64_t xs_n[3];
     int64_t n_avg, n_flux, n_tp_samp, tp_launched;
+    double tp_gap_dt;             /* TP dt the stored candidate gaps were drawn for     */
     int64_t *iedf[2], *ieadf[2], *eedf, *sp_e[2], *sp_ang[2];
     int64_t cnt[C_NCOUNT];
 } orc_state;
@@ -430,7 +439,7 @@ static double v_rf(orc_state *S, uint32_t l)
 }
 
 /* deposit both charged species and solve the field for time step l */
-static void field_for_step(orc_state *S, uint32_t l)
+static void deposit_all(orc_state *S)
 {
     int N = S->P.ncell;
     for (int s = 0; s < 2; s++) {
@@ -441,7 +450,17 @@ static void field_for_step(orc_state *S, uint32_t l)
             orc_deposit(&p->xi[k], 1, N, S->q[s]);
         }
     }
-    orc_poisson(N, S->dx, S->P.w, S->q[SP_I], S->q[SP_E], v_rf(S, l), S->phi, S->E);
+}
+
+static void solve_for_step(orc_state *S, uint32_t l)
+{
+    orc_poisson(S->P.ncell, S->dx, S->P.w, S->q[SP_I], S->q[SP_E], v_rf(S, l), S->phi, S->E);
+}
+
+static void field_for_step(orc_state *S, uint32_t l)
+{
+    deposit_all(S);
+    solve_for_step(S, l);
 }
 
 /* derived quantities of the null-collision method (Sec. "Particle
@@ -524,13 +543,18 @@ void orc_derived(const orc_state *S, double out[8])
 /* Initial loading (Sec. "Kinetic Particle Simulation"): positions uniform
  * over the gap, velocities Maxwellian at temperature T (eV), by Box-Muller.
  * The sampled velocity is taken as v^(-1/2).  Ids are tag | k. */
-void orc_init_species(orc_state *S, int s, int64_t n, double T_eV)
+void orc_init_species_range(orc_state *S, int s, int64_t k0, int64_t n, double T_eV);
+void orc_init_species(orc_state *S, int s, int64_t n, double T_eV) { orc_init_species_range(S, s, 0, n, T_eV); }
+
+/* the particles k0 .. k0 + n - 1 of the initial loading (ids tag | k): the
+ * share of one rank when the particles are split over several */
+void orc_init_species_range(orc_state *S, int s, int64_t k0, int64_t n, double T_eV)
 {
     orc_sp *p = &S->sp[s];
     double vth = sqrt(T_eV * O_QE / mass_of(s));
     double N = (double)S->P.ncell;
     p->n = 0;
-    for (int64_t k = 0; k < n && k < p->cap; k++) {
+    for (int64_t k = k0; k < k0 + n && k - k0 < p->cap; k++) {
         uint64_t id = TAG[s] | (uint64_t)k;
         uint32_t a[4], b[4];
         draw(S->P.seed, id, 0, PUR_INIT, a);
@@ -791,11 +815,18 @@ static void wall_ion(orc_state *S, int64_t k, uint32_t l, int electrode)
 }
 
 void orc_tp_step(orc_state *S, int64_t nsteps, double dt_tp);
+static double gamma_mt(double k, uint64_t seed, uint64_t id, uint32_t e, uint32_t base);
 
 /* One PIC/MCC cycle l -> l+1 for both charged species (Fig. 4 order: the
  * field E^l is already known; interpolate, push (leapfrog, Eqs. for r and
  * v), walls, collisions; then charge assignment and field solve for l+1). */
-static void pic_one_step(orc_state *S)
+/* One PIC/MCC cycle in two halves.  orc_step_particles: interpolation, push,
+ * walls and collisions of every particle and the charge assignment of
+ * x^{l+1} into q; orc_step_field: the field solve of step l+1 from q, the
+ * time averages and the coupled TP step.  Between the two a caller that
+ * holds only a share of the particles (the particles split over several
+ * ranks) replaces q by the sum over the ranks (orc_set_deposit). */
+void orc_step_particles(orc_state *S)
 {
     uint32_t l = S->step;
     int N = S->P.ncell;
@@ -829,7 +860,13 @@ static void pic_one_step(orc_state *S)
         }
     }
     S->step = l + 1;
-    field_for_step(S, S->step);
+    deposit_all(S);
+}
+
+void orc_step_field(orc_state *S)
+{
+    int N = S->P.ncell;
+    solve_for_step(S, S->step);
     /* time averages (Sec. "Kinetic Particle Simulation": averaging) */
     for (int m = 0; m <= N; m++) {
         S->sum_q[0][m] += (double)S->q[0][m];
@@ -857,6 +894,23 @@ static void pic_one_step(orc_state *S)
     }
     if (S->P.sputter && S->P.tp_every > 0 && S->step % (uint32_t)S->P.tp_every == 0)
         orc_tp_step(S, 1, S->P.tp_every * S->P.dt);
+}
+
+static void pic_one_step(orc_state *S)
+{
+    orc_step_particles(S);
+    orc_step_field(S);
+}
+
+/* the field solve of the current step from the deposit held (after
+ * orc_set_deposit at creation) */
+void orc_solve(orc_state *S) { solve_for_step(S, S->step); }
+
+/* the charge assignment the next field solve uses (int64[N+1] each) */
+void orc_set_deposit(orc_state *S, const int64_t *q_e, const int64_t *q_i)
+{
+    memcpy(S->q[SP_E], q_e, sizeof(int64_t) * (S->P.ncell + 1));
+    memcpy(S->q[SP_I], q_i, sizeof(int64_t) * (S->P.ncell + 1));
 }
 
 void orc_step(orc_state *S, int64_t nsteps)
@@ -915,10 +969,109 @@ void orc_tp_scatter(int model, const double g[3], uint32_t r1, uint32_t r2, doub
 }
 
 /* One TP step (Sec. "Test Particle Method"): free flight x += v_x dt, sticking
- * at either wall with the absorbed flux recorded, and a binary hard-sphere
- * collision with a thermal Ar partner with probability 1 - exp(-n sigma g dt)
- * (Eq. collisionprobability1 with tau_c = 1/(n sigma g)); isotropic
- * scattering in the centre-of-mass frame. */
+ * at either wall with the absorbed flux recorded, and a binary collision with
+ * a partner w from the Maxwellian gas with probability p(g) = 1 - exp(-n
+ * sigma(g) g dt), g = |v - w| (Eq. collisionprobability1 with tau_c = 1/(n
+ * sigma(g) g)); scattering in the centre-of-mass frame (orc_tp_scatter).
+ *
+ * tp_mode 1 is the method as the paper states it: every step draws a partner
+ * (PUR_TP_GAS) and the test word (PUR_TP_COLL word 0).
+ *
+ * tp_mode 0 takes the same per-step law in two parts, as the null-collision
+ * method does for the charged particles (Sec. "Particle Collisions"):
+ *  - With sigma(g) g = K g^alpha (hard spheres: K = sigma, alpha = 1; VHS and
+ *    M1: alpha = 2 - 2 omega <= 1), p(g) <= n K dt g^alpha <= n K dt
+ *    (|v|^alpha + |w|^alpha).  So every step is a candidate with the
+ *    probability P^ = n K dt (|v|^alpha + <|w|^alpha>), independently of the
+ *    other steps, and the steps between candidates are geometric.
+ *    P^ is that bound rounded up to 8 significant bits (tp_cand_prob).
+ *  - A candidate draws one partner from (|v|^alpha + |w|^alpha) f(w) / (|v|^alpha
+ *    + <|w|^alpha>) -- a Maxwellian w with probability |v|^alpha / (|v|^alpha +
+ *    <|w|^alpha>), else |w|^2/c^2 ~ Gamma((3 + alpha)/2) in an isotropic
+ *    direction -- and collides with probability p(g) (|v|^alpha +
+ *    <|w|^alpha>) / (P^ (|v|^alpha + |w|^alpha)) <= 1 (PUR_TP_CAND,
+ *    PUR_TP_CAND + 1 word 1).
+ *  - P^ times the proposal density times that probability is f(w) p(g): the
+ *    law of the literal test.  |v| changes only at a collision, so the next
+ *    gap is drawn at the current |v| after each candidate (PUR_TP_GAP); an
+ *    atom's first gap is drawn at the first step that moves it (PUR_TP_GAP0).
+ *  - nev holds the next candidate step plus one (0: none drawn yet; a step
+ *    index below the current one, left by the event-driven flight, is
+ *    redrawn the same way).  The scattering uses PUR_TP_COLL words 1, 2 as
+ *    in tp_mode 1.  It needs P^ <= 1 (dt << tau_c, Sec. "Limitations and
+ *    Constraints"); a larger P^ counts as NUMERICS. */
+
+/* TP steps from one candidate to the next at the per-step probability Ph:
+ * geometric, by inversion, 1 + floor(ln R / ln(1 - Ph)) */
+uint32_t orc_tp_gap(double Ph, uint32_t w)
+{
+    if (!(Ph < 1.0)) return 1u;
+    if (!(Ph > 0.0)) return 2147483647u;
+    double x = log(u23(w)) / log1p(-Ph);
+    if (!(x < 2147483646.0)) return 2147483647u;
+    return 1u + (uint32_t)floor(x);
+}
+
+/* <|w|^alpha> of the Maxwellian gas of most probable speed c */
+static double gas_mean_pow(double c, double alpha)
+{
+    return pow(c, alpha) * tgamma(0.5 * (3.0 + alpha)) / tgamma(1.5);
+}
+
+/* x rounded up to 8 significant bits (0, NaN and infinity unchanged) */
+static double round_up8(double x)
+{
+    if (!(x > 0.0) || isinf(x)) return x;
+    int e;
+    double m = frexp(x, &e);
+    return ldexp(ceil(m * 256.0) / 256.0, e);
+}
+
+/* The candidate probability per step P^ of an atom of speed vm: the bound
+ * n K dt (|v|^alpha + <|w|^alpha>) rounded up to 8 significant bits.  Any
+ * larger value is a majorant too (the acceptance below carries the ratio),
+ * and the rounding lets implementations that evaluate the bound in other
+ * precisions reach the same P^, hence the same gaps. */
+static double tp_cand_prob(const orc_state *S, double vm, double dt_tp)
+{
+    double c = sqrt(2.0 * O_KB * S->P.Tg / O_MAR);
+    double alpha = S->P.tp_model == 0 ? 1.0 : 2.0 - 2.0 * S->P.omega;
+    double K = S->P.tp_model == 0 ? S->P.sigma_tp : orc_tp_sigma(S, 1.0);
+    return round_up8(S->ngas * K * dt_tp * (pow(vm, alpha) + gas_mean_pow(c, alpha)));
+}
+
+/* one candidate of tp_mode 0 at step s: returns 1 and the partner w when it
+ * is a real collision */
+static int tp_candidate(orc_state *S, uint64_t id, uint32_t s, const double v[3], double dt_tp, double w[3])
+{
+    double c = sqrt(2.0 * O_KB * S->P.Tg / O_MAR);
+    double alpha = S->P.tp_model == 0 ? 1.0 : 2.0 - 2.0 * S->P.omega;
+    double K = S->P.tp_model == 0 ? S->P.sigma_tp : orc_tp_sigma(S, 1.0);
+    double b = S->ngas * K * dt_tp;
+    double vm = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    double va = pow(vm, alpha), ma = gas_mean_pow(c, alpha);
+    uint32_t a[4], e[4];
+    draw(S->P.seed, id, s, PUR_TP_CAND, a);
+    draw(S->P.seed, id, s, PUR_TP_CAND + 1, e);
+    if (u23(a[0]) * (va + ma) < va) {
+        double vg = c / sqrt(2.0), n1, n2, n3, n4;
+        box_muller(a[1], a[2], &n1, &n2);
+        box_muller(a[3], e[0], &n3, &n4);
+        w[0] = vg * n1; w[1] = vg * n2; w[2] = vg * n3;
+    } else {
+        double x2 = S->P.tp_model == 0 ? -log(u23(a[1]) * u23(a[2]))
+                                       : gamma_mt(0.5 * (3.0 + alpha), S->P.seed, id, s, PUR_TP_GAMMA);
+        double sp = c * sqrt(x2), d[3];
+        iso_dir(a[3], e[0], d);
+        w[0] = sp * d[0]; w[1] = sp * d[1]; w[2] = sp * d[2];
+    }
+    double g = sqrt((v[0] - w[0]) * (v[0] - w[0]) + (v[1] - w[1]) * (v[1] - w[1]) + (v[2] - w[2]) * (v[2] - w[2]));
+    double wm = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    /* accept with p(g) (|v|^alpha + <|w|^alpha>) / (P^ (|v|^alpha + |w|^alpha)) */
+    double Ph = tp_cand_prob(S, vm, dt_tp);
+    return u23(e[1]) * Ph * (va + pow(wm, alpha)) < (va + ma) * -expm1(-b * pow(g, alpha));
+}
+
 void orc_tp_step(orc_state *S, int64_t nsteps, double dt_tp)
 {
     orc_sp *p = &S->sp[SP_TP];
@@ -926,6 +1079,11 @@ void orc_tp_step(orc_state *S, int64_t nsteps, double dt_tp)
     double dx = S->dx;
     double vg = sqrt(O_KB * S->P.Tg / O_MAR);
     double mu = O_MAL + O_MAR;
+    int geo = S->P.tp_mode == 0;
+    if (geo && dt_tp != S->tp_gap_dt) {          /* gaps drawn for another dt: redraw them all */
+        for (int64_t k = 0; k < p->n; k++) p->nev[k] = 0;
+        S->tp_gap_dt = dt_tp;
+    }
     for (int64_t it = 0; it < nsteps; it++) {
         uint32_t s = S->tp_step;
         for (int64_t k = 0; k < p->n; k++) {
@@ -945,27 +1103,56 @@ void orc_tp_step(orc_state *S, int64_t nsteps, double dt_tp)
                 p->alive[k] = 0;
                 continue;
             }
-            uint32_t cg[4], cc[4];
-            draw(S->P.seed, p->id[k], s, PUR_TP_GAS, cg);
-            double n1, n2, n3, n4;
-            box_muller(cg[0], cg[1], &n1, &n2);
-            box_muller(cg[2], cg[3], &n3, &n4);
-            double w[3] = {vg * n1, vg * n2, vg * n3};
-            double g[3] = {p->vx[k] - w[0], p->vy[k] - w[1], p->vz[k] - w[2]};
-            double gm = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
-            double sig = gm > 0.0 ? orc_tp_sigma(S, gm) : 0.0;
-            double P = 1.0 - exp(-S->ngas * sig * gm * dt_tp);
-            draw(S->P.seed, p->id[k], s, PUR_TP_COLL, cc);
-            if (u23(cc[0]) < P) {
+            double v[3] = {p->vx[k], p->vy[k], p->vz[k]};
+            double w[3], g[3];
+            int hit;
+            if (geo) {
+                uint32_t nv = p->nev[k];
+                if (nv == 0u || (int32_t)(nv - 1u - s) < 0) {       /* first gap of this atom */
+                    uint32_t r[4];
+                    draw(S->P.seed, p->id[k], s, PUR_TP_GAP0, r);
+                    double Ph = tp_cand_prob(S, sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]), dt_tp);
+                    if (!(Ph <= 1.0)) S->cnt[C_NUMERICS]++;
+                    nv = s + orc_tp_gap(Ph, r[0]);
+                    p->nev[k] = nv;
+                }
+                if (nv - 1u != s) continue;                           /* not a candidate */
+                hit = tp_candidate(S, p->id[k], s, v, dt_tp, w);
+            } else {
+                uint32_t cg[4], cc0[4];
+                draw(S->P.seed, p->id[k], s, PUR_TP_GAS, cg);
+                double n1, n2, n3, n4;
+                box_muller(cg[0], cg[1], &n1, &n2);
+                box_muller(cg[2], cg[3], &n3, &n4);
+                w[0] = vg * n1; w[1] = vg * n2; w[2] = vg * n3;
+                double gx = v[0] - w[0], gy = v[1] - w[1], gz = v[2] - w[2];
+                double gm0 = sqrt(gx * gx + gy * gy + gz * gz);
+                double sig = gm0 > 0.0 ? orc_tp_sigma(S, gm0) : 0.0;
+                double P = 1.0 - exp(-S->ngas * sig * gm0 * dt_tp);
+                draw(S->P.seed, p->id[k], s, PUR_TP_COLL, cc0);
+                hit = u23(cc0[0]) < P;
+            }
+            if (hit) {
+                uint32_t cc[4];
+                draw(S->P.seed, p->id[k], s, PUR_TP_COLL, cc);
+                for (int i = 0; i < 3; i++) g[i] = v[i] - w[i];
+                double gm = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
                 double d[3];
                 orc_tp_scatter(S->P.tp_model, g, cc[1], cc[2], d);
-                double vc[3] = {(O_MAL * p->vx[k] + O_MAR * w[0]) / mu,
-                                (O_MAL * p->vy[k] + O_MAR * w[1]) / mu,
-                                (O_MAL * p->vz[k] + O_MAR * w[2]) / mu};
+                double vc[3] = {(O_MAL * v[0] + O_MAR * w[0]) / mu, (O_MAL * v[1] + O_MAR * w[1]) / mu,
+                                (O_MAL * v[2] + O_MAR * w[2]) / mu};
                 p->vx[k] = vc[0] + (O_MAR / mu) * gm * d[0];
                 p->vy[k] = vc[1] + (O_MAR / mu) * gm * d[1];
                 p->vz[k] = vc[2] + (O_MAR / mu) * gm * d[2];
                 S->cnt[C_TPCOLL]++;
+            }
+            if (geo) {                                                /* the next candidate */
+                uint32_t r[4];
+                draw(S->P.seed, p->id[k], s, PUR_TP_GAP, r);
+                double vm = sqrt(p->vx[k] * p->vx[k] + p->vy[k] * p->vy[k] + p->vz[k] * p->vz[k]);
+                double Ph = tp_cand_prob(S, vm, dt_tp);
+                if (!(Ph <= 1.0)) S->cnt[C_NUMERICS]++;
+                p->nev[k] = s + 1u + orc_tp_gap(Ph, r[0]);
             }
         }
         /* grid moments of the TP density and mean velocity (Sec. "Limitations
@@ -1053,12 +1240,12 @@ int orc_tpf_partner(uint64_t seed, uint64_t id, uint32_t e, double Tg, const dou
 /* Gamma variate of shape k >= 1 (Marsaglia and Tsang, ACM TOMS 26, 2000):
  * d = k - 1/3, x normal, v = (1 + x/sqrt(9d))^3, accepted when
  * ln U < x^2/2 + d - d v + d ln v; attempt t draws (id, e, TPF_GAMMA + t). */
-static double gamma_mt(double k, uint64_t seed, uint64_t id, uint32_t e)
+static double gamma_mt(double k, uint64_t seed, uint64_t id, uint32_t e, uint32_t base)
 {
     double d = k - 1.0 / 3.0, cc = 1.0 / sqrt(9.0 * d);
     for (int t = 0; t < TPF_GAMMA_TRIES; t++) {
         uint32_t r[4];
-        draw(seed, id, e, PUR_TPF_GAMMA + t, r);
+        draw(seed, id, e, base + t, r);
         double x, unused;
         box_muller(r[0], r[1], &x, &unused);
         double v = 1.0 + cc * x;
@@ -1163,7 +1350,7 @@ int64_t orc_tp_flight(orc_state *S, int64_t max_events)
                     box_muller(a[3], b[0], &n3, &n4);
                     w[0] = vg * n1; w[1] = vg * n2; w[2] = vg * n3;
                 } else {
-                    double sp = c * sqrt(gamma_mt(0.5 * (3.0 + alpha), S->P.seed, p->id[k], e));
+                    double sp = c * sqrt(gamma_mt(0.5 * (3.0 + alpha), S->P.seed, p->id[k], e, PUR_TPF_GAMMA));
                     double dd[3];
                     iso_dir(a[3], b[0], dd);
                     w[0] = sp * dd[0]; w[1] = sp * dd[1]; w[2] = sp * dd[2];
@@ -1255,12 +1442,20 @@ void orc_hypotheses(const orc_state *S, double out[6])
 /* Mono-energetic source: n atoms launched from the left electrode with a
  * Thompson energy (cut off at Lambda E_ion) and a cosine angle; ids
  * tag | (atoms launched before + k). */
+void orc_tp_launch_ids(orc_state *S, int64_t n, double E_ion, int64_t id0);
 void orc_tp_launch(orc_state *S, int64_t n, double E_ion)
+{
+    int64_t id0 = S->tp_launched;
+    S->tp_launched += n;
+    orc_tp_launch_ids(S, n, E_ion, id0);
+}
+
+/* the atoms id0 .. id0 + n - 1 of a source (the share of one rank when a
+ * source is split over several) */
+void orc_tp_launch_ids(orc_state *S, int64_t n, double E_ion, int64_t id0)
 {
     double Emax = lambda_ar_al() * E_ion;
     double N = (double)S->P.ncell;
-    int64_t id0 = S->tp_launched;
-    S->tp_launched += n;
     for (int64_t k = 0; k < n; k++) {
         uint64_t id = TAG[SP_TP] | (uint64_t)(id0 + k);
         uint32_t ce[4];

@@ -49,8 +49,8 @@ class PicParams(C.Structure):
                 ("sort_every_i", C.c_int32), ("sort_every_tp", C.c_int32),
                 ("ctas_per_sm", C.c_int32), ("strict", C.c_int32), ("waveform", C.c_int32),
                 ("circuit", C.c_int32), ("rf_phase", C.c_double), ("c_block", C.c_double),
-                ("tp_model", C.c_int32), ("tp_pad", C.c_int32), ("tp_dref", C.c_double),
-                ("tp_omega", C.c_double), ("tp_tref", C.c_double)]
+                ("tp_model", C.c_int32), ("tp_mode", C.c_int32), ("tp_dref", C.c_double),
+                ("tp_omega", C.c_double), ("tp_tref", C.c_double), ("id_offset", C.c_int64)]
 
 
 class ServerOpts(C.Structure):
@@ -84,7 +84,7 @@ REQUEST_STATES = ["queued", "running", "converged", "max_periods", "rejected", "
 
 
 class TpSource(C.Structure):
-    _fields_ = [("n", C.c_int64), ("e_ion_ev", C.c_double)]
+    _fields_ = [("n", C.c_int64), ("e_ion_ev", C.c_double), ("first_id", C.c_int64)]
 
 
 def lib():
@@ -101,6 +101,7 @@ def lib():
             "pic_create": [C.POINTER(PicParams), vp, C.POINTER(vp)],
             "pic_step": [vp, i64],
             "pic_sync": [vp],
+            "pic_exchange_slot": [vp, C.POINTER(vp), pi64],
             "pic_diag": [vp, C.c_int, vp, i64, pi64],
             "pic_reset_averages": [vp],
             "pic_counters": [vp, vp, i64, pi64],
@@ -178,6 +179,21 @@ def _stream_handle(stream):
     if isinstance(stream, int):
         return stream
     return stream.cuda_stream
+
+
+class _CudaArray:
+    """A device buffer owned by the library, exposed to torch through the
+    CUDA array interface (no copy, no ownership)."""
+
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
+def _device_view(ptr, n, dtype):
+    import torch
+    typestr = {torch.int64: "<i8", torch.float64: "<f8"}[dtype]
+    return torch.as_tensor(_CudaArray(ptr, n, typestr), device="cuda")
 
 
 def default_params() -> PicParams:
@@ -281,9 +297,20 @@ class Discharge:
         E = np.ascontiguousarray(E, dtype=np.float64)
         _check(lib().pic_set_field(self.h, _ptr(E)))
 
-    def tp_launch(self, n, e_ion_ev):
-        src = TpSource(int(n), float(e_ion_ev))
+    def tp_launch(self, n, e_ion_ev, first_id=-1):
+        """Atoms of a mono-energetic source; first_id >= 0 gives them the ids
+        first_id .. first_id + n - 1 (one rank's share of a split source)."""
+        src = TpSource(int(n), float(e_ion_ev), int(first_id))
         _check(lib().tp_launch(self.h, C.byref(src)))
+
+    def exchange_slot(self):
+        """The device int64 block of the current step that ranks sharing one
+        discharge sum in place before the next step (``pic_exchange_slot``),
+        as a torch tensor viewing the context's memory."""
+        import torch
+        ptr, n = C.c_void_p(), C.c_int64()
+        _check(lib().pic_exchange_slot(self.h, C.byref(ptr), C.byref(n)))
+        return _device_view(ptr.value, n.value, torch.int64)
 
     def tp_step(self, n=1, count_alive=True):
         a = C.c_int64()

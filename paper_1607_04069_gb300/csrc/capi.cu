@@ -61,6 +61,8 @@ struct pic_ctx {
     size_t arena_bytes = 0, small_bytes = 0;
     int sms = 0, grid_mover = 0, grid_tp = 0, grid_sort = 0;
     long long h_step = 0, h_tp_step = 0, tp_launched = 0;
+    float tp_gap_scale = 0.0f;       // TP step length (as Dev::tp_scale) the kept candidate gaps belong to
+    long long exch_stride = 0;       // words per array of a rotating deposit slot
     long long acc_upto = 0;          // last step whose state entered the time averages
     unsigned int cur[3] = {0, 0, 0}; // active ping-pong halves (each compaction flips one)
     long long period = 0;            // steps per RF period when that is a whole number, else 0
@@ -102,11 +104,17 @@ void carve(pic_ctx* c, char* base, size_t* small_end, size_t* total)
     const int N1 = c->p.n_cells + 1;
     Dev& d = c->d;
     d.ctl = L.take<Ctl>(base, 1);
-    for (int k = 0; k < 3; ++k)
-        for (int s = 0; s < 2; ++s) {
-            d.qbuf[k][s] = L.take<unsigned long long>(base, N1);
-            d.fbuf[k][s] = L.take<long long>(base, N1);
-        }
+    // each rotating slot is one block [q_e | q_i | f_e | f_i] of exch_stride words
+    // per array (256-byte aligned), so that it can be summed over ranks in one call
+    const size_t stride = ((size_t)N1 + 31) & ~(size_t)31;
+    c->exch_stride = (long long)stride;
+    for (int k = 0; k < 3; ++k) {
+        unsigned long long* blk = L.take<unsigned long long>(base, 4 * stride);
+        d.qbuf[k][0] = blk;
+        d.qbuf[k][1] = blk + stride;
+        d.fbuf[k][0] = (long long*)(blk + 2 * stride);
+        d.fbuf[k][1] = (long long*)(blk + 3 * stride);
+    }
     for (int s = 0; s < 2; ++s) {
         d.diag.sum_q[s] = L.take<unsigned long long>(base, 2 * N1);
         d.diag.sum_flux[s] = L.take<long long>(base, 2 * N1);
@@ -167,6 +175,8 @@ int validate(const pic_params* p)
         return fail(PIC_ERR_INVALID_ARG, "n_cells must be a power of two in [4, 4096]");
     if (p->pos_precision != 32 && p->pos_precision != 64)
         return fail(PIC_ERR_INVALID_ARG, "pos_precision must be 32 or 64");
+    if (p->id_offset < 0 || p->id_offset + (p->n_e0 > p->n_i0 ? p->n_e0 : p->n_i0) > (1ll << 61))
+        return fail(PIC_ERR_INVALID_ARG, "id_offset must be >= 0 and leave the ids below 2^61");
     if (p->n_e0 < 0 || p->n_i0 < 0 || p->cap_e < p->n_e0 || p->cap_i < p->n_i0 || p->cap_tp < 0)
         return fail(PIC_ERR_INVALID_ARG, "counts must be >= 0 and within the capacities");
     if (p->cap_e >= (1ll << 31) || p->cap_i >= (1ll << 31) || p->cap_tp >= (1ll << 32) - 1)
@@ -175,6 +185,7 @@ int validate(const pic_params* p)
         p->sort_every_tp < 0 || p->ctas_per_sm < 0)
         return fail(PIC_ERR_INVALID_ARG, "negative period");
     if (!(p->tp_dt >= 0) || !(p->sigma_tp >= 0)) return fail(PIC_ERR_INVALID_ARG, "tp_dt, sigma_tp >= 0");
+    if (p->tp_mode != 0 && p->tp_mode != 1) return fail(PIC_ERR_INVALID_ARG, "tp_mode must be 0 or 1");
     if (p->tp_model < 0 || p->tp_model > 2 ||
         (p->tp_model > 0 && !(p->tp_dref > 0 && p->tp_omega >= 0.5 && p->tp_omega <= 1.0 && p->tp_tref > 0)))
         return fail(PIC_ERR_INVALID_ARG, "tp_model 0..2; VHS/M1 need tp_dref > 0, 0.5 <= tp_omega <= 1, tp_tref > 0");
@@ -261,6 +272,8 @@ void derive(pic_ctx* c)
     d.tpf_scale = (float)(4294967296.0 / p.gap_m);
     d.tpf_kt = (float)(256.0 * p.gap_m);
     d.tp_model = p.tp_model;
+    d.tp_mode = p.tp_mode;
+    d.tp_ma = (float)(2.0 * std::sqrt(2.0 * kKB * p.gas_temp_k / kMAR) / std::sqrt(kPI));   // <|w|>
     double nK = 0.0;                                    // n K of the VHS / M1 law
     if (p.tp_model > 0) {
         // sigma(g) g = K g^alpha, K = pi d^2 (2 k T_ref / m_r)^(omega - 1/2) / Gamma(5/2 - omega)
@@ -275,6 +288,7 @@ void derive(pic_ctx* c)
         d.tp_nK_dt = (float)(nK * p.tp_dt);
         d.tpf_nK = (float)nK;
         d.tpf_malpha = (float)(std::pow(c, alpha) * std::tgamma(0.5 * (3.0 + alpha)) / std::tgamma(1.5));
+        d.tp_ma = d.tpf_malpha;
         d.tpf_gk = (float)(0.5 * (3.0 + alpha));
     }
     d.Emax_hist = (float)(2.0 * p.rf_volt_v > 0 ? 2.0 * p.rf_volt_v : 1.0);
@@ -398,6 +412,15 @@ int run_tp_step(pic_ctx* c, const Dev& d)
     cudaEvent_t stop;
     int rc = timer_begin(c, 1, &stop);
     if (rc) return rc;
+    if (d.tp_mode == 0 && d.tp_scale != c->tp_gap_scale) {
+        // candidate gaps kept per atom were drawn for another TP step length:
+        // every atom draws its next candidate afresh at this step (the
+        // candidate process is memoryless)
+        for (int h = 0; h < 2; ++h)
+            CK(cudaMemsetAsync(d.buf[kTP][h].nev, 0, ((size_t)(c->p.cap_tp > 0 ? c->p.cap_tp : 1) + 3) / 4 * 16,
+                               c->stream));
+        c->tp_gap_scale = d.tp_scale;
+    }
     CK(launch_tp_step(d, c->grid_tp, c->stream));
     rc = timer_end(c, stop);
     if (rc) return rc;
@@ -532,8 +555,10 @@ int pic_create(const pic_params* pin, void* stream, pic_ctx** out)
     for (int s = 0; s < 2 && e == cudaSuccess; ++s)
         e = cudaMemsetAsync(c->d.evflag[s], 0, (size_t)(s == kE ? c->p.cap_e : c->p.cap_i) + 4, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d.ctl, &h, sizeof h, cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = launch_init(c->d, kE, c->p.n_e0, (float)std::sqrt(c->p.te0_ev * kQE / kME), c->stream);
-    if (e == cudaSuccess) e = launch_init(c->d, kI, c->p.n_i0, (float)std::sqrt(c->p.ti0_ev * kQE / kMAR), c->stream);
+    if (e == cudaSuccess)
+        e = launch_init(c->d, kE, c->p.n_e0, c->p.id_offset, (float)std::sqrt(c->p.te0_ev * kQE / kME), c->stream);
+    if (e == cudaSuccess)
+        e = launch_init(c->d, kI, c->p.n_i0, c->p.id_offset, (float)std::sqrt(c->p.ti0_ev * kQE / kMAR), c->stream);
     // the loading is uniform in space but in id order: bring it into cell order
     for (int sp = 0; sp < 2 && e == cudaSuccess; ++sp) {
         if ((sp == kE ? c->p.n_e0 : c->p.n_i0) <= 0) continue;
@@ -1056,10 +1081,23 @@ int pic_set_field(pic_ctx* c, const double* E)
 int tp_launch(pic_ctx* c, const tp_source* src)
 {
     if (!c || !src || src->n < 0 || !(src->e_ion_ev >= 0)) return fail(PIC_ERR_INVALID_ARG, "bad source");
+    if (src->first_id >= 0 && src->first_id + src->n > (1ll << 61))
+        return fail(PIC_ERR_INVALID_ARG, "source ids must stay below 2^61");
     CK(cudaSetDevice(c->device));
     const float Emax = (float)(c->derived[7] * src->e_ion_ev);
-    CK(launch_tp_launch(c->d, src->n, c->tp_launched, Emax, c->stream));
+    CK(launch_tp_launch(c->d, src->n, src->first_id >= 0 ? src->first_id : c->tp_launched, Emax, c->stream));
     c->tp_launched += src->n;
+    return PIC_OK;
+}
+
+int pic_exchange_slot(pic_ctx* c, int64_t** dev, int64_t* n_words)
+{
+    if (!c || !dev || !n_words) return fail(PIC_ERR_INVALID_ARG, "NULL argument");
+    if (c->p.circuit) return fail(PIC_ERR_INVALID_ARG, "the series capacitor needs the whole wall charge: "
+                                                       "no split discharge with circuit 1");
+    const int slot = (int)(c->h_step % 3);
+    *dev = (int64_t*)c->d.qbuf[slot][0];
+    *n_words = 4 * c->exch_stride;
     return PIC_OK;
 }
 

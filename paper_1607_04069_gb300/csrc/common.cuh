@@ -50,7 +50,7 @@ enum : uint32_t {
     kPurGap = 7, kPurGap0 = 8,
     kPurSpTrial = 16, kPurSpEmit = 32, kPurSpId = 48, kPurTpGas = 64, kPurTpColl = 65,
     kPurTpLaunch = 66, kPurTpfFlight = 70, kPurTpfScatter = 71, kPurTpfPartner = 72, kPurTpfCand = 200,
-    kPurTpfGamma = 202
+    kPurTpfGamma = 202, kPurTpCand = 256, kPurTpGamma = 258, kPurTpGap = 290, kPurTpGap0 = 291
 };
 
 // species and id tags
@@ -171,7 +171,8 @@ struct Dev {                   // everything a kernel needs, passed by value
     // electrons absorbed at x = 0 (Ctl::wall_dn), circ_a = 2 (1 - beta) / A,
     // circ_b = 2 beta, beta = 1 / (1 + L c / eps0)
     double circ_a, circ_b;
-    int circuit, pad3;
+    int circuit;
+    int tp_mode;                     // TP step collisions: 0 thinned candidates, 1 the literal test
     // event-driven TP flight
     float tpf_c;                     // most probable speed of the gas, sqrt(2 k T / M_Ar)
     float tpf_nsig;                  // n sigma_tp, 1/m
@@ -190,7 +191,7 @@ struct Dev {                   // everything a kernel needs, passed by value
     const float2* xs_tab[3];
     int xs_n[3], xs_pad;
     float c2f;                       // A / (2 dx): E per unit of the integer bracket
-    float pad2;
+    float tp_ma;                     // <|w|^alpha> of the gas (hard spheres: <|w|> = 2 c / sqrt(pi))
     // push
     float qm_dt[2];                  // (q/m) dt
     float push32;                    // dt 2^32 / L  (fixed-point displacement per m/s)

@@ -16,7 +16,8 @@ constexpr int kTpThreads = 256;
 size_t mover_smem(int ncell);
 size_t tp_smem(int ncell);
 cudaError_t mover_occupancy(const Dev& d, int* blocks_per_sm);
-cudaError_t launch_init(const Dev& d, int s, long long n, float vth, cudaStream_t st);
+// initial loading of n particles with ids tag | (id0 + k)
+cudaError_t launch_init(const Dev& d, int s, long long n, long long id0, float vth, cudaStream_t st);
 // mode 0: one PIC/MCC step; mode 1: deposit the current state and solve the field
 cudaError_t launch_mover(const Dev& d, const StepArgs& a, int grid, int mode, cudaStream_t st);
 // one step of every discharge of a batch (32-bit positions); sample: the launch

@@ -17,12 +17,12 @@ namespace pg {
 // Initial loading (Sec. "Kinetic Particle Simulation"): uniform positions,
 // Maxwellian velocities at T (eV) by Box-Muller, ids tag | k.
 template <bool P64>
-__global__ void k_init(Dev d, int s, long long n, float vth)
+__global__ void k_init(Dev d, int s, long long n, long long id0, float vth)
 {
     const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (k >= n) return;
     const SpBuf B = d.buf[s][d.ctl->cur[s]];
-    const uint64_t id = id_tag(s) | (uint64_t)k;
+    const uint64_t id = id_tag(s) | (uint64_t)(id0 + k);
     const uint4 a = draw(d.seed, id, 0, kPurInit);
     const uint4 b = draw(d.seed, id, 1, kPurInit);
     const uint32_t fx = a.x | 1u;
@@ -1118,13 +1118,13 @@ size_t mover_smem(int ncell)
            kQueueCap * 4;
 }
 
-cudaError_t launch_init(const Dev& d, int s, long long n, float vth, cudaStream_t st)
+cudaError_t launch_init(const Dev& d, int s, long long n, long long id0, float vth, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
     const int T = 256;
     const long long G = (n + T - 1) / T;
-    if (d.pos64 && s != kTP) k_init<true><<<(unsigned)G, T, 0, st>>>(d, s, n, vth);
-    else k_init<false><<<(unsigned)G, T, 0, st>>>(d, s, n, vth);
+    if (d.pos64 && s != kTP) k_init<true><<<(unsigned)G, T, 0, st>>>(d, s, n, id0, vth);
+    else k_init<false><<<(unsigned)G, T, 0, st>>>(d, s, n, id0, vth);
     return cudaGetLastError();
 }
 

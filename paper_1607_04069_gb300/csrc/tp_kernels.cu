@@ -259,6 +259,271 @@ __global__ void __launch_bounds__(kTpThreads, 2) k_tp_step(Dev d)
 }
 
 
+// ---------------------------------------------------------------- TP step, thinned candidates
+// tp_mode 0 (Sec. "Test Particle Method", Eq. collisionprobability1 with a
+// partner w from the Maxwellian gas): the per-step probability p(g) = 1 -
+// exp(-n K dt g^alpha) (hard spheres: K = sigma_tp, alpha = 1) is bounded by
+// n K dt (|v|^alpha + |w|^alpha) (alpha <= 1), so every step is a candidate
+// with P^ = n K dt (|v|^alpha + <|w|^alpha>), rounded up to 8 significant
+// bits; the steps between candidates are geometric and each atom keeps its
+// next candidate step plus one in nev (0: none drawn yet, drawn at the first
+// step that moves it).  A candidate draws one partner from (|v|^alpha +
+// |w|^alpha) f(w) and collides with probability p(g) (|v|^alpha +
+// <|w|^alpha>) / (P^ (|v|^alpha + |w|^alpha)); the product is f(w) p(g), the
+// per-step law, and |v| changes only at a collision.  The stream thus reads
+// x, v_x and the candidate step and writes x; v_y, v_z and the id are read
+// only at candidates and at the walls.  Random words: (id, s, TP_GAP0) for the
+// first gap, (id, s, TP_CAND / TP_CAND + 1) for the proposal, (id, s,
+// TP_GAMMA + t) for its gamma attempts (VHS / M1), (id, s, TP_COLL) words 1, 2
+// for the scattering, (id, s, TP_GAP) for the next gap; s the TP step.
+
+// x rounded up to 8 significant bits (0, NaN and infinity unchanged)
+__device__ __forceinline__ float round_up8(float x)
+{
+    if (!(x > 0.0f) || isinf(x)) return x;
+    int e;
+    const float m = frexpf(x, &e);
+    return ldexpf(ceilf(m * 256.0f) * (1.0f / 256.0f), e);
+}
+
+// TP steps from one candidate to the next at the per-step probability Ph:
+// 1 + floor(ln R / ln(1 - Ph)), the floor of the FP64 quotient; FP32 first,
+// FP64 when an integer lies within the FP32 error of the quotient.
+__device__ __noinline__ uint32_t tp_gap(float Ph, uint32_t w)
+{
+    if (!(Ph < 1.0f)) return 1u;
+    if (!(Ph > 0.0f)) return 2147483647u;
+    const float uf = u23(w);
+    const float xf = logf(uf) / log1pf(-Ph);
+    if (xf < 1.0e6f) {
+        const float dl = 8e-7f * xf + 1e-6f;
+        const float a = floorf(xf - dl), b = floorf(xf + dl);
+        if (a == b) return 1u + (uint32_t)a;
+    }
+    const double x = log(((double)(w >> 9) + 0.5) * 0x1p-23) / log1p(-(double)Ph);
+    if (!(x < 2147483646.0)) return 2147483647u;
+    return 1u + (uint32_t)floor(x);
+}
+
+// the per-step candidate probability P^ of an atom of speed vm
+template <bool LAW>
+__device__ __forceinline__ float tp_cand_prob(const Dev& d, float vm)
+{
+    return LAW ? round_up8(d.tp_nK_dt * (powf(vm, d.tp_alpha) + d.tp_ma))
+               : round_up8(d.tp_nsig_dt * (vm + d.tp_ma));
+}
+
+// Gamma variate of shape k >= 1 (Marsaglia and Tsang, ACM TOMS 26, 2000),
+// attempt t from Philox(id, ctr, base + t); d after 32 rejections
+__device__ __noinline__ float gamma_mt(float k, uint64_t seed, uint64_t id, uint32_t ctr, uint32_t base)
+{
+    const float dd = k - (1.0f / 3.0f), cc = 1.0f / sqrtf(9.0f * dd);
+    for (int t = 0; t < 32; ++t) {
+        const uint4 r = draw(seed, id, ctr, base + t);
+        const float x = box_muller(r.x, r.y).x;
+        float v = 1.0f + cc * x;
+        if (v <= 0.0f) continue;
+        v = v * v * v;
+        if (logf(u23(r.z)) < 0.5f * x * x + dd - dd * v + dd * logf(v)) return dd * v;
+    }
+    return dd;
+}
+
+// An atom whose candidate step is due (or not drawn yet) at TP step s: draws
+// the first gap if needed, handles the candidate and draws the next gap.
+// Returns the new v_x; v_y, v_z and nev are stored here.  *hit: a collision.
+template <bool LAW>
+__device__ __noinline__ float tp_candidate(const Dev& d, const SpBuf& B, long long i, uint32_t s, float vx,
+                                           uint32_t nv, bool* hit)
+{
+    float vy = B.vy[i], vz = B.vz[i];
+    const uint64_t id = B.id[i];
+    const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
+    float vm = sqrtf(vx * vx + vy * vy + vz * vz);
+    *hit = false;
+    if (nv == 0u || (int)(nv - 1u - s) < 0) {                 // first gap of this atom
+        const float Ph = tp_cand_prob<LAW>(d, vm);
+        if (!(Ph <= 1.0f)) atomicAdd(&d.ctl->cnt[kCntNumerics], 1ull);
+        nv = s + tp_gap(Ph, draw(d.seed, id, s, kPurTpGap0).x);
+    }
+    if (nv - 1u != s) {
+        B.nev[i] = nv;
+        return vx;
+    }
+    uint4 cw[2];
+    cw[0] = make_uint4((uint32_t)id, (uint32_t)(id >> 32), s, kPurTpCand);
+    cw[1] = make_uint4((uint32_t)id, (uint32_t)(id >> 32), s, kPurTpCand + 1);
+    philox_n<2>(cw, k0, k1);
+    const uint4 a = cw[0], b = cw[1];
+    const float c = d.tpf_c;
+    const float va = LAW ? powf(vm, d.tp_alpha) : vm;
+    float wx, wy, wz;
+    if (u23(a.x) * (va + d.tp_ma) < va) {                    // a Maxwellian partner
+        const float2 n12 = box_muller(a.y, a.z), n34 = box_muller(a.w, b.x);
+        wx = d.vth_gas * n12.x; wy = d.vth_gas * n12.y; wz = d.vth_gas * n34.x;
+    } else {                                                 // |w|^alpha-weighted partner
+        const float x2 = LAW ? gamma_mt(d.tpf_gk, d.seed, id, s, kPurTpGamma) : -logf(u23(a.y) * u23(a.z));
+        const float sp = c * sqrtf(x2);
+        const float3 dd = iso_dir(a.w, b.x);
+        wx = sp * dd.x; wy = sp * dd.y; wz = sp * dd.z;
+    }
+    const float gx = vx - wx, gy = vy - wy, gz = vz - wz;
+    const float gm = sqrtf(gx * gx + gy * gy + gz * gz);
+    const float wm = sqrtf(wx * wx + wy * wy + wz * wz);
+    const float Ph = tp_cand_prob<LAW>(d, vm);
+    const float ga = LAW ? powf(gm, d.tp_alpha) : gm, wa = LAW ? powf(wm, d.tp_alpha) : wm;
+    const float bK = LAW ? d.tp_nK_dt : d.tp_nsig_dt;
+    if (u23(b.y) * Ph * (va + wa) < (va + d.tp_ma) * -expm1f(-bK * ga)) {   // a real collision
+        const uint4 cc = draw(d.seed, id, s, kPurTpColl);
+        const float3 dir = LAW ? tp_scatter_dir(d.tp_model, gx, gy, gz, gm, cc.y, cc.z) : iso_dir(cc.y, cc.z);
+        const float mu_al = (float)(kMAL / (kMAL + kMAR)), mu_ar = (float)(kMAR / (kMAL + kMAR));
+        vx = mu_al * vx + mu_ar * wx + mu_ar * gm * dir.x;
+        vy = mu_al * vy + mu_ar * wy + mu_ar * gm * dir.y;
+        vz = mu_al * vz + mu_ar * wz + mu_ar * gm * dir.z;
+        B.vy[i] = vy;
+        B.vz[i] = vz;
+        vm = sqrtf(vx * vx + vy * vy + vz * vz);
+        *hit = true;
+    }
+    const float Pn = tp_cand_prob<LAW>(d, vm);
+    if (!(Pn <= 1.0f)) atomicAdd(&d.ctl->cnt[kCntNumerics], 1ull);
+    B.nev[i] = s + 1u + tp_gap(Pn, draw(d.seed, id, s, kPurTpGap).x);
+    return vx;
+}
+
+// An atom that reached an electrode: its energy and angle into that
+// electrode's deposition histograms (Sec. "Wall Interactions" of the TPM)
+__device__ __noinline__ void tp_stick(const Dev& d, const SpBuf& B, long long i, int el, float vx)
+{
+    const float vy = B.vy[i], vz = B.vz[i];
+    const float v2 = vx * vx + vy * vy + vz * vz;
+    const float E = v2 * (float)(0.5 * kMAL / kQE);
+    const float ct = fminf(v2 > 0.0f ? fabsf(vx) * rsqrtf(v2) : 1.0f, 1.0f);
+    atomicAdd(&d.diag.sp_e[el][hist_bin(E, 300.0f, kNbSpE)], 1ull);
+    atomicAdd(&d.diag.sp_ang[el][clamp_bin(acosf(ct) * (float)(180.0 / kPI), kNbAng)], 1ull);
+    atomicAdd(&d.ctl->cnt[el == 0 ? kCntTpDepL : kCntTpDepR], 1ull);
+}
+
+template <bool LAW>
+__global__ void __launch_bounds__(kTpThreads, 4) k_tp_step_geo(Dev d)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = d.ncell;
+    TpAcc A;
+    A.cnt = (unsigned int*)smem_raw;
+    A.whi = A.cnt + N;
+    A.wlo = A.whi + N;
+    A.flo = A.wlo + N;
+    A.fhi = (int*)(A.flo + N + 1);
+    __shared__ unsigned int s_coll;
+    __shared__ int s_last;
+
+    Ctl* ctl = d.ctl;
+    const unsigned int s = ctl->tp_step;
+    const long long n = ctl->n[kTP];
+    const bool sample = d.diag_every > 0 && ((s + 1) % (unsigned)d.diag_every == 0);
+    const long long G4 = (n + 3) >> 2;
+    const long long g0 = G4 * blockIdx.x / gridDim.x, g1 = G4 * (blockIdx.x + 1) / gridDim.x;
+    if (sample)
+        for (int m = threadIdx.x; m <= N; m += blockDim.x) {
+            if (m < N) A.cnt[m] = A.whi[m] = A.wlo[m] = 0;
+            A.flo[m] = 0;
+            A.fhi[m] = 0;
+        }
+    if (threadIdx.x == 0) s_coll = 0;
+    __syncthreads();
+
+    const SpBuf B = d.buf[kTP][ctl->cur[kTP]];
+    unsigned int ncoll = 0;
+    for (long long t0 = g0; t0 < g1; t0 += kTpTileGroups) {
+        const long long t1 = min(g1, t0 + kTpTileGroups);
+        long long g = t0 + threadIdx.x;
+        uint4 P = make_uint4(0u, 0u, 0u, 0u), NV = P;
+        float4 VX = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (g < t1) {
+            P = ((const uint4*)B.pos)[g];
+            VX = ((const float4*)B.vx)[g];
+            NV = ((const uint4*)B.nev)[g];
+        }
+        for (; g < t1; g += blockDim.x) {
+            uint32_t x[4] = {P.x, P.y, P.z, P.w};
+            float vx[4] = {VX.x, VX.y, VX.z, VX.w};
+            const uint32_t nv[4] = {NV.x, NV.y, NV.z, NV.w};
+            if (g + blockDim.x < t1) {                    // the next group, in flight meanwhile
+                P = ((const uint4*)B.pos)[g + blockDim.x];
+                VX = ((const float4*)B.vx)[g + blockDim.x];
+                NV = ((const uint4*)B.nev)[g + blockDim.x];
+            }
+            if (4 * g + 4 > n)                             // slots past n hold no atom
+#pragma unroll
+                for (int u = 1; u < 4; ++u)
+                    if (4 * g + u >= n) x[u] = 0u;
+            if ((x[0] | x[1] | x[2] | x[3]) == 0u) continue;
+            bool moved = false;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (x[u] == 0u) continue;
+                const long long np = (long long)x[u] + __float2ll_rn(vx[u] * d.tp_scale);
+                if (np <= 0 || np >= 4294967296LL) {       // sticks at an electrode
+                    tp_stick(d, B, 4 * g + u, np <= 0 ? 0 : 1, vx[u]);
+                    x[u] = 0u;
+                    continue;
+                }
+                x[u] = (uint32_t)np;
+                if (nv[u] == 0u || (int)(nv[u] - 1u - s) <= 0) {   // a candidate due, or no gap yet
+                    bool hit;
+                    vx[u] = tp_candidate<LAW>(d, B, 4 * g + u, s, vx[u], nv[u], &hit);
+                    if (hit) {
+                        moved = true;
+                        ++ncoll;
+                    }
+                }
+                if (sample) {
+                    uint32_t j, wr;
+                    cell_of(x[u], d.kshift, j, wr);
+                    atomicAdd(&A.cnt[j], 1u);
+                    atomicAdd(&A.whi[j], wr >> 16);
+                    atomicAdd(&A.wlo[j], wr & 0xffffu);
+                    const long long vq = (long long)__float2int_rn(vx[u]);
+                    const long long w16 = (long long)(wr >> 16);
+                    tp_add64(A, j, vq * (65536 - w16));
+                    tp_add64(A, j + 1, vq * w16);
+                }
+            }
+            ((uint4*)B.pos)[g] = make_uint4(x[0], x[1], x[2], x[3]);
+            if (moved) ((float4*)B.vx)[g] = make_float4(vx[0], vx[1], vx[2], vx[3]);
+        }
+        if (sample) {                                      // this tile's tallies into the step's histograms
+            __syncthreads();
+            tp_flush(A, N, d.tp_q, d.tp_flux, threadIdx.x, blockDim.x);
+            __syncthreads();
+        }
+    }
+    ncoll = __reduce_add_sync(0xffffffffu, ncoll);
+    if ((threadIdx.x & 31) == 0 && ncoll) atomicAdd(&s_coll, ncoll);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_coll) atomicAdd(&ctl->cnt[kCntTpColl], (unsigned long long)s_coll);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&ctl->tp_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int m = threadIdx.x; m <= N; m += blockDim.x) {
+        if (sample) {
+            red_split(d.diag.tp_dens + 2 * m, __ldcg(d.tp_q + m));
+            red_split_signed(d.diag.tp_vx + 2 * m, __ldcg(d.tp_flux + m));
+        }
+        d.tp_q[m] = 0;
+        d.tp_flux[m] = 0;
+    }
+    if (threadIdx.x == 0) {
+        ctl->tp_step = s + 1;
+        if (sample) ctl->n_tp_samp += 1;
+        ctl->tp_done = 0;
+    }
+}
+
 // ---------------------------------------------------------------- event-driven flight
 // The gridless alternative to the per-step collision test (Sec. "Kinetic
 // Particle Simulation": free flight tau = -tau_c ln R_f between events; Sec.
@@ -273,22 +538,6 @@ __global__ void __launch_bounds__(kTpThreads, 2) k_tp_step(Dev d)
 // proposal t and (id, e, TPF_SCATTER); e is kept per atom (SpBuf::nev).  One
 // thread takes one atom through up to kmax events per launch.
 constexpr int kTpfTries = 64;                     // proposals per collision (each accepted w.p. >= 1/2)
-
-// Gamma variate of shape k >= 1 (Marsaglia and Tsang, ACM TOMS 26, 2000),
-// attempt t from Philox(id, e, TPF_GAMMA + t); d after 32 rejections
-__device__ __noinline__ float gamma_mt(float k, uint64_t seed, uint64_t id, uint32_t e)
-{
-    const float dd = k - (1.0f / 3.0f), cc = 1.0f / sqrtf(9.0f * dd);
-    for (int t = 0; t < 32; ++t) {
-        const uint4 r = draw(seed, id, e, kPurTpfGamma + t);
-        const float x = box_muller(r.x, r.y).x;
-        float v = 1.0f + cc * x;
-        if (v <= 0.0f) continue;
-        v = v * v * v;
-        if (logf(u23(r.z)) < 0.5f * x * x + dd - dd * v + dd * logf(v)) return dd * v;
-    }
-    return dd;
-}
 
 __device__ __forceinline__ float mean_rel_speed(float vm, float c)
 {
@@ -479,7 +728,7 @@ __global__ void __launch_bounds__(kTpThreads) k_tp_flight(Dev d, int kmax)
                         const float2 n12 = box_muller(a.y, a.z), n34 = box_muller(a.w, b.x);
                         wx = vg * n12.x; wy = vg * n12.y; wz = vg * n34.x;
                     } else {
-                        const float sp = c * sqrtf(gamma_mt(d.tpf_gk, d.seed, id, e));
+                        const float sp = c * sqrtf(gamma_mt(d.tpf_gk, d.seed, id, e, kPurTpfGamma));
                         const float3 dd = iso_dir(a.w, b.x);
                         wx = sp * dd.x; wy = sp * dd.y; wz = sp * dd.z;
                     }
@@ -588,13 +837,20 @@ cudaError_t launch_tp_flight(const Dev& d, int kmax, long long n, cudaStream_t s
 cudaError_t launch_tp_step(const Dev& d, int grid, cudaStream_t st)
 {
     const size_t sm = tp_smem(d.ncell);
+    const void* fn = d.tp_mode == 0
+                         ? (d.tp_model ? (const void*)k_tp_step_geo<true> : (const void*)k_tp_step_geo<false>)
+                         : (d.tp_model ? (const void*)k_tp_step<true> : (const void*)k_tp_step<false>);
     if (sm > 48 * 1024) {
-        const void* fn = d.tp_model ? (const void*)k_tp_step<true> : (const void*)k_tp_step<false>;
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
     }
-    if (d.tp_model) k_tp_step<true><<<grid, kTpThreads, sm, st>>>(d);
-    else k_tp_step<false><<<grid, kTpThreads, sm, st>>>(d);
+    if (d.tp_mode == 0) {
+        if (d.tp_model) k_tp_step_geo<true><<<grid, kTpThreads, sm, st>>>(d);
+        else k_tp_step_geo<false><<<grid, kTpThreads, sm, st>>>(d);
+    } else {
+        if (d.tp_model) k_tp_step<true><<<grid, kTpThreads, sm, st>>>(d);
+        else k_tp_step<false><<<grid, kTpThreads, sm, st>>>(d);
+    }
     return cudaGetLastError();
 }
 

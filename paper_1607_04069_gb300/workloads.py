@@ -96,7 +96,8 @@ def oracle_params(cfg: dict) -> dict:
                 diag_every=cfg["diag_every"], waveform=cfg.get("waveform", 0), circuit=cfg.get("circuit", 0),
                 phase=cfg.get("rf_phase", 0.0), cb=cfg.get("c_block", math.inf),
                 dref=cfg.get("tp_dref", 0.0), omega=cfg.get("tp_omega", 0.5), tref=cfg.get("tp_tref", 273.0),
-                tp_model=cfg.get("tp_model", 0), coll_mode=cfg.get("coll_mode", 0))
+                tp_model=cfg.get("tp_model", 0), coll_mode=cfg.get("coll_mode", 0),
+                tp_mode=cfg.get("tp_mode", 0))
 
 
 # ------------------------------------------------------------- particle sets

@@ -297,12 +297,17 @@ def test_sputter_launch_parity(E_ion, V0):
 
 
 # ------------------------------------------------------------------ test particles
-def test_tp_transport_parity():
+@pytest.mark.parametrize("tp_mode", [0, 1], ids=["thinned", "literal"])
+def test_tp_transport_parity(tp_mode):
     """Mono-energetic 300 eV source, 200 TP steps of 1 ns: every atom's state
     within FP32 rounding of the oracle's, the same atoms deposited, and the
-    counts conserved (launched = deposited + in flight)."""
+    counts conserved (launched = deposited + in flight).  tp_mode 0: thinned
+    candidates with geometric gaps; an atom whose candidate probability lies
+    within FP32 rounding of a step of its 8-bit grid may draw another gap on
+    the two sides (about 3e-5 per draw), so up to 1 in 2000 atoms may follow
+    another history.  tp_mode 1: the literal test every step."""
     cfg = W.tp_transport(n_atoms=50_000)
-    cfg.update(cap_tp=60_000, n_e0=0, n_i0=0, sort_every_tp=0)
+    cfg.update(cap_tp=60_000, n_e0=0, n_i0=0, sort_every_tp=0, tp_mode=tp_mode)
     d = gpu_discharge(cfg)
     orc = oracle_for(cfg, cap=10, cap_tp=60_000)
     d.tp_launch(50_000, 300.0)
@@ -310,14 +315,16 @@ def test_tp_transport_parity():
     alive = d.tp_step(200)
     orc.tp_step(200, cfg["tp_dt"])
     c, oc = d.counters(), orc.counters()
+    slack = 4 if tp_mode == 1 else 25
     assert c["tp_dep_l"] + c["tp_dep_r"] + alive == 50_000
-    assert abs(c["tp_coll"] - oc["tp_coll"]) <= 2
-    assert abs(c["tp_dep_r"] - oc["tp_dep_r"]) <= 2 and abs(c["tp_dep_l"] - oc["tp_dep_l"]) <= 2
+    assert abs(c["tp_coll"] - oc["tp_coll"]) <= slack // 2
+    assert abs(c["tp_dep_r"] - oc["tp_dep_r"]) <= slack // 2 and abs(c["tp_dep_l"] - oc["tp_dep_l"]) <= slack // 2
     g, o, only_g, only_o = match(d.get_species(2), orc.get_species(2))
-    assert len(only_g) + len(only_o) <= 4
+    assert len(only_g) + len(only_o) <= slack
     vmag = np.sqrt(o["vx"]**2 + o["vy"]**2 + o["vz"]**2)
     bad = np.abs(g["vx"] - o["vx"]) > 1e-3 * vmag + 1e-2
-    assert bad.sum() <= 4
+    assert bad.sum() <= slack
+    assert c["tp_coll"] > 1000 and c["numerics"] == oc["numerics"] == 0
     d.close()
 
 

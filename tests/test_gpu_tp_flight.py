@@ -134,13 +134,18 @@ def test_vhs_and_m1_flights_match_oracle(model):
     d.close()
 
 
+@pytest.mark.parametrize("tp_mode", [0, 1], ids=["thinned", "literal"])
 @pytest.mark.parametrize("model", [1, 2], ids=["vhs", "m1"])
-def test_vhs_and_m1_per_step_transport_matches_oracle(model):
+def test_vhs_and_m1_per_step_transport_matches_oracle(model, tp_mode):
     """tp_step under the VHS and M1 laws (per-step probability 1 -
-    exp(-n K g^alpha dt) with a sampled partner): 200 steps of 1 ns, every
-    atom within FP32 rounding of the oracle's, the same atoms deposited."""
+    exp(-n K g^alpha dt) with a sampled partner; thinned candidates or the
+    test every step): 200 steps of 1 ns, every atom within FP32 rounding of
+    the oracle's, the same atoms deposited.  With thinned candidates an atom
+    whose candidate probability lies within FP32 rounding of a step of its
+    8-bit grid may draw another gap on the two sides (about 3e-5 per draw),
+    so up to 1 in 2000 atoms may follow another history."""
     cfg = W.tp_transport(n_atoms=50_000)
-    cfg.update(cap_tp=60_000, n_e0=0, n_i0=0, sort_every_tp=0, tp_model=model, **VHS)
+    cfg.update(cap_tp=60_000, n_e0=0, n_i0=0, sort_every_tp=0, tp_model=model, tp_mode=tp_mode, **VHS)
     d = gpu_discharge(cfg)
     orc = oracle_for(cfg, cap=10, cap_tp=60_000)
     d.tp_launch(50_000, 300.0)
@@ -149,9 +154,11 @@ def test_vhs_and_m1_per_step_transport_matches_oracle(model):
     orc.tp_step(200, cfg["tp_dt"])
     c, oc = d.counters(), orc.counters()
     assert c["tp_dep_l"] + c["tp_dep_r"] + alive == 50_000
-    assert abs(c["tp_coll"] - oc["tp_coll"]) <= 3
+    slack = 6 if tp_mode == 1 else 25
+    assert abs(c["tp_coll"] - oc["tp_coll"]) <= slack // 2
     g, o, only_g, only_o = match(d.get_species(2), orc.get_species(2))
-    assert len(only_g) + len(only_o) <= 6
+    assert len(only_g) + len(only_o) <= slack
     vmag = np.sqrt(o["vx"]**2 + o["vy"]**2 + o["vz"]**2)
-    assert (np.abs(g["vx"] - o["vx"]) > 1e-3 * vmag + 1e-2).sum() <= 6
+    assert (np.abs(g["vx"] - o["vx"]) > 1e-3 * vmag + 1e-2).sum() <= slack
+    assert c["numerics"] == oc["numerics"] == 0
     d.close()

@@ -569,7 +569,8 @@ def test_tp_ballistic_flight_without_collisions():
     assert e[min(int(E / 300 * 600), 599)] == n
 
 
-def test_tp_collision_rate_in_maxwellian_gas():
+@pytest.mark.parametrize("tp_mode", [0, 1])
+def test_tp_collision_rate_in_maxwellian_gas(tp_mode):
     """TP collision probability per step for speed v in a Maxwellian gas:
     n sigma <g> dt - (n sigma dt)^2 <g^2>/2 + O(3), with the textbook mean
     relative speed <g> = c[(s + 1/(2s)) erf(s) + exp(-s^2)/sqrt(pi)],
@@ -577,7 +578,7 @@ def test_tp_collision_rate_in_maxwellian_gas():
     n, p, T, dt, sig = 400_000, 0.5, 300.0, 2e-8, 3e-19
     for v in (300.0, 2000.0):
         rng = np.random.default_rng(int(v))
-        orc = O.Oracle(prm(L=100.0, ncell=1024, p=p, Tg=T, sigma_tp=sig), 1, 1, n)
+        orc = O.Oracle(prm(L=100.0, ncell=1024, p=p, Tg=T, sigma_tp=sig, tp_mode=tp_mode), 1, 1, n)
         load(orc, 2, np.full(n, 512.0), _mono(n, v, rng))
         orc.tp_step(1, dt)
         ngas = p / (KB * T)
@@ -591,14 +592,82 @@ def test_tp_collision_rate_in_maxwellian_gas():
         assert abs(got - n * pexp) < 4.5 * math.sqrt(n * pexp)
 
 
-def test_tp_thermalizes_to_gas_temperature():
+def _rel_speed_density(g, v, c):
+    """Density of g = |v - w| for a fixed velocity of magnitude v and w from
+    the Maxwellian of most probable speed c (kinetic theory)."""
+    return g / (v * c * math.sqrt(math.pi)) * (np.exp(-(g - v) ** 2 / c**2) - np.exp(-(g + v) ** 2 / c**2))
+
+
+@pytest.mark.parametrize("model", [0, 1, 2])
+def test_tp_candidate_thinning_gives_the_exact_per_step_law(model):
+    """The thinned candidates of the TP step (tp_mode 0) reproduce the per-step
+    law of Eq. collisionprobability1 with a sampled partner exactly, not only
+    to first order: at P^ ~ 0.6 the collision probability of one step equals
+    E_w[1 - exp(-n K dt g^alpha)], by quadrature over the density of the
+    relative speed, within the binomial error, in both modes; and the
+    post-collision speeds of the two modes have one distribution (KS).  Hard
+    spheres, VHS and M1 (omega = 0.81)."""
+    n, p, T, v = 200_000, 0.5, 300.0, 2000.0
+    ngas = p / (KB * T)
+    c = math.sqrt(2 * KB * T / MAR)
+    kw = dict(L=100.0, ncell=1024, p=p, Tg=T, sigma_tp=3e-19, tp_model=model, dref=4.17e-10, omega=0.81,
+              tref=273.0, seed=31 + model)
+    probe = O.Oracle(prm(**kw), 1, 1, 1)
+    alpha = 1.0 if model == 0 else 2.0 - 2.0 * 0.81
+    K = probe.tp_sigma(1.0) if model else 3e-19
+    ma = c**alpha * special.gamma(0.5 * (3 + alpha)) / special.gamma(1.5)
+    dt = 0.6 / (ngas * K * (v**alpha + ma))                       # P^ = 0.6
+    b = ngas * K * dt
+    g = np.linspace(0.0, v + 12 * c, 400_001)
+    fg = _rel_speed_density(g, v, c)
+    assert abs(np.trapezoid(fg, g) - 1) < 1e-9
+    P = float(np.trapezoid(fg * -np.expm1(-b * g**alpha), g))
+    speeds = []
+    for mode in (0, 1):
+        rng = np.random.default_rng(77)
+        orc = O.Oracle(prm(tp_mode=mode, **kw), 1, 1, n)
+        load(orc, 2, np.full(n, 512.0), _mono(n, v, rng))
+        orc.tp_step(1, dt)
+        got = orc.counters()["tp_coll"]
+        assert abs(got - n * P) < 4.5 * math.sqrt(n * P * (1 - P)), (mode, got, n * P)
+        assert orc.counters()["numerics"] == 0
+        sp = orc.get_species(2)
+        vm = np.sqrt(sp["vx"]**2 + sp["vy"]**2 + sp["vz"]**2)
+        speeds.append(vm[np.abs(vm - v) > 1e-6 * v])
+    assert stats.ks_2samp(speeds[0], speeds[1]).pvalue > 1e-3
+
+
+def test_tp_candidate_gap_is_geometric():
+    """TP steps between candidates at the per-step probability P^: gap n has
+    probability (1 - P^)^(n-1) P^ (chi-square over 1..40 and the tail, and the
+    mean 1/P^); P^ >= 1 makes every step a candidate, P^ = 0 none."""
+    Ph = 0.07
+    words = [int(O.philox([k, 9, 4, 290], [5, 6])[0]) for k in range(60_000)]
+    g = np.array([O.tp_gap(Ph, w) for w in words])
+    assert g.min() >= 1
+    nmax = 40
+    obs = np.bincount(np.minimum(g, nmax + 1), minlength=nmax + 2)[1:]
+    exp_ = np.array([(1 - Ph) ** (m - 1) * Ph for m in range(1, nmax + 1)] + [(1 - Ph) ** nmax]) * len(g)
+    assert stats.chi2.sf(((obs - exp_) ** 2 / exp_).sum(), len(exp_) - 1) > 1e-3
+    assert abs(g.mean() - 1 / Ph) < 5 * math.sqrt((1 - Ph) / Ph**2 / len(g))
+    assert O.tp_gap(1.0, 123) == 1 and O.tp_gap(1.5, 123) == 1
+    assert O.tp_gap(0.0, 123) == 2**31 - 1
+
+
+@pytest.mark.parametrize("tp_mode", [0, 1])
+def test_tp_thermalizes_to_gas_temperature(tp_mode):
     """Hard-sphere Al-Ar collisions relax the Al velocity distribution to a
-    Maxwellian at the gas temperature: <v_x^2> = kT/M_Al."""
+    Maxwellian at the gas temperature: <v_x^2> = kT/M_Al (both collision
+    modes; the thinned candidates need P^ <= 1, hence the shorter step)."""
     n, p, T = 40_000, 5.0, 300.0
     rng = np.random.default_rng(4)
-    orc = O.Oracle(prm(L=1e6, ncell=1024, p=p, Tg=T, sigma_tp=3e-19), 1, 1, n)
+    orc = O.Oracle(prm(L=1e6, ncell=1024, p=p, Tg=T, sigma_tp=3e-19, tp_mode=tp_mode), 1, 1, n)
     load(orc, 2, np.full(n, 512.0) + rng.uniform(-1, 1, n), _mono(n, math.sqrt(2 * 5 * QE / MAL), rng))
-    orc.tp_step(300, 1e-6)            # P ~ 0.2 per step: ~60 collisions per atom
+    if tp_mode == 1:
+        orc.tp_step(300, 1e-6)        # P ~ 0.2 per step: ~60 collisions per atom
+    else:
+        orc.tp_step(3000, 1e-7)       # P^ <= 0.25 per step
+    assert orc.counters()["numerics"] == 0
     tp = orc.get_species(2)
     ref = KB * T / MAL
     for comp in ("vx", "vy", "vz"):
@@ -941,14 +1010,16 @@ def test_event_driven_uncollided_fraction_in_cold_gas():
     assert abs(got - n * P) < 4.5 * math.sqrt(n * P * (1 - P))
 
 
-def test_event_driven_flight_agrees_with_the_per_step_test():
+@pytest.mark.parametrize("tp_mode", [0, 1])
+def test_event_driven_flight_agrees_with_the_per_step_test(tp_mode):
     """The two TP transport schemes of the oracle, written independently --
-    the per-step collision test (orc_tp_step, dt = 5 ns, nu dt < 1e-3) and
+    the per-step collision test (orc_tp_step, dt = 5 ns, nu dt < 1e-3; with
+    thinned candidates, tp_mode 0, and with the literal test, tp_mode 1) and
     the event-driven flight -- give the same energetic arrivals (> 2 eV) at
     the far electrode from a 300 eV-ion source: count within 4.5 standard
     deviations, energy distribution by a two-sample KS test."""
     n, N, L = 3000, 64, 0.02
-    P = prm(L=L, ncell=N, p=0.5, Tg=300.0, sigma_tp=3e-19, seed=21)
+    P = prm(L=L, ncell=N, p=0.5, Tg=300.0, sigma_tp=3e-19, seed=21, tp_mode=tp_mode)
     a = O.Oracle(P, 1, 1, n)
     b = O.Oracle(P, 1, 1, n)
     a.tp_launch(n, 300.0)
@@ -1075,13 +1146,16 @@ def test_vhs_uncollided_fraction_in_cold_gas():
     assert abs(got - n * P) < 4.5 * math.sqrt(n * P * (1 - P))
 
 
+@pytest.mark.parametrize("tp_mode", [0, 1])
 @pytest.mark.parametrize("model", [1, 2])
-def test_vhs_and_m1_flights_agree_with_the_per_step_test(model):
+def test_vhs_and_m1_flights_agree_with_the_per_step_test(model, tp_mode):
     """Under the VHS and M1 laws the event-driven flight (majorant rate, null
-    events, gamma-distributed partner speeds) and the per-step test give the
-    same energetic arrivals at the far electrode from a 300 eV-ion source."""
+    events, gamma-distributed partner speeds) and the per-step test (both
+    modes) give the same energetic arrivals at the far electrode from a
+    300 eV-ion source."""
     n, N, L = 3000, 64, 0.02
-    P = prm(L=L, ncell=N, p=0.5, Tg=300.0, seed=23, tp_model=model, dref=4.17e-10, omega=0.81, tref=273.0)
+    P = prm(L=L, ncell=N, p=0.5, Tg=300.0, seed=23, tp_model=model, dref=4.17e-10, omega=0.81, tref=273.0,
+            tp_mode=tp_mode)
     a = O.Oracle(P, 1, 1, n)
     b = O.Oracle(P, 1, 1, n)
     a.tp_launch(n, 300.0)
