@@ -628,18 +628,17 @@ def main():
         h2d = sum(sum(a.nbytes for a in pinned[s]) for s in (0, 1))
         cap = max(len(pinned[s][0]) for s in (0, 1)) * 5 // 4 + 65536
         d2 = P.Discharge(P.params_from_workload(cfg, n_e0=0, n_i0=0, cap_e=cap, cap_i=cap), stream=stream)
-        slot = d2.exchange_slot() if ws > 1 else None
         barrier(ws)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for s in (0, 1):
             d2.set_species(s, *pinned[s])
-        if slot is not None:
-            shard.allreduce_(slot)
+        if ws > 1:
+            shard.allreduce_(d2.exchange_slot())
         for _ in range(args.e2e_steps):
             d2.step(1)
-            if slot is not None:
-                shard.allreduce_(slot)
+            if ws > 1:
+                shard.allreduce_(d2.exchange_slot())
         out = [d2.diag(k) for k in ("phi", "n_e", "n_i", "iedf_l")]
         cnt = d2.counters()
         torch.cuda.synchronize()

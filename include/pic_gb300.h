@@ -162,12 +162,13 @@ int pic_sync(pic_ctx* ctx);
  * the caller sums this device block over the ranks in place (an int64 sum
  * all-reduce, e.g. NCCL on the context's stream): *dev receives the
  * context-owned device int64[*n_words] of the current step -- the electron
- * and ion deposits and their flux moments, padded with zeros.  Time averages
- * of the charge, potential and fluxes are then those of the whole discharge
- * on every rank; histograms, counters and test particles stay per rank and
- * add up.  The pointer stays valid for the context's life; its contents
- * change every step.  PIC_ERR_INVALID_ARG with circuit 1 (the series
- * capacitor needs the whole wall charge each step). */
+ * and ion deposits and their flux moments, padded with zeros.  The blocks
+ * rotate over three buffers, one per step, so ask for the pointer after
+ * every step (each stays valid for the context's life).  Time averages of
+ * the charge, potential and fluxes are then those of the whole discharge on
+ * every rank; histograms, counters and test particles stay per rank and add
+ * up.  PIC_ERR_INVALID_ARG with circuit 1 (the series capacitor needs the
+ * whole wall charge each step). */
 int pic_exchange_slot(pic_ctx* ctx, int64_t** dev, int64_t* n_words);
 
 /* Diagnostics (Sec. "Simulation Results", Figs. 5-9), written to host memory:

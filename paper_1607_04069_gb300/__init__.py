@@ -191,9 +191,13 @@ class _CudaArray:
 
 
 def _device_view(ptr, n, dtype):
+    """A torch tensor that aliases n elements at device address ptr."""
     import torch
     typestr = {torch.int64: "<i8", torch.float64: "<f8"}[dtype]
-    return torch.as_tensor(_CudaArray(ptr, n, typestr), device="cuda")
+    t = torch.as_tensor(_CudaArray(ptr, n, typestr))
+    if t.data_ptr() != int(ptr) or t.device.type != "cuda":
+        raise RuntimeError("torch copied the library's buffer instead of viewing it")
+    return t
 
 
 def default_params() -> PicParams:
@@ -306,11 +310,15 @@ class Discharge:
     def exchange_slot(self):
         """The device int64 block of the current step that ranks sharing one
         discharge sum in place before the next step (``pic_exchange_slot``),
-        as a torch tensor viewing the context's memory."""
+        as a torch tensor viewing the context's memory.  The block rotates
+        with the step: ask for it after every step."""
         import torch
         ptr, n = C.c_void_p(), C.c_int64()
         _check(lib().pic_exchange_slot(self.h, C.byref(ptr), C.byref(n)))
-        return _device_view(ptr.value, n.value, torch.int64)
+        views = self.__dict__.setdefault("_views", {})
+        if ptr.value not in views:
+            views[ptr.value] = _device_view(ptr.value, n.value, torch.int64)
+        return views[ptr.value]
 
     def tp_step(self, n=1, count_alive=True):
         a = C.c_int64()

@@ -541,7 +541,11 @@ int pic_create(const pic_params* pin, void* stream, pic_ctx** out)
     }
     c->grid_mover = c->sms * per_sm;
     if (c->grid_mover > kMaxTallyRows) c->grid_mover = kMaxTallyRows - kMaxTallyRows % c->sms;
-    c->grid_tp = c->sms * 4;
+    {                                  // the TP step: a multiple of the SMs by its occupancy
+        int tp_per_sm = 0;
+        if (tp_occupancy(c->d, &tp_per_sm) != cudaSuccess || tp_per_sm < 1) tp_per_sm = 2;
+        c->grid_tp = c->sms * tp_per_sm;
+    }
     c->grid_sort = c->sms * 8;
 
     Ctl h;
@@ -712,6 +716,31 @@ static int read_ctl(pic_ctx* c, Ctl* h)
 {
     CK(cudaStreamSynchronize(c->stream));
     CK(cudaMemcpy(h, c->d.ctl, sizeof *h, cudaMemcpyDeviceToHost));
+    return PIC_OK;
+}
+
+// Event counts: the TP kernels' counts in the control block plus the step
+// launch's per-CTA rows (d.tally).  tot[kNumCnt].
+static int count_events(pic_ctx* c, const Ctl& h, unsigned long long* tot)
+{
+    std::vector<unsigned long long> rows((size_t)kMaxTallyRows * kNumCnt);
+    CK(cudaMemcpy(rows.data(), c->d.tally, rows.size() * 8, cudaMemcpyDeviceToHost));
+    for (int k = 0; k < kNumCnt; ++k) tot[k] = h.cnt[k];
+    for (size_t r = 0; r < (size_t)kMaxTallyRows; ++r)
+        for (int k = 0; k < kNumCnt; ++k) tot[k] += rows[r * kNumCnt + k];
+    return PIC_OK;
+}
+
+// test particles in flight: launched + sputtered - deposited
+static int tp_in_flight(pic_ctx* c, int64_t* n)
+{
+    Ctl h;
+    int rc = read_ctl(c, &h);
+    if (rc) return rc;
+    unsigned long long tot[kNumCnt];
+    if ((rc = count_events(c, h, tot))) return rc;
+    *n = c->tp_launched + (int64_t)tot[kCntSputL] + (int64_t)tot[kCntSputR] - (int64_t)tot[kCntTpDepL] -
+         (int64_t)tot[kCntTpDepR];
     return PIC_OK;
 }
 
@@ -953,12 +982,8 @@ int pic_counters(pic_ctx* c, int64_t* out, int64_t cap, int64_t* n_written)
                                 kCntSputR, kCntTpDepL, kCntTpDepR, kCntNumerics, kCntElastic,
                                 kCntExcit, kCntCx, kCntIso, kCntTpColl, kCntCapacity};
     // the step launch keeps its counts per CTA (rows of d.tally)
-    std::vector<unsigned long long> rows((size_t)kMaxTallyRows * kNumCnt);
-    CK(cudaMemcpy(rows.data(), c->d.tally, rows.size() * 8, cudaMemcpyDeviceToHost));
     unsigned long long tot[kNumCnt];
-    for (int k = 0; k < kNumCnt; ++k) tot[k] = h.cnt[k];
-    for (size_t r = 0; r < (size_t)kMaxTallyRows; ++r)
-        for (int k = 0; k < kNumCnt; ++k) tot[k] += rows[r * kNumCnt + k];
+    if ((rc = count_events(c, h, tot))) return rc;
     for (int i = 0; i < kNumCnt; ++i) v[5 + i] = (int64_t)tot[order[i]];
     const int64_t n = 5 + kNumCnt;
     for (int64_t i = 0; i < n && i < cap; ++i) out[i] = v[i];
@@ -1110,11 +1135,8 @@ int tp_step(pic_ctx* c, int64_t n, int64_t* n_alive)
         if (rc) return rc;
     }
     if (n_alive) {
-        Ctl h;
-        int rc = read_ctl(c, &h);
+        int rc = tp_in_flight(c, n_alive);
         if (rc) return rc;
-        *n_alive = c->tp_launched + (int64_t)h.cnt[kCntSputL] + (int64_t)h.cnt[kCntSputR] -
-                   (int64_t)h.cnt[kCntTpDepL] - (int64_t)h.cnt[kCntTpDepR];
     }
     return PIC_OK;
 }
@@ -1140,11 +1162,10 @@ int tp_flight(pic_ctx* c, int64_t max_events, int64_t* n_alive)
     }
     if (n_alive) {
         if (!any) {                                    // no launch: count the live atoms as they are
-            Ctl h;
-            int rc = read_ctl(c, &h);
+            int64_t n = 0;
+            int rc = tp_in_flight(c, &n);
             if (rc) return rc;
-            alive = (unsigned long long)(c->tp_launched + (int64_t)h.cnt[kCntSputL] + (int64_t)h.cnt[kCntSputR] -
-                                         (int64_t)h.cnt[kCntTpDepL] - (int64_t)h.cnt[kCntTpDepR]);
+            alive = (unsigned long long)n;
         }
         *n_alive = (int64_t)alive;
     }

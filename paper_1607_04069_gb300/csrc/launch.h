@@ -12,6 +12,10 @@ constexpr int kMoverThreads = 256;
 #endif
 constexpr int kMoverMinBlocks = PG_MOVER_MIN_BLOCKS;   // resident CTAs per SM the register budget is sized for
 constexpr int kTpThreads = 256;
+#ifndef PG_TP_MIN_BLOCKS
+#define PG_TP_MIN_BLOCKS 4
+#endif
+constexpr int kTpMinBlocks = PG_TP_MIN_BLOCKS;   // resident CTAs per SM the TP step's registers are sized for
 
 size_t mover_smem(int ncell);
 size_t tp_smem(int ncell);
@@ -35,6 +39,8 @@ cudaError_t launch_field(const Dev& d, double v_left, int accumulate, cudaStream
 cudaError_t launch_entry_nev(const Dev& d, int s, unsigned int half, long long n, unsigned int l0, cudaStream_t st);
 cudaError_t launch_sort(const Dev& d, int s, int grid, cudaStream_t st);
 cudaError_t launch_tp_step(const Dev& d, int grid, cudaStream_t st);
+// resident CTAs per SM of the TP step kernel of d's collision mode and law
+cudaError_t tp_occupancy(const Dev& d, int* blocks_per_sm);
 // event-driven flight: every live TP atom through at most kmax events; the
 // atoms still alive are added to Ctl::tpf_alive
 cudaError_t launch_tp_flight(const Dev& d, int kmax, long long n, cudaStream_t st);

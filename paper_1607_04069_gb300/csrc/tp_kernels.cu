@@ -405,7 +405,7 @@ __device__ __noinline__ void tp_stick(const Dev& d, const SpBuf& B, long long i,
 }
 
 template <bool LAW>
-__global__ void __launch_bounds__(kTpThreads, 4) k_tp_step_geo(Dev d)
+__global__ void __launch_bounds__(kTpThreads, kTpMinBlocks) k_tp_step_geo(Dev d)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = d.ncell;
@@ -834,12 +834,26 @@ cudaError_t launch_tp_flight(const Dev& d, int kmax, long long n, cudaStream_t s
     return cudaGetLastError();
 }
 
+static const void* tp_step_fn(const Dev& d)
+{
+    return d.tp_mode == 0 ? (d.tp_model ? (const void*)k_tp_step_geo<true> : (const void*)k_tp_step_geo<false>)
+                          : (d.tp_model ? (const void*)k_tp_step<true> : (const void*)k_tp_step<false>);
+}
+
+cudaError_t tp_occupancy(const Dev& d, int* blocks_per_sm)
+{
+    const size_t sm = tp_smem(d.ncell);
+    if (sm > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(tp_step_fn(d), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, tp_step_fn(d), kTpThreads, sm);
+}
+
 cudaError_t launch_tp_step(const Dev& d, int grid, cudaStream_t st)
 {
     const size_t sm = tp_smem(d.ncell);
-    const void* fn = d.tp_mode == 0
-                         ? (d.tp_model ? (const void*)k_tp_step_geo<true> : (const void*)k_tp_step_geo<false>)
-                         : (d.tp_model ? (const void*)k_tp_step<true> : (const void*)k_tp_step<false>);
+    const void* fn = tp_step_fn(d);
     if (sm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;

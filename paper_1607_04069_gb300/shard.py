@@ -95,12 +95,11 @@ class SplitDischarge:
         self.rank, self.world, self.group = rank, world, group
         self.cfg = shard_workload(cfg, rank, world)
         self.d = Discharge(params_from_workload(self.cfg, **over), stream=stream)
-        self._slot = self.d.exchange_slot() if world > 1 else None
         self._exchange()
 
     def _exchange(self):
         if self.world > 1:
-            allreduce_(self._slot, self.group)
+            allreduce_(self.d.exchange_slot(), self.group)
 
     def step(self, n: int = 1):
         for _ in range(int(n)):

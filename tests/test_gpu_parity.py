@@ -477,3 +477,19 @@ def test_capacity_overflow_is_reported_and_state_stays_consistent():
     assert ne - ni == 20_000 - d.counters()["imp_e_l"] - d.counters()["imp_e_r"] + d.counters()["imp_i_l"] + d.counters()["imp_i_r"]
     d.sync()                   # the error is reported once
     d.close()
+
+
+def test_atoms_in_flight_counts_coupled_births():
+    """tp_step's count of atoms in flight includes the atoms that ion impacts
+    sputtered inside the step launch (counted per CTA there): it equals the
+    atoms actually held, and launched = deposited + in flight."""
+    cfg = W.ccp_sputter(n_per_species=20_000, n_cells=64, seed=95)
+    cfg.update(rf_volt_v=1000.0, dt=W.T_RF / 400, tp_every=20, sort_every_tp=0)
+    d = gpu_discharge(cfg)
+    d.step(1600)
+    alive = d.tp_step(1)
+    c = d.counters()
+    held = len(d.get_species(2)["id"])
+    assert c["sputtered_l"] + c["sputtered_r"] > 100
+    assert alive == held == c["sputtered_l"] + c["sputtered_r"] - c["tp_dep_l"] - c["tp_dep_r"]
+    d.close()

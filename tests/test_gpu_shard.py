@@ -46,9 +46,8 @@ def test_split_discharge_equals_the_whole(torch, prec):
     whole = P.Discharge(P.params_from_workload(cfg))
     parts = [P.Discharge(P.params_from_workload(shard.shard_workload(cfg, r, 2), sort_every_e=11 + r))
              for r in (0, 1)]
-    slots = [p.exchange_slot() for p in parts]
-
     def exchange():
+        slots = [p.exchange_slot() for p in parts]           # the block of the current step
         s = slots[0] + slots[1]
         for t in slots:
             t.copy_(s)
