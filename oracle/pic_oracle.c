@@ -651,11 +651,24 @@ void orc_counters(const orc_state *S, int64_t *out)
 /* ======================= the PIC/MCC step ================================ */
 /* bin of x on [0, xmax) in nb bins; below the range the first bin, at or
  * above it the last (the scaled value is clamped before the conversion) */
+/* Integers decided by floating point (a histogram bin, the process of a
+ * collision, a sputter trial, the partner and the acceptance of a TP
+ * candidate) are decided in FP32, the precision of the GPU path's kinematics,
+ * on the oracle's FP64 operands rounded to FP32; everything else stays FP64. */
 static int bin_of(double x, double xmax, int nb)
 {
-    double t = x / xmax * (double)nb;
-    if (!(t < (double)nb)) return nb - 1;
-    if (!(t >= 0.0)) return 0;
+    float t = (float)x / (float)xmax * (float)nb;
+    if (!(t < (float)nb)) return nb - 1;
+    if (!(t >= 0.0f)) return 0;
+    return (int)t;
+}
+
+/* 1-degree bin of a polar angle given in degrees */
+static int ang_bin(double deg)
+{
+    float t = (float)deg;
+    if (!(t < (float)NB_ANG)) return NB_ANG - 1;
+    if (!(t >= 0.0f)) return 0;
     return (int)t;
 }
 
@@ -679,7 +692,7 @@ static void sputter(orc_state *S, uint64_t ion_id, uint32_t l, double E, int ele
     for (int k = 0; k < Nt; k++) {
         uint32_t t[4];
         draw(S->P.seed, ion_id, l, PUR_SP_TRIAL + (k >> 2), t);
-        if (!(u23(t[k & 3]) <= Y / (double)Nt)) continue;
+        if (!((float)u23(t[k & 3]) <= (float)Y / (float)Nt)) continue;
         uint32_t ce[4], ci[4];
         draw(S->P.seed, ion_id, l, PUR_SP_EMIT + k, ce);
         draw(S->P.seed, ion_id, l, PUR_SP_ID + k, ci);
@@ -715,20 +728,21 @@ static void mcc_electron(orc_state *S, int64_t k, uint32_t l)
     double nu_el = S->ngas * sg[0] * v;
     double nu_exc = S->ngas * sg[1] * v;
     double nu_ion = S->ngas * sg[2] * v;
-    double r = u23(c[1]) * S->nu_max_e;
+    float r = (float)u23(c[1]) * (float)S->nu_max_e;        /* the process, in FP32 */
+    float f_el = (float)nu_el, f_exc = (float)nu_exc, f_ion = (float)nu_ion;
     double d[3];
     iso_dir(c[2], c[3], d);
-    if (r < nu_el) {
+    if (r < f_el) {
         double cchi = v > 0.0 ? (d[0] * p->vx[k] + d[1] * p->vy[k] + d[2] * p->vz[k]) / v : 1.0;
         double fac = 1.0 - (2.0 * O_ME / O_MAR) * (1.0 - cchi);
         double vn = v * sqrt(fac);
         p->vx[k] = vn * d[0]; p->vy[k] = vn * d[1]; p->vz[k] = vn * d[2];
         S->cnt[C_ELASTIC]++;
-    } else if (r < nu_el + nu_exc) {
+    } else if (r < f_el + f_exc) {
         double vn = sqrt(2.0 * (eps - O_EXC_TH) * O_QE / O_ME);
         p->vx[k] = vn * d[0]; p->vy[k] = vn * d[1]; p->vz[k] = vn * d[2];
         S->cnt[C_EXCIT]++;
-    } else if (r < nu_el + nu_exc + nu_ion) {
+    } else if (r < f_el + f_exc + f_ion) {
         double epr = eps - O_ION_TH;
         uint32_t ci[4], cn[4], cb[4];
         draw(S->P.seed, p->id[k], l, PUR_IONIZE, ci);
@@ -807,9 +821,7 @@ static void wall_ion(orc_state *S, int64_t k, uint32_t l, int electrode)
     double emax = S->P.V0 > 0.0 ? 2.0 * S->P.V0 : 1.0;   /* [0, 2 V0]; [0, 1 eV] without a source */
     hist_add(S->iedf[electrode], NB_IEDF, E, emax);
     int be = bin_of(E, emax, NB_IEADF_E);
-    int ba = (int)th;
-    if (ba > NB_ANG - 1) ba = NB_ANG - 1;
-    S->ieadf[electrode][be * NB_ANG + ba]++;
+    S->ieadf[electrode][be * NB_ANG + ang_bin(th)]++;
     S->cnt[electrode == 0 ? C_IMP_I_L : C_IMP_I_R]++;
     if (S->P.sputter) sputter(S, p->id[k], l, E, electrode);
 }
@@ -1053,7 +1065,7 @@ static int tp_candidate(orc_state *S, uint64_t id, uint32_t s, const double v[3]
     uint32_t a[4], e[4];
     draw(S->P.seed, id, s, PUR_TP_CAND, a);
     draw(S->P.seed, id, s, PUR_TP_CAND + 1, e);
-    if (u23(a[0]) * (va + ma) < va) {
+    if ((float)u23(a[0]) * ((float)va + (float)ma) < (float)va) {   /* the partner's law, in FP32 */
         double vg = c / sqrt(2.0), n1, n2, n3, n4;
         box_muller(a[1], a[2], &n1, &n2);
         box_muller(a[3], e[0], &n3, &n4);
@@ -1069,7 +1081,9 @@ static int tp_candidate(orc_state *S, uint64_t id, uint32_t s, const double v[3]
     double wm = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
     /* accept with p(g) (|v|^alpha + <|w|^alpha>) / (P^ (|v|^alpha + |w|^alpha)) */
     double Ph = tp_cand_prob(S, vm, dt_tp);
-    return u23(e[1]) * Ph * (va + pow(wm, alpha)) < (va + ma) * -expm1(-b * pow(g, alpha));
+    float acc_l = (float)u23(e[1]) * (float)Ph * ((float)va + (float)pow(wm, alpha));   /* in FP32 */
+    float acc_r = ((float)va + (float)ma) * (float)(-expm1(-b * pow(g, alpha)));
+    return acc_l < acc_r;
 }
 
 void orc_tp_step(orc_state *S, int64_t nsteps, double dt_tp)
@@ -1096,9 +1110,7 @@ void orc_tp_step(orc_state *S, int64_t nsteps, double dt_tp)
                 double ct = v2 > 0.0 ? fabs(p->vx[k]) / sqrt(v2) : 1.0;
                 if (ct > 1.0) ct = 1.0;
                 hist_add(S->sp_e[el], NB_SPE, E, 300.0);
-                int ba = (int)(acos(ct) * 180.0 / O_PI);
-                if (ba > NB_ANG - 1) ba = NB_ANG - 1;
-                S->sp_ang[el][ba]++;
+                S->sp_ang[el][ang_bin(acos(ct) * 180.0 / O_PI)]++;
                 S->cnt[el == 0 ? C_TPDEP_L : C_TPDEP_R]++;
                 p->alive[k] = 0;
                 continue;
@@ -1323,9 +1335,7 @@ int64_t orc_tp_flight(orc_state *S, int64_t max_events)
                 double ct = vm > 0.0 ? fabs(v[0]) / vm : 1.0;
                 if (ct > 1.0) ct = 1.0;
                 hist_add(S->sp_e[el], NB_SPE, E, 300.0);
-                int ba = (int)(acos(ct) * 180.0 / O_PI);
-                if (ba > NB_ANG - 1) ba = NB_ANG - 1;
-                S->sp_ang[el][ba]++;
+                S->sp_ang[el][ang_bin(acos(ct) * 180.0 / O_PI)]++;
                 S->cnt[el == 0 ? C_TPDEP_L : C_TPDEP_R]++;
                 p->alive[k] = 0;
                 p->xi[k] = xw;

@@ -1,16 +1,19 @@
-"""Writes tests/golden/steady_state_sputter256.json: the oracle's statistics of
-the reduced sputtering discharge at periodic steady operation, over many
-seeds, for the GPU steady-state parity test.
+"""Writes the oracle's statistics of a discharge at periodic steady operation,
+over many seeds, for the GPU steady-state parity tests:
 
-Only ``oracle/`` computes here.  The discharge is the 50 mm / 0.5 Pa /
-300 V / 13.56 MHz sputtering case with 256 cells and 100k e- + 100k Ar+
-superparticles (32-bit positions, sputtering on, TP steps of 40 PIC steps),
-from the uniform Maxwellian loading: 10 RF periods to settle, then the time
-averages over 10 RF periods (Sec. "Kinetic Particle Simulation": averaging
-after a steady state; Sec. "Simulation Results", Figs. 5-9).  The atoms still
-in flight at the end then continue by TP steps until they deposit (at most
-MAX_TP_STEPS), so that the deposited energy and angle distributions have
-thousands of entries.
+* tests/golden/steady_state_sputter256.json (--case sputter256): the 50 mm /
+  0.5 Pa / 300 V / 13.56 MHz sputtering case with 256 cells and 100k e- +
+  100k Ar+ superparticles (sputtering on, TP steps of 40 PIC steps);
+* tests/golden/steady_state_ccp128.json (--case ccp128): the 25 mm / 3 Pa /
+  100 V case with 128 cells and 20k e- + 20k Ar+.
+
+Only ``oracle/`` computes here.  From the uniform Maxwellian loading: 10 RF
+periods to settle, then the time averages over 10 RF periods (Sec. "Kinetic
+Particle Simulation": averaging after a steady state; Sec. "Simulation
+Results", Figs. 5-9).  In the sputtering case the atoms still in flight at
+the end then continue by TP steps until they deposit (at most MAX_TP_STEPS),
+so that the deposited energy and angle distributions have thousands of
+entries.
 
 For every profile the file holds the mean over the seeds and the standard
 deviation of one seed; for every histogram the pooled counts and the mean
@@ -18,8 +21,9 @@ two-sample KS distance between seeds (which gives the effective number of
 independent samples of a correlated histogram).  The oracle source's hash is
 recorded; a CPU test checks it against the current oracle.
 
-Usage: python tests/golden/make_steady_state_ref.py [--seeds 16] [--workers N]
-(--quick writes a tiny run to --out, to try the script).
+Usage: python tests/golden/make_steady_state_ref.py [--case sputter256|ccp128]
+[--seeds 16] [--workers N] (--quick writes a tiny run to --out, to try the
+script).
 """
 from __future__ import annotations
 
@@ -37,10 +41,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(os.path.dirname(HERE))
 sys.path.insert(0, ROOT)
 
-OUT = os.path.join(HERE, "steady_state_sputter256.json")
-SEED0 = 7001
-N_PER_SPECIES = 100_000
-N_CELLS = 256
+CASES = {"sputter256": dict(out="steady_state_sputter256.json", seed0=7001, n=100_000, cells=256, tp=True),
+         "ccp128": dict(out="steady_state_ccp128.json", seed0=9001, n=20_000, cells=128, tp=False)}
 WARM_PERIODS, AVG_PERIODS = 10, 10
 MAX_TP_STEPS = 200_000
 PROFILES = ("phi", "n_e", "n_i", "gamma_e", "gamma_i", "tp_dens", "tp_vx")
@@ -48,9 +50,11 @@ HISTS = ("iedf_l", "iedf_r", "eedf", "ieadf_l", "ieadf_r", "sputter_e_l", "sputt
          "sputter_ang_r")
 
 
-def workload(seed: int, n: int = N_PER_SPECIES) -> dict:
+def workload(case: str, seed: int, n: int) -> dict:
     from paper_1607_04069_gb300 import workloads as W
-    return W.ccp_sputter(n_per_species=n, n_cells=N_CELLS, seed=seed)
+    if case == "ccp128":
+        return W.ccp_small(n_per_species=n, seed=seed)
+    return W.ccp_sputter(n_per_species=n, n_cells=CASES[case]["cells"], seed=seed)
 
 
 def oracle_hash() -> str:
@@ -59,12 +63,13 @@ def oracle_hash() -> str:
 
 
 def run_seed(job) -> dict:
-    """job = (seed, superparticles per species, steps of a settling and an
-    averaging period block, settling periods, averaging periods, TP step cap)"""
+    """job = (case, seed, superparticles per species, steps of a settling and
+    an averaging period block, settling periods, averaging periods, TP step
+    cap)"""
     import oracle as O
     from paper_1607_04069_gb300 import workloads as W
-    seed, n_sp, P, warm, avg, max_tp = job
-    cfg = workload(seed, n_sp)
+    case, seed, n_sp, P, warm, avg, max_tp = job
+    cfg = workload(case, seed, n_sp)
     n = cfg["n_e0"]
     orc = O.Oracle(W.oracle_params(cfg), 2 * n, 2 * n, 400_000)
     orc.init_species(0, n, cfg["te0_ev"])
@@ -80,7 +85,7 @@ def run_seed(job) -> dict:
     # the atoms in flight continue by TP steps of the coupled length until they deposit
     tp_dt = cfg["tp_every"] * cfg["dt"]
     done = 0
-    while orc.counters()["n_tp"] > 0 and done < max_tp:
+    while cfg["sputter_enable"] and orc.counters()["n_tp"] > 0 and done < max_tp:
         orc.tp_step(1000, tp_dt)
         done += 1000
     for k in ("sputter_e_l", "sputter_e_r", "sputter_ang_l", "sputter_ang_r"):
@@ -106,22 +111,26 @@ def marginals(h):
 def main():
     import argparse
     ap = argparse.ArgumentParser()
+    ap.add_argument("--case", default="sputter256", choices=sorted(CASES))
     ap.add_argument("--seeds", type=int, default=16)
     ap.add_argument("--workers", type=int, default=os.cpu_count() or 1)
-    ap.add_argument("--out", default=OUT)
+    ap.add_argument("--out", default=None)
     ap.add_argument("--quick", action="store_true")
     opt = ap.parse_args()
-    seeds = [SEED0 + k for k in range(opt.seeds)]
+    case = CASES[opt.case]
+    out_path = opt.out or os.path.join(HERE, case["out"])
+    seeds = [case["seed0"] + k for k in range(opt.seeds)]
     if opt.quick:
-        jobs = [(s, 2000, 30, 1, 1, 3000) for s in seeds]
+        jobs = [(opt.case, s, 2000, 30, 1, 1, 3000) for s in seeds]
     else:
-        P = workload(SEED0)["steps_per_period"]
-        jobs = [(s, N_PER_SPECIES, P, WARM_PERIODS, AVG_PERIODS, MAX_TP_STEPS) for s in seeds]
+        P = workload(opt.case, seeds[0], case["n"])["steps_per_period"]
+        jobs = [(opt.case, s, case["n"], P, WARM_PERIODS, AVG_PERIODS, MAX_TP_STEPS) for s in seeds]
     with mp.get_context("spawn").Pool(min(opt.workers, len(jobs))) as pool:
         runs = pool.map(run_seed, jobs)
     n_seeds = len(seeds)
     ref = {"what": "oracle statistics of the reduced sputtering discharge, see make_steady_state_ref.py",
-           "oracle_sha16": oracle_hash(), "seeds": seeds, "n_per_species": N_PER_SPECIES, "n_cells": N_CELLS,
+           "oracle_sha16": oracle_hash(), "case": opt.case, "seeds": seeds, "n_per_species": case["n"],
+           "n_cells": case["cells"],
            "warm_periods": WARM_PERIODS, "avg_periods": AVG_PERIODS, "max_tp_steps": MAX_TP_STEPS,
            "profiles": {}, "hists": {}}
     for k in PROFILES:
@@ -143,9 +152,9 @@ def main():
     ref["tp_left_max"] = int(max(r["tp_left"] for r in runs))
     ref["tp_steps_after_max"] = int(max(r["tp_steps_after"] for r in runs))
     ref["seconds_per_seed"] = float(np.mean([r["seconds"] for r in runs]))
-    with open(opt.out, "w") as fh:
+    with open(out_path, "w") as fh:
         json.dump(ref, fh, separators=(",", ":"))
-    print(f"wrote {opt.out}: {n_seeds} seeds, {ref['seconds_per_seed']:.0f} s each, tp left {ref['tp_left_max']}")
+    print(f"wrote {out_path}: {n_seeds} seeds, {ref['seconds_per_seed']:.0f} s each, tp left {ref['tp_left_max']}")
 
 
 if __name__ == "__main__":

@@ -10,13 +10,18 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 
 
-def test_steady_state_reference_was_written_by_the_current_oracle():
-    with open(os.path.join(HERE, "golden", "steady_state_sputter256.json")) as fh:
+import pytest
+
+
+@pytest.mark.parametrize("case,cells,n", [("sputter256", 256, 100_000), ("ccp128", 128, 20_000)])
+def test_steady_state_reference_was_written_by_the_current_oracle(case, cells, n):
+    with open(os.path.join(HERE, "golden", f"steady_state_{case}.json")) as fh:
         ref = json.load(fh)
     with open(os.path.join(ROOT, "oracle", "pic_oracle.c"), "rb") as fh:
         assert ref["oracle_sha16"] == hashlib.sha256(fh.read()).hexdigest()[:16], \
             "oracle changed: rerun tests/golden/make_steady_state_ref.py"
-    assert len(ref["seeds"]) >= 8 and ref["n_cells"] == 256 and ref["n_per_species"] == 100_000
+    assert len(ref["seeds"]) >= 8 and ref["n_cells"] == cells and ref["n_per_species"] == n
     for k in ("phi", "n_e", "n_i", "gamma_i"):
-        assert len(ref["profiles"][k]["mean"]) == 257
-    assert all(h["pair_D_mean"] for h in ref["hists"].values())
+        assert len(ref["profiles"][k]["mean"]) == cells + 1
+    for k in ("iedf_l", "iedf_r", "eedf"):
+        assert ref["hists"][k]["pair_D_mean"] > 0
