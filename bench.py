@@ -228,38 +228,76 @@ def oracle_rate(cfg, n_sample, steps, warmup=1):
     return (cnt["n_e"] + cnt["n_i"]) * steps / dt, dt
 
 
-def measure_rows(d, cfg, peak, cmp_ms, cmp_n, nsort_particles, n_atoms):
-    """Per-row measurements besides the fused step kernel: test-particle flight
-    (a separate run of n_atoms atoms, far larger than L2), compaction, and the
-    FP64 field solve of the diagnostics."""
-    import torch
+def tp_step_time(n_atoms, steps=20, warm=3):
+    """Mean launch time (s) of the TP step on n_atoms atoms of the TP workload
+    (thinned candidates), after warm steps, by the library's launch timers."""
     import paper_1607_04069_gb300 as P
     from paper_1607_04069_gb300 import workloads as W
-    rows = {}
-    # a8: TP flight, one kernel per TP step
     tc = W.tp_transport(n_atoms=n_atoms)
     tc.update(cap_tp=n_atoms + 1024, n_e0=0, n_i0=0, sort_every_tp=0)
     t = P.Discharge(P.params_from_workload(tc))
     t.tp_launch(n_atoms, 300.0)
-    t.tp_step(3, count_alive=False)
+    t.tp_step(warm, count_alive=False)
     t.sync()
     t.timing(True)
-    t.tp_step(20, count_alive=False)
+    t.tp_step(steps, count_alive=False)
     t.sync()
     ms, n = t.kernel_time("tp")
     t.close()
-    per = ms / n * 1e-3
+    return ms / n * 1e-3
+
+
+def measure_rows(d, cfg, peak, cmp_ms, cmp_n, nsort_particles, n_atoms, want=None):
+    """Per-row measurements besides the fused step kernel: test-particle flight
+    (a separate run of n_atoms atoms, far larger than L2), compaction, and the
+    FP64 field solve of the diagnostics.  want: the rows to measure (None: all)."""
+    import torch
+    import paper_1607_04069_gb300 as P
+    from paper_1607_04069_gb300 import workloads as W
+    rows = {}
+    on = lambda name: want is None or name in want
+    tc = W.tp_transport(n_atoms=n_atoms)
+    tc.update(cap_tp=n_atoms + 1024, n_e0=0, n_i0=0, sort_every_tp=0)
+    # a8: TP flight, one kernel per TP step
+    per = tp_step_time(n_atoms) if on("a8_tp_step") else None
     # the method moves x, v_x, v_y, v_z (read and write) and reads the id per atom-step (40 B);
     # with thinned candidates this design reads x, v_x and the candidate step and writes x (16 B)
-    ach = ALGO_BYTES * n_atoms / per / 1e9
-    rows["a8_tp_step"] = {"workload": "tp_transport: %d Al atoms, 0.5 Pa 300 K Ar, dt 1 ns, thinned "
-                                      "collision candidates" % n_atoms,
-                          "value": n_atoms / per, "unit": "atom-steps/s", "mean_launch_us": per * 1e6,
-                          "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                                       "frac": ach / peak, "algorithmic_bytes_per_atom_step": ALGO_BYTES,
-                                       "design_bytes_per_atom_step": 16,
-                                       "design_frac": 16 * n_atoms / per / 1e9 / peak}}
+    ach = ALGO_BYTES * n_atoms / per / 1e9 if per else 0.0
+    if per:
+        rows["a8_tp_step"] = {"workload": "tp_transport: %d Al atoms, 0.5 Pa 300 K Ar, dt 1 ns, thinned "
+                                          "collision candidates" % n_atoms,
+                              "value": n_atoms / per, "unit": "atom-steps/s", "mean_launch_us": per * 1e6,
+                              "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                                           "frac": ach / peak, "algorithmic_bytes_per_atom_step": ALGO_BYTES,
+                                           "design_bytes_per_atom_step": 16,
+                                           "design_frac": 16 * n_atoms / per / 1e9 / peak}}
     # a8, event-driven form: the same source run to deposition, one launch per 32 events per atom
+    if on("a8_tp_flight"):
+        rows.update(measure_flights(tc, n_atoms))
+    if on("n1_circuit_step"):
+        rows["n1_circuit_step"] = measure_circuit(cfg)
+    # a9: compaction (counting sort by cell of one species) in the timed run
+    if cmp_n and on("a9_compaction"):
+        per_sort = cmp_ms / cmp_n * 1e-3
+        sb = 2 * 28 + 4       # read + write x, v_x, v_y, v_z, id, next-candidate step; one count pass
+        ach = sb * nsort_particles / per_sort / 1e9
+        rows["a9_compaction"] = {"value": nsort_particles / per_sort, "unit": "particles/s",
+                                 "mean_sort_us": per_sort * 1e6,
+                                 "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                                              "frac": ach / peak, "algorithmic_bytes_per_particle": sb}}
+    if on("cfg1_ccp_small"):
+        rows["cfg1_ccp_small"] = measure_cfg1()
+    if on("a7_poisson_fp64"):
+        rows["a7_poisson_fp64"] = measure_poisson(d, cfg)
+    return rows
+
+
+def measure_flights(tc, n_atoms):
+    """The TP source run to deposition by the event-driven flight, under hard
+    spheres, VHS and M1."""
+    import torch
+    import paper_1607_04069_gb300 as P
+    rows = {}
     t = P.Discharge(P.params_from_workload(tc))
     t.tp_launch(n_atoms, 300.0)
     t.sync()
@@ -292,7 +330,12 @@ def measure_rows(d, cfg, peak, cmp_ms, cmp_n, nsort_particles, n_atoms):
             "collisions_per_atom": cnt["tp_coll"] / n_atoms, "still_in_flight": int(left),
             "deposited_far": int(cnt["tp_dep_r"])}
         t.close()
-    # NEXT-1: the step with the two-harmonic source and the series capacitor
+    return rows
+
+
+def measure_circuit(cfg):
+    """NEXT-1: the step with the series capacitor against the ideal source."""
+    import paper_1607_04069_gb300 as P
     per_launch = {}
     cb = 10.0 * 8.8541878128e-12 / cfg["gap_m"]
     for name, over in (("circuit", dict(circuit=1, c_block=cb)), ("ideal", {}),
@@ -308,22 +351,46 @@ def measure_rows(d, cfg, peak, cmp_ms, cmp_n, nsort_particles, n_atoms):
         dc.close()
         per_launch[name] = (ms / n * 1e-3, c2["n_e_slots"] + c2["n_i_slots"])
     per, slots = per_launch["circuit"]
-    rows["n1_circuit_step"] = {"workload": cfg["name"] + ", sine source through c = 10 eps0/L",
-                               "value": slots / per, "unit": "particle-steps/s", "mean_launch_us": per * 1e6,
-                               "ideal_source_mean_launch_us": per_launch["ideal"][0] * 1e6,
-                               "two_harmonic_circuit_mean_launch_us": per_launch["two_harmonic_circuit"][0] * 1e6,
-                               "note": "mean step launch by CUDA events, all without an L2 flush between steps; the "
-                                       "two-harmonic source peaks at 2 V0, so its electrons collide more often"}
-    # a9: compaction (counting sort by cell of one species) in the timed run
-    if cmp_n:
-        per_sort = cmp_ms / cmp_n * 1e-3
-        sb = 2 * 28 + 4       # read + write x, v_x, v_y, v_z, id, next-candidate step; one count pass
-        ach = sb * nsort_particles / per_sort / 1e9
-        rows["a9_compaction"] = {"value": nsort_particles / per_sort, "unit": "particles/s",
-                                 "mean_sort_us": per_sort * 1e6,
-                                 "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                                              "frac": ach / peak, "algorithmic_bytes_per_particle": sb}}
-    # a7 (diagnostic form): FP64 Thomas-equivalent solve of the current deposit, one CTA
+    return {"workload": cfg["name"] + ", sine source through c = 10 eps0/L",
+            "value": slots / per, "unit": "particle-steps/s", "mean_launch_us": per * 1e6,
+            "ideal_source_mean_launch_us": per_launch["ideal"][0] * 1e6,
+            "two_harmonic_circuit_mean_launch_us": per_launch["two_harmonic_circuit"][0] * 1e6,
+            "note": "mean step launch by CUDA events, all without an L2 flush between steps; the "
+                    "two-harmonic source peaks at 2 V0, so its electrons collide more often"}
+
+
+def measure_cfg1():
+    """The 25 mm / 128-cell discharge with 64-bit positions, 20 RF periods in
+    full from the loading, and the oracle over the same 20 periods on one
+    host core."""
+    import torch
+    import paper_1607_04069_gb300 as P
+    from paper_1607_04069_gb300 import workloads as W
+    sc = W.ccp_small()
+    ds = P.Discharge(P.params_from_workload(sc))
+    nsteps = sc["periods"] * sc["steps_per_period"]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    ds.step(nsteps)
+    e1.record()
+    torch.cuda.synchronize()
+    gpu_s = e0.elapsed_time(e1) * 1e-3
+    cs = ds.counters()
+    ds.close()
+    n_avg = 0.5 * (sc["n_e0"] + sc["n_i0"] + cs["n_e_slots"] + cs["n_i_slots"])
+    rate_o, sec_o = oracle_rate(dict(sc, weight=sc["weight"]), sc["n_e0"], nsteps, warmup=0)
+    return {"workload": sc["name"] + ", 20 RF periods (8000 steps) from the loading",
+            "value": n_avg * nsteps / gpu_s, "unit": "particle-steps/s", "gpu_s": gpu_s,
+            "oracle_s": sec_o, "oracle_particle_steps_per_s": rate_o, "oracle_cores": 1,
+            "note": "one launch per step, no L2 flush (the 40k-particle state is L2-resident); "
+                    "slot counts include holes"}
+
+
+def measure_poisson(d, cfg):
+    """a7 (diagnostic form): the FP64 field solve of the current deposit, one CTA."""
+    import torch
+    import paper_1607_04069_gb300 as P
     f = d.get_field()
     qi = torch.tensor(f["q_i"], device="cuda")
     qe = torch.tensor(f["q_e"], device="cuda")
@@ -336,9 +403,8 @@ def measure_rows(d, cfg, peak, cmp_ms, cmp_n, nsort_particles, n_atoms):
         P.op_poisson(qi, qe, cfg["n_cells"], dx, cfg["weight"], 0.0)
     e1.record()
     torch.cuda.synchronize()
-    rows["a7_poisson_fp64"] = {"value": e0.elapsed_time(e1) / 20 * 1e3, "unit": "us per solve",
-                               "nodes": cfg["n_cells"] + 1, "bound": "latency (one CTA)"}
-    return rows
+    return {"value": e0.elapsed_time(e1) / 20 * 1e3, "unit": "us per solve",
+            "nodes": cfg["n_cells"] + 1, "bound": "latency (one CTA)"}
 
 
 def measure_batched(n_discharges, steps, warmup, peak, run_periods=20):
@@ -416,7 +482,7 @@ def measure_batched(n_discharges, steps, warmup, peak, run_periods=20):
                          "design_frac": DESIGN_BYTES * n_part / (best_ms * 1e-3) / 1e9 / peak}}
 
 
-def measure_served(n_requests, rate_hz, max_periods, tol=0.01, seed=1239):
+def measure_served(n_requests, rate_hz, max_periods, tol=0.01, seed=1239, criterion="inventory", window=1):
     """The served form: a Poisson stream of discharge requests drawn from the
     batched workload's ranges, each run to periodic steady state (relative
     period-to-period change of the cycle-averaged n_e and n_i below tol, at
@@ -429,8 +495,9 @@ def measure_served(n_requests, rate_hz, max_periods, tol=0.01, seed=1239):
     cfgs = W.batched(n_requests, seed=seed)
     arrivals = W.poisson_arrivals(rate_hz, n_requests, seed)
     out = {}
+    crit = {"inventory": 0, "profile": 1}[criterion]
     for mode, batched in (("batched", 1), ("plain_loop", 0)):
-        srv = P.Server(batched=batched, max_periods=max_periods, tol=tol)
+        srv = P.Server(batched=batched, max_periods=max_periods, tol=tol, criterion=crit, window_periods=window)
         t0 = srv.clock()
         ids = []
         for c, a in zip(cfgs, arrivals):
@@ -438,6 +505,7 @@ def measure_served(n_requests, rate_hz, max_periods, tol=0.01, seed=1239):
                 time.sleep(min(0.005, max(0.0, t0 + a - srv.clock())))
             ids.append(srv.submit(P.params_from_workload(c), t0 + a))
         infos = [srv.wait(i) for i in ids]
+        errors = sorted({srv.error(i) for i, info in zip(ids, infos) if info["state"] in ("failed", "rejected")})
         st = srv.stats()
         srv.close()
         lat = np.array([i["t_done"] - i["t_arrival"] for i in infos])
@@ -447,15 +515,17 @@ def measure_served(n_requests, rate_hz, max_periods, tol=0.01, seed=1239):
                      "discharges_per_hour": len(ok) * 3600.0 / span, "span_s": span,
                      "converged": sum(i["state"] == "converged" for i in infos),
                      "hit_max_periods": sum(i["state"] == "max_periods" for i in infos),
-                     "failed": len(infos) - len(ok),
+                     "failed": len(infos) - len(ok), "failure_reasons": errors,
                      "periods_mean": float(np.mean([i["periods"] for i in infos])),
                      "last_change_median": float(np.median([i["change"] for i in infos])),
                      "particle_steps_per_s_busy": st["particle_steps"] / max(st["busy_s"], 1e-9)}
     b, l = out["batched"], out["plain_loop"]
+    measure = ("relative L2 change of the window-averaged n_e and n_i profiles" if criterion == "profile"
+               else "relative change of the window-averaged e- and Ar+ inventories")
     return {"workload": f"{n_requests} requests, Poisson arrivals at {rate_hz:g}/s, sizes and conditions drawn "
-                        f"as in the batched workload, each run to steady state (relative change of the "
-                        f"period-averaged e- and Ar+ inventories < {tol:g} between RF periods, at most "
-                        f"{max_periods} periods)",
+                        f"as in the batched workload, each run to steady state ({measure} < {tol:g} between "
+                        f"windows of {window} RF periods, at most {max_periods} periods)",
+            "criterion": criterion, "window_periods": window, "max_periods": max_periods,
             "value": b["discharges_per_hour"], "unit": "discharges/hour",
             "p50_latency_s": b["p50_latency_s"], "p99_latency_s": b["p99_latency_s"],
             "speedup_vs_plain_loop": b["discharges_per_hour"] / l["discharges_per_hour"],
@@ -520,11 +590,18 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=300)
     ap.add_argument("--no-rows", action="store_true")
+    ap.add_argument("--rows", default="all",
+                    help="comma-separated rows to measure (a8_tp_step, a8_tp_flight, n1_circuit_step, "
+                         "a9_compaction, cfg1_ccp_small, a7_poisson_fp64, b_batched, c_served) or all")
+    ap.add_argument("--tp-step-only", type=int, default=0,
+                    help="time only the TP step on this many atoms (profiling runs) and print it")
     ap.add_argument("--tp-atoms", type=int, default=100_000_000)
     ap.add_argument("--batch-discharges", type=int, default=256)
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-rate", type=float, default=4.0)
     ap.add_argument("--serve-max-periods", type=int, default=20)
+    ap.add_argument("--serve-criterion", default="inventory", choices=["inventory", "profile"])
+    ap.add_argument("--serve-window", type=int, default=1)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_setup()
@@ -539,6 +616,10 @@ def main():
     from paper_1607_04069_gb300 import shard
 
     torch.cuda.set_device(local)
+    if args.tp_step_only > 0:
+        per = tp_step_time(args.tp_step_only)
+        print(json.dumps({"tp_step_atoms": args.tp_step_only, "mean_launch_us": per * 1e6}), flush=True)
+        return
     # one discharge; with several ranks its superparticles are split over them
     cfg_all = workload(args.n_per_species * ws, 1236)
     cfg = shard.shard_workload(cfg_all, rank, ws)
@@ -659,12 +740,14 @@ def main():
                          f"{nst} full PIC/MCC steps in {dt:.1f} s"}
     clocks = clk.summary()
     rows = None
+    want = None if args.rows == "all" else set(args.rows.split(","))
     if rank == 0 and not args.no_rows:
-        rows = measure_rows(sd.d, cfg, peak, cmp_ms, cmp_n, 0.25 * (n_start + n_end), args.tp_atoms)
-        if args.batch_discharges > 0:
+        rows = measure_rows(sd.d, cfg, peak, cmp_ms, cmp_n, 0.25 * (n_start + n_end), args.tp_atoms, want)
+        if args.batch_discharges > 0 and (want is None or "b_batched" in want):
             rows["b_batched"] = measure_batched(args.batch_discharges, 30, 10, peak)
-        if args.serve_requests > 0:
-            rows["c_served"] = measure_served(args.serve_requests, args.serve_rate, args.serve_max_periods)
+        if args.serve_requests > 0 and (want is None or "c_served" in want):
+            rows["c_served"] = measure_served(args.serve_requests, args.serve_rate, args.serve_max_periods,
+                                              criterion=args.serve_criterion, window=args.serve_window)
     if rank == 0:
         line = {"metric": "particle-steps/s", "value": value, "unit": "particle-steps/s", "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,

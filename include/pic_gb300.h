@@ -40,7 +40,9 @@ extern "C" {
 #define PIC_ERR_NUMERICS (-5)        /* an electron exceeded the null-collision energy cap */
 #define PIC_ERR_CUDA (-7)            /* a CUDA call failed (detail in pic_last_error)      */
 #define PIC_ERR_NO_DEVICE (-8)       /* no CUDA device is visible                          */
-#define PIC_ERR_TIMEOUT (-9)         /* pic_server_wait: the request had not finished      */
+#define PIC_ERR_TIMEOUT (-9)         /* pic_server_wait: the request had not finished;     */
+                                     /* pic_sync: a kernel's bounded wait for a bulk copy  */
+                                     /* gave up (the step's results are not valid)         */
 
 enum pic_species { PIC_ELECTRON = 0, PIC_ION = 1, PIC_ATOM = 2 };
 
@@ -388,6 +390,15 @@ int pic_batch_ctx(pic_batch* b, int slot, pic_ctx** out);
  * 0 for the automatic division). */
 int pic_batch_set_target(pic_batch* b, int64_t particles_per_cta);
 
+/* How the launch runs those CTA slots.  particles_per_chunk > 0 (default
+ * 131072): a grid of resident CTAs (a few per SM) takes chunks of
+ * consecutive slots of one member from a work counter, paying the member's
+ * deposit copy and field solve once per chunk instead of once per slot; the
+ * last fifth of each member's slots form one-slot chunks at the end, so the
+ * launch ends on short work.  0: one CTA per slot, scheduled by the
+ * hardware.  The members' results are the same either way. */
+int pic_batch_set_chunk(pic_batch* b, int64_t particles_per_chunk);
+
 /* Advance every member n_steps steps (one launch per step plus each
  * member's due compactions).  Asynchronous, as pic_step. */
 int pic_batch_step(pic_batch* b, int64_t n_steps);
@@ -438,10 +449,14 @@ void pic_batch_destroy(pic_batch* b);
  * is below tol, the request completes with state CONVERGED (or MAX_PERIODS
  * when max_periods > 0 periods have run), its last window-averaged n_e, n_i
  * and phi are kept on the host and its device state is released.  Every
- * request needs a whole number of steps per RF period, a multiple of the
- * chunk set by the first admitted request; batched, it also follows the
- * pic_batch rules (32-bit positions, one dt and diag_every).  Others
- * complete as FAILED, and a state larger than the whole budget as REJECTED.  The change is that of
+ * request needs a whole number of steps per RF period (else FAILED).  The
+ * first request admitted while nothing runs sets the chunk; a later request
+ * joins only if its period is a multiple of the chunk and the chunk a
+ * multiple of its diag_every, and otherwise waits at the head of the queue
+ * until the running discharges have finished (the chunk is then set anew).
+ * Batched, a request also follows the pic_batch rules (32-bit positions,
+ * one dt and diag_every; else FAILED).  A state larger than the whole
+ * budget completes as REJECTED.  The change is that of
  * the inventory, the spatial integral of the density (criterion
  * PIC_STEADY_INVENTORY, the default: in steady state generation and losses
  * balance, Sec. "Simulation Results"), or of the profile in L2 over the

@@ -128,6 +128,7 @@ def lib():
             "pic_batch_remove": [vp, C.c_int],
             "pic_batch_ctx": [vp, C.c_int, C.POINTER(vp)],
             "pic_batch_set_target": [vp, i64],
+            "pic_batch_set_chunk": [vp, i64],
             "pic_batch_step": [vp, i64],
             "pic_batch_sync": [vp],
             "pic_batch_graphs": [vp, C.c_int],
@@ -373,7 +374,7 @@ class Batch:
     them (``pic_batch_*``).  Members share dt and diag_every, use 32-bit
     positions and a whole number of steps per RF period."""
 
-    def __init__(self, stream=None, particles_per_cta=None):
+    def __init__(self, stream=None, particles_per_cta=None, particles_per_chunk=None):
         self.stream = _stream_handle(stream)
         h = C.c_void_p()
         _check(lib().pic_batch_create(C.c_void_p(self.stream), C.byref(h)))
@@ -381,6 +382,12 @@ class Batch:
         self._params = {}
         if particles_per_cta is not None:
             _check(lib().pic_batch_set_target(self.h, int(particles_per_cta)))
+        if particles_per_chunk is not None:
+            self.set_chunk(particles_per_chunk)
+
+    def set_chunk(self, particles_per_chunk):
+        """Resident CTAs taking chunks of this many particles (0: one CTA per slot)."""
+        _check(lib().pic_batch_set_chunk(self.h, int(particles_per_chunk)))
 
     def add(self, params) -> int:
         if isinstance(params, dict):

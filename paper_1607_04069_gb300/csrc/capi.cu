@@ -676,6 +676,7 @@ int pic_sync(pic_ctx* c)
         if (err & kErrCapacity) return fail(PIC_ERR_CAPACITY, "a birth or launch exceeded the capacity");
         if (err & kErrNumerics) return fail(PIC_ERR_NUMERICS, "electron energy above eps_max");
         if (err & kErrIndex) return fail(PIC_ERR_NUMERICS, "a 64-bit position outside [0, n_cells)");
+        if (err & kErrTimeout) return fail(PIC_ERR_TIMEOUT, "a kernel's wait for a bulk copy into shared memory gave up");
     }
     return PIC_OK;
 }
@@ -1272,6 +1273,13 @@ struct pic_batch {
     std::vector<int> h_owner;
     int grid = 0, max_ncell = 0;
     bool dirty = true;
+    // resident-CTA launch: chunks of CTA slots taken from a work counter
+    long long chunk = 131072;              // particles per chunk; 0: one CTA per slot
+    std::vector<BatchChunk> h_chunk;
+    BatchChunk* d_chunk = nullptr;
+    size_t chunk_cap = 0;
+    unsigned int* d_work = nullptr;
+    int grid_res = 0;                      // resident CTAs of the chunked launch
     // CUDA graph of one sampling period (diag_every launches), replayed while
     // no compaction falls inside it; captured on a private stream
     bool use_graph = false;
@@ -1330,6 +1338,38 @@ int batch_rebuild(pic_batch* b)
         cta += ncta;
     }
     b->grid = cta;
+    // chunks of consecutive CTA slots of one member; the last fifth of each
+    // member's slots go, one per chunk, to the end of the list, so the launch
+    // ends on short pieces of work
+    b->h_chunk.clear();
+    std::vector<BatchChunk> tail;
+    for (size_t k = 0; k < b->h_ent.size(); ++k) {
+        const int ncta = b->h_ent[k].ncta;
+        const int per = (int)std::max(1ll, b->chunk / std::max(1ll, target));
+        const int head = per > 1 ? (ncta * 4 / 5) / per * per : ncta;
+        for (int v = 0; v < head; v += per) b->h_chunk.push_back(BatchChunk{(int)k, v, std::min(head, v + per), 0});
+        for (int v = head; v < ncta; ++v) tail.push_back(BatchChunk{(int)k, v, v + 1, 0});
+    }
+    b->h_chunk.insert(b->h_chunk.end(), tail.begin(), tail.end());
+    {
+        int dev = 0, sms = 1;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        b->grid_res = (int)std::min<long long>((long long)sms * std::max(per_sm, 1), (long long)b->h_chunk.size());
+    }
+    if (b->h_chunk.size() > b->chunk_cap) {
+        if (b->d_chunk) CK(cudaFree(b->d_chunk));
+        b->d_chunk = nullptr;
+        b->chunk_cap = b->h_chunk.size() + 256;
+        CK(cudaMalloc(&b->d_chunk, b->chunk_cap * sizeof(BatchChunk)));
+    }
+    if (!b->d_work) {
+        CK(cudaMalloc(&b->d_work, 2 * sizeof(unsigned int)));
+        CK(cudaMemsetAsync(b->d_work, 0, 2 * sizeof(unsigned int), b->stream));
+    }
+    if (!b->h_chunk.empty())
+        CK(cudaMemcpyAsync(b->d_chunk, b->h_chunk.data(), b->h_chunk.size() * sizeof(BatchChunk),
+                           cudaMemcpyHostToDevice, b->stream));
     if (b->gexec) {
         CK(cudaGraphExecDestroy(b->gexec));
         b->gexec = nullptr;
@@ -1371,6 +1411,15 @@ int batch_advance(pic_batch* b)
     return PIC_OK;
 }
 
+// one step launch of every member: resident CTAs taking chunks, or one CTA per slot
+cudaError_t batch_launch(pic_batch* b, bool sample, cudaStream_t st)
+{
+    if (b->chunk > 0)
+        return launch_mover_batch_chunks(b->d_ent, b->d_chunk, (int)b->h_chunk.size(), b->d_work, b->grid_res,
+                                         b->max_ncell, sample, st);
+    return launch_mover_batch(b->d_ent, b->d_owner, b->grid, b->max_ncell, sample, st);
+}
+
 // Whether a member compacts after one of the first m - 1 steps from step l on.
 bool batch_sort_inside(const pic_batch* b, long long l, int m)
 {
@@ -1392,8 +1441,7 @@ int batch_capture(pic_batch* b, int m)
     if (!b->cap_stream) CK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
     CK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
-    for (int j = 0; j < m && e == cudaSuccess; ++j)
-        e = launch_mover_batch(b->d_ent, b->d_owner, b->grid, b->max_ncell, j == m - 1, b->cap_stream);
+    for (int j = 0; j < m && e == cudaSuccess; ++j) e = batch_launch(b, j == m - 1, b->cap_stream);
     cudaGraph_t g = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
     if (e == cudaSuccess) e = e2;
@@ -1523,6 +1571,15 @@ int pic_batch_ctx(pic_batch* b, int slot, pic_ctx** out)
     return PIC_OK;
 }
 
+int pic_batch_set_chunk(pic_batch* b, int64_t particles_per_chunk)
+{
+    if (!b || particles_per_chunk < 0) return fail(PIC_ERR_INVALID_ARG, "bad batch or chunk size");
+    CK(cudaStreamSynchronize(b->stream));
+    b->chunk = particles_per_chunk;
+    b->dirty = true;
+    return PIC_OK;
+}
+
 int pic_batch_set_target(pic_batch* b, int64_t particles_per_cta)
 {
     if (!b || (particles_per_cta != 0 && particles_per_cta < 1024))
@@ -1571,8 +1628,7 @@ int pic_batch_step(pic_batch* b, int64_t n)
         int rc = batch_timer(b, block ? de : 1, true);
         if (rc) return rc;
         if (block) CK(cudaGraphLaunch(b->gexec, b->stream));
-        else CK(launch_mover_batch(b->d_ent, b->d_owner, b->grid, b->max_ncell, de > 0 && (l + 1) % de == 0,
-                                   b->stream));
+        else CK(batch_launch(b, de > 0 && (l + 1) % de == 0, b->stream));
         rc = batch_timer(b, 0, false);
         if (rc) return rc;
         const int m = block ? de : 1;
@@ -1663,6 +1719,8 @@ void pic_batch_destroy(pic_batch* b)
     }
     if (b->d_ent) cudaFree(b->d_ent);
     if (b->d_owner) cudaFree(b->d_owner);
+    if (b->d_chunk) cudaFree(b->d_chunk);
+    if (b->d_work) cudaFree(b->d_work);
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     for (cudaEvent_t ev : b->tev) cudaEventDestroy(ev);

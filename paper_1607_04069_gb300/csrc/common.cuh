@@ -66,7 +66,7 @@ enum {
 };
 
 // error bits of Ctl::err
-enum : uint32_t { kErrCapacity = 1u, kErrNumerics = 2u, kErrIndex = 4u };
+enum : uint32_t { kErrCapacity = 1u, kErrNumerics = 2u, kErrIndex = 4u, kErrTimeout = 8u };
 
 // ---------------------------------------------------------------- state
 struct SpBuf {                 // one species, one ping-pong half (structure of arrays)
@@ -225,6 +225,12 @@ struct BatchEntry {
     int cta0, ncta;            // CTAs [cta0, cta0 + ncta) of the launch
 };
 
+// A chunk of the batched launch with resident CTAs: CTA slots [v0, v1) of
+// discharge `member`, run one after another by one CTA.
+struct BatchChunk {
+    int member, v0, v1, pad;
+};
+
 // global nanosecond timer, comparable across SMs
 __device__ __forceinline__ unsigned long long gtimer()
 {
@@ -371,6 +377,50 @@ __device__ __forceinline__ float3 emit(float uE, float uT, float uP, float Emax,
 __device__ __forceinline__ float lambda_ar_al()
 {
     return (float)(4.0 * kMAR * kMAL / ((kMAR + kMAL) * (kMAR + kMAL)));
+}
+
+// ---------------------------------------------------------------- bulk copies (TMA)
+// One-dimensional bulk copies global -> shared memory by the tensor memory
+// accelerator, completing on a shared-memory mbarrier (transaction count in
+// bytes).  Addresses and sizes are multiples of 16 bytes.
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// make the barrier initialisation visible to the bulk-copy (async) proxy
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// order earlier generic-proxy accesses of shared memory before later bulk copies into it
+__device__ __forceinline__ void async_proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// Wait for the barrier's phase `parity` to complete, at most max_tries polls
+// (each may suspend the thread for a short while); false if it never did.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned max_tries)
+{
+    const unsigned a = smem_addr(bar);
+    for (unsigned i = 0; i < max_tries; ++i) {
+        unsigned ok;
+        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                     : "=r"(ok)
+                     : "r"(a), "r"(parity)
+                     : "memory");
+        if (ok) return true;
+    }
+    return false;
 }
 
 // ---------------------------------------------------------------- histogram bins

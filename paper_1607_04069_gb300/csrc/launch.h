@@ -11,9 +11,13 @@ constexpr int kMoverThreads = 256;
 #define PG_MOVER_MIN_BLOCKS 2
 #endif
 constexpr int kMoverMinBlocks = PG_MOVER_MIN_BLOCKS;   // resident CTAs per SM the register budget is sized for
+#ifndef PG_MOVER_PDL
+#define PG_MOVER_PDL 1
+#endif
+constexpr int kMoverPdl = PG_MOVER_PDL;           // step launches overlap the previous launch's tail
 constexpr int kTpThreads = 256;
 #ifndef PG_TP_MIN_BLOCKS
-#define PG_TP_MIN_BLOCKS 4
+#define PG_TP_MIN_BLOCKS 3
 #endif
 constexpr int kTpMinBlocks = PG_TP_MIN_BLOCKS;   // resident CTAs per SM the TP step's registers are sized for
 
@@ -29,6 +33,10 @@ cudaError_t launch_mover(const Dev& d, const StepArgs& a, int grid, int mode, cu
 // must have been called with max_ncell first.
 cudaError_t launch_mover_batch(const BatchEntry* ent, const int* owner, int grid, int max_ncell, bool sample,
                                cudaStream_t st);
+// the same with resident CTAs taking chunks of CTA slots from the work counter
+// work[2] (zero before the first launch; each launch leaves it zero)
+cudaError_t launch_mover_batch_chunks(const BatchEntry* ent, const BatchChunk* chunks, int nchunks, unsigned int* work,
+                                      int grid, int max_ncell, bool sample, cudaStream_t st);
 // the shared-memory attribute of both batch instantiations (set before a graph
 // capture), and the resident CTAs per SM it allows (blocks_per_sm may be NULL)
 cudaError_t mover_batch_attr(int max_ncell, int* blocks_per_sm);

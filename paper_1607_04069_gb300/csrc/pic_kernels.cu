@@ -517,8 +517,11 @@ __device__ void flush_tile(const Acc& A, int N, unsigned int jlo, unsigned int j
 // each thread loads its next group before working on the current one.
 // The body of one step launch for one discharge, run by CTA `cta` of the
 // `ncta` CTAs the discharge has in the launch.
+// reuse_field: the CTA ran the previous body call for the same discharge and
+// step, so its shared memory already holds that step's deposit and field.
 template <bool P64, int MODE, bool SAMPLE>
-__device__ __forceinline__ void mover_body(const Dev& d, const StepArgs& a, int cta, int ncta, bool sample_on = true)
+__device__ __forceinline__ void mover_body(const Dev& d, const StepArgs& a, int cta, int ncta, bool sample_on = true,
+                                           bool reuse_field = false)
 {
     using PosT = typename std::conditional<P64, double, uint32_t>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -542,6 +545,7 @@ __device__ __forceinline__ void mover_body(const Dev& d, const StepArgs& a, int 
     __shared__ unsigned int s_jlo, s_jhi, s_qn;
     __shared__ int s_last, s_overflow;
     __shared__ unsigned long long s_evmax, s_flushns;
+    __shared__ double s_vel;                    // electrode potential of the field in shared memory
 
     unsigned long long* tr = d.trace ? d.trace + (size_t)cta * kTraceSlots : nullptr;
     if (tr && threadIdx.x == 0) tr[0] = gtimer();
@@ -552,7 +556,7 @@ __device__ __forceinline__ void mover_body(const Dev& d, const StepArgs& a, int 
     // that its latency passes during the deposit copy
     const long long wall_dn = MODE == 0 && a.field_mode == kFieldCircuit ? ctl->wall_dn : 0ll;
     const unsigned int field_override = MODE == 0 ? ctl->field_override : 0u;
-    if (MODE == 0) {
+    if (MODE == 0 && !reuse_field) {
         // both deposits of x^l (slot l%3) into shared memory: asynchronous
         // 16-byte copies, all in flight at once (arrays 256-byte aligned, padded)
         const int slot = l % 3;
@@ -628,20 +632,22 @@ __device__ __forceinline__ void mover_body(const Dev& d, const StepArgs& a, int 
     __syncthreads();
     if (tr && threadIdx.x == 0) tr[1] = gtimer();
     double v_el = a.v_left;                     // electrode potential of step l
-    if (MODE == 0) {
+    if (MODE == 0 && !reuse_field) {
         // field of step l: every CTA solves from the deposit of x^l
         if (field_override) {
             for (int i = threadIdx.x; i < N1; i += blockDim.x) sE[i] = d.E32[i];
         } else {
             v_el = block_field_f32(d, sqe, sqi, sE, a, wall_dn);
         }
+        if (threadIdx.x == 0) s_vel = v_el;
     }
     __syncthreads();
     if (tr && threadIdx.x == 0) tr[2] = gtimer();
-    if (MODE == 0) {
+    if (MODE == 0 && !reuse_field) {
         for (int i = threadIdx.x; i < N; i += blockDim.x) sEd[i] = make_float2(sE[i], sE[i + 1] - sE[i]);
         __syncthreads();
     }
+    if (reuse_field) v_el = s_vel;
     if (tr && threadIdx.x == 0) tr[3] = gtimer();
 
     const float qmdt = d.qm_dt[s];
@@ -875,6 +881,12 @@ __device__ __forceinline__ void mover_body(const Dev& d, const StepArgs& a, int 
 template <bool P64, int MODE, bool SAMPLE>
 __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks) k_mover(Dev d, StepArgs a)
 {
+    // Launched with programmatic stream serialization: the next launch in the
+    // stream may place its CTAs on SMs as this launch's CTAs exit, and every
+    // CTA waits here until the previous launch has completed and its writes
+    // are visible (a hardware dependency, not a spin), before any global access.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     mover_body<P64, MODE, SAMPLE>(d, a, blockIdx.x, gridDim.x);
 }
 
@@ -908,6 +920,65 @@ __global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks)
     }
     __syncthreads();
     mover_body<false, 0, SAMPLE>(sd, sa, (int)blockIdx.x - e.cta0, e.ncta);
+}
+
+// The batched step with resident CTAs: the launch has a few CTAs per SM, and
+// each takes chunks of consecutive CTA slots of one discharge from a work
+// counter (chunks[c]: discharge, first and last slot).  A chunk's slots run
+// one after another through the step body; the first pays the deposit copy
+// and field solve of that discharge, the others reuse them.  work[0] hands
+// out chunks, work[1] counts the CTAs that have finished; the last resets both
+// for the next launch.
+template <bool SAMPLE>
+__global__ void __launch_bounds__(kMoverThreads, kMoverMinBlocks)
+    k_mover_batch_chunks(const BatchEntry* __restrict__ ent, const BatchChunk* __restrict__ chunks, int nchunks,
+                         unsigned int* work)
+{
+    __shared__ __align__(16) Dev sd;
+    __shared__ StepArgs sa;
+    __shared__ int s_c, s_member;
+    if (threadIdx.x == 0) s_member = -1;
+    for (;;) {
+        __syncthreads();                          // the previous body (and its commit) are done
+        if (threadIdx.x == 0) s_c = (int)atomicAdd(&work[0], 1u);
+        __syncthreads();
+        const int c = s_c;
+        if (c >= nchunks) break;
+        const BatchChunk ch = chunks[c];
+        const bool same = ch.member == s_member;
+        if (!same) {
+            const BatchEntry& e = ent[ch.member];
+            const unsigned int* src = (const unsigned int*)&e.d;
+            unsigned int* dst = (unsigned int*)&sd;
+            for (int i = threadIdx.x; i < (int)(sizeof(Dev) / 4); i += blockDim.x) dst[i] = src[i];
+            if (threadIdx.x == 0) {
+                const Ctl* cc = e.d.ctl;
+                const unsigned int l = cc->step;
+                StepArgs a = e.phase[l % e.period];
+                a.step = l;
+                a.accumulate = l >= e.acc_from ? 1 : 0;
+                a.cur[0] = cc->cur[0];
+                a.cur[1] = cc->cur[1];
+                a.cur[2] = cc->cur[2];
+                sa = a;
+                s_member = ch.member;
+            }
+            __syncthreads();
+        }
+        const int ncta = ent[ch.member].ncta;
+        for (int v = ch.v0; v < ch.v1; ++v) {
+            mover_body<false, 0, SAMPLE>(sd, sa, v, ncta, true, same || v > ch.v0);
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&work[1], 1u) == gridDim.x - 1) {
+            work[0] = 0;
+            work[1] = 0;
+            __threadfence();
+        }
+    }
 }
 
 // ---------------------------------------------------------------- standalone ops
@@ -1152,10 +1223,19 @@ static cudaError_t launch_mover_t(const Dev& d, const StepArgs& a, int grid, int
                                : (sample ? (const void*)k_mover<P64, 0, true> : (const void*)k_mover<P64, 0, false>);
     cudaError_t e = set_smem_attr(fn, sm);
     if (e != cudaSuccess) return e;
-    if (mode == 1) k_mover<P64, 1, false><<<grid, kMoverThreads, sm, st>>>(d, a);
-    else if (sample) k_mover<P64, 0, true><<<grid, kMoverThreads, sm, st>>>(d, a);
-    else k_mover<P64, 0, false><<<grid, kMoverThreads, sm, st>>>(d, a);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kMoverThreads);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = kMoverPdl;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (mode == 1) return cudaLaunchKernelEx(&cfg, k_mover<P64, 1, false>, d, a);
+    if (sample) return cudaLaunchKernelEx(&cfg, k_mover<P64, 0, true>, d, a);
+    return cudaLaunchKernelEx(&cfg, k_mover<P64, 0, false>, d, a);
 }
 
 cudaError_t launch_mover_batch(const BatchEntry* ent, const int* owner, int grid, int max_ncell, bool sample,
@@ -1167,10 +1247,23 @@ cudaError_t launch_mover_batch(const BatchEntry* ent, const int* owner, int grid
     return cudaGetLastError();
 }
 
+cudaError_t launch_mover_batch_chunks(const BatchEntry* ent, const BatchChunk* chunks, int nchunks, unsigned int* work,
+                                      int grid, int max_ncell, bool sample, cudaStream_t st)
+{
+    const size_t sm = mover_smem(max_ncell);      // attribute set by mover_batch_attr
+    if (sample) k_mover_batch_chunks<true><<<grid, kMoverThreads, sm, st>>>(ent, chunks, nchunks, work);
+    else k_mover_batch_chunks<false><<<grid, kMoverThreads, sm, st>>>(ent, chunks, nchunks, work);
+    return cudaGetLastError();
+}
+
 cudaError_t mover_batch_attr(int max_ncell, int* blocks_per_sm)
 {
     const size_t sm = mover_smem(max_ncell);
     cudaError_t e = set_smem_attr((const void*)k_mover_batch<true>, sm);
+    if (e != cudaSuccess) return e;
+    e = set_smem_attr((const void*)k_mover_batch_chunks<true>, sm);
+    if (e != cudaSuccess) return e;
+    e = set_smem_attr((const void*)k_mover_batch_chunks<false>, sm);
     if (e != cudaSuccess) return e;
     e = set_smem_attr((const void*)k_mover_batch<false>, sm);
     if (e != cudaSuccess || !blocks_per_sm) return e;

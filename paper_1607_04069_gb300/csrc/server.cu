@@ -91,8 +91,10 @@ struct pic_server {
     std::vector<Request*> running;       // touched by the worker only
     int64_t next_id = 1;
     int64_t bytes_used = 0;
-    long long period = 0, chunk = 0;     // steps per RF period of the first admitted request, and
-                                         // per worker chunk (a divisor of every admitted period)
+    long long period = 0, chunk = 0;     // steps per RF period of the first request admitted since the
+                                         // server was last idle, and per worker chunk (a divisor of
+                                         // every running period and a multiple of every running
+                                         // diag_every); both reset when nothing runs
     bool stop = false;
     std::string fatal;
     pic_server_stats st;
@@ -125,14 +127,35 @@ void release(pic_server* S, Request* r)
     r->slot = -1;
 }
 
+// The worker's chunk for a first request of period P and sampling stride de:
+// the largest chunk P / m, m <= chunks_per_period, that divides P and is a
+// multiple of de (P itself when none is).
+long long chunk_for(const pic_server* S, long long P, int de)
+{
+    const int want = std::max(1, S->o.chunks_per_period);
+    for (int m = want; m >= 1; --m)
+        if (P % m == 0 && (P / m) % de == 0) return P / m;
+    return P;
+}
+
+// Whether r can join the running discharges: its period a multiple of the
+// chunk and the chunk a multiple of its sampling stride.  A request that cannot
+// waits in the queue until the running ones have finished.
+bool fits(const pic_server* S, const Request* r)
+{
+    const long long P = steps_per_period(r->p);
+    if (P == 0 || S->period == 0) return true;        // (P == 0 fails at admission)
+    const int de = r->p.diag_every > 0 ? r->p.diag_every : 1;
+    return P % S->chunk == 0 && S->chunk % de == 0;
+}
+
 // Admit r: create its discharge.  Returns false (and completes r as failed)
-// if the parameters do not fit the server's step schedule or creation fails.
+// if its RF period is not a whole number of steps or creation fails.
 bool admit(pic_server* S, Request* r)
 {
     const long long P = steps_per_period(r->p);
     std::string why;
     if (P == 0) why = "the RF period is not a whole number of steps";
-    else if (S->period > 0 && P % S->chunk != 0) why = "RF period incompatible with the running discharges";
     int rc = PIC_OK;
     if (why.empty()) {
         if (S->batch) {
@@ -149,17 +172,6 @@ bool admit(pic_server* S, Request* r)
         return false;
     }
     r->period = P;
-    if (S->period == 0) {
-        S->period = P;
-        const int de = r->p.diag_every > 0 ? r->p.diag_every : 1;
-        const int want = std::max(1, S->o.chunks_per_period);
-        S->chunk = P;
-        for (int m = want; m >= 1; --m)
-            if (P % m == 0 && (P / m) % de == 0) {
-                S->chunk = P / m;
-                break;
-            }
-    }
     std::lock_guard<std::mutex> lk(S->mu);
     r->info.state = PIC_REQ_RUNNING;
     r->info.t_admit = S->now();
@@ -239,9 +251,16 @@ void work(pic_server* S)
             std::unique_lock<std::mutex> lk(S->mu);
             S->cv_work.wait(lk, [&] { return S->stop || !S->queue.empty() || !S->running.empty(); });
             if (S->stop) break;
+            if (S->running.empty()) S->period = S->chunk = 0;   // idle: the next request sets the schedule
             while (!S->queue.empty()) {                     // arrival order, within the budget
                 Request* r = S->req[S->queue.front()].get();
                 if (S->bytes_used + r->info.bytes > S->o.hbm_budget_bytes) break;
+                if (!fits(S, r)) break;                     // waits until the running ones finish
+                const long long P = steps_per_period(r->p);
+                if (S->period == 0 && P > 0) {
+                    S->period = P;
+                    S->chunk = chunk_for(S, P, r->p.diag_every > 0 ? r->p.diag_every : 1);
+                }
                 S->queue.pop_front();
                 S->bytes_used += r->info.bytes;
                 adm.push_back(r);

@@ -101,6 +101,30 @@ __device__ __forceinline__ float3 tp_scatter_dir(int model, float gx, float gy, 
                        cc * uz + sc * (ce * e1z + se * e2z));
 }
 
+// The fixed-point move of one TP step: the new position, or the electrode
+// reached (0 at x = 0, 1 at x = L; -1 inside).  The displacement rint(v_x dt
+// 2^32 / L) is converted to 32 bits and the exit is a wrap-around test, as in
+// the step kernel; 64-bit integer conversions run on the FP64 units, which
+// this part has few of.  A displacement beyond +-2^31 units (far more than a
+// step of any realistic atom) takes the 64-bit form.
+__device__ __forceinline__ int tp_move(uint32_t x, float vx, float scale, uint32_t* xn)
+{
+    const float fd = vx * scale;
+    if (fabsf(fd) < 2147483520.0f) {
+        const int disp = __float2int_rn(fd);
+        const uint32_t xm = x + (uint32_t)disp;
+        if (disp > 0 && xm < x) return 1;
+        if (disp < 0 && (0u - (uint32_t)disp) >= x) return 0;
+        *xn = xm;
+        return -1;
+    }
+    const long long np = (long long)x + __float2ll_rn(fd);
+    if (np <= 0) return 0;
+    if (np >= 4294967296LL) return 1;
+    *xn = (uint32_t)np;
+    return -1;
+}
+
 // LAW: the VHS / M1 laws (tp_model 1, 2); else hard spheres
 template <bool LAW>
 __global__ void __launch_bounds__(kTpThreads, 2) k_tp_step(Dev d)
@@ -166,9 +190,9 @@ __global__ void __launch_bounds__(kTpThreads, 2) k_tp_step(Dev d)
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 if (x[u] == 0u) continue;
-                const long long np = (long long)x[u] + __float2ll_rn(vx[u] * d.tp_scale);
-                if (np <= 0 || np >= 4294967296LL) {       // sticks at an electrode
-                    const int el = np <= 0 ? 0 : 1;
+                uint32_t xm = 0u;
+                const int el = tp_move(x[u], vx[u], d.tp_scale, &xm);
+                if (el >= 0) {                              // sticks at an electrode
                     const float v2 = vx[u] * vx[u] + vy[u] * vy[u] + vz[u] * vz[u];
                     const float E = v2 * (float)(0.5 * kMAL / kQE);
                     const float ct = fminf(v2 > 0.0f ? fabsf(vx[u]) * rsqrtf(v2) : 1.0f, 1.0f);
@@ -180,7 +204,7 @@ __global__ void __launch_bounds__(kTpThreads, 2) k_tp_step(Dev d)
                     x[u] = 0u;
                     continue;
                 }
-                x[u] = (uint32_t)np;
+                x[u] = xm;
                 // Collision test u < Pc(g), Pc = 1 - exp(-n sigma g dt), g = |v - w| for the gas
                 // partner w of this step.  First against an upper bound of g that needs only the
                 // Box-Muller radii (n1^2 + n2^2 = r1^2, n3^2 <= r2^2): most atoms fail it, and the
@@ -404,6 +428,41 @@ __device__ __noinline__ void tp_stick(const Dev& d, const SpBuf& B, long long i,
     atomicAdd(&d.ctl->cnt[el == 0 ? kCntTpDepL : kCntTpDepR], 1ull);
 }
 
+// The stream of the thinned-candidate TP step is staged in shared memory by
+// bulk copies, one pipeline per warp: the CTA's contiguous run of 4-atom
+// groups is split into one contiguous run per warp, cut into tiles of 32
+// groups (one per lane), and lane 0 keeps the next tiles' x, v_x and
+// candidate-step arrays (3 x 512 B per tile) in flight in a ring of stages,
+// each with its own mbarrier.  Warps do not wait for one another, so a lane
+// busy with a rare candidate holds up only its own warp.  x is stored back
+// from registers; v_x only where a group's atom collided.  Sample steps cut
+// the run into spans of 16384 groups (65536 atoms, the limit of the 32-bit
+// shared tallies) and flush the tallies between spans.
+#ifndef PG_TP_WARP_TILE
+#define PG_TP_WARP_TILE 64
+#endif
+#ifndef PG_TP_STAGES
+#define PG_TP_STAGES 2
+#endif
+constexpr int kTpWarpTile = PG_TP_WARP_TILE;             // groups per warp tile
+constexpr int kTpLaneGroups = kTpWarpTile / 32;          // groups per lane and tile
+constexpr int kTpMaxStages = PG_TP_STAGES;
+constexpr unsigned kTpTmaSpin = 1u << 22;                // polls of a tile's barrier before giving up
+
+// stages per warp: half as many above 1024 cells, whose tallies take more shared memory
+__host__ __device__ __forceinline__ int tp_stages(int N)
+{
+    return N <= 1024 ? kTpMaxStages : (kTpMaxStages > 1 ? kTpMaxStages / 2 : 1);
+}
+__host__ __device__ __forceinline__ size_t tp_tally_bytes128(int N)
+{
+    return (((size_t)N * 12 + (size_t)(N + 1) * 8) + 127) & ~(size_t)127;
+}
+size_t tp_geo_smem(int N)
+{
+    return tp_tally_bytes128(N) + (size_t)(kTpThreads / 32) * tp_stages(N) * 3 * kTpWarpTile * 16;
+}
+
 template <bool LAW>
 __global__ void __launch_bounds__(kTpThreads, kTpMinBlocks) k_tp_step_geo(Dev d)
 {
@@ -415,6 +474,7 @@ __global__ void __launch_bounds__(kTpThreads, kTpMinBlocks) k_tp_step_geo(Dev d)
     A.wlo = A.whi + N;
     A.flo = A.wlo + N;
     A.fhi = (int*)(A.flo + N + 1);
+    __shared__ __align__(8) uint64_t s_bar[kTpThreads / 32][kTpMaxStages];
     __shared__ unsigned int s_coll;
     __shared__ int s_last;
 
@@ -424,6 +484,12 @@ __global__ void __launch_bounds__(kTpThreads, kTpMinBlocks) k_tp_step_geo(Dev d)
     const bool sample = d.diag_every > 0 && ((s + 1) % (unsigned)d.diag_every == 0);
     const long long G4 = (n + 3) >> 2;
     const long long g0 = G4 * blockIdx.x / gridDim.x, g1 = G4 * (blockIdx.x + 1) / gridDim.x;
+    const SpBuf B = d.buf[kTP][ctl->cur[kTP]];
+    const int S = tp_stages(N);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    constexpr unsigned kArr = kTpWarpTile * 16u;                // bytes per array of a tile
+    unsigned char* ring = smem_raw + tp_tally_bytes128(N) + (size_t)wid * S * 3 * kArr;   // 16-byte aligned
+    uint64_t* bars = s_bar[wid];
     if (sample)
         for (int m = threadIdx.x; m <= N; m += blockDim.x) {
             if (m < N) A.cnt[m] = A.whi[m] = A.wlo[m] = 0;
@@ -431,76 +497,117 @@ __global__ void __launch_bounds__(kTpThreads, kTpMinBlocks) k_tp_step_geo(Dev d)
             A.fhi[m] = 0;
         }
     if (threadIdx.x == 0) s_coll = 0;
+    if (lane == 0) {
+        for (int q = 0; q < S; ++q) mbar_init(&bars[q], 1);
+        mbar_init_fence();
+    }
     __syncthreads();
 
-    const SpBuf B = d.buf[kTP][ctl->cur[kTP]];
+    // tile t of the warp's run [a, b) into stage q % S
+    auto issue = [&](long long a, long long b, long long t, unsigned q) {
+        const long long gs = a + t * kTpWarpTile;
+        const unsigned bytes = (unsigned)(min((long long)kTpWarpTile, b - gs) * 16);
+        unsigned char* buf = ring + (size_t)(q % (unsigned)S) * 3 * kArr;
+        uint64_t* bar = &bars[q % (unsigned)S];
+        mbar_expect_tx(bar, 3 * bytes);
+        bulk_g2s(buf, (const uint4*)B.pos + gs, bytes, bar);
+        bulk_g2s(buf + kArr, (const float4*)B.vx + gs, bytes, bar);
+        bulk_g2s(buf + 2 * kArr, (const uint4*)B.nev + gs, bytes, bar);
+    };
+
     unsigned int ncoll = 0;
-    for (long long t0 = g0; t0 < g1; t0 += kTpTileGroups) {
-        const long long t1 = min(g1, t0 + kTpTileGroups);
-        long long g = t0 + threadIdx.x;
-        uint4 P = make_uint4(0u, 0u, 0u, 0u), NV = P;
-        float4 VX = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (g < t1) {
-            P = ((const uint4*)B.pos)[g];
-            VX = ((const float4*)B.vx)[g];
-            NV = ((const uint4*)B.nev)[g];
+    unsigned q0 = 0;                                        // tiles this warp consumed so far
+    bool dead = false;                                      // a wait gave up: this warp skips the rest
+    const long long span = sample ? kTpTileGroups : (g1 - g0);
+    for (long long t0 = g0; t0 < g1; t0 += span) {
+        const long long t1 = min(g1, t0 + span);
+        const long long a = t0 + (t1 - t0) * wid / nw, b = t0 + (t1 - t0) * (wid + 1) / nw;
+        const long long nt = dead ? 0 : (b - a + kTpWarpTile - 1) / kTpWarpTile;
+        if (lane == 0 && nt > 0) {
+            async_proxy_fence();                            // the previous span's reads of the ring are done
+            for (long long t = 0; t < min((long long)S, nt); ++t) issue(a, b, t, q0 + (unsigned)t);
         }
-        for (; g < t1; g += blockDim.x) {
-            uint32_t x[4] = {P.x, P.y, P.z, P.w};
-            float vx[4] = {VX.x, VX.y, VX.z, VX.w};
-            const uint32_t nv[4] = {NV.x, NV.y, NV.z, NV.w};
-            if (g + blockDim.x < t1) {                    // the next group, in flight meanwhile
-                P = ((const uint4*)B.pos)[g + blockDim.x];
-                VX = ((const float4*)B.vx)[g + blockDim.x];
-                NV = ((const uint4*)B.nev)[g + blockDim.x];
-            }
-            if (4 * g + 4 > n)                             // slots past n hold no atom
-#pragma unroll
-                for (int u = 1; u < 4; ++u)
-                    if (4 * g + u >= n) x[u] = 0u;
-            if ((x[0] | x[1] | x[2] | x[3]) == 0u) continue;
-            bool moved = false;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (x[u] == 0u) continue;
-                const long long np = (long long)x[u] + __float2ll_rn(vx[u] * d.tp_scale);
-                if (np <= 0 || np >= 4294967296LL) {       // sticks at an electrode
-                    tp_stick(d, B, 4 * g + u, np <= 0 ? 0 : 1, vx[u]);
-                    x[u] = 0u;
-                    continue;
+        __syncwarp();
+        for (long long t = 0; t < nt; ++t) {
+            const unsigned q = q0 + (unsigned)t;
+            const bool ok = mbar_wait(&bars[q % (unsigned)S], (q / (unsigned)S) & 1u, kTpTmaSpin);
+            if (__any_sync(0xffffffffu, !ok)) {             // let this warp's copies in flight land, then stop
+                if (lane == 0) {
+                    atomicOr(&ctl->err, kErrTimeout);
+                    for (long long u = t; u < min(nt, t + S); ++u)
+                        mbar_wait(&bars[(q0 + (unsigned)u) % (unsigned)S], ((q0 + (unsigned)u) / (unsigned)S) & 1u,
+                                  kTpTmaSpin);
                 }
-                x[u] = (uint32_t)np;
-                if (nv[u] == 0u || (int)(nv[u] - 1u - s) <= 0) {   // a candidate due, or no gap yet
-                    bool hit;
-                    vx[u] = tp_candidate<LAW>(d, B, 4 * g + u, s, vx[u], nv[u], &hit);
-                    if (hit) {
-                        moved = true;
-                        ++ncoll;
+                __syncwarp();
+                dead = true;
+                break;
+            }
+            const long long gs = a + t * kTpWarpTile;
+            const unsigned char* buf = ring + (size_t)(q % (unsigned)S) * 3 * kArr;
+#pragma unroll 1
+            for (int r = 0; r < kTpLaneGroups; ++r) {
+                const int e = lane + 32 * r;
+                if (gs + e >= b) break;
+                const long long g = gs + e;
+                const uint4 P = ((const uint4*)buf)[e];
+                const float4 VX = ((const float4*)(buf + kArr))[e];
+                const uint4 NV = ((const uint4*)(buf + 2 * kArr))[e];
+                uint32_t x[4] = {P.x, P.y, P.z, P.w};
+                float vx[4] = {VX.x, VX.y, VX.z, VX.w};
+                const uint32_t nv[4] = {NV.x, NV.y, NV.z, NV.w};
+                if (4 * g + 4 > n)                             // slots past n hold no atom
+#pragma unroll
+                    for (int u = 1; u < 4; ++u)
+                        if (4 * g + u >= n) x[u] = 0u;
+                if ((x[0] | x[1] | x[2] | x[3]) != 0u) {
+                    bool moved = false;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        if (x[u] == 0u) continue;
+                        uint32_t xm = 0u;
+                        const int el = tp_move(x[u], vx[u], d.tp_scale, &xm);
+                        if (el >= 0) {                          // sticks at an electrode
+                            tp_stick(d, B, 4 * g + u, el, vx[u]);
+                            x[u] = 0u;
+                            continue;
+                        }
+                        x[u] = xm;
+                        if (nv[u] == 0u || (int)(nv[u] - 1u - s) <= 0) {   // a candidate due, or no gap yet
+                            bool hit;
+                            vx[u] = tp_candidate<LAW>(d, B, 4 * g + u, s, vx[u], nv[u], &hit);
+                            if (hit) {
+                                moved = true;
+                                ++ncoll;
+                            }
+                        }
+                        if (sample) {
+                            uint32_t j, wr;
+                            cell_of(x[u], d.kshift, j, wr);
+                            atomicAdd(&A.cnt[j], 1u);
+                            atomicAdd(&A.whi[j], wr >> 16);
+                            atomicAdd(&A.wlo[j], wr & 0xffffu);
+                            const long long vq = (long long)__float2int_rn(vx[u]);
+                            const long long w16 = (long long)(wr >> 16);
+                            tp_add64(A, j, vq * (65536 - w16));
+                            tp_add64(A, j + 1, vq * w16);
+                        }
                     }
-                }
-                if (sample) {
-                    uint32_t j, wr;
-                    cell_of(x[u], d.kshift, j, wr);
-                    atomicAdd(&A.cnt[j], 1u);
-                    atomicAdd(&A.whi[j], wr >> 16);
-                    atomicAdd(&A.wlo[j], wr & 0xffffu);
-                    const long long vq = (long long)__float2int_rn(vx[u]);
-                    const long long w16 = (long long)(wr >> 16);
-                    tp_add64(A, j, vq * (65536 - w16));
-                    tp_add64(A, j + 1, vq * w16);
+                    ((uint4*)B.pos)[g] = make_uint4(x[0], x[1], x[2], x[3]);
+                    if (moved) ((float4*)B.vx)[g] = make_float4(vx[0], vx[1], vx[2], vx[3]);
                 }
             }
-            ((uint4*)B.pos)[g] = make_uint4(x[0], x[1], x[2], x[3]);
-            if (moved) ((float4*)B.vx)[g] = make_float4(vx[0], vx[1], vx[2], vx[3]);
+            __syncwarp();                                     // the stage is read: refill it
+            if (lane == 0 && t + S < nt) issue(a, b, t + S, q + (unsigned)S);
         }
-        if (sample) {                                      // this tile's tallies into the step's histograms
+        q0 += (unsigned)nt;
+        if (sample) {                                          // this span's tallies into the step's histograms
             __syncthreads();
             tp_flush(A, N, d.tp_q, d.tp_flux, threadIdx.x, blockDim.x);
             __syncthreads();
         }
     }
     ncoll = __reduce_add_sync(0xffffffffu, ncoll);
-    if ((threadIdx.x & 31) == 0 && ncoll) atomicAdd(&s_coll, ncoll);
+    if (lane == 0 && ncoll) atomicAdd(&s_coll, ncoll);
     __syncthreads();
     if (threadIdx.x == 0 && s_coll) atomicAdd(&ctl->cnt[kCntTpColl], (unsigned long long)s_coll);
     __threadfence();
@@ -840,9 +947,11 @@ static const void* tp_step_fn(const Dev& d)
                           : (d.tp_model ? (const void*)k_tp_step<true> : (const void*)k_tp_step<false>);
 }
 
+static size_t tp_step_smem(const Dev& d) { return d.tp_mode == 0 ? tp_geo_smem(d.ncell) : tp_smem(d.ncell); }
+
 cudaError_t tp_occupancy(const Dev& d, int* blocks_per_sm)
 {
-    const size_t sm = tp_smem(d.ncell);
+    const size_t sm = tp_step_smem(d);
     if (sm > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(tp_step_fn(d), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
@@ -852,7 +961,7 @@ cudaError_t tp_occupancy(const Dev& d, int* blocks_per_sm)
 
 cudaError_t launch_tp_step(const Dev& d, int grid, cudaStream_t st)
 {
-    const size_t sm = tp_smem(d.ncell);
+    const size_t sm = tp_step_smem(d);
     const void* fn = tp_step_fn(d);
     if (sm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

@@ -75,9 +75,16 @@ def _same(a, b, what):
             assert np.array_equal(a[sp][k], b[sp][k]), (what, sp, k)
 
 
-def test_batch_equals_alone(P):
+@pytest.mark.parametrize("per_cta,chunk", [(16_384, 131_072), (2_048, 8_192), (16_384, 0)],
+                         ids=["default", "chunks_of_4_slots", "one_cta_per_slot"])
+def test_batch_equals_alone(P, per_cta, chunk):
+    """Every member bit for bit equal to the discharge stepped alone, with the
+    resident CTAs taking chunks of slots (the default launch: here the
+    members' 2-5 slots are one-slot chunks; with 2048 particles per slot
+    they form chunks of 4 slots whose later slots reuse the field of the
+    first, and one-slot tail chunks) and with one CTA per slot."""
     steps = 120
-    b = P.Batch(particles_per_cta=16_384)          # 3, 2, 5 and 2 CTAs
+    b = P.Batch(particles_per_cta=per_cta, particles_per_chunk=chunk)
     slots = [b.add(P.params_from_workload(c)) for c in MEMBERS]
     assert slots == [0, 1, 2, 3]
     b.step(steps // 2)

@@ -112,7 +112,7 @@ def test_deposit_edge_sizes():
 
 # ------------------------------------------------------------------ field solve
 @pytest.mark.parametrize("ncell", [4, 128, 1024, 2048, 4096])
-def test_poisson_matches_oracle(ncell):
+def test_poisson_matches_oracle(ncell, record):
     """Exact double-prefix-sum solve on the GPU vs the oracle's Thomas sweep.
     Tolerance: the oracle's own forward error, which grows with the condition
     number of the 1D Laplacian (~ N^2): max(1e-12, N^2 eps / 100) of max
@@ -130,6 +130,8 @@ def test_poisson_matches_oracle(ncell):
                               dx, w, v_left)
         phi, E = phi.cpu().numpy(), E.cpu().numpy()
         phi_o, E_o = O.poisson(ncell, dx, w, q_i, q_e, v_left)
+        record(f"poisson.N{ncell}.V{v_left:g}.phi_max_rel", float(np.abs(phi - phi_o).max() / np.abs(phi_o).max()))
+        record(f"poisson.N{ncell}.V{v_left:g}.E_max_rel", float(np.abs(E - E_o).max() / np.abs(E_o).max()))
         assert np.abs(phi - phi_o).max() <= tol * np.abs(phi_o).max()
         assert np.abs(E - E_o).max() <= 100 * tol * np.abs(E_o).max()
 
@@ -152,7 +154,7 @@ def _smooth_field(ncell, scale, seed):
 
 
 @pytest.mark.parametrize("prec", [32, 64])
-def test_one_step_push_parity(prec):
+def test_one_step_push_parity(prec, record):
     """Gather + leapfrog + wall, collisions off (p = 0): every particle's
     v_x^{l+1/2} and displacement within 1e-5 relative of the oracle, v_y, v_z
     untouched, the same particles absorbed, and Sum q = 2^32 x alive."""
@@ -183,10 +185,12 @@ def test_one_step_push_parity(prec):
         # velocity error scale: |v_old| + |dv| (v^{l+1/2} may cancel to ~0)
         vscale = np.abs(vx0) + np.abs(o["vx"] - vx0)
         dvx = np.abs(g["vx"] - o["vx"])
+        record(f"push.u{prec}.species{s}.dvx_max_rel", float((dvx / (vscale + 1e-30)).max()))
         assert (dvx <= 1e-5 * vscale + 1e-3).all(), _worst(dvx / (vscale + 1e-30), o["id"])
         # displacement error: 1e-5 of the same scale times dt/dx, plus the position resolution
         tol = 1e-5 * vscale * dt / (cfg["gap_m"] / ncell) + (2 * unit if prec == 32 else 1e-9)
         dxi = np.abs(g["xi"] - o["xi"])
+        record(f"push.u{prec}.species{s}.dx_max_cells", float(dxi.max()))
         assert (dxi <= tol).all(), _worst(dxi / tol, o["id"])
         vy0 = dict(zip(sets[s]["id"].tolist(), sets[s]["vy"].tolist()))
         assert np.array_equal(g["vy"], np.array([vy0[i] for i in g["id"].tolist()], dtype=np.float32))
@@ -202,7 +206,7 @@ def test_one_step_push_parity(prec):
 
 # ------------------------------------------------------------------ one-step MCC
 @pytest.mark.parametrize("case", ["electrons", "ions"])
-def test_one_step_collision_parity(case):
+def test_one_step_collision_parity(case, record):
     """Null-collision MCC from identical Philox words: the same particles
     collide with the same process, post-collision velocities within FP32
     rounding, ionisation children with the same ids and states."""
@@ -242,6 +246,7 @@ def test_one_step_collision_parity(case):
         Eg = 0.5 * mass * (g["vx"].astype(np.float64)**2 + g["vy"]**2.0 + g["vz"]**2.0) / QE
         Eo = 0.5 * mass * (o["vx"]**2 + o["vy"]**2 + o["vz"]**2) / QE
         dE = np.abs(Eg - Eo)
+        record(f"collision.{case}.species{s}.dE_max_rel", float((dE / (E0 + Eo + 16.0)).max()))
         assert (dE <= 2e-6 * (E0 + Eo + 16.0)).all(), _worst(dE / (E0 + Eo + 16.0), o["id"])
         # directions
         vg = np.stack([g["vx"], g["vy"], g["vz"]]).astype(np.float64)
@@ -360,7 +365,7 @@ def test_bitwise_independent_of_order_and_sort_period():
 
 
 # ------------------------------------------------------------------ full size, bench launch shape
-def test_full_size_step_matches_oracle():
+def test_full_size_step_matches_oracle(record):
     """The sputtering discharge at its full size (2M e- + 2M Ar+, 1024 cells)
     in the benchmark's launch configuration: after one step every particle
     matches the oracle's within the one-step tolerances, charge is conserved
@@ -383,6 +388,8 @@ def test_full_size_step_matches_oracle():
         assert len(only_g) == 0 and len(only_o) == 0
         vmag = np.sqrt(o["vx"]**2 + o["vy"]**2 + o["vz"]**2)
         for comp in ("vx", "vy", "vz"):
+            record(f"full_size_step.species{mass == MAR:d}.{comp}_max_rel",
+                   float((np.abs(g[comp] - o[comp]) / (vmag + 1e-30)).max()))
             assert (np.abs(g[comp] - o[comp]) <= 2e-5 * vmag + 1e-2).all(), comp
         unit = cfg["n_cells"] / 2.0**32
         disp_tol = 2e-5 * vmag * cfg["dt"] / (cfg["gap_m"] / cfg["n_cells"]) + 2 * unit
@@ -390,6 +397,8 @@ def test_full_size_step_matches_oracle():
     f, fo = d.get_field(), orc.get_field()
     alive = [len(d.get_species(s)["id"]) for s in (0, 1)]
     assert int(f["q_e"].sum()) == 2**32 * alive[0] and int(f["q_i"].sum()) == 2**32 * alive[1]
+    record("full_size_step.E_max_rel", float(np.abs(f["E"] - fo["E"]).max() / np.abs(fo["E"]).max()))
+    record("full_size_step.deposit_equal", bool(np.array_equal(f["q_e"], fo["q_e"]) and np.array_equal(f["q_i"], fo["q_i"])))
     assert np.abs(f["E"] - fo["E"]).max() <= 1e-5 * np.abs(fo["E"]).max()
     d.close()
 

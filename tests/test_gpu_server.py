@@ -126,3 +126,23 @@ def test_plain_loop_checks_each_request_at_its_own_period(P):
     want = _alone(b, 2, period=2 * PERIOD)
     for k in ("n_e", "n_i", "phi"):
         assert np.array_equal(got[k], want[k]), k
+
+
+@pytest.mark.parametrize("batched", [1, 0], ids=["batched", "plain"])
+def test_request_of_another_period_waits_for_the_running_ones(P, batched):
+    """A request whose RF period (420 steps) is no multiple of the running
+    chunk (40 steps of a 400-step period) waits at the head of the queue,
+    runs once the first request has finished -- with a chunk of its own --
+    and gives the result of the discharge stepped alone."""
+    a = _cfg(4_000, 71)
+    b = _cfg(4_000, 72, dt=W.T_RF / 420)
+    s = P.Server(batched=batched, max_periods=2, tol=1e-12)
+    ra, rb = s.submit(P.params_from_workload(a)), s.submit(P.params_from_workload(b))
+    ia, ib = s.wait(ra, timeout=120.0), s.wait(rb, timeout=120.0)
+    got = {k: s.result(rb, k) for k in ("n_e", "n_i", "phi")}
+    s.close()
+    assert ia["state"] == ib["state"] == "max_periods" and ib["periods"] == 2
+    assert ib["t_admit"] >= ia["t_done"]
+    want = _alone(b, 2, period=420)
+    for k in ("n_e", "n_i", "phi"):
+        assert np.array_equal(got[k], want[k]), k
