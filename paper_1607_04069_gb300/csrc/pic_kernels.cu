@@ -786,6 +786,11 @@ __device__ __forceinline__ void mover_body(const Dev& d, const StepArgs& a, int 
                 for (int u = 0; u < 4; ++u) {
                     if (!(evm & (1u << u))) continue;
                     const long long i = 4 * g + u;
+                    // the event reads v_y, v_z and the id, which the stream does not
+                    // load: bring their lines to L2 now, well before it runs
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(B.vy + i));
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(B.vz + i));
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(B.id + i));
                     const unsigned int q = atomicAdd(&s_qn, 1u);
                     if (q < (unsigned)kQueueCap) {
                         squeue[q] = ((uint32_t)(i - chunk0) << 2) | kind[u];
