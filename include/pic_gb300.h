@@ -393,10 +393,12 @@ int pic_batch_set_target(pic_batch* b, int64_t particles_per_cta);
 /* How the launch runs those CTA slots.  particles_per_chunk > 0 (default
  * 131072): a grid of resident CTAs (a few per SM) takes chunks of
  * consecutive slots of one member from a work counter, paying the member's
- * deposit copy and field solve once per chunk instead of once per slot; the
- * last fifth of each member's slots form one-slot chunks at the end, so the
- * launch ends on short work.  0: one CTA per slot, scheduled by the
- * hardware.  The members' results are the same either way. */
+ * deposit copy and field solve once per chunk instead of once per slot; a
+ * chunk holds at most 1/(2R) of all slots (R resident CTAs), so a small
+ * batch still spreads over every SM, and the last fifth of each member's
+ * slots form one-slot chunks at the end, so the launch ends on short work.
+ * 0: one CTA per slot, scheduled by the hardware.  The members' results are
+ * the same either way. */
 int pic_batch_set_chunk(pic_batch* b, int64_t particles_per_chunk);
 
 /* Advance every member n_steps steps (one launch per step plus each

@@ -1340,23 +1340,25 @@ int batch_rebuild(pic_batch* b)
     b->grid = cta;
     // chunks of consecutive CTA slots of one member; the last fifth of each
     // member's slots go, one per chunk, to the end of the list, so the launch
-    // ends on short pieces of work
+    // ends on short pieces of work.  A chunk holds at most a 2R-th of all
+    // slots (R resident CTAs), so that a small batch -- a request loop holds
+    // a few discharges -- still spreads over the whole GPU
+    int dev = 0, sms = 1;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const long long resident = (long long)sms * std::max(per_sm, 1);
+    const long long per_cap = std::max(1ll, (long long)b->grid / (2 * resident));
     b->h_chunk.clear();
     std::vector<BatchChunk> tail;
     for (size_t k = 0; k < b->h_ent.size(); ++k) {
         const int ncta = b->h_ent[k].ncta;
-        const int per = (int)std::max(1ll, b->chunk / std::max(1ll, target));
+        const int per = (int)std::max(1ll, std::min(b->chunk / std::max(1ll, target), per_cap));
         const int head = per > 1 ? (ncta * 4 / 5) / per * per : ncta;
         for (int v = 0; v < head; v += per) b->h_chunk.push_back(BatchChunk{(int)k, v, std::min(head, v + per), 0});
         for (int v = head; v < ncta; ++v) tail.push_back(BatchChunk{(int)k, v, v + 1, 0});
     }
     b->h_chunk.insert(b->h_chunk.end(), tail.begin(), tail.end());
-    {
-        int dev = 0, sms = 1;
-        CK(cudaGetDevice(&dev));
-        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        b->grid_res = (int)std::min<long long>((long long)sms * std::max(per_sm, 1), (long long)b->h_chunk.size());
-    }
+    b->grid_res = (int)std::min<long long>(resident, (long long)b->h_chunk.size());
     if (b->h_chunk.size() > b->chunk_cap) {
         if (b->d_chunk) CK(cudaFree(b->d_chunk));
         b->d_chunk = nullptr;

@@ -221,11 +221,18 @@ __device__ __noinline__ void ev_ion_wall(const Dev& d, uint64_t id, uint32_t l, 
 }
 
 // split of the grid between the two species, proportional to their counts
+// CTAs for the electrons: their share of the particles, an electron weighted
+// 1.16 Ar+ (nearly all queued events are electron candidates, so an electron
+// CTA's event phase is longer; at this weight the median electron and Ar+
+// CTAs of the 2M + 2M sputtering discharge end together).  Results do not
+// depend on the division.
+constexpr float kElectronWeight = 1.16f;
 __device__ __forceinline__ int electron_ctas(long long ne, long long ni, int G)
 {
     if (ne <= 0) return 0;
     if (ni <= 0) return G;
-    int Ge = (int)((float)G * ((float)ne / (float)(ne + ni)) + 0.5f);
+    const float we = kElectronWeight * (float)ne;
+    int Ge = (int)((float)G * (we / (we + (float)ni)) + 0.5f);
     return Ge < 1 ? 1 : (Ge > G - 1 ? G - 1 : Ge);
 }
 
