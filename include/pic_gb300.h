@@ -173,6 +173,16 @@ int pic_sync(pic_ctx* ctx);
  * whole wall charge each step). */
 int pic_exchange_slot(pic_ctx* ctx, int64_t** dev, int64_t* n_words);
 
+/* Test of the bounded waits of the TP step (Sec. "Test Particle Method";
+ * tp_step): with enable != 0, from the next TP step on, warp 0 of the first
+ * CTA issues none of its bulk copies into shared memory, so its first wait
+ * on a tile's barrier runs out (after 4096 polls instead of 2^22) with no
+ * copy in flight.  The kernel sets its timeout bit, that warp's atoms do
+ * not move, the launch completes, and the next pic_sync returns
+ * PIC_ERR_TIMEOUT; the context stays usable.  enable = 0 restores the
+ * normal step.  Waits for the stream first.  Intended for tests only. */
+int pic_test_wait_timeout(pic_ctx* ctx, int enable);
+
 /* Diagnostics (Sec. "Simulation Results", Figs. 5-9), written to host memory:
  *  0 PHI      time-averaged potential, V, N+1 nodes
  *  1 NE 2 NI  time-averaged densities, m^-3, N+1 nodes

@@ -102,6 +102,7 @@ def lib():
             "pic_step": [vp, i64],
             "pic_sync": [vp],
             "pic_exchange_slot": [vp, C.POINTER(vp), pi64],
+            "pic_test_wait_timeout": [vp, C.c_int],
             "pic_diag": [vp, C.c_int, vp, i64, pi64],
             "pic_reset_averages": [vp],
             "pic_counters": [vp, vp, i64, pi64],
@@ -320,6 +321,11 @@ class Discharge:
         if ptr.value not in views:
             views[ptr.value] = _device_view(ptr.value, n.value, torch.int64)
         return views[ptr.value]
+
+    def test_wait_timeout(self, enable=True):
+        """Make the TP step's first bounded wait of one warp run out
+        (``pic_test_wait_timeout``; for tests)."""
+        _check(lib().pic_test_wait_timeout(self.h, int(bool(enable))))
 
     def tp_step(self, n=1, count_alive=True):
         a = C.c_int64()

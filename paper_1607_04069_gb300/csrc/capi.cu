@@ -273,6 +273,8 @@ void derive(pic_ctx* c)
     d.tpf_kt = (float)(256.0 * p.gap_m);
     d.tp_model = p.tp_model;
     d.tp_mode = p.tp_mode;
+    d.tp_wait_spin = 1u << 22;                 // polls: far beyond any copy's latency
+    d.tp_wait_test = 0;
     d.tp_ma = (float)(2.0 * std::sqrt(2.0 * kKB * p.gas_temp_k / kMAR) / std::sqrt(kPI));   // <|w|>
     double nK = 0.0;                                    // n K of the VHS / M1 law
     if (p.tp_model > 0) {
@@ -1113,6 +1115,17 @@ int tp_launch(pic_ctx* c, const tp_source* src)
     const float Emax = (float)(c->derived[7] * src->e_ion_ev);
     CK(launch_tp_launch(c->d, src->n, src->first_id >= 0 ? src->first_id : c->tp_launched, Emax, c->stream));
     c->tp_launched += src->n;
+    return PIC_OK;
+}
+
+int pic_test_wait_timeout(pic_ctx* c, int enable)
+{
+    if (!c) return fail(PIC_ERR_INVALID_ARG, "ctx is NULL");
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(c->stream));
+    c->d.tp_wait_test = enable ? 1 : 0;
+    c->d.tp_wait_spin = enable ? 4096u : (1u << 22);
+    sync_desc(c);
     return PIC_OK;
 }
 

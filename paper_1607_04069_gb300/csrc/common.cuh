@@ -192,6 +192,8 @@ struct Dev {                   // everything a kernel needs, passed by value
     int xs_n[3], xs_pad;
     float c2f;                       // A / (2 dx): E per unit of the integer bracket
     float tp_ma;                     // <|w|^alpha> of the gas (hard spheres: <|w|> = 2 c / sqrt(pi))
+    unsigned int tp_wait_spin;       // polls of a TP tile's barrier before the wait gives up
+    int tp_wait_test;                // 1: warp 0 of CTA 0 issues no copies, so its first wait runs out
     // push
     float qm_dt[2];                  // (q/m) dt
     float push32;                    // dt 2^32 / L  (fixed-point displacement per m/s)

@@ -447,7 +447,6 @@ __device__ __noinline__ void tp_stick(const Dev& d, const SpBuf& B, long long i,
 constexpr int kTpWarpTile = PG_TP_WARP_TILE;             // groups per warp tile
 constexpr int kTpLaneGroups = kTpWarpTile / 32;          // groups per lane and tile
 constexpr int kTpMaxStages = PG_TP_STAGES;
-constexpr unsigned kTpTmaSpin = 1u << 22;                // polls of a tile's barrier before giving up
 
 // stages per warp: half as many above 1024 cells, whose tallies take more shared memory
 __host__ __device__ __forceinline__ int tp_stages(int N)
@@ -515,6 +514,9 @@ __global__ void __launch_bounds__(kTpThreads, kTpMinBlocks) k_tp_step_geo(Dev d)
         bulk_g2s(buf + 2 * kArr, (const uint4*)B.nev + gs, bytes, bar);
     };
 
+    // the test of the bounded wait: one warp issues no copies, so its first
+    // wait runs out with nothing in flight (pic_test_wait_timeout)
+    const bool no_copies = d.tp_wait_test && blockIdx.x == 0 && wid == 0;
     unsigned int ncoll = 0;
     unsigned q0 = 0;                                        // tiles this warp consumed so far
     bool dead = false;                                      // a wait gave up: this warp skips the rest
@@ -523,20 +525,21 @@ __global__ void __launch_bounds__(kTpThreads, kTpMinBlocks) k_tp_step_geo(Dev d)
         const long long t1 = min(g1, t0 + span);
         const long long a = t0 + (t1 - t0) * wid / nw, b = t0 + (t1 - t0) * (wid + 1) / nw;
         const long long nt = dead ? 0 : (b - a + kTpWarpTile - 1) / kTpWarpTile;
-        if (lane == 0 && nt > 0) {
+        if (lane == 0 && nt > 0 && !no_copies) {
             async_proxy_fence();                            // the previous span's reads of the ring are done
             for (long long t = 0; t < min((long long)S, nt); ++t) issue(a, b, t, q0 + (unsigned)t);
         }
         __syncwarp();
         for (long long t = 0; t < nt; ++t) {
             const unsigned q = q0 + (unsigned)t;
-            const bool ok = mbar_wait(&bars[q % (unsigned)S], (q / (unsigned)S) & 1u, kTpTmaSpin);
+            const bool ok = mbar_wait(&bars[q % (unsigned)S], (q / (unsigned)S) & 1u, d.tp_wait_spin);
             if (__any_sync(0xffffffffu, !ok)) {             // let this warp's copies in flight land, then stop
                 if (lane == 0) {
                     atomicOr(&ctl->err, kErrTimeout);
-                    for (long long u = t; u < min(nt, t + S); ++u)
-                        mbar_wait(&bars[(q0 + (unsigned)u) % (unsigned)S], ((q0 + (unsigned)u) / (unsigned)S) & 1u,
-                                  kTpTmaSpin);
+                    if (!no_copies)                         // (tiles t .. t + S - 1 were issued)
+                        for (long long u = t; u < min(nt, t + S); ++u)
+                            mbar_wait(&bars[(q0 + (unsigned)u) % (unsigned)S],
+                                      ((q0 + (unsigned)u) / (unsigned)S) & 1u, d.tp_wait_spin);
                 }
                 __syncwarp();
                 dead = true;
@@ -597,7 +600,7 @@ __global__ void __launch_bounds__(kTpThreads, kTpMinBlocks) k_tp_step_geo(Dev d)
                 }
             }
             __syncwarp();                                     // the stage is read: refill it
-            if (lane == 0 && t + S < nt) issue(a, b, t + S, q + (unsigned)S);
+            if (lane == 0 && t + S < nt && !no_copies) issue(a, b, t + S, q + (unsigned)S);
         }
         q0 += (unsigned)nt;
         if (sample) {                                          // this span's tallies into the step's histograms

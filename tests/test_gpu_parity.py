@@ -488,6 +488,48 @@ def test_capacity_overflow_is_reported_and_state_stays_consistent():
     d.close()
 
 
+def test_tp_step_bounded_wait_runs_out_and_is_reported():
+    """The TP step's waits on its bulk copies are bounded.  One warp that
+    issues no copies waits until its limit runs out: the launch completes,
+    pic_sync reports PIC_ERR_TIMEOUT once, that warp's atoms stay where they
+    were, and the next steps, on the same context, move them again."""
+    import paper_1607_04069_gb300 as P
+    n = 1_000_000
+    tc = W.tp_transport(n_atoms=n)
+    tc.update(cap_tp=n + 1024, n_e0=0, n_i0=0, sort_every_tp=0, tp_mode=0)
+    d = P.Discharge(P.params_from_workload(tc))
+    d.tp_launch(n, 300.0)
+    d.tp_step(2, count_alive=False)
+    d.sync()
+
+    def positions():
+        sp = d.get_species(2)
+        order = np.argsort(sp["id"])
+        return sp["id"][order], sp["xi"][order]
+
+    id0, x0 = positions()
+    d.test_wait_timeout(True)
+    d.tp_step(1, count_alive=False)
+    with pytest.raises(P.PicError) as e:
+        d.sync()
+    assert e.value.code == -9
+    d.sync()                                   # reported once
+    d.test_wait_timeout(False)
+    id1, x1 = positions()
+    _, a, b = np.intersect1d(id0, id1, assume_unique=True, return_indices=True)
+    still = id1[b][x1[b] == x0[a]]
+    assert 0 < len(still) < n // 1000          # one warp's run of groups did not move
+    alive = d.tp_step(3)
+    d.sync()
+    id2, x2 = positions()
+    _, a, b = np.intersect1d(id1, id2, assume_unique=True, return_indices=True)
+    moved = x2[b] != x1[a]
+    assert moved[np.isin(id1[a], still)].all()
+    c = d.counters()
+    assert c["tp_dep_l"] + c["tp_dep_r"] + alive == n
+    d.close()
+
+
 def test_atoms_in_flight_counts_coupled_births():
     """tp_step's count of atoms in flight includes the atoms that ion impacts
     sputtered inside the step launch (counted per CTA there): it equals the
