@@ -1142,7 +1142,7 @@ void orc_tp_step(orc_state *S, int64_t nsteps, double dt_tp)
                 double sig = gm0 > 0.0 ? orc_tp_sigma(S, gm0) : 0.0;
                 double P = 1.0 - exp(-S->ngas * sig * gm0 * dt_tp);
                 draw(S->P.seed, p->id[k], s, PUR_TP_COLL, cc0);
-                hit = u23(cc0[0]) < P;
+                hit = (float)u23(cc0[0]) < (float)P;               /* in FP32 */
             }
             if (hit) {
                 uint32_t cc[4];
@@ -1230,7 +1230,7 @@ int orc_tpf_partner(uint64_t seed, uint64_t id, uint32_t e, double Tg, const dou
         uint32_t a[4], b[4];
         draw(seed, id, e, PUR_TPF_PARTNER + 2 * t, a);
         draw(seed, id, e, PUR_TPF_PARTNER + 2 * t + 1, b);
-        if (u23(a[0]) * (vm + mw) < vm) {
+        if ((float)u23(a[0]) * ((float)vm + (float)mw) < (float)vm) {   /* in FP32 */
             double n1, n2, n3, n4;
             box_muller(a[1], a[2], &n1, &n2);
             box_muller(a[3], b[0], &n3, &n4);
@@ -1244,7 +1244,7 @@ int orc_tpf_partner(uint64_t seed, uint64_t id, uint32_t e, double Tg, const dou
         double g[3] = {v[0] - w[0], v[1] - w[1], v[2] - w[2]};
         double gm = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
         double wm = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
-        if (u23(b[1]) * (vm + wm) < gm) return t + 1;
+        if ((float)u23(b[1]) * ((float)vm + (float)wm) < (float)gm) return t + 1;   /* in FP32 */
     }
     return TPF_TRIES + 1;
 }
@@ -1263,7 +1263,7 @@ static double gamma_mt(double k, uint64_t seed, uint64_t id, uint32_t e, uint32_
         double v = 1.0 + cc * x;
         if (v <= 0.0) continue;
         v = v * v * v;
-        if (log(u23(r[2])) < 0.5 * x * x + d - d * v + d * log(v)) return d * v;
+        if ((float)log(u23(r[2])) < (float)(0.5 * x * x + d - d * v + d * log(v))) return d * v;   /* in FP32 */
     }
     return d;
 }
@@ -1354,7 +1354,7 @@ int64_t orc_tp_flight(orc_state *S, int64_t max_events)
                 uint32_t a[4], b[4];
                 draw(S->P.seed, p->id[k], e, PUR_TPF_CAND, a);
                 draw(S->P.seed, p->id[k], e, PUR_TPF_CAND + 1, b);
-                if (u23(a[0]) * (va + ma) < va) {
+                if ((float)u23(a[0]) * ((float)va + (float)ma) < (float)va) {   /* in FP32 */
                     double vg = c / sqrt(2.0), n1, n2, n3, n4;
                     box_muller(a[1], a[2], &n1, &n2);
                     box_muller(a[3], b[0], &n3, &n4);
@@ -1368,7 +1368,7 @@ int64_t orc_tp_flight(orc_state *S, int64_t max_events)
                 double gg[3] = {v[0] - w[0], v[1] - w[1], v[2] - w[2]};
                 double gmm = sqrt(gg[0] * gg[0] + gg[1] * gg[1] + gg[2] * gg[2]);
                 double wm = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
-                if (!(u23(b[1]) * (va + pow(wm, alpha)) < pow(gmm, alpha))) {
+                if (!((float)u23(b[1]) * ((float)va + (float)pow(wm, alpha)) < (float)pow(gmm, alpha))) {   /* FP32 */
                     p->nev[k] = e + 1u;                   /* a null event: the flight goes on */
                     continue;
                 }
