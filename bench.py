@@ -602,6 +602,9 @@ def main():
     ap.add_argument("--serve-max-periods", type=int, default=20)
     ap.add_argument("--serve-criterion", default="inventory", choices=["inventory", "profile"])
     ap.add_argument("--serve-window", type=int, default=1)
+    ap.add_argument("--settle-periods", type=int, default=10,
+                    help="after the other measurements, step the discharge to this many RF periods and time "
+                         "600 more steps the same way (0: skip)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_setup()
@@ -748,6 +751,24 @@ def main():
         if args.serve_requests > 0 and (want is None or "c_served" in want):
             rows["c_served"] = measure_served(args.serve_requests, args.serve_rate, args.serve_max_periods,
                                               criterion=args.serve_criterion, window=args.serve_window)
+    # the same discharge at steady operation: stepped on to settle_periods RF periods
+    # from its loading, then 600 steps timed as above (its particle count has decayed
+    # from the 2M + 2M of the loading)
+    settled = None
+    done = args.warmup + args.steps + 400 + 400
+    target = args.settle_periods * cfg["steps_per_period"]
+    if args.settle_periods > 0 and target > done:
+        d.step(target - done)
+        sd.sync()
+        n_s0 = sd.alive() // ws
+        st_ms = allreduce_max(sum(timed_steps(d, stream, 600, flush, clean)), ws)
+        sd.sync()
+        n_s1 = sd.alive() // ws
+        settled = {"periods_before": args.settle_periods, "ms_per_step": st_ms / 600,
+                   "value": allreduce_sum(0.5 * (n_s0 + n_s1) * 600, ws) / (st_ms * 1e-3),
+                   "particles_per_gpu": int(0.5 * (n_s0 + n_s1)),
+                   "note": "600 steps timed as the headline after the discharge ran this many RF periods "
+                           "from its loading"}
     if rank == 0:
         line = {"metric": "particle-steps/s", "value": value, "unit": "particle-steps/s", "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
@@ -759,6 +780,7 @@ def main():
                 "schedule_400": {"ms_per_step": sched_ms / 400, "value": sched_value,
                                  "note": "400 further steps timed the same way: one compaction of each "
                                          "species and ten coupled test-particle steps fall inside"},
+                "settled": settled,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": int(launches), "rows": rows,
                 "kernel_us": {"step_alone_mean": mover_ms / max(mover_n, 1) * 1e3, "steps_alone": mover_n,
