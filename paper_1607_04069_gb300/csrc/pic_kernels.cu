@@ -1105,13 +1105,15 @@ __global__ void k_sort_scan(Dev d)
     if (t == 0) d.ctl->sort_total = tot;
 }
 
-// Scatter: each CTA takes a contiguous run of slots, counts its particles per
-// cell in shared memory, reserves one sub-range per touched cell of the
-// cell's global range (one global atomic per cell and CTA instead of one per
-// warp and cell), and hands out slots of those sub-ranges with shared-memory
-// atomics.  Order inside a cell is unspecified.
+// Scatter straight from registers (the Ar+, which stay cell-ordered between
+// compactions, so a warp's particles fall in one or two cells and its stores
+// are already runs): each CTA takes a contiguous run of slots, counts its
+// particles per cell in shared memory, reserves one sub-range per touched
+// cell of the cell's global range (one global atomic per cell and CTA
+// instead of one per warp and cell), and hands out slots of those sub-ranges
+// with shared-memory atomics.  Order inside a cell is unspecified.
 template <typename PosT>
-__global__ void k_sort_scatter(Dev d, int s)
+__global__ void k_sort_scatter_direct(Dev d, int s)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned int* cur_slot = (unsigned int*)smem_raw;          // [ncell]: count, then next slot
@@ -1181,6 +1183,182 @@ __global__ void k_sort_scatter(Dev d, int s)
             }
             __syncthreads();
         }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&d.ctl->sort_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        d.ctl->n[s] = d.ctl->sort_total;
+        d.ctl->cur[s] = cur ^ 1u;
+        d.ctl->sort_done = 0;
+    }
+}
+
+// Staged scatter (electrons and test particles, whose cell order is gone a
+// few steps after a compaction): each CTA takes a contiguous run of slots,
+// counts its particles per cell in shared memory, and reserves one sub-range
+// per touched cell of the cell's global range (one global atomic per cell and
+// CTA).  It then moves
+// its run in chunks of kSortChunk particles: a counting sort of the chunk by
+// cell in shared memory, then each cell's part of the chunk written as one
+// contiguous run of its sub-range.  Scattering every particle straight from
+// registers made one L2 write request per particle and array for cell-mixed
+// input (electrons), which bounded the kernel; runs of several particles
+// per cell share requests and fill whole sectors.  Order inside a cell is
+// unspecified.
+constexpr int kSortThreads = 1024;
+#ifndef PG_SORT_PER
+#define PG_SORT_PER 4
+#endif
+constexpr int kSortPer = PG_SORT_PER;                         // particles per thread and chunk
+constexpr int kSortChunk = kSortThreads * kSortPer;
+// shared memory at the largest case, 4096 cells and 64-bit positions, within the 227 KB a CTA may have
+static_assert(4096 * 12 + (size_t)kSortChunk * (8 + 8 + 4 * 5) <= 227 * 1024, "staged sort chunk too large");
+template <typename PosT>
+size_t sort_scatter_smem_t(int ncell)
+{
+    return (size_t)ncell * 12 + (size_t)kSortChunk * (sizeof(PosT) + 8 + 4 * 5);
+}
+size_t sort_scatter_smem(int ncell, bool p64)
+{
+    return p64 ? sort_scatter_smem_t<double>(ncell) : sort_scatter_smem_t<uint32_t>(ncell);
+}
+
+template <typename PosT>
+__global__ void __launch_bounds__(kSortThreads) k_sort_scatter_staged(Dev d, int s)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = d.ncell;
+    // [cur_slot u32 N][hc u32 N][ho u32 N][x PosT C][id u64 C][vx vy vz nev cell u32 C]
+    unsigned int* cur_slot = (unsigned int*)smem_raw;        // this CTA's next slot of each cell
+    unsigned int* hc = cur_slot + N;                          // the chunk's count per cell
+    unsigned int* ho = hc + N;                                // the chunk's first staged entry per cell
+    unsigned char* stg = smem_raw + (((size_t)N * 12 + 15) & ~(size_t)15);
+    PosT* sx = (PosT*)stg;
+    uint64_t* sid = (uint64_t*)(stg + (size_t)kSortChunk * sizeof(PosT));
+    float* svx = (float*)(sid + kSortChunk);
+    float* svy = svx + kSortChunk;
+    float* svz = svy + kSortChunk;
+    uint32_t* snev = (uint32_t*)(svz + kSortChunk);
+    uint32_t* scell = snev + kSortChunk;
+    __shared__ int s_last;
+    __shared__ long long sh_scan[32];
+
+    const long long n = d.ctl->n[s];
+    const unsigned int cur = d.ctl->cur[s];
+    const SpBuf A = d.buf[s][cur], Bn = d.buf[s][cur ^ 1u];
+    const PosT* PA = (const PosT*)A.pos;
+    PosT* PB = (PosT*)Bn.pos;
+    const int lane = threadIdx.x & 31, T = blockDim.x;
+    const long long i0 = n * blockIdx.x / gridDim.x, i1 = n * (blockIdx.x + 1) / gridDim.x;
+    for (int m = threadIdx.x; m < N; m += T) {
+        cur_slot[m] = 0;
+        hc[m] = 0;
+    }
+    __syncthreads();
+
+    // cell of slot i, or 0xffffffff for a removed slot
+    auto cell_at = [&](PosT x) -> uint32_t {
+        if (!is_alive(x)) return 0xffffffffu;
+        uint32_t j, wr;
+        cell_of(x, d.kshift, j, wr);
+        return j < (uint32_t)N ? j : 0xffffffffu;
+    };
+    // lanes of one cell share one shared-memory atomic (cell-ordered input would
+    // otherwise serialise on a single counter); returns the lane's rank
+    auto add_count = [&](unsigned int* cnt, uint32_t j) -> unsigned int {
+        const unsigned grp = __match_any_sync(0xffffffffu, j);
+        const int leader = __ffs(grp) - 1;
+        const unsigned int rank = __popc(grp & ((1u << lane) - 1u));
+        unsigned int base = 0;
+        if (j != 0xffffffffu && lane == leader) base = atomicAdd(&cnt[j], (unsigned)__popc(grp));
+        return __shfl_sync(0xffffffffu, base, leader) + rank;
+    };
+
+    // 1. this CTA's particles per cell, then one sub-range of every touched cell
+    const long long i1r = i0 + (i1 - i0 + T - 1) / T * T;     // whole warps: collectives above
+    for (long long i = i0 + threadIdx.x; i < i1r; i += T) {
+        const uint32_t j = i < i1 ? cell_at(PA[i]) : 0xffffffffu;
+        add_count(cur_slot, j);
+    }
+    __syncthreads();
+    for (int m = threadIdx.x; m < N; m += T) {
+        const unsigned int c = cur_slot[m];
+        if (c) cur_slot[m] = atomicAdd(&d.sort_off[m], c);
+    }
+    __syncthreads();
+
+    // 2. the run in chunks: count by cell, stage in cell order, write each cell's part as one run
+    const int seg = (N + T - 1) / T;                          // cells per thread in the scan
+    const int m0 = min((int)threadIdx.x * seg, N), m1 = min(m0 + seg, N);
+    for (long long c0 = i0; c0 < i1; c0 += kSortChunk) {
+        PosT x[kSortPer];
+        float fx[kSortPer], fy[kSortPer], fz[kSortPer];
+        uint64_t fid[kSortPer];
+        uint32_t fnev[kSortPer], jj[kSortPer], rk[kSortPer];
+#pragma unroll
+        for (int k = 0; k < kSortPer; ++k) {                  // all loads in flight together
+            const long long i = c0 + threadIdx.x + (long long)k * T;
+            x[k] = 0;
+            fx[k] = fy[k] = fz[k] = 0.0f;
+            fid[k] = 0;
+            fnev[k] = 0;
+            if (i < i1) {
+                x[k] = PA[i];
+                fx[k] = A.vx[i];
+                fy[k] = A.vy[i];
+                fz[k] = A.vz[i];
+                fid[k] = A.id[i];
+                fnev[k] = A.nev[i];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kSortPer; ++k) {
+            const long long i = c0 + threadIdx.x + (long long)k * T;
+            jj[k] = i < i1 ? cell_at(x[k]) : 0xffffffffu;
+            rk[k] = add_count(hc, jj[k]);
+        }
+        __syncthreads();
+        long long a = 0;
+        for (int m = m0; m < m1; ++m) a += hc[m];
+        long long tot_l;
+        long long off = block_exclusive_scan(a, sh_scan, tot_l);
+        const unsigned int tot = (unsigned int)tot_l;
+        for (int m = m0; m < m1; ++m) {
+            ho[m] = (unsigned int)off;
+            off += hc[m];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kSortPer; ++k) {
+            if (jj[k] == 0xffffffffu) continue;
+            const unsigned int p = ho[jj[k]] + rk[k];
+            sx[p] = x[k];
+            sid[p] = fid[k];
+            svx[p] = fx[k];
+            svy[p] = fy[k];
+            svz[p] = fz[k];
+            snev[p] = fnev[k];
+            scell[p] = jj[k];
+        }
+        __syncthreads();
+        for (unsigned int p = threadIdx.x; p < tot; p += T) {
+            const uint32_t j = scell[p];
+            const unsigned int o = cur_slot[j] + (p - ho[j]);
+            PB[o] = sx[p];
+            Bn.vx[o] = svx[p];
+            Bn.vy[o] = svy[p];
+            Bn.vz[o] = svz[p];
+            Bn.id[o] = sid[p];
+            Bn.nev[o] = snev[p];
+        }
+        __syncthreads();
+        for (int m = threadIdx.x; m < N; m += T) {
+            cur_slot[m] += hc[m];
+            hc[m] = 0;
+        }
+        __syncthreads();
     }
     __threadfence();
     __syncthreads();
@@ -1304,8 +1482,22 @@ cudaError_t launch_sort(const Dev& d, int s, int grid, cudaStream_t st)
     if (p64) k_sort_count<double><<<gs, 1024, sm, st>>>(d, s);
     else k_sort_count<uint32_t><<<gs, 1024, sm, st>>>(d, s);
     k_sort_scan<<<1, 1024, 0, st>>>(d);
-    if (p64) k_sort_scatter<double><<<gs, 1024, sm, st>>>(d, s);
-    else k_sort_scatter<uint32_t><<<gs, 1024, sm, st>>>(d, s);
+    if (s == kI) {                                  // cell-ordered: stores are runs already
+        if (p64) k_sort_scatter_direct<double><<<gs, 1024, sm, st>>>(d, s);
+        else k_sort_scatter_direct<uint32_t><<<gs, 1024, sm, st>>>(d, s);
+        return cudaGetLastError();
+    }
+    // cell-mixed: the staged scatter on its resident CTAs (one or two per SM, by its shared memory)
+    const size_t ss = sort_scatter_smem(d.ncell, p64);
+    const void* fn = p64 ? (const void*)k_sort_scatter_staged<double> : (const void*)k_sort_scatter_staged<uint32_t>;
+    cudaError_t e = set_smem_attr(fn, ss);
+    if (e != cudaSuccess) return e;
+    int per_sm = 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kSortThreads, ss);
+    if (e != cudaSuccess) return e;
+    const int gsc = std::max(1, (grid >= 8 ? grid / 8 : 1) * std::max(per_sm, 1));
+    if (p64) k_sort_scatter_staged<double><<<gsc, kSortThreads, ss, st>>>(d, s);
+    else k_sort_scatter_staged<uint32_t><<<gsc, kSortThreads, ss, st>>>(d, s);
     return cudaGetLastError();
 }
 
