@@ -59,7 +59,7 @@ struct pic_ctx {
     Dev d_coupled;                   // same, with the coupled TP time step
     void* arena = nullptr;
     size_t arena_bytes = 0, small_bytes = 0;
-    int sms = 0, grid_mover = 0, grid_tp = 0, grid_sort = 0;
+    int sms = 0, grid_mover = 0, grid_tp = 0, grid_tp_sample = 0, grid_sort = 0;
     long long h_step = 0, h_tp_step = 0, tp_launched = 0;
     float tp_gap_scale = 0.0f;       // TP step length (as Dev::tp_scale) the kept candidate gaps belong to
     long long exch_stride = 0;       // words per array of a rotating deposit slot
@@ -423,7 +423,9 @@ int run_tp_step(pic_ctx* c, const Dev& d)
                                c->stream));
         c->tp_gap_scale = d.tp_scale;
     }
-    CK(launch_tp_step(d, c->grid_tp, c->stream));
+    // the device's TP step counter (ctl->tp_step) advances with every launch, as h_tp_step does
+    const bool sample = d.diag_every > 0 && (c->h_tp_step + 1) % d.diag_every == 0;
+    CK(launch_tp_step(d, sample ? c->grid_tp_sample : c->grid_tp, sample, c->stream));
     rc = timer_end(c, stop);
     if (rc) return rc;
     c->h_tp_step++;
@@ -544,9 +546,13 @@ int pic_create(const pic_params* pin, void* stream, pic_ctx** out)
     c->grid_mover = c->sms * per_sm;
     if (c->grid_mover > kMaxTallyRows) c->grid_mover = kMaxTallyRows - kMaxTallyRows % c->sms;
     {                                  // the TP step: a multiple of the SMs by its occupancy
-        int tp_per_sm = 0;
-        if (tp_occupancy(c->d, &tp_per_sm) != cudaSuccess || tp_per_sm < 1) tp_per_sm = 2;
-        c->grid_tp = c->sms * tp_per_sm;
+        int tp_per_sm = 0, tp_per_sm_sample = 0;
+        if (tp_occupancy(c->d, false, &tp_per_sm) != cudaSuccess || tp_per_sm < 1) tp_per_sm = 2;
+        if (tp_occupancy(c->d, true, &tp_per_sm_sample) != cudaSuccess || tp_per_sm_sample < 1) tp_per_sm_sample = 2;
+        // a launch without the tallies holds at least as many CTAs per SM as one with
+        // them (the occupancy query can answer less, for the carveout it assumes)
+        c->grid_tp = c->sms * std::max(tp_per_sm, tp_per_sm_sample);
+        c->grid_tp_sample = c->sms * tp_per_sm_sample;
     }
     c->grid_sort = c->sms * 8;
 

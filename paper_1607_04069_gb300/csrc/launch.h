@@ -46,9 +46,12 @@ cudaError_t launch_field(const Dev& d, double v_left, int accumulate, cudaStream
 // first null-collision candidate step of n uploaded particles that are first pushed at step l0
 cudaError_t launch_entry_nev(const Dev& d, int s, unsigned int half, long long n, unsigned int l0, cudaStream_t st);
 cudaError_t launch_sort(const Dev& d, int s, int grid, cudaStream_t st);
-cudaError_t launch_tp_step(const Dev& d, int grid, cudaStream_t st);
-// resident CTAs per SM of the TP step kernel of d's collision mode and law
-cudaError_t tp_occupancy(const Dev& d, int* blocks_per_sm);
+// one TP step; sample: the step adds to the time averages (thinned-candidate
+// mode: only then does the launch carry the tallies in shared memory)
+cudaError_t launch_tp_step(const Dev& d, int grid, bool sample, cudaStream_t st);
+// resident CTAs per SM of the TP step kernel of d's collision mode and law,
+// for a sample step or another
+cudaError_t tp_occupancy(const Dev& d, bool sample, int* blocks_per_sm);
 // event-driven flight: every live TP atom through at most kmax events; the
 // atoms still alive are added to Ctl::tpf_alive
 cudaError_t launch_tp_flight(const Dev& d, int kmax, long long n, cudaStream_t st);

@@ -50,6 +50,25 @@ __device__ void tp_flush(const TpAcc& A, int N, unsigned long long* q, long long
     }
 }
 
+// A run of consecutive atoms of one lane in cell j, summed as the shared
+// tallies are (per-lane sums stay below the tallies' 65536-atom span bound).
+constexpr uint32_t kTpNoRun = 0xffffffffu;
+struct TpRun {
+    uint32_t j, cnt = 0, whi = 0, wlo = 0;
+    long long f0 = 0, f1 = 0;    // flux moment at nodes j and j+1
+};
+__device__ __forceinline__ void tp_run_flush(const TpAcc& A, TpRun& r)
+{
+    if (r.j == kTpNoRun) return;
+    atomicAdd(&A.cnt[r.j], r.cnt);
+    atomicAdd(&A.whi[r.j], r.whi);
+    atomicAdd(&A.wlo[r.j], r.wlo);
+    if (r.f0) tp_add64(A, (int)r.j, r.f0);
+    if (r.f1) tp_add64(A, (int)r.j + 1, r.f1);
+    r.cnt = r.whi = r.wlo = 0;
+    r.f0 = r.f1 = 0;
+}
+
 struct TpGrp {                 // one group of four atoms, as loaded
     uint4 P;
     float4 VX, VY, VZ;
@@ -460,18 +479,28 @@ __host__ __device__ __forceinline__ size_t tp_tally_bytes128(int N)
 {
     return (((size_t)N * 12 + (size_t)(N + 1) * 8) + 127) & ~(size_t)127;
 }
-size_t tp_geo_smem(int N)
+// the warps' rings alone (steps that take no samples), and with the tallies after them
+__host__ __device__ __forceinline__ size_t tp_ring_smem(int N)
 {
-    return tp_tally_bytes128(N) + (size_t)(kTpThreads / 32) * tp_stages(N) * 3 * kTpWarpTile * 16;
+    return (size_t)(kTpThreads / 32) * tp_stages(N) * 3 * kTpWarpTile * 16;
 }
+size_t tp_geo_smem(int N) { return tp_ring_smem(N) + tp_tally_bytes128(N); }
 
-template <bool LAW>
+// SAMPLE: this step adds to the time averages.  The host picks the
+// instantiation from its own count of TP steps, which the last CTA's increment
+// of ctl->tp_step mirrors; only a sample launch carries the tallies in its
+// shared memory (the others hold the rings alone and leave the L1 part of the
+// SM's on-chip memory larger).  A sample launch sums each lane's consecutive
+// atoms of one cell in registers and adds the run to the shared tallies when
+// the cell changes: sputtered atoms crowd into a few cells near the electrodes,
+// where per-atom shared atomics on one address serialise.
+template <bool LAW, bool SAMPLE>
 __global__ void __launch_bounds__(kTpThreads, kTpMinBlocks) k_tp_step_geo(Dev d)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = d.ncell;
-    TpAcc A;
-    A.cnt = (unsigned int*)smem_raw;
+    TpAcc A;                                                 // after the rings (sample launches only)
+    A.cnt = (unsigned int*)(smem_raw + tp_ring_smem(N));
     A.whi = A.cnt + N;
     A.wlo = A.whi + N;
     A.flo = A.wlo + N;
@@ -483,14 +512,14 @@ __global__ void __launch_bounds__(kTpThreads, kTpMinBlocks) k_tp_step_geo(Dev d)
     Ctl* ctl = d.ctl;
     const unsigned int s = ctl->tp_step;
     const long long n = ctl->n[kTP];
-    const bool sample = d.diag_every > 0 && ((s + 1) % (unsigned)d.diag_every == 0);
+    constexpr bool sample = SAMPLE;
     const long long G4 = (n + 3) >> 2;
     const long long g0 = G4 * blockIdx.x / gridDim.x, g1 = G4 * (blockIdx.x + 1) / gridDim.x;
     const SpBuf B = d.buf[kTP][ctl->cur[kTP]];
     const int S = tp_stages(N);
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr unsigned kArr = kTpWarpTile * 16u;                // bytes per array of a tile
-    unsigned char* ring = smem_raw + tp_tally_bytes128(N) + (size_t)wid * S * 3 * kArr;   // 16-byte aligned
+    unsigned char* ring = smem_raw + (size_t)wid * S * 3 * kArr;   // 16-byte aligned
     uint64_t* bars = s_bar[wid];
     if (sample)
         for (int m = threadIdx.x; m <= N; m += blockDim.x) {
@@ -524,6 +553,8 @@ __global__ void __launch_bounds__(kTpThreads, kTpMinBlocks) k_tp_step_geo(Dev d)
     // wait runs out with nothing in flight (pic_test_wait_timeout)
     const bool no_copies = d.tp_wait_test && blockIdx.x == 0 && wid == 0;
     unsigned int ncoll = 0;
+    TpRun run;                                              // this lane's pending run of one cell
+    run.j = kTpNoRun;
     unsigned int phase[kTpMaxStages];                       // waits completed on each stage's barrier
 #pragma unroll
     for (int st = 0; st < kTpMaxStages; ++st) phase[st] = 0;
@@ -613,13 +644,17 @@ __global__ void __launch_bounds__(kTpThreads, kTpMinBlocks) k_tp_step_geo(Dev d)
                         if (sample) {
                             uint32_t j, wr;
                             cell_of(x[u], d.kshift, j, wr);
-                            atomicAdd(&A.cnt[j], 1u);
-                            atomicAdd(&A.whi[j], wr >> 16);
-                            atomicAdd(&A.wlo[j], wr & 0xffffu);
+                            if (j != run.j) {
+                                tp_run_flush(A, run);
+                                run.j = j;
+                            }
                             const long long vq = (long long)__float2int_rn(vx[u]);
                             const long long w16 = (long long)(wr >> 16);
-                            tp_add64(A, j, vq * (65536 - w16));
-                            tp_add64(A, j + 1, vq * w16);
+                            run.cnt += 1u;
+                            run.whi += wr >> 16;
+                            run.wlo += wr & 0xffffu;
+                            run.f0 += vq * (65536 - w16);
+                            run.f1 += vq * w16;
                         }
                     }
                     ((uint4*)B.pos)[g] = make_uint4(x[0], x[1], x[2], x[3]);
@@ -630,6 +665,8 @@ __global__ void __launch_bounds__(kTpThreads, kTpMinBlocks) k_tp_step_geo(Dev d)
             tile[st] = claim(st);
         }
         if (sample) {                                          // this span's tallies into the step's histograms
+            tp_run_flush(A, run);
+            run.j = kTpNoRun;
             __syncthreads();
             tp_flush(A, N, d.tp_q, d.tp_flux, threadIdx.x, blockDim.x);
             if (threadIdx.x == 0) s_tile = 0;
@@ -971,35 +1008,44 @@ cudaError_t launch_tp_flight(const Dev& d, int kmax, long long n, cudaStream_t s
     return cudaGetLastError();
 }
 
-static const void* tp_step_fn(const Dev& d)
+static const void* tp_step_fn(const Dev& d, bool sample)
 {
-    return d.tp_mode == 0 ? (d.tp_model ? (const void*)k_tp_step_geo<true> : (const void*)k_tp_step_geo<false>)
-                          : (d.tp_model ? (const void*)k_tp_step<true> : (const void*)k_tp_step<false>);
+    if (d.tp_mode != 0) return d.tp_model ? (const void*)k_tp_step<true> : (const void*)k_tp_step<false>;
+    if (sample) return d.tp_model ? (const void*)k_tp_step_geo<true, true> : (const void*)k_tp_step_geo<false, true>;
+    return d.tp_model ? (const void*)k_tp_step_geo<true, false> : (const void*)k_tp_step_geo<false, false>;
 }
 
-static size_t tp_step_smem(const Dev& d) { return d.tp_mode == 0 ? tp_geo_smem(d.ncell) : tp_smem(d.ncell); }
-
-cudaError_t tp_occupancy(const Dev& d, int* blocks_per_sm)
+static size_t tp_step_smem(const Dev& d, bool sample)
 {
-    const size_t sm = tp_step_smem(d);
-    if (sm > 48 * 1024) {
-        const cudaError_t e = cudaFuncSetAttribute(tp_step_fn(d), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    return d.tp_mode == 0 ? (sample ? tp_geo_smem(d.ncell) : tp_ring_smem(d.ncell)) : tp_smem(d.ncell);
+}
+
+cudaError_t tp_occupancy(const Dev& d, bool sample, int* blocks_per_sm)
+{
+    const size_t sm = tp_step_smem(d, sample);
+    if (sm > 40 * 1024) {                  // (with the static shared memory, 48 KB of rings pass the default limit)
+        const cudaError_t e = cudaFuncSetAttribute(tp_step_fn(d, sample), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
     }
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, tp_step_fn(d), kTpThreads, sm);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, tp_step_fn(d, sample), kTpThreads, sm);
 }
 
-cudaError_t launch_tp_step(const Dev& d, int grid, cudaStream_t st)
+cudaError_t launch_tp_step(const Dev& d, int grid, bool sample, cudaStream_t st)
 {
-    const size_t sm = tp_step_smem(d);
-    const void* fn = tp_step_fn(d);
-    if (sm > 48 * 1024) {
+    const size_t sm = tp_step_smem(d, sample);
+    const void* fn = tp_step_fn(d, sample);
+    if (sm > 40 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
     }
     if (d.tp_mode == 0) {
-        if (d.tp_model) k_tp_step_geo<true><<<grid, kTpThreads, sm, st>>>(d);
-        else k_tp_step_geo<false><<<grid, kTpThreads, sm, st>>>(d);
+        if (sample) {
+            if (d.tp_model) k_tp_step_geo<true, true><<<grid, kTpThreads, sm, st>>>(d);
+            else k_tp_step_geo<false, true><<<grid, kTpThreads, sm, st>>>(d);
+        } else {
+            if (d.tp_model) k_tp_step_geo<true, false><<<grid, kTpThreads, sm, st>>>(d);
+            else k_tp_step_geo<false, false><<<grid, kTpThreads, sm, st>>>(d);
+        }
     } else {
         if (d.tp_model) k_tp_step<true><<<grid, kTpThreads, sm, st>>>(d);
         else k_tp_step<false><<<grid, kTpThreads, sm, st>>>(d);
