@@ -453,9 +453,9 @@ __device__ __noinline__ void tp_stick(const Dev& d, const SpBuf& B, long long i,
 // claim one at a time from a shared counter (a warp slowed by a rare
 // candidate takes fewer), and lane 0 keeps the next tile's x, v_x and
 // candidate-step arrays (3 x 1 KB per tile) in flight in a ring of two
-// stages, each with its own mbarrier (100M atoms: 345 us per step, against
-// 416 us with 32-group tiles in four stages and 364 us with one group per
-// thread loaded ahead into registers).  Warps do not wait for one another,
+// stages, each with its own mbarrier (100M atoms, tallies in every launch:
+// 345 us per step, against 416 us with 32-group tiles in four stages and
+// 364 us with one group per thread loaded ahead into registers).  Warps do not wait for one another,
 // so a lane busy with a rare candidate holds up only its own warp.  x is
 // stored back from registers; v_x only where a group's atom collided.
 // Sample steps cut the run into spans of 16384 groups (65536 atoms, the
