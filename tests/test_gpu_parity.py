@@ -204,6 +204,60 @@ def test_one_step_push_parity(prec, record):
     d.close()
 
 
+@pytest.mark.parametrize("ne,ni", [(0, 0), (1, 0), (0, 1), (3, 2), (5, 9)])
+def test_empty_and_tiny_species_steps(ne, ni, record):
+    """Degenerate sizes of the stream: a species with no particle (every CTA of
+    it empty), a single particle, a partial group of four, ionisation children
+    appended after one particle.  Forty full steps (field, push, walls,
+    collisions at 30 Pa: a few elastic events and ionisations) against the
+    oracle: the same particles alive, the same collision and wall counts,
+    Sum q = 2^32 x alive, velocities within 1e-3 and positions within 0.05
+    cells.  (The FP32 field and push differ from the oracle's FP64 by about
+    1e-5 over forty steps; an excitation or ionisation near its threshold
+    amplifies that in the speed it leaves, by eps / (eps - threshold), and
+    ionisation children start at their parent's position, so a slow ion
+    carries its parent's drift.  The test is about the sizes: the counts are
+    exact.)"""
+    ncell = 128
+    cfg = W.ccp_small(n_per_species=1000)
+    cfg.update(n_cells=ncell, pressure_pa=30.0, rf_volt_v=100.0, pos_precision=32, sputter_enable=0,
+               sort_every_e=0, sort_every_i=0, n_e0=0, n_i0=0, cap_e=1024, cap_i=1024,
+               gap_m=0.02, dt=2e-11)
+    d = gpu_discharge(cfg)
+    orc = oracle_for(cfg, cap=1024)
+    sets = {0: W.random_particles(ne, ncell, 0, math.sqrt(30 * QE / ME), 11, 32),
+            1: W.random_particles(ni, ncell, 1, 3e3, 12, 32)}
+    _load_both(d, orc, sets, 32)
+    steps = 40
+    d.step(steps)
+    d.sync()
+    orc.step(steps)
+    c, oc = d.counters(), orc.counters()
+    for k in ("elastic", "excitation", "ionizations", "cx", "iso", "imp_e_l", "imp_e_r", "imp_i_l", "imp_i_r"):
+        assert c[k] == oc[k], (k, c[k], oc[k])
+    for s in (0, 1):
+        g, o, only_g, only_o = match(d.get_species(s), orc.get_species(s))
+        assert len(only_g) == 0 and len(only_o) == 0, (s, len(only_g), len(only_o))
+        if len(o["id"]) == 0:
+            continue
+        vo = np.stack([o["vx"], o["vy"], o["vz"]])
+        vg = np.stack([g["vx"], g["vy"], g["vz"]]).astype(np.float64)
+        scale = np.linalg.norm(vo, axis=0) + 1e4
+        dv = np.linalg.norm(vg - vo, axis=0)
+        record(f"tiny.{ne}_{ni}.species{s}.dv_max_rel", float((dv / scale).max()))
+        assert (dv <= 1e-3 * scale).all(), _worst(dv / scale, o["id"])
+        dxi = np.abs(g["xi"] - o["xi"])
+        record(f"tiny.{ne}_{ni}.species{s}.dx_max_cells", float(dxi.max()))
+        assert (dxi <= 0.05).all(), _worst(dxi, o["id"])
+    # (the field follows the positions: a superparticle of this weight moved by
+    # 0.02 cells shifts E by a few V/m, so only the charge is compared here)
+    f = d.get_field()
+    alive = [len(d.get_species(s)["id"]) for s in (0, 1)]
+    assert int(f["q_e"].sum()) == 2**32 * alive[0] and int(f["q_i"].sum()) == 2**32 * alive[1]
+    assert np.isfinite(f["E"]).all()
+    d.close()
+
+
 # ------------------------------------------------------------------ one-step MCC
 @pytest.mark.parametrize("case", ["electrons", "ions"])
 def test_one_step_collision_parity(case, record):
@@ -330,6 +384,32 @@ def test_tp_transport_parity(tp_mode):
     bad = np.abs(g["vx"] - o["vx"]) > 1e-3 * vmag + 1e-2
     assert bad.sum() <= slack
     assert c["tp_coll"] > 1000 and c["numerics"] == oc["numerics"] == 0
+    d.close()
+
+
+@pytest.mark.parametrize("tp_mode", [0, 1], ids=["thinned", "literal"])
+@pytest.mark.parametrize("n", [1, 3, 6])
+def test_tp_tiny_sources(n, tp_mode):
+    """A source of one to six atoms (one partial group of four, every other
+    CTA of the TP step empty, sample steps among them): 400 TP steps of 20 ns
+    against the oracle, the same atoms deposited at the same electrodes, the
+    same collisions, and the atoms in flight within FP32 rounding."""
+    cfg = W.tp_transport(n_atoms=n)
+    cfg.update(cap_tp=64, n_e0=0, n_i0=0, sort_every_tp=0, tp_mode=tp_mode, tp_dt=2e-8)
+    d = gpu_discharge(cfg)
+    orc = oracle_for(cfg, cap=10, cap_tp=64)
+    d.tp_launch(n, 300.0)
+    orc.tp_launch(n, 300.0)
+    alive = d.tp_step(400)
+    orc.tp_step(400, cfg["tp_dt"])
+    c, oc = d.counters(), orc.counters()
+    for k in ("tp_dep_l", "tp_dep_r", "tp_coll"):
+        assert c[k] == oc[k], (k, c[k], oc[k])
+    assert c["tp_dep_l"] + c["tp_dep_r"] + alive == n
+    g, o, only_g, only_o = match(d.get_species(2), orc.get_species(2))
+    assert len(only_g) == 0 and len(only_o) == 0
+    vmag = np.sqrt(o["vx"]**2 + o["vy"]**2 + o["vz"]**2)
+    assert (np.abs(g["vx"] - o["vx"]) <= 1e-3 * vmag + 1e-2).all()
     d.close()
 
 
