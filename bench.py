@@ -209,6 +209,61 @@ def extra_launches(cfg, h):
     return n
 
 
+def _oracle_all_cores_worker(cfg, n_sample, steps, barrier, out):
+    """One process of oracle_rate_all_cores: build its sample, wait for the
+    others, then time its steps on the wall clock."""
+    import oracle as O
+    from paper_1607_04069_gb300 import workloads as W
+    c = dict(cfg)
+    c["weight"] = cfg["weight"] * cfg["n_e0"] / n_sample
+    orc = O.Oracle(W.oracle_params(c), 2 * n_sample + 65536, 2 * n_sample + 65536, 65536)
+    orc.init_species(0, n_sample, c["te0_ev"])
+    orc.init_species(1, n_sample, c["ti0_ev"])
+    orc.field()
+    orc.step(1)
+    barrier.wait(timeout=300)        # (a sibling that failed breaks it: this one ends too)
+    t0 = time.time()
+    orc.step(steps)
+    t1 = time.time()
+    cnt = orc.counters()
+    out.put(((cnt["n_e"] + cnt["n_i"]) * steps, t0, t1))
+
+
+def oracle_rate_all_cores(cfg, n_sample, steps, limit=180.0):
+    """The oracle as it stands on every logical CPU of the host: one spawned
+    process per CPU, each stepping its own sample of the same discharge, all
+    started together; the rate is their particle-steps over the wall time
+    from the first start to the last end.  None if a process failed or the
+    run took longer than `limit` seconds."""
+    import multiprocessing as mp
+    import queue
+    nproc = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    barrier, out = ctx.Barrier(nproc), ctx.Queue()
+    procs = [ctx.Process(target=_oracle_all_cores_worker, args=(cfg, n_sample, steps, barrier, out))
+             for _ in range(nproc)]
+    for p in procs:
+        p.start()
+    res, deadline = [], time.time() + limit
+    try:
+        while len(res) < nproc and time.time() < deadline:
+            try:
+                res.append(out.get(timeout=1.0))
+            except queue.Empty:
+                if any(p.exitcode not in (None, 0) for p in procs):
+                    break
+    finally:
+        for p in procs:
+            p.join(timeout=5)
+            if p.is_alive():
+                p.terminate()
+                p.join()
+    if len(res) < nproc:
+        return None
+    wall = max(r[2] for r in res) - min(r[1] for r in res)
+    return sum(r[0] for r in res) / wall, nproc, wall
+
+
 def oracle_rate(cfg, n_sample, steps, warmup=1):
     """FP64 oracle on a sample of the same discharge: n_sample superparticles
     per species with the weight scaled so the density is unchanged."""
@@ -741,6 +796,14 @@ def main():
         cpu = {"value": rate, "unit": "particle-steps/s", "cores": 1, "kind": "oracle", **host_cpu(),
                "sample": f"{n_sample}+{n_sample} superparticles of the same discharge, "
                          f"{nst} full PIC/MCC steps in {dt:.1f} s"}
+        # the same oracle on every logical CPU (one process each), for context
+        n_all, st_all = 250_000, 200
+        r = oracle_rate_all_cores(cfg, n_all, st_all)
+        if r is not None:
+            r_all, nproc, wall = r
+            cpu["all_cores"] = {"value": r_all, "unit": "particle-steps/s", "processes": nproc,
+                                "sample": f"{nproc} processes, each {n_all}+{n_all} superparticles of the same "
+                                          f"discharge for {st_all} steps, {wall:.1f} s wall"}
     clocks = clk.summary()
     rows = None
     want = None if args.rows == "all" else set(args.rows.split(","))
