@@ -797,7 +797,7 @@ def main():
                "sample": f"{n_sample}+{n_sample} superparticles of the same discharge, "
                          f"{nst} full PIC/MCC steps in {dt:.1f} s"}
         # the same oracle on every logical CPU (one process each), for context
-        n_all, st_all = 250_000, 200
+        n_all, st_all = 1_000_000, 100           # samples far larger than a core's caches
         r = oracle_rate_all_cores(cfg, n_all, st_all)
         if r is not None:
             r_all, nproc, wall = r
